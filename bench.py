@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the SUPA hot path on GB300: showers/s through
+simulate -> downsample -> fetch of the point clouds.
+
+Workload (default): 1,000,000 showers, E ~ U[1,100], polar angle U[0,30 deg],
+entry within +-1 cell, 30 layers x 3 slices, 30 x 64 x 64 images centred on
+the shower axis, hits handed out in 64M-hit chunks.  One step = one pass of
+the whole path over the batch with inputs resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl supa|reference]
+
+Under torchrun each rank develops its own batch (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "showers/s"
+FETCH_CHUNK = 64 << 20  # hits per supa_fetch_hits call (1 GiB of float4)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="supa", choices=["supa", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c5"])
+    ap.add_argument("--showers", type=int, default=0, help="override the batch size")
+    ap.add_argument("--voxel-chunk", type=int, default=32768)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(name: str, n: int):
+    from paper_2202_05012_gb300 import inputs
+    if name == "c1":
+        g, p = inputs.workload_c1(n or 1000)
+        return g, p, 0, dict(workload="plain SUPA, 1k showers, E U[1,10], 10 layers, 10x32x32", seed=0)
+    if name == "c5":
+        g, p = inputs.workload_c5(n or 200_000)
+        return g, p, 4, dict(workload="plain SUPA, E log-U[10,1000], 0-45 deg, 50 layers, 50x128x128", seed=4)
+    g, p = inputs.workload_c2(n or 1_000_000)
+    return g, p, 1, dict(workload="plain SUPA, 1M showers, E U[1,100], 0-30 deg, +-1 cell entry, 30 layers, "
+                                  "30x64x64 axis-centred images, 64M-hit chunks", seed=1)
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def stored_traffic(kernel: str, workload_key: str):
+    """DRAM bytes per launch from a committed ncu capture, valid only while the
+    kernel source is unchanged (sha256 of its translation unit)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel][workload_key]
+    except (OSError, ValueError, KeyError):
+        return None
+    src = os.path.join(ROOT, "paper_2202_05012_gb300", "csrc", rec["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+
+
+# ------------------------------------------------------------------ oracle ---
+
+def oracle_sample(geom, prims, seed, seconds, chunk=500):
+    """Time the FP64 oracle (simulate on all host cores, then downsample) on
+    consecutive chunks of the workload until `seconds` have passed."""
+    import oracle
+    threads = os.cpu_count() or 1
+    done, t0 = 0, time.perf_counter()
+    steps = 0
+    while done < len(prims):
+        p = prims[done:done + chunk]
+        r = oracle.simulate(geom, p, seed, shower_id_base=done, n_threads=threads)
+        rx, ry = oracle.roi_origins(geom, p)
+        oracle.voxelize(r["x"], r["y"], r["z"], r["E"], r["offsets"], geom, rx, ry)
+        steps += int(r["steps"].sum())
+        done += len(p)
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, steps / dt, done, dt, threads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    geom, prims, seed, conf = workload(args.workload, args.showers)
+    per_step = max(1, int(args.cpu_seconds / max(args.steps, 1)))
+    for _ in range(args.warmup):
+        oracle_sample(geom, prims[:200], seed, 0.0, chunk=200)
+    vals, n_done, t_tot = [], 0, 0.0
+    for k in range(args.steps):
+        v, sps, done, dt, threads = oracle_sample(geom, prims, seed, per_step)
+        vals.append(v)
+        n_done += done
+        t_tot += dt
+    value = n_done / t_tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "showers/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": conf,
+        "cpu_baseline": {"value": value, "unit": "showers/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {done} showers of the workload per step (simulate on {threads} threads, "
+                                   f"downsample single-threaded)"},
+        "e2e": {"value": value, "unit": "showers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm ---
+
+def run_supa(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2202_05012_gb300 import supa as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    geom, prims, seed, conf = workload(args.workload, args.showers)
+    n = len(prims)
+    base = rank * n  # each rank develops its own showers (global ids differ)
+    if world > 1:
+        from paper_2202_05012_gb300 import inputs
+        prims = inputs.primaries(n, seed + 1000 * rank, e_lo=float(prims["E"].min()), e_hi=float(prims["E"].max()))
+    L, ny, nx = geom.n_layers, geom.ny, geom.nx
+    gh = S.supa_init_geometry(geom)
+    max_hits = int(n * {"c1": 400, "c2": 1500, "c5": 9000}[args.workload]) + (8 << 20)
+    b = S.supa_batch_create([gh], n, {"max_hits": max_hits, "lpt_order": 1})
+    d_prim = S.primaries_to_device(prims)
+    V = min(args.voxel_chunk, n)
+    grid = torch.empty((V, L, ny, nx), dtype=torch.float32, device="cuda")
+    oor = torch.empty(V, dtype=torch.float64, device="cuda")
+    fbuf = torch.empty((FETCH_CHUNK, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev["sim0"].record(stream)
+        S.supa_simulate(b, d_prim, n, seed, base)
+        if ev is not None:
+            ev["sim1"].record(stream)
+        info = S.supa_batch_get_info(b)
+        launches = 1 + 3 + 3  # step kernel, offset scan, energy-ordered queue
+        vox_ms = 0.0
+        for c0 in range(0, n, V):
+            c1 = min(n, c0 + V)
+            if ev is not None:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            S.supa_voxelize(b, c0, c1, grid, oor)
+            launches += 1
+            if ev is not None:
+                e1.record(stream)
+                ev["vox"].append((e0, e1, c1 - c0))
+        for h0 in range(0, info.n_hits, FETCH_CHUNK):
+            S.supa_fetch_hits(b, h0, FETCH_CHUNK, fbuf)
+            launches += 1
+        return info, launches
+
+    for _ in range(args.warmup):
+        info, _ = step()
+    torch.cuda.synchronize()
+    n_hits, n_steps = info.n_hits, info.n_steps
+    hits_per_shower = n_hits / n
+
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = []
+    t_start.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        ev = {"sim0": torch.cuda.Event(enable_timing=True), "sim1": torch.cuda.Event(enable_timing=True), "vox": []}
+        info, nl = step(ev)
+        launches += nl
+        evs.append(ev)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    sim_ms = sum(e["sim0"].elapsed_time(e["sim1"]) for e in evs) / args.steps
+    vox_launch = [(a.elapsed_time(c), m) for e in evs for (a, c, m) in e["vox"]]
+    vox_ms = sum(x for x, _ in vox_launch) / args.steps
+    value = args.steps * n * world / (elapsed_ms / 1000.0)
+
+    # roofline of the dominant kernel (the downsampling kernel, HBM-write bound):
+    # algorithmic bytes = images written + hits read + out-of-region sums
+    pk, pk_kind = peaks()
+    full = [(x, m) for x, m in vox_launch if m == V] or vox_launch
+    avg_ms = sum(x for x, _ in full) / len(full)
+    bytes_per_shower = L * ny * nx * 4 + 16 * hits_per_shower + 8
+    achieved = full[0][1] * bytes_per_shower / (avg_ms / 1000.0) / 1e9
+    traffic = stored_traffic("supa_voxel_kernel", args.workload)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": "supa_voxel_kernel",
+            "peak_source": pk_kind, "bytes_per_shower": bytes_per_shower, "showers_per_launch": full[0][1]}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "showers/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(conf, showers=n, layers=L, grid=[L, ny, nx], fetch_chunk_hits=FETCH_CHUNK,
+                       voxel_chunk_showers=V, l2="inputs larger than L2 (hit pool and image chunks >> 129 MB)",
+                       parallelism=f"replicas x{world}"),
+        "particle_steps_per_s": n_steps * args.steps * world / (elapsed_ms / 1000.0),
+        "hits_per_shower": hits_per_shower, "steps_per_shower": n_steps / n,
+        "phase_ms": {"simulate": sim_ms, "voxelize": vox_ms, "step_total": elapsed_ms / args.steps},
+        "simulate_showers_per_s": n / (sim_ms / 1000.0),
+        "simulate_particle_steps_per_s": n_steps / (sim_ms / 1000.0),
+        "roofline": roof, "gpu_launches": launches, "clocks": clk,
+    }
+
+    if not args.no_e2e:
+        out["e2e"] = e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sps, done, dt, threads = oracle_sample(geom, prims, seed, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": "showers/s", "cores": threads, "kind": "oracle",
+                               "sample": f"first {done} showers of this workload in {dt:.1f} s (simulate on "
+                                         f"{threads} threads, downsample single-threaded)",
+                               "particle_steps_per_s": sps}
+    S.supa_destroy_batch(b)
+    S.supa_destroy_geometry(gh)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
+    """Same metric through the public API with host buffers: primaries copied
+    from pinned host memory each step, the point cloud (all hits) and the
+    per-shower FP64 layer sums read back to pinned host memory.  Images stay
+    on the device, consumed chunk by chunk."""
+    import torch
+    import torch.distributed as dist
+    h_prim = torch.from_numpy(np.ascontiguousarray(prims).view(np.uint8)).pin_memory()
+    d_prim = torch.empty_like(h_prim, device="cuda")
+    info = S.supa_batch_get_info(b)
+    cap = int(info.n_hits * 1.05) + 1024
+    h_hits = torch.empty((cap, 4), dtype=torch.float32, pin_memory=True)
+    h_ls = torch.empty((n, geom.n_layers), dtype=torch.float64, pin_memory=True)
+    stream = torch.cuda.current_stream()
+    h2d = d2h = 0
+
+    def step():
+        nonlocal h2d, d2h
+        d_prim.copy_(h_prim, non_blocking=True)
+        S.supa_simulate(b, d_prim, n, seed, base)
+        inf = S.supa_batch_get_info(b)
+        for c0 in range(0, n, V):
+            S.supa_voxelize(b, c0, min(n, c0 + V), grid, oor)
+        got = 0
+        while got < inf.n_hits:
+            m = S.supa_fetch_hits(b, got, min(FETCH_CHUNK, cap - got), h_hits[got:], dst_is_device=False)
+            got += m
+            if m == 0:
+                break
+        ls = S.info_arrays(inf)["layer_sum"]
+        h_ls.copy_(ls, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d = h_prim.numel()
+        d2h = inf.n_hits * 16 + h_ls.numel() * 8
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    return {"value": args.steps * n * world / dt, "unit": "showers/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_supa(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * supa.h -- C ABI of the GB300 SUPA shower library (libsupa.so).
+ *
+ * SUPA (Sinha et al., "SUPA: A Lightweight Diagnostic Simulator for Machine
+ * Learning in Particle Physics", arXiv 2202.05012) develops a shower by
+ * applying one rule to every live particle at every slice of a layered
+ * detector (Sec. 3, Algorithm 1): stop and deposit the energy, split into two
+ * daughters, or pass through.  Deposits are grouped into readout layers
+ * (Sec. 3, "layer configuration") and can be downsampled into per-layer
+ * images (App. A.5, "Downsampling").  This library runs that process for
+ * batches of showers on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - The return value is a status: SUPA_OK (0) or a negative SUPA_ERR_* code.
+ *    supa_last_error() gives a message for the last failure on the calling
+ *    thread.
+ *  - Pointers named *_dev are device pointers; every other pointer is a host
+ *    pointer.  Buffers passed in stay owned by the caller; the library only
+ *    reads inputs and writes outputs.  Handles (supa_geometry, supa_batch)
+ *    are created and destroyed by the library.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    that take a stream are asynchronous on it unless stated otherwise;
+ *    device-side errors (pool overflow) surface at the next synchronising
+ *    call on the batch (supa_batch_get_info).
+ *  - Layouts: a hit is four float32 (x, y, z, E) = 16 bytes; images are
+ *    float32 [shower][layer][ny][nx] with x fastest.
+ */
+#ifndef SUPA_H
+#define SUPA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SUPA_OK 0
+#define SUPA_ERR_INVALID_ARG (-1)
+#define SUPA_ERR_OOM (-2)
+#define SUPA_ERR_OVERFLOW (-3)
+#define SUPA_ERR_TIMEOUT (-4)
+#define SUPA_ERR_CUDA (-5)
+#define SUPA_ERR_NOT_READY (-6)
+
+#define SUPA_MAX_SLICES 255
+#define SUPA_MAX_LAYERS 64
+#define SUPA_MAX_GEOMS 8
+
+/* Split-angle laws p_theta and p_eps (Algorithm 1 "Parameters"; Table 2). */
+#define SUPA_THETA_FIXED 0   /* theta = theta_lo                          */
+#define SUPA_THETA_UNIFORM 1 /* theta ~ U(theta_lo, theta_hi)             */
+#define SUPA_EPS_ZERO 0      /* eps = 0: symmetric splits (SUPAv1, v2)    */
+#define SUPA_EPS_UNIFORM 1   /* eps ~ U(-f theta, f theta), f = eps_frac  */
+/* Daughter kinematics (Sec. 3 "momentum conservation"; Algorithm 1).
+ * MOMENTUM: daughter 0 gets E(theta/2+eps)/theta and is deflected by
+ * theta/2-eps at azimuth omega, daughter 1 gets the rest and is deflected by
+ * theta/2+eps at omega+pi (opening angle theta, E_0 delta_0 = E_1 delta_1).
+ * LITERAL: both deflected by theta/2+eps, as the position lines of
+ * Algorithm 1 read. */
+#define SUPA_SPLIT_MOMENTUM 0
+#define SUPA_SPLIT_LITERAL 1
+/* Region of interest of each layer image (App. A.5). */
+#define SUPA_ROI_FIXED 0 /* centred on the z axis                           */
+#define SUPA_ROI_AXIS 1  /* centred on the incidence axis at mid-layer depth */
+
+/* Geometry and model parameters (Algorithm 1 "Parameters"; Sec. 4.2 dead
+ * material).  All arrays are host arrays of n_slices entries, copied. */
+typedef struct {
+    int32_t n_slices;              /* slices z_k = k*dz, k = 0..n_slices-1 (1..255) */
+    float dz;                      /* slice gap Delta z (> 0)                       */
+    const int32_t *slice_to_layer; /* layer of each slice, -1 = dead material       */
+    int32_t n_layers;              /* readout layers (1..64)                        */
+    const double *p_stop;          /* p_stop[k] in [0,1]                            */
+    const double *p_split;         /* p_split[k], p_stop[k] + p_split[k] <= 1       */
+    int32_t theta_mode;            /* SUPA_THETA_*                                  */
+    double theta_lo, theta_hi;     /* radians, 0 < theta_lo <= theta_hi < pi/2      */
+    int32_t eps_mode;              /* SUPA_EPS_*                                    */
+    double eps_frac;               /* 0 <= eps_frac < 1/2                           */
+    int32_t split_mode;            /* SUPA_SPLIT_*                                  */
+    double e_min;                  /* energy cut: E < e_min stops (0 = no cut)      */
+    double uz_min;                 /* a survivor with u_z <= uz_min escapes (> 0)   */
+    int32_t nx, ny;                /* image cells per layer; nx*ny multiple of 4    */
+    float wx, wy;                  /* cell size                                     */
+    int32_t roi_mode;              /* SUPA_ROI_*                                    */
+} supa_geometry_desc;
+
+/* One primary particle (Sec. 3 initial particle; Sec. 4.2 conditioning on
+ * impact energy, angle and position): energy, impact point on slice 0, polar
+ * angle from the z axis and azimuth (radians), index into the launch's
+ * geometry list.  24 bytes, no padding. */
+typedef struct {
+    float E, x0, y0, theta, phi;
+    uint32_t geom;
+} supa_primary;
+
+/* Launch tuning; zero fields pick defaults (or the autotuned values). */
+typedef struct {
+    int32_t warps_per_block; /* warps of the persistent step kernel          */
+    int32_t blocks_per_sm;   /* resident step-kernel blocks per SM           */
+    int32_t stack_depth;     /* particles held per warp in shared memory     */
+    int32_t flush_threshold; /* staged hits per warp before a flush to HBM   */
+    int32_t record_tags;     /* 1: also keep each hit's lineage id           */
+    int32_t lpt_order;       /* 1: hand out showers by decreasing energy     */
+    int64_t max_hits;        /* hit pool capacity (0: sized from free memory)*/
+} supa_launch_config;
+
+/* Per-batch results after a simulation (device pointers stay owned by the
+ * batch and valid until the next simulation or supa_destroy_batch). */
+typedef struct {
+    int64_t n_showers;
+    int64_t n_hits;             /* total hits                                  */
+    int64_t n_steps;            /* particle-slice visits (particle-steps)      */
+    int32_t max_layers;         /* stride of layer_sums_dev                    */
+    int32_t status;             /* SUPA_OK or the device-side error            */
+    const int64_t *offsets_dev; /* [n+1] first hit of each shower, shower order */
+    const uint32_t *counts_dev; /* [n] hits per shower                         */
+    const uint32_t *steps_dev;  /* [n] particle-steps per shower               */
+    const double *layer_sums_dev; /* [n][max_layers] FP64 deposit per layer    */
+    const double *dead_dev;     /* [n] energy stopped in dead slices           */
+    const double *leak_dev;     /* [n] energy alive after the last slice       */
+    const double *escape_dev;   /* [n] energy of escaped particles             */
+} supa_batch_info;
+
+typedef struct supa_geometry supa_geometry;
+typedef struct supa_batch supa_batch;
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *supa_last_error(void);
+
+/* Validate a geometry and upload its per-slice tables (thresholds for the
+ * stop/split/pass draw of Algorithm 1).  Rejects p outside [0,1],
+ * p_stop + p_split > 1, layer ids out of range, and parameters whose lineage
+ * ids could exceed 64 bits (more than 62 splits on one path). */
+int supa_init_geometry(const supa_geometry_desc *desc, supa_geometry **out);
+int supa_destroy_geometry(supa_geometry *g);
+
+/* Allocate a reusable batch for up to max_showers showers over the given
+ * geometries (1..SUPA_MAX_GEOMS, which must outlive the batch).  cfg may be
+ * NULL.  Synchronous (allocates device memory). */
+int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_t max_showers,
+                      const supa_launch_config *cfg, supa_batch **out);
+int supa_destroy_batch(supa_batch *b);
+
+/* Develop n showers (Algorithm 1 applied to every particle at every slice,
+ * Sec. 3).  Shower i uses primary prim_dev[i] and the global id
+ * shower_id_base + i, which keys its random stream together with the slice
+ * and the particle's lineage id, so any shower can be replayed alone.
+ * Asynchronous on `stream`; launches kernels only (no allocation, no host
+ * synchronisation), so it can be captured in a CUDA graph. */
+int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64_t seed,
+                  uint64_t shower_id_base, void *stream);
+
+/* supa_batch_create + supa_simulate in one call; *out must be destroyed with
+ * supa_destroy_batch. */
+int supa_simulate_batch(const supa_geometry *const *geoms, int32_t n_geoms, const supa_primary *prim_dev,
+                        int64_t n, uint64_t seed, uint64_t shower_id_base, const supa_launch_config *cfg,
+                        supa_batch **out, void *stream);
+
+/* Wait for the batch's last simulation on `stream` and report totals and
+ * result pointers.  Returns SUPA_ERR_OVERFLOW if the hit pool or a particle
+ * stack overflowed (re-run with a smaller batch or a larger max_hits). */
+int supa_batch_get_info(supa_batch *b, supa_batch_info *info, void *stream);
+
+/* Copy hits [first_hit, first_hit + max_hits) of the batch, in shower order
+ * (the point cloud of Sec. 3: each hit is (x, y, z, E)), into dst, a device
+ * buffer if dst_is_device else a host buffer.  *n_written receives the count
+ * (fewer at the end of the batch).  Requires supa_batch_get_info first. */
+int supa_fetch_hits(supa_batch *b, int64_t first_hit, int64_t max_hits, void *dst, int32_t dst_is_device,
+                    int64_t *n_written, void *stream);
+
+/* Same ranges as supa_fetch_hits, lineage ids (uint64) of the hits; needs
+ * record_tags = 1 at batch creation. */
+int supa_fetch_hit_tags(supa_batch *b, int64_t first_hit, int64_t max_hits, uint64_t *dst_dev,
+                        int64_t *n_written, void *stream);
+
+/* Downsample showers [shower_begin, shower_end) of the batch into images
+ * (App. A.5: per layer, a rectangular region of nx x ny cells; each cell sums
+ * the energy of the points inside it).  grid_dev is float32
+ * [shower_end - shower_begin][max_layers][ny][nx]; out_of_roi_dev (may be
+ * NULL) receives per shower the FP64 energy outside every region.  All
+ * geometries of the batch must share nx, ny, wx, wy.  Every cell is written. */
+int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev,
+                  double *out_of_roi_dev, void *stream);
+
+/* Downsample caller-provided hits: hits_dev float4 (x,y,z,E), shower s owns
+ * hits [offsets_dev[s], offsets_dev[s+1]); a hit's layer is
+ * slice_to_layer[rint(z/dz)] of geometry g; roi_x0_dev/roi_y0_dev are the low
+ * corners of each region, float32 [n_showers][n_layers].  grid_dev is float32
+ * [n_showers][n_layers][ny][nx]. */
+int supa_voxelize_hits(const supa_geometry *g, const float *hits_dev, const int64_t *offsets_dev,
+                       int64_t n_showers, const float *roi_x0_dev, const float *roi_y0_dev, float *grid_dev,
+                       double *out_of_roi_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUPA_H */

@@ -1,0 +1,621 @@
+// api.cu -- host implementation of the C ABI declared in include/supa.h.
+//
+// Owns geometry tables and batch buffers, validates arguments, sizes the
+// persistent launch, and maps device-side error words to status codes.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "supa_internal.cuh"
+
+using namespace supa;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(SUPA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SUPA_CUDA(call)                                              \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+// Threshold for "alpha < p" with alpha = r0 * 2^-32 and r0 a 32-bit word:
+// r0 < p*2^32 <=> r0 < ceil(p*2^32) (the scaling by 2^32 is exact).
+unsigned long long threshold(double p) {
+    const double v = std::ceil(p * 4294967296.0);
+    if (v <= 0.0) return 0ull;
+    if (v >= 4294967296.0) return 4294967296ull;
+    return (unsigned long long)v;
+}
+
+}  // namespace
+
+struct supa_geometry {
+    GeomDev rec;  // slice_off = layer_off = 0
+    std::vector<unsigned long long> t_stop, t_ss;
+    std::vector<int8_t> s2l;
+    std::vector<float> zmid;
+    int device = 0;
+    GeomDev *d_rec = nullptr;
+    unsigned long long *d_tstop = nullptr, *d_tss = nullptr;
+    int8_t *d_s2l = nullptr;
+    float *d_zmid = nullptr;
+};
+
+struct supa_batch {
+    int device = 0;
+    std::vector<const supa_geometry *> geoms;
+    int64_t max_showers = 0;
+    int max_layers = 1;
+    bool tags = false, lpt = false;
+    // tables
+    GeomDev *d_geoms = nullptr;
+    unsigned long long *d_tstop = nullptr, *d_tss = nullptr;
+    int8_t *d_s2l = nullptr;
+    float *d_zmid = nullptr;
+    // inputs
+    supa_primary *d_prim = nullptr;
+    uint32_t *d_queue = nullptr, *d_bucket = nullptr;
+    // hit pool
+    float4 *d_pool = nullptr;
+    unsigned long long *d_tags = nullptr;
+    int *d_page_next = nullptr;
+    int n_pages = 0;
+    // per shower
+    unsigned long long *d_hit_start = nullptr;
+    uint32_t *d_hit_count = nullptr, *d_steps = nullptr;
+    double *d_lsum = nullptr, *d_dead = nullptr, *d_leak = nullptr, *d_escape = nullptr;
+    int64_t *d_offsets = nullptr;
+    unsigned long long *d_scan_tmp = nullptr;
+    // control: [0] queue head, [1] page counter, [2] error; totals [0] steps, [1] hits
+    int *d_ctrl = nullptr;
+    unsigned long long *d_totals = nullptr;
+    SpillRec *d_spill = nullptr;
+    int spill_cap = 0;
+    // launch shape
+    int grid = 0, block = 0, stack_cap = 0, stage_cap = 0, flush_thr = 0;
+    size_t smem = 0;
+    int warp_bytes = 0;
+    // state
+    int64_t last_n = -1;
+    bool info_valid = false;
+    int64_t n_hits = 0, n_steps = 0;
+    float4 *d_stage = nullptr;
+    int64_t stage_cap_hits = 0;
+};
+
+extern "C" {
+
+const char *supa_last_error(void) { return g_last_error.c_str(); }
+
+int supa_init_geometry(const supa_geometry_desc *d, supa_geometry **out) {
+    if (!d || !out) return fail(SUPA_ERR_INVALID_ARG, "supa_init_geometry: null argument");
+    *out = nullptr;
+    if (d->n_slices < 1 || d->n_slices > SUPA_MAX_SLICES)
+        return fail(SUPA_ERR_INVALID_ARG, "n_slices must be in [1, %d], got %d", SUPA_MAX_SLICES, d->n_slices);
+    if (d->n_layers < 1 || d->n_layers > SUPA_MAX_LAYERS)
+        return fail(SUPA_ERR_INVALID_ARG, "n_layers must be in [1, %d], got %d", SUPA_MAX_LAYERS, d->n_layers);
+    if (!d->slice_to_layer || !d->p_stop || !d->p_split)
+        return fail(SUPA_ERR_INVALID_ARG, "slice_to_layer, p_stop and p_split are required");
+    if (!(d->dz > 0.0f) || !std::isfinite(d->dz)) return fail(SUPA_ERR_INVALID_ARG, "dz must be positive");
+    if (d->theta_mode != SUPA_THETA_FIXED && d->theta_mode != SUPA_THETA_UNIFORM)
+        return fail(SUPA_ERR_INVALID_ARG, "unknown theta_mode %d", d->theta_mode);
+    if (d->eps_mode != SUPA_EPS_ZERO && d->eps_mode != SUPA_EPS_UNIFORM)
+        return fail(SUPA_ERR_INVALID_ARG, "unknown eps_mode %d", d->eps_mode);
+    if (d->split_mode != SUPA_SPLIT_MOMENTUM && d->split_mode != SUPA_SPLIT_LITERAL)
+        return fail(SUPA_ERR_INVALID_ARG, "unknown split_mode %d", d->split_mode);
+    if (d->roi_mode != SUPA_ROI_FIXED && d->roi_mode != SUPA_ROI_AXIS)
+        return fail(SUPA_ERR_INVALID_ARG, "unknown roi_mode %d", d->roi_mode);
+    const double th_hi = d->theta_mode == SUPA_THETA_FIXED ? d->theta_lo : d->theta_hi;
+    if (!(d->theta_lo > 0.0) || !(th_hi >= d->theta_lo) || !(th_hi < M_PI / 2))
+        return fail(SUPA_ERR_INVALID_ARG, "need 0 < theta_lo <= theta_hi < pi/2");
+    const double ef = d->eps_mode == SUPA_EPS_UNIFORM ? d->eps_frac : 0.0;
+    if (!(ef >= 0.0 && ef < 0.5)) return fail(SUPA_ERR_INVALID_ARG, "eps_frac must be in [0, 1/2)");
+    if (!(d->e_min >= 0.0) || !std::isfinite(d->e_min)) return fail(SUPA_ERR_INVALID_ARG, "e_min must be >= 0");
+    if (!(d->uz_min > 0.0 && d->uz_min < 1.0)) return fail(SUPA_ERR_INVALID_ARG, "uz_min must be in (0, 1)");
+    if (d->nx < 1 || d->ny < 1 || (int64_t)d->nx * d->ny % 4 != 0 || (int64_t)d->nx * d->ny > (1 << 24))
+        return fail(SUPA_ERR_INVALID_ARG, "nx*ny must be a positive multiple of 4 (got %d x %d)", d->nx, d->ny);
+    if (!(d->wx > 0.0f) || !(d->wy > 0.0f)) return fail(SUPA_ERR_INVALID_ARG, "cell sizes must be positive");
+    // Lineage ids are heap indices (primary 1, daughters 2l, 2l+1) held in
+    // 64 bits: at most 62 splits on one path.  Without an energy cut a path
+    // splits at most once per slice.
+    if (d->n_slices > 62 && !(d->e_min > 0.0))
+        return fail(SUPA_ERR_INVALID_ARG, "more than 62 slices needs e_min > 0 to bound the lineage depth");
+
+    supa_geometry *g = new supa_geometry();
+    const int n = d->n_slices;
+    g->t_stop.resize(n);
+    g->t_ss.resize(n);
+    g->s2l.resize(n);
+    std::vector<int> kmin(d->n_layers, 1 << 30), kmax(d->n_layers, -1);
+    for (int k = 0; k < n; ++k) {
+        const double ps = d->p_stop[k], pp = d->p_split[k];
+        if (!(ps >= 0.0 && ps <= 1.0 && pp >= 0.0 && pp <= 1.0) || ps + pp > 1.0 + 1e-12) {
+            delete g;
+            return fail(SUPA_ERR_INVALID_ARG, "slice %d: need p_stop, p_split in [0,1] and p_stop + p_split <= 1", k);
+        }
+        const int l = d->slice_to_layer[k];
+        if (l < -1 || l >= d->n_layers) {
+            delete g;
+            return fail(SUPA_ERR_INVALID_ARG, "slice %d: layer %d out of range", k, l);
+        }
+        g->t_stop[k] = threshold(ps);
+        g->t_ss[k] = threshold(ps + pp);
+        g->s2l[k] = (int8_t)l;
+        if (l >= 0) {
+            kmin[l] = std::min(kmin[l], k);
+            kmax[l] = std::max(kmax[l], k);
+        }
+    }
+    g->zmid.resize(d->n_layers);
+    for (int l = 0; l < d->n_layers; ++l) {
+        if (kmax[l] < 0) {
+            delete g;
+            return fail(SUPA_ERR_INVALID_ARG, "layer %d has no slice", l);
+        }
+        // mid depth of the layer, float32 as the downsampling kernel uses it
+        g->zmid[l] = (d->dz * (float)(kmin[l] + kmax[l])) * 0.5f;
+    }
+    GeomDev &r = g->rec;
+    r.n_slices = n;
+    r.n_layers = d->n_layers;
+    r.slice_off = 0;
+    r.layer_off = 0;
+    r.dz = d->dz;
+    r.e_min = (float)d->e_min;
+    r.uz_min = (float)d->uz_min;
+    r.theta_lo = (float)d->theta_lo;
+    r.theta_span = d->theta_mode == SUPA_THETA_UNIFORM ? (float)(d->theta_hi - d->theta_lo) : 0.0f;
+    r.eps_frac = (float)ef;
+    r.split_literal = d->split_mode == SUPA_SPLIT_LITERAL;
+    r.nx = d->nx;
+    r.ny = d->ny;
+    r.wx = d->wx;
+    r.wy = d->wy;
+    r.roi_axis = d->roi_mode == SUPA_ROI_AXIS;
+    // Each split leaves a daughter at most q = 1/2 + eps_frac of its parent's
+    // energy and only particles with E >= e_min split, so a primary below
+    // e_min * q^-61 splits at most 62 times on any path.
+    r.e0_max = d->n_slices <= 62 ? INFINITY : (float)std::min(3.0e38, d->e_min * std::pow(0.5 + ef, -61.0));
+
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = dalloc(&g->d_rec, 1);
+    if (e == cudaSuccess) e = dalloc(&g->d_tstop, n);
+    if (e == cudaSuccess) e = dalloc(&g->d_tss, n);
+    if (e == cudaSuccess) e = dalloc(&g->d_s2l, n);
+    if (e == cudaSuccess) e = dalloc(&g->d_zmid, d->n_layers);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_rec, &g->rec, sizeof(GeomDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_tstop, g->t_stop.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_tss, g->t_ss.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_s2l, g->s2l.data(), n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_zmid, g->zmid.data(), d->n_layers * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        supa_destroy_geometry(g);
+        return cuda_fail(e, "supa_init_geometry");
+    }
+    *out = g;
+    return SUPA_OK;
+}
+
+int supa_destroy_geometry(supa_geometry *g) {
+    if (!g) return SUPA_OK;
+    cudaFree(g->d_rec);
+    cudaFree(g->d_tstop);
+    cudaFree(g->d_tss);
+    cudaFree(g->d_s2l);
+    cudaFree(g->d_zmid);
+    delete g;
+    return SUPA_OK;
+}
+
+int supa_destroy_batch(supa_batch *b) {
+    if (!b) return SUPA_OK;
+    void *ptrs[] = {b->d_geoms, b->d_tstop, b->d_tss, b->d_s2l, b->d_zmid, b->d_prim, b->d_queue,
+                    b->d_bucket, b->d_pool, b->d_tags, b->d_page_next, b->d_hit_start, b->d_hit_count,
+                    b->d_steps, b->d_lsum, b->d_dead, b->d_leak, b->d_escape, b->d_offsets, b->d_scan_tmp,
+                    b->d_ctrl, b->d_totals, b->d_spill, b->d_stage};
+    for (void *p : ptrs) cudaFree(p);
+    delete b;
+    return SUPA_OK;
+}
+
+int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_t max_showers,
+                      const supa_launch_config *cfg_in, supa_batch **out) {
+    if (!geoms || !out) return fail(SUPA_ERR_INVALID_ARG, "supa_batch_create: null argument");
+    *out = nullptr;
+    if (n_geoms < 1 || n_geoms > SUPA_MAX_GEOMS)
+        return fail(SUPA_ERR_INVALID_ARG, "n_geoms must be in [1, %d]", SUPA_MAX_GEOMS);
+    if (max_showers < 1 || max_showers > ((int64_t)1 << 32) - 1)
+        return fail(SUPA_ERR_INVALID_ARG, "max_showers must be in [1, 2^32)");
+    supa_launch_config cfg{};
+    if (cfg_in) cfg = *cfg_in;
+    for (int i = 0; i < n_geoms; ++i)
+        if (!geoms[i]) return fail(SUPA_ERR_INVALID_ARG, "geometry %d is null", i);
+
+    supa_batch *b = new supa_batch();
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    b->geoms.assign(geoms, geoms + n_geoms);
+    b->max_showers = max_showers;
+    b->tags = cfg.record_tags != 0;
+    b->lpt = cfg.lpt_order != 0;
+
+    // concatenated geometry tables
+    std::vector<GeomDev> recs;
+    std::vector<unsigned long long> ts, tss;
+    std::vector<int8_t> s2l;
+    std::vector<float> zm;
+    for (int i = 0; i < n_geoms; ++i) {
+        GeomDev r = geoms[i]->rec;
+        r.slice_off = (int)ts.size();
+        r.layer_off = (int)zm.size();
+        recs.push_back(r);
+        ts.insert(ts.end(), geoms[i]->t_stop.begin(), geoms[i]->t_stop.end());
+        tss.insert(tss.end(), geoms[i]->t_ss.begin(), geoms[i]->t_ss.end());
+        s2l.insert(s2l.end(), geoms[i]->s2l.begin(), geoms[i]->s2l.end());
+        zm.insert(zm.end(), geoms[i]->zmid.begin(), geoms[i]->zmid.end());
+        b->max_layers = std::max(b->max_layers, r.n_layers);
+    }
+
+    // launch shape
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    const int wpb = cfg.warps_per_block > 0 ? cfg.warps_per_block : 8;
+    if (wpb > 16) {
+        supa_destroy_batch(b);
+        return fail(SUPA_ERR_INVALID_ARG, "warps_per_block must be <= 16");
+    }
+    b->block = wpb * 32;
+    b->stack_cap = cfg.stack_depth > 0 ? cfg.stack_depth : 128;
+    if (b->stack_cap < 64 || b->stack_cap % 2) {
+        supa_destroy_batch(b);
+        return fail(SUPA_ERR_INVALID_ARG, "stack_depth must be an even number >= 64");
+    }
+    b->flush_thr = cfg.flush_threshold > 0 ? cfg.flush_threshold : 64;
+    b->stage_cap = b->flush_thr + 32;
+    b->warp_bytes = (int)warp_smem_bytes(b->stack_cap, b->stage_cap, b->tags);
+    b->smem = (size_t)b->warp_bytes * wpb;
+    int occ = 0;
+    e = step_kernel_attributes(b->block, b->smem, &occ);
+    if (e != cudaSuccess || occ < 1) {
+        supa_destroy_batch(b);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel occupancy");
+        return fail(SUPA_ERR_INVALID_ARG, "step kernel does not fit on an SM (%zu B shared memory)", b->smem);
+    }
+    const int bps = cfg.blocks_per_sm > 0 ? std::min(cfg.blocks_per_sm, occ) : occ;
+    b->grid = bps * sms;
+    const int64_t n_warps = (int64_t)b->grid * wpb;
+    b->spill_cap = 2048;
+
+    // hit pool
+    int64_t max_hits = cfg.max_hits;
+    if (max_hits <= 0) {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const int64_t want = max_showers * 2048 + (4 << 20);
+        const int64_t cap = (int64_t)(free_b * 0.4) / (b->tags ? 24 : 16);
+        max_hits = std::min(want, cap);
+    }
+    b->n_pages = (int)((max_hits + kPageHits - 1) / kPageHits + n_warps + 1);
+
+    const int64_t n = max_showers;
+    if (e == cudaSuccess) e = dalloc(&b->d_geoms, n_geoms);
+    if (e == cudaSuccess) e = dalloc(&b->d_tstop, ts.size());
+    if (e == cudaSuccess) e = dalloc(&b->d_tss, tss.size());
+    if (e == cudaSuccess) e = dalloc(&b->d_s2l, s2l.size());
+    if (e == cudaSuccess) e = dalloc(&b->d_zmid, zm.size());
+    if (e == cudaSuccess) e = dalloc(&b->d_prim, n);
+    if (e == cudaSuccess && b->lpt) e = dalloc(&b->d_queue, n);
+    if (e == cudaSuccess && b->lpt) e = dalloc(&b->d_bucket, 256);
+    if (e == cudaSuccess) e = dalloc(&b->d_pool, (size_t)b->n_pages * kPageHits);
+    if (e == cudaSuccess && b->tags) e = dalloc(&b->d_tags, (size_t)b->n_pages * kPageHits);
+    if (e == cudaSuccess) e = dalloc(&b->d_page_next, b->n_pages);
+    if (e == cudaSuccess) e = dalloc(&b->d_hit_start, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_hit_count, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_steps, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_lsum, (size_t)n * b->max_layers);
+    if (e == cudaSuccess) e = dalloc(&b->d_dead, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_leak, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_escape, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_offsets, n + 1);
+    if (e == cudaSuccess) e = dalloc(&b->d_scan_tmp, scan_tmp_elems(n) + 1);
+    if (e == cudaSuccess) e = dalloc(&b->d_ctrl, 4);
+    if (e == cudaSuccess) e = dalloc(&b->d_totals, 2);
+    if (e == cudaSuccess) e = dalloc(&b->d_spill, (size_t)n_warps * b->spill_cap);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_geoms, recs.data(), recs.size() * sizeof(GeomDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tstop, ts.data(), ts.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tss, tss.data(), tss.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_s2l, s2l.data(), s2l.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_zmid, zm.data(), zm.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        supa_destroy_batch(b);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return fail(SUPA_ERR_OOM, "supa_batch_create: out of device memory (max_hits = %lld)", (long long)max_hits);
+        }
+        return cuda_fail(e, "supa_batch_create");
+    }
+    *out = b;
+    return SUPA_OK;
+}
+
+int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64_t seed, uint64_t shower_id_base,
+                  void *stream) {
+    if (!b || (!prim_dev && n > 0)) return fail(SUPA_ERR_INVALID_ARG, "supa_simulate: null argument");
+    if (n < 0 || n > b->max_showers)
+        return fail(SUPA_ERR_INVALID_ARG, "n = %lld exceeds the batch capacity %lld", (long long)n,
+                    (long long)b->max_showers);
+    if (shower_id_base + (uint64_t)n > (1ull << 32))
+        return fail(SUPA_ERR_INVALID_ARG, "shower ids must stay below 2^32");
+    cudaStream_t st = (cudaStream_t)stream;
+    b->info_valid = false;
+    b->last_n = n;
+    if (n > 0) SUPA_CUDA(cudaMemcpyAsync(b->d_prim, prim_dev, n * sizeof(supa_primary), cudaMemcpyDeviceToDevice, st));
+    SUPA_CUDA(cudaMemsetAsync(b->d_ctrl, 0, 4 * sizeof(int), st));
+    SUPA_CUDA(cudaMemsetAsync(b->d_totals, 0, 2 * sizeof(unsigned long long), st));
+    if (b->lpt && n > 0) SUPA_CUDA(launch_lpt_queue(b->d_prim, n, b->d_queue, b->d_bucket, st));
+    StepParams p{};
+    p.prim = b->d_prim;
+    p.queue = b->lpt ? b->d_queue : nullptr;
+    p.n = n;
+    p.n_geoms = (int)b->geoms.size();
+    p.seed = seed;
+    p.shower_id_base = shower_id_base;
+    p.geoms = b->d_geoms;
+    p.t_stop = b->d_tstop;
+    p.t_ss = b->d_tss;
+    p.s2l = b->d_s2l;
+    p.pool = b->d_pool;
+    p.tag_pool = b->d_tags;
+    p.page_next = b->d_page_next;
+    p.n_pages = b->n_pages;
+    p.page_counter = b->d_ctrl + 1;
+    p.hit_start = b->d_hit_start;
+    p.hit_count = b->d_hit_count;
+    p.steps = b->d_steps;
+    p.lsum = b->d_lsum;
+    p.lsum_stride = b->max_layers;
+    p.dead = b->d_dead;
+    p.leak = b->d_leak;
+    p.escape = b->d_escape;
+    p.queue_head = b->d_ctrl;
+    p.error = b->d_ctrl + 2;
+    p.totals = b->d_totals;
+    p.spill = b->d_spill;
+    p.spill_cap = b->spill_cap;
+    p.stack_cap = b->stack_cap;
+    p.stage_cap = b->stage_cap;
+    p.flush_thr = b->flush_thr;
+    p.warp_smem_bytes = b->warp_bytes;
+    if (n > 0) SUPA_CUDA(launch_step(p, b->grid, b->block, b->smem, st));
+    SUPA_CUDA(launch_scan_counts(b->d_hit_count, n, b->d_offsets, b->d_scan_tmp, st));
+    return SUPA_OK;
+}
+
+int supa_simulate_batch(const supa_geometry *const *geoms, int32_t n_geoms, const supa_primary *prim_dev, int64_t n,
+                        uint64_t seed, uint64_t shower_id_base, const supa_launch_config *cfg, supa_batch **out,
+                        void *stream) {
+    if (!out) return fail(SUPA_ERR_INVALID_ARG, "supa_simulate_batch: null out");
+    int rc = supa_batch_create(geoms, n_geoms, n > 0 ? n : 1, cfg, out);
+    if (rc != SUPA_OK) return rc;
+    rc = supa_simulate(*out, prim_dev, n, seed, shower_id_base, stream);
+    if (rc != SUPA_OK) {
+        supa_destroy_batch(*out);
+        *out = nullptr;
+    }
+    return rc;
+}
+
+int supa_batch_get_info(supa_batch *b, supa_batch_info *info, void *stream) {
+    if (!b || !info) return fail(SUPA_ERR_INVALID_ARG, "supa_batch_get_info: null argument");
+    if (b->last_n < 0) return fail(SUPA_ERR_NOT_READY, "no simulation has run on this batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    int ctrl[4];
+    unsigned long long tot[2];
+    long long nh = 0;
+    SUPA_CUDA(cudaMemcpyAsync(ctrl, b->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, st));
+    SUPA_CUDA(cudaMemcpyAsync(tot, b->d_totals, sizeof(tot), cudaMemcpyDeviceToHost, st));
+    SUPA_CUDA(cudaMemcpyAsync(&nh, b->d_offsets + b->last_n, sizeof(nh), cudaMemcpyDeviceToHost, st));
+    SUPA_CUDA(cudaStreamSynchronize(st));
+    memset(info, 0, sizeof(*info));
+    info->n_showers = b->last_n;
+    info->n_hits = nh;
+    info->n_steps = (int64_t)tot[0];
+    info->max_layers = b->max_layers;
+    info->offsets_dev = b->d_offsets;
+    info->counts_dev = b->d_hit_count;
+    info->steps_dev = b->d_steps;
+    info->layer_sums_dev = b->d_lsum;
+    info->dead_dev = b->d_dead;
+    info->leak_dev = b->d_leak;
+    info->escape_dev = b->d_escape;
+    if (ctrl[2] == kErrBadPrimary) {
+        info->status = SUPA_ERR_INVALID_ARG;
+        return fail(SUPA_ERR_INVALID_ARG, "a primary was invalid (geometry index, energy <= 0 or above the lineage "
+                    "bound, polar angle outside [0, pi/2), or a non-finite field); its shower is empty");
+    }
+    if (ctrl[2] != 0) {
+        info->status = SUPA_ERR_OVERFLOW;
+        return fail(SUPA_ERR_OVERFLOW, "simulation overflowed its %s (error word %d); use fewer showers per batch%s",
+                    (ctrl[2] & kErrPoolOverflow) ? "hit pool" : "particle spill stack", ctrl[2],
+                    (ctrl[2] & kErrPoolOverflow) ? " or a larger max_hits" : "");
+    }
+    b->n_hits = nh;
+    b->n_steps = (int64_t)tot[0];
+    b->info_valid = true;
+    return SUPA_OK;
+}
+
+static int fetch_common(supa_batch *b, int64_t first, int64_t max_hits, void *dst, bool dev, bool tags,
+                        int64_t *n_written, void *stream) {
+    if (!b || !dst || !n_written) return fail(SUPA_ERR_INVALID_ARG, "supa_fetch_hits: null argument");
+    if (!b->info_valid) return fail(SUPA_ERR_NOT_READY, "call supa_batch_get_info after the simulation first");
+    if (tags && !b->tags) return fail(SUPA_ERR_INVALID_ARG, "the batch was created without record_tags");
+    if (first < 0 || max_hits < 0) return fail(SUPA_ERR_INVALID_ARG, "negative range");
+    const int64_t count = std::max<int64_t>(0, std::min(max_hits, b->n_hits - first));
+    *n_written = count;
+    if (count == 0) return SUPA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    FetchParams p{};
+    p.src.pool = b->d_pool;
+    p.src.page_next = b->d_page_next;
+    p.src.hit_start = b->d_hit_start;
+    p.src.hit_count = b->d_hit_count;
+    p.src.offsets = b->d_offsets;
+    p.tag_pool = tags ? b->d_tags : nullptr;
+    p.n_showers = b->last_n;
+    if (dev) {
+        p.first = first;
+        p.count = count;
+        p.dst = tags ? nullptr : (float4 *)dst;
+        p.dst_tags = tags ? (unsigned long long *)dst : nullptr;
+        SUPA_CUDA(launch_fetch(p, st));
+        return SUPA_OK;
+    }
+    // host destination: gather into a device staging buffer, then copy out
+    const int64_t chunk = std::min<int64_t>(count, (int64_t)64 << 20);
+    if (b->stage_cap_hits < chunk) {
+        SUPA_CUDA(cudaStreamSynchronize(st));
+        cudaFree(b->d_stage);
+        b->d_stage = nullptr;
+        b->stage_cap_hits = 0;
+        SUPA_CUDA(dalloc(&b->d_stage, (size_t)chunk));
+        b->stage_cap_hits = chunk;
+    }
+    for (int64_t done = 0; done < count; done += chunk) {
+        const int64_t m = std::min(chunk, count - done);
+        p.first = first + done;
+        p.count = m;
+        p.dst = b->d_stage;
+        SUPA_CUDA(launch_fetch(p, st));
+        SUPA_CUDA(cudaMemcpyAsync((char *)dst + done * 16, b->d_stage, m * 16, cudaMemcpyDeviceToHost, st));
+    }
+    SUPA_CUDA(cudaStreamSynchronize(st));
+    return SUPA_OK;
+}
+
+int supa_fetch_hits(supa_batch *b, int64_t first_hit, int64_t max_hits, void *dst, int32_t dst_is_device,
+                    int64_t *n_written, void *stream) {
+    return fetch_common(b, first_hit, max_hits, dst, dst_is_device != 0, false, n_written, stream);
+}
+
+int supa_fetch_hit_tags(supa_batch *b, int64_t first_hit, int64_t max_hits, uint64_t *dst_dev, int64_t *n_written,
+                        void *stream) {
+    return fetch_common(b, first_hit, max_hits, dst_dev, true, true, n_written, stream);
+}
+
+static int pick_group(int L, int cells) {
+    const int per = cells * 4;
+    int G = std::max(1, std::min(L, (64 * 1024) / per));
+    return G;
+}
+
+int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev, double *out_of_roi_dev,
+                  void *stream) {
+    if (!b || !grid_dev) return fail(SUPA_ERR_INVALID_ARG, "supa_voxelize: null argument");
+    if (!b->info_valid) return fail(SUPA_ERR_NOT_READY, "call supa_batch_get_info after the simulation first");
+    if (shower_begin < 0 || shower_end < shower_begin || shower_end > b->last_n)
+        return fail(SUPA_ERR_INVALID_ARG, "shower range [%lld, %lld) outside the batch", (long long)shower_begin,
+                    (long long)shower_end);
+    const GeomDev &g0 = b->geoms[0]->rec;
+    for (auto *g : b->geoms)
+        if (g->rec.nx != g0.nx || g->rec.ny != g0.ny || g->rec.wx != g0.wx || g->rec.wy != g0.wy)
+            return fail(SUPA_ERR_INVALID_ARG, "all geometries of the batch must share the image grid");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = shower_end - shower_begin;
+    if (n == 0) return SUPA_OK;
+    const size_t cells = (size_t)g0.nx * g0.ny;
+    if ((size_t)(grid_dev) % 16 != 0) return fail(SUPA_ERR_INVALID_ARG, "grid_dev must be 16-byte aligned");
+    if (cells * 4 > 200 * 1024) return fail(SUPA_ERR_INVALID_ARG, "one layer image exceeds 200 KiB of shared memory");
+    if (out_of_roi_dev) SUPA_CUDA(cudaMemsetAsync(out_of_roi_dev, 0, n * sizeof(double), st));
+    VoxParams p{};
+    p.src.pool = b->d_pool;
+    p.src.page_next = b->d_page_next;
+    p.src.hit_start = b->d_hit_start;
+    p.src.hit_count = b->d_hit_count;
+    p.s_begin = shower_begin;
+    p.n_showers = n;
+    p.L = b->max_layers;
+    p.G = pick_group(p.L, (int)cells);
+    p.n_groups = (p.L + p.G - 1) / p.G;
+    p.nx = g0.nx;
+    p.ny = g0.ny;
+    p.wx = g0.wx;
+    p.wy = g0.wy;
+    p.prim = b->d_prim;
+    p.geoms = b->d_geoms;
+    p.single_geom = 0;
+    p.s2l = b->d_s2l;
+    p.zmid = b->d_zmid;
+    p.grid = grid_dev;
+    p.oor = out_of_roi_dev;
+    SUPA_CUDA(launch_voxelize(p, st));
+    return SUPA_OK;
+}
+
+int supa_voxelize_hits(const supa_geometry *g, const float *hits_dev, const int64_t *offsets_dev, int64_t n_showers,
+                       const float *roi_x0_dev, const float *roi_y0_dev, float *grid_dev, double *out_of_roi_dev,
+                       void *stream) {
+    if (!g || !offsets_dev || !roi_x0_dev || !roi_y0_dev || !grid_dev || (!hits_dev && n_showers > 0))
+        return fail(SUPA_ERR_INVALID_ARG, "supa_voxelize_hits: null argument");
+    if (n_showers < 0) return fail(SUPA_ERR_INVALID_ARG, "negative shower count");
+    if ((size_t)(grid_dev) % 16 != 0 || (size_t)(hits_dev) % 16 != 0)
+        return fail(SUPA_ERR_INVALID_ARG, "hits_dev and grid_dev must be 16-byte aligned");
+    const size_t cells = (size_t)g->rec.nx * g->rec.ny;
+    if (cells * 4 > 200 * 1024) return fail(SUPA_ERR_INVALID_ARG, "one layer image exceeds 200 KiB of shared memory");
+    if (n_showers == 0) return SUPA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (out_of_roi_dev) SUPA_CUDA(cudaMemsetAsync(out_of_roi_dev, 0, n_showers * sizeof(double), st));
+    VoxParams p{};
+    p.src.hits = (const float4 *)hits_dev;
+    p.src.offsets = offsets_dev;
+    p.s_begin = 0;
+    p.n_showers = n_showers;
+    p.L = g->rec.n_layers;
+    p.G = pick_group(p.L, (int)cells);
+    p.n_groups = (p.L + p.G - 1) / p.G;
+    p.nx = g->rec.nx;
+    p.ny = g->rec.ny;
+    p.wx = g->rec.wx;
+    p.wy = g->rec.wy;
+    p.geoms = g->d_rec;
+    p.single_geom = 1;
+    p.s2l = g->d_s2l;
+    p.zmid = g->d_zmid;
+    p.roi_x0 = roi_x0_dev;
+    p.roi_y0 = roi_y0_dev;
+    p.grid = grid_dev;
+    p.oor = out_of_roi_dev;
+    SUPA_CUDA(launch_voxelize(p, st));
+    return SUPA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,348 @@
+// aux_kernels.cu -- downsampling (App. A.5), hit fetch, offset scan and the
+// energy-ordered work queue of the SUPA library.
+#include "supa_internal.cuh"
+
+namespace supa {
+
+namespace {
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// Walks the hits of one shower.  In pages mode the hits of shower s start at
+// hit_start[s] in the pool and continue along page_next; in contiguous mode
+// they are hits[offsets[s] ...).
+struct ShowerHits {
+    const float4 *seg_ptr;  // current contiguous segment
+    int seg_len;
+    int64_t remaining;
+    int page;
+    const HitSource *src;
+
+    __device__ void init(const HitSource &hs, int64_t s) {
+        src = &hs;
+        if (hs.pool) {
+            const unsigned long long st = hs.hit_start[s];
+            remaining = hs.hit_count[s];
+            page = (int)(st / kPageHits);
+            const int off = (int)(st % kPageHits);
+            seg_ptr = hs.pool + st;
+            seg_len = (int)imin64(remaining, kPageHits - off);
+        } else {
+            const int64_t a = hs.offsets[s], b = hs.offsets[s + 1];
+            remaining = b - a;
+            page = -1;
+            seg_ptr = hs.hits + a;
+            seg_len = (int)imin64(remaining, (int64_t)1 << 30);
+        }
+    }
+    // Advance past the current segment; false when the shower is exhausted.
+    __device__ bool next() {
+        remaining -= seg_len;
+        if (remaining <= 0) return false;
+        if (src->pool) {
+            page = src->page_next[page];
+            seg_ptr = src->pool + (size_t)page * kPageHits;
+            seg_len = (int)imin64(remaining, kPageHits);
+        } else {
+            seg_ptr += seg_len;
+            seg_len = (int)imin64(remaining, (int64_t)1 << 30);
+        }
+        return true;
+    }
+};
+
+__device__ __forceinline__ double block_sum_double(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    return t;  // valid in thread 0
+}
+
+}  // namespace
+
+size_t vox_smem_bytes(int G, int nx, int ny) { return (size_t)G * nx * ny * sizeof(float); }
+
+// One CTA per (shower, group of G layers): zero the group's images in shared
+// memory, bin the shower's hits of those layers with shared-memory atomics,
+// then copy the finished images to HBM with one bulk asynchronous copy (TMA
+// engine, cp.async.bulk) -- the images of consecutive layers of a shower are
+// contiguous in the [shower][layer][ny][nx] layout.
+__global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
+    extern __shared__ __align__(128) float tile[];
+    __shared__ float roi_x[SUPA_MAX_LAYERS], roi_y[SUPA_MAX_LAYERS];
+    __shared__ double red[32];
+    const int64_t srel = blockIdx.x / p.n_groups;
+    const int grp = blockIdx.x % p.n_groups;
+    const int64_t s = p.s_begin + srel;
+    const int l0 = grp * p.G;
+    const int G = min(p.G, p.L - l0);
+    const int cells = p.nx * p.ny;
+    const int tile_floats = G * cells;
+
+    // zero the images (16-byte shared stores)
+    float4 *t4 = reinterpret_cast<float4 *>(tile);
+    for (int i = threadIdx.x; i < tile_floats / 4; i += blockDim.x) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    const GeomDev g = p.geoms[p.single_geom ? 0 : p.prim[s].geom];
+    const float half_x = (float)p.nx * p.wx * 0.5f;
+    const float half_y = (float)p.ny * p.wy * 0.5f;
+    if (threadIdx.x < G) {
+        const int l = l0 + threadIdx.x;
+        float rx = -half_x, ry = -half_y;
+        if (p.roi_x0) {
+            if (l < g.n_layers) {
+                rx = p.roi_x0[s * g.n_layers + l];
+                ry = p.roi_y0[s * g.n_layers + l];
+            }
+        } else if (g.roi_axis && l < g.n_layers) {
+            // centred on the incidence axis at the layer's mid depth
+            const supa_primary pr = p.prim[s];
+            const float t = tanf(pr.theta);
+            const float tx = __fmul_rn(t, cosf(pr.phi));
+            const float ty = __fmul_rn(t, sinf(pr.phi));
+            const float zm = p.zmid[g.layer_off + l];
+            rx = __fsub_rn(__fmul_rn(zm, tx), half_x);
+            ry = __fsub_rn(__fmul_rn(zm, ty), half_y);
+        }
+        roi_x[threadIdx.x] = rx;
+        roi_y[threadIdx.x] = ry;
+    }
+    __syncthreads();
+
+    double oor = 0.0;
+    ShowerHits it;
+    it.init(p.src, s);
+    if (it.remaining > 0) {
+        do {
+            for (int j = threadIdx.x; j < it.seg_len; j += blockDim.x) {
+                const float4 h = __ldg(it.seg_ptr + j);
+                const int k = (int)rintf(__fdiv_rn(h.z, g.dz));
+                const int layer = (k >= 0 && k < g.n_slices) ? (int)__ldg(p.s2l + g.slice_off + k) : -1;
+                if (layer < 0) {
+                    if (grp == 0) oor += (double)h.w;
+                    continue;
+                }
+                const int li = layer - l0;
+                if (li < 0 || li >= G) continue;
+                const float fx = floorf(__fdiv_rn(__fsub_rn(h.x, roi_x[li]), p.wx));
+                const float fy = floorf(__fdiv_rn(__fsub_rn(h.y, roi_y[li]), p.wy));
+                if (fx >= 0.0f && fx < (float)p.nx && fy >= 0.0f && fy < (float)p.ny)
+                    atomicAdd(&tile[li * cells + (int)fy * p.nx + (int)fx], h.w);
+                else
+                    oor += (double)h.w;
+            }
+        } while (it.next());
+    }
+    const double tot = block_sum_double(oor, red);
+    if (threadIdx.x == 0 && p.oor && tot != 0.0) atomicAdd(&p.oor[srel], tot);
+    __syncthreads();
+
+    // bulk copy of the finished images to global memory (async proxy)
+    if (threadIdx.x == 0) {
+        float *dst = p.grid + ((size_t)srel * p.L + l0) * cells;
+        const unsigned saddr = (unsigned)__cvta_generic_to_shared(tile);
+        const unsigned bytes = (unsigned)tile_floats * 4u;
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(saddr),
+                     "r"(bytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+    }
+}
+
+cudaError_t launch_voxelize(const VoxParams &p, cudaStream_t st) {
+    const size_t smem = vox_smem_bytes(p.G, p.nx, p.ny);
+    cudaError_t e = cudaFuncSetAttribute(supa_voxel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = p.n_showers * p.n_groups;
+    if (blocks == 0) return cudaSuccess;
+    supa_voxel_kernel<<<(unsigned)blocks, 256, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fetch ---
+// Copy canonical hits [first, first+count) (shower order) to dst.  Every warp
+// finds the first shower overlapping the range by binary search over the
+// offsets, then warps stride over the overlapping showers.
+__global__ void supa_fetch_kernel(const FetchParams p, const int64_t *canon) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t lo_hit = p.first, hi_hit = p.first + p.count;
+    // first shower s with canon[s+1] > lo_hit
+    int64_t a = 0, b = p.n_showers;  // answer in [a, b)
+    while (a < b) {
+        const int64_t m = (a + b) >> 1;
+        if (canon[m + 1] > lo_hit) b = m; else a = m + 1;
+    }
+    for (int64_t s = a + warp; s < p.n_showers; s += n_warps) {
+        const int64_t s0 = canon[s];
+        if (s0 >= hi_hit) break;
+        ShowerHits it;
+        it.init(p.src, s);
+        int64_t i0 = 0;  // index within the shower of the segment start
+        if (it.remaining <= 0) continue;
+        do {
+            for (int j = lane; j < it.seg_len; j += 32) {
+                const int64_t gidx = s0 + i0 + j;
+                if (gidx < lo_hit || gidx >= hi_hit) continue;
+                const size_t src_index = (size_t)(it.seg_ptr - p.src.pool) + j;
+                if (p.dst_tags)
+                    p.dst_tags[gidx - lo_hit] = p.tag_pool[src_index];
+                else
+                    p.dst[gidx - lo_hit] = it.seg_ptr[j];
+            }
+            i0 += it.seg_len;
+        } while (it.next());
+    }
+}
+
+cudaError_t launch_fetch(const FetchParams &p, cudaStream_t st) {
+    if (p.count <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    supa_fetch_kernel<<<sms * 8, 256, 0, st>>>(p, p.src.offsets);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- scan ---
+// Exclusive scan of per-shower hit counts into int64 offsets [n+1]:
+// per-block totals, a single-block scan of the totals, then the final pass.
+namespace {
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *warp_tot, long long &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        long long x = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
+        long long xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(kFull, xi, o);
+            if (lane >= o) xi += t;
+        }
+        warp_tot[lane] = xi - x;  // exclusive per-warp offsets
+        if (lane == 31) warp_tot[32] = xi;
+    }
+    __syncthreads();
+    const long long res = warp_tot[wid] + inc - v;
+    total = warp_tot[32];
+    __syncthreads();
+    return res;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(kScanThreads) scan_block_totals(const uint32_t *c, int64_t n, unsigned long long *bt) {
+    __shared__ long long wt[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    long long v = 0;
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) v += c[base + i];
+    long long total;
+    block_exclusive_scan(v, wt, total);
+    if (threadIdx.x == 0) bt[blockIdx.x] = (unsigned long long)total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_totals(unsigned long long *bt, int64_t nb) {
+    __shared__ long long wt[33];
+    long long carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+        const int64_t i = b0 + threadIdx.x;
+        const long long v = i < nb ? (long long)bt[i] : 0;
+        long long total;
+        const long long ex = block_exclusive_scan(v, wt, total);
+        if (i < nb) bt[i] = (unsigned long long)(carry + ex);
+        carry += total;
+    }
+    if (threadIdx.x == 0) bt[nb] = (unsigned long long)carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_final(const uint32_t *c, int64_t n, const unsigned long long *bt,
+                                                           int64_t nb, int64_t *off) {
+    __shared__ long long wt[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    long long v[kScanItems];
+    long long sum = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? (long long)c[base + i] : 0;
+        sum += v[i];
+    }
+    long long total;
+    long long ex = block_exclusive_scan(sum, wt, total) + (long long)bt[blockIdx.x];
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) off[base + i] = ex;
+        ex += v[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[n] = (int64_t)bt[nb];
+}
+
+size_t scan_tmp_elems(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
+
+cudaError_t launch_scan_counts(const uint32_t *counts, int64_t n, int64_t *offsets, unsigned long long *block_tmp,
+                               cudaStream_t st) {
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb > 0) scan_block_totals<<<(unsigned)nb, kScanThreads, 0, st>>>(counts, n, block_tmp);
+    scan_totals<<<1, kScanThreads, 0, st>>>(block_tmp, nb);
+    scan_final<<<(unsigned)(nb > 0 ? nb : 1), kScanThreads, 0, st>>>(counts, n, block_tmp, nb, offsets);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- LPT queue ---
+// Hand showers out by decreasing primary energy (longest work first): a
+// counting sort of the showers into 256 buckets of log2(E) at 1/4 octave.
+namespace {
+constexpr int kBuckets = 256;
+__device__ __forceinline__ int energy_bucket(float E) {
+    const int b = (int)floorf(log2f(fmaxf(E, 1e-30f)) * 4.0f) + 64;
+    return kBuckets - 1 - min(max(b, 0), kBuckets - 1);  // high energy first
+}
+}  // namespace
+
+__global__ void lpt_histogram(const supa_primary *prim, int64_t n, uint32_t *cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[energy_bucket(prim[i].E)], 1u);
+}
+
+__global__ void lpt_scan(uint32_t *cnt) {
+    __shared__ long long wt[33];
+    const long long v = threadIdx.x < kBuckets ? cnt[threadIdx.x] : 0;
+    long long total;
+    const long long ex = block_exclusive_scan(v, wt, total);
+    if (threadIdx.x < kBuckets) cnt[threadIdx.x] = (uint32_t)ex;
+}
+
+__global__ void lpt_scatter(const supa_primary *prim, int64_t n, uint32_t *cursor, uint32_t *queue) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t pos = atomicAdd(&cursor[energy_bucket(prim[i].E)], 1u);
+        queue[pos] = (uint32_t)i;
+    }
+}
+
+cudaError_t launch_lpt_queue(const supa_primary *prim, int64_t n, uint32_t *queue, uint32_t *bucket_cnt,
+                             cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(bucket_cnt, 0, kBuckets * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)imin64((n + 255) / 256, 4096);
+    if (blocks == 0) return cudaSuccess;
+    lpt_histogram<<<blocks, 256, 0, st>>>(prim, n, bucket_cnt);
+    lpt_scan<<<1, kBuckets, 0, st>>>(bucket_cnt);
+    lpt_scatter<<<blocks, 256, 0, st>>>(prim, n, bucket_cnt, queue);
+    return cudaGetLastError();
+}
+
+}  // namespace supa

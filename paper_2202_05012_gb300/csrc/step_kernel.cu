@@ -1,0 +1,404 @@
+// step_kernel.cu -- persistent particle-step kernel: SUPA Algorithm 1 applied
+// to every live particle of every shower (Sec. 3, "Propagation Model").
+//
+// Work decomposition (GB300-first, not the paper's serial loop):
+//  * A persistent grid; each warp takes one shower at a time from a device
+//    work queue (one atomicAdd per shower) and develops it completely.
+//  * Each lane holds one live particle in registers.  At a split the lane
+//    keeps daughter 0 and pushes daughter 1 onto the warp's particle stack in
+//    shared memory (ballot + popc compaction, no atomics); empty lanes refill
+//    from the stack.  A stack that outgrows shared memory spills its oldest
+//    half to a per-warp region of global scratch.
+//  * Stops are staged as float4 hits in shared memory and flushed with
+//    coalesced 16-byte stores to the warp's current page of the hit pool
+//    once flush_thr hits are staged.
+//  * Per-layer deposits are summed in FP64 in shared memory; dead, leaked and
+//    escaped energy in FP64 lane registers.
+// Every random draw is keyed by (seed; shower id, slice, lineage id), so the
+// result does not depend on which warp runs a shower or in which order.
+#include "philox.cuh"
+#include "supa_internal.cuh"
+
+namespace supa {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct WarpSmem {
+    float4 *stage;
+    unsigned long long *stage_tag;
+    unsigned long long *slin;
+    double *lsum;
+    float *sx, *sy, *sux, *suy, *suz, *sE;
+    uint8_t *sk;
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+__device__ inline WarpSmem carve(unsigned char *base, int C, int H, bool tags) {
+    WarpSmem w;
+    size_t o = 0;
+    w.stage = reinterpret_cast<float4 *>(base + o);
+    o += size_t(16) * H;
+    w.stage_tag = reinterpret_cast<unsigned long long *>(base + o);
+    if (tags) o += size_t(8) * H;
+    w.slin = reinterpret_cast<unsigned long long *>(base + o);
+    o += size_t(8) * C;
+    w.lsum = reinterpret_cast<double *>(base + o);
+    o += size_t(8) * SUPA_MAX_LAYERS;
+    float *f = reinterpret_cast<float *>(base + o);
+    w.sx = f;
+    w.sy = f + C;
+    w.sux = f + 2 * C;
+    w.suy = f + 3 * C;
+    w.suz = f + 4 * C;
+    w.sE = f + 5 * C;
+    o += size_t(24) * C;
+    w.sk = base + o;
+    return w;
+}
+
+struct Particle {
+    float x, y, ux, uy, uz, E;
+    unsigned long long lin;
+    int k;
+};
+
+__device__ __forceinline__ void smem_store(const WarpSmem &w, int i, const Particle &q) {
+    w.sx[i] = q.x; w.sy[i] = q.y; w.sux[i] = q.ux; w.suy[i] = q.uy; w.suz[i] = q.uz; w.sE[i] = q.E;
+    w.slin[i] = q.lin;
+    w.sk[i] = (uint8_t)q.k;
+}
+
+__device__ __forceinline__ Particle smem_load(const WarpSmem &w, int i) {
+    Particle q;
+    q.x = w.sx[i]; q.y = w.sy[i]; q.ux = w.sux[i]; q.uy = w.suy[i]; q.uz = w.suz[i]; q.E = w.sE[i];
+    q.lin = w.slin[i];
+    q.k = w.sk[i];
+    return q;
+}
+
+__device__ __forceinline__ SpillRec to_rec(const Particle &q) {
+    SpillRec r;
+    r.x = q.x; r.y = q.y; r.ux = q.ux; r.uy = q.uy; r.uz = q.uz; r.E = q.E;
+    r.lin_lo = (uint32_t)q.lin; r.lin_hi = (uint32_t)(q.lin >> 32); r.k = q.k;
+    return r;
+}
+
+__device__ __forceinline__ Particle from_rec(const SpillRec &r) {
+    Particle q;
+    q.x = r.x; q.y = r.y; q.ux = r.ux; q.uy = r.uy; q.uz = r.uz; q.E = r.E;
+    q.lin = ((unsigned long long)r.lin_hi << 32) | r.lin_lo; q.k = r.k;
+    return q;
+}
+
+// Deflect unit vector (ux,uy,uz) by polar angle delta toward w (a unit vector
+// perpendicular to u): u' = cos(delta) u + sin(delta) w, renormalised.
+__device__ __forceinline__ void deflect(float ux, float uy, float uz, float wx, float wy, float wz, float sd,
+                                        float cd, float &ox, float &oy, float &oz) {
+    ox = fmaf(cd, ux, sd * wx);
+    oy = fmaf(cd, uy, sd * wy);
+    oz = fmaf(cd, uz, sd * wz);
+    const float inv = rsqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz)));
+    ox *= inv; oy *= inv; oz *= inv;
+}
+
+// A survivor of slice k either leaks (last slice), escapes (u_z too small)
+// or moves in a straight line to slice k+1.  Returns true if still alive.
+__device__ __forceinline__ bool advance(Particle &q, const GeomDev &g, double &leak, double &esc) {
+    if (q.k == g.n_slices - 1) { leak += (double)q.E; return false; }
+    if (q.uz <= g.uz_min) { esc += (double)q.E; return false; }
+    q.x += g.dz * (q.ux / q.uz);
+    q.y += g.dz * (q.uy / q.uz);
+    q.k += 1;
+    return true;
+}
+
+struct PageCursor {
+    int page;  // current page (-1: none)
+    int off;   // next free slot in the page
+};
+
+// Take a fresh page from the pool and link it after the current one.
+// Lane-uniform.  Returns false if the pool is exhausted.
+__device__ __forceinline__ bool next_page(const StepParams &p, PageCursor &pc, int lane) {
+    int np = 0;
+    if (lane == 0) {
+        np = atomicAdd(p.page_counter, 1);
+        if (np < p.n_pages && pc.page >= 0) p.page_next[pc.page] = np;
+    }
+    np = __shfl_sync(kFull, np, 0);
+    if (np >= p.n_pages) return false;
+    pc.page = np;
+    pc.off = 0;
+    return true;
+}
+
+// Write `count` staged hits to the page chain.  Lane-uniform.
+__device__ __forceinline__ bool flush(const StepParams &p, const WarpSmem &w, int count, PageCursor &pc, int lane) {
+    int done = 0;
+    while (done < count) {
+        if (pc.off == kPageHits && !next_page(p, pc, lane)) return false;
+        const int m = min(count - done, kPageHits - pc.off);
+        const size_t base = (size_t)pc.page * kPageHits + pc.off;
+        for (int j = lane; j < m; j += 32) p.pool[base + j] = w.stage[done + j];
+        if (p.tag_pool)
+            for (int j = lane; j < m; j += 32) p.tag_pool[base + j] = w.stage_tag[done + j];
+        pc.off += m;
+        done += m;
+    }
+    __syncwarp();
+    return true;
+}
+
+}  // namespace
+
+size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags) {
+    size_t o = size_t(16) * stage_cap + (tags ? size_t(8) * stage_cap : 0) + size_t(8) * stack_cap +
+               size_t(8) * SUPA_MAX_LAYERS + size_t(24) * stack_cap + size_t(stack_cap);
+    return align16(o);
+}
+
+__global__ void __launch_bounds__(512) supa_step_kernel(const StepParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warp_global = blockIdx.x * (blockDim.x >> 5) + wib;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int C = p.stack_cap;
+    const bool tags = p.tag_pool != nullptr;
+    const WarpSmem w = carve(smem_raw + (size_t)wib * p.warp_smem_bytes, C, p.stage_cap, tags);
+    SpillRec *spill = p.spill + (size_t)warp_global * p.spill_cap;
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+
+    PageCursor pc{-1, kPageHits};
+    unsigned long long warp_steps = 0, warp_hits = 0;
+
+    while (true) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(p.queue_head, 1);
+        q = __shfl_sync(kFull, q, 0);
+        if (q >= p.n) break;
+        if ((*((volatile int *)p.error) & (kErrPoolOverflow | kErrSpillOverflow)) != 0) break;
+        const int64_t s = p.queue ? (int64_t)p.queue[q] : (int64_t)q;
+        const supa_primary pr = p.prim[s];
+        if (pr.geom >= (uint32_t)p.n_geoms || !(pr.E > 0.0f) || !(pr.E <= p.geoms[pr.geom].e0_max) ||
+            !(pr.theta >= 0.0f && pr.theta < 1.5707963f) || !isfinite(pr.phi) || !isfinite(pr.x0) ||
+            !isfinite(pr.y0)) {
+            // invalid primary: report it and leave an empty shower behind
+            if (lane == 0) {
+                atomicOr(p.error, kErrBadPrimary);
+                p.hit_start[s] = 0; p.hit_count[s] = 0; p.steps[s] = 0;
+                p.dead[s] = 0.0; p.leak[s] = 0.0; p.escape[s] = 0.0;
+            }
+            for (int l = lane; l < p.lsum_stride; l += 32) p.lsum[(size_t)s * p.lsum_stride + l] = 0.0;
+            continue;
+        }
+        const GeomDev g = p.geoms[pr.geom];
+        const uint32_t sid = (uint32_t)(p.shower_id_base + (uint64_t)s);
+
+        for (int l = lane; l < g.n_layers; l += 32) w.lsum[l] = 0.0;
+        if (pc.off == kPageHits && !next_page(p, pc, lane)) {
+            if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
+            break;
+        }
+        const unsigned long long start = (unsigned long long)pc.page * kPageHits + pc.off;
+
+        // Initial particle (Sec. 3): impact point on slice 0, incidence direction.
+        Particle cur;
+        bool have = (lane == 0);
+        {
+            float st, ct, sp, cp;
+            sincosf(pr.theta, &st, &ct);
+            sincosf(pr.phi, &sp, &cp);
+            cur.x = pr.x0; cur.y = pr.y0;
+            cur.ux = st * cp; cur.uy = st * sp; cur.uz = ct;
+            cur.E = pr.E; cur.lin = 1ull; cur.k = 0;
+        }
+        int stack_n = 0, spill_n = 0, staged = 0;
+        uint32_t n_hits = 0, n_steps = 0;
+        double dead = 0.0, leak = 0.0, esc = 0.0;
+        bool failed = false;
+        __syncwarp();
+
+        while (true) {
+            // ---- refill empty lanes from the stack (and the spill region) ----
+            const unsigned empty = __ballot_sync(kFull, !have);
+            const int n_empty = __popc(empty);
+            if (n_empty > stack_n && spill_n > 0) {
+                const int m = min(spill_n, min(C - stack_n, C / 2));
+                for (int j = lane; j < m; j += 32) smem_store(w, stack_n + j, from_rec(spill[spill_n - m + j]));
+                stack_n += m;
+                spill_n -= m;
+                __syncwarp();
+            }
+            const int n_pop = min(n_empty, stack_n);
+            if (!have) {
+                const int r = __popc(empty & lt_mask);
+                if (r < n_pop) {
+                    cur = smem_load(w, stack_n - 1 - r);
+                    have = true;
+                }
+            }
+            stack_n -= n_pop;
+            __syncwarp();
+            const unsigned act = __ballot_sync(kFull, have);
+            if (act == 0) break;
+
+            // ---- one step of Algorithm 1 for every active lane ----
+            bool push = false, hit = false;
+            Particle dau;
+            float4 h;
+            unsigned long long hit_lin = 0;
+            if (have) {
+                n_steps += 1;
+                const uint4 r = philox4x32_10(
+                    make_uint4(sid, (uint32_t)cur.k, (uint32_t)cur.lin, (uint32_t)(cur.lin >> 32)), key0, key1);
+                const int so = g.slice_off + cur.k;
+                const unsigned long long r0 = r.x;
+                if (r0 < __ldg(p.t_stop + so) || cur.E < g.e_min) {
+                    // stop: deposit the energy at slice k
+                    const int layer = __ldg(p.s2l + so);
+                    if (layer < 0) {
+                        dead += (double)cur.E;
+                    } else {
+                        hit = true;
+                        h = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
+                        hit_lin = cur.lin;
+                        atomicAdd(&w.lsum[layer], (double)cur.E);
+                    }
+                    have = false;
+                } else {
+                    if (r0 < __ldg(p.t_ss + so)) {
+                        // split into two daughters
+                        const float theta = fmaf(g.theta_span, u24(r.y), g.theta_lo);
+                        // E_0 / E = (theta/2 + eps)/theta = 1/2 + eps_frac (2U - 1)
+                        const float f = fmaf(g.eps_frac, fmaf(2.0f, u24(r.z), -1.0f), 0.5f);
+                        const float d1 = theta * f;                               // theta/2 + eps
+                        const float d0 = g.split_literal ? d1 : theta * (1.0f - f);  // theta/2 - eps
+                        float sw, cw;
+                        sincospif(2.0f * u24(r.w), &sw, &cw);  // omega = 2 pi U
+                        // orthonormal frame (e1, e2) perpendicular to u (Duff et al. 2017)
+                        const float a = -1.0f / (1.0f + cur.uz);
+                        const float b = cur.ux * cur.uy * a;
+                        const float e1x = fmaf(cur.ux * cur.ux, a, 1.0f), e1y = b, e1z = -cur.ux;
+                        const float e2x = b, e2y = fmaf(cur.uy * cur.uy, a, 1.0f), e2z = -cur.uy;
+                        const float wx = fmaf(cw, e1x, sw * e2x);
+                        const float wy = fmaf(cw, e1y, sw * e2y);
+                        const float wz = fmaf(cw, e1z, sw * e2z);
+                        float s0, c0, s1, c1;
+                        sincosf(d0, &s0, &c0);
+                        sincosf(d1, &s1, &c1);
+                        dau = cur;
+                        deflect(cur.ux, cur.uy, cur.uz, -wx, -wy, -wz, s1, c1, dau.ux, dau.uy, dau.uz);
+                        deflect(cur.ux, cur.uy, cur.uz, wx, wy, wz, s0, c0, cur.ux, cur.uy, cur.uz);
+                        const float E0 = cur.E * f;
+                        dau.E = cur.E - E0;
+                        cur.E = E0;
+                        dau.lin = 2ull * cur.lin + 1ull;
+                        cur.lin = 2ull * cur.lin;
+                        push = advance(dau, g, leak, esc);
+                    }
+                    have = advance(cur, g, leak, esc);
+                }
+            }
+
+            // ---- push daughters 1 onto the warp stack ----
+            const unsigned pm = __ballot_sync(kFull, push);
+            const int np = __popc(pm);
+            if (np) {
+                if (stack_n + np > C) {
+                    // spill the oldest half of the stack to global scratch
+                    const int m = C / 2;
+                    if (spill_n + m > p.spill_cap) {
+                        if (lane == 0) atomicOr(p.error, kErrSpillOverflow);
+                        failed = true;
+                        break;
+                    }
+                    for (int j = lane; j < m; j += 32) spill[spill_n + j] = to_rec(smem_load(w, j));
+                    __syncwarp();
+                    for (int j0 = m; j0 < stack_n; j0 += 32) {
+                        const int j = j0 + lane;
+                        Particle t;
+                        if (j < stack_n) t = smem_load(w, j);
+                        __syncwarp();
+                        if (j < stack_n) smem_store(w, j - m, t);
+                        __syncwarp();
+                    }
+                    stack_n -= m;
+                    spill_n += m;
+                }
+                if (push) smem_store(w, stack_n + __popc(pm & lt_mask), dau);
+                stack_n += np;
+                __syncwarp();
+            }
+
+            // ---- stage hits, flush to the page chain past the threshold ----
+            const unsigned hm = __ballot_sync(kFull, hit);
+            const int nh = __popc(hm);
+            if (nh) {
+                if (hit) {
+                    const int idx = staged + __popc(hm & lt_mask);
+                    w.stage[idx] = h;
+                    if (tags) w.stage_tag[idx] = hit_lin;
+                }
+                staged += nh;
+                n_hits += nh;
+                __syncwarp();
+                if (staged >= p.flush_thr) {
+                    if (!flush(p, w, staged, pc, lane)) {
+                        if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
+                        failed = true;
+                        break;
+                    }
+                    staged = 0;
+                }
+            }
+        }
+        if (failed) break;
+        if (staged && !flush(p, w, staged, pc, lane)) {
+            if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
+            break;
+        }
+
+        // ---- per-shower records ----
+        for (int o = 16; o > 0; o >>= 1) {
+            n_steps += __shfl_xor_sync(kFull, n_steps, o);
+            dead += __shfl_xor_sync(kFull, dead, o);
+            leak += __shfl_xor_sync(kFull, leak, o);
+            esc += __shfl_xor_sync(kFull, esc, o);
+        }
+        __syncwarp();
+        for (int l = lane; l < g.n_layers; l += 32) p.lsum[(size_t)s * p.lsum_stride + l] = w.lsum[l];
+        for (int l = g.n_layers + lane; l < p.lsum_stride; l += 32) p.lsum[(size_t)s * p.lsum_stride + l] = 0.0;
+        if (lane == 0) {
+            p.hit_start[s] = start;
+            p.hit_count[s] = n_hits;
+            p.steps[s] = n_steps;
+            p.dead[s] = dead;
+            p.leak[s] = leak;
+            p.escape[s] = esc;
+        }
+        warp_steps += n_steps;
+        warp_hits += n_hits;
+        __syncwarp();
+    }
+    if (lane == 0 && (warp_steps | warp_hits)) {
+        atomicAdd(&p.totals[0], warp_steps);
+        atomicAdd(&p.totals[1], warp_hits);
+    }
+}
+
+cudaError_t launch_step(const StepParams &p, int grid, int block, size_t smem, cudaStream_t st) {
+    supa_step_kernel<<<grid, block, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t step_kernel_attributes(int block, size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(supa_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, supa_step_kernel, block, smem);
+}
+
+}  // namespace supa

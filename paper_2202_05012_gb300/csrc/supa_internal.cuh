@@ -1,0 +1,136 @@
+// supa_internal.cuh -- device-side records shared by the SUPA kernels and the
+// host code of the C ABI.  Nothing here is visible through include/supa.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/supa.h"
+
+namespace supa {
+
+// Hits live in a pool of fixed-size pages.  A warp writes the hits of the
+// shower it is developing at the end of its current page and takes a fresh
+// page (linked from the old one through page_next) when the page is full,
+// so the hits of one shower form one contiguous run of the warp's page chain.
+constexpr int kPageHits = 4096;  // 64 KiB of float4 hits per page
+
+// Per-geometry constants, one record per geometry of a launch.
+struct GeomDev {
+    int n_slices, n_layers;
+    int slice_off;   // first entry of this geometry in the slice tables
+    int layer_off;   // first entry of this geometry in the per-layer tables
+    float dz, e_min, uz_min;
+    float theta_lo, theta_span;  // theta = theta_lo + theta_span * U
+    float eps_frac;              // eps = eps_frac * theta * (2U - 1); 0 for SUPA_EPS_ZERO
+    int split_literal;           // 1: both daughters deflected by theta/2 + eps
+    int nx, ny;
+    float wx, wy;
+    int roi_axis;
+    float e0_max;  // largest primary energy whose lineage ids fit 64 bits
+};
+
+// Particle record of the per-warp global spill stack (36 bytes).
+struct SpillRec {
+    float x, y, ux, uy, uz, E;
+    uint32_t lin_lo, lin_hi;
+    int32_t k;
+};
+
+struct StepParams {
+    // inputs
+    const supa_primary *prim;
+    const uint32_t *queue;  // order in which showers are handed out (nullptr = identity)
+    int64_t n;
+    int n_geoms;
+    uint64_t seed;
+    uint64_t shower_id_base;
+    const GeomDev *geoms;
+    const unsigned long long *t_stop;  // [slices] stop iff r0 < t_stop
+    const unsigned long long *t_ss;    // [slices] split iff t_stop <= r0 < t_ss
+    const int8_t *s2l;                 // [slices] layer or -1
+    // hit pool
+    float4 *pool;
+    unsigned long long *tag_pool;  // nullable
+    int *page_next;
+    int n_pages;
+    int *page_counter;
+    // per-shower results
+    unsigned long long *hit_start;
+    uint32_t *hit_count;
+    uint32_t *steps;
+    double *lsum;
+    int lsum_stride;
+    double *dead, *leak, *escape;
+    // control and totals
+    int *queue_head;
+    int *error;
+    unsigned long long *totals;  // [0] particle-steps, [1] hits
+    // scratch
+    SpillRec *spill;
+    int spill_cap;        // records per warp
+    int stack_cap;        // particles per warp in shared memory
+    int stage_cap;        // staged hits per warp (>= flush_thr + 32)
+    int flush_thr;
+    int warp_smem_bytes;  // shared memory per warp
+};
+
+// Device error word bits.
+constexpr int kErrPoolOverflow = 1;
+constexpr int kErrSpillOverflow = 2;
+constexpr int kErrBadPrimary = 4;
+
+size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags);
+
+// Kernel launchers (defined in the .cu files, called by the C ABI).
+cudaError_t launch_step(const StepParams &p, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t step_kernel_attributes(int block, size_t smem, int *blocks_per_sm);
+cudaError_t launch_scan_counts(const uint32_t *counts, int64_t n, int64_t *offsets, unsigned long long *block_tmp,
+                               cudaStream_t st);
+size_t scan_tmp_elems(int64_t n);
+cudaError_t launch_lpt_queue(const supa_primary *prim, int64_t n, uint32_t *queue, uint32_t *bucket_cnt,
+                             cudaStream_t st);
+
+struct HitSource {
+    // pages mode (pool != nullptr) or contiguous mode (hits != nullptr)
+    const float4 *pool;
+    const int *page_next;
+    const unsigned long long *hit_start;
+    const uint32_t *hit_count;
+    const float4 *hits;
+    const int64_t *offsets;
+};
+
+struct VoxParams {
+    HitSource src;
+    int64_t s_begin, n_showers;
+    int L;         // layer stride of the grid
+    int G;         // layers per CTA
+    int n_groups;  // ceil(L / G)
+    int nx, ny;
+    float wx, wy;
+    // batch mode: ROI from the primaries; explicit mode: roi_x0/roi_y0
+    const supa_primary *prim;
+    const GeomDev *geoms;
+    int single_geom;  // explicit mode: geometry 0 for every shower
+    const int8_t *s2l;
+    const float *zmid;  // per geometry-layer mid depth (layer_off + l)
+    const float *roi_x0, *roi_y0;
+    float *grid;
+    double *oor;
+};
+
+cudaError_t launch_voxelize(const VoxParams &p, cudaStream_t st);
+size_t vox_smem_bytes(int G, int nx, int ny);
+
+struct FetchParams {
+    HitSource src;
+    const unsigned long long *tag_pool;  // fetch tags instead of hits when non-null
+    int64_t n_showers;
+    int64_t first, count;
+    float4 *dst;
+    unsigned long long *dst_tags;
+};
+cudaError_t launch_fetch(const FetchParams &p, cudaStream_t st);
+
+}  // namespace supa

@@ -1,0 +1,272 @@
+"""Thin Python binding of libsupa.so (the C ABI of include/supa.h).
+
+Every function here has the name of the C entry point it calls and does
+argument marshalling only: torch tensors provide device memory and streams,
+and every step of the computation runs in the library's CUDA kernels.  There
+is no CPU fallback: if the library cannot be loaded, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+from . import inputs as _inputs
+
+SUPA_OK = 0
+SUPA_ERR_INVALID_ARG = -1
+SUPA_ERR_OOM = -2
+SUPA_ERR_OVERFLOW = -3
+SUPA_ERR_TIMEOUT = -4
+SUPA_ERR_CUDA = -5
+SUPA_ERR_NOT_READY = -6
+
+EXPORTED = (
+    "supa_last_error", "supa_init_geometry", "supa_destroy_geometry", "supa_batch_create", "supa_destroy_batch",
+    "supa_simulate", "supa_simulate_batch", "supa_batch_get_info", "supa_fetch_hits", "supa_fetch_hit_tags",
+    "supa_voxelize", "supa_voxelize_hits",
+)
+
+
+class SupaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class supa_geometry_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_slices", ctypes.c_int32), ("dz", ctypes.c_float),
+        ("slice_to_layer", ctypes.POINTER(ctypes.c_int32)), ("n_layers", ctypes.c_int32),
+        ("p_stop", ctypes.POINTER(ctypes.c_double)), ("p_split", ctypes.POINTER(ctypes.c_double)),
+        ("theta_mode", ctypes.c_int32), ("theta_lo", ctypes.c_double), ("theta_hi", ctypes.c_double),
+        ("eps_mode", ctypes.c_int32), ("eps_frac", ctypes.c_double), ("split_mode", ctypes.c_int32),
+        ("e_min", ctypes.c_double), ("uz_min", ctypes.c_double),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("wx", ctypes.c_float), ("wy", ctypes.c_float),
+        ("roi_mode", ctypes.c_int32),
+    ]
+
+
+class supa_launch_config(ctypes.Structure):
+    _fields_ = [
+        ("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
+        ("flush_threshold", ctypes.c_int32), ("record_tags", ctypes.c_int32), ("lpt_order", ctypes.c_int32),
+        ("max_hits", ctypes.c_int64),
+    ]
+
+
+class supa_batch_info(ctypes.Structure):
+    _fields_ = [
+        ("n_showers", ctypes.c_int64), ("n_hits", ctypes.c_int64), ("n_steps", ctypes.c_int64),
+        ("max_layers", ctypes.c_int32), ("status", ctypes.c_int32),
+        ("offsets_dev", ctypes.c_void_p), ("counts_dev", ctypes.c_void_p), ("steps_dev", ctypes.c_void_p),
+        ("layer_sums_dev", ctypes.c_void_p), ("dead_dev", ctypes.c_void_p), ("leak_dev", ctypes.c_void_p),
+        ("escape_dev", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libsupa.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libsupa.so not found at {_build.LIB}; run the build first")
+        L = ctypes.CDLL(_build.LIB)
+        L.supa_last_error.restype = ctypes.c_char_p
+        L.supa_init_geometry.argtypes = [ctypes.POINTER(supa_geometry_desc), ctypes.POINTER(_VP)]
+        L.supa_destroy_geometry.argtypes = [_VP]
+        L.supa_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, _I64,
+                                         ctypes.POINTER(supa_launch_config), ctypes.POINTER(_VP)]
+        L.supa_destroy_batch.argtypes = [_VP]
+        L.supa_simulate.argtypes = [_VP, _VP, _I64, ctypes.c_uint64, ctypes.c_uint64, _VP]
+        L.supa_simulate_batch.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, _VP, _I64, ctypes.c_uint64,
+                                          ctypes.c_uint64, ctypes.POINTER(supa_launch_config), ctypes.POINTER(_VP),
+                                          _VP]
+        L.supa_batch_get_info.argtypes = [_VP, ctypes.POINTER(supa_batch_info), _VP]
+        L.supa_fetch_hits.argtypes = [_VP, _I64, _I64, _VP, ctypes.c_int32, ctypes.POINTER(_I64), _VP]
+        L.supa_fetch_hit_tags.argtypes = [_VP, _I64, _I64, _VP, ctypes.POINTER(_I64), _VP]
+        L.supa_voxelize.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP]
+        L.supa_voxelize_hits.argtypes = [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]
+        for name in EXPORTED[1:]:
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, name: str):
+    if rc != SUPA_OK:
+        msg = lib().supa_last_error().decode()
+        raise SupaError(rc, f"{name}: {msg}")
+
+
+def _ptr(x) -> int | None:
+    """Device or host address of a torch tensor / numpy array / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def supa_last_error() -> str:
+    return lib().supa_last_error().decode()
+
+
+def supa_init_geometry(geom) -> int:
+    """Upload a geometry (an inputs.Geometry or any object with its fields)."""
+    s2l = np.ascontiguousarray(geom.slice_to_layer, dtype=np.int32)
+    ps = np.ascontiguousarray(geom.p_stop, dtype=np.float64)
+    pp = np.ascontiguousarray(geom.p_split, dtype=np.float64)
+    d = supa_geometry_desc(
+        int(geom.n_slices), float(geom.dz), s2l.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(geom.n_layers),
+        ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        int(geom.theta_mode), float(geom.theta_lo), float(geom.theta_hi), int(geom.eps_mode), float(geom.eps_frac),
+        int(geom.split_mode), float(geom.e_min), float(geom.uz_min), int(geom.nx), int(geom.ny), float(geom.wx),
+        float(geom.wy), int(geom.roi_mode))
+    out = _VP()
+    _check(lib().supa_init_geometry(ctypes.byref(d), ctypes.byref(out)), "supa_init_geometry")
+    return out.value
+
+
+def supa_destroy_geometry(g: int):
+    _check(lib().supa_destroy_geometry(g), "supa_destroy_geometry")
+
+
+def _cfg(cfg: dict | None):
+    if cfg is None:
+        return None
+    c = supa_launch_config()
+    for k, v in cfg.items():
+        setattr(c, k, int(v))
+    return ctypes.byref(c)
+
+
+def supa_batch_create(geoms: list[int], max_showers: int, cfg: dict | None = None) -> int:
+    arr = (_VP * len(geoms))(*geoms)
+    out = _VP()
+    _check(lib().supa_batch_create(arr, len(geoms), int(max_showers), _cfg(cfg), ctypes.byref(out)),
+           "supa_batch_create")
+    return out.value
+
+
+def supa_destroy_batch(b: int):
+    _check(lib().supa_destroy_batch(b), "supa_destroy_batch")
+
+
+def supa_simulate(b: int, prim_dev, n: int, seed: int, shower_id_base: int = 0, stream=None):
+    _check(lib().supa_simulate(b, _ptr(prim_dev), int(n), int(seed) & (2**64 - 1), int(shower_id_base),
+                               _stream(stream)), "supa_simulate")
+
+
+def supa_simulate_batch(geoms: list[int], prim_dev, n: int, seed: int, shower_id_base: int = 0,
+                        cfg: dict | None = None, stream=None) -> int:
+    arr = (_VP * len(geoms))(*geoms)
+    out = _VP()
+    _check(lib().supa_simulate_batch(arr, len(geoms), _ptr(prim_dev), int(n), int(seed) & (2**64 - 1),
+                                     int(shower_id_base), _cfg(cfg), ctypes.byref(out), _stream(stream)),
+           "supa_simulate_batch")
+    return out.value
+
+
+def supa_batch_get_info(b: int, stream=None) -> supa_batch_info:
+    info = supa_batch_info()
+    _check(lib().supa_batch_get_info(b, ctypes.byref(info), _stream(stream)), "supa_batch_get_info")
+    return info
+
+
+def supa_fetch_hits(b: int, first_hit: int, max_hits: int, dst, dst_is_device: bool | None = None,
+                    stream=None) -> int:
+    if dst_is_device is None:
+        dst_is_device = bool(getattr(dst, "is_cuda", False))
+    n = _I64()
+    _check(lib().supa_fetch_hits(b, int(first_hit), int(max_hits), _ptr(dst), int(dst_is_device), ctypes.byref(n),
+                                 _stream(stream)), "supa_fetch_hits")
+    return n.value
+
+
+def supa_fetch_hit_tags(b: int, first_hit: int, max_hits: int, dst_dev, stream=None) -> int:
+    n = _I64()
+    _check(lib().supa_fetch_hit_tags(b, int(first_hit), int(max_hits), _ptr(dst_dev), ctypes.byref(n),
+                                     _stream(stream)), "supa_fetch_hit_tags")
+    return n.value
+
+
+def supa_voxelize(b: int, shower_begin: int, shower_end: int, grid_dev, out_of_roi_dev=None, stream=None):
+    _check(lib().supa_voxelize(b, int(shower_begin), int(shower_end), _ptr(grid_dev), _ptr(out_of_roi_dev),
+                               _stream(stream)), "supa_voxelize")
+
+
+def supa_voxelize_hits(g: int, hits_dev, offsets_dev, n_showers: int, roi_x0_dev, roi_y0_dev, grid_dev,
+                       out_of_roi_dev=None, stream=None):
+    _check(lib().supa_voxelize_hits(g, _ptr(hits_dev), _ptr(offsets_dev), int(n_showers), _ptr(roi_x0_dev),
+                                    _ptr(roi_y0_dev), _ptr(grid_dev), _ptr(out_of_roi_dev), _stream(stream)),
+           "supa_voxelize_hits")
+
+
+# ---- marshalling helpers ----------------------------------------------------
+
+def primaries_to_device(prims: np.ndarray, device="cuda"):
+    """Copy a PRIMARY_DTYPE array into a device byte tensor (24 bytes each)."""
+    import torch
+    assert prims.dtype == _inputs.PRIMARY_DTYPE
+    t = torch.from_numpy(np.ascontiguousarray(prims).view(np.uint8))
+    return t.to(device)
+
+
+class _DeviceArray:
+    """Exposes a library-owned device buffer through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def device_view(ptr: int, shape: tuple, dtype):
+    """Zero-copy torch view of a library-owned device buffer."""
+    import torch
+    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.float64: "<f8", torch.float32: "<f4"}[dtype]
+    if int(np.prod(shape)) == 0:
+        return torch.zeros(shape, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, tuple(shape), typestr), device="cuda")
+
+
+def info_arrays(info: supa_batch_info):
+    """Per-shower result buffers of a batch as torch views (valid until the
+    batch's next simulation).  counts and steps are uint32 read as int32."""
+    import torch
+    n, L = info.n_showers, info.max_layers
+    return dict(
+        offsets=device_view(info.offsets_dev, (n + 1,), torch.int64),
+        counts=device_view(info.counts_dev, (n,), torch.int32),
+        steps=device_view(info.steps_dev, (n,), torch.int32),
+        layer_sum=device_view(info.layer_sums_dev, (n, L), torch.float64),
+        dead=device_view(info.dead_dev, (n,), torch.float64),
+        leak=device_view(info.leak_dev, (n,), torch.float64),
+        escape=device_view(info.escape_dev, (n,), torch.float64),
+    )
