@@ -90,7 +90,7 @@ def test_escape_and_leak_paths():
 
 @pytest.mark.parametrize("cfg", [
     {"stack_depth": 64, "flush_threshold": 32, "warps_per_block": 4},
-    {"stack_depth": 256, "flush_threshold": 256, "warps_per_block": 16, "blocks_per_sm": 1},
+    {"stack_depth": 256, "flush_threshold": 256, "warps_per_block": 8, "blocks_per_sm": 1},
     {"lpt_order": 1},
 ])
 def test_launch_shapes_do_not_change_results(cfg):
