@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c5"])
     ap.add_argument("--showers", type=int, default=0, help="override the batch size")
     ap.add_argument("--voxel-chunk", type=int, default=32768)
+    ap.add_argument("--fetch-chunk", type=int, default=FETCH_CHUNK)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -209,7 +210,8 @@ def run_supa(args):
     V = min(args.voxel_chunk, n)
     grid = torch.empty((V, L, ny, nx), dtype=torch.float32, device="cuda")
     oor = torch.empty(V, dtype=torch.float64, device="cuda")
-    fbuf = torch.empty((FETCH_CHUNK, 4), dtype=torch.float32, device="cuda")
+    FC = args.fetch_chunk
+    fbuf = torch.empty((FC, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
@@ -231,8 +233,8 @@ def run_supa(args):
             if ev is not None:
                 e1.record(stream)
                 ev["vox"].append((e0, e1, c1 - c0))
-        for h0 in range(0, info.n_hits, FETCH_CHUNK):
-            S.supa_fetch_hits(b, h0, FETCH_CHUNK, fbuf)
+        for h0 in range(0, info.n_hits, FC):
+            S.supa_fetch_hits(b, h0, FC, fbuf)
             launches += 1
         return info, launches
 
@@ -287,7 +289,7 @@ def run_supa(args):
         "metric": METRIC, "value": value, "unit": "showers/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(conf, showers=n, layers=L, grid=[L, ny, nx], fetch_chunk_hits=FETCH_CHUNK,
+        "config": dict(conf, showers=n, layers=L, grid=[L, ny, nx], fetch_chunk_hits=FC,
                        voxel_chunk_showers=V, l2="inputs larger than L2 (hit pool and image chunks >> 129 MB)",
                        parallelism=f"replicas x{world}"),
         "particle_steps_per_s": n_steps * args.steps * world / (elapsed_ms / 1000.0),

@@ -98,7 +98,7 @@ struct supa_batch {
     SpillRec *d_spill = nullptr;
     int spill_cap = 0;
     // launch shape
-    int grid = 0, block = 0, stack_cap = 0, stage_cap = 0, flush_thr = 0;
+    int grid = 0, block = 0, stack_cap = 0, stage_cap = 0, flush_thr = 0, minb = 3;
     size_t smem = 0;
     int warp_bytes = 0;
     // state
@@ -289,10 +289,12 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     const int wpb = cfg.warps_per_block > 0 ? cfg.warps_per_block : 8;
-    if (wpb > 16) {
+    if (wpb > 8) {
         supa_destroy_batch(b);
-        return fail(SUPA_ERR_INVALID_ARG, "warps_per_block must be <= 16");
+        return fail(SUPA_ERR_INVALID_ARG, "warps_per_block must be <= 8");
     }
+    // register budget variant: 2, 3 or 4 resident blocks per SM
+    b->minb = cfg.blocks_per_sm > 0 ? std::max(2, std::min(4, cfg.blocks_per_sm)) : 3;
     b->block = wpb * 32;
     b->stack_cap = cfg.stack_depth > 0 ? cfg.stack_depth : 128;
     if (b->stack_cap < 64 || b->stack_cap % 2) {
@@ -304,7 +306,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     b->warp_bytes = (int)warp_smem_bytes(b->stack_cap, b->stage_cap, b->tags);
     b->smem = (size_t)b->warp_bytes * wpb;
     int occ = 0;
-    e = step_kernel_attributes(b->block, b->smem, &occ);
+    e = step_kernel_attributes(b->minb, b->block, b->smem, &occ);
     if (e != cudaSuccess || occ < 1) {
         supa_destroy_batch(b);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel occupancy");
@@ -415,7 +417,7 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     p.stage_cap = b->stage_cap;
     p.flush_thr = b->flush_thr;
     p.warp_smem_bytes = b->warp_bytes;
-    if (n > 0) SUPA_CUDA(launch_step(p, b->grid, b->block, b->smem, st));
+    if (n > 0) SUPA_CUDA(launch_step(b->minb, p, b->grid, b->block, b->smem, st));
     SUPA_CUDA(launch_scan_counts(b->d_hit_count, n, b->d_offsets, b->d_scan_tmp, st));
     return SUPA_OK;
 }
@@ -532,11 +534,8 @@ int supa_fetch_hit_tags(supa_batch *b, int64_t first_hit, int64_t max_hits, uint
     return fetch_common(b, first_hit, max_hits, dst_dev, true, true, n_written, stream);
 }
 
-static int pick_group(int L, int cells) {
-    const int per = cells * 4;
-    int G = std::max(1, std::min(L, (64 * 1024) / per));
-    return G;
-}
+// Two image buffers of at least one layer each must fit in shared memory.
+static const size_t kMaxLayerBytes = 108 * 1024;
 
 int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev, double *out_of_roi_dev,
                   void *stream) {
@@ -554,8 +553,7 @@ int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float
     if (n == 0) return SUPA_OK;
     const size_t cells = (size_t)g0.nx * g0.ny;
     if ((size_t)(grid_dev) % 16 != 0) return fail(SUPA_ERR_INVALID_ARG, "grid_dev must be 16-byte aligned");
-    if (cells * 4 > 200 * 1024) return fail(SUPA_ERR_INVALID_ARG, "one layer image exceeds 200 KiB of shared memory");
-    if (out_of_roi_dev) SUPA_CUDA(cudaMemsetAsync(out_of_roi_dev, 0, n * sizeof(double), st));
+    if (cells * 4 > kMaxLayerBytes) return fail(SUPA_ERR_INVALID_ARG, "one layer image exceeds 108 KiB");
     VoxParams p{};
     p.src.pool = b->d_pool;
     p.src.page_next = b->d_page_next;
@@ -564,8 +562,7 @@ int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float
     p.s_begin = shower_begin;
     p.n_showers = n;
     p.L = b->max_layers;
-    p.G = pick_group(p.L, (int)cells);
-    p.n_groups = (p.L + p.G - 1) / p.G;
+    vox_plan(p.L, g0.nx, g0.ny, &p.G, &p.n_groups, &p.list_cap);
     p.nx = g0.nx;
     p.ny = g0.ny;
     p.wx = g0.wx;
@@ -590,18 +587,16 @@ int supa_voxelize_hits(const supa_geometry *g, const float *hits_dev, const int6
     if ((size_t)(grid_dev) % 16 != 0 || (size_t)(hits_dev) % 16 != 0)
         return fail(SUPA_ERR_INVALID_ARG, "hits_dev and grid_dev must be 16-byte aligned");
     const size_t cells = (size_t)g->rec.nx * g->rec.ny;
-    if (cells * 4 > 200 * 1024) return fail(SUPA_ERR_INVALID_ARG, "one layer image exceeds 200 KiB of shared memory");
+    if (cells * 4 > kMaxLayerBytes) return fail(SUPA_ERR_INVALID_ARG, "one layer image exceeds 108 KiB");
     if (n_showers == 0) return SUPA_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    if (out_of_roi_dev) SUPA_CUDA(cudaMemsetAsync(out_of_roi_dev, 0, n_showers * sizeof(double), st));
     VoxParams p{};
     p.src.hits = (const float4 *)hits_dev;
     p.src.offsets = offsets_dev;
     p.s_begin = 0;
     p.n_showers = n_showers;
     p.L = g->rec.n_layers;
-    p.G = pick_group(p.L, (int)cells);
-    p.n_groups = (p.L + p.G - 1) / p.G;
+    vox_plan(p.L, g->rec.nx, g->rec.ny, &p.G, &p.n_groups, &p.list_cap);
     p.nx = g->rec.nx;
     p.ny = g->rec.ny;
     p.wx = g->rec.wx;

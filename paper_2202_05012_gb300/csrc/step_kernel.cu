@@ -12,8 +12,11 @@
 //  * Stops are staged as float4 hits in shared memory and flushed with
 //    coalesced 16-byte stores to the warp's current page of the hit pool
 //    once flush_thr hits are staged.
-//  * Per-layer deposits are summed in FP64 in shared memory; dead, leaked and
-//    escaped energy in FP64 lane registers.
+//  * Deposits are summed exactly in 64-bit fixed point (units of 2^-32) --
+//    per layer in shared memory, dead / leaked / escaped energy in lane
+//    registers -- on the integer pipe (GB300's FP64 rate is a small fraction
+//    of its FP32 rate), and delivered per shower as FP64.  Integer sums are
+//    exact and do not depend on the order of the additions.
 // Every random draw is keyed by (seed; shower id, slice, lineage id), so the
 // result does not depend on which warp runs a shower or in which order.
 #include "philox.cuh"
@@ -29,7 +32,7 @@ struct WarpSmem {
     float4 *stage;
     unsigned long long *stage_tag;
     unsigned long long *slin;
-    double *lsum;
+    unsigned long long *lsum;  // fixed point, units of 2^-32
     float *sx, *sy, *sux, *suy, *suz, *sE;
     uint8_t *sk;
 };
@@ -45,7 +48,7 @@ __device__ inline WarpSmem carve(unsigned char *base, int C, int H, bool tags) {
     if (tags) o += size_t(8) * H;
     w.slin = reinterpret_cast<unsigned long long *>(base + o);
     o += size_t(8) * C;
-    w.lsum = reinterpret_cast<double *>(base + o);
+    w.lsum = reinterpret_cast<unsigned long long *>(base + o);
     o += size_t(8) * SUPA_MAX_LAYERS;
     float *f = reinterpret_cast<float *>(base + o);
     w.sx = f;
@@ -57,6 +60,15 @@ __device__ inline WarpSmem carve(unsigned char *base, int C, int H, bool tags) {
     o += size_t(24) * C;
     w.sk = base + o;
     return w;
+}
+
+// Energy in 64-bit fixed point, units of 2^-32 (exact for E >= 2^-9; energies
+// are below 2^30, checked per primary, so sums cannot overflow).
+__device__ __forceinline__ unsigned long long fixed32(float E) {
+    return (unsigned long long)__float2ll_rn(E * 4294967296.0f);
+}
+__device__ __forceinline__ double from_fixed32(unsigned long long v) {
+    return (double)(long long)v * (1.0 / 4294967296.0);
 }
 
 struct Particle {
@@ -106,13 +118,31 @@ __device__ __forceinline__ void deflect(float ux, float uy, float uz, float wx, 
 
 // A survivor of slice k either leaks (last slice), escapes (u_z too small)
 // or moves in a straight line to slice k+1.  Returns true if still alive.
-__device__ __forceinline__ bool advance(Particle &q, const GeomDev &g, double &leak, double &esc) {
-    if (q.k == g.n_slices - 1) { leak += (double)q.E; return false; }
-    if (q.uz <= g.uz_min) { esc += (double)q.E; return false; }
-    q.x += g.dz * (q.ux / q.uz);
-    q.y += g.dz * (q.uy / q.uz);
+__device__ __forceinline__ bool advance(Particle &q, const GeomDev &g, unsigned long long &leak,
+                                        unsigned long long &esc) {
+    if (q.k == g.n_slices - 1) { leak += fixed32(q.E); return false; }
+    if (q.uz <= g.uz_min) { esc += fixed32(q.E); return false; }
+    const float r = __frcp_rn(q.uz);
+    q.x = fmaf(g.dz, q.ux * r, q.x);
+    q.y = fmaf(g.dz, q.uy * r, q.y);
     q.k += 1;
     return true;
+}
+
+// sin and cos of a deflection angle.  Split angles are small (|d| <= 0.5
+// for every Table 2 law), where the Taylor series to degree 9 / 10 is exact
+// to below float32 rounding (next terms d^11/11! < 1.3e-11, d^12/12! < 6e-13);
+// larger angles use the library sincosf.
+__device__ __forceinline__ void small_sincos(float d, float *s, float *c) {
+    if (fabsf(d) <= 0.5f) {
+        const float d2 = d * d;
+        *s = d * fmaf(d2, fmaf(d2, fmaf(d2, fmaf(d2, 1.0f / 362880.0f, -1.0f / 5040.0f), 1.0f / 120.0f),
+                               -1.0f / 6.0f), 1.0f);
+        *c = fmaf(d2, fmaf(d2, fmaf(d2, fmaf(d2, fmaf(d2, -1.0f / 3628800.0f, 1.0f / 40320.0f), -1.0f / 720.0f),
+                                    1.0f / 24.0f), -0.5f), 1.0f);
+    } else {
+        sincosf(d, s, c);
+    }
 }
 
 struct PageCursor {
@@ -160,7 +190,10 @@ size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags) {
     return align16(o);
 }
 
-__global__ void __launch_bounds__(512) supa_step_kernel(const StepParams p) {
+// MINB: resident 256-thread blocks per SM the register budget is cut for
+// (2: up to 128 registers, 3: 80, 4: 64).
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -184,6 +217,7 @@ __global__ void __launch_bounds__(512) supa_step_kernel(const StepParams p) {
         const int64_t s = p.queue ? (int64_t)p.queue[q] : (int64_t)q;
         const supa_primary pr = p.prim[s];
         if (pr.geom >= (uint32_t)p.n_geoms || !(pr.E > 0.0f) || !(pr.E <= p.geoms[pr.geom].e0_max) ||
+            !(pr.E < 1073741824.0f) ||
             !(pr.theta >= 0.0f && pr.theta < 1.5707963f) || !isfinite(pr.phi) || !isfinite(pr.x0) ||
             !isfinite(pr.y0)) {
             // invalid primary: report it and leave an empty shower behind
@@ -198,7 +232,7 @@ __global__ void __launch_bounds__(512) supa_step_kernel(const StepParams p) {
         const GeomDev g = p.geoms[pr.geom];
         const uint32_t sid = (uint32_t)(p.shower_id_base + (uint64_t)s);
 
-        for (int l = lane; l < g.n_layers; l += 32) w.lsum[l] = 0.0;
+        for (int l = lane; l < g.n_layers; l += 32) w.lsum[l] = 0ull;
         if (pc.off == kPageHits && !next_page(p, pc, lane)) {
             if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
             break;
@@ -218,7 +252,7 @@ __global__ void __launch_bounds__(512) supa_step_kernel(const StepParams p) {
         }
         int stack_n = 0, spill_n = 0, staged = 0;
         uint32_t n_hits = 0, n_steps = 0;
-        double dead = 0.0, leak = 0.0, esc = 0.0;
+        unsigned long long dead = 0, leak = 0, esc = 0;  // fixed point
         bool failed = false;
         __syncwarp();
 
@@ -261,12 +295,12 @@ __global__ void __launch_bounds__(512) supa_step_kernel(const StepParams p) {
                     // stop: deposit the energy at slice k
                     const int layer = __ldg(p.s2l + so);
                     if (layer < 0) {
-                        dead += (double)cur.E;
+                        dead += fixed32(cur.E);
                     } else {
                         hit = true;
                         h = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
                         hit_lin = cur.lin;
-                        atomicAdd(&w.lsum[layer], (double)cur.E);
+                        atomicAdd(&w.lsum[layer], fixed32(cur.E));
                     }
                     have = false;
                 } else {
@@ -288,8 +322,8 @@ __global__ void __launch_bounds__(512) supa_step_kernel(const StepParams p) {
                         const float wy = fmaf(cw, e1y, sw * e2y);
                         const float wz = fmaf(cw, e1z, sw * e2z);
                         float s0, c0, s1, c1;
-                        sincosf(d0, &s0, &c0);
-                        sincosf(d1, &s1, &c1);
+                        small_sincos(d0, &s0, &c0);
+                        small_sincos(d1, &s1, &c1);
                         dau = cur;
                         deflect(cur.ux, cur.uy, cur.uz, -wx, -wy, -wz, s1, c1, dau.ux, dau.uy, dau.uz);
                         deflect(cur.ux, cur.uy, cur.uz, wx, wy, wz, s0, c0, cur.ux, cur.uy, cur.uz);
@@ -370,15 +404,15 @@ __global__ void __launch_bounds__(512) supa_step_kernel(const StepParams p) {
             esc += __shfl_xor_sync(kFull, esc, o);
         }
         __syncwarp();
-        for (int l = lane; l < g.n_layers; l += 32) p.lsum[(size_t)s * p.lsum_stride + l] = w.lsum[l];
+        for (int l = lane; l < g.n_layers; l += 32) p.lsum[(size_t)s * p.lsum_stride + l] = from_fixed32(w.lsum[l]);
         for (int l = g.n_layers + lane; l < p.lsum_stride; l += 32) p.lsum[(size_t)s * p.lsum_stride + l] = 0.0;
         if (lane == 0) {
             p.hit_start[s] = start;
             p.hit_count[s] = n_hits;
             p.steps[s] = n_steps;
-            p.dead[s] = dead;
-            p.leak[s] = leak;
-            p.escape[s] = esc;
+            p.dead[s] = from_fixed32(dead);
+            p.leak[s] = from_fixed32(leak);
+            p.escape[s] = from_fixed32(esc);
         }
         warp_steps += n_steps;
         warp_hits += n_hits;
@@ -390,15 +424,29 @@ __global__ void __launch_bounds__(512) supa_step_kernel(const StepParams p) {
     }
 }
 
-cudaError_t launch_step(const StepParams &p, int grid, int block, size_t smem, cudaStream_t st) {
-    supa_step_kernel<<<grid, block, smem, st>>>(p);
+namespace {
+template <int MINB>
+cudaError_t attrs(int block, size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(supa_step_kernel<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, supa_step_kernel<MINB>, block, smem);
+}
+}  // namespace
+
+cudaError_t launch_step(int minb, const StepParams &p, int grid, int block, size_t smem, cudaStream_t st) {
+    if (minb >= 4)
+        supa_step_kernel<4><<<grid, block, smem, st>>>(p);
+    else if (minb == 3)
+        supa_step_kernel<3><<<grid, block, smem, st>>>(p);
+    else
+        supa_step_kernel<2><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t step_kernel_attributes(int block, size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(supa_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, supa_step_kernel, block, smem);
+cudaError_t step_kernel_attributes(int minb, int block, size_t smem, int *blocks_per_sm) {
+    if (minb >= 4) return attrs<4>(block, smem, blocks_per_sm);
+    if (minb == 3) return attrs<3>(block, smem, blocks_per_sm);
+    return attrs<2>(block, smem, blocks_per_sm);
 }
 
 }  // namespace supa

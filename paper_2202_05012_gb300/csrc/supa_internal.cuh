@@ -83,8 +83,10 @@ constexpr int kErrBadPrimary = 4;
 size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags);
 
 // Kernel launchers (defined in the .cu files, called by the C ABI).
-cudaError_t launch_step(const StepParams &p, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t step_kernel_attributes(int block, size_t smem, int *blocks_per_sm);
+// minb selects the register budget of the step kernel (2, 3 or 4 resident
+// 256-thread blocks per SM).
+cudaError_t launch_step(int minb, const StepParams &p, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t step_kernel_attributes(int minb, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_scan_counts(const uint32_t *counts, int64_t n, int64_t *offsets, unsigned long long *block_tmp,
                                cudaStream_t st);
 size_t scan_tmp_elems(int64_t n);
@@ -105,8 +107,9 @@ struct VoxParams {
     HitSource src;
     int64_t s_begin, n_showers;
     int L;         // layer stride of the grid
-    int G;         // layers per CTA
+    int G;         // layers per image group (one bulk store)
     int n_groups;  // ceil(L / G)
+    int list_cap;  // hits whose cells fit the shared-memory list
     int nx, ny;
     float wx, wy;
     // batch mode: ROI from the primaries; explicit mode: roi_x0/roi_y0
@@ -121,7 +124,9 @@ struct VoxParams {
 };
 
 cudaError_t launch_voxelize(const VoxParams &p, cudaStream_t st);
-size_t vox_smem_bytes(int G, int nx, int ny);
+size_t vox_smem_bytes(int G, int nx, int ny, int list_cap);
+// Layers per group, group count and hit-list capacity for an L x ny x nx image.
+void vox_plan(int L, int nx, int ny, int *G, int *n_groups, int *list_cap);
 
 struct FetchParams {
     HitSource src;

@@ -51,9 +51,13 @@ def _shower_ids(offsets):
     return np.repeat(np.arange(len(offsets) - 1), np.diff(offsets))
 
 
-def compare(gpu, ora, geoms, prims):
+def compare(gpu, ora, geoms, prims, pos_rtol=RTOL):
     """Per-shower comparison; returns a dict of statistics and asserts the
-    tolerances on every shower whose decisions all agree."""
+    tolerances on every shower whose decisions all agree.
+
+    pos_rtol: position tolerance.  A step moves x by dz * u_x / u_z, so an
+    FP32 error e in the direction becomes e / u_z in the slope: near grazing
+    incidence (u_z down to the escape cut) callers pass a looser bound."""
     n = len(prims)
     gidx = prims["geom"].astype(np.int64)
     dz = np.array([geoms[i].dz for i in gidx])
@@ -107,7 +111,7 @@ def compare(gpu, ora, geoms, prims):
         max_err_E=float(err_E.max(initial=0)),
     )
     assert np.array_equal(zg, zo), "hit depths must be the slice planes exactly"
-    assert stats["max_err_x"] <= RTOL and stats["max_err_y"] <= RTOL, stats
+    assert stats["max_err_x"] <= pos_rtol and stats["max_err_y"] <= pos_rtol, stats
     assert stats["max_err_E"] <= RTOL, stats
     assert stats["flip_rate"] < MAX_FLIP_RATE, stats
     # per-shower bookkeeping on clean showers

@@ -14,13 +14,13 @@ from gpu_helpers import compare, run_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _check(geoms, prims, seed, cfg=None, base=0):
+def _check(geoms, prims, seed, cfg=None, base=0, pos_rtol=1e-5):
     gpu = run_gpu(geoms, prims, seed, cfg=cfg, shower_id_base=base)
     if len(geoms) == 1:
         ora = oracle.simulate(geoms[0], prims, seed, shower_id_base=base, n_threads=8)
     else:
         ora = _oracle_multi(geoms, prims, seed, base)
-    return compare(gpu, ora, geoms, prims), gpu, ora
+    return compare(gpu, ora, geoms, prims, pos_rtol=pos_rtol), gpu, ora
 
 
 def _oracle_multi(geoms, prims, seed, base):
@@ -84,7 +84,9 @@ def test_dead_material_literal_split_fixed_angles():
 def test_escape_and_leak_paths():
     g = inputs.supa_d(10, p_stop=0.005, p_split=0.3, e_min=0.0)
     p = inputs.primaries(300, 23, e_lo=1.0, e_hi=5.0, theta_max_deg=88.0)
-    st, gpu, ora = _check([g], p, seed=9)
+    # near the escape cut the slope u_x/u_z amplifies FP32 direction error by
+    # up to 1/uz_min = 1000: positions are held to 1e-5 * 100 here
+    st, gpu, ora = _check([g], p, seed=9, pos_rtol=1e-3)
     assert ora["escape"].sum() > 0 and ora["leak"].sum() > 0
 
 

@@ -68,10 +68,12 @@ def test_batch_voxelize_matches_oracle_and_conserves():
         grid = torch.full((200, 30, 64, 64), -1.0, dtype=torch.float32, device="cuda")
         oor = torch.zeros(200, dtype=torch.float64, device="cuda")
         S.supa_voxelize(b, 0, 200, grid, oor)
-        # chunked voxelisation gives the same images
+        # chunked voxelisation gives the same images (float32 cell sums from
+        # shared-memory atomics: equal up to the order of additions)
         g2 = torch.full((120, 30, 64, 64), -1.0, dtype=torch.float32, device="cuda")
         S.supa_voxelize(b, 80, 200, g2, None)
-        assert torch.equal(g2, grid[80:])
+        assert torch.equal(g2 != 0, grid[80:] != 0)
+        assert torch.allclose(g2, grid[80:], rtol=1e-6, atol=0)
         grid_g = grid.cpu().numpy().astype(np.float64)
         arr = S.info_arrays(info)
         ls = arr["layer_sum"].cpu().numpy()
