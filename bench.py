@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="supa", choices=["supa", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"])
     ap.add_argument("--showers", type=int, default=0, help="override the batch size")
     ap.add_argument("--voxel-chunk", type=int, default=32768)
     ap.add_argument("--fetch-chunk", type=int, default=FETCH_CHUNK)
@@ -369,10 +369,85 @@ def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
             "d2h_bytes_per_step": d2h}
 
 
+def run_c3(args):
+    """Uneven batch: 4M showers, E log-uniform [1,1000] (multiplicity spans
+    ~1000x), geometries of 10/20/30/50 layers mixed in each persistent launch;
+    launch shape chosen by the autotuner; each 1M-shower launch replayed from a
+    captured CUDA graph.  Simulation only (hits and FP64 layer sums)."""
+    import torch
+
+    from paper_2202_05012_gb300 import inputs
+    from paper_2202_05012_gb300 import supa as S
+
+    torch.cuda.set_device(0)
+    n = args.showers or 4_000_000
+    sub = min(n, 1_000_000)
+    geoms, prims = inputs.workload_c3(n)
+    gh = [S.supa_init_geometry(g) for g in geoms]
+    d_prim = S.primaries_to_device(prims)
+    cfg = {"lpt_order": 1, "max_hits": int(sub * 5000) + (16 << 20)}
+    tuned, tune_ms = S.supa_autotune(gh, d_prim, sub, seed=2, cfg=cfg)
+    b = S.supa_batch_create(gh, sub, tuned)
+    graphs = []
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    for j in range(0, n, sub):
+        m = min(sub, n - j)
+        view = d_prim[j * 24:(j + m) * 24]
+        with torch.cuda.stream(s):
+            S.supa_simulate(b, view, m, 2, j)  # warm the launch path before capture
+            S.supa_batch_get_info(b)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+                S.supa_simulate(b, view, m, 2, j)
+            graphs.append(g)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+
+    def step():
+        steps = hits = 0
+        for g in graphs:
+            g.replay()
+            info = S.supa_batch_get_info(b)
+            steps += info.n_steps
+            hits += info.n_hits
+        return steps, hits
+
+    for _ in range(args.warmup):
+        step()
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        steps, hits = step()
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    out = {
+        "metric": METRIC, "value": args.steps * n / (ms / 1000.0), "unit": "showers/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "uneven batch: 4M showers, E log-U[1,1000], 10/20/30/50-layer geometries mixed per "
+                               "launch, graph-captured 1M-shower launches, autotuned", "showers": n,
+                   "showers_per_launch": sub, "launch_config": tuned, "autotune_sample_ms": tune_ms},
+        "particle_steps_per_s": args.steps * steps / (ms / 1000.0), "hits_per_shower": hits / n,
+        "steps_per_shower": steps / n, "gpu_launches": args.steps * len(graphs) * (1 + 3 + 3), "clocks": clk,
+    }
+    S.supa_destroy_batch(b)
+    for g in gh:
+        S.supa_destroy_geometry(g)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c3":
+        run_c3(args)
     else:
         run_supa(args)
 

@@ -157,6 +157,17 @@ int supa_simulate_batch(const supa_geometry *const *geoms, int32_t n_geoms, cons
                         int64_t n, uint64_t seed, uint64_t shower_id_base, const supa_launch_config *cfg,
                         supa_batch **out, void *stream);
 
+/* Autotuner of the persistent step kernel's launch shape (no counterpart in
+ * the paper, which runs one particle at a time): times supa_simulate on the
+ * first min(n, 131072) showers of prim_dev for candidate register budgets
+ * (blocks_per_sm 2..4), warps per block, shared-memory stack depths and flush
+ * thresholds (coordinate descent), and writes the fastest into *cfg, keeping
+ * its other fields (max_hits is taken per shower of the full batch).
+ * *best_ms (may be NULL) receives the sample's time.  Synchronous; allocates
+ * temporary batches. */
+int supa_autotune(const supa_geometry *const *geoms, int32_t n_geoms, const supa_primary *prim_dev, int64_t n,
+                  uint64_t seed, supa_launch_config *cfg, double *best_ms, void *stream);
+
 /* Wait for the batch's last simulation on `stream` and report totals and
  * result pointers.  Returns SUPA_ERR_OVERFLOW if the hit pool or a particle
  * stack overflowed (re-run with a smaller batch or a larger max_hits). */
@@ -179,7 +190,11 @@ int supa_fetch_hit_tags(supa_batch *b, int64_t first_hit, int64_t max_hits, uint
  * the energy of the points inside it).  grid_dev is float32
  * [shower_end - shower_begin][max_layers][ny][nx]; out_of_roi_dev (may be
  * NULL) receives per shower the FP64 energy outside every region.  All
- * geometries of the batch must share nx, ny, wx, wy.  Every cell is written. */
+ * geometries of the batch must share nx, ny, wx, wy.  Every cell is written.
+ * May be enqueued directly after supa_simulate on the same stream (no host
+ * synchronisation, so both can be captured in one CUDA graph); if that
+ * simulation fails, supa_batch_get_info reports it and the images are
+ * unspecified. */
 int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev,
                   double *out_of_roi_dev, void *stream);
 

@@ -301,7 +301,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
         supa_destroy_batch(b);
         return fail(SUPA_ERR_INVALID_ARG, "stack_depth must be an even number >= 64");
     }
-    b->flush_thr = cfg.flush_threshold > 0 ? cfg.flush_threshold : 64;
+    b->flush_thr = cfg.flush_threshold > 0 ? cfg.flush_threshold : 128;
     b->stage_cap = b->flush_thr + 32;
     b->warp_bytes = (int)warp_smem_bytes(b->stack_cap, b->stage_cap, b->tags);
     b->smem = (size_t)b->warp_bytes * wpb;
@@ -436,6 +436,77 @@ int supa_simulate_batch(const supa_geometry *const *geoms, int32_t n_geoms, cons
     return rc;
 }
 
+int supa_autotune(const supa_geometry *const *geoms, int32_t n_geoms, const supa_primary *prim_dev, int64_t n,
+                  uint64_t seed, supa_launch_config *cfg, double *best_ms, void *stream) {
+    if (!geoms || !prim_dev || !cfg || n < 1) return fail(SUPA_ERR_INVALID_ARG, "supa_autotune: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t sample = std::min<int64_t>(n, 1 << 17);
+    supa_launch_config best = *cfg;
+    if (best.max_hits > 0) best.max_hits = (int64_t)((double)best.max_hits * sample / n) + (1 << 20);
+    if (best.blocks_per_sm <= 0) best.blocks_per_sm = 3;
+    if (best.warps_per_block <= 0) best.warps_per_block = 8;
+    if (best.stack_depth <= 0) best.stack_depth = 128;
+    if (best.flush_threshold <= 0) best.flush_threshold = 128;
+    cudaEvent_t e0, e1;
+    SUPA_CUDA(cudaEventCreate(&e0));
+    SUPA_CUDA(cudaEventCreate(&e1));
+    auto eval = [&](const supa_launch_config &c) -> double {
+        supa_batch *b = nullptr;
+        if (supa_batch_create(geoms, n_geoms, sample, &c, &b) != SUPA_OK) return INFINITY;
+        double ms = INFINITY;
+        supa_batch_info info;
+        if (supa_simulate(b, prim_dev, sample, seed, 0, stream) == SUPA_OK &&
+            supa_batch_get_info(b, &info, stream) == SUPA_OK) {
+            for (int rep = 0; rep < 2; ++rep) {
+                float t = 0.f;
+                if (cudaEventRecord(e0, st) != cudaSuccess) break;
+                if (supa_simulate(b, prim_dev, sample, seed, 0, stream) != SUPA_OK) break;
+                if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+                cudaEventElapsedTime(&t, e0, e1);
+                ms = std::min(ms, (double)t);
+            }
+        }
+        supa_destroy_batch(b);
+        return ms;
+    };
+    double best_t = eval(best);
+    auto consider = [&](supa_launch_config c) {
+        const double t = eval(c);
+        if (t < best_t) {
+            best_t = t;
+            best = c;
+        }
+    };
+    const int shapes[][2] = {{2, 8}, {3, 8}, {4, 8}, {2, 4}, {3, 4}, {4, 4}};
+    const supa_launch_config start = best;
+    for (auto &s : shapes) {
+        supa_launch_config c = start;
+        c.blocks_per_sm = s[0];
+        c.warps_per_block = s[1];
+        if (c.blocks_per_sm != start.blocks_per_sm || c.warps_per_block != start.warps_per_block) consider(c);
+    }
+    for (int depth : {96, 128, 192, 256}) {
+        supa_launch_config c = best;
+        c.stack_depth = depth;
+        if (depth != best.stack_depth) consider(c);
+    }
+    for (int ft : {32, 64, 128, 256}) {
+        supa_launch_config c = best;
+        c.flush_threshold = ft;
+        if (ft != best.flush_threshold) consider(c);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!std::isfinite(best_t)) return fail(SUPA_ERR_CUDA, "supa_autotune: no candidate launch shape ran");
+    cfg->blocks_per_sm = best.blocks_per_sm;
+    cfg->warps_per_block = best.warps_per_block;
+    cfg->stack_depth = best.stack_depth;
+    cfg->flush_threshold = best.flush_threshold;
+    if (best_ms) *best_ms = best_t;
+    g_last_error.clear();
+    return SUPA_OK;
+}
+
 int supa_batch_get_info(supa_batch *b, supa_batch_info *info, void *stream) {
     if (!b || !info) return fail(SUPA_ERR_INVALID_ARG, "supa_batch_get_info: null argument");
     if (b->last_n < 0) return fail(SUPA_ERR_NOT_READY, "no simulation has run on this batch");
@@ -540,7 +611,9 @@ static const size_t kMaxLayerBytes = 108 * 1024;
 int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev, double *out_of_roi_dev,
                   void *stream) {
     if (!b || !grid_dev) return fail(SUPA_ERR_INVALID_ARG, "supa_voxelize: null argument");
-    if (!b->info_valid) return fail(SUPA_ERR_NOT_READY, "call supa_batch_get_info after the simulation first");
+    // Stream order is enough: the images read what the last supa_simulate on
+    // this stream wrote, so both calls can sit in one captured graph.
+    if (b->last_n < 0) return fail(SUPA_ERR_NOT_READY, "no simulation has been enqueued on this batch");
     if (shower_begin < 0 || shower_end < shower_begin || shower_end > b->last_n)
         return fail(SUPA_ERR_INVALID_ARG, "shower range [%lld, %lld) outside the batch", (long long)shower_begin,
                     (long long)shower_end);

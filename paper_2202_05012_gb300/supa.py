@@ -26,7 +26,7 @@ SUPA_ERR_NOT_READY = -6
 EXPORTED = (
     "supa_last_error", "supa_init_geometry", "supa_destroy_geometry", "supa_batch_create", "supa_destroy_batch",
     "supa_simulate", "supa_simulate_batch", "supa_batch_get_info", "supa_fetch_hits", "supa_fetch_hit_tags",
-    "supa_voxelize", "supa_voxelize_hits",
+    "supa_voxelize", "supa_voxelize_hits", "supa_autotune",
 )
 
 
@@ -100,6 +100,8 @@ def lib(build_if_missing: bool = True):
         L.supa_fetch_hit_tags.argtypes = [_VP, _I64, _I64, _VP, ctypes.POINTER(_I64), _VP]
         L.supa_voxelize.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP]
         L.supa_voxelize_hits.argtypes = [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]
+        L.supa_autotune.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, _VP, _I64, ctypes.c_uint64,
+                                    ctypes.POINTER(supa_launch_config), ctypes.POINTER(ctypes.c_double), _VP]
         for name in EXPORTED[1:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -227,6 +229,19 @@ def supa_voxelize_hits(g: int, hits_dev, offsets_dev, n_showers: int, roi_x0_dev
     _check(lib().supa_voxelize_hits(g, _ptr(hits_dev), _ptr(offsets_dev), int(n_showers), _ptr(roi_x0_dev),
                                     _ptr(roi_y0_dev), _ptr(grid_dev), _ptr(out_of_roi_dev), _stream(stream)),
            "supa_voxelize_hits")
+
+
+def supa_autotune(geoms: list[int], prim_dev, n: int, seed: int, cfg: dict | None = None,
+                  stream=None) -> tuple[dict, float]:
+    """Returns (tuned launch config as a dict, sample time in ms)."""
+    arr = (_VP * len(geoms))(*geoms)
+    c = supa_launch_config()
+    for k, v in (cfg or {}).items():
+        setattr(c, k, int(v))
+    ms = ctypes.c_double()
+    _check(lib().supa_autotune(arr, len(geoms), _ptr(prim_dev), int(n), int(seed) & (2**64 - 1), ctypes.byref(c),
+                               ctypes.byref(ms), _stream(stream)), "supa_autotune")
+    return {name: getattr(c, name) for name, _ in supa_launch_config._fields_}, ms.value
 
 
 # ---- marshalling helpers ----------------------------------------------------
