@@ -1,0 +1,104 @@
+"""FP64 oracle of the shower surrogate network -- TEST INFRASTRUCTURE.
+
+The surrogate has no counterpart in the SUPA paper: it is a small MLP that
+stands in for the low-energy tail of a shower (sub-showers below a cutoff
+energy E_s).  Architecture: 6 inputs -> 3 hidden layers of 256 with GELU
+(exact form x * Phi(x)) -> 60 outputs = 30 means mu_j and 30 log-variances
+s_j of the per-layer deposit fractions, layers counted from the sub-shower's
+start layer.  Loss: Gaussian negative log-likelihood averaged over layers and
+samples, L = mean_b (1/30) sum_j [ (y_j - mu_j)^2 exp(-s_j) / 2 + s_j / 2 ].
+Optimiser: Adam (Kingma & Ba 2015) with bias correction.
+
+Plain numpy float64, one matrix formula per step; no fusion or reordering.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erf
+
+N_IN, N_HID, N_OUT, N_LAYERS_OUT = 6, 256, 60, 30
+SHAPES = [(N_HID, N_IN), (N_HID, N_HID), (N_HID, N_HID), (N_OUT, N_HID)]
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    # d/dz [z Phi(z)] = Phi(z) + z phi(z)
+    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+
+
+def forward(params, X):
+    """params: list of (W [out, in], b [out]); X [B, 6].  Returns the output
+    [B, 60] and the cache needed by backward."""
+    acts = [X]
+    pre = []
+    h = X
+    for i, (W, b) in enumerate(params):
+        z = h @ W.T + b
+        pre.append(z)
+        h = gelu(z) if i < len(params) - 1 else z
+        acts.append(h)
+    return h, (acts, pre)
+
+
+def nll(out, Y):
+    """Gaussian NLL, mean over samples and the 30 layers."""
+    mu, s = out[:, :N_LAYERS_OUT], out[:, N_LAYERS_OUT:]
+    return float(np.mean(0.5 * (Y - mu) ** 2 * np.exp(-s) + 0.5 * s))
+
+
+def nll_grad(out, Y):
+    """d loss / d out, [B, 60]."""
+    B = out.shape[0]
+    mu, s = out[:, :N_LAYERS_OUT], out[:, N_LAYERS_OUT:]
+    r = Y - mu
+    g_mu = -r * np.exp(-s) / (B * N_LAYERS_OUT)
+    g_s = (0.5 - 0.5 * r * r * np.exp(-s)) / (B * N_LAYERS_OUT)
+    return np.concatenate([g_mu, g_s], axis=1)
+
+
+def backward(params, cache, g_out):
+    """Gradients [(dW, db)] of the loss given d loss / d out."""
+    acts, pre = cache
+    grads = [None] * len(params)
+    g = g_out
+    for i in range(len(params) - 1, -1, -1):
+        W, _ = params[i]
+        if i < len(params) - 1:
+            g = g * gelu_grad(pre[i])  # through the activation of layer i
+        grads[i] = (g.T @ acts[i], g.sum(axis=0))
+        g = g @ W  # d loss / d input of layer i
+    return grads
+
+
+def loss_and_grads(params, X, Y):
+    out, cache = forward(params, X)
+    return nll(out, Y), backward(params, cache, nll_grad(out, Y))
+
+
+class Adam:
+    def __init__(self, params, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.lr, self.b1, self.b2, self.eps = lr, beta1, beta2, eps
+        self.t = 0
+        self.m = [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
+        self.v = [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
+
+    def step(self, params, grads):
+        self.t += 1
+        c1 = 1.0 - self.b1 ** self.t
+        c2 = 1.0 - self.b2 ** self.t
+        new = []
+        for i, ((W, b), (gW, gb)) in enumerate(zip(params, grads)):
+            out = []
+            for j, (p, g) in enumerate(((W, gW), (b, gb))):
+                m = self.b1 * self.m[i][j] + (1 - self.b1) * g
+                v = self.b2 * self.v[i][j] + (1 - self.b2) * g * g
+                self.m[i] = tuple(m if jj == j else self.m[i][jj] for jj in range(2))
+                self.v[i] = tuple(v if jj == j else self.v[i][jj] for jj in range(2))
+                out.append(p - self.lr * (m / c1) / (np.sqrt(v / c2) + self.eps))
+            new.append(tuple(out))
+        return new

@@ -1,0 +1,56 @@
+// tc_gemm.cuh -- BF16 tensor-core GEMM for the surrogate network on sm_103a:
+// tcgen05.mma with FP32 accumulation in tensor memory (TMEM), operands staged
+// in shared memory by TMA (cp.async.bulk.tensor, 128-byte swizzle), stages
+// released through mbarriers, fused epilogues.
+//
+//   C[M x N] = A[M x K] * B[N x K]^T      (A, B bf16, K contiguous)
+//
+// One CTA owns a 128-row tile of C and all N <= 256 columns; blockIdx.y
+// splits K (split-K partial products are added with float atomics).
+// Warp 0 lane 0 issues TMA loads, warp 1 owns the TMEM allocation and its
+// lane 0 issues the MMAs, all four warps run the epilogue (warp w reads
+// TMEM lanes 32w..32w+31 = rows of the tile).
+//
+// Every mbarrier wait is bounded: on expiry the CTA records an error code,
+// stops issuing work, drains what it issued (again bounded), frees its TMEM
+// and returns.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace supa {
+
+enum GemmEpilogue : int {
+    EPI_BIAS_GELU = 0,  // z = acc + bias; store z (f32), gelu(z) (bf16) and its transpose (bf16)
+    EPI_BIAS_F32 = 1,   // acc + bias -> f32
+    EPI_GELU_BWD = 2,   // g = acc * gelu'(z); store g (bf16), its transpose, column sums (bias gradient)
+    EPI_ATOMIC_F32 = 3, // out += acc (split-K partial products)
+    EPI_GELU_ONLY = 4,  // z = acc + bias; store gelu(z) (bf16) only (inference)
+};
+
+struct GemmArgs {
+    int M, N, K;        // N in {64, 128, 256}; K multiple of 64
+    int k_blocks_per_split;
+    int epi;
+    const float *bias;  // [N]
+    float *out_f32;     // [M][ld] (BIAS_F32, ATOMIC_F32) or z (BIAS_GELU)
+    __nv_bfloat16 *out_bf16;   // [M][ld]
+    __nv_bfloat16 *outT_bf16;  // [N][ldT]
+    const float *z_in;  // [M][ld] (GELU_BWD)
+    float *colsum;      // [N] (GELU_BWD)
+    int ld, ldT;
+    int *error;         // device error word
+};
+
+constexpr int kGemmStages = 4;
+constexpr int kTileM = 128;
+constexpr int kTileK = 64;
+
+size_t gemm_smem_bytes(int N);
+cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &a, int splits, cudaStream_t st);
+// Tensor map of a row-major bf16 matrix [rows][cols] (cols contiguous) read in
+// boxes of 64 columns x box_rows rows with the 128-byte swizzle.
+int make_bf16_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+
+}  // namespace supa

@@ -115,6 +115,34 @@ def primaries(n: int, seed: int, *, e_lo: float, e_hi: float, log_uniform: bool 
     return p
 
 
+def mlp_init(seed: int, shapes=((256, 6), (256, 256), (256, 256), (60, 256))):
+    """Seeded initial parameters of the surrogate network: weights
+    U(-1/sqrt(fan_in), 1/sqrt(fan_in)), biases zero; float64 [(W, b)]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for n_out, n_in in shapes:
+        a = 1.0 / math.sqrt(n_in)
+        out.append((rng.uniform(-a, a, (n_out, n_in)), np.zeros(n_out)))
+    return out
+
+
+def subshower_primaries(n: int, seed: int, *, e_lo: float = 0.05, e_hi: float = 1.0, theta_max_deg: float = 45.0,
+                        n_layers: int = 30, slices_per_layer: int = 3) -> tuple[np.ndarray, np.ndarray]:
+    """Seeded sub-shower starts for surrogate training data: E log-uniform in
+    [e_lo, e_hi], polar angle U[0, theta_max], azimuth U[0, 2pi), start layer
+    U{0..n_layers-1} and start slice uniform within that layer.  Returns the
+    primaries (geometry field = start slice << 16) and the start slices."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = np.zeros(n, dtype=PRIMARY_DTYPE)
+    p["E"] = np.exp(rng.uniform(math.log(e_lo), math.log(e_hi), n)).astype(np.float32)
+    p["theta"] = rng.uniform(0.0, math.radians(theta_max_deg), n).astype(np.float32)
+    p["phi"] = rng.uniform(0.0, 2 * math.pi, n).astype(np.float32)
+    layer = rng.integers(0, n_layers, n)
+    k0 = (layer * slices_per_layer + rng.integers(0, slices_per_layer, n)).astype(np.uint32)
+    p["geom"] = k0 << np.uint32(16)
+    return p, k0
+
+
 # ---- the workloads of the benchmark configurations ------------------------
 
 def workload_c1(n: int = 1000):
