@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--pipeline", type=int, default=8,
+                    help="sub-batches per step; >1 overlaps simulation of one with downsampling of the previous")
     return ap.parse_args()
 
 
@@ -184,7 +186,235 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm ---
 
+class Pipeline:
+    """One step = the whole path over the batch, cut into sub-batches that
+    alternate between two library batches: stream A simulates sub-batch j+1
+    while stream B downsamples and fetches sub-batch j.  The step kernel is
+    ALU-bound and the downsampling kernel HBM-bound, so each SM runs both:
+    2 step-kernel blocks (80 registers) and 1 downsampling CTA per SM."""
+
+    def __init__(self, S, gh, d_prim, n, n_sub, seed, base, hits_per_shower_cap, V, L, ny, nx, FC):
+        import torch
+        self.S, self.seed, self.base, self.n = S, seed, base, n
+        self.sub = -(-n // n_sub)
+        self.ranges = [(j, min(n, j + self.sub)) for j in range(0, n, self.sub)]
+        cfg = {"max_hits": int(self.sub * hits_per_shower_cap) + (8 << 20), "lpt_order": 1,
+               "blocks_per_sm": 2, "voxel_ctas_per_sm": 1}
+        self.batches = [S.supa_batch_create([gh], self.sub, cfg) for _ in range(2)]
+        self.d_prim = d_prim
+        self.V = min(V, self.sub)
+        self.grid = torch.empty((self.V, L, ny, nx), dtype=torch.float32, device="cuda")
+        self.oor = torch.empty(self.V, dtype=torch.float64, device="cuda")
+        self.FC = FC
+        self.fbuf = torch.empty((FC, 4), dtype=torch.float32, device="cuda")
+        self.sA, self.sB = torch.cuda.Stream(), torch.cuda.Stream()
+        self.ev_sim = [torch.cuda.Event() for _ in range(2)]
+        self.ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def _sim(self, j, prim_src):
+        a, b = self.ranges[j]
+        if j >= 2:
+            self.sA.wait_event(self.ev_out[j % 2])  # the pool of batch j%2 is free again
+        self.S.supa_simulate(self.batches[j % 2], prim_src[a * 24:b * 24], b - a, self.seed, self.base + a,
+                             stream=self.sA)
+        self.ev_sim[j % 2].record(self.sA)
+
+    def step(self, prim_src=None, host_hits=None, host_ls=None):
+        """Returns (particle-steps, hits, kernel launches).  With host buffers
+        the hits and layer sums of every sub-batch are read back to them."""
+        import torch
+        S = self.S
+        prim_src = self.d_prim if prim_src is None else prim_src
+        cur = torch.cuda.current_stream()
+        self.sA.wait_stream(cur)
+        self.sB.wait_stream(cur)
+        steps = hits = launches = 0
+        self._sim(0, prim_src)
+        for j, (a, b) in enumerate(self.ranges):
+            if j + 1 < len(self.ranges):
+                self._sim(j + 1, prim_src)
+            bt = self.batches[j % 2]
+            self.sB.wait_event(self.ev_sim[j % 2])
+            info = S.supa_batch_get_info(bt, stream=self.sB)
+            launches += 1 + 3 + 3
+            m = b - a
+            for c0 in range(0, m, self.V):
+                S.supa_voxelize(bt, c0, min(m, c0 + self.V), self.grid, self.oor, stream=self.sB)
+                launches += 1
+            if host_hits is None:
+                for h0 in range(0, info.n_hits, self.FC):
+                    S.supa_fetch_hits(bt, h0, self.FC, self.fbuf, stream=self.sB)
+                    launches += 1
+            else:
+                got = 0
+                while got < info.n_hits:
+                    k = S.supa_fetch_hits(bt, got, self.FC, host_hits[hits + got:], dst_is_device=False,
+                                          stream=self.sB)
+                    got += k
+                    launches += 1
+                with torch.cuda.stream(self.sB):
+                    host_ls[a:b].copy_(S.info_arrays(info)["layer_sum"], non_blocking=True)
+            self.ev_out[j % 2].record(self.sB)
+            steps += info.n_steps
+            hits += info.n_hits
+        cur.wait_stream(self.sA)
+        cur.wait_stream(self.sB)
+        return steps, hits, launches
+
+    def close(self):
+        for b in self.batches:
+            self.S.supa_destroy_batch(b)
+
+
 def run_supa(args):
+    """Pipelined step (default): see Pipeline.  The kernels' rooflines and
+    phase times come from an isolated, serial pass over one sub-batch."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2202_05012_gb300 import supa as S
+
+    if args.pipeline <= 1:
+        return run_supa_serial(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    geom, prims, seed, conf = workload(args.workload, args.showers)
+    n = len(prims)
+    base = rank * n
+    if world > 1:
+        from paper_2202_05012_gb300 import inputs
+        prims = inputs.primaries(n, seed + 1000 * rank, e_lo=float(prims["E"].min()), e_hi=float(prims["E"].max()))
+    L, ny, nx = geom.n_layers, geom.ny, geom.nx
+    gh = S.supa_init_geometry(geom)
+    cap = {"c1": 400, "c2": 1500, "c5": 9000}[args.workload]
+    d_prim = S.primaries_to_device(prims)
+    pipe = Pipeline(S, gh, d_prim, n, args.pipeline, seed, base, cap, args.voxel_chunk, L, ny, nx, args.fetch_chunk)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pipe.step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    launches = n_steps = n_hits = 0
+    for _ in range(args.steps):
+        st, hi, nl = pipe.step()
+        n_steps, n_hits, launches = st, hi, launches + nl
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = args.steps * n * world / (elapsed_ms / 1000.0)
+    hits_per_shower = n_hits / n
+
+    # isolated serial pass on one sub-batch with the full launch shapes:
+    # simulate timing and the downsampling kernel's roofline
+    a, b = pipe.ranges[0]
+    m = b - a
+    iso = S.supa_batch_create([gh], pipe.sub, {"max_hits": int(pipe.sub * cap) + (8 << 20), "lpt_order": 1})
+    V = pipe.V
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sim_ms = []
+    for rep in range(3):
+        e[0].record(stream)
+        S.supa_simulate(iso, d_prim[a * 24:b * 24], m, seed, base + a)
+        e[1].record(stream)
+        S.supa_batch_get_info(iso)
+        sim_ms.append(e[0].elapsed_time(e[1]))
+    info = S.supa_batch_get_info(iso)
+    vox = []
+    for rep in range(3):
+        for c0 in range(0, m - V + 1, V):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S.supa_voxelize(iso, c0, c0 + V, pipe.grid, pipe.oor)
+            e1.record(stream)
+            vox.append((e0, e1))
+    torch.cuda.synchronize()
+    vox_ms = [x.elapsed_time(y) for x, y in vox]
+    S.supa_destroy_batch(iso)
+    sim_iso = min(sim_ms)
+    avg_vox = sum(vox_ms) / len(vox_ms)
+    pk, pk_kind = peaks()
+    bytes_per_shower = L * ny * nx * 4 + 16 * (info.n_hits / m) + 8
+    achieved = V * bytes_per_shower / (avg_vox / 1000.0) / 1e9
+    traffic = stored_traffic("supa_voxel_kernel", args.workload)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": "supa_voxel_kernel",
+            "peak_source": pk_kind, "bytes_per_shower": bytes_per_shower, "showers_per_launch": V,
+            "measured": "isolated launches, CUDA events on the launching stream"}
+    out = {
+        "metric": METRIC, "value": value, "unit": "showers/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(conf, showers=n, layers=L, grid=[L, ny, nx], fetch_chunk_hits=args.fetch_chunk,
+                       voxel_chunk_showers=V, sub_batches=len(pipe.ranges),
+                       l2="inputs larger than L2 (hit pool and image chunks >> 129 MB)",
+                       parallelism=f"replicas x{world}"),
+        "particle_steps_per_s": n_steps * args.steps * world / (elapsed_ms / 1000.0),
+        "hits_per_shower": hits_per_shower, "steps_per_shower": n_steps / n,
+        "phase_ms_isolated": {"simulate_per_1M": sim_iso * 1e6 / m, "voxelize_per_1M": avg_vox * 1e6 / V,
+                              "step_total_pipelined": elapsed_ms / args.steps},
+        "simulate_showers_per_s": m / (sim_iso / 1000.0),
+        "simulate_particle_steps_per_s": info.n_steps / (sim_iso / 1000.0),
+        "roofline": roof, "gpu_launches": launches, "clocks": clk,
+    }
+    if not args.no_e2e:
+        h_prim = torch.from_numpy(np.ascontiguousarray(prims).view(np.uint8)).pin_memory()
+        d_prim2 = torch.empty_like(h_prim, device="cuda")
+        h_hits = torch.empty((int(n_hits * 1.02) + 4096, 4), dtype=torch.float32, pin_memory=True)
+        h_ls = torch.empty((n, L), dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            d_prim2.copy_(h_prim, non_blocking=True)
+            r = pipe.step(prim_src=d_prim2, host_hits=h_hits, host_ls=h_ls)
+            torch.cuda.synchronize()
+            return r
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st, hi, _ = e2e_step()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        out["e2e"] = {"value": args.steps * n * world / dt, "unit": "showers/s", "h2d_bytes_per_step": n * 24,
+                      "d2h_bytes_per_step": hi * 16 + n * L * 8}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sps, done, dt, threads = oracle_sample(geom, prims, seed, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": "showers/s", "cores": threads, "kind": "oracle",
+                               "sample": f"first {done} showers of this workload in {dt:.1f} s (simulate on "
+                                         f"{threads} threads, downsample single-threaded)",
+                               "particle_steps_per_s": sps}
+    pipe.close()
+    S.supa_destroy_geometry(gh)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_supa_serial(args):
     import torch
     import torch.distributed as dist
 

@@ -98,7 +98,7 @@ struct supa_batch {
     SpillRec *d_spill = nullptr;
     int spill_cap = 0;
     // launch shape
-    int grid = 0, block = 0, stack_cap = 0, stage_cap = 0, flush_thr = 0, minb = 3;
+    int grid = 0, block = 0, stack_cap = 0, stage_cap = 0, flush_thr = 0, minb = 3, voxel_ctas = 0;
     size_t smem = 0;
     int warp_bytes = 0;
     // state
@@ -293,8 +293,9 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
         supa_destroy_batch(b);
         return fail(SUPA_ERR_INVALID_ARG, "warps_per_block must be <= 8");
     }
-    // register budget variant: 2, 3 or 4 resident blocks per SM
-    b->minb = cfg.blocks_per_sm > 0 ? std::max(2, std::min(4, cfg.blocks_per_sm)) : 3;
+    // register budget: the 64-register build for 4 blocks per SM, else 80
+    b->minb = cfg.blocks_per_sm >= 4 ? 4 : 3;
+    b->voxel_ctas = std::max(0, cfg.voxel_ctas_per_sm);
     b->block = wpb * 32;
     b->stack_cap = cfg.stack_depth > 0 ? cfg.stack_depth : 128;
     if (b->stack_cap < 64 || b->stack_cap % 2) {
@@ -647,6 +648,7 @@ int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float
     p.zmid = b->d_zmid;
     p.grid = grid_dev;
     p.oor = out_of_roi_dev;
+    p.ctas_per_sm = b->voxel_ctas;
     SUPA_CUDA(launch_voxelize(p, st));
     return SUPA_OK;
 }

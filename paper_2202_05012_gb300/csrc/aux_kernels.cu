@@ -234,6 +234,7 @@ cudaError_t launch_voxelize(const VoxParams &p, cudaStream_t st) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, supa_voxel_kernel, 512, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (p.ctas_per_sm > 0) per_sm = std::min(per_sm, p.ctas_per_sm);
     const int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, p.n_showers);
     supa_voxel_kernel<<<(unsigned)grid, 512, smem, st>>>(p);
     return cudaGetLastError();

@@ -62,10 +62,20 @@ __device__ inline WarpSmem carve(unsigned char *base, int C, int H, bool tags) {
     return w;
 }
 
-// Energy in 64-bit fixed point, units of 2^-32 (exact for E >= 2^-9; energies
-// are below 2^30, checked per primary, so sums cannot overflow).
+// Energy in 64-bit fixed point, units of 2^-32: E = m * 2^(e-23) with a 24-bit
+// significand m becomes m << (e + 9), exact for E >= 2^-9 and rounded to the
+// nearest unit below (ties up).  Integer shifts only: a float -> int64
+// conversion would run on the FP64 unit.  Energies are positive and below
+// 2^30 (checked per primary), so the sums cannot overflow.
 __device__ __forceinline__ unsigned long long fixed32(float E) {
-    return (unsigned long long)__float2ll_rn(E * 4294967296.0f);
+    const uint32_t bits = __float_as_uint(E);
+    const int e = (int)((bits >> 23) & 0xFFu);
+    if (e == 0) return 0ull;  // zero (energies are never subnormal here)
+    const unsigned long long m = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 127 + 9;
+    if (sh >= 0) return m << sh;
+    if (sh < -24) return 0ull;
+    return (m + (1ull << (-sh - 1))) >> (-sh);
 }
 __device__ __forceinline__ double from_fixed32(unsigned long long v) {
     return (double)(long long)v * (1.0 / 4294967296.0);
@@ -191,7 +201,7 @@ size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags) {
 }
 
 // MINB: resident 256-thread blocks per SM the register budget is cut for
-// (2: up to 128 registers, 3: 80, 4: 64).
+// (3: 80 registers, 4: 64).
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -436,17 +446,14 @@ cudaError_t attrs(int block, size_t smem, int *blocks_per_sm) {
 cudaError_t launch_step(int minb, const StepParams &p, int grid, int block, size_t smem, cudaStream_t st) {
     if (minb >= 4)
         supa_step_kernel<4><<<grid, block, smem, st>>>(p);
-    else if (minb == 3)
-        supa_step_kernel<3><<<grid, block, smem, st>>>(p);
     else
-        supa_step_kernel<2><<<grid, block, smem, st>>>(p);
+        supa_step_kernel<3><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t step_kernel_attributes(int minb, int block, size_t smem, int *blocks_per_sm) {
     if (minb >= 4) return attrs<4>(block, smem, blocks_per_sm);
-    if (minb == 3) return attrs<3>(block, smem, blocks_per_sm);
-    return attrs<2>(block, smem, blocks_per_sm);
+    return attrs<3>(block, smem, blocks_per_sm);
 }
 
 }  // namespace supa

@@ -83,8 +83,8 @@ constexpr int kErrBadPrimary = 4;
 size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags);
 
 // Kernel launchers (defined in the .cu files, called by the C ABI).
-// minb selects the register budget of the step kernel (2, 3 or 4 resident
-// 256-thread blocks per SM).
+// minb selects the register budget of the step kernel (3 or 4 resident
+// 256-thread blocks per SM: 80 or 64 registers).
 cudaError_t launch_step(int minb, const StepParams &p, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t step_kernel_attributes(int minb, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_scan_counts(const uint32_t *counts, int64_t n, int64_t *offsets, unsigned long long *block_tmp,
@@ -110,6 +110,7 @@ struct VoxParams {
     int G;         // layers per image group (one bulk store)
     int n_groups;  // ceil(L / G)
     int list_cap;  // hits whose cells fit the shared-memory list
+    int ctas_per_sm;  // persistent grid size per SM (0: as many as fit)
     int nx, ny;
     float wx, wy;
     // batch mode: ROI from the primaries; explicit mode: roi_x0/roi_y0
