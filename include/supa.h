@@ -211,6 +211,42 @@ int supa_voxelize_hits(const supa_geometry *g, const float *hits_dev, const int6
                        int64_t n_showers, const float *roi_x0_dev, const float *roi_y0_dev, float *grid_dev,
                        double *out_of_roi_dev, void *stream);
 
+/* ---- surrogate network -------------------------------------------------
+ * The paper has no counterpart: the hybrid path replaces the sub-showers of
+ * particles below a cutoff energy E_s by a small network that predicts their
+ * per-layer deposits.  The network maps 6 features (log E, the direction
+ * cosines u_x, u_y, u_z, the position of the start slice within its layer,
+ * the number of layers left behind the start layer) through three hidden
+ * layers of 256 with GELU to 60 outputs: means mu_j and log-variances s_j of
+ * the deposit fractions of layers start + j, j = 0..29.  Loss: Gaussian
+ * negative log-likelihood, mean over samples and layers.  Compute: BF16
+ * tensor-core GEMMs (tcgen05, TMA) with FP32 accumulation, FP32 master
+ * weights and Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Parameters are exchanged as a packed float32 vector of
+ * supa_surrogate_param_count() values: W1 [256][6], b1 [256], W2 [256][256],
+ * b2, W3 [256][256], b3, W4 [60][256], b4 [60] (row-major). */
+typedef struct supa_surrogate supa_surrogate;
+
+int32_t supa_surrogate_param_count(void);
+/* batch: minibatch rows (a multiple of 128); params_host: initial values. */
+int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogate **out);
+int supa_surrogate_destroy(supa_surrogate *s);
+/* Current FP32 master parameters (synchronous). */
+int supa_surrogate_get_params(supa_surrogate *s, float *params_host);
+/* Loss and gradients of one minibatch without an update (synchronous):
+ * x_dev float32 [batch][6], y_dev float32 [batch][30]. */
+int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float *y_dev, float *grads_host,
+                             double *loss_host, void *stream);
+/* One Adam step on one minibatch (asynchronous); adds the minibatch loss to
+ * *loss_acc_dev (device FP64) when it is not NULL. */
+int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float *y_dev, float lr,
+                              double *loss_acc_dev, void *stream);
+/* Inference: x_dev float32 [n][6] -> out_dev float32 [n][60] (asynchronous). */
+int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, void *stream);
+/* Synchronise and report a tensor-core pipeline that gave up waiting
+ * (SUPA_ERR_TIMEOUT) since the last check. */
+int supa_surrogate_check(supa_surrogate *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,10 @@ unsigned long long threshold(double p) {
 
 }  // namespace
 
+namespace supa {
+int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace supa
+
 struct supa_geometry {
     GeomDev rec;  // slice_off = layer_off = 0
     std::vector<unsigned long long> t_stop, t_ss;

@@ -228,6 +228,9 @@ cudaError_t launch_voxelize(const VoxParams &p, cudaStream_t st) {
     const size_t smem = vox_smem_bytes(p.G, p.nx, p.ny, p.list_cap);
     cudaError_t e = cudaFuncSetAttribute(supa_voxel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(supa_voxel_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

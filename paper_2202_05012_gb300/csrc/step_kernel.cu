@@ -439,6 +439,11 @@ template <int MINB>
 cudaError_t attrs(int block, size_t smem, int *blocks_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(supa_step_kernel<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // largest shared-memory carve-out, so downsampling CTAs of another batch
+    // can share the SM with these blocks
+    e = cudaFuncSetAttribute(supa_step_kernel<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, supa_step_kernel<MINB>, block, smem);
 }
 }  // namespace

@@ -75,6 +75,9 @@ struct StepParams {
     int warp_smem_bytes;  // shared memory per warp
 };
 
+// Record the message returned by supa_last_error() and return `code`.
+int set_last_error(int code, const char *msg);
+
 // Device error word bits.
 constexpr int kErrPoolOverflow = 1;
 constexpr int kErrSpillOverflow = 2;

@@ -1,0 +1,440 @@
+// surrogate.cu -- the BF16 tensor-core surrogate network of the hybrid path
+// (no counterpart in the SUPA paper): an MLP 6 -> 256 -> 256 -> 256 -> 60
+// with exact GELU, trained with a Gaussian negative log-likelihood and Adam,
+// evaluated in minibatches of `batch` rows.
+//
+// Layout.  Every GEMM is C = A * B^T with both operands K-major (tc_gemm.cuh),
+// so the engine keeps each activation in both orientations (the forward
+// epilogue writes h and h^T) and each weight as W and W^T in BF16, next to
+// FP32 master weights and Adam moments.  The 6 inputs are padded to 64
+// columns and the 60 outputs to 64 rows; the padding stays exactly zero
+// (zero inputs and zero output gradients give zero updates).
+//
+// Training step: pack inputs -> 4 forward GEMMs (bias+GELU epilogues) ->
+// loss kernel (NLL, d loss / d out) -> per layer a data-gradient GEMM
+// (GELU-backward epilogue, bias gradient by column sums) and a split-K
+// weight-gradient GEMM (float atomics) -> Adam -> BF16 weight copies.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "supa_internal.cuh"
+#include "tc_gemm.cuh"
+
+using namespace supa;
+
+namespace {
+
+constexpr int kIn = 6, kInPad = 64, kHid = 256, kOut = 60, kOutPad = 64, kLayersOut = 30;
+// packed user parameter vector: W1, b1, W2, b2, W3, b3, W4, b4
+constexpr int kNParams = kHid * kIn + kHid + 2 * (kHid * kHid + kHid) + kOut * kHid + kOut;
+
+// offsets of the padded FP32 master block
+struct Off {
+    static constexpr size_t W1 = 0, b1 = W1 + kHid * kInPad, W2 = b1 + kHid, b2 = W2 + kHid * kHid, W3 = b2 + kHid,
+                            b3 = W3 + kHid * kHid, W4 = b3 + kHid, b4 = W4 + kOutPad * kHid, total = b4 + kOutPad;
+};
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+}
+
+__global__ void pack_inputs(const float *x, int64_t n, int B, __nv_bfloat16 *X0, __nv_bfloat16 *X0T) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= B) return;
+    float v[kIn];
+    for (int j = 0; j < kIn; ++j) v[j] = r < n ? x[(size_t)r * kIn + j] : 0.0f;
+    for (int j = 0; j < kInPad; ++j) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(j < kIn ? v[j] : 0.0f);
+        X0[(size_t)r * kInPad + j] = h;
+        X0T[(size_t)j * B + r] = h;
+    }
+}
+
+// Gaussian NLL over the 30 layers, mean over the batch: writes d loss / d out
+// (bf16, both orientations; padding columns zero), adds the bias gradient of
+// the last layer and the loss sum.
+__global__ void nll_loss(const float *out, const float *y, int B, __nv_bfloat16 *G4, __nv_bfloat16 *G4T, float *gb4,
+                         double *loss_sum) {
+    __shared__ float colsum[kOutPad];
+    __shared__ double red[32];
+    for (int j = threadIdx.x; j < kOutPad; j += blockDim.x) colsum[j] = 0.0f;
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (r < B) {
+        const float inv = 1.0f / (float)(B * kLayersOut);
+        for (int j = 0; j < kLayersOut; ++j) {
+            const float mu = out[(size_t)r * kOutPad + j], s = out[(size_t)r * kOutPad + kLayersOut + j];
+            const float res = y[(size_t)r * kLayersOut + j] - mu;
+            const float e = expf(-s);
+            l += 0.5 * (double)(res * res * e) + 0.5 * (double)s;
+            const float gmu = -res * e * inv;
+            const float gs = (0.5f - 0.5f * res * res * e) * inv;
+            G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(gmu);
+            G4[(size_t)r * kOutPad + kLayersOut + j] = __float2bfloat16_rn(gs);
+            G4T[(size_t)j * B + r] = __float2bfloat16_rn(gmu);
+            G4T[(size_t)(kLayersOut + j) * B + r] = __float2bfloat16_rn(gs);
+            atomicAdd(&colsum[j], gmu);
+            atomicAdd(&colsum[kLayersOut + j], gs);
+        }
+        for (int j = kOut; j < kOutPad; ++j) {
+            G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(0.0f);
+            G4T[(size_t)j * B + r] = __float2bfloat16_rn(0.0f);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        atomicAdd(loss_sum, t / (double)(B * kLayersOut));
+    }
+    for (int j = threadIdx.x; j < kOut; j += blockDim.x) atomicAdd(&gb4[j], colsum[j]);
+}
+
+// Adam with bias correction (c1 = 1 - beta1^t, c2 = 1 - beta2^t).
+__global__ void adam_update(float *p, float *m, float *v, const float *g, size_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// BF16 copies of a master weight [rows][cols]: W and (optionally) W^T.
+__global__ void cast_weight(const float *W, int rows, int cols, __nv_bfloat16 *Wb, __nv_bfloat16 *WTb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    const int r = i / cols, c = i % cols;
+    const __nv_bfloat16 h = __float2bfloat16_rn(W[i]);
+    Wb[i] = h;
+    if (WTb) WTb[(size_t)c * rows + r] = h;
+}
+
+}  // namespace
+
+struct supa_surrogate {
+    int B = 0;
+    int t = 0;  // Adam step count
+    float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+    float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    __nv_bfloat16 *W1b, *W2b, *W3b, *W4b, *W2Tb, *W3Tb, *W4Tb;
+    __nv_bfloat16 *X0, *X0T, *H1, *H2, *H3, *H1T, *H2T, *H3T, *G4, *G4T, *G3, *G2, *G1, *G3T, *G2T, *G1T;
+    float *Z1, *Z2, *Z3, *OUT;
+    double *loss_tmp = nullptr;
+    int *error = nullptr;
+    CUtensorMap mX0, mH1, mH2, mH3, mG4, mG3, mG2, mG4T, mG3T, mG2T, mG1T;  // A operands (box 128 rows)
+    CUtensorMap mW1, mW2, mW3, mW4, mW4T, mW3T, mW2T, mH3Tb, mH2Tb, mH1Tb, mX0Tb;  // B operands
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+int sfail(int code, const std::string &m) { return set_last_error(code, m.c_str()); }
+
+template <typename T>
+bool grab(supa_surrogate *s, T **p, size_t n) {
+    if (dalloc(p, n) != cudaSuccess) return false;
+    s->allocs.push_back((void *)*p);
+    return true;
+}
+
+void free_all(supa_surrogate *s) {
+    for (void *p : s->allocs) cudaFree(p);
+    s->allocs.clear();
+}
+
+int weight_copies(supa_surrogate *s, cudaStream_t st) {
+    const int T = 256;
+    cast_weight<<<(kHid * kInPad + T - 1) / T, T, 0, st>>>(s->master + Off::W1, kHid, kInPad, s->W1b, nullptr);
+    cast_weight<<<(kHid * kHid + T - 1) / T, T, 0, st>>>(s->master + Off::W2, kHid, kHid, s->W2b, s->W2Tb);
+    cast_weight<<<(kHid * kHid + T - 1) / T, T, 0, st>>>(s->master + Off::W3, kHid, kHid, s->W3b, s->W3Tb);
+    cast_weight<<<(kOutPad * kHid + T - 1) / T, T, 0, st>>>(s->master + Off::W4, kOutPad, kHid, s->W4b, s->W4Tb);
+    return cudaGetLastError() == cudaSuccess ? SUPA_OK : SUPA_ERR_CUDA;
+}
+
+GemmArgs gargs(int M, int N, int K, int epi, int *err) {
+    GemmArgs a{};
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.k_blocks_per_split = K / kTileK;
+    a.epi = epi;
+    a.error = err;
+    return a;
+}
+
+cudaError_t gemm(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs a, cudaStream_t st, int m_tiles_target = 0) {
+    int splits = 1;
+    if (a.epi == EPI_ATOMIC_F32) {
+        const int kb = a.K / kTileK;
+        const int m_tiles = (a.M + kTileM - 1) / kTileM;
+        const int want = std::max(1, std::min(kb, 152 / m_tiles));
+        a.k_blocks_per_split = (kb + want - 1) / want;
+        splits = (kb + a.k_blocks_per_split - 1) / a.k_blocks_per_split;
+    }
+    (void)m_tiles_target;
+    return launch_gemm(ta, tb, a, splits, st);
+}
+
+// Forward pass of one minibatch whose packed inputs are in X0/X0T.  train:
+// also keep pre-activations and transposed activations for the backward.
+cudaError_t forward(supa_surrogate *s, bool train, cudaStream_t st) {
+    const int B = s->B;
+    const int ep = train ? EPI_BIAS_GELU : EPI_GELU_ONLY;
+    GemmArgs a = gargs(B, kHid, kInPad, ep, s->error);
+    a.bias = s->master + Off::b1; a.out_f32 = s->Z1; a.out_bf16 = s->H1; a.outT_bf16 = s->H1T; a.ld = kHid; a.ldT = B;
+    cudaError_t e = gemm(s->mX0, s->mW1, a, st);
+    if (e != cudaSuccess) return e;
+    a = gargs(B, kHid, kHid, ep, s->error);
+    a.bias = s->master + Off::b2; a.out_f32 = s->Z2; a.out_bf16 = s->H2; a.outT_bf16 = s->H2T; a.ld = kHid; a.ldT = B;
+    if ((e = gemm(s->mH1, s->mW2, a, st)) != cudaSuccess) return e;
+    a = gargs(B, kHid, kHid, ep, s->error);
+    a.bias = s->master + Off::b3; a.out_f32 = s->Z3; a.out_bf16 = s->H3; a.outT_bf16 = s->H3T; a.ld = kHid; a.ldT = B;
+    if ((e = gemm(s->mH2, s->mW3, a, st)) != cudaSuccess) return e;
+    a = gargs(B, kOutPad, kHid, EPI_BIAS_F32, s->error);
+    a.bias = s->master + Off::b4; a.out_f32 = s->OUT; a.ld = kOutPad;
+    return gemm(s->mH3, s->mW4, a, st);
+}
+
+// Loss and gradients of the minibatch in X0 with targets y (grad zeroed first).
+cudaError_t backward(supa_surrogate *s, const float *y, cudaStream_t st) {
+    const int B = s->B;
+    cudaError_t e = cudaMemsetAsync(s->grad, 0, Off::total * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    nll_loss<<<(B + 255) / 256, 256, 0, st>>>(s->OUT, y, B, s->G4, s->G4T, s->grad + Off::b4, s->loss_tmp);
+    // layer 4
+    GemmArgs a = gargs(kOutPad, kHid, B, EPI_ATOMIC_F32, s->error);
+    a.out_f32 = s->grad + Off::W4; a.ld = kHid;
+    if ((e = gemm(s->mG4T, s->mH3Tb, a, st)) != cudaSuccess) return e;
+    a = gargs(B, kHid, kOutPad, EPI_GELU_BWD, s->error);
+    a.z_in = s->Z3; a.out_bf16 = s->G3; a.outT_bf16 = s->G3T; a.colsum = s->grad + Off::b3; a.ld = kHid; a.ldT = B;
+    if ((e = gemm(s->mG4, s->mW4T, a, st)) != cudaSuccess) return e;
+    // layer 3
+    a = gargs(kHid, kHid, B, EPI_ATOMIC_F32, s->error);
+    a.out_f32 = s->grad + Off::W3; a.ld = kHid;
+    if ((e = gemm(s->mG3T, s->mH2Tb, a, st)) != cudaSuccess) return e;
+    a = gargs(B, kHid, kHid, EPI_GELU_BWD, s->error);
+    a.z_in = s->Z2; a.out_bf16 = s->G2; a.outT_bf16 = s->G2T; a.colsum = s->grad + Off::b2; a.ld = kHid; a.ldT = B;
+    if ((e = gemm(s->mG3, s->mW3T, a, st)) != cudaSuccess) return e;
+    // layer 2
+    a = gargs(kHid, kHid, B, EPI_ATOMIC_F32, s->error);
+    a.out_f32 = s->grad + Off::W2; a.ld = kHid;
+    if ((e = gemm(s->mG2T, s->mH1Tb, a, st)) != cudaSuccess) return e;
+    a = gargs(B, kHid, kHid, EPI_GELU_BWD, s->error);
+    a.z_in = s->Z1; a.out_bf16 = s->G1; a.outT_bf16 = s->G1T; a.colsum = s->grad + Off::b1; a.ld = kHid; a.ldT = B;
+    if ((e = gemm(s->mG2, s->mW2T, a, st)) != cudaSuccess) return e;
+    // layer 1
+    a = gargs(kHid, kInPad, B, EPI_ATOMIC_F32, s->error);
+    a.out_f32 = s->grad + Off::W1; a.ld = kInPad;
+    return gemm(s->mG1T, s->mX0Tb, a, st);
+}
+
+int check_error_word(supa_surrogate *s) {
+    int h = 0;
+    if (cudaMemcpy(&h, s->error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SUPA_ERR_CUDA;
+    if (h) return sfail(SUPA_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting on its pipeline (error word " +
+                                              std::to_string(h) + ")");
+    return SUPA_OK;
+}
+
+// packed user vector <-> padded master block (host side)
+void unpack_params(const float *p, std::vector<float> &mst) {
+    mst.assign(Off::total, 0.0f);
+    size_t o = 0;
+    for (int r = 0; r < kHid; ++r)
+        for (int c = 0; c < kIn; ++c) mst[Off::W1 + r * kInPad + c] = p[o++];
+    for (int r = 0; r < kHid; ++r) mst[Off::b1 + r] = p[o++];
+    for (int i = 0; i < kHid * kHid; ++i) mst[Off::W2 + i] = p[o++];
+    for (int r = 0; r < kHid; ++r) mst[Off::b2 + r] = p[o++];
+    for (int i = 0; i < kHid * kHid; ++i) mst[Off::W3 + i] = p[o++];
+    for (int r = 0; r < kHid; ++r) mst[Off::b3 + r] = p[o++];
+    for (int i = 0; i < kOut * kHid; ++i) mst[Off::W4 + i] = p[o++];
+    for (int r = 0; r < kOut; ++r) mst[Off::b4 + r] = p[o++];
+}
+
+void pack_params(const std::vector<float> &mst, float *p) {
+    size_t o = 0;
+    for (int r = 0; r < kHid; ++r)
+        for (int c = 0; c < kIn; ++c) p[o++] = mst[Off::W1 + r * kInPad + c];
+    for (int r = 0; r < kHid; ++r) p[o++] = mst[Off::b1 + r];
+    for (int i = 0; i < kHid * kHid; ++i) p[o++] = mst[Off::W2 + i];
+    for (int r = 0; r < kHid; ++r) p[o++] = mst[Off::b2 + r];
+    for (int i = 0; i < kHid * kHid; ++i) p[o++] = mst[Off::W3 + i];
+    for (int r = 0; r < kHid; ++r) p[o++] = mst[Off::b3 + r];
+    for (int i = 0; i < kOut * kHid; ++i) p[o++] = mst[Off::W4 + i];
+    for (int r = 0; r < kOut; ++r) p[o++] = mst[Off::b4 + r];
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t supa_surrogate_param_count(void) { return kNParams; }
+
+int supa_surrogate_destroy(supa_surrogate *s) {
+    if (!s) return SUPA_OK;
+    free_all(s);
+    delete s;
+    return SUPA_OK;
+}
+
+int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogate **out) {
+    if (!out || !params_host) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_create: null argument");
+    *out = nullptr;
+    if (batch < 128 || batch % 128 != 0 || batch > (1 << 20))
+        return sfail(SUPA_ERR_INVALID_ARG, "batch must be a positive multiple of 128 up to 2^20");
+    supa_surrogate *s = new supa_surrogate();
+    s->B = batch;
+    const size_t B = batch;
+    bool ok = grab(s, &s->master, Off::total) && grab(s, &s->m, Off::total) && grab(s, &s->v, Off::total) &&
+              grab(s, &s->grad, Off::total) && grab(s, &s->W1b, (size_t)kHid * kInPad) &&
+              grab(s, &s->W2b, (size_t)kHid * kHid) && grab(s, &s->W3b, (size_t)kHid * kHid) &&
+              grab(s, &s->W4b, (size_t)kOutPad * kHid) && grab(s, &s->W2Tb, (size_t)kHid * kHid) &&
+              grab(s, &s->W3Tb, (size_t)kHid * kHid) && grab(s, &s->W4Tb, (size_t)kHid * kOutPad) &&
+              grab(s, &s->X0, B * kInPad) && grab(s, &s->X0T, B * kInPad) && grab(s, &s->H1, B * kHid) &&
+              grab(s, &s->H2, B * kHid) && grab(s, &s->H3, B * kHid) && grab(s, &s->H1T, B * kHid) &&
+              grab(s, &s->H2T, B * kHid) && grab(s, &s->H3T, B * kHid) && grab(s, &s->G4, B * kOutPad) &&
+              grab(s, &s->G4T, B * kTileM) && grab(s, &s->G3, B * kHid) && grab(s, &s->G2, B * kHid) &&
+              grab(s, &s->G1, B * kHid) && grab(s, &s->G3T, B * kHid) && grab(s, &s->G2T, B * kHid) &&
+              grab(s, &s->G1T, B * kHid) && grab(s, &s->Z1, B * kHid) && grab(s, &s->Z2, B * kHid) &&
+              grab(s, &s->Z3, B * kHid) && grab(s, &s->OUT, B * kOutPad) && grab(s, &s->loss_tmp, 1) &&
+              grab(s, &s->error, 1);
+    if (!ok) {
+        supa_surrogate_destroy(s);
+        return sfail(SUPA_ERR_OOM, "supa_surrogate_create: out of device memory");
+    }
+    // tensor maps: A operands read 128-row boxes, B operands N-row boxes
+    int rc = 0;
+    rc |= make_bf16_map(&s->mX0, s->X0, B, kInPad, 128);
+    rc |= make_bf16_map(&s->mH1, s->H1, B, kHid, 128);
+    rc |= make_bf16_map(&s->mH2, s->H2, B, kHid, 128);
+    rc |= make_bf16_map(&s->mH3, s->H3, B, kHid, 128);
+    rc |= make_bf16_map(&s->mG4, s->G4, B, kOutPad, 128);
+    rc |= make_bf16_map(&s->mG3, s->G3, B, kHid, 128);
+    rc |= make_bf16_map(&s->mG2, s->G2, B, kHid, 128);
+    // d out^T is read as the A operand of the 64-row weight gradient: it is
+    // kept 128 rows high (rows 64..127 stay zero) so every load is one full tile
+    rc |= make_bf16_map(&s->mG4T, s->G4T, kTileM, B, 128);
+    rc |= make_bf16_map(&s->mG3T, s->G3T, kHid, B, 128);
+    rc |= make_bf16_map(&s->mG2T, s->G2T, kHid, B, 128);
+    rc |= make_bf16_map(&s->mG1T, s->G1T, kHid, B, 128);
+    rc |= make_bf16_map(&s->mW1, s->W1b, kHid, kInPad, kHid);
+    rc |= make_bf16_map(&s->mW2, s->W2b, kHid, kHid, kHid);
+    rc |= make_bf16_map(&s->mW3, s->W3b, kHid, kHid, kHid);
+    rc |= make_bf16_map(&s->mW4, s->W4b, kOutPad, kHid, kOutPad);
+    rc |= make_bf16_map(&s->mW4T, s->W4Tb, kHid, kOutPad, kHid);
+    rc |= make_bf16_map(&s->mW3T, s->W3Tb, kHid, kHid, kHid);
+    rc |= make_bf16_map(&s->mW2T, s->W2Tb, kHid, kHid, kHid);
+    rc |= make_bf16_map(&s->mH3Tb, s->H3T, kHid, B, kHid);
+    rc |= make_bf16_map(&s->mH2Tb, s->H2T, kHid, B, kHid);
+    rc |= make_bf16_map(&s->mH1Tb, s->H1T, kHid, B, kHid);
+    rc |= make_bf16_map(&s->mX0Tb, s->X0T, kInPad, B, kInPad);
+    if (rc != 0) {
+        supa_surrogate_destroy(s);
+        return sfail(SUPA_ERR_CUDA, "supa_surrogate_create: cuTensorMapEncodeTiled failed");
+    }
+    std::vector<float> mst;
+    unpack_params(params_host, mst);
+    cudaError_t e = cudaMemcpy(s->master, mst.data(), Off::total * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(s->m, 0, Off::total * 4);
+    if (e == cudaSuccess) e = cudaMemset(s->v, 0, Off::total * 4);
+    if (e == cudaSuccess) e = cudaMemset(s->error, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->G4T, 0, B * kTileM * sizeof(__nv_bfloat16));
+    if (e != cudaSuccess || weight_copies(s, 0) != SUPA_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        supa_surrogate_destroy(s);
+        return sfail(SUPA_ERR_CUDA, "supa_surrogate_create: upload failed");
+    }
+    *out = s;
+    return SUPA_OK;
+}
+
+int supa_surrogate_get_params(supa_surrogate *s, float *params_host) {
+    if (!s || !params_host) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_get_params: null argument");
+    std::vector<float> mst(Off::total);
+    if (cudaMemcpy(mst.data(), s->master, Off::total * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return sfail(SUPA_ERR_CUDA, "supa_surrogate_get_params: copy failed");
+    pack_params(mst, params_host);
+    return SUPA_OK;
+}
+
+int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float *y_dev, float *grads_host,
+                             double *loss_host, void *stream) {
+    if (!s || !x_dev || !y_dev || !grads_host) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_gradients: null");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(s->loss_tmp, 0, sizeof(double), st) != cudaSuccess)
+        return sfail(SUPA_ERR_CUDA, "memset failed");
+    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0, s->X0T);
+    cudaError_t e = forward(s, true, st);
+    if (e == cudaSuccess) e = backward(s, y_dev, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("gradients: ") + cudaGetErrorString(e));
+    int rc = check_error_word(s);
+    if (rc != SUPA_OK) return rc;
+    std::vector<float> g(Off::total);
+    if (cudaMemcpy(g.data(), s->grad, Off::total * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return sfail(SUPA_ERR_CUDA, "gradient copy failed");
+    pack_params(g, grads_host);
+    if (loss_host && cudaMemcpy(loss_host, s->loss_tmp, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return sfail(SUPA_ERR_CUDA, "loss copy failed");
+    return SUPA_OK;
+}
+
+int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float *y_dev, float lr,
+                              double *loss_acc_dev, void *stream) {
+    if (!s || !x_dev || !y_dev) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_step: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    double *loss = loss_acc_dev ? loss_acc_dev : s->loss_tmp;
+    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0, s->X0T);
+    cudaError_t e = forward(s, true, st);
+    if (e == cudaSuccess) {
+        // backward() writes the minibatch loss into s->loss_tmp; point it at the accumulator
+        double *keep = s->loss_tmp;
+        s->loss_tmp = loss;
+        e = backward(s, y_dev, st);
+        s->loss_tmp = keep;
+    }
+    if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
+    s->t += 1;
+    const float c1 = 1.0f - std::pow(s->beta1, (float)s->t), c2 = 1.0f - std::pow(s->beta2, (float)s->t);
+    adam_update<<<296, 256, 0, st>>>(s->master, s->m, s->v, s->grad, Off::total, lr, s->beta1, s->beta2, s->eps, c1,
+                                     c2);
+    if (weight_copies(s, st) != SUPA_OK) return sfail(SUPA_ERR_CUDA, "weight copies failed");
+    return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_step launch failed");
+}
+
+int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, void *stream) {
+    if (!s || (!x_dev && n > 0) || (!out_dev && n > 0))
+        return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_forward: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t r0 = 0; r0 < n; r0 += s->B) {
+        const int64_t m = std::min<int64_t>(s->B, n - r0);
+        pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev + r0 * kIn, m, s->B, s->X0, s->X0T);
+        cudaError_t e = forward(s, false, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(out_dev + r0 * kOut, kOut * 4, s->OUT, kOutPad * 4, kOut * 4, m,
+                                  cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));
+    }
+    return SUPA_OK;
+}
+
+int supa_surrogate_check(supa_surrogate *s) {
+    if (!s) return sfail(SUPA_ERR_INVALID_ARG, "null surrogate");
+    if (cudaDeviceSynchronize() != cudaSuccess) return sfail(SUPA_ERR_CUDA, "device error");
+    return check_error_word(s);
+}
+
+}  // extern "C"

@@ -26,7 +26,9 @@ SUPA_ERR_NOT_READY = -6
 EXPORTED = (
     "supa_last_error", "supa_init_geometry", "supa_destroy_geometry", "supa_batch_create", "supa_destroy_batch",
     "supa_simulate", "supa_simulate_batch", "supa_batch_get_info", "supa_fetch_hits", "supa_fetch_hit_tags",
-    "supa_voxelize", "supa_voxelize_hits", "supa_autotune",
+    "supa_voxelize", "supa_voxelize_hits", "supa_autotune", "supa_surrogate_param_count", "supa_surrogate_create",
+    "supa_surrogate_destroy", "supa_surrogate_get_params", "supa_surrogate_gradients", "supa_surrogate_train_step",
+    "supa_surrogate_forward", "supa_surrogate_check",
 )
 
 
@@ -102,6 +104,14 @@ def lib(build_if_missing: bool = True):
         L.supa_voxelize_hits.argtypes = [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]
         L.supa_autotune.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, _VP, _I64, ctypes.c_uint64,
                                     ctypes.POINTER(supa_launch_config), ctypes.POINTER(ctypes.c_double), _VP]
+        L.supa_surrogate_param_count.argtypes = []
+        L.supa_surrogate_create.argtypes = [ctypes.c_int32, _VP, ctypes.POINTER(_VP)]
+        L.supa_surrogate_destroy.argtypes = [_VP]
+        L.supa_surrogate_get_params.argtypes = [_VP, _VP]
+        L.supa_surrogate_gradients.argtypes = [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _VP]
+        L.supa_surrogate_train_step.argtypes = [_VP, _VP, _VP, ctypes.c_float, _VP, _VP]
+        L.supa_surrogate_forward.argtypes = [_VP, _VP, _I64, _VP, _VP]
+        L.supa_surrogate_check.argtypes = [_VP]
         for name in EXPORTED[1:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -242,6 +252,67 @@ def supa_autotune(geoms: list[int], prim_dev, n: int, seed: int, cfg: dict | Non
     _check(lib().supa_autotune(arr, len(geoms), _ptr(prim_dev), int(n), int(seed) & (2**64 - 1), ctypes.byref(c),
                                ctypes.byref(ms), _stream(stream)), "supa_autotune")
     return {name: getattr(c, name) for name, _ in supa_launch_config._fields_}, ms.value
+
+
+def supa_surrogate_param_count() -> int:
+    return lib().supa_surrogate_param_count()
+
+
+def supa_surrogate_create(batch: int, params: np.ndarray) -> int:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == supa_surrogate_param_count()
+    out = _VP()
+    _check(lib().supa_surrogate_create(int(batch), p.ctypes.data, ctypes.byref(out)), "supa_surrogate_create")
+    return out.value
+
+
+def supa_surrogate_destroy(s: int):
+    _check(lib().supa_surrogate_destroy(s), "supa_surrogate_destroy")
+
+
+def supa_surrogate_get_params(s: int) -> np.ndarray:
+    p = np.zeros(supa_surrogate_param_count(), dtype=np.float32)
+    _check(lib().supa_surrogate_get_params(s, p.ctypes.data), "supa_surrogate_get_params")
+    return p
+
+
+def supa_surrogate_gradients(s: int, x_dev, y_dev, stream=None) -> tuple[np.ndarray, float]:
+    g = np.zeros(supa_surrogate_param_count(), dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(lib().supa_surrogate_gradients(s, _ptr(x_dev), _ptr(y_dev), g.ctypes.data, ctypes.byref(loss),
+                                          _stream(stream)), "supa_surrogate_gradients")
+    return g, loss.value
+
+
+def supa_surrogate_train_step(s: int, x_dev, y_dev, lr: float, loss_acc_dev=None, stream=None):
+    _check(lib().supa_surrogate_train_step(s, _ptr(x_dev), _ptr(y_dev), float(lr), _ptr(loss_acc_dev),
+                                           _stream(stream)), "supa_surrogate_train_step")
+
+
+def supa_surrogate_forward(s: int, x_dev, n: int, out_dev, stream=None):
+    _check(lib().supa_surrogate_forward(s, _ptr(x_dev), int(n), _ptr(out_dev), _stream(stream)),
+           "supa_surrogate_forward")
+
+
+def supa_surrogate_check(s: int):
+    _check(lib().supa_surrogate_check(s), "supa_surrogate_check")
+
+
+def pack_mlp_params(params) -> np.ndarray:
+    """[(W, b)] -> the packed float32 vector of the C ABI (W row-major, then b)."""
+    return np.concatenate([np.concatenate([np.asarray(W).ravel(), np.asarray(b).ravel()]) for W, b in params]
+                          ).astype(np.float32)
+
+
+def unpack_mlp_params(vec: np.ndarray, shapes=((256, 6), (256, 256), (256, 256), (60, 256))):
+    out, o = [], 0
+    for r, c in shapes:
+        W = vec[o:o + r * c].reshape(r, c)
+        o += r * c
+        b = vec[o:o + r]
+        o += r
+        out.append((W, b))
+    return out
 
 
 # ---- marshalling helpers ----------------------------------------------------

@@ -1,0 +1,100 @@
+"""The BF16 tensor-core surrogate network against its FP64 oracle: forward
+outputs, loss, gradients (relative norm error and cosine per tensor), and a
+short Adam trajectory."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2202_05012_gb300 import inputs
+from paper_2202_05012_gb300 import supa as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(B, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = np.stack([rng.uniform(-3, 0, B), *rng.normal(0, 0.3, (2, B)), rng.uniform(0.7, 1, B), rng.uniform(0, 1, B),
+                  rng.uniform(0, 1, B)], 1)
+    Y = np.abs(rng.normal(0.05, 0.05, (B, 30)))
+    return X, Y
+
+
+def _f32_params(seed):
+    p = inputs.mlp_init(seed)
+    rng = np.random.default_rng(seed)
+    p = [(W, rng.normal(0, 0.05, b.shape)) for W, b in p]
+    vec = S.pack_mlp_params(p)
+    return vec, [(W.astype(np.float64), b.astype(np.float64)) for W, b in S.unpack_mlp_params(vec)]
+
+
+def test_gradients_match_fp64_oracle():
+    import torch
+    B = 1024
+    vec, params = _f32_params(7)
+    X, Y = _batch(B, 1)
+    s = S.supa_surrogate_create(B, vec)
+    try:
+        xd = torch.from_numpy(X.astype(np.float32)).cuda()
+        yd = torch.from_numpy(Y.astype(np.float32)).cuda()
+        g, loss = S.supa_surrogate_gradients(s, xd, yd)
+        ref_loss, ref = mlp.loss_and_grads(params, X, Y)
+        assert abs(loss - ref_loss) <= 1e-2 * abs(ref_loss) + 1e-4
+        gg = S.unpack_mlp_params(g.astype(np.float64))
+        for i, ((gW, gb), (rW, rb)) in enumerate(zip(gg, ref)):
+            for a, r, name in ((gW, rW, f"W{i + 1}"), (gb, rb, f"b{i + 1}")):
+                rel = np.linalg.norm(a - r) / np.linalg.norm(r)
+                cos = np.dot(a.ravel(), r.ravel()) / (np.linalg.norm(a) * np.linalg.norm(r))
+                assert rel < 2e-2 and cos > 0.999, (name, rel, cos)
+    finally:
+        S.supa_surrogate_destroy(s)
+
+
+def test_forward_matches_fp64_oracle_including_ragged_tail():
+    import torch
+    vec, params = _f32_params(8)
+    n = 1000  # not a multiple of the minibatch: the last chunk is ragged
+    X, _ = _batch(n, 2)
+    s = S.supa_surrogate_create(256, vec)
+    try:
+        xd = torch.from_numpy(X.astype(np.float32)).cuda()
+        out = torch.full((n, 60), np.nan, dtype=torch.float32, device="cuda")
+        S.supa_surrogate_forward(s, xd, n, out)
+        S.supa_surrogate_check(s)
+        got = out.cpu().numpy().astype(np.float64)
+        ref, _ = mlp.forward(params, X)
+        scale = np.abs(ref).max()
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - ref)) < 2e-2 * scale
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-2
+    finally:
+        S.supa_surrogate_destroy(s)
+
+
+def test_adam_trajectory_follows_oracle():
+    import torch
+    B = 512
+    vec, params = _f32_params(9)
+    X, Y = _batch(B, 3)
+    s = S.supa_surrogate_create(B, vec)
+    try:
+        xd = torch.from_numpy(X.astype(np.float32)).cuda()
+        yd = torch.from_numpy(Y.astype(np.float32)).cuda()
+        acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+        opt = mlp.Adam(params, lr=3e-4)
+        ours, ref = [], []
+        for step in range(30):
+            acc.zero_()
+            S.supa_surrogate_train_step(s, xd, yd, 3e-4, acc)
+            ours.append(acc.item())
+            loss, grads = mlp.loss_and_grads(params, X, Y)
+            ref.append(loss)
+            params = opt.step(params, grads)
+        S.supa_surrogate_check(s)
+        ours, ref = np.array(ours), np.array(ref)
+        assert ours[-1] < ours[0] - 0.005  # it learns (the NLL can go negative)
+        np.testing.assert_allclose(ours, ref, rtol=3e-2, atol=1e-3)
+        p = S.unpack_mlp_params(S.supa_surrogate_get_params(s).astype(np.float64))
+        for (W, b), (rW, rb) in zip(p, params):
+            assert np.linalg.norm(W - rW) / np.linalg.norm(rW) < 2e-2
+    finally:
+        S.supa_surrogate_destroy(s)
