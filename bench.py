@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--pipeline", type=int, default=8,
+    ap.add_argument("--pipeline", type=int, default=1,
                     help="sub-batches per step; >1 overlaps simulation of one with downsampling of the previous")
     return ap.parse_args()
 

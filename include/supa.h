@@ -86,9 +86,11 @@ typedef struct {
 } supa_geometry_desc;
 
 /* One primary particle (Sec. 3 initial particle; Sec. 4.2 conditioning on
- * impact energy, angle and position): energy, impact point on slice 0, polar
- * angle from the z axis and azimuth (radians), index into the launch's
- * geometry list.  24 bytes, no padding. */
+ * impact energy, angle and position): energy, impact point, polar angle from
+ * the z axis and azimuth (radians).  `geom`: bits 0-15 index the launch's
+ * geometry list, bits 16-31 give the slice the particle enters on (0 for a
+ * shower; later slices start sub-showers, e.g. surrogate training data).
+ * 24 bytes, no padding. */
 typedef struct {
     float E, x0, y0, theta, phi;
     uint32_t geom;
@@ -124,6 +126,9 @@ typedef struct {
     const double *dead_dev;     /* [n] energy stopped in dead slices           */
     const double *leak_dev;     /* [n] energy alive after the last slice       */
     const double *escape_dev;   /* [n] energy of escaped particles             */
+    int64_t n_diverted;         /* hybrid path: particles handed to the network */
+    const double *sur_leak_dev; /* hybrid path: [n] energy the network did not
+                                   deposit (NULL on the plain path)            */
 } supa_batch_info;
 
 typedef struct supa_geometry supa_geometry;
@@ -241,11 +246,35 @@ int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float 
  * *loss_acc_dev (device FP64) when it is not NULL. */
 int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float *y_dev, float lr,
                               double *loss_acc_dev, void *stream);
+/* One epoch over a training set of n samples (x_dev [n][6], y_dev [n][30]):
+ * floor(n / batch) Adam steps on minibatches gathered in the order of the
+ * permutation i -> (a i + c) mod n that `seed` picks.  Asynchronous; adds
+ * each minibatch loss to *loss_acc_dev when it is not NULL. */
+int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,
+                               float lr, double *loss_acc_dev, void *stream);
 /* Inference: x_dev float32 [n][6] -> out_dev float32 [n][60] (asynchronous). */
 int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, void *stream);
 /* Synchronise and report a tensor-core pipeline that gave up waiting
  * (SUPA_ERR_TIMEOUT) since the last check. */
 int supa_surrogate_check(supa_surrogate *s);
+
+/* Switch a batch to the hybrid path: from the next supa_simulate on, a
+ * particle whose energy is below e_s when it reaches a slice of a readout
+ * layer is not stepped; it joins a device queue (at most queue_capacity
+ * particles, else SUPA_ERR_OVERFLOW), the network predicts its deposits in
+ * the next 30 layers, deposits are drawn (Philox normals keyed by shower,
+ * slice and lineage), added to the layer sums and emitted as one hit per
+ * non-empty layer (at the particle's straight-line position at the layer's
+ * mid depth) after the shower's stepped hits.  The energy the draws leave
+ * over is reported as sur_leak.  s = NULL or e_s <= 0 returns the batch to
+ * the plain path.  s must outlive the batch.  Synchronous (allocates). */
+int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity);
+
+/* Training set of the network from a plain simulation of sub-showers (each
+ * primary entering on its start slice, see supa_primary.geom): x_dev float32
+ * [n][6] features of the start, y_dev float32 [n][30] deposit fractions of
+ * layers start + 0..29 (FP64 layer sums / E).  Synchronous. */
+int supa_build_training_set(supa_batch *b, float e_s, float *x_dev, float *y_dev, void *stream);
 
 #ifdef __cplusplus
 }

@@ -56,8 +56,11 @@ class _Geom(ctypes.Structure):
 
 class _Primary(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
-                ("theta", ctypes.c_double), ("phi", ctypes.c_double)]
+                ("theta", ctypes.c_double), ("phi", ctypes.c_double), ("start_slice", ctypes.c_int)]
 
+
+_PRIMARY_NP = np.dtype([("E", "<f8"), ("x0", "<f8"), ("y0", "<f8"), ("theta", "<f8"), ("phi", "<f8"),
+                        ("start_slice", "<i4"), ("pad", "<i4")])
 
 _P = ctypes.POINTER
 
@@ -118,9 +121,11 @@ def simulate(geom, prims: np.ndarray, seed: int, shower_id_base: int = 0, n_thre
               int(geom.theta_mode), float(geom.theta_lo), float(geom.theta_hi), int(geom.eps_mode),
               float(geom.eps_frac), int(geom.split_mode), float(geom.e_min), float(geom.uz_min))
     n = len(prims)
-    pr = np.zeros((n, 5), dtype=np.float64)
-    for i, f in enumerate(("E", "x0", "y0", "theta", "phi")):
-        pr[:, i] = prims[f].astype(np.float64)
+    assert ctypes.sizeof(_Primary) == _PRIMARY_NP.itemsize
+    pr = np.zeros(max(n, 1), dtype=_PRIMARY_NP)
+    for f in ("E", "x0", "y0", "theta", "phi"):
+        pr[f][:n] = prims[f].astype(np.float64)
+    pr["start_slice"][:n] = (prims["geom"].astype(np.uint32) >> np.uint32(16)).astype(np.int32)
     res = _Result()
     rc = lib().ora_simulate(ctypes.byref(g), _ptr(pr), n, int(seed) & (2**64 - 1), int(shower_id_base),
                             int(n_threads), ctypes.byref(res))

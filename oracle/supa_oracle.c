@@ -164,7 +164,8 @@ static int simulate_one(const ora_geom *g, const ora_primary *p, uint64_t seed,
     q0.ux = sin(p->theta) * cos(p->phi);
     q0.uy = sin(p->theta) * sin(p->phi);
     q0.uz = cos(p->theta);
-    q0.E = p->E; q0.slice = 0; q0.depth = 0; q0.lineage = 1;
+    q0.E = p->E; q0.slice = p->start_slice; q0.depth = 0; q0.lineage = 1;
+    if (q0.slice < 0 || q0.slice >= g->n_slices) return -1;
     if (push_particle(w, q0)) return -1;
 
     while (w->n_stack > 0) {

@@ -44,9 +44,11 @@ typedef struct {
 } ora_geom;
 
 /* One primary: initial energy, impact position and incidence angles
- * (Sec. 3 initial particle; Sec. 4.2 conditioning). */
+ * (Sec. 3 initial particle; Sec. 4.2 conditioning), and the slice it enters
+ * on (0 for a shower; a later slice starts a sub-shower there). */
 typedef struct {
     double E, x0, y0, theta, phi;
+    int start_slice;
 } ora_primary;
 
 typedef struct {

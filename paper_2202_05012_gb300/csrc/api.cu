@@ -64,6 +64,7 @@ struct supa_geometry {
     std::vector<unsigned long long> t_stop, t_ss;
     std::vector<int8_t> s2l;
     std::vector<float> zmid;
+    std::vector<LayerInfo> linfo;
     int device = 0;
     GeomDev *d_rec = nullptr;
     unsigned long long *d_tstop = nullptr, *d_tss = nullptr;
@@ -82,6 +83,21 @@ struct supa_batch {
     unsigned long long *d_tstop = nullptr, *d_tss = nullptr;
     int8_t *d_s2l = nullptr;
     float *d_zmid = nullptr;
+    LayerInfo *d_linfo = nullptr;
+    // hybrid path
+    supa_surrogate *sur = nullptr;
+    float e_s = 0.0f;
+    int sq_cap = 0;
+    SurInfer inf;
+    SurRec *d_sq_rec = nullptr;
+    float *d_sq_feat = nullptr, *d_dep = nullptr;
+    unsigned *d_sq_count = nullptr;
+    uint32_t *d_scount = nullptr, *d_scursor = nullptr, *d_tot = nullptr;
+    int64_t *d_soff = nullptr;
+    float4 *d_sur_hits = nullptr;
+    double *d_sur_leak = nullptr;
+    unsigned long long *d_scan_tmp2 = nullptr;
+    int64_t n_diverted = 0;
     // inputs
     supa_primary *d_prim = nullptr;
     uint32_t *d_queue = nullptr, *d_bucket = nullptr;
@@ -177,11 +193,16 @@ int supa_init_geometry(const supa_geometry_desc *d, supa_geometry **out) {
         }
     }
     g->zmid.resize(d->n_layers);
+    g->linfo.resize(d->n_layers);
     for (int l = 0; l < d->n_layers; ++l) {
         if (kmax[l] < 0) {
             delete g;
             return fail(SUPA_ERR_INVALID_ARG, "layer %d has no slice", l);
         }
+        int cnt = 0;
+        for (int k = 0; k < n; ++k) cnt += d->slice_to_layer[k] == l;
+        g->linfo[l].k_first = (int16_t)kmin[l];
+        g->linfo[l].n_slices = (int16_t)cnt;
         // mid depth of the layer, float32 as the downsampling kernel uses it
         g->zmid[l] = (d->dz * (float)(kmin[l] + kmax[l])) * 0.5f;
     }
@@ -237,8 +258,28 @@ int supa_destroy_geometry(supa_geometry *g) {
     return SUPA_OK;
 }
 
+static void free_hybrid(supa_batch *b) {
+    void *ptrs[] = {b->d_sq_rec, b->d_sq_feat, b->d_dep, b->d_sq_count, b->d_scount, b->d_scursor, b->d_tot,
+                    b->d_soff, b->d_sur_hits, b->d_sur_leak, b->d_scan_tmp2};
+    for (void *p : ptrs) cudaFree(p);
+    surrogate_infer_free(&b->inf);
+    b->d_sq_rec = nullptr;
+    b->d_sq_feat = b->d_dep = nullptr;
+    b->d_sq_count = nullptr;
+    b->d_scount = b->d_scursor = b->d_tot = nullptr;
+    b->d_soff = nullptr;
+    b->d_sur_hits = nullptr;
+    b->d_sur_leak = nullptr;
+    b->d_scan_tmp2 = nullptr;
+    b->sur = nullptr;
+    b->e_s = 0.0f;
+    b->sq_cap = 0;
+}
+
 int supa_destroy_batch(supa_batch *b) {
     if (!b) return SUPA_OK;
+    free_hybrid(b);
+    cudaFree(b->d_linfo);
     void *ptrs[] = {b->d_geoms, b->d_tstop, b->d_tss, b->d_s2l, b->d_zmid, b->d_prim, b->d_queue,
                     b->d_bucket, b->d_pool, b->d_tags, b->d_page_next, b->d_hit_start, b->d_hit_count,
                     b->d_steps, b->d_lsum, b->d_dead, b->d_leak, b->d_escape, b->d_offsets, b->d_scan_tmp,
@@ -277,6 +318,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     std::vector<unsigned long long> ts, tss;
     std::vector<int8_t> s2l;
     std::vector<float> zm;
+    std::vector<LayerInfo> li;
     for (int i = 0; i < n_geoms; ++i) {
         GeomDev r = geoms[i]->rec;
         r.slice_off = (int)ts.size();
@@ -286,6 +328,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
         tss.insert(tss.end(), geoms[i]->t_ss.begin(), geoms[i]->t_ss.end());
         s2l.insert(s2l.end(), geoms[i]->s2l.begin(), geoms[i]->s2l.end());
         zm.insert(zm.end(), geoms[i]->zmid.begin(), geoms[i]->zmid.end());
+        li.insert(li.end(), geoms[i]->linfo.begin(), geoms[i]->linfo.end());
         b->max_layers = std::max(b->max_layers, r.n_layers);
     }
 
@@ -339,6 +382,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     if (e == cudaSuccess) e = dalloc(&b->d_tss, tss.size());
     if (e == cudaSuccess) e = dalloc(&b->d_s2l, s2l.size());
     if (e == cudaSuccess) e = dalloc(&b->d_zmid, zm.size());
+    if (e == cudaSuccess) e = dalloc(&b->d_linfo, li.size());
     if (e == cudaSuccess) e = dalloc(&b->d_prim, n);
     if (e == cudaSuccess && b->lpt) e = dalloc(&b->d_queue, n);
     if (e == cudaSuccess && b->lpt) e = dalloc(&b->d_bucket, 256);
@@ -362,6 +406,8 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tss, tss.data(), tss.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_s2l, s2l.data(), s2l.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_zmid, zm.data(), zm.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_linfo, li.data(), li.size() * sizeof(LayerInfo), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         supa_destroy_batch(b);
         if (e == cudaErrorMemoryAllocation) {
@@ -422,8 +468,104 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     p.stage_cap = b->stage_cap;
     p.flush_thr = b->flush_thr;
     p.warp_smem_bytes = b->warp_bytes;
+    const bool hybrid = b->sur != nullptr;
+    if (hybrid) {
+        p.e_s = b->e_s;
+        p.linfo = b->d_linfo;
+        p.sq_rec = b->d_sq_rec;
+        p.sq_feat = b->d_sq_feat;
+        p.sq_count = b->d_sq_count;
+        p.sq_cap = b->sq_cap;
+        SUPA_CUDA(cudaMemsetAsync(b->d_sq_count, 0, sizeof(unsigned), st));
+        SUPA_CUDA(cudaMemsetAsync(b->d_scount, 0, (size_t)std::max<int64_t>(n, 1) * 4, st));
+        SUPA_CUDA(cudaMemsetAsync(b->d_scursor, 0, (size_t)std::max<int64_t>(n, 1) * 4, st));
+        SUPA_CUDA(cudaMemsetAsync(b->d_sur_leak, 0, (size_t)std::max<int64_t>(n, 1) * 8, st));
+    }
     if (n > 0) SUPA_CUDA(launch_step(b->minb, p, b->grid, b->block, b->smem, st));
-    SUPA_CUDA(launch_scan_counts(b->d_hit_count, n, b->d_offsets, b->d_scan_tmp, st));
+    if (!hybrid) {
+        SUPA_CUDA(launch_scan_counts(b->d_hit_count, n, b->d_offsets, b->d_scan_tmp, st));
+        return SUPA_OK;
+    }
+    // hybrid: network over the queue, deposits, surrogate hit segments
+    SUPA_CUDA(surrogate_infer_run(b->sur, &b->inf, b->d_sq_feat, b->d_sq_count, st));
+    SurParams sp{};
+    sp.rec = b->d_sq_rec;
+    sp.count = b->d_sq_count;
+    sp.cap = b->sq_cap;
+    sp.out = b->inf.OUT;
+    sp.prim = b->d_prim;
+    sp.geoms = b->d_geoms;
+    sp.zmid = b->d_zmid;
+    sp.seed = seed;
+    sp.shower_id_base = shower_id_base;
+    sp.dep = b->d_dep;
+    sp.lsum = b->d_lsum;
+    sp.lsum_stride = b->max_layers;
+    sp.sur_leak = b->d_sur_leak;
+    sp.scount = b->d_scount;
+    sp.soff = b->d_soff;
+    sp.scursor = b->d_scursor;
+    sp.hits = b->d_sur_hits;
+    SUPA_CUDA(launch_sur_deposits(sp, st));
+    SUPA_CUDA(launch_scan_counts(b->d_scount, n, b->d_soff, b->d_scan_tmp2, st));
+    SUPA_CUDA(launch_sur_hits(sp, st));
+    SUPA_CUDA(launch_add_counts(b->d_hit_count, b->d_scount, n, b->d_tot, st));
+    SUPA_CUDA(launch_scan_counts(b->d_tot, n, b->d_offsets, b->d_scan_tmp, st));
+    return SUPA_OK;
+}
+
+int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity) {
+    if (!b) return fail(SUPA_ERR_INVALID_ARG, "supa_batch_set_surrogate: null batch");
+    free_hybrid(b);
+    b->last_n = -1;
+    b->info_valid = false;
+    if (!s || !(e_s > 0.0f)) return SUPA_OK;
+    if (queue_capacity < 128 || queue_capacity > (int64_t)1 << 30)
+        return fail(SUPA_ERR_INVALID_ARG, "queue_capacity must be in [128, 2^30]");
+    const int cap = (int)((queue_capacity + 127) / 128 * 128);
+    const int64_t n = b->max_showers;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dalloc(&b->d_sq_rec, cap);
+    if (e == cudaSuccess) e = dalloc(&b->d_sq_feat, (size_t)cap * kSurIn);
+    if (e == cudaSuccess) e = dalloc(&b->d_dep, (size_t)cap * kSurLayers);
+    if (e == cudaSuccess) e = dalloc(&b->d_sq_count, 1);
+    if (e == cudaSuccess) e = dalloc(&b->d_scount, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_scursor, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_tot, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_soff, n + 1);
+    if (e == cudaSuccess) e = dalloc(&b->d_sur_hits, (size_t)cap * kSurLayers);
+    if (e == cudaSuccess) e = dalloc(&b->d_sur_leak, n);
+    if (e == cudaSuccess) e = dalloc(&b->d_scan_tmp2, scan_tmp_elems(n) + 1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_hybrid(b);
+        return fail(SUPA_ERR_OOM, "supa_batch_set_surrogate: out of device memory");
+    }
+    const int rc = surrogate_infer_init(s, cap, &b->inf);
+    if (rc != SUPA_OK) {
+        free_hybrid(b);
+        return rc;
+    }
+    b->sur = s;
+    b->e_s = e_s;
+    b->sq_cap = cap;
+    return SUPA_OK;
+}
+
+int supa_build_training_set(supa_batch *b, float e_s, float *x_dev, float *y_dev, void *stream) {
+    if (!b || !x_dev || !y_dev || !(e_s > 0.0f))
+        return fail(SUPA_ERR_INVALID_ARG, "supa_build_training_set: bad argument");
+    if (b->last_n < 0) return fail(SUPA_ERR_NOT_READY, "no simulation has been enqueued on this batch");
+    if (b->sur) return fail(SUPA_ERR_INVALID_ARG, "training sets come from plain (not hybrid) simulations");
+    cudaStream_t st = (cudaStream_t)stream;
+    int *bad = b->d_ctrl + 3;
+    SUPA_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    SUPA_CUDA(launch_training_set(b->d_prim, b->last_n, b->d_geoms, b->d_s2l, b->d_linfo, b->d_lsum, b->max_layers,
+                                  e_s, x_dev, y_dev, bad, st));
+    int h = 0;
+    SUPA_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SUPA_CUDA(cudaStreamSynchronize(st));
+    if (h) return fail(SUPA_ERR_INVALID_ARG, "a sub-shower starts on a slice outside every readout layer");
     return SUPA_OK;
 }
 
@@ -522,6 +664,8 @@ int supa_batch_get_info(supa_batch *b, supa_batch_info *info, void *stream) {
     SUPA_CUDA(cudaMemcpyAsync(ctrl, b->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, st));
     SUPA_CUDA(cudaMemcpyAsync(tot, b->d_totals, sizeof(tot), cudaMemcpyDeviceToHost, st));
     SUPA_CUDA(cudaMemcpyAsync(&nh, b->d_offsets + b->last_n, sizeof(nh), cudaMemcpyDeviceToHost, st));
+    unsigned diverted = 0;
+    if (b->sur) SUPA_CUDA(cudaMemcpyAsync(&diverted, b->d_sq_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     SUPA_CUDA(cudaStreamSynchronize(st));
     memset(info, 0, sizeof(*info));
     info->n_showers = b->last_n;
@@ -529,12 +673,29 @@ int supa_batch_get_info(supa_batch *b, supa_batch_info *info, void *stream) {
     info->n_steps = (int64_t)tot[0];
     info->max_layers = b->max_layers;
     info->offsets_dev = b->d_offsets;
-    info->counts_dev = b->d_hit_count;
+    info->counts_dev = b->sur ? b->d_tot : b->d_hit_count;
     info->steps_dev = b->d_steps;
     info->layer_sums_dev = b->d_lsum;
     info->dead_dev = b->d_dead;
     info->leak_dev = b->d_leak;
     info->escape_dev = b->d_escape;
+    info->n_diverted = diverted;
+    info->sur_leak_dev = b->sur ? b->d_sur_leak : nullptr;
+    b->n_diverted = diverted;
+    if (b->sur) {
+        int gemm_err = 0;
+        const int rc = supa_surrogate_check(b->sur);
+        if (rc != SUPA_OK) gemm_err = rc;
+        if (gemm_err) {
+            info->status = gemm_err;
+            return gemm_err;
+        }
+    }
+    if (ctrl[2] & kErrQueueOverflow) {
+        info->status = SUPA_ERR_OVERFLOW;
+        return fail(SUPA_ERR_OVERFLOW, "%u particles fell below E_s but the surrogate queue holds %d; raise "
+                    "queue_capacity", diverted, b->sq_cap);
+    }
     if (ctrl[2] == kErrBadPrimary) {
         info->status = SUPA_ERR_INVALID_ARG;
         return fail(SUPA_ERR_INVALID_ARG, "a primary was invalid (geometry index, energy <= 0 or above the lineage "
@@ -568,6 +729,11 @@ static int fetch_common(supa_batch *b, int64_t first, int64_t max_hits, void *ds
     p.src.hit_start = b->d_hit_start;
     p.src.hit_count = b->d_hit_count;
     p.src.offsets = b->d_offsets;
+    if (b->sur) {
+        p.src.sur_hits = b->d_sur_hits;
+        p.src.sur_off = b->d_soff;
+        p.src.sur_count = b->d_scount;
+    }
     p.tag_pool = tags ? b->d_tags : nullptr;
     p.n_showers = b->last_n;
     if (dev) {
@@ -637,6 +803,11 @@ int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float
     p.src.page_next = b->d_page_next;
     p.src.hit_start = b->d_hit_start;
     p.src.hit_count = b->d_hit_count;
+    if (b->sur) {
+        p.src.sur_hits = b->d_sur_hits;
+        p.src.sur_off = b->d_soff;
+        p.src.sur_count = b->d_scount;
+    }
     p.s_begin = shower_begin;
     p.n_showers = n;
     p.L = b->max_layers;

@@ -226,8 +226,10 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
         if ((*((volatile int *)p.error) & (kErrPoolOverflow | kErrSpillOverflow)) != 0) break;
         const int64_t s = p.queue ? (int64_t)p.queue[q] : (int64_t)q;
         const supa_primary pr = p.prim[s];
-        if (pr.geom >= (uint32_t)p.n_geoms || !(pr.E > 0.0f) || !(pr.E <= p.geoms[pr.geom].e0_max) ||
-            !(pr.E < 1073741824.0f) ||
+        const uint32_t gi = pr.geom & 0xFFFFu;  // geometry index
+        const int k0 = (int)(pr.geom >> 16);    // slice the particle enters on (0 for a shower)
+        if (gi >= (uint32_t)p.n_geoms || k0 >= p.geoms[gi].n_slices || !(pr.E > 0.0f) ||
+            !(pr.E <= p.geoms[gi].e0_max) || !(pr.E < 1073741824.0f) ||
             !(pr.theta >= 0.0f && pr.theta < 1.5707963f) || !isfinite(pr.phi) || !isfinite(pr.x0) ||
             !isfinite(pr.y0)) {
             // invalid primary: report it and leave an empty shower behind
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
             for (int l = lane; l < p.lsum_stride; l += 32) p.lsum[(size_t)s * p.lsum_stride + l] = 0.0;
             continue;
         }
-        const GeomDev g = p.geoms[pr.geom];
+        const GeomDev g = p.geoms[gi];
         const uint32_t sid = (uint32_t)(p.shower_id_base + (uint64_t)s);
 
         for (int l = lane; l < g.n_layers; l += 32) w.lsum[l] = 0ull;
@@ -249,7 +251,8 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
         }
         const unsigned long long start = (unsigned long long)pc.page * kPageHits + pc.off;
 
-        // Initial particle (Sec. 3): impact point on slice 0, incidence direction.
+        // Initial particle (Sec. 3): impact point on its entry slice (0 for a
+        // shower's primary), incidence direction.
         Particle cur;
         bool have = (lane == 0);
         {
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
             sincosf(pr.phi, &sp, &cp);
             cur.x = pr.x0; cur.y = pr.y0;
             cur.ux = st * cp; cur.uy = st * sp; cur.uz = ct;
-            cur.E = pr.E; cur.lin = 1ull; cur.k = 0;
+            cur.E = pr.E; cur.lin = 1ull; cur.k = k0;
         }
         int stack_n = 0, spill_n = 0, staged = 0;
         uint32_t n_hits = 0, n_steps = 0;
@@ -289,6 +292,45 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
             __syncwarp();
             const unsigned act = __ballot_sync(kFull, have);
             if (act == 0) break;
+
+            // ---- hybrid path: hand particles below E_s (in a readout layer)
+            //      to the surrogate queue instead of stepping them ----
+            if (p.e_s > 0.0f) {
+                int lay = -1;
+                const bool divert = have && cur.E < p.e_s && (lay = __ldg(p.s2l + g.slice_off + cur.k)) >= 0;
+                const unsigned dm = __ballot_sync(kFull, divert);
+                if (dm) {
+                    unsigned base = 0;
+                    if (lane == 0) base = atomicAdd(p.sq_count, (unsigned)__popc(dm));
+                    base = __shfl_sync(kFull, base, 0);
+                    if (divert) {
+                        const unsigned idx = base + (unsigned)__popc(dm & lt_mask);
+                        if (idx < (unsigned)p.sq_cap) {
+                            SurRec rec;
+                            rec.shower = (uint32_t)s;
+                            rec.k = (int16_t)cur.k;
+                            rec.layer = (int16_t)lay;
+                            rec.x = cur.x;
+                            rec.y = cur.y;
+                            const float r = __frcp_rn(cur.uz);
+                            rec.tx = cur.ux * r;
+                            rec.ty = cur.uy * r;
+                            rec.E = cur.E;
+                            rec.lin_lo = (uint32_t)cur.lin;
+                            rec.lin_hi = (uint32_t)(cur.lin >> 32);
+                            p.sq_rec[idx] = rec;
+                            float f[kSurIn];
+                            surrogate_features(cur.E, cur.ux, cur.uy, cur.uz, cur.k, lay, g.n_layers,
+                                               p.linfo[g.layer_off + lay], p.e_s, f);
+#pragma unroll
+                            for (int i = 0; i < kSurIn; ++i) p.sq_feat[(size_t)idx * kSurIn + i] = f[i];
+                        } else {
+                            atomicOr(p.error, kErrQueueOverflow);
+                        }
+                        have = false;
+                    }
+                }
+            }
 
             // ---- one step of Algorithm 1 for every active lane ----
             bool push = false, hit = false;

@@ -2,6 +2,7 @@
 // host code of the C ABI.  Nothing here is visible through include/supa.h.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +30,79 @@ struct GeomDev {
     int roi_axis;
     float e0_max;  // largest primary energy whose lineage ids fit 64 bits
 };
+
+// ---- hybrid path: particles below E_s handed to the surrogate network ----
+constexpr int kSurIn = 6;       // features
+constexpr int kSurLayers = 30;  // predicted layers (start layer + 0..29)
+
+// A diverted particle: where it is and what it carries.
+struct SurRec {
+    uint32_t shower;  // index in the batch
+    int16_t k;        // slice of diversion
+    int16_t layer;    // its readout layer
+    float x, y;       // position on slice k
+    float tx, ty;     // slopes u_x/u_z, u_y/u_z
+    float E;
+    uint32_t lin_lo, lin_hi;
+};
+
+// Per-layer tables used by the features (first slice and slice count).
+struct LayerInfo {
+    int16_t k_first, n_slices;
+};
+
+// The 6 inputs of the surrogate for a particle of energy E on slice k of
+// layer l: log(E / E_s), the direction cosines, the position of the slice
+// within its layer, and the layers left from l to the back (over 30).
+__host__ __device__ inline void surrogate_features(float E, float ux, float uy, float uz, int k, int l, int n_layers,
+                                                   LayerInfo li, float e_s, float *f) {
+    f[0] = logf(E / e_s);
+    f[1] = ux;
+    f[2] = uy;
+    f[3] = uz;
+    f[4] = (float)(k - li.k_first) / (float)li.n_slices;
+    const float rem = (float)(n_layers - l) / (float)kSurLayers;
+    f[5] = rem < 1.0f ? rem : 1.0f;
+}
+
+// Inference buffers for a queue of up to `cap` diverted particles (owned by
+// a batch): bf16 inputs and ping-pong hidden activations, f32 outputs [cap][64].
+struct SurInfer {
+    int cap = 0;
+    void *X0 = nullptr, *Ha = nullptr, *Hb = nullptr;
+    float *OUT = nullptr;
+    CUtensorMap mX0, mHa, mHb;
+};
+int surrogate_infer_init(supa_surrogate *s, int cap, SurInfer *inf);
+void surrogate_infer_free(SurInfer *inf);
+// Outputs of the first min(*count_dev, cap) rows of feat [cap][6] into inf->OUT.
+cudaError_t surrogate_infer_run(supa_surrogate *s, SurInfer *inf, const float *feat, const unsigned *count_dev,
+                                cudaStream_t st);
+
+struct SurParams {
+    const SurRec *rec;
+    const unsigned *count;  // queue length (device)
+    int cap;
+    const float *out;       // network outputs [cap][64]
+    const supa_primary *prim;
+    const GeomDev *geoms;
+    const float *zmid;
+    uint64_t seed, shower_id_base;
+    float *dep;             // [cap][30] drawn deposits
+    double *lsum;
+    int lsum_stride;
+    double *sur_leak;       // [n]
+    uint32_t *scount;       // [n] surrogate hits per shower
+    const int64_t *soff;    // [n+1] exclusive scan of scount
+    uint32_t *scursor;      // [n]
+    float4 *hits;           // surrogate hit segments
+};
+cudaError_t launch_sur_deposits(const SurParams &p, cudaStream_t st);
+cudaError_t launch_sur_hits(const SurParams &p, cudaStream_t st);
+cudaError_t launch_add_counts(const uint32_t *a, const uint32_t *b, int64_t n, uint32_t *out, cudaStream_t st);
+cudaError_t launch_training_set(const supa_primary *prim, int64_t n, const GeomDev *geoms, const int8_t *s2l,
+                                const LayerInfo *linfo, const double *lsum, int stride, float e_s, float *x, float *y,
+                                int *bad, cudaStream_t st);
 
 // Particle record of the per-warp global spill stack (36 bytes).
 struct SpillRec {
@@ -73,6 +147,13 @@ struct StepParams {
     int stage_cap;        // staged hits per warp (>= flush_thr + 32)
     int flush_thr;
     int warp_smem_bytes;  // shared memory per warp
+    // hybrid path (e_s = 0: off)
+    float e_s;
+    const LayerInfo *linfo;  // per geometry layer (layer_off + l)
+    SurRec *sq_rec;
+    float *sq_feat;          // [sq_cap][6]
+    unsigned *sq_count;
+    int sq_cap;
 };
 
 // Record the message returned by supa_last_error() and return `code`.
@@ -82,6 +163,7 @@ int set_last_error(int code, const char *msg);
 constexpr int kErrPoolOverflow = 1;
 constexpr int kErrSpillOverflow = 2;
 constexpr int kErrBadPrimary = 4;
+constexpr int kErrQueueOverflow = 16;
 
 size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags);
 
@@ -104,6 +186,10 @@ struct HitSource {
     const uint32_t *hit_count;
     const float4 *hits;
     const int64_t *offsets;
+    // hybrid path: surrogate hits follow the stepped ones (null otherwise)
+    const float4 *sur_hits;
+    const int64_t *sur_off;
+    const uint32_t *sur_count;
 };
 
 struct VoxParams {

@@ -45,15 +45,19 @@ cudaError_t dalloc(T **p, size_t n) {
     return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
 }
 
-__global__ void pack_inputs(const float *x, int64_t n, int B, __nv_bfloat16 *X0, __nv_bfloat16 *X0T) {
+// Inputs [n][6] float32 -> X0 [B][64] bf16 (and its transpose when X0T is
+// not null); rows past n (or past *n_dev) are zero.
+__global__ void pack_inputs(const float *x, int64_t n, const unsigned *n_dev, int B, __nv_bfloat16 *X0,
+                            __nv_bfloat16 *X0T) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= B) return;
+    if (n_dev) n = min((int64_t)*n_dev, n);
     float v[kIn];
     for (int j = 0; j < kIn; ++j) v[j] = r < n ? x[(size_t)r * kIn + j] : 0.0f;
     for (int j = 0; j < kInPad; ++j) {
         const __nv_bfloat16 h = __float2bfloat16_rn(j < kIn ? v[j] : 0.0f);
         X0[(size_t)r * kInPad + j] = h;
-        X0T[(size_t)j * B + r] = h;
+        if (X0T) X0T[(size_t)j * B + r] = h;
     }
 }
 
@@ -113,6 +117,16 @@ __global__ void adam_update(float *p, float *m, float *v, const float *g, size_t
     }
 }
 
+// Rows (a i + c) mod n, i = i0 .. i0 + B - 1, of x [n][6] and y [n][30].
+__global__ void gather_rows(const float *x, const float *y, int64_t n, uint64_t a, uint64_t c, int64_t i0, int B,
+                            float *xs, float *ys) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= B) return;
+    const uint64_t src = (a * (uint64_t)(i0 + r) + c) % (uint64_t)n;
+    for (int j = 0; j < kIn; ++j) xs[(size_t)r * kIn + j] = x[src * kIn + j];
+    for (int j = 0; j < kLayersOut; ++j) ys[(size_t)r * kLayersOut + j] = y[src * kLayersOut + j];
+}
+
 // BF16 copies of a master weight [rows][cols]: W and (optionally) W^T.
 __global__ void cast_weight(const float *W, int rows, int cols, __nv_bfloat16 *Wb, __nv_bfloat16 *WTb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -133,6 +147,7 @@ struct supa_surrogate {
     __nv_bfloat16 *W1b, *W2b, *W3b, *W4b, *W2Tb, *W3Tb, *W4Tb;
     __nv_bfloat16 *X0, *X0T, *H1, *H2, *H3, *H1T, *H2T, *H3T, *G4, *G4T, *G3, *G2, *G1, *G3T, *G2T, *G1T;
     float *Z1, *Z2, *Z3, *OUT;
+    float *Xs = nullptr, *Ys = nullptr;  // gathered minibatch (epoch training)
     double *loss_tmp = nullptr;
     int *error = nullptr;
     CUtensorMap mX0, mH1, mH2, mH3, mG4, mG3, mG2, mG4T, mG3T, mG2T, mG1T;  // A operands (box 128 rows)
@@ -280,6 +295,62 @@ void pack_params(const std::vector<float> &mst, float *p) {
 
 }  // namespace
 
+// ---- inference over a device-counted queue (hybrid path) -----------------
+
+namespace supa {
+
+void surrogate_infer_free(SurInfer *inf) {
+    cudaFree(inf->X0);
+    cudaFree(inf->Ha);
+    cudaFree(inf->Hb);
+    cudaFree(inf->OUT);
+    inf->X0 = inf->Ha = inf->Hb = nullptr;
+    inf->OUT = nullptr;
+    inf->cap = 0;
+}
+
+int surrogate_infer_init(supa_surrogate *s, int cap, SurInfer *inf) {
+    (void)s;
+    inf->cap = cap;
+    const size_t C = (size_t)cap;
+    if (cudaMalloc(&inf->X0, C * kInPad * 2) != cudaSuccess || cudaMalloc(&inf->Ha, C * kHid * 2) != cudaSuccess ||
+        cudaMalloc(&inf->Hb, C * kHid * 2) != cudaSuccess ||
+        cudaMalloc((void **)&inf->OUT, C * kOutPad * 4) != cudaSuccess) {
+        cudaGetLastError();
+        surrogate_infer_free(inf);
+        return set_last_error(SUPA_ERR_OOM, "surrogate queue buffers: out of device memory");
+    }
+    int rc = make_bf16_map(&inf->mX0, inf->X0, C, kInPad, 128);
+    rc |= make_bf16_map(&inf->mHa, inf->Ha, C, kHid, 128);
+    rc |= make_bf16_map(&inf->mHb, inf->Hb, C, kHid, 128);
+    if (rc) {
+        surrogate_infer_free(inf);
+        return set_last_error(SUPA_ERR_CUDA, "surrogate queue buffers: cuTensorMapEncodeTiled failed");
+    }
+    return SUPA_OK;
+}
+
+cudaError_t surrogate_infer_run(supa_surrogate *s, SurInfer *inf, const float *feat, const unsigned *count_dev,
+                                cudaStream_t st) {
+    const int C = inf->cap;
+    pack_inputs<<<(C + 255) / 256, 256, 0, st>>>(feat, C, count_dev, C, (__nv_bfloat16 *)inf->X0, nullptr);
+    GemmArgs a = gargs(C, kHid, kInPad, EPI_GELU_ONLY, s->error);
+    a.bias = s->master + Off::b1; a.out_bf16 = (__nv_bfloat16 *)inf->Ha; a.ld = kHid; a.m_dev = count_dev;
+    cudaError_t e = gemm(inf->mX0, s->mW1, a, st);
+    if (e != cudaSuccess) return e;
+    a = gargs(C, kHid, kHid, EPI_GELU_ONLY, s->error);
+    a.bias = s->master + Off::b2; a.out_bf16 = (__nv_bfloat16 *)inf->Hb; a.ld = kHid; a.m_dev = count_dev;
+    if ((e = gemm(inf->mHa, s->mW2, a, st)) != cudaSuccess) return e;
+    a = gargs(C, kHid, kHid, EPI_GELU_ONLY, s->error);
+    a.bias = s->master + Off::b3; a.out_bf16 = (__nv_bfloat16 *)inf->Ha; a.ld = kHid; a.m_dev = count_dev;
+    if ((e = gemm(inf->mHb, s->mW3, a, st)) != cudaSuccess) return e;
+    a = gargs(C, kOutPad, kHid, EPI_BIAS_F32, s->error);
+    a.bias = s->master + Off::b4; a.out_f32 = inf->OUT; a.ld = kOutPad; a.m_dev = count_dev;
+    return gemm(inf->mHa, s->mW4, a, st);
+}
+
+}  // namespace supa
+
 extern "C" {
 
 int32_t supa_surrogate_param_count(void) { return kNParams; }
@@ -311,7 +382,7 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
               grab(s, &s->G1, B * kHid) && grab(s, &s->G3T, B * kHid) && grab(s, &s->G2T, B * kHid) &&
               grab(s, &s->G1T, B * kHid) && grab(s, &s->Z1, B * kHid) && grab(s, &s->Z2, B * kHid) &&
               grab(s, &s->Z3, B * kHid) && grab(s, &s->OUT, B * kOutPad) && grab(s, &s->loss_tmp, 1) &&
-              grab(s, &s->error, 1);
+              grab(s, &s->error, 1) && grab(s, &s->Xs, B * kIn) && grab(s, &s->Ys, B * kLayersOut);
     if (!ok) {
         supa_surrogate_destroy(s);
         return sfail(SUPA_ERR_OOM, "supa_surrogate_create: out of device memory");
@@ -376,7 +447,7 @@ int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float 
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(s->loss_tmp, 0, sizeof(double), st) != cudaSuccess)
         return sfail(SUPA_ERR_CUDA, "memset failed");
-    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0, s->X0T);
+    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, nullptr, s->B, s->X0, s->X0T);
     cudaError_t e = forward(s, true, st);
     if (e == cudaSuccess) e = backward(s, y_dev, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -397,7 +468,7 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
     if (!s || !x_dev || !y_dev) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_step: null argument");
     cudaStream_t st = (cudaStream_t)stream;
     double *loss = loss_acc_dev ? loss_acc_dev : s->loss_tmp;
-    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0, s->X0T);
+    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, nullptr, s->B, s->X0, s->X0T);
     cudaError_t e = forward(s, true, st);
     if (e == cudaSuccess) {
         // backward() writes the minibatch loss into s->loss_tmp; point it at the accumulator
@@ -415,13 +486,40 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_step launch failed");
 }
 
+int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,
+                               float lr, double *loss_acc_dev, void *stream) {
+    if (!s || !x_dev || !y_dev || n < s->B)
+        return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_epoch: need at least one full minibatch");
+    cudaStream_t st = (cudaStream_t)stream;
+    // permutation i -> (a i + c) mod n with gcd(a, n) = 1
+    uint64_t a = (seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull) % (uint64_t)n;
+    if (a == 0) a = 1;
+    auto gcd = [](uint64_t u, uint64_t v) {
+        while (v) {
+            const uint64_t t = u % v;
+            u = v;
+            v = t;
+        }
+        return u;
+    };
+    while (gcd(a, (uint64_t)n) != 1) a = (a + 1) % (uint64_t)n == 0 ? 1 : a + 1;
+    const uint64_t c = (seed ^ 0xD1B54A32D192ED03ull) % (uint64_t)n;
+    const int64_t steps = n / s->B;
+    for (int64_t k = 0; k < steps; ++k) {
+        gather_rows<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, y_dev, n, a, c, k * s->B, s->B, s->Xs, s->Ys);
+        const int rc = supa_surrogate_train_step(s, s->Xs, s->Ys, lr, loss_acc_dev, stream);
+        if (rc != SUPA_OK) return rc;
+    }
+    return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_epoch launch failed");
+}
+
 int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, void *stream) {
     if (!s || (!x_dev && n > 0) || (!out_dev && n > 0))
         return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_forward: null argument");
     cudaStream_t st = (cudaStream_t)stream;
     for (int64_t r0 = 0; r0 < n; r0 += s->B) {
         const int64_t m = std::min<int64_t>(s->B, n - r0);
-        pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev + r0 * kIn, m, s->B, s->X0, s->X0T);
+        pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev + r0 * kIn, m, nullptr, s->B, s->X0, s->X0T);
         cudaError_t e = forward(s, false, st);
         if (e == cudaSuccess)
             e = cudaMemcpy2DAsync(out_dev + r0 * kOut, kOut * 4, s->OUT, kOutPad * 4, kOut * 4, m,

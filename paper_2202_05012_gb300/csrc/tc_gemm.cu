@@ -120,6 +120,11 @@ __global__ void __launch_bounds__(128, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kTileM;
+    // rows present: M, or fewer when a device-side count says so (a CTA with
+    // no rows leaves before touching barriers or tensor memory)
+    int M = g.M;
+    if (g.m_dev) M = (int)min((unsigned)M, *g.m_dev);
+    if (m0 >= M) return;
     const int kb0 = blockIdx.y * g.k_blocks_per_split;
     const int nkb = min(g.k_blocks_per_split, g.K / kTileK - kb0);
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(128, 1)
     const bool ok = nkb > 0 && mbar_wait(&done_bar, 0) && !*abort_v;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const int row = m0 + warp * 32 + lane;
-    const bool live = row < g.M;
+    const bool live = row < M;
     if (ok) {
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1

@@ -41,6 +41,7 @@ struct GemmArgs {
     float *colsum;      // [N] (GELU_BWD)
     int ld, ldT;
     int *error;         // device error word
+    const unsigned *m_dev;  // optional device row count: rows >= min(M, *m_dev) are skipped
 };
 
 constexpr int kGemmStages = 4;

@@ -28,7 +28,8 @@ EXPORTED = (
     "supa_simulate", "supa_simulate_batch", "supa_batch_get_info", "supa_fetch_hits", "supa_fetch_hit_tags",
     "supa_voxelize", "supa_voxelize_hits", "supa_autotune", "supa_surrogate_param_count", "supa_surrogate_create",
     "supa_surrogate_destroy", "supa_surrogate_get_params", "supa_surrogate_gradients", "supa_surrogate_train_step",
-    "supa_surrogate_forward", "supa_surrogate_check",
+    "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
+    "supa_build_training_set",
 )
 
 
@@ -65,7 +66,7 @@ class supa_batch_info(ctypes.Structure):
         ("max_layers", ctypes.c_int32), ("status", ctypes.c_int32),
         ("offsets_dev", ctypes.c_void_p), ("counts_dev", ctypes.c_void_p), ("steps_dev", ctypes.c_void_p),
         ("layer_sums_dev", ctypes.c_void_p), ("dead_dev", ctypes.c_void_p), ("leak_dev", ctypes.c_void_p),
-        ("escape_dev", ctypes.c_void_p),
+        ("escape_dev", ctypes.c_void_p), ("n_diverted", ctypes.c_int64), ("sur_leak_dev", ctypes.c_void_p),
     ]
 
 
@@ -112,6 +113,9 @@ def lib(build_if_missing: bool = True):
         L.supa_surrogate_train_step.argtypes = [_VP, _VP, _VP, ctypes.c_float, _VP, _VP]
         L.supa_surrogate_forward.argtypes = [_VP, _VP, _I64, _VP, _VP]
         L.supa_surrogate_check.argtypes = [_VP]
+        L.supa_surrogate_train_epoch.argtypes = [_VP, _VP, _VP, _I64, ctypes.c_uint64, ctypes.c_float, _VP, _VP]
+        L.supa_batch_set_surrogate.argtypes = [_VP, _VP, ctypes.c_float, _I64]
+        L.supa_build_training_set.argtypes = [_VP, ctypes.c_float, _VP, _VP, _VP]
         for name in EXPORTED[1:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -296,6 +300,20 @@ def supa_surrogate_forward(s: int, x_dev, n: int, out_dev, stream=None):
 
 def supa_surrogate_check(s: int):
     _check(lib().supa_surrogate_check(s), "supa_surrogate_check")
+
+
+def supa_surrogate_train_epoch(s: int, x_dev, y_dev, n: int, seed: int, lr: float, loss_acc_dev=None, stream=None):
+    _check(lib().supa_surrogate_train_epoch(s, _ptr(x_dev), _ptr(y_dev), int(n), int(seed) & (2**64 - 1), float(lr),
+                                            _ptr(loss_acc_dev), _stream(stream)), "supa_surrogate_train_epoch")
+
+
+def supa_batch_set_surrogate(b: int, s: int | None, e_s: float, queue_capacity: int):
+    _check(lib().supa_batch_set_surrogate(b, s, float(e_s), int(queue_capacity)), "supa_batch_set_surrogate")
+
+
+def supa_build_training_set(b: int, e_s: float, x_dev, y_dev, stream=None):
+    _check(lib().supa_build_training_set(b, float(e_s), _ptr(x_dev), _ptr(y_dev), _stream(stream)),
+           "supa_build_training_set")
 
 
 def pack_mlp_params(params) -> np.ndarray:

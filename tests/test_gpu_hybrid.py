@@ -1,0 +1,138 @@
+"""Sub-shower starts, the surrogate's training set, and the hybrid path
+(plain stepping above E_s, network deposits below it)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_2202_05012_gb300 import inputs
+from paper_2202_05012_gb300 import supa as S
+
+from gpu_helpers import compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+E_S = 1.0
+
+
+def _features_ref(prims, start, geom, e_s):
+    """The 6 network inputs written out from their definition: log(E/E_s),
+    direction cosines, position of the start slice in its layer, layers left
+    (over 30, capped at 1)."""
+    th = prims["theta"].astype(np.float64)
+    ph = prims["phi"].astype(np.float64)
+    lay = geom.slice_to_layer[start]
+    kfirst = np.array([np.nonzero(geom.slice_to_layer == l)[0].min() for l in lay])
+    nsl = np.array([np.count_nonzero(geom.slice_to_layer == l) for l in lay])
+    return np.stack([np.log(prims["E"].astype(np.float64) / e_s), np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph),
+                     np.cos(th), (start - kfirst) / nsl, np.minimum(1.0, (geom.n_layers - lay) / 30.0)], 1), lay
+
+
+def test_subshower_starts_match_oracle():
+    g = inputs.supa_d(30)
+    p, start = inputs.subshower_primaries(2000, 5, e_lo=0.05, e_hi=5.0)
+    compare(run_gpu([g], p, seed=3), oracle.simulate(g, p, 3, n_threads=8), [g], p)
+
+
+def test_training_set_matches_oracle_targets():
+    import torch
+    g = inputs.supa_d(30)
+    n = 4096
+    p, start = inputs.subshower_primaries(n, 6)
+    gh = S.supa_init_geometry(g)
+    b = S.supa_batch_create([gh], n, {})
+    try:
+        S.supa_simulate(b, S.primaries_to_device(p), n, 4)
+        S.supa_batch_get_info(b)
+        x = torch.zeros((n, 6), dtype=torch.float32, device="cuda")
+        y = torch.zeros((n, 30), dtype=torch.float32, device="cuda")
+        S.supa_build_training_set(b, E_S, x, y)
+        X, Y = x.cpu().numpy(), y.cpu().numpy()
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_destroy_geometry(gh)
+    Xr, lay = _features_ref(p, start, g, E_S)
+    np.testing.assert_allclose(X, Xr, rtol=1e-5, atol=1e-6)
+    ora = oracle.simulate(g, p, 4, n_threads=8)
+    Yr = np.zeros((n, 30))
+    for s in range(n):
+        m = min(30, g.n_layers - lay[s])
+        Yr[s, :m] = ora["layer_sum"][s, lay[s]:lay[s] + m] / float(p["E"][s])
+    same = np.abs(Y - Yr).max(1) < 1e-4
+    assert same.mean() > 0.999
+    np.testing.assert_allclose(Y[same], Yr[same], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(Y.sum(1), Yr.sum(1), atol=2e-3)
+
+
+def _surrogate(seed=1):
+    return S.supa_surrogate_create(1024, S.pack_mlp_params(inputs.mlp_init(seed)))
+
+
+def test_hybrid_conserves_energy_and_emits_after_stepped_hits():
+    import torch
+    g = inputs.supa_d(30, grid=64, roi_mode=inputs.ROI_AXIS)
+    n = 3000
+    p = inputs.primaries(n, 7, e_lo=5.0, e_hi=60.0, theta_max_deg=30.0)
+    gh = S.supa_init_geometry(g)
+    sur = _surrogate()
+    b = S.supa_batch_create([gh], n, {"record_tags": 1})
+    try:
+        S.supa_batch_set_surrogate(b, sur, E_S, 4_000_000)
+        d = S.primaries_to_device(p)
+        S.supa_simulate(b, d, n, 9)
+        info = S.supa_batch_get_info(b)
+        assert info.n_diverted > 0
+        arr = {k: v.cpu().numpy() for k, v in S.info_arrays(info).items()}
+        sleak = S.device_view(info.sur_leak_dev, (n,), torch.float64).cpu().numpy()
+        tot = arr["layer_sum"].sum(1) + arr["dead"] + arr["leak"] + arr["escape"] + sleak
+        np.testing.assert_allclose(tot, p["E"].astype(np.float64), rtol=1e-5)
+        hits = torch.zeros((info.n_hits, 4), dtype=torch.float32, device="cuda")
+        assert S.supa_fetch_hits(b, 0, info.n_hits, hits) == info.n_hits
+        h = hits.cpu().numpy().astype(np.float64)
+        sh = np.repeat(np.arange(n), np.diff(arr["offsets"]))
+        np.testing.assert_allclose(np.bincount(sh, weights=h[:, 3], minlength=n), arr["layer_sum"].sum(1), rtol=1e-5)
+        tags = torch.zeros(info.n_hits, dtype=torch.int64, device="cuda")
+        S.supa_fetch_hit_tags(b, 0, info.n_hits, tags)
+        t = tags.cpu().numpy()
+        assert (t == 0).sum() > 0 and (t != 0).sum() > 0  # surrogate hits carry tag 0
+        # within each shower the stepped hits come first
+        first_zero = np.array([np.argmax(t[a:c] == 0) if (t[a:c] == 0).any() else c - a
+                               for a, c in zip(arr["offsets"][:-1], arr["offsets"][1:])])
+        for s in range(0, n, 97):
+            seg = t[arr["offsets"][s]:arr["offsets"][s + 1]]
+            assert np.all(seg[first_zero[s]:] == 0)
+        grid = torch.zeros((n, 30, 64, 64), dtype=torch.float32, device="cuda")
+        oor = torch.zeros(n, dtype=torch.float64, device="cuda")
+        S.supa_voxelize(b, 0, n, grid, oor)
+        np.testing.assert_allclose(grid.double().sum((1, 2, 3)).cpu().numpy() + oor.cpu().numpy(),
+                                   arr["layer_sum"].sum(1), rtol=1e-4)
+        # replay gives the same showers
+        S.supa_simulate(b, d, n, 9)
+        info2 = S.supa_batch_get_info(b)
+        arr2 = {k: v.cpu().numpy() for k, v in S.info_arrays(info2).items()}
+        assert info2.n_hits == info.n_hits and info2.n_diverted == info.n_diverted
+        np.testing.assert_allclose(arr2["layer_sum"], arr["layer_sum"], rtol=1e-9, atol=1e-12)
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_surrogate_destroy(sur)
+        S.supa_destroy_geometry(gh)
+
+
+def test_hybrid_queue_overflow_is_an_error():
+    g = inputs.supa_d(30)
+    p = inputs.primaries(200, 8, e_lo=50.0, e_hi=60.0)
+    gh = S.supa_init_geometry(g)
+    sur = _surrogate()
+    b = S.supa_batch_create([gh], 200, {})
+    try:
+        S.supa_batch_set_surrogate(b, sur, E_S, 128)
+        S.supa_simulate(b, S.primaries_to_device(p), 200, 1)
+        with pytest.raises(S.SupaError) as ei:
+            S.supa_batch_get_info(b)
+        assert ei.value.code == S.SUPA_ERR_OVERFLOW
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_surrogate_destroy(sur)
+        S.supa_destroy_geometry(gh)
