@@ -51,6 +51,7 @@ class _Geom(ctypes.Structure):
         ("theta_mode", ctypes.c_int), ("theta_lo", ctypes.c_double), ("theta_hi", ctypes.c_double),
         ("eps_mode", ctypes.c_int), ("eps_frac", ctypes.c_double),
         ("split_mode", ctypes.c_int), ("e_min", ctypes.c_double), ("uz_min", ctypes.c_double),
+        ("e_s", ctypes.c_double),
     ]
 
 
@@ -74,6 +75,10 @@ class _Result(ctypes.Structure):
         ("layer_sum", _P(ctypes.c_double)), ("dead", _P(ctypes.c_double)), ("leak", _P(ctypes.c_double)),
         ("escape", _P(ctypes.c_double)), ("n_splits", _P(ctypes.c_int64)), ("max_depth", _P(ctypes.c_int32)),
         ("status", ctypes.c_int),
+        ("n_div", ctypes.c_int64), ("div_shower", _P(ctypes.c_int64)), ("div_k", _P(ctypes.c_int32)),
+        ("div_layer", _P(ctypes.c_int32)), ("div_x", _P(ctypes.c_double)), ("div_y", _P(ctypes.c_double)),
+        ("div_ux", _P(ctypes.c_double)), ("div_uy", _P(ctypes.c_double)), ("div_uz", _P(ctypes.c_double)),
+        ("div_E", _P(ctypes.c_double)), ("div_lin", _P(ctypes.c_uint64)),
     ]
 
 
@@ -110,16 +115,19 @@ def philox(ctr, key) -> np.ndarray:
     return np.array(list(o), dtype=np.uint32)
 
 
-def simulate(geom, prims: np.ndarray, seed: int, shower_id_base: int = 0, n_threads: int = 1) -> dict:
+def simulate(geom, prims: np.ndarray, seed: int, shower_id_base: int = 0, n_threads: int = 1,
+             e_s: float = 0.0) -> dict:
     """Run Algorithm 1 on every shower; returns numpy arrays (hits sorted per
-    shower by slice then lineage) and per-shower FP64 bookkeeping."""
+    shower by slice then lineage) and per-shower FP64 bookkeeping.  With
+    e_s > 0, particles below e_s on a readout slice are returned as the
+    'div' records (hybrid path) instead of being stepped."""
     s2l = np.ascontiguousarray(geom.slice_to_layer, dtype=np.int32)
     ps = np.ascontiguousarray(geom.p_stop, dtype=np.float64)
     pp = np.ascontiguousarray(geom.p_split, dtype=np.float64)
     g = _Geom(int(geom.n_slices), float(geom.dz), s2l.ctypes.data_as(_P(ctypes.c_int)), int(geom.n_layers),
               ps.ctypes.data_as(_P(ctypes.c_double)), pp.ctypes.data_as(_P(ctypes.c_double)),
               int(geom.theta_mode), float(geom.theta_lo), float(geom.theta_hi), int(geom.eps_mode),
-              float(geom.eps_frac), int(geom.split_mode), float(geom.e_min), float(geom.uz_min))
+              float(geom.eps_frac), int(geom.split_mode), float(geom.e_min), float(geom.uz_min), float(e_s))
     n = len(prims)
     assert ctypes.sizeof(_Primary) == _PRIMARY_NP.itemsize
     pr = np.zeros(max(n, 1), dtype=_PRIMARY_NP)
@@ -149,6 +157,13 @@ def simulate(geom, prims: np.ndarray, seed: int, shower_id_base: int = 0, n_thre
             escape=arr(res.escape, n, np.float64), n_splits=arr(res.n_splits, n, np.int64),
             max_depth=arr(res.max_depth, n, np.int32),
         )
+        nd = res.n_div
+        out["div"] = dict(
+            shower=arr(res.div_shower, nd, np.int64), k=arr(res.div_k, nd, np.int32),
+            layer=arr(res.div_layer, nd, np.int32), x=arr(res.div_x, nd, np.float64),
+            y=arr(res.div_y, nd, np.float64), ux=arr(res.div_ux, nd, np.float64), uy=arr(res.div_uy, nd, np.float64),
+            uz=arr(res.div_uz, nd, np.float64), E=arr(res.div_E, nd, np.float64),
+            lineage=arr(res.div_lin, nd, np.uint64))
     finally:
         lib().ora_free_result(ctypes.byref(res))
     return out

@@ -1,0 +1,81 @@
+"""FP64 oracle of the surrogate side of the hybrid path -- TEST INFRASTRUCTURE.
+
+The SUPA paper has no surrogate; this follows the library's stated rule for
+it.  For every particle set aside below E_s (oracle.simulate(..., e_s=...)
+returns them):
+  1. features: log(E / E_s), direction cosines, position of the slice in its
+     layer (k - first slice) / slices in the layer, layers left from the
+     particle's layer to the back over 30 (capped at 1);
+  2. the FP64 network (oracle.mlp) gives mu_j and s_j, j = 0..29;
+  3. n_j: standard normals by Box-Muller from Philox4x32-10 blocks with
+     counter (shower id, slice | 1 << 16 | block << 20, lineage lo, lineage
+     hi), block = 0..7, key = seed; from each block's words (w0, w1, w2, w3)
+     the pairs (w0, w1) and (w2, w3) give u1 = ((w >> 8) + 1) 2^-24 and
+     u2 = (w >> 8) 2^-24, z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2);
+  4. d_j = E max(0, mu_j + exp(s_j / 2) n_j) for layers inside the
+     detector, scaled by E / sum d when the sum exceeds E;
+  5. one hit per layer with d_j > 0 at the straight-line position at the
+     layer's mid depth.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import mlp, philox
+
+
+def features(div: dict, geom, e_s: float) -> np.ndarray:
+    s2l = np.asarray(geom.slice_to_layer)
+    L = int(geom.n_layers)
+    first = np.array([np.nonzero(s2l == l)[0].min() for l in range(L)])
+    count = np.array([np.count_nonzero(s2l == l) for l in range(L)])
+    lay = div["layer"]
+    return np.stack([np.log(div["E"] / e_s), div["ux"], div["uy"], div["uz"],
+                     (div["k"] - first[lay]) / count[lay], np.minimum(1.0, (L - lay) / 30.0)], 1)
+
+
+def normals(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    z = []
+    for blk in range(8):
+        w = philox(((shower_id) & 0xFFFFFFFF, k | (1 << 16) | (blk << 20), lineage & 0xFFFFFFFF,
+                    (lineage >> 32) & 0xFFFFFFFF), key)
+        for p in range(2):
+            u1 = ((int(w[2 * p]) >> 8) + 1) * 2.0 ** -24
+            u2 = (int(w[2 * p + 1]) >> 8) * 2.0 ** -24
+            rad = math.sqrt(-2.0 * math.log(u1))
+            z.append(rad * math.cos(2 * math.pi * u2))
+            z.append(rad * math.sin(2 * math.pi * u2))
+    return np.array(z)
+
+
+def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int = 0) -> dict:
+    """Per diverted particle: the drawn deposits d [n_div, 30] and the hits."""
+    X = features(div, geom, e_s)
+    out, _ = mlp.forward(params, X) if len(X) else (np.zeros((0, 60)), None)
+    L = int(geom.n_layers)
+    s2l = np.asarray(geom.slice_to_layer)
+    zmid = np.array([geom.dz * (np.nonzero(s2l == l)[0].min() + np.nonzero(s2l == l)[0].max()) * 0.5
+                     for l in range(L)])
+    nd = len(X)
+    d = np.zeros((nd, 30))
+    hits = []
+    for i in range(nd):
+        n = normals(shower_id_base + int(div["shower"][i]), int(div["k"][i]), int(div["lineage"][i]), seed)
+        l0 = int(div["layer"][i])
+        E = div["E"][i]
+        for j in range(30):
+            if l0 + j < L:
+                d[i, j] = E * max(0.0, out[i, j] + math.exp(0.5 * out[i, 30 + j]) * n[j])
+        tot = d[i].sum()
+        if tot > E:
+            d[i] *= E / tot
+        zk = div["k"][i] * geom.dz
+        for j in range(30):
+            if d[i, j] > 0:
+                zm = zmid[l0 + j]
+                hits.append((int(div["shower"][i]), div["x"][i] + (zm - zk) * div["ux"][i] / div["uz"][i],
+                             div["y"][i] + (zm - zk) * div["uy"][i] / div["uz"][i], zm, d[i, j], l0 + j))
+    return dict(d=d, out=out, hits=np.array(hits).reshape(-1, 6))

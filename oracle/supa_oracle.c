@@ -89,7 +89,19 @@ typedef struct {
 typedef struct {
     hit_t *hits; int64_t n_hits, cap_hits;
     particle_t *stack; int64_t n_stack, cap_stack;
+    particle_t *div; int64_t n_div, cap_div;  /* hybrid path: set aside */
 } work_t;
+
+static int push_div(work_t *w, particle_t q) {
+    if (w->n_div == w->cap_div) {
+        int64_t nc = w->cap_div ? 2 * w->cap_div : 64;
+        particle_t *p = (particle_t *)realloc(w->div, (size_t)nc * sizeof(particle_t));
+        if (!p) return -1;
+        w->div = p; w->cap_div = nc;
+    }
+    w->div[w->n_div++] = q;
+    return 0;
+}
 
 static int push_hit(work_t *w, hit_t h) {
     if (w->n_hits == w->cap_hits) {
@@ -152,7 +164,7 @@ static int survive(const ora_geom *g, work_t *w, particle_t q, shower_acc_t *acc
 static int simulate_one(const ora_geom *g, const ora_primary *p, uint64_t seed,
                         uint64_t shower_id, work_t *w, shower_acc_t *acc) {
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    w->n_hits = 0; w->n_stack = 0;
+    w->n_hits = 0; w->n_stack = 0; w->n_div = 0;
     memset(acc->layer_sum, 0, sizeof(double) * (size_t)g->n_layers);
     acc->steps = 0; acc->n_splits = 0; acc->max_depth = 0;
     acc->dead = acc->leak = acc->escape = 0.0;
@@ -171,6 +183,13 @@ static int simulate_one(const ora_geom *g, const ora_primary *p, uint64_t seed,
     while (w->n_stack > 0) {
         particle_t q = w->stack[--w->n_stack];
         const int k = q.slice;
+        /* Hybrid path: below e_s on a readout slice the particle is set
+         * aside for the surrogate instead of being stepped (float32
+         * comparison, the kernel's precision). */
+        if (g->e_s > 0.0 && (float)q.E < (float)g->e_s && g->slice_to_layer[k] >= 0) {
+            if (push_div(w, q)) return -1;
+            continue;
+        }
         acc->steps += 1;
 
         /* Algorithm 1: draw theta, eps, alpha (and omega) for (shower, slice, lineage). */
@@ -236,6 +255,8 @@ void ora_free_result(ora_result *r) {
     free(r->hit_offset); free(r->steps); free(r->layer_sum);
     free(r->dead); free(r->leak); free(r->escape);
     free(r->n_splits); free(r->max_depth);
+    free(r->div_shower); free(r->div_k); free(r->div_layer); free(r->div_x); free(r->div_y);
+    free(r->div_ux); free(r->div_uy); free(r->div_uz); free(r->div_E); free(r->div_lin);
     memset(r, 0, sizeof(*r));
 }
 
@@ -254,9 +275,11 @@ int ora_simulate(const ora_geom *g, const ora_primary *prim, int64_t n,
     out->n_splits = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     out->max_depth = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
     hit_t **per_shower = (hit_t **)calloc((size_t)n + 1, sizeof(hit_t *));
+    particle_t **per_div = (particle_t **)calloc((size_t)n + 1, sizeof(particle_t *));
+    int64_t *div_count = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     if (!out->hit_offset || !out->steps || !out->layer_sum || !out->dead || !out->leak ||
-        !out->escape || !out->n_splits || !out->max_depth || !per_shower) {
-        free(per_shower); ora_free_result(out); return -1;
+        !out->escape || !out->n_splits || !out->max_depth || !per_shower || !per_div || !div_count) {
+        free(per_shower); free(per_div); free(div_count); ora_free_result(out); return -1;
     }
     int failed = 0;
     if (n_threads < 1) n_threads = 1;
@@ -283,9 +306,45 @@ int ora_simulate(const ora_geom *g, const ora_primary *prim, int64_t n,
             per_shower[s] = (hit_t *)malloc(sizeof(hit_t) * (size_t)(w.n_hits + 1));
             if (!per_shower[s]) { failed = 1; continue; }
             memcpy(per_shower[s], w.hits, sizeof(hit_t) * (size_t)w.n_hits);
+            div_count[s] = w.n_div;
+            if (w.n_div) {
+                per_div[s] = (particle_t *)malloc(sizeof(particle_t) * (size_t)w.n_div);
+                if (!per_div[s]) { failed = 1; continue; }
+                memcpy(per_div[s], w.div, sizeof(particle_t) * (size_t)w.n_div);
+            }
         }
-        free(acc.layer_sum); free(w.hits); free(w.stack);
+        free(acc.layer_sum); free(w.hits); free(w.stack); free(w.div);
     }
+    if (!failed) {
+        int64_t nd = 0;
+        for (int64_t s = 0; s < n; ++s) nd += div_count[s];
+        out->n_div = nd;
+        out->div_shower = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nd + 1));
+        out->div_k = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nd + 1));
+        out->div_layer = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nd + 1));
+        out->div_x = (double *)malloc(sizeof(double) * (size_t)(nd + 1));
+        out->div_y = (double *)malloc(sizeof(double) * (size_t)(nd + 1));
+        out->div_ux = (double *)malloc(sizeof(double) * (size_t)(nd + 1));
+        out->div_uy = (double *)malloc(sizeof(double) * (size_t)(nd + 1));
+        out->div_uz = (double *)malloc(sizeof(double) * (size_t)(nd + 1));
+        out->div_E = (double *)malloc(sizeof(double) * (size_t)(nd + 1));
+        out->div_lin = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nd + 1));
+        if (!out->div_shower || !out->div_k || !out->div_layer || !out->div_x || !out->div_y || !out->div_ux ||
+            !out->div_uy || !out->div_uz || !out->div_E || !out->div_lin) failed = 1;
+        int64_t j = 0;
+        for (int64_t s = 0; s < n && !failed; ++s) {
+            for (int64_t i = 0; i < div_count[s]; ++i, ++j) {
+                const particle_t *q = &per_div[s][i];
+                out->div_shower[j] = s; out->div_k[j] = q->slice;
+                out->div_layer[j] = g->slice_to_layer[q->slice];
+                out->div_x[j] = q->x; out->div_y[j] = q->y;
+                out->div_ux[j] = q->ux; out->div_uy[j] = q->uy; out->div_uz[j] = q->uz;
+                out->div_E[j] = q->E; out->div_lin[j] = q->lineage;
+            }
+        }
+    }
+    for (int64_t s = 0; s < n; ++s) free(per_div[s]);
+    free(per_div); free(div_count);
     if (!failed) {
         for (int64_t s = 0; s < n; ++s) out->hit_offset[s + 1] += out->hit_offset[s];
         const int64_t nh = out->hit_offset[n];

@@ -41,6 +41,9 @@ typedef struct {
     int split_mode;             /* MOMENTUM (default) or LITERAL reading   */
     double e_min;               /* energy cut (0 = none)                   */
     double uz_min;              /* escape cut on the z direction cosine    */
+    double e_s;                 /* hybrid path: a particle below e_s on a  */
+                                /* readout slice is set aside, not stepped */
+                                /* (0 = plain path)                        */
 } ora_geom;
 
 /* One primary: initial energy, impact position and incidence angles
@@ -66,6 +69,12 @@ typedef struct {
     int64_t *n_splits;
     int32_t *max_depth;         /* splits on the deepest lineage */
     int status;                 /* 0 ok, <0 error */
+    /* hybrid path: particles set aside, in shower order */
+    int64_t n_div;
+    int64_t *div_shower;
+    int32_t *div_k, *div_layer;
+    double *div_x, *div_y, *div_ux, *div_uy, *div_uz, *div_E;
+    uint64_t *div_lin;
 } ora_result;
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ctr[4], key[2] -> out[4]. */

@@ -59,7 +59,7 @@ def compare(gpu, ora, geoms, prims, pos_rtol=RTOL):
     FP32 error e in the direction becomes e / u_z in the slope: near grazing
     incidence (u_z down to the escape cut) callers pass a looser bound."""
     n = len(prims)
-    gidx = prims["geom"].astype(np.int64)
+    gidx = prims["geom"].astype(np.int64) & 0xFFFF  # high bits: start slice
     dz = np.array([geoms[i].dz for i in gidx])
     # canonical order within each shower: (slice, lineage)
     g_sh = _shower_ids(gpu["offsets"])

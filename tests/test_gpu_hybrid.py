@@ -120,6 +120,61 @@ def test_hybrid_conserves_energy_and_emits_after_stepped_hits():
         S.supa_destroy_geometry(gh)
 
 
+def test_hybrid_matches_oracle():
+    """Same set-aside decisions and stepped hits as the FP64 oracle; the
+    network's deposits agree within BF16 tolerance (per shower, per layer)."""
+    import torch
+    from oracle import hybrid
+    g = inputs.supa_d(30, grid=64, roi_mode=inputs.ROI_AXIS)
+    n = 300
+    p = inputs.primaries(n, 11, e_lo=5.0, e_hi=60.0, theta_max_deg=30.0)
+    vec = S.pack_mlp_params(inputs.mlp_init(3))
+    params64 = [(W.astype(np.float64), b.astype(np.float64)) for W, b in S.unpack_mlp_params(vec)]
+    gh = S.supa_init_geometry(g)
+    sur = S.supa_surrogate_create(1024, vec)
+    b = S.supa_batch_create([gh], n, {"record_tags": 1})
+    try:
+        S.supa_batch_set_surrogate(b, sur, E_S, 1_000_000)
+        S.supa_simulate(b, S.primaries_to_device(p), n, 13)
+        info = S.supa_batch_get_info(b)
+        arr = {k: v.cpu().numpy() for k, v in S.info_arrays(info).items()}
+        hits = torch.zeros((info.n_hits, 4), dtype=torch.float32, device="cuda")
+        tags = torch.zeros(info.n_hits, dtype=torch.int64, device="cuda")
+        S.supa_fetch_hits(b, 0, info.n_hits, hits)
+        S.supa_fetch_hit_tags(b, 0, info.n_hits, tags)
+        h, t = hits.cpu().numpy(), tags.cpu().numpy().view(np.uint64)
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_surrogate_destroy(sur)
+        S.supa_destroy_geometry(gh)
+    ora = oracle.simulate(g, p, 13, n_threads=8, e_s=E_S)
+    div = ora["div"]
+    dep = hybrid.deposits(div, params64, g, E_S, 13)
+    # the same particles are set aside (float32 decisions on both sides)
+    assert abs(info.n_diverted - len(div["E"])) <= max(2, 1e-3 * len(div["E"]))
+    # stepped hits: same (slice, lineage) keys per shower
+    sh = np.repeat(np.arange(n), np.diff(arr["offsets"]))
+    stepped = t != 0
+    same = 0
+    for s in range(n):
+        m = (sh == s) & stepped
+        a = sorted(zip(np.rint(h[m, 2]).astype(int).tolist(), t[m].tolist()))
+        o = ora["offsets"]
+        bkeys = sorted(zip(ora["slice"][o[s]:o[s + 1]].tolist(), ora["lineage"][o[s]:o[s + 1]].tolist()))
+        same += a == bkeys
+    assert same >= n - 2
+    # layer sums: oracle stepped part + network deposits
+    ls = ora["layer_sum"].copy()
+    for j in range(30):
+        ok = div["layer"] + j < g.n_layers
+        np.add.at(ls, (div["shower"][ok], div["layer"][ok] + j), dep["d"][ok, j])
+    E0 = p["E"].astype(np.float64)
+    err = np.abs(arr["layer_sum"] - ls).sum(1) / E0
+    assert np.quantile(err, 0.99) < 3e-2, np.quantile(err, 0.99)
+    np.testing.assert_allclose(arr["layer_sum"].sum(1), ls.sum(1), rtol=2e-2)
+    assert abs((~stepped).sum() - len(dep["hits"])) <= 0.03 * len(dep["hits"])
+
+
 def test_hybrid_queue_overflow_is_an_error():
     g = inputs.supa_d(30)
     p = inputs.primaries(200, 8, e_lo=50.0, e_hi=60.0)
