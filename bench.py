@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-hybrid", action="store_true", help="skip the plain-vs-surrogate comparison")
+    ap.add_argument("--e-s", type=float, default=1.0, help="surrogate cutoff energy E_s")
+    ap.add_argument("--train-samples", type=int, default=2_000_000)
+    ap.add_argument("--epochs", type=int, default=5)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--pipeline", type=int, default=1,
                     help="sub-batches per step; >1 overlaps simulation of one with downsampling of the previous")
     return ap.parse_args()
@@ -532,6 +537,10 @@ def run_supa_serial(args):
 
     if not args.no_e2e:
         out["e2e"] = e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world)
+    if world == 1 and args.workload == "c2" and not args.no_hybrid:
+        plain = {"step_ms": elapsed_ms / args.steps, "simulate_ms": sim_ms, "steps": n_steps,
+                 "profiles": profiles_of(S, b, n, L)}
+        out["hybrid"] = hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor, fbuf, plain)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sps, done, dt, threads = oracle_sample(geom, prims, seed, args.cpu_seconds)
         out["cpu_baseline"] = {"value": v, "unit": "showers/s", "cores": threads, "kind": "oracle",
@@ -544,6 +553,104 @@ def run_supa_serial(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+PROFILE_BINS, PROFILE_RMAX = 64, 8.0
+
+
+def profiles_of(S, b, n, L):
+    """Mean longitudinal (per-layer energy / E0) and lateral (energy / E0 per
+    0.125-wide ring around the incidence axis) profiles of the batch."""
+    import torch
+    lo = torch.zeros(L, dtype=torch.float64, device="cuda")
+    la = torch.zeros(PROFILE_BINS, dtype=torch.float64, device="cuda")
+    S.supa_profiles(b, 0, n, PROFILE_BINS, PROFILE_RMAX, lo, la)
+    return lo.cpu().numpy() / n, la.cpu().numpy() / n
+
+
+def profile_errors(ref, got, thr=0.005):
+    """Largest relative deviation over profile bins holding >= thr of the
+    energy, and the relative deviation of the mean total deposit."""
+    (rl, rr), (gl, gr) = ref, got
+
+    def err(a, b):
+        m = a >= thr
+        return float(np.max(np.abs(b[m] - a[m]) / a[m]))
+
+    return {"longitudinal": err(rl, gl), "lateral": err(rr, gr),
+            "total_deposit": float(abs(gl.sum() - rl.sum()) / rl.sum()), "bin_threshold": thr}
+
+
+def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor, fbuf, L, profiles=False):
+    """The whole path in hybrid mode over n showers in sub-batches: simulate
+    (stepping above E_s, network below), downsample, fetch.  Returns timings
+    and (optionally) accumulated profiles."""
+    import torch
+    mean_e = float(prims["E"].mean())
+    cap = int(4.0 * mean_e / e_s * sub) + (1 << 20)
+    hb = S.supa_batch_create([gh], sub, {"max_hits": int(sub * max(400, 40 * mean_e)) + (8 << 20), "lpt_order": 1})
+    S.supa_batch_set_surrogate(hb, net, e_s, cap)
+    lo = torch.zeros(L, dtype=torch.float64, device="cuda")
+    la = torch.zeros(PROFILE_BINS, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    sim_ms = 0.0
+    steps = diverted = hits = 0
+    FC = fbuf.shape[0]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for j in range(0, n, sub):
+        m = min(sub, n - j)
+        ev[2].record(stream)
+        S.supa_simulate(hb, d_prim[j * 24:(j + m) * 24], m, seed, base + j)
+        ev[3].record(stream)
+        info = S.supa_batch_get_info(hb)
+        sim_ms += ev[2].elapsed_time(ev[3])
+        steps += info.n_steps
+        diverted += info.n_diverted
+        hits += info.n_hits
+        for c0 in range(0, m, V):
+            S.supa_voxelize(hb, c0, min(m, c0 + V), grid, oor)
+        for h0 in range(0, info.n_hits, FC):
+            S.supa_fetch_hits(hb, h0, FC, fbuf)
+        if profiles:
+            S.supa_profiles(hb, 0, m, PROFILE_BINS, PROFILE_RMAX, lo, la)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = ev[0].elapsed_time(ev[1])
+    S.supa_destroy_batch(hb)
+    out = dict(total_ms=total_ms, simulate_ms=sim_ms, steps=steps, diverted=diverted, hits=hits, queue_capacity=cap)
+    if profiles:
+        out["profiles"] = (lo.cpu().numpy() / n, la.cpu().numpy() / n)
+    return out
+
+
+def hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor, fbuf, plain):
+    """Train the surrogate on plain-method sub-showers, run the same showers
+    in hybrid mode, and compare throughput and profiles with the plain run."""
+    from paper_2202_05012_gb300 import surrogate_train as T
+    data = T.training_set(args.train_samples, args.e_s, seed=3, n_layers=geom.n_layers)
+    net, log = T.train(data, epochs=args.epochs, lr=args.lr)
+    gen_s = data["seconds"]
+    del data
+    sub = 125_000
+    L = geom.n_layers
+    hybrid_run(S, gh, prims, d_prim, min(n, sub), seed, base, net, args.e_s, sub, V, grid, oor, fbuf, L)  # warm-up
+    prof = hybrid_run(S, gh, prims, d_prim, n, seed, base, net, args.e_s, sub, V, grid, oor, fbuf, L, True)
+    timed = hybrid_run(S, gh, prims, d_prim, n, seed, base, net, args.e_s, sub, V, grid, oor, fbuf, L)
+    S.supa_surrogate_destroy(net)
+    errs = profile_errors(plain["profiles"], prof["profiles"])
+    return {
+        "e_s": args.e_s, "showers_per_s": n / (timed["total_ms"] / 1000.0),
+        "plain_showers_per_s": n / (plain["step_ms"] / 1000.0),
+        "simulate_showers_per_s": n / (timed["simulate_ms"] / 1000.0),
+        "plain_simulate_showers_per_s": n / (plain["simulate_ms"] / 1000.0),
+        "particle_steps_per_shower": timed["steps"] / n, "plain_particle_steps_per_shower": plain["steps"] / n,
+        "diverted_per_shower": timed["diverted"] / n, "profile_error": errs,
+        "profile_binning": {"lateral_bins": PROFILE_BINS, "r_max": PROFILE_RMAX},
+        "training": {"samples": args.train_samples, "data_seconds": gen_s, **log},
+        "note": "hybrid timed in 125k-shower sub-batches (network over each sub-batch's queue); plain as one batch",
+    }
 
 
 def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):

@@ -207,6 +207,16 @@ int supa_fetch_hit_tags(supa_batch *b, int64_t first_hit, int64_t max_hits, uint
 int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev,
                   double *out_of_roi_dev, void *stream);
 
+/* Shower-shape profiles of showers [shower_begin, shower_end), added to the
+ * caller's FP64 accumulators (Sec. 5.1 layer energies; lateral spread):
+ * longi_dev[l] += layer energy / E0 per shower (max_layers entries);
+ * lat_dev[b] += hit energy / E0 for hits at transverse distance r from the
+ * incidence axis through the impact point, b = floor(r / r_max * nbins),
+ * the last bin collecting r >= r_max (nbins entries, 1..4096).
+ * Asynchronous. */
+int supa_profiles(supa_batch *b, int64_t shower_begin, int64_t shower_end, int32_t nbins, float r_max,
+                  double *longi_dev, double *lat_dev, void *stream);
+
 /* Downsample caller-provided hits: hits_dev float4 (x,y,z,E), shower s owns
  * hits [offsets_dev[s], offsets_dev[s+1]); a hit's layer is
  * slice_to_layer[rint(z/dz)] of geometry g; roi_x0_dev/roi_y0_dev are the low

@@ -307,6 +307,50 @@ cudaError_t launch_fetch(const FetchParams &p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ profiles ---
+// Shower-shape profiles summed over a range of showers (Sec. 5.1 "layer
+// energy"; lateral spread around the shower axis):
+//   longi[l] += layer_sum[s][l] / E0_s
+//   lat[b]   += E_hit / E0_s for hits whose transverse distance r from the
+//               incidence axis through the impact point (at the hit's depth)
+//               falls in bin b = floor(r / r_max * nbins) (last bin: overflow).
+// One CTA per shower; FP32 shared-memory bins, FP64 global sums.
+__global__ void __launch_bounds__(256) supa_profile_kernel(const ProfileParams p) {
+    extern __shared__ float pbins[];
+    const int64_t srel = blockIdx.x;
+    const int64_t s = p.s_begin + srel;
+    for (int i = threadIdx.x; i < p.nbins; i += blockDim.x) pbins[i] = 0.0f;
+    __syncthreads();
+    const supa_primary pr = p.prim[s];
+    const double inv = 1.0 / (double)pr.E;
+    for (int l = threadIdx.x; l < p.L; l += blockDim.x)
+        atomicAdd(&p.longi[l], p.lsum[(size_t)s * p.L + l] * inv);
+    const float t = tanf(pr.theta);
+    const float tx = t * cosf(pr.phi), ty = t * sinf(pr.phi);
+    const float scale = (float)p.nbins / p.r_max;
+    ShowerHits it;
+    it.init(p.src, s);
+    if (it.remaining > 0) {
+        do {
+            for (int j = threadIdx.x; j < it.seg_len; j += blockDim.x) {
+                const float4 h = __ldg(it.seg_ptr + j);
+                const float r = hypotf(h.x - fmaf(h.z, tx, pr.x0), h.y - fmaf(h.z, ty, pr.y0));
+                const int b = min((int)(r * scale), p.nbins - 1);
+                atomicAdd(&pbins[b], h.w);
+            }
+        } while (it.next());
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.nbins; i += blockDim.x)
+        if (pbins[i] != 0.0f) atomicAdd(&p.lat[i], (double)pbins[i] * inv);
+}
+
+cudaError_t launch_profiles(const ProfileParams &p, cudaStream_t st) {
+    if (p.n_showers <= 0) return cudaSuccess;
+    supa_profile_kernel<<<(unsigned)p.n_showers, 256, p.nbins * sizeof(float), st>>>(p);
+    return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- scan ---
 // Exclusive scan of per-shower hit counts into int64 offsets [n+1]:
 // per-block totals, a single-block scan of the totals, then the final pass.

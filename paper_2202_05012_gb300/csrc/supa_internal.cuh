@@ -218,6 +218,17 @@ size_t vox_smem_bytes(int G, int nx, int ny, int list_cap);
 // Layers per group, group count and hit-list capacity for an L x ny x nx image.
 void vox_plan(int L, int nx, int ny, int *G, int *n_groups, int *list_cap);
 
+struct ProfileParams {
+    HitSource src;
+    const supa_primary *prim;
+    const double *lsum;  // [n][L]
+    int64_t s_begin, n_showers;
+    int L, nbins;
+    float r_max;
+    double *longi, *lat;
+};
+cudaError_t launch_profiles(const ProfileParams &p, cudaStream_t st);
+
 struct FetchParams {
     HitSource src;
     const unsigned long long *tag_pool;  // fetch tags instead of hits when non-null

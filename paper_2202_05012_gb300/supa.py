@@ -29,7 +29,7 @@ EXPORTED = (
     "supa_voxelize", "supa_voxelize_hits", "supa_autotune", "supa_surrogate_param_count", "supa_surrogate_create",
     "supa_surrogate_destroy", "supa_surrogate_get_params", "supa_surrogate_gradients", "supa_surrogate_train_step",
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
-    "supa_build_training_set",
+    "supa_build_training_set", "supa_profiles",
 )
 
 
@@ -116,6 +116,7 @@ def lib(build_if_missing: bool = True):
         L.supa_surrogate_train_epoch.argtypes = [_VP, _VP, _VP, _I64, ctypes.c_uint64, ctypes.c_float, _VP, _VP]
         L.supa_batch_set_surrogate.argtypes = [_VP, _VP, ctypes.c_float, _I64]
         L.supa_build_training_set.argtypes = [_VP, ctypes.c_float, _VP, _VP, _VP]
+        L.supa_profiles.argtypes = [_VP, _I64, _I64, ctypes.c_int32, ctypes.c_float, _VP, _VP, _VP]
         for name in EXPORTED[1:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -309,6 +310,12 @@ def supa_surrogate_train_epoch(s: int, x_dev, y_dev, n: int, seed: int, lr: floa
 
 def supa_batch_set_surrogate(b: int, s: int | None, e_s: float, queue_capacity: int):
     _check(lib().supa_batch_set_surrogate(b, s, float(e_s), int(queue_capacity)), "supa_batch_set_surrogate")
+
+
+def supa_profiles(b: int, shower_begin: int, shower_end: int, nbins: int, r_max: float, longi_dev, lat_dev,
+                  stream=None):
+    _check(lib().supa_profiles(b, int(shower_begin), int(shower_end), int(nbins), float(r_max), _ptr(longi_dev),
+                               _ptr(lat_dev), _stream(stream)), "supa_profiles")
 
 
 def supa_build_training_set(b: int, e_s: float, x_dev, y_dev, stream=None):

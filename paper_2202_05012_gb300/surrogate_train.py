@@ -1,0 +1,78 @@
+"""Surrogate workflow on top of the C ABI (orchestration only: every step
+runs in the library's kernels).
+
+  data = training_set(n, e_s, seed)            # plain-method sub-showers
+  net, log = train(data, epochs, batch, lr)    # tcgen05 training epochs
+  ... supa_batch_set_surrogate(batch, net, e_s, capacity) ...
+
+Sub-showers start below E_s (energy log-uniform in [e_min, E_s], polar angle
+U[0, 45 deg], start layer uniform, start slice uniform within it) in the
+30-layer detector; targets are their per-layer deposit fractions from the
+start layer on.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import inputs
+from . import supa as S
+
+# Algorithmic FLOPs per sample of one training step of 6-256-256-256-60:
+# forward 2 * sum(in * out), backward twice that (data and weight gradients,
+# minus the unused input gradient of the first layer).
+_LAYERS = [(6, 256), (256, 256), (256, 256), (256, 60)]
+FWD_FLOPS = sum(2 * a * b for a, b in _LAYERS)
+TRAIN_FLOPS = FWD_FLOPS + 2 * FWD_FLOPS - 2 * 6 * 256
+
+
+def training_set(n: int, e_s: float, seed: int, n_layers: int = 30, device="cuda"):
+    """Simulate n sub-showers with the plain kernel and build (X, Y) on the GPU."""
+    import torch
+    g = inputs.supa_d(n_layers)
+    prims, _ = inputs.subshower_primaries(n, seed, e_lo=g.e_min, e_hi=e_s, n_layers=n_layers)
+    gh = S.supa_init_geometry(g)
+    b = S.supa_batch_create([gh], n, {"max_hits": n * 80 + (4 << 20), "lpt_order": 1})
+    try:
+        d = S.primaries_to_device(prims, device)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.supa_simulate(b, d, n, seed)
+        info = S.supa_batch_get_info(b)
+        x = torch.empty((n, 6), dtype=torch.float32, device=device)
+        y = torch.empty((n, 30), dtype=torch.float32, device=device)
+        S.supa_build_training_set(b, e_s, x, y)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return dict(x=x, y=y, n=n, e_s=e_s, seconds=dt, steps=info.n_steps)
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_destroy_geometry(gh)
+
+
+def train(data: dict, epochs: int = 20, batch: int = 16384, lr: float = 1e-3, seed: int = 0, init_seed: int = 1):
+    """Adam epochs on the GPU; returns (network handle, log)."""
+    import torch
+    net = S.supa_surrogate_create(batch, S.pack_mlp_params(inputs.mlp_init(init_seed)))
+    n = data["n"]
+    steps = n // batch
+    losses = []
+    acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for ep in range(epochs):
+        acc.zero_()
+        S.supa_surrogate_train_epoch(net, data["x"], data["y"], n, seed * 1000 + ep, lr, acc)
+        losses.append(acc)  # read after the loop (no synchronisation per epoch)
+        acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ev1.record()
+    torch.cuda.synchronize()
+    S.supa_surrogate_check(net)
+    ms = ev0.elapsed_time(ev1)
+    per_epoch = [float(l.item()) / steps for l in losses]
+    flops = TRAIN_FLOPS * steps * batch * epochs
+    return net, dict(epochs=epochs, batch=batch, lr=lr, steps_per_epoch=steps, seconds=ms / 1000.0,
+                     seconds_per_epoch=ms / 1000.0 / epochs, loss_per_epoch=per_epoch,
+                     tflops=flops / (ms / 1000.0) / 1e12, samples_per_s=steps * batch * epochs / (ms / 1000.0))

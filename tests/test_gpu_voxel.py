@@ -91,6 +91,40 @@ def test_batch_voxelize_matches_oracle_and_conserves():
         S.supa_destroy_geometry(gh)
 
 
+def test_profiles_match_oracle():
+    """Longitudinal (layer energy / E0) and lateral (energy / E0 in rings
+    around the incidence axis) profiles against the same sums over the
+    oracle's showers."""
+    import torch
+    g = inputs.supa_d(30, grid=64, roi_mode=inputs.ROI_AXIS)
+    n = 500
+    p = inputs.primaries(n, 41, e_lo=1.0, e_hi=50.0, theta_max_deg=30.0, entry_halfwidth=0.25)
+    gh = S.supa_init_geometry(g)
+    b = S.supa_batch_create([gh], n, {})
+    try:
+        S.supa_simulate(b, S.primaries_to_device(p), n, 21)
+        S.supa_batch_get_info(b)
+        lo = torch.zeros(30, dtype=torch.float64, device="cuda")
+        la = torch.zeros(64, dtype=torch.float64, device="cuda")
+        S.supa_profiles(b, 0, n, 64, 8.0, lo, la)
+        lo, la = lo.cpu().numpy(), la.cpu().numpy()
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_destroy_geometry(gh)
+    ora = oracle.simulate(g, p, 21, n_threads=8)
+    E0 = p["E"].astype(np.float64)
+    np.testing.assert_allclose(lo, (ora["layer_sum"] / E0[:, None]).sum(0), rtol=1e-4, atol=1e-6)
+    sh = np.repeat(np.arange(n), np.diff(ora["offsets"]))
+    th, ph = p["theta"].astype(np.float64)[sh], p["phi"].astype(np.float64)[sh]
+    ax = p["x0"].astype(np.float64)[sh] + ora["z"] * np.tan(th) * np.cos(ph)
+    ay = p["y0"].astype(np.float64)[sh] + ora["z"] * np.tan(th) * np.sin(ph)
+    r = np.hypot(ora["x"] - ax, ora["y"] - ay)
+    bins = np.minimum((r * 8.0).astype(int), 63)
+    ref = np.bincount(bins, weights=ora["E"] / E0[sh], minlength=64)
+    np.testing.assert_allclose(la, ref, rtol=2e-3, atol=1e-3)
+    np.testing.assert_allclose(la.sum(), ref.sum(), rtol=1e-5)
+
+
 def test_voxelize_rejects_bad_ranges():
     import torch
     g = inputs.supa_d(3)
