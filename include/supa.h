@@ -217,6 +217,22 @@ int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float
 int supa_profiles(supa_batch *b, int64_t shower_begin, int64_t shower_end, int32_t nbins, float r_max,
                   double *longi_dev, double *lat_dev, void *stream);
 
+/* First-hit offsets of every shower from per-shower hit counts, without
+ * allocating anything (the paper has no counterpart; this serves callers
+ * that may not call cudaMalloc, e.g. code running under a host framework
+ * whose memory pool owns every allocation, or code on a path that must not
+ * wait on the allocator).  offsets_dev[0] = 0, offsets_dev[s+1] =
+ * offsets_dev[s] + counts_dev[s] for s < n (int64, n + 1 entries): the scan
+ * supa_simulate runs after each simulation.  Its scratch is a fixed 32 KiB
+ * array inside the library's device image, present on every GPU that loads
+ * the library until the process exits; n may be at most 16,769,024
+ * (larger n: SUPA_ERR_INVALID_ARG, nothing launched).  The first call on a
+ * device looks up the array's device address, so make that first call
+ * before capturing a stream into a graph.  All calls share the one array:
+ * calls that overlap on the GPU (different streams, or different threads
+ * without ordering) race and give wrong offsets.  Asynchronous on stream. */
+int supa_shower_offsets_noalloc(const uint32_t *counts_dev, int64_t n, int64_t *offsets_dev, void *stream);
+
 /* Downsample caller-provided hits: hits_dev float4 (x,y,z,E), shower s owns
  * hits [offsets_dev[s], offsets_dev[s+1]); a hit's layer is
  * slice_to_layer[rint(z/dz)] of geometry g; roi_x0_dev/roi_y0_dev are the low

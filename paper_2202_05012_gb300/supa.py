@@ -29,7 +29,7 @@ EXPORTED = (
     "supa_voxelize", "supa_voxelize_hits", "supa_autotune", "supa_surrogate_param_count", "supa_surrogate_create",
     "supa_surrogate_destroy", "supa_surrogate_get_params", "supa_surrogate_gradients", "supa_surrogate_train_step",
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
-    "supa_build_training_set", "supa_profiles",
+    "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc",
 )
 
 
@@ -117,6 +117,7 @@ def lib(build_if_missing: bool = True):
         L.supa_batch_set_surrogate.argtypes = [_VP, _VP, ctypes.c_float, _I64]
         L.supa_build_training_set.argtypes = [_VP, ctypes.c_float, _VP, _VP, _VP]
         L.supa_profiles.argtypes = [_VP, _I64, _I64, ctypes.c_int32, ctypes.c_float, _VP, _VP, _VP]
+        L.supa_shower_offsets_noalloc.argtypes = [_VP, _I64, _VP, _VP]
         for name in EXPORTED[1:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -316,6 +317,12 @@ def supa_profiles(b: int, shower_begin: int, shower_end: int, nbins: int, r_max:
                   stream=None):
     _check(lib().supa_profiles(b, int(shower_begin), int(shower_end), int(nbins), float(r_max), _ptr(longi_dev),
                                _ptr(lat_dev), _stream(stream)), "supa_profiles")
+
+
+def supa_shower_offsets_noalloc(counts_dev, n: int, offsets_dev, stream=None):
+    """First-hit offsets from per-shower counts; allocates nothing (see include/supa.h)."""
+    _check(lib().supa_shower_offsets_noalloc(_ptr(counts_dev), int(n), _ptr(offsets_dev), _stream(stream)),
+           "supa_shower_offsets_noalloc")
 
 
 def supa_build_training_set(b: int, e_s: float, x_dev, y_dev, stream=None):
