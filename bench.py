@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="supa", choices=["supa", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5", "surrogate"])
+    ap.add_argument("--e-s-sweep", type=float, nargs="+", default=[0.2, 0.5, 1.0, 2.0, 5.0])
     ap.add_argument("--showers", type=int, default=0, help="override the batch size")
     ap.add_argument("--voxel-chunk", type=int, default=32768)
     ap.add_argument("--fetch-chunk", type=int, default=FETCH_CHUNK)
@@ -581,15 +582,16 @@ def profile_errors(ref, got, thr=0.005):
             "total_deposit": float(abs(gl.sum() - rl.sum()) / rl.sum()), "bin_threshold": thr}
 
 
-def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor, fbuf, L, profiles=False):
+def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor, fbuf, L, profiles=False, mode=0,
+               voxelize=True):
     """The whole path in hybrid mode over n showers in sub-batches: simulate
     (stepping above E_s, network below), downsample, fetch.  Returns timings
     and (optionally) accumulated profiles."""
     import torch
-    mean_e = float(prims["E"].mean())
+    mean_e = float(prims["E"][:n].mean())
     cap = int(4.0 * mean_e / e_s * sub) + (1 << 20)
     hb = S.supa_batch_create([gh], sub, {"max_hits": int(sub * max(400, 40 * mean_e)) + (8 << 20), "lpt_order": 1})
-    S.supa_batch_set_surrogate(hb, net, e_s, cap)
+    S.supa_batch_set_surrogate(hb, net, e_s, cap, mode)
     lo = torch.zeros(L, dtype=torch.float64, device="cuda")
     la = torch.zeros(PROFILE_BINS, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -609,8 +611,9 @@ def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor,
         steps += info.n_steps
         diverted += info.n_diverted
         hits += info.n_hits
-        for c0 in range(0, m, V):
-            S.supa_voxelize(hb, c0, min(m, c0 + V), grid, oor)
+        if voxelize:
+            for c0 in range(0, m, V):
+                S.supa_voxelize(hb, c0, min(m, c0 + V), grid, oor)
         for h0 in range(0, info.n_hits, FC):
             S.supa_fetch_hits(hb, h0, FC, fbuf)
         if profiles:
@@ -635,22 +638,94 @@ def hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor
     del data
     sub = 125_000
     L = geom.n_layers
-    hybrid_run(S, gh, prims, d_prim, min(n, sub), seed, base, net, args.e_s, sub, V, grid, oor, fbuf, L)  # warm-up
-    prof = hybrid_run(S, gh, prims, d_prim, n, seed, base, net, args.e_s, sub, V, grid, oor, fbuf, L, True)
-    timed = hybrid_run(S, gh, prims, d_prim, n, seed, base, net, args.e_s, sub, V, grid, oor, fbuf, L)
+    out = {"e_s": args.e_s, "plain_showers_per_s": n / (plain["step_ms"] / 1000.0),
+           "plain_simulate_showers_per_s": n / (plain["simulate_ms"] / 1000.0),
+           "plain_particle_steps_per_shower": plain["steps"] / n,
+           "profile_binning": {"lateral_bins": PROFILE_BINS, "r_max": PROFILE_RMAX},
+           "training": {"samples": args.train_samples, "data_seconds": gen_s, **log},
+           "note": "hybrid timed in 125k-shower sub-batches (network over each sub-batch's queue); plain as one "
+                   "batch; same showers and seeds"}
+    for mode, name in ((1, "mean"), (0, "sample")):
+        hybrid_run(S, gh, prims, d_prim, min(n, sub), seed, base, net, args.e_s, sub, V, grid, oor, fbuf, L,
+                   mode=mode)  # warm-up
+        prof = hybrid_run(S, gh, prims, d_prim, n, seed, base, net, args.e_s, sub, V, grid, oor, fbuf, L, True,
+                          mode=mode)
+        timed = hybrid_run(S, gh, prims, d_prim, n, seed, base, net, args.e_s, sub, V, grid, oor, fbuf, L, mode=mode)
+        out[name] = {"showers_per_s": n / (timed["total_ms"] / 1000.0),
+                     "simulate_showers_per_s": n / (timed["simulate_ms"] / 1000.0),
+                     "particle_steps_per_shower": timed["steps"] / n, "diverted_per_shower": timed["diverted"] / n,
+                     "profile_error": profile_errors(plain["profiles"], prof["profiles"])}
     S.supa_surrogate_destroy(net)
-    errs = profile_errors(plain["profiles"], prof["profiles"])
-    return {
-        "e_s": args.e_s, "showers_per_s": n / (timed["total_ms"] / 1000.0),
-        "plain_showers_per_s": n / (plain["step_ms"] / 1000.0),
-        "simulate_showers_per_s": n / (timed["simulate_ms"] / 1000.0),
-        "plain_simulate_showers_per_s": n / (plain["simulate_ms"] / 1000.0),
-        "particle_steps_per_shower": timed["steps"] / n, "plain_particle_steps_per_shower": plain["steps"] / n,
-        "diverted_per_shower": timed["diverted"] / n, "profile_error": errs,
-        "profile_binning": {"lateral_bins": PROFILE_BINS, "r_max": PROFILE_RMAX},
-        "training": {"samples": args.train_samples, "data_seconds": gen_s, **log},
-        "note": "hybrid timed in 125k-shower sub-batches (network over each sub-batch's queue); plain as one batch",
-    }
+    return out
+
+
+def run_surrogate(args):
+    """Surrogate training at the C4 sizes (10M plain-method sub-showers below
+    E_s, 20 epochs) and the hybrid run of C5 (50 layers, E log-uniform
+    [10,1000], 0-45 deg) against the plain run on the same seeds, for a sweep
+    of E_s: showers/s (simulate only; images excluded to keep the sweep
+    short) and profile errors."""
+    import torch
+
+    from paper_2202_05012_gb300 import inputs
+    from paper_2202_05012_gb300 import supa as S
+    from paper_2202_05012_gb300 import surrogate_train as T
+
+    torch.cuda.set_device(0)
+    n5 = args.showers or 100_000
+    g5, p5 = inputs.workload_c5(n5)
+    gh = S.supa_init_geometry(g5)
+    d5 = S.primaries_to_device(p5)
+    L = g5.n_layers
+    V = 1024
+    grid = torch.empty((V, L, g5.ny, g5.nx), dtype=torch.float32, device="cuda")
+    oor = torch.empty(V, dtype=torch.float64, device="cuda")
+    fbuf = torch.empty((args.fetch_chunk, 4), dtype=torch.float32, device="cuda")
+    sub = 25_000
+    # plain reference on the same showers
+    pb = S.supa_batch_create([gh], sub, {"max_hits": sub * 30_000 + (8 << 20), "lpt_order": 1})
+    lo = torch.zeros(L, dtype=torch.float64, device="cuda")
+    la = torch.zeros(PROFILE_BINS, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_ms = 0.0
+    plain_steps = 0
+    for j in range(0, n5, sub):
+        m = min(sub, n5 - j)
+        e0.record()
+        S.supa_simulate(pb, d5[j * 24:(j + m) * 24], m, 4, j)
+        e1.record()
+        info = S.supa_batch_get_info(pb)
+        plain_ms += e0.elapsed_time(e1)
+        plain_steps += info.n_steps
+        S.supa_profiles(pb, 0, m, PROFILE_BINS, PROFILE_RMAX, lo, la)
+    torch.cuda.synchronize()
+    plain_prof = (lo.cpu().numpy() / n5, la.cpu().numpy() / n5)
+    S.supa_destroy_batch(pb)
+    out = {"metric": METRIC, "workload": "surrogate training (C4 sizes) + hybrid C5 vs plain, E_s sweep",
+           "c5_showers": n5, "plain": {"simulate_showers_per_s": n5 / (plain_ms / 1000.0),
+                                       "particle_steps_per_shower": plain_steps / n5}, "sweep": []}
+    for e_s in args.e_s_sweep:
+        data = T.training_set(args.train_samples, e_s, seed=3, n_layers=30)
+        net, log = T.train(data, epochs=args.epochs, lr=args.lr)
+        row = {"e_s": e_s, "training": {"data_seconds": data["seconds"], "samples": data["n"], **log}}
+        del data
+        # sub-batches small enough that the queue (about 4 E / E_s particles
+        # per shower, ~2 KB each with the network's activations) stays < 40 GB
+        sub_h = max(1000, min(sub, int(16e6 * e_s / (4.0 * float(p5["E"].mean())))))
+        for mode, name in ((1, "mean"), (0, "sample")):
+            prof = hybrid_run(S, gh, p5, d5, n5, 4, 0, net, e_s, sub_h, V, grid, oor, fbuf, L, True, mode=mode,
+                              voxelize=False)
+            timed = hybrid_run(S, gh, p5, d5, n5, 4, 0, net, e_s, sub_h, V, grid, oor, fbuf, L, mode=mode,
+                               voxelize=False)
+            row[name] = {"simulate_showers_per_s": n5 / (timed["simulate_ms"] / 1000.0),
+                         "particle_steps_per_shower": timed["steps"] / n5,
+                         "diverted_per_shower": timed["diverted"] / n5,
+                         "profile_error": profile_errors(plain_prof, prof["profiles"])}
+        S.supa_surrogate_destroy(net)
+        out["sweep"].append(row)
+        print(json.dumps(row), flush=True)
+    S.supa_destroy_geometry(gh)
+    print(json.dumps(out), flush=True)
 
 
 def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
@@ -785,6 +860,8 @@ def main():
         run_reference(args)
     elif args.workload == "c3":
         run_c3(args)
+    elif args.workload == "surrogate":
+        run_surrogate(args)
     else:
         run_supa(args)
 

@@ -284,17 +284,23 @@ int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, flo
  * (SUPA_ERR_TIMEOUT) since the last check. */
 int supa_surrogate_check(supa_surrogate *s);
 
+/* Deposit rule of the hybrid path for layer start + j of a particle of
+ * energy E, from the network's mu_j and s_j. */
+#define SUPA_SURROGATE_SAMPLE 0 /* d_j = E max(0, mu_j + exp(s_j/2) n_j), n_j ~ N(0,1) */
+#define SUPA_SURROGATE_MEAN 1   /* d_j = E max(0, mu_j): the predicted mean   */
+
 /* Switch a batch to the hybrid path: from the next supa_simulate on, a
  * particle whose energy is below e_s when it reaches a slice of a readout
  * layer is not stepped; it joins a device queue (at most queue_capacity
  * particles, else SUPA_ERR_OVERFLOW), the network predicts its deposits in
- * the next 30 layers, deposits are drawn (Philox normals keyed by shower,
- * slice and lineage), added to the layer sums and emitted as one hit per
+ * the next 30 layers, deposits follow `mode` (SUPA_SURROGATE_*; normals from
+ * Philox keyed by shower, slice and lineage) and, scaled down when they add
+ * up to more than E, are added to the layer sums and emitted as one hit per
  * non-empty layer (at the particle's straight-line position at the layer's
- * mid depth) after the shower's stepped hits.  The energy the draws leave
- * over is reported as sur_leak.  s = NULL or e_s <= 0 returns the batch to
- * the plain path.  s must outlive the batch.  Synchronous (allocates). */
-int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity);
+ * mid depth) after the shower's stepped hits.  The energy left over is
+ * reported as sur_leak.  s = NULL or e_s <= 0 returns the batch to the plain
+ * path.  s must outlive the batch.  Synchronous (allocates). */
+int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity, int32_t mode);
 
 /* Training set of the network from a plain simulation of sub-showers (each
  * primary entering on its start slice, see supa_primary.geom): x_dev float32

@@ -51,8 +51,9 @@ def normals(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
     return np.array(z)
 
 
-def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int = 0) -> dict:
-    """Per diverted particle: the drawn deposits d [n_div, 30] and the hits."""
+def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int = 0, mode: int = 0) -> dict:
+    """Per diverted particle: the drawn deposits d [n_div, 30] and the hits.
+    mode 0: d_j = E max(0, mu_j + exp(s_j/2) n_j); mode 1: d_j = E max(0, mu_j)."""
     X = features(div, geom, e_s)
     out, _ = mlp.forward(params, X) if len(X) else (np.zeros((0, 60)), None)
     L = int(geom.n_layers)
@@ -68,7 +69,8 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
         E = div["E"][i]
         for j in range(30):
             if l0 + j < L:
-                d[i, j] = E * max(0.0, out[i, j] + math.exp(0.5 * out[i, 30 + j]) * n[j])
+                f = out[i, j] if mode == 1 else out[i, j] + math.exp(0.5 * out[i, 30 + j]) * n[j]
+                d[i, j] = E * max(0.0, f)
         tot = d[i].sum()
         if tot > E:
             d[i] *= E / tot

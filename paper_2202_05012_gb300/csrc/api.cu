@@ -88,6 +88,7 @@ struct supa_batch {
     supa_surrogate *sur = nullptr;
     float e_s = 0.0f;
     int sq_cap = 0;
+    int sur_mode = SUPA_SURROGATE_SAMPLE;
     SurInfer inf;
     SurRec *d_sq_rec = nullptr;
     float *d_sq_feat = nullptr, *d_dep = nullptr;
@@ -489,6 +490,7 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     // hybrid: network over the queue, deposits, surrogate hit segments
     SUPA_CUDA(surrogate_infer_run(b->sur, &b->inf, b->d_sq_feat, b->d_sq_count, st));
     SurParams sp{};
+    sp.mode = b->sur_mode;
     sp.rec = b->d_sq_rec;
     sp.count = b->d_sq_count;
     sp.cap = b->sq_cap;
@@ -514,8 +516,10 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     return SUPA_OK;
 }
 
-int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity) {
+int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity, int32_t mode) {
     if (!b) return fail(SUPA_ERR_INVALID_ARG, "supa_batch_set_surrogate: null batch");
+    if (mode != SUPA_SURROGATE_SAMPLE && mode != SUPA_SURROGATE_MEAN)
+        return fail(SUPA_ERR_INVALID_ARG, "unknown surrogate mode %d", mode);
     free_hybrid(b);
     b->last_n = -1;
     b->info_valid = false;
@@ -548,6 +552,7 @@ int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_
     }
     b->sur = s;
     b->e_s = e_s;
+    b->sur_mode = mode;
     b->sq_cap = cap;
     return SUPA_OK;
 }

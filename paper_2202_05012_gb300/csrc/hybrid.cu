@@ -55,14 +55,19 @@ __global__ void sur_deposits(const SurParams p) {
         const supa_primary pr = p.prim[r.shower];
         const GeomDev g = p.geoms[pr.geom & 0xFFFFu];
         float z[32];
-        normals32((uint32_t)(p.shower_id_base + r.shower), r.k, r.lin_lo, r.lin_hi, p.seed, z);
+        if (p.mode == SUPA_SURROGATE_SAMPLE)
+            normals32((uint32_t)(p.shower_id_base + r.shower), r.k, r.lin_lo, r.lin_hi, p.seed, z);
         const float *o = p.out + (size_t)i * 64;
         float d[kSurLayers];
         float sum = 0.0f;
 #pragma unroll
         for (int j = 0; j < kSurLayers; ++j) {
             float v = 0.0f;
-            if (r.layer + j < g.n_layers) v = r.E * fmaxf(0.0f, fmaf(expf(0.5f * o[kSurLayers + j]), z[j], o[j]));
+            if (r.layer + j < g.n_layers) {
+                const float f = p.mode == SUPA_SURROGATE_SAMPLE ? fmaf(expf(0.5f * o[kSurLayers + j]), z[j], o[j])
+                                                               : o[j];
+                v = r.E * fmaxf(0.0f, f);
+            }
             d[j] = v;
             sum += v;
         }

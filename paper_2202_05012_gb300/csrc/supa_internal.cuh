@@ -80,6 +80,7 @@ cudaError_t surrogate_infer_run(supa_surrogate *s, SurInfer *inf, const float *f
                                 cudaStream_t st);
 
 struct SurParams {
+    int mode;  // SUPA_SURROGATE_SAMPLE or SUPA_SURROGATE_MEAN
     const SurRec *rec;
     const unsigned *count;  // queue length (device)
     int cap;

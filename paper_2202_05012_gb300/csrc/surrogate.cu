@@ -46,12 +46,13 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 // Inputs [n][6] float32 -> X0 [B][64] bf16 (and its transpose when X0T is
-// not null); rows past n (or past *n_dev) are zero.
+// not null); rows past n are zero, rows past *n_dev are not written (the
+// GEMMs skip them).
 __global__ void pack_inputs(const float *x, int64_t n, const unsigned *n_dev, int B, __nv_bfloat16 *X0,
                             __nv_bfloat16 *X0T) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= B) return;
-    if (n_dev) n = min((int64_t)*n_dev, n);
+    if (n_dev && r >= (int64_t)*n_dev) return;
     float v[kIn];
     for (int j = 0; j < kIn; ++j) v[j] = r < n ? x[(size_t)r * kIn + j] : 0.0f;
     for (int j = 0; j < kInPad; ++j) {

@@ -105,7 +105,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const GemmArgs g) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kGemmStages];
@@ -190,12 +190,15 @@ __global__ void __launch_bounds__(128, 1)
     // ---- epilogue: warp w owns rows 32w..32w+31 of the tile ----
     const bool ok = nkb > 0 && mbar_wait(&done_bar, 0) && !*abort_v;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const int row = m0 + warp * 32 + lane;
+    // warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31 (rows) and split
+    // the columns in halves
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = m0 + quarter * 32 + lane;
     const bool live = row < M;
     if (ok) {
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-        for (int c0 = 0; c0 < N; c0 += 32) {
+        for (int c0 = half * (N / 2); c0 < (half + 1) * (N / 2); c0 += 32) {
             float v[32];
             tmem_ld32(lane_addr + c0, v);
             if (g.epi == EPI_ATOMIC_F32) {
@@ -279,7 +282,7 @@ cudaError_t launch_n(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArg
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.M + kTileM - 1) / kTileM, splits);
-    tc_gemm_kernel<N><<<grid, 128, smem, st>>>(ta, tb, a);
+    tc_gemm_kernel<N><<<grid, 256, smem, st>>>(ta, tb, a);
     return cudaGetLastError();
 }
 

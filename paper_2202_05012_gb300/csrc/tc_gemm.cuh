@@ -8,8 +8,9 @@
 // One CTA owns a 128-row tile of C and all N <= 256 columns; blockIdx.y
 // splits K (split-K partial products are added with float atomics).
 // Warp 0 lane 0 issues TMA loads, warp 1 owns the TMEM allocation and its
-// lane 0 issues the MMAs, all four warps run the epilogue (warp w reads
-// TMEM lanes 32w..32w+31 = rows of the tile).
+// lane 0 issues the MMAs, all eight warps run the epilogue (warps w and
+// w + 4 read TMEM lanes 32(w%4)..+31 = rows of the tile, one half of the
+// columns each).
 //
 // Every mbarrier wait is bounded: on expiry the CTA records an error code,
 // stops issuing work, drains what it issued (again bounded), frees its TMEM

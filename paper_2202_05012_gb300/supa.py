@@ -114,7 +114,7 @@ def lib(build_if_missing: bool = True):
         L.supa_surrogate_forward.argtypes = [_VP, _VP, _I64, _VP, _VP]
         L.supa_surrogate_check.argtypes = [_VP]
         L.supa_surrogate_train_epoch.argtypes = [_VP, _VP, _VP, _I64, ctypes.c_uint64, ctypes.c_float, _VP, _VP]
-        L.supa_batch_set_surrogate.argtypes = [_VP, _VP, ctypes.c_float, _I64]
+        L.supa_batch_set_surrogate.argtypes = [_VP, _VP, ctypes.c_float, _I64, ctypes.c_int32]
         L.supa_build_training_set.argtypes = [_VP, ctypes.c_float, _VP, _VP, _VP]
         L.supa_profiles.argtypes = [_VP, _I64, _I64, ctypes.c_int32, ctypes.c_float, _VP, _VP, _VP]
         L.supa_shower_offsets_noalloc.argtypes = [_VP, _I64, _VP, _VP]
@@ -309,8 +309,13 @@ def supa_surrogate_train_epoch(s: int, x_dev, y_dev, n: int, seed: int, lr: floa
                                             _ptr(loss_acc_dev), _stream(stream)), "supa_surrogate_train_epoch")
 
 
-def supa_batch_set_surrogate(b: int, s: int | None, e_s: float, queue_capacity: int):
-    _check(lib().supa_batch_set_surrogate(b, s, float(e_s), int(queue_capacity)), "supa_batch_set_surrogate")
+SUPA_SURROGATE_SAMPLE = 0
+SUPA_SURROGATE_MEAN = 1
+
+
+def supa_batch_set_surrogate(b: int, s: int | None, e_s: float, queue_capacity: int, mode: int = SUPA_SURROGATE_SAMPLE):
+    _check(lib().supa_batch_set_surrogate(b, s, float(e_s), int(queue_capacity), int(mode)),
+           "supa_batch_set_surrogate")
 
 
 def supa_profiles(b: int, shower_begin: int, shower_end: int, nbins: int, r_max: float, longi_dev, lat_dev,

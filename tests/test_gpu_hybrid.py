@@ -120,7 +120,8 @@ def test_hybrid_conserves_energy_and_emits_after_stepped_hits():
         S.supa_destroy_geometry(gh)
 
 
-def test_hybrid_matches_oracle():
+@pytest.mark.parametrize("mode", [S.SUPA_SURROGATE_SAMPLE, S.SUPA_SURROGATE_MEAN])
+def test_hybrid_matches_oracle(mode):
     """Same set-aside decisions and stepped hits as the FP64 oracle; the
     network's deposits agree within BF16 tolerance (per shower, per layer)."""
     import torch
@@ -134,7 +135,7 @@ def test_hybrid_matches_oracle():
     sur = S.supa_surrogate_create(1024, vec)
     b = S.supa_batch_create([gh], n, {"record_tags": 1})
     try:
-        S.supa_batch_set_surrogate(b, sur, E_S, 1_000_000)
+        S.supa_batch_set_surrogate(b, sur, E_S, 1_000_000, mode)
         S.supa_simulate(b, S.primaries_to_device(p), n, 13)
         info = S.supa_batch_get_info(b)
         arr = {k: v.cpu().numpy() for k, v in S.info_arrays(info).items()}
@@ -149,7 +150,7 @@ def test_hybrid_matches_oracle():
         S.supa_destroy_geometry(gh)
     ora = oracle.simulate(g, p, 13, n_threads=8, e_s=E_S)
     div = ora["div"]
-    dep = hybrid.deposits(div, params64, g, E_S, 13)
+    dep = hybrid.deposits(div, params64, g, E_S, 13, mode=mode)
     # the same particles are set aside (float32 decisions on both sides)
     assert abs(info.n_diverted - len(div["E"])) <= max(2, 1e-3 * len(div["E"]))
     # stepped hits: same (slice, lineage) keys per shower
