@@ -100,6 +100,17 @@ __device__ __forceinline__ double block_sum_double(double v, double *red) {
 // Showers with more hits than the list holds re-read their hits per group.
 namespace {
 constexpr unsigned kNoCell = 0xFFFFFFFFu;
+constexpr int kTouchCap = 2048;  // touched cells remembered per image buffer
+
+// Add E to an image cell; the first deposit into a cell records it so that
+// the buffer can be reset cell by cell after its store.
+__device__ __forceinline__ void deposit(float *tile, uint32_t *touched, int *n_touched, int cell, float E) {
+    const float old = atomicAdd(&tile[cell], E);
+    if (old == 0.0f) {
+        const int i = atomicAdd(n_touched, 1);
+        if (i < kTouchCap) touched[i] = (uint32_t)cell;
+    }
+}
 
 __device__ __forceinline__ void bulk_store(float *dst, const float *src, unsigned bytes) {
     const unsigned saddr = (unsigned)__cvta_generic_to_shared(src);
@@ -128,14 +139,25 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
     extern __shared__ __align__(128) unsigned char vsm[];
     __shared__ float roi_x[SUPA_MAX_LAYERS], roi_y[SUPA_MAX_LAYERS];
     __shared__ double red[32];
+    __shared__ int touched_n[2];
     const int cells = p.nx * p.ny;
     const int tile_floats = p.G * cells;
     float *const tile0 = reinterpret_cast<float *>(vsm);
     float *const tile1 = tile0 + tile_floats;
-    uint2 *list = reinterpret_cast<uint2 *>(vsm + (size_t)2 * tile_floats * sizeof(float));
+    uint32_t *const touched0 = reinterpret_cast<uint32_t *>(tile1 + tile_floats);
+    uint32_t *const touched1 = touched0 + kTouchCap;
+    uint2 *list = reinterpret_cast<uint2 *>(touched1 + kTouchCap);
     const float half_x = (float)p.nx * p.wx * 0.5f;
     const float half_y = (float)p.ny * p.wy * 0.5f;
     int phase = 0;
+    // Both image buffers start zero and are kept zero between uses: after a
+    // buffer's bulk store has been read, only the cells it touched (listed in
+    // touched0/1; a full clear if that list overflowed) are reset.
+    {
+        float4 *t4 = reinterpret_cast<float4 *>(tile0);
+        for (int i = threadIdx.x; i < 2 * tile_floats / 4; i += blockDim.x) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (threadIdx.x < 2) touched_n[threadIdx.x] = 0;
+    }
 
     for (int64_t item = blockIdx.x; item < p.n_showers; item += gridDim.x) {
         const int64_t s = p.s_begin + item;
@@ -189,18 +211,27 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
             const int l0 = grp * p.G;
             const int G = min(p.G, p.L - l0);
             float *tile = phase ? tile1 : tile0;
+            uint32_t *touched = phase ? touched1 : touched0;
             // the store issued from this buffer two groups ago must have read it
             if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
             __syncthreads();
-            float4 *t4 = reinterpret_cast<float4 *>(tile);
-            for (int i = threadIdx.x; i < G * cells / 4; i += blockDim.x) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int nt = touched_n[phase];
+            __syncthreads();
+            if (threadIdx.x == 0) touched_n[phase] = 0;
+            if (nt > kTouchCap) {
+                float4 *t4 = reinterpret_cast<float4 *>(tile);
+                for (int i = threadIdx.x; i < tile_floats / 4; i += blockDim.x) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                for (int i = threadIdx.x; i < nt; i += blockDim.x) tile[touched[i]] = 0.0f;
+            }
             __syncthreads();
             if (listed) {
                 for (int j = threadIdx.x; j < count; j += blockDim.x) {
                     const uint2 e = list[j];
                     const int li = (int)(e.x >> 24) - l0;
                     if (e.x != kNoCell && li >= 0 && li < G)
-                        atomicAdd(&tile[li * cells + (int)(e.x & 0xFFFFFFu)], __uint_as_float(e.y));
+                        deposit(tile, touched, &touched_n[phase], li * cells + (int)(e.x & 0xFFFFFFu),
+                                __uint_as_float(e.y));
                 }
             } else if (count > 0) {
                 ShowerHits it2;
@@ -212,7 +243,7 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
                         const unsigned key = hit_key(h, g, p.s2l, roi_x, roi_y, p, dead);
                         const int li = (int)(key >> 24) - l0;
                         if (key != kNoCell && li >= 0 && li < G)
-                            atomicAdd(&tile[li * cells + (int)(key & 0xFFFFFFu)], h.w);
+                            deposit(tile, touched, &touched_n[phase], li * cells + (int)(key & 0xFFFFFFu), h.w);
                     }
                 } while (it2.next());
             }
@@ -227,7 +258,8 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
 }
 
 size_t vox_smem_bytes(int G, int nx, int ny, int list_cap) {
-    return (size_t)2 * G * nx * ny * sizeof(float) + (size_t)list_cap * 8;
+    return (size_t)2 * G * nx * ny * sizeof(float) + (size_t)2 * kTouchCap * sizeof(uint32_t) +
+           (size_t)list_cap * 8;
 }
 
 void vox_plan(int L, int nx, int ny, int *G, int *n_groups, int *list_cap) {
@@ -236,9 +268,9 @@ void vox_plan(int L, int nx, int ny, int *G, int *n_groups, int *list_cap) {
     ng = std::max(1, std::min(ng, L));
     *G = (L + ng - 1) / ng;
     *n_groups = (L + *G - 1) / *G;
-    const size_t tiles = 2 * (size_t)(*G) * layer_bytes;
-    const size_t budget = tiles <= 80 * 1024 ? 108 * 1024 : 220 * 1024;
-    *list_cap = tiles < budget ? (int)((budget - tiles) / 8) : 0;
+    const size_t fixed = 2 * (size_t)(*G) * layer_bytes + 2 * kTouchCap * sizeof(uint32_t);
+    const size_t budget = fixed <= 96 * 1024 ? 108 * 1024 : 220 * 1024;
+    *list_cap = fixed < budget ? (int)((budget - fixed) / 8) : 0;
 }
 
 cudaError_t launch_voxelize(const VoxParams &p, cudaStream_t st) {

@@ -53,13 +53,17 @@ __global__ void pack_inputs(const float *x, int64_t n, const unsigned *n_dev, in
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= B) return;
     if (n_dev && r >= (int64_t)*n_dev) return;
-    float v[kIn];
-    for (int j = 0; j < kIn; ++j) v[j] = r < n ? x[(size_t)r * kIn + j] : 0.0f;
-    for (int j = 0; j < kInPad; ++j) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(j < kIn ? v[j] : 0.0f);
-        X0[(size_t)r * kInPad + j] = h;
-        if (X0T) X0T[(size_t)j * B + r] = h;
-    }
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r < n)
+        for (int j = 0; j < kIn; ++j) v[j] = x[(size_t)r * kIn + j];
+    // one 128-byte row: the 6 features, then zeros
+    uint4 *row = reinterpret_cast<uint4 *>(X0 + (size_t)r * kInPad);
+    __nv_bfloat162 h[4];
+    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    row[0] = *reinterpret_cast<const uint4 *>(h);
+    for (int j = 1; j < kInPad / 8; ++j) row[j] = make_uint4(0u, 0u, 0u, 0u);
+    if (X0T)
+        for (int j = 0; j < kInPad; ++j) X0T[(size_t)j * B + r] = __float2bfloat16_rn(j < kIn ? v[j] : 0.0f);
 }
 
 // Gaussian NLL over the 30 layers, mean over the batch: writes d loss / d out
@@ -72,28 +76,39 @@ __global__ void nll_loss(const float *out, const float *y, int B, __nv_bfloat16 
     for (int j = threadIdx.x; j < kOutPad; j += blockDim.x) colsum[j] = 0.0f;
     __syncthreads();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = r < B;
+    const unsigned lane = threadIdx.x & 31;
     double l = 0.0;
-    if (r < B) {
-        const float inv = 1.0f / (float)(B * kLayersOut);
-        for (int j = 0; j < kLayersOut; ++j) {
+    const float inv = 1.0f / (float)(B * kLayersOut);
+    for (int j = 0; j < kLayersOut; ++j) {
+        float gmu = 0.0f, gs = 0.0f;
+        if (live) {
             const float mu = out[(size_t)r * kOutPad + j], s = out[(size_t)r * kOutPad + kLayersOut + j];
             const float res = y[(size_t)r * kLayersOut + j] - mu;
             const float e = expf(-s);
             l += 0.5 * (double)(res * res * e) + 0.5 * (double)s;
-            const float gmu = -res * e * inv;
-            const float gs = (0.5f - 0.5f * res * res * e) * inv;
+            gmu = -res * e * inv;
+            gs = (0.5f - 0.5f * res * res * e) * inv;
             G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(gmu);
             G4[(size_t)r * kOutPad + kLayersOut + j] = __float2bfloat16_rn(gs);
             G4T[(size_t)j * B + r] = __float2bfloat16_rn(gmu);
             G4T[(size_t)(kLayersOut + j) * B + r] = __float2bfloat16_rn(gs);
+        }
+        // bias gradient: column sums, one shared atomic per warp and column
+        for (int o = 16; o > 0; o >>= 1) {
+            gmu += __shfl_xor_sync(0xFFFFFFFFu, gmu, o);
+            gs += __shfl_xor_sync(0xFFFFFFFFu, gs, o);
+        }
+        if (lane == 0) {
             atomicAdd(&colsum[j], gmu);
             atomicAdd(&colsum[kLayersOut + j], gs);
         }
+    }
+    if (live)
         for (int j = kOut; j < kOutPad; ++j) {
             G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(0.0f);
             G4T[(size_t)j * B + r] = __float2bfloat16_rn(0.0f);
         }
-    }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
     __syncthreads();
