@@ -278,7 +278,9 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
  * each minibatch loss to *loss_acc_dev when it is not NULL. */
 int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,
                                float lr, double *loss_acc_dev, void *stream);
-/* Inference: x_dev float32 [n][6] -> out_dev float32 [n][60] (asynchronous). */
+/* Inference: x_dev float32 [n][6] (8-byte aligned) -> out_dev float32
+ * [n][60], 0 <= n < 2^31, in one launch of the fused network kernel
+ * (asynchronous; a pipeline timeout shows in supa_surrogate_check). */
 int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, void *stream);
 /* Synchronise and report a tensor-core pipeline that gave up waiting
  * (SUPA_ERR_TIMEOUT) since the last check. */
@@ -307,6 +309,15 @@ int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_
  * [n][6] features of the start, y_dev float32 [n][30] deposit fractions of
  * layers start + 0..29 (FP64 layer sums / E).  Synchronous. */
 int supa_build_training_set(supa_batch *b, float e_s, float *x_dev, float *y_dev, void *stream);
+
+/* The particles the last hybrid simulation of b diverted to the network, as
+ * sub-shower primaries: each enters on its slice of diversion (geom = the
+ * shower's geometry index | slice << 16) with its energy, position and
+ * direction -- the inputs a matched training set is simulated from.  Writes
+ * min(n, capacity) primaries to out_dev and the queue length n to *n_out.
+ * Like the surrogate itself this has no counterpart in the SUPA paper.
+ * Synchronous. */
+int supa_export_diverted(supa_batch *b, supa_primary *out_dev, int64_t capacity, int64_t *n_out, void *stream);
 
 #ifdef __cplusplus
 }

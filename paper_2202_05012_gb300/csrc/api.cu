@@ -92,6 +92,7 @@ struct supa_batch {
     SurInfer inf;
     SurRec *d_sq_rec = nullptr;
     float *d_sq_feat = nullptr, *d_dep = nullptr;
+    uint8_t *d_pcnt = nullptr;
     unsigned *d_sq_count = nullptr;
     uint32_t *d_scount = nullptr, *d_scursor = nullptr, *d_tot = nullptr;
     int64_t *d_soff = nullptr;
@@ -260,12 +261,13 @@ int supa_destroy_geometry(supa_geometry *g) {
 }
 
 static void free_hybrid(supa_batch *b) {
-    void *ptrs[] = {b->d_sq_rec, b->d_sq_feat, b->d_dep, b->d_sq_count, b->d_scount, b->d_scursor, b->d_tot,
+    void *ptrs[] = {b->d_sq_rec, b->d_sq_feat, b->d_dep, b->d_pcnt, b->d_sq_count, b->d_scount, b->d_scursor, b->d_tot,
                     b->d_soff, b->d_sur_hits, b->d_sur_leak, b->d_scan_tmp2};
     for (void *p : ptrs) cudaFree(p);
     surrogate_infer_free(&b->inf);
     b->d_sq_rec = nullptr;
     b->d_sq_feat = b->d_dep = nullptr;
+    b->d_pcnt = nullptr;
     b->d_sq_count = nullptr;
     b->d_scount = b->d_scursor = b->d_tot = nullptr;
     b->d_soff = nullptr;
@@ -501,6 +503,7 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     sp.seed = seed;
     sp.shower_id_base = shower_id_base;
     sp.dep = b->d_dep;
+    sp.pcnt = b->d_pcnt;
     sp.lsum = b->d_lsum;
     sp.lsum_stride = b->max_layers;
     sp.sur_leak = b->d_sur_leak;
@@ -532,6 +535,7 @@ int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_
     if (e == cudaSuccess) e = dalloc(&b->d_sq_rec, cap);
     if (e == cudaSuccess) e = dalloc(&b->d_sq_feat, (size_t)cap * kSurIn);
     if (e == cudaSuccess) e = dalloc(&b->d_dep, (size_t)cap * kSurLayers);
+    if (e == cudaSuccess) e = dalloc(&b->d_pcnt, (size_t)cap);
     if (e == cudaSuccess) e = dalloc(&b->d_sq_count, 1);
     if (e == cudaSuccess) e = dalloc(&b->d_scount, n);
     if (e == cudaSuccess) e = dalloc(&b->d_scursor, n);
@@ -571,6 +575,23 @@ int supa_build_training_set(supa_batch *b, float e_s, float *x_dev, float *y_dev
     SUPA_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     SUPA_CUDA(cudaStreamSynchronize(st));
     if (h) return fail(SUPA_ERR_INVALID_ARG, "a sub-shower starts on a slice outside every readout layer");
+    return SUPA_OK;
+}
+
+int supa_export_diverted(supa_batch *b, supa_primary *out_dev, int64_t capacity, int64_t *n_out, void *stream) {
+    if (!b || !n_out || capacity < 0 || (capacity > 0 && !out_dev))
+        return fail(SUPA_ERR_INVALID_ARG, "supa_export_diverted: bad argument");
+    *n_out = 0;
+    if (!b->sur) return fail(SUPA_ERR_INVALID_ARG, "supa_export_diverted: the batch is not in hybrid mode");
+    if (b->last_n < 0) return fail(SUPA_ERR_NOT_READY, "no simulation has been enqueued on this batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    SUPA_CUDA(cudaMemcpyAsync(&h, b->d_sq_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SUPA_CUDA(cudaStreamSynchronize(st));
+    const int64_t n = std::min<int64_t>((int64_t)h, (int64_t)b->sq_cap);
+    SUPA_CUDA(launch_export_diverted(b->d_sq_rec, std::min(n, capacity), b->d_prim, out_dev, st));
+    SUPA_CUDA(cudaStreamSynchronize(st));
+    *n_out = n;
     return SUPA_OK;
 }
 

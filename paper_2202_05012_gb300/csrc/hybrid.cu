@@ -24,89 +24,222 @@ namespace supa {
 
 namespace {
 
-// 32 standard normals (Box-Muller) for one diverted particle.
-__device__ void normals32(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed, float *z) {
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Standard normal n_j of a diverted particle, j = lane (0..31): Box-Muller on
+// Philox block j / 4 of its stream (tag 1, keyed by shower, slice and
+// lineage); words 2p and 2p + 1 of a block give the pair (n_{4b+2p},
+// n_{4b+2p+1}) = rad (cos, sin)(2 pi u2), p = (j / 2) mod 2.
+__device__ float lane_normal(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed, int lane) {
+    const int blk = lane >> 2, pr = (lane >> 1) & 1;
+    const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (1u << 16) | ((uint32_t)blk << 20), lin_lo, lin_hi),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint32_t w0 = pr ? r.z : r.x, w1 = pr ? r.w : r.y;
+    const float u1 = (float)((w0 >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
+    const float u2 = u24(w1);
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    return (lane & 1) ? rad * sn : rad * cs;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
-    for (int blk = 0; blk < 8; ++blk) {
-        const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (1u << 16) | ((uint32_t)blk << 20), lin_lo, lin_hi),
-                                      k0, k1);
-        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const float u1 = (float)((w[2 * p] >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
-            const float u2 = u24(w[2 * p + 1]);
-            const float rad = sqrtf(-2.0f * logf(u1));
-            float sn, cs;
-            sincospif(2.0f * u2, &sn, &cs);
-            z[4 * blk + 2 * p] = rad * cs;
-            z[4 * blk + 2 * p + 1] = rad * sn;
-        }
-    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Contiguous range of queue entries of this warp: consecutive entries mostly
+// belong to one shower (the step kernel queues a warp's diverted particles
+// together), so runs stay whole.
+__device__ __forceinline__ void warp_range(unsigned n, unsigned &i0, unsigned &i1) {
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5, w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned per = (n + nw - 1) / nw;
+    i0 = min(n, w * per);
+    i1 = min(n, i0 + per);
 }
 
 }  // namespace
 
-// Pass 1: deposits per diverted particle, layer sums, hit counts, leakage.
+// Pass 1, one warp per diverted particle (lane j = layer start + j): deposits,
+// hit count per particle, and -- summed over each run of consecutive queue
+// entries of one shower before the atomics -- layer sums, surrogate leakage
+// and hit counts per shower.  Lane L keeps the run's sums of absolute layers
+// L and L + 32, in 64-bit fixed point (integer adds: the FP64 unit of this
+// GPU is far too slow for a double add per deposit), converted to FP64 once
+// per run.  Queue records are read 32 at a time (lane k holds entry g0 + k)
+// and the network outputs of 8 entries are in flight at once.
 __global__ void sur_deposits(const SurParams p) {
     const unsigned n = min(*p.count, (unsigned)p.cap);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const SurRec r = p.rec[i];
-        const supa_primary pr = p.prim[r.shower];
-        const GeomDev g = p.geoms[pr.geom & 0xFFFFu];
-        float z[32];
-        if (p.mode == SUPA_SURROGATE_SAMPLE)
-            normals32((uint32_t)(p.shower_id_base + r.shower), r.k, r.lin_lo, r.lin_hi, p.seed, z);
-        const float *o = p.out + (size_t)i * 64;
-        float d[kSurLayers];
-        float sum = 0.0f;
+    const int lane = threadIdx.x & 31;
+    const bool sample = p.mode == SUPA_SURROGATE_SAMPLE;
+    unsigned i0, i1;
+    warp_range(n, i0, i1);
+    int cur = -1;
+    unsigned long long acc_lo = 0, acc_hi = 0;
+    long long leak = 0;
+    unsigned cnt = 0;
+    auto flush = [&]() {
+        if (cur < 0) return;
+        double *ls = p.lsum + (size_t)cur * p.lsum_stride;
+        if (acc_lo) atomicAdd(&ls[lane], from_fixed32(acc_lo));
+        if (acc_hi) atomicAdd(&ls[lane + 32], from_fixed32(acc_hi));
 #pragma unroll
-        for (int j = 0; j < kSurLayers; ++j) {
-            float v = 0.0f;
-            if (r.layer + j < g.n_layers) {
-                const float f = p.mode == SUPA_SURROGATE_SAMPLE ? fmaf(expf(0.5f * o[kSurLayers + j]), z[j], o[j])
-                                                               : o[j];
-                v = r.E * fmaxf(0.0f, f);
-            }
-            d[j] = v;
-            sum += v;
+        for (int o = 16; o > 0; o >>= 1) leak += __shfl_xor_sync(kFull, leak, o);
+        if (lane == 0) {
+            atomicAdd(&p.sur_leak[cur], (double)leak * (1.0 / 4294967296.0));
+            if (cnt) atomicAdd(&p.scount[cur], cnt);
         }
-        const float scale = sum > r.E ? r.E / sum : 1.0f;
-        double kept = 0.0;
-        int cnt = 0;
+        acc_lo = acc_hi = 0;
+        leak = 0;
+        cnt = 0;
+    };
+    for (unsigned g0 = i0; g0 < i1; g0 += 32) {
+        const int m = (int)min(32u, i1 - g0);
+        uint32_t r_sh = 0, r_lo = 0, r_hi = 0;
+        int r_k = 0, r_layer = 0, r_nl = 0;
+        float r_E = 0.0f;
+        if (lane < m) {
+            const SurRec r = p.rec[g0 + lane];
+            r_sh = r.shower;
+            r_k = r.k;
+            r_layer = r.layer;
+            r_E = r.E;
+            r_lo = r.lin_lo;
+            r_hi = r.lin_hi;
+            r_nl = p.geoms[p.prim[r.shower].geom & 0xFFFFu].n_layers;
+        }
+        for (int k0 = 0; k0 < m; k0 += 8) {
+            float mu[8], sg[8];
 #pragma unroll
-        for (int j = 0; j < kSurLayers; ++j) {
-            const float v = d[j] * scale;
-            p.dep[(size_t)i * kSurLayers + j] = v;
-            if (v > 0.0f) {
-                ++cnt;
-                kept += (double)v;
-                atomicAdd(&p.lsum[(size_t)r.shower * p.lsum_stride + r.layer + j], (double)v);
+            for (int u = 0; u < 8; ++u) {
+                const bool ld = k0 + u < m && lane < kSurLayers;
+                const float *o = p.out + (size_t)(g0 + k0 + u) * 64;
+                mu[u] = ld ? o[lane] : 0.0f;
+                sg[u] = (ld && sample) ? o[kSurLayers + lane] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u;
+                if (k >= m) break;
+                const int sh = (int)__shfl_sync(kFull, r_sh, k);
+                const int layer = __shfl_sync(kFull, r_layer, k);
+                const int nl = __shfl_sync(kFull, r_nl, k);
+                const float E = __shfl_sync(kFull, r_E, k);
+                if (sh != cur) {
+                    flush();
+                    cur = sh;
+                }
+                int kk = 0;
+                uint32_t lo = 0, hi = 0;
+                if (sample) {  // uniform
+                    kk = __shfl_sync(kFull, r_k, k);
+                    lo = __shfl_sync(kFull, r_lo, k);
+                    hi = __shfl_sync(kFull, r_hi, k);
+                }
+                float v = 0.0f;
+                if (lane < kSurLayers && layer + lane < nl) {
+                    float f = mu[u];
+                    if (sample)
+                        f = fmaf(expf(0.5f * sg[u]),
+                                 lane_normal((uint32_t)(p.shower_id_base + (uint32_t)sh), kk, lo, hi, p.seed, lane), f);
+                    v = E * fmaxf(0.0f, f);
+                }
+                const float sum = warp_sum(v);
+                if (sum > E) v *= E / sum;
+                const unsigned i = g0 + (unsigned)k;
+                if (lane < kSurLayers) p.dep[(size_t)i * kSurLayers + lane] = v;
+                const unsigned nz = __ballot_sync(kFull, v > 0.0f);
+                const unsigned long long fv = fixed32(v);
+                if (lane == 0) {
+                    p.pcnt[i] = (uint8_t)__popc(nz);
+                    cnt += (unsigned)__popc(nz);
+                    leak += (long long)fixed32(E);
+                }
+                leak -= (long long)fv;
+                // deposit of absolute layer a comes from lane a - layer
+                const int src_lo = lane - layer, src_hi = lane + 32 - layer;
+                const unsigned long long w_lo = __shfl_sync(kFull, fv, src_lo & 31),
+                                         w_hi = __shfl_sync(kFull, fv, src_hi & 31);
+                if (src_lo >= 0 && src_lo < kSurLayers) acc_lo += w_lo;
+                if (src_hi >= 0 && src_hi < kSurLayers) acc_hi += w_hi;
             }
         }
-        atomicAdd(&p.sur_leak[r.shower], (double)r.E - kept);
-        if (cnt) atomicAdd(&p.scount[r.shower], (unsigned)cnt);
     }
+    flush();
 }
 
 // Pass 2: the hits, into each shower's segment [soff[s], soff[s] + scount[s]).
+// Per group of 32 queue entries, one cursor atomic per run of one shower
+// (segmented scan of the per-particle counts), then one particle at a time
+// with lane j writing the hit of layer start + j when its deposit is > 0 --
+// a particle's hits are consecutive, in layer order.
 __global__ void sur_hits(const SurParams p) {
     const unsigned n = min(*p.count, (unsigned)p.cap);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const SurRec r = p.rec[i];
-        const supa_primary pr = p.prim[r.shower];
-        const GeomDev g = p.geoms[pr.geom & 0xFFFFu];
-        const float *d = p.dep + (size_t)i * kSurLayers;
-        int cnt = 0;
-        for (int j = 0; j < kSurLayers; ++j) cnt += d[j] > 0.0f;
-        if (!cnt) continue;
-        int64_t at = p.soff[r.shower] + (int64_t)atomicAdd(&p.scursor[r.shower], (unsigned)cnt);
-        const float zk = (float)r.k * g.dz;
-        for (int j = 0; j < kSurLayers; ++j) {
-            if (!(d[j] > 0.0f)) continue;
-            const float zm = p.zmid[g.layer_off + r.layer + j];
-            const float dz = zm - zk;
-            p.hits[at++] = make_float4(fmaf(dz, r.tx, r.x), fmaf(dz, r.ty, r.y), zm, d[j]);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned i0, i1;
+    warp_range(n, i0, i1);
+    for (unsigned g0 = i0; g0 < i1; g0 += 32) {
+        const unsigned i = g0 + lane;
+        const int m = (int)min(32u, i1 - g0);
+        const bool valid = lane < m;
+        int sh = -1 - lane, r_loff = 0;
+        unsigned c = 0;
+        float r_x = 0.f, r_y = 0.f, r_tx = 0.f, r_ty = 0.f, r_zk = 0.f;
+        if (valid) {
+            const SurRec r = p.rec[i];
+            sh = (int)r.shower;
+            c = p.pcnt[i];
+            const GeomDev &g = p.geoms[p.prim[r.shower].geom & 0xFFFFu];
+            r_loff = g.layer_off + r.layer;
+            r_zk = (float)r.k * g.dz;
+            r_x = r.x;
+            r_y = r.y;
+            r_tx = r.tx;
+            r_ty = r.ty;
+        }
+        // runs of equal shower among the lanes
+        const int prev = __shfl_up_sync(kFull, sh, 1);
+        const unsigned heads = __ballot_sync(kFull, lane == 0 || prev != sh);
+        const int start = 31 - __clz(heads & (lt | (1u << lane)));
+        const unsigned later = heads & ~(lt | (1u << lane));
+        const int end = later ? __ffs(later) - 2 : 31;
+        // inclusive prefix of c over the warp
+        unsigned inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const unsigned exc = inc - c;
+        const unsigned run_exc = exc - __shfl_sync(kFull, exc, start);
+        const unsigned run_tot = __shfl_sync(kFull, inc, end) - __shfl_sync(kFull, exc, start);
+        unsigned base = 0;
+        if (lane == end && valid && run_tot) base = atomicAdd(&p.scursor[sh], run_tot);
+        base = __shfl_sync(kFull, base, end);
+        const int64_t at_lane = valid ? p.soff[sh] + (int64_t)(base + run_exc) : 0;
+        for (int k0 = 0; k0 < m; k0 += 8) {
+            float d[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                d[u] = (k0 + u < m && lane < kSurLayers) ? p.dep[(size_t)(g0 + k0 + u) * kSurLayers + lane] : 0.0f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u;
+                if (k >= m) break;
+                const int64_t at = __shfl_sync(kFull, at_lane, k);
+                const int loff = __shfl_sync(kFull, r_loff, k);
+                const float zk = __shfl_sync(kFull, r_zk, k), x = __shfl_sync(kFull, r_x, k),
+                            y = __shfl_sync(kFull, r_y, k), tx = __shfl_sync(kFull, r_tx, k),
+                            ty = __shfl_sync(kFull, r_ty, k);
+                const unsigned nz = __ballot_sync(kFull, d[u] > 0.0f);
+                if (d[u] > 0.0f) {
+                    const float zm = p.zmid[loff + lane];
+                    const float dz = zm - zk;
+                    p.hits[at + __popc(nz & lt)] = make_float4(fmaf(dz, tx, x), fmaf(dz, ty, y), zm, d[u]);
+                }
+            }
         }
     }
 }
@@ -143,13 +276,37 @@ __global__ void training_set(const supa_primary *prim, int64_t n, const GeomDev 
     }
 }
 
+// The diverted particles of the last hybrid run as sub-shower primaries: each
+// enters on its slice of diversion with its energy, position and direction
+// (polar angle and azimuth from the slopes), in the geometry of its shower.
+__global__ void export_diverted(const SurRec *rec, int64_t n, const supa_primary *prim, supa_primary *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const SurRec r = rec[i];
+        supa_primary q;
+        q.E = r.E;
+        q.x0 = r.x;
+        q.y0 = r.y;
+        q.theta = atanf(sqrtf(r.tx * r.tx + r.ty * r.ty));
+        q.phi = atan2f(r.ty, r.tx);
+        q.geom = (prim[r.shower].geom & 0xFFFFu) | ((uint32_t)r.k << 16);
+        out[i] = q;
+    }
+}
+
+cudaError_t launch_export_diverted(const SurRec *rec, int64_t n, const supa_primary *prim, supa_primary *out,
+                                   cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    export_diverted<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, st>>>(rec, n, prim, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sur_deposits(const SurParams &p, cudaStream_t st) {
-    sur_deposits<<<2048, 128, 0, st>>>(p);
+    sur_deposits<<<4096, 128, 0, st>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sur_hits(const SurParams &p, cudaStream_t st) {
-    sur_hits<<<2048, 128, 0, st>>>(p);
+    sur_hits<<<4096, 128, 0, st>>>(p);
     return cudaGetLastError();
 }
 

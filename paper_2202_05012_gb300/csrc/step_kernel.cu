@@ -62,25 +62,6 @@ __device__ inline WarpSmem carve(unsigned char *base, int C, int H, bool tags) {
     return w;
 }
 
-// Energy in 64-bit fixed point, units of 2^-32: E = m * 2^(e-23) with a 24-bit
-// significand m becomes m << (e + 9), exact for E >= 2^-9 and rounded to the
-// nearest unit below (ties up).  Integer shifts only: a float -> int64
-// conversion would run on the FP64 unit.  Energies are positive and below
-// 2^30 (checked per primary), so the sums cannot overflow.
-__device__ __forceinline__ unsigned long long fixed32(float E) {
-    const uint32_t bits = __float_as_uint(E);
-    const int e = (int)((bits >> 23) & 0xFFu);
-    if (e == 0) return 0ull;  // zero (energies are never subnormal here)
-    const unsigned long long m = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
-    const int sh = e - 127 + 9;
-    if (sh >= 0) return m << sh;
-    if (sh < -24) return 0ull;
-    return (m + (1ull << (-sh - 1))) >> (-sh);
-}
-__device__ __forceinline__ double from_fixed32(unsigned long long v) {
-    return (double)(long long)v * (1.0 / 4294967296.0);
-}
-
 struct Particle {
     float x, y, ux, uy, uz, E;
     unsigned long long lin;

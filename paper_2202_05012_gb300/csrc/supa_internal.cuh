@@ -35,6 +35,25 @@ struct GeomDev {
 constexpr int kSurIn = 6;       // features
 constexpr int kSurLayers = 30;  // predicted layers (start layer + 0..29)
 
+// Energy in 64-bit fixed point, units of 2^-32: E = m * 2^(e-23) with a 24-bit
+// significand m becomes m << (e + 9), exact for E >= 2^-9 and rounded to the
+// nearest unit below (ties up).  Integer shifts only: a float -> int64
+// conversion would run on the FP64 unit.  Energies are positive and below
+// 2^30 (checked per primary), so the sums cannot overflow.
+__device__ __forceinline__ unsigned long long fixed32(float E) {
+    const uint32_t bits = __float_as_uint(E);
+    const int e = (int)((bits >> 23) & 0xFFu);
+    if (e == 0) return 0ull;  // zero (energies are never subnormal here)
+    const unsigned long long m = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 127 + 9;
+    if (sh >= 0) return m << sh;
+    if (sh < -24) return 0ull;
+    return (m + (1ull << (-sh - 1))) >> (-sh);
+}
+__device__ __forceinline__ double from_fixed32(unsigned long long v) {
+    return (double)(long long)v * (1.0 / 4294967296.0);
+}
+
 // A diverted particle: where it is and what it carries.
 struct SurRec {
     uint32_t shower;  // index in the batch
@@ -66,12 +85,10 @@ __host__ __device__ inline void surrogate_features(float E, float ux, float uy, 
 }
 
 // Inference buffers for a queue of up to `cap` diverted particles (owned by
-// a batch): bf16 inputs and ping-pong hidden activations, f32 outputs [cap][64].
+// a batch): the network's outputs [cap][64] (f32).
 struct SurInfer {
     int cap = 0;
-    void *X0 = nullptr, *Ha = nullptr, *Hb = nullptr;
-    float *OUT = nullptr;
-    CUtensorMap mX0, mHa, mHb;
+    float *OUT = nullptr;  // network outputs [cap][64]
 };
 int surrogate_infer_init(supa_surrogate *s, int cap, SurInfer *inf);
 void surrogate_infer_free(SurInfer *inf);
@@ -90,6 +107,7 @@ struct SurParams {
     const float *zmid;
     uint64_t seed, shower_id_base;
     float *dep;             // [cap][30] drawn deposits
+    uint8_t *pcnt;          // [cap] hits per diverted particle
     double *lsum;
     int lsum_stride;
     double *sur_leak;       // [n]
@@ -100,6 +118,8 @@ struct SurParams {
 };
 cudaError_t launch_sur_deposits(const SurParams &p, cudaStream_t st);
 cudaError_t launch_sur_hits(const SurParams &p, cudaStream_t st);
+cudaError_t launch_export_diverted(const SurRec *rec, int64_t n, const supa_primary *prim, supa_primary *out,
+                                   cudaStream_t st);
 cudaError_t launch_add_counts(const uint32_t *a, const uint32_t *b, int64_t n, uint32_t *out, cudaStream_t st);
 cudaError_t launch_training_set(const supa_primary *prim, int64_t n, const GeomDev *geoms, const int8_t *s2l,
                                 const LayerInfo *linfo, const double *lsum, int stride, float e_s, float *x, float *y,

@@ -1,0 +1,322 @@
+// sur_mlp.cu -- inference of the surrogate network 6 -> 256 -> 256 -> 256 ->
+// 64 in one persistent kernel: the activations of a 128-row tile never leave
+// the SM.
+//
+// Per tile, layer l's accumulator lives in tensor memory (two 256-column
+// accumulators, alternating by layer), its epilogue (bias, GELU, BF16) writes
+// the activation straight into shared memory in the 128-byte-swizzled
+// K-major layout the next layer's tcgen05.mma reads, one 64-column K-block
+// at a time, and the MMAs of layer l+1 start on each K-block as soon as it
+// is written -- so the tensor core works while the epilogue is still busy
+// with the rest of the layer.  Only the 6 inputs (24 B) and the 64 outputs
+// (256 B) of a row touch HBM.
+//
+// Shared memory (230,400 B with alignment slack):
+//   X   2 x 16 KB   inputs of two tiles (bf16, columns 0..15 used, K = 16)
+//   H   64 KB       hidden activation, 4 K-blocks of 128 rows x 64 columns
+//   W1  32 KB       resident: 256 rows x 64 columns (columns 0..15 used)
+//   W4  32 KB       resident: 4 K-blocks of 64 rows x 64 columns
+//   S   2 x 32 KB   ring of W2 / W3 K-blocks (256 rows x 64 columns), TMA
+// Warps: 0 TMA producer, 1 tensor-memory owner and MMA issuer, 2-3 pack the
+// inputs of each tile, 4-19 epilogue (warp w reads TMEM lanes 32(w%4)..+31
+// and columns 16((w-4)/4)..+15 of every K-block).
+//
+// Every wait is bounded (about two seconds): on expiry the CTA sets the error
+// word, stops, lets its TMA loads and MMAs finish (bounded), frees tensor
+// memory and returns.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "tc_gemm.cuh"
+#include "tc_prims.cuh"
+
+namespace supa {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kMlpThreads = 640;
+constexpr int kRows = 128;
+constexpr uint32_t kXBytes = kRows * 128;    // one input tile
+constexpr uint32_t kHBlk = kRows * 128;      // one K-block of H
+constexpr uint32_t kWBlk = 256 * 128;        // one K-block of a 256-row weight
+constexpr uint32_t kW4Blk = 64 * 128;        // one K-block of W4
+constexpr uint32_t oX = 0, oH = 2 * kXBytes, oW1 = oH + 4 * kHBlk, oW4 = oW1 + kWBlk, oS = oW4 + 4 * kW4Blk;
+constexpr uint32_t kMlpSmem = oS + 2 * kWBlk + 1024;
+constexpr int kEpiWarps = 16;
+
+__global__ void __launch_bounds__(kMlpThreads, 1)
+    sur_mlp_kernel(const __grid_constant__ CUtensorMap tw1, const __grid_constant__ CUtensorMap tw2,
+                   const __grid_constant__ CUtensorMap tw3, const __grid_constant__ CUtensorMap tw4,
+                   const MlpInferArgs g) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t w_res;       // W1 and W4 resident
+    __shared__ __align__(8) uint64_t w_full[2];   // ring stage holds a K-block
+    __shared__ __align__(8) uint64_t w_empty[2];  // the MMAs have read the stage
+    __shared__ __align__(8) uint64_t x_full[2];   // input tile packed
+    __shared__ __align__(8) uint64_t x_empty[2];  // layer-1 MMA has read it
+    __shared__ __align__(8) uint64_t h_ready[4];  // K-block kb of H written
+    __shared__ __align__(8) uint64_t acc_full;    // a layer's accumulator is final
+    __shared__ __align__(8) uint64_t drain;       // all MMAs of this CTA done
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int M = g.rows;
+    if (g.count) M = (int)min((unsigned)M, *g.count);
+    const int tiles = (M + kRows - 1) / kRows;
+    if ((int)blockIdx.x >= tiles) return;
+    const int my_tiles = (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+
+    if (threadIdx.x == 0) {
+        mbar_init(&w_res, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&w_full[i], 1);
+            mbar_init(&w_empty[i], 1);
+            mbar_init(&x_full[i], 2);
+            mbar_init(&x_empty[i], 1);
+        }
+        for (int i = 0; i < 4; ++i) mbar_init(&h_ready[i], kEpiWarps);
+        mbar_init(&acc_full, 1);
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t acc0 = tmem, acc1 = tmem + 256;
+    volatile int *abort_v = &abort_flag;
+    auto fail = [&]() {
+        if (!*abort_v) atomicOr(g.error, kErrTimeout);
+        *abort_v = 1;
+    };
+
+    int issued = 0;  // ring loads issued by the producer
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer: resident W1, W4; then W2, W3 K-blocks per tile ----
+            mbar_expect_tx(&w_res, kWBlk + 4 * kW4Blk);
+            tma_load_2d(base + oW1, &tw1, 0, 0, &w_res);
+            for (int kb = 0; kb < 4; ++kb) tma_load_2d(base + oW4 + kb * kW4Blk, &tw4, kb * 64, 0, &w_res);
+            for (int t = 0; t < my_tiles && !*abort_v; ++t)
+                for (int layer = 2; layer <= 3 && !*abort_v; ++layer)
+                    for (int kb = 0; kb < 4; ++kb) {
+                        const int c = issued, s = c & 1;
+                        if (c >= 2 && !mbar_wait(&w_empty[s], ((c >> 1) - 1) & 1)) {
+                            fail();
+                            break;
+                        }
+                        if (*abort_v) break;
+                        mbar_expect_tx(&w_full[s], kWBlk);
+                        tma_load_2d(base + oS + s * kWBlk, layer == 2 ? &tw2 : &tw3, kb * 64, 0, &w_full[s]);
+                        issued = c + 1;
+                    }
+            if (*abort_v) {
+                // let the loads in flight land before the CTA exits
+                mbar_wait(&w_res, 0);
+                for (int i = max(0, issued - 2); i < issued; ++i) mbar_wait(&w_full[i & 1], (i >> 1) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            constexpr uint32_t id256 = idesc_bf16(kRows, 256), id64 = idesc_bf16(kRows, 64);
+            const uint32_t sX = smem_u32(base + oX), sH = smem_u32(base + oH), sW1 = smem_u32(base + oW1),
+                           sW4 = smem_u32(base + oW4), sS = smem_u32(base + oS);
+            bool ok = mbar_wait(&w_res, 0);
+            if (!ok) fail();
+            uint32_t hc = 0;  // completions of h_ready consumed (one per hidden layer)
+            int wc = 0;       // ring stages consumed
+            for (int t = 0; t < my_tiles && ok && !*abort_v; ++t) {
+                const int xb = t & 1;
+                if (!mbar_wait(&x_full[xb], (t >> 1) & 1)) {
+                    fail();
+                    break;
+                }
+                fence_after_sync();
+                // layer 1: K = 16 (6 inputs, zero padded), into accumulator 0
+                mma_bf16(acc0, sw128_desc(sX + xb * kXBytes), sw128_desc(sW1), id256, 0u);
+                mma_commit(&x_empty[xb]);
+                mma_commit(&acc_full);
+                // layers 2 and 3 from H, weights through the ring
+                for (int layer = 2; layer <= 3 && ok; ++layer) {
+                    const uint32_t acc = layer == 2 ? acc1 : acc0;
+                    for (int kb = 0; kb < 4; ++kb) {
+                        const int s = wc & 1;
+                        if (*abort_v || !mbar_wait(&h_ready[kb], hc & 1) || !mbar_wait(&w_full[s], (wc >> 1) & 1)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        fence_after_sync();
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma_bf16(acc, sw128_desc(sH + kb * kHBlk + k * 32), sw128_desc(sS + s * kWBlk + k * 32),
+                                     id256, (kb > 0 || k > 0) ? 1u : 0u);
+                        mma_commit(&w_empty[s]);
+                        ++wc;
+                    }
+                    ++hc;
+                    if (ok) mma_commit(&acc_full);
+                }
+                if (!ok) break;
+                // layer 4: 64 outputs from H and the resident W4, into accumulator 1
+                for (int kb = 0; kb < 4; ++kb) {
+                    if (*abort_v || !mbar_wait(&h_ready[kb], hc & 1)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    fence_after_sync();
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        mma_bf16(acc1, sw128_desc(sH + kb * kHBlk + k * 32), sw128_desc(sW4 + kb * kW4Blk + k * 32),
+                                 id64, (kb > 0 || k > 0) ? 1u : 0u);
+                }
+                ++hc;
+                if (!ok) break;
+                mma_commit(&acc_full);
+            }
+            // every MMA issued by this thread completes before tensor memory is freed
+            mma_commit(&drain);
+            mbar_wait(&drain, 0);
+        }
+    } else if (warp < 4) {
+        // ---- input packing: 6 features -> bf16, columns 6..15 zero ----
+        const int tid = threadIdx.x - 64;
+        for (int t = 0; t < my_tiles; ++t) {
+            const int xb = t & 1;
+            // warp-uniform decision (both warps of the packer take the same path)
+            if (!__all_sync(0xFFFFFFFFu, !*abort_v && (t < 2 || mbar_wait(&x_empty[xb], ((t >> 1) - 1) & 1)))) {
+                fail();
+                break;
+            }
+            const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kRows;
+            uint8_t *xs = base + oX + xb * kXBytes;
+            for (int r = tid; r < kRows; r += 64) {
+                const int row = m0 + r;
+                float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (row < M) {
+                    const float2 *src = reinterpret_cast<const float2 *>(g.x + (size_t)row * 6);
+                    const float2 a = src[0], b = src[1], c = src[2];
+                    f[0] = a.x; f[1] = a.y; f[2] = b.x; f[3] = b.y; f[4] = c.x; f[5] = c.y;
+                }
+                *reinterpret_cast<uint4 *>(xs + sw128_offset(r, 0)) =
+                    make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), 0u);
+                *reinterpret_cast<uint4 *>(xs + sw128_offset(r, 1)) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            fence_smem_to_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&x_full[xb]);
+        }
+    } else {
+        // ---- epilogue: 16 warps; warp (q, h) owns rows 32q.. and columns 16h.. of each K-block ----
+        const int q = warp & 3, h = (warp - 4) >> 2;
+        const int r = q * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        uint8_t *hs = base + oH;
+        uint32_t ac = 0;  // completions of acc_full consumed
+        for (int t = 0; t < my_tiles; ++t) {
+            const int row = ((int)blockIdx.x + t * (int)gridDim.x) * kRows + r;
+            bool ok = true;
+            for (int layer = 1; layer <= 3; ++layer) {
+                // warp-uniform, so that the .sync.aligned TMEM loads see the whole warp
+                if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full, ac & 1))) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                ++ac;
+                fence_after_sync();
+                const uint32_t acc = (layer == 2 ? acc1 : acc0) + lane_off;
+                const float *bias = layer == 1 ? g.b1 : layer == 2 ? g.b2 : g.b3;
+                for (int kb = 0; kb < 4; ++kb) {
+                    const int c0 = kb * 64 + h * 16;
+                    float v[16];
+                    tmem_ld16(acc + c0, v);
+                    const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
+                    uint32_t p[8];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 bb = __ldg(b4 + i);
+                        p[2 * i] = gelu2_bf16(__fadd2_rn(make_float2(v[4 * i], v[4 * i + 1]), make_float2(bb.x, bb.y)));
+                        p[2 * i + 1] =
+                            gelu2_bf16(__fadd2_rn(make_float2(v[4 * i + 2], v[4 * i + 3]), make_float2(bb.z, bb.w)));
+                    }
+                    uint8_t *blk = hs + kb * kHBlk;
+                    *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
+                    *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) = make_uint4(p[4], p[5], p[6], p[7]);
+                    fence_smem_to_async();
+                    fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&h_ready[kb]);
+                }
+            }
+            if (!ok) break;
+            if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full, ac & 1))) {
+                fail();
+                break;
+            }
+            ++ac;
+            fence_after_sync();
+            const int c0 = h * 16;
+            float v[16];
+            tmem_ld16(acc1 + lane_off + c0, v);
+            fence_before_sync();
+            if (row < M) {
+                float *o = g.out + (size_t)row * g.ld + c0;
+                if (c0 + 16 <= g.ncols && (g.ld & 3) == 0 && ((uintptr_t)g.out & 15) == 0) {
+                    const float4 *b4 = reinterpret_cast<const float4 *>(g.b4 + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 bb = __ldg(b4 + i);
+                        reinterpret_cast<float4 *>(o)[i] =
+                            make_float4(v[4 * i] + bb.x, v[4 * i + 1] + bb.y, v[4 * i + 2] + bb.z, v[4 * i + 3] + bb.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < g.ncols) o[j] = v[j] + g.b4[c0 + j];
+                }
+            }
+        }
+    }
+
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const CUtensorMap &w3,
+                           const CUtensorMap &w4, const MlpInferArgs &a, cudaStream_t st) {
+    if (a.rows < 0 || a.ncols < 0 || a.ncols > 64 || a.ld < a.ncols || !a.x || !a.out || !a.error ||
+        ((uintptr_t)a.x & 7))
+        return cudaErrorInvalidValue;
+    if (a.rows == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(sur_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = (a.rows + kRows - 1) / kRows;
+    sur_mlp_kernel<<<std::max(1, std::min(tiles, sms)), kMlpThreads, kMlpSmem, st>>>(w1, w2, w3, w4, a);
+    return cudaGetLastError();
+}
+
+}  // namespace supa

@@ -220,11 +220,11 @@ cudaError_t gemm(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs a, cudaS
     return launch_gemm(ta, tb, a, splits, st);
 }
 
-// Forward pass of one minibatch whose packed inputs are in X0/X0T.  train:
-// also keep pre-activations and transposed activations for the backward.
-cudaError_t forward(supa_surrogate *s, bool train, cudaStream_t st) {
+// Forward pass of one training minibatch whose packed inputs are in X0/X0T,
+// keeping pre-activations and transposed activations for the backward.
+cudaError_t forward(supa_surrogate *s, cudaStream_t st) {
     const int B = s->B;
-    const int ep = train ? EPI_BIAS_GELU : EPI_GELU_ONLY;
+    const int ep = EPI_BIAS_GELU;
     GemmArgs a = gargs(B, kHid, kInPad, ep, s->error);
     a.bias = s->master + Off::b1; a.out_f32 = s->Z1; a.out_bf16 = s->H1; a.outT_bf16 = s->H1T; a.ld = kHid; a.ldT = B;
     cudaError_t e = gemm(s->mX0, s->mW1, a, st);
@@ -316,11 +316,7 @@ void pack_params(const std::vector<float> &mst, float *p) {
 namespace supa {
 
 void surrogate_infer_free(SurInfer *inf) {
-    cudaFree(inf->X0);
-    cudaFree(inf->Ha);
-    cudaFree(inf->Hb);
     cudaFree(inf->OUT);
-    inf->X0 = inf->Ha = inf->Hb = nullptr;
     inf->OUT = nullptr;
     inf->cap = 0;
 }
@@ -328,41 +324,30 @@ void surrogate_infer_free(SurInfer *inf) {
 int surrogate_infer_init(supa_surrogate *s, int cap, SurInfer *inf) {
     (void)s;
     inf->cap = cap;
-    const size_t C = (size_t)cap;
-    if (cudaMalloc(&inf->X0, C * kInPad * 2) != cudaSuccess || cudaMalloc(&inf->Ha, C * kHid * 2) != cudaSuccess ||
-        cudaMalloc(&inf->Hb, C * kHid * 2) != cudaSuccess ||
-        cudaMalloc((void **)&inf->OUT, C * kOutPad * 4) != cudaSuccess) {
+    if (cudaMalloc((void **)&inf->OUT, (size_t)cap * kOutPad * 4) != cudaSuccess) {
         cudaGetLastError();
         surrogate_infer_free(inf);
         return set_last_error(SUPA_ERR_OOM, "surrogate queue buffers: out of device memory");
     }
-    int rc = make_bf16_map(&inf->mX0, inf->X0, C, kInPad, 128);
-    rc |= make_bf16_map(&inf->mHa, inf->Ha, C, kHid, 128);
-    rc |= make_bf16_map(&inf->mHb, inf->Hb, C, kHid, 128);
-    if (rc) {
-        surrogate_infer_free(inf);
-        return set_last_error(SUPA_ERR_CUDA, "surrogate queue buffers: cuTensorMapEncodeTiled failed");
-    }
     return SUPA_OK;
 }
 
+// The fused kernel over the first min(*count_dev, cap) rows of the queue.
 cudaError_t surrogate_infer_run(supa_surrogate *s, SurInfer *inf, const float *feat, const unsigned *count_dev,
                                 cudaStream_t st) {
-    const int C = inf->cap;
-    pack_inputs<<<(C + 255) / 256, 256, 0, st>>>(feat, C, count_dev, C, (__nv_bfloat16 *)inf->X0, nullptr);
-    GemmArgs a = gargs(C, kHid, kInPad, EPI_GELU_ONLY, s->error);
-    a.bias = s->master + Off::b1; a.out_bf16 = (__nv_bfloat16 *)inf->Ha; a.ld = kHid; a.m_dev = count_dev;
-    cudaError_t e = gemm(inf->mX0, s->mW1, a, st);
-    if (e != cudaSuccess) return e;
-    a = gargs(C, kHid, kHid, EPI_GELU_ONLY, s->error);
-    a.bias = s->master + Off::b2; a.out_bf16 = (__nv_bfloat16 *)inf->Hb; a.ld = kHid; a.m_dev = count_dev;
-    if ((e = gemm(inf->mHa, s->mW2, a, st)) != cudaSuccess) return e;
-    a = gargs(C, kHid, kHid, EPI_GELU_ONLY, s->error);
-    a.bias = s->master + Off::b3; a.out_bf16 = (__nv_bfloat16 *)inf->Ha; a.ld = kHid; a.m_dev = count_dev;
-    if ((e = gemm(inf->mHb, s->mW3, a, st)) != cudaSuccess) return e;
-    a = gargs(C, kOutPad, kHid, EPI_BIAS_F32, s->error);
-    a.bias = s->master + Off::b4; a.out_f32 = inf->OUT; a.ld = kOutPad; a.m_dev = count_dev;
-    return gemm(inf->mHa, s->mW4, a, st);
+    MlpInferArgs a{};
+    a.x = feat;
+    a.rows = inf->cap;
+    a.count = count_dev;
+    a.b1 = s->master + Off::b1;
+    a.b2 = s->master + Off::b2;
+    a.b3 = s->master + Off::b3;
+    a.b4 = s->master + Off::b4;
+    a.out = inf->OUT;
+    a.ld = kOutPad;
+    a.ncols = kOutPad;
+    a.error = s->error;
+    return launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4, a, st);
 }
 
 }  // namespace supa
@@ -464,7 +449,7 @@ int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float 
     if (cudaMemsetAsync(s->loss_tmp, 0, sizeof(double), st) != cudaSuccess)
         return sfail(SUPA_ERR_CUDA, "memset failed");
     pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, nullptr, s->B, s->X0, s->X0T);
-    cudaError_t e = forward(s, true, st);
+    cudaError_t e = forward(s, st);
     if (e == cudaSuccess) e = backward(s, y_dev, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("gradients: ") + cudaGetErrorString(e));
@@ -485,7 +470,7 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
     cudaStream_t st = (cudaStream_t)stream;
     double *loss = loss_acc_dev ? loss_acc_dev : s->loss_tmp;
     pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, nullptr, s->B, s->X0, s->X0T);
-    cudaError_t e = forward(s, true, st);
+    cudaError_t e = forward(s, st);
     if (e == cudaSuccess) {
         // backward() writes the minibatch loss into s->loss_tmp; point it at the accumulator
         double *keep = s->loss_tmp;
@@ -532,16 +517,21 @@ int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const floa
 int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, void *stream) {
     if (!s || (!x_dev && n > 0) || (!out_dev && n > 0))
         return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_forward: null argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    for (int64_t r0 = 0; r0 < n; r0 += s->B) {
-        const int64_t m = std::min<int64_t>(s->B, n - r0);
-        pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev + r0 * kIn, m, nullptr, s->B, s->X0, s->X0T);
-        cudaError_t e = forward(s, false, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(out_dev + r0 * kOut, kOut * 4, s->OUT, kOutPad * 4, kOut * 4, m,
-                                  cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));
-    }
+    if (n < 0 || n > INT32_MAX) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_forward: n out of range");
+    if ((uintptr_t)x_dev & 7) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_forward: x must be 8-byte aligned");
+    MlpInferArgs a{};
+    a.x = x_dev;
+    a.rows = (int)n;
+    a.b1 = s->master + Off::b1;
+    a.b2 = s->master + Off::b2;
+    a.b3 = s->master + Off::b3;
+    a.b4 = s->master + Off::b4;
+    a.out = out_dev;
+    a.ld = kOut;
+    a.ncols = kOut;
+    a.error = s->error;
+    const cudaError_t e = launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));
     return SUPA_OK;
 }
 

@@ -4,123 +4,13 @@
 #include <algorithm>
 
 #include "tc_gemm.cuh"
+#include "tc_prims.cuh"
 
 namespace supa {
 
 namespace {
 
-constexpr int kErrGemmTimeout = 8;
-constexpr long long kWaitCycles = 4000000000ll;  // about two seconds at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Wait until the phase of parity `parity` of the barrier has completed.
-// Bounded: returns false after about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];\n" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major tile stored as rows of 128
-// bytes with the 128-byte swizzle (the layout TMA writes with
-// CU_TENSOR_MAP_SWIZZLE_128B): 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address / 16
-    d |= (uint64_t)1 << 16;                            // leading byte offset (unused with this swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                            // descriptor version of tcgen05
-    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::f16: BF16 A and B, FP32 accumulator, both
-// operands K-major, M x N tile.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// erf for the GELU epilogues: the rational approximation of Abramowitz &
-// Stegun, Handbook of Mathematical Functions (1964), formula 7.1.26 (after
-// Hastings), |error| <= 1.5e-7 for x >= 0, extended by odd symmetry -- far
-// below the BF16 resolution of the stored activations.
-__device__ __forceinline__ float erf_as(float x) {
-    const float a = fabsf(x);
-    const float t = __frcp_rn(fmaf(0.3275911f, a, 1.0f));
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-    return copysignf(1.0f - poly * __expf(-a * a), x);
-}
-
-// GELU(z) = z Phi(z) with Phi(z) = (1 + erf(z / sqrt 2)) / 2; its derivative
-// Phi(z) + z phi(z), phi the standard normal density.
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
-
-__device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * __expf(-0.5f * z * z) * 0.39894228040143268f;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&h);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
+using namespace tc;
 
 // Warp roles: 0 issues TMA loads, 1 owns tensor memory and issues the MMAs,
 // 4..11 run the epilogue (warps 4+q and 8+q read TMEM lanes 32q..32q+31, one
@@ -229,10 +119,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const int quarter = warp & 3, half = (warp - 4) >> 2;
         for (int t = 0; t < my_tiles; ++t) {
             const int b = t & 1;
-            const bool ok = nkb > 0 && !*abort_v && mbar_wait(&done_bar[b], (t >> 1) & 1) && !*abort_v;
+            // warp-uniform, so that the .sync.aligned TMEM loads see the whole warp
+            const bool ok =
+                __all_sync(0xFFFFFFFFu, nkb > 0 && !*abort_v && mbar_wait(&done_bar[b], (t >> 1) & 1) && !*abort_v);
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             if (!ok) {
-                if (lane == 0 && nkb > 0) atomicOr(g.error, kErrGemmTimeout);
+                if (lane == 0 && nkb > 0) atomicOr(g.error, kErrTimeout);
                 *abort_v = 1;
                 break;
             }
@@ -257,7 +149,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                                                v[4 * j + 2] + g.bias[c0 + 4 * j + 2],
                                                v[4 * j + 3] + g.bias[c0 + 4 * j + 3]);
                     }
-                } else if (g.epi == EPI_BIAS_GELU || g.epi == EPI_GELU_ONLY) {
+                } else if (g.epi == EPI_BIAS_GELU) {
                     float h[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
@@ -265,22 +157,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         h[j] = gelu(v[j]);
                     }
                     if (live) {
-                        if (g.epi == EPI_BIAS_GELU) {
-                            float4 *z = reinterpret_cast<float4 *>(g.out_f32 + (size_t)row * g.ld + c0);
+                        float4 *z = reinterpret_cast<float4 *>(g.out_f32 + (size_t)row * g.ld + c0);
 #pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                z[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                        }
+                        for (int j = 0; j < 8; ++j)
+                            z[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                         uint4 *o = reinterpret_cast<uint4 *>(g.out_bf16 + (size_t)row * g.ld + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
                             o[j] = make_uint4(pack_bf16(h[8 * j], h[8 * j + 1]), pack_bf16(h[8 * j + 2], h[8 * j + 3]),
                                               pack_bf16(h[8 * j + 4], h[8 * j + 5]),
                                               pack_bf16(h[8 * j + 6], h[8 * j + 7]));
-                        if (g.epi == EPI_BIAS_GELU)
 #pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                g.outT_bf16[(size_t)(c0 + j) * g.ldT + row] = __float2bfloat16_rn(h[j]);
+                        for (int j = 0; j < 32; ++j)
+                            g.outT_bf16[(size_t)(c0 + j) * g.ldT + row] = __float2bfloat16_rn(h[j]);
                     }
                 } else if (g.epi == EPI_GELU_BWD) {
                     float d[32];

@@ -5,12 +5,13 @@
 //
 //   C[M x N] = A[M x K] * B[N x K]^T      (A, B bf16, K contiguous)
 //
-// One CTA owns a 128-row tile of C and all N <= 256 columns; blockIdx.y
-// splits K (split-K partial products are added with float atomics).
-// Warp 0 lane 0 issues TMA loads, warp 1 owns the TMEM allocation and its
-// lane 0 issues the MMAs, all eight warps run the epilogue (warps w and
-// w + 4 read TMEM lanes 32(w%4)..+31 = rows of the tile, one half of the
-// columns each).
+// A persistent CTA walks 128-row tiles of C (all N <= 256 columns each)
+// with two TMEM accumulators, so the epilogue of one tile overlaps the MMAs
+// of the next; blockIdx.y splits K (split-K partial products are added with
+// float atomics).  Warp 0 lane 0 issues TMA loads, warp 1 owns the TMEM
+// allocation and its lane 0 issues the MMAs, warps 4..11 run the epilogue
+// (warps 4+q and 8+q read TMEM lanes 32q..32q+31 = rows of the tile, one
+// half of the columns each).
 //
 // Every mbarrier wait is bounded: on expiry the CTA records an error code,
 // stops issuing work, drains what it issued (again bounded), frees its TMEM
@@ -27,7 +28,6 @@ enum GemmEpilogue : int {
     EPI_BIAS_F32 = 1,   // acc + bias -> f32
     EPI_GELU_BWD = 2,   // g = acc * gelu'(z); store g (bf16), its transpose, column sums (bias gradient)
     EPI_ATOMIC_F32 = 3, // out += acc (split-K partial products)
-    EPI_GELU_ONLY = 4,  // z = acc + bias; store gelu(z) (bf16) only (inference)
 };
 
 struct GemmArgs {
@@ -51,6 +51,22 @@ constexpr int kTileK = 64;
 
 size_t gemm_smem_bytes(int N);
 cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &a, int splits, cudaStream_t st);
+// The whole network 6 -> 256 -> 256 -> 256 -> 64 (GELU after the hidden
+// layers) in one persistent kernel for inference (sur_mlp.cu).
+struct MlpInferArgs {
+    const float *x;         // [rows][6] inputs
+    int rows;               // rows present, or the capacity when `count` is set
+    const unsigned *count;  // optional device row count: rows = min(rows, *count)
+    const float *b1, *b2, *b3, *b4;  // biases [256], [256], [256], [64]
+    float *out;             // [rows][ld] outputs, columns 0..ncols-1 written
+    int ld, ncols;
+    int *error;             // device error word (|= 8: a pipeline wait expired)
+};
+// w1: [256][64] in boxes of 256 rows; w2, w3: [256][256] in boxes of 256
+// rows; w4: [64][256] in boxes of 64 rows (make_bf16_map, K contiguous).
+cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const CUtensorMap &w3,
+                           const CUtensorMap &w4, const MlpInferArgs &a, cudaStream_t st);
+
 // Tensor map of a row-major bf16 matrix [rows][cols] (cols contiguous) read in
 // boxes of 64 columns x box_rows rows with the 128-byte swizzle.
 int make_bf16_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);

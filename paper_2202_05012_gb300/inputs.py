@@ -151,12 +151,12 @@ def workload_c1(n: int = 1000):
     return supa_d(10, grid=32, roi_mode=ROI_FIXED), primaries(n, 0, e_lo=1.0, e_hi=10.0)
 
 
-def workload_c2(n: int = 1_000_000):
+def workload_c2(n: int = 1_000_000, seed: int = 1):
     """1,000,000 showers, seed 1: E ~ U[1,100], polar angle U[0,30 deg],
     entry within +-1 cell, 30 layers, 30 x 64 x 64 grid centred on the
-    nominal shower axis."""
+    nominal shower axis (another seed: more showers of the same kind)."""
     g = supa_d(30, grid=64, roi_mode=ROI_AXIS)
-    return g, primaries(n, 1, e_lo=1.0, e_hi=100.0, theta_max_deg=30.0, entry_halfwidth=g.wx)
+    return g, primaries(n, seed, e_lo=1.0, e_hi=100.0, theta_max_deg=30.0, entry_halfwidth=g.wx)
 
 
 def workload_c3(n: int = 4_000_000):
@@ -166,8 +166,9 @@ def workload_c3(n: int = 4_000_000):
     return geoms, primaries(n, 2, e_lo=1.0, e_hi=1000.0, log_uniform=True, n_geoms=4)
 
 
-def workload_c5(n: int = 10_000_000):
+def workload_c5(n: int = 10_000_000, seed: int = 4):
     """10,000,000 showers, seed 4: E log-uniform [10,1000], polar angle
-    U[0,45 deg], 50 layers, 50 x 128 x 128 grid."""
+    U[0,45 deg], 50 layers, 50 x 128 x 128 grid (another seed: more showers
+    of the same kind)."""
     g = supa_d(50, grid=128, roi_mode=ROI_AXIS)
-    return g, primaries(n, 4, e_lo=10.0, e_hi=1000.0, log_uniform=True, theta_max_deg=45.0)
+    return g, primaries(n, seed, e_lo=10.0, e_hi=1000.0, log_uniform=True, theta_max_deg=45.0)

@@ -29,7 +29,7 @@ EXPORTED = (
     "supa_voxelize", "supa_voxelize_hits", "supa_autotune", "supa_surrogate_param_count", "supa_surrogate_create",
     "supa_surrogate_destroy", "supa_surrogate_get_params", "supa_surrogate_gradients", "supa_surrogate_train_step",
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
-    "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc",
+    "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc", "supa_export_diverted",
 )
 
 
@@ -118,6 +118,7 @@ def lib(build_if_missing: bool = True):
         L.supa_build_training_set.argtypes = [_VP, ctypes.c_float, _VP, _VP, _VP]
         L.supa_profiles.argtypes = [_VP, _I64, _I64, ctypes.c_int32, ctypes.c_float, _VP, _VP, _VP]
         L.supa_shower_offsets_noalloc.argtypes = [_VP, _I64, _VP, _VP]
+        L.supa_export_diverted.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I64), _VP]
         for name in EXPORTED[1:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -333,6 +334,17 @@ def supa_shower_offsets_noalloc(counts_dev, n: int, offsets_dev, stream=None):
 def supa_build_training_set(b: int, e_s: float, x_dev, y_dev, stream=None):
     _check(lib().supa_build_training_set(b, float(e_s), _ptr(x_dev), _ptr(y_dev), _stream(stream)),
            "supa_build_training_set")
+
+
+def supa_export_diverted(b: int, out_dev=None, stream=None) -> int:
+    """Diverted particles of the last hybrid run as sub-shower primaries into
+    out_dev (a uint8 tensor of 24-byte records, or None to only count);
+    returns how many the queue held."""
+    n = _I64(0)
+    cap = 0 if out_dev is None else out_dev.numel() * out_dev.element_size() // 24
+    _check(lib().supa_export_diverted(b, _ptr(out_dev) if cap else None, cap, ctypes.byref(n), _stream(stream)),
+           "supa_export_diverted")
+    return int(n.value)
 
 
 def pack_mlp_params(params) -> np.ndarray:

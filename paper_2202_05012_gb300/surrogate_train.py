@@ -2,6 +2,8 @@
 runs in the library's kernels).
 
   data = training_set(n, e_s, seed)            # plain-method sub-showers
+  data = training_set_matched(geom, prims, e_s, n, seed)   # ... started from
+                                               # the particles a workload diverts
   net, log = train(data, epochs, batch, lr)    # tcgen05 training epochs
   ... supa_batch_set_surrogate(batch, net, e_s, capacity) ...
 
@@ -46,6 +48,59 @@ def training_set(n: int, e_s: float, seed: int, n_layers: int = 30, device="cuda
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         return dict(x=x, y=y, n=n, e_s=e_s, seconds=dt, steps=info.n_steps)
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_destroy_geometry(gh)
+
+
+def training_set_matched(geom, prims, e_s: float, n_max: int, seed: int, device="cuda",
+                         shower_batch: int = 50_000):
+    """A training set matched to what the network replaces: the showers
+    `prims` of a workload run in hybrid mode (any network: only the queue of
+    particles diverted below e_s is used), those particles become sub-shower
+    primaries (supa_export_diverted), and each is simulated by the plain
+    method in the same geometry.  At most n_max samples."""
+    import torch
+    gh = S.supa_init_geometry(geom)
+    net = S.supa_surrogate_create(128, S.pack_mlp_params(inputs.mlp_init(0)))
+    d = S.primaries_to_device(prims, device)
+    mean_e = float(prims["E"].mean())
+    cap = int(4.0 * mean_e / e_s * shower_batch) + (1 << 20)
+    hb = S.supa_batch_create([gh], shower_batch,
+                             {"max_hits": int(shower_batch * max(400, 40 * mean_e)) + (8 << 20), "lpt_order": 1})
+    chunks, got = [], 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    try:
+        S.supa_batch_set_surrogate(hb, net, e_s, cap, S.SUPA_SURROGATE_MEAN)
+        for j in range(0, len(prims), shower_batch):
+            m = min(shower_batch, len(prims) - j)
+            S.supa_simulate(hb, d[j * 24:(j + m) * 24], m, seed, j)
+            S.supa_batch_get_info(hb)
+            k = min(S.supa_export_diverted(hb), n_max - got)
+            buf = torch.empty(k * 24, dtype=torch.uint8, device=device)
+            S.supa_export_diverted(hb, buf)
+            chunks.append(buf)
+            got += k
+            if got >= n_max:
+                break
+    finally:
+        S.supa_destroy_batch(hb)
+        S.supa_surrogate_destroy(net)
+    del d
+    sub = torch.cat(chunks)
+    del chunks
+    n = sub.numel() // 24
+    b = S.supa_batch_create([gh], n, {"max_hits": n * 80 + (4 << 20), "lpt_order": 1})
+    try:
+        S.supa_simulate(b, sub, n, seed + 1)
+        info = S.supa_batch_get_info(b)
+        x = torch.empty((n, 6), dtype=torch.float32, device=device)
+        y = torch.empty((n, 30), dtype=torch.float32, device=device)
+        S.supa_build_training_set(b, e_s, x, y)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return dict(x=x, y=y, n=n, e_s=e_s, seconds=dt, steps=info.n_steps, matched=True)
     finally:
         S.supa_destroy_batch(b)
         S.supa_destroy_geometry(gh)
