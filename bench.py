@@ -51,9 +51,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-hybrid", action="store_true", help="skip the plain-vs-surrogate comparison")
     ap.add_argument("--e-s", type=float, default=1.0, help="surrogate cutoff energy E_s")
-    ap.add_argument("--train-samples", type=int, default=2_000_000)
-    ap.add_argument("--epochs", type=int, default=5)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--train-samples", type=int, default=10_000_000)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--lr", type=float, default=2e-3, help="initial learning rate")
+    ap.add_argument("--lr-final", type=float, default=5e-5, help="learning rate of the last epoch (geometric decay)")
+    ap.add_argument("--train-showers", type=int, default=0,
+                    help="showers of the workload (another seed) whose diverted particles seed the training set")
     ap.add_argument("--pipeline", type=int, default=1,
                     help="sub-batches per step; >1 overlaps simulation of one with downsampling of the previous")
     return ap.parse_args()
@@ -628,21 +631,36 @@ def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor,
     return out
 
 
+def matched_training(args, T, make, e_s, mean_e):
+    """Training set from the particles that showers of the same workload
+    (another seed) divert below e_s, each simulated as a plain sub-shower;
+    then the Adam epochs.  Returns (net, training log)."""
+    # at least ~E / E_s diverted particles per shower; the set stops growing
+    # once train_samples are in
+    n_show = args.train_showers or int(min(2_000_000, max(50_000, 2.5 * args.train_samples * e_s / mean_e)))
+    g_t, p_t = make(n_show)
+    data = T.training_set_matched(g_t, p_t, e_s, args.train_samples, seed=5)
+    net, log = T.train(data, epochs=args.epochs, lr=args.lr, lr_final=args.lr_final)
+    return net, {"samples": data["n"], "data_seconds": data["seconds"], "training_showers": n_show,
+                 "set": "matched: diverted particles of the workload's showers (seed 11/14), stepped plainly",
+                 **log}
+
+
 def hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor, fbuf, plain):
-    """Train the surrogate on plain-method sub-showers, run the same showers
-    in hybrid mode, and compare throughput and profiles with the plain run."""
+    """Train the surrogate on sub-showers started from the particles the
+    workload diverts, run the same showers in hybrid mode, and compare
+    throughput and profiles with the plain run."""
+    from paper_2202_05012_gb300 import inputs
     from paper_2202_05012_gb300 import surrogate_train as T
-    data = T.training_set(args.train_samples, args.e_s, seed=3, n_layers=geom.n_layers)
-    net, log = T.train(data, epochs=args.epochs, lr=args.lr)
-    gen_s = data["seconds"]
-    del data
+    net, tlog = matched_training(args, T, lambda m: inputs.workload_c2(m, seed=11), args.e_s,
+                                 float(prims["E"].mean()))
     sub = 125_000
     L = geom.n_layers
     out = {"e_s": args.e_s, "plain_showers_per_s": n / (plain["step_ms"] / 1000.0),
            "plain_simulate_showers_per_s": n / (plain["simulate_ms"] / 1000.0),
            "plain_particle_steps_per_shower": plain["steps"] / n,
            "profile_binning": {"lateral_bins": PROFILE_BINS, "r_max": PROFILE_RMAX},
-           "training": {"samples": args.train_samples, "data_seconds": gen_s, **log},
+           "training": tlog,
            "note": "hybrid timed in 125k-shower sub-batches (network over each sub-batch's queue); plain as one "
                    "batch; same showers and seeds"}
     for mode, name in ((1, "mean"), (0, "sample")):
@@ -705,13 +723,11 @@ def run_surrogate(args):
            "c5_showers": n5, "plain": {"simulate_showers_per_s": n5 / (plain_ms / 1000.0),
                                        "particle_steps_per_shower": plain_steps / n5}, "sweep": []}
     for e_s in args.e_s_sweep:
-        data = T.training_set(args.train_samples, e_s, seed=3, n_layers=30)
-        net, log = T.train(data, epochs=args.epochs, lr=args.lr)
-        row = {"e_s": e_s, "training": {"data_seconds": data["seconds"], "samples": data["n"], **log}}
-        del data
+        net, tlog = matched_training(args, T, lambda m: inputs.workload_c5(m, seed=14), e_s, float(p5["E"].mean()))
+        row = {"e_s": e_s, "training": tlog}
         # sub-batches small enough that the queue (about 4 E / E_s particles
-        # per shower, ~2 KB each with the network's activations) stays < 40 GB
-        sub_h = max(1000, min(sub, int(16e6 * e_s / (4.0 * float(p5["E"].mean())))))
+        # per shower, ~1 KB each with outputs, deposits and hits) stays < 32 GB
+        sub_h = max(1000, min(sub, int(32e6 * e_s / (4.0 * float(p5["E"].mean())))))
         for mode, name in ((1, "mean"), (0, "sample")):
             prof = hybrid_run(S, gh, p5, d5, n5, 4, 0, net, e_s, sub_h, V, grid, oor, fbuf, L, True, mode=mode,
                               voxelize=False)

@@ -248,14 +248,17 @@ int supa_voxelize_hits(const supa_geometry *g, const float *hits_dev, const int6
  * per-layer deposits.  The network maps 6 features (log E, the direction
  * cosines u_x, u_y, u_z, the position of the start slice within its layer,
  * the number of layers left behind the start layer) through three hidden
- * layers of 256 with GELU to 60 outputs: means mu_j and log-variances s_j of
- * the deposit fractions of layers start + j, j = 0..29.  Loss: Gaussian
- * negative log-likelihood, mean over samples and layers.  Compute: BF16
+ * layers of 256 with GELU to 90 outputs: means mu_j and log-variances s_j of
+ * the deposit fractions of layers start + j, j = 0..29, and the mean lateral
+ * distances rho_j of those deposits from the particle's axis.  Targets:
+ * fractions y_j and energy-weighted mean distances R_j ([.][60]).  Loss,
+ * mean over samples and layers: (y_j - mu_j)^2 e^-s_j / 2 + s_j / 2
+ * + y_j (rho_j - R_j)^2 / 2.  Compute: BF16
  * tensor-core GEMMs (tcgen05, TMA) with FP32 accumulation, FP32 master
  * weights and Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  * Parameters are exchanged as a packed float32 vector of
  * supa_surrogate_param_count() values: W1 [256][6], b1 [256], W2 [256][256],
- * b2, W3 [256][256], b3, W4 [60][256], b4 [60] (row-major). */
+ * b2, W3 [256][256], b3, W4 [90][256], b4 [90] (row-major). */
 typedef struct supa_surrogate supa_surrogate;
 
 int32_t supa_surrogate_param_count(void);
@@ -265,21 +268,21 @@ int supa_surrogate_destroy(supa_surrogate *s);
 /* Current FP32 master parameters (synchronous). */
 int supa_surrogate_get_params(supa_surrogate *s, float *params_host);
 /* Loss and gradients of one minibatch without an update (synchronous):
- * x_dev float32 [batch][6], y_dev float32 [batch][30]. */
+ * x_dev float32 [batch][6], y_dev float32 [batch][60]. */
 int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float *y_dev, float *grads_host,
                              double *loss_host, void *stream);
 /* One Adam step on one minibatch (asynchronous); adds the minibatch loss to
  * *loss_acc_dev (device FP64) when it is not NULL. */
 int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float *y_dev, float lr,
                               double *loss_acc_dev, void *stream);
-/* One epoch over a training set of n samples (x_dev [n][6], y_dev [n][30]):
+/* One epoch over a training set of n samples (x_dev [n][6], y_dev [n][60]):
  * floor(n / batch) Adam steps on minibatches gathered in the order of the
  * permutation i -> (a i + c) mod n that `seed` picks.  Asynchronous; adds
  * each minibatch loss to *loss_acc_dev when it is not NULL. */
 int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,
                                float lr, double *loss_acc_dev, void *stream);
 /* Inference: x_dev float32 [n][6] (8-byte aligned) -> out_dev float32
- * [n][60], 0 <= n < 2^31, in one launch of the fused network kernel
+ * [n][90], 0 <= n < 2^31, in one launch of the fused network kernel
  * (asynchronous; a pipeline timeout shows in supa_surrogate_check). */
 int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, void *stream);
 /* Synchronise and report a tensor-core pipeline that gave up waiting
@@ -298,16 +301,20 @@ int supa_surrogate_check(supa_surrogate *s);
  * the next 30 layers, deposits follow `mode` (SUPA_SURROGATE_*; normals from
  * Philox keyed by shower, slice and lineage) and, scaled down when they add
  * up to more than E, are added to the layer sums and emitted as one hit per
- * non-empty layer (at the particle's straight-line position at the layer's
- * mid depth) after the shower's stepped hits.  The energy left over is
+ * non-empty layer after the shower's stepped hits: at the layer's mid depth,
+ * displaced from the particle's straight line by sigma_j (m1, m2) with
+ * sigma_j = max(0, rho_j) sqrt(2/pi) and standard normals m1, m2 (Philox
+ * stream tag 2, same keys).  The energy left over is
  * reported as sur_leak.  s = NULL or e_s <= 0 returns the batch to the plain
  * path.  s must outlive the batch.  Synchronous (allocates). */
 int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity, int32_t mode);
 
 /* Training set of the network from a plain simulation of sub-showers (each
  * primary entering on its start slice, see supa_primary.geom): x_dev float32
- * [n][6] features of the start, y_dev float32 [n][30] deposit fractions of
- * layers start + 0..29 (FP64 layer sums / E).  Synchronous. */
+ * [n][6] features of the start; y_dev float32 [n][60]: deposit fractions of
+ * layers start + 0..29 (FP64 layer sums / E), then the energy-weighted mean
+ * distance of each of those layers' hits from the sub-shower's axis (0 for
+ * an empty layer).  Synchronous. */
 int supa_build_training_set(supa_batch *b, float e_s, float *x_dev, float *y_dev, void *stream);
 
 /* The particles the last hybrid simulation of b diverted to the network, as

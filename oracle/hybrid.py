@@ -14,8 +14,18 @@ returns them):
      u2 = (w >> 8) 2^-24, z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2);
   4. d_j = E max(0, mu_j + exp(s_j / 2) n_j) for layers inside the
      detector, scaled by E / sum d when the sum exceeds E;
-  5. one hit per layer with d_j > 0 at the straight-line position at the
-     layer's mid depth.
+  5. one hit per layer with d_j > 0 at the layer's mid depth, displaced
+     from the particle's straight-line position by sigma_j (m1, m2):
+     sigma_j = max(0, rho_j) sqrt(2 / pi) (an isotropic 2-D Gaussian whose
+     mean distance is the predicted rho_j), (m1, m2) the Box-Muller pair of
+     Philox block j / 2 with counter (shower id, slice | 2 << 16 | block <<
+     20, lineage lo, lineage hi), words (w0, w1) for even j, (w2, w3) odd.
+
+training_targets() writes out the network's targets from a plain
+simulation of sub-showers: deposit fractions y_j of layers start + j and
+the energy-weighted mean distance R_j of those layers' hits from the
+sub-shower's axis (the straight line of its start direction through its
+entry point), 0 for an empty layer.
 """
 from __future__ import annotations
 
@@ -34,6 +44,55 @@ def features(div: dict, geom, e_s: float) -> np.ndarray:
     lay = div["layer"]
     return np.stack([np.log(div["E"] / e_s), div["ux"], div["uy"], div["uz"],
                      (div["k"] - first[lay]) / count[lay], np.minimum(1.0, (L - lay) / 30.0)], 1)
+
+
+def _box_muller(w0: int, w1: int):
+    u1 = ((int(w0) >> 8) + 1) * 2.0 ** -24
+    u2 = (int(w1) >> 8) * 2.0 ** -24
+    rad = math.sqrt(-2.0 * math.log(u1))
+    return rad * math.cos(2 * math.pi * u2), rad * math.sin(2 * math.pi * u2)
+
+
+def offset_normals(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
+    """[30, 2] standard normal pairs of the lateral hit displacements."""
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    m = np.zeros((30, 2))
+    for blk in range(15):
+        w = philox(((shower_id) & 0xFFFFFFFF, k | (2 << 16) | (blk << 20), lineage & 0xFFFFFFFF,
+                    (lineage >> 32) & 0xFFFFFFFF), key)
+        m[2 * blk] = _box_muller(w[0], w[1])
+        m[2 * blk + 1] = _box_muller(w[2], w[3])
+    return m
+
+
+def training_targets(geom, prims, res) -> np.ndarray:
+    """Y [n, 60] of sub-showers `prims` (start slice in geom >> 16) from
+    their plain simulation `res` (oracle.simulate)."""
+    s2l = np.asarray(geom.slice_to_layer)
+    L = int(geom.n_layers)
+    n = len(prims)
+    Y = np.zeros((n, 60))
+    off = res["offsets"]
+    for s in range(n):
+        k0 = int(prims["geom"][s]) >> 16
+        l0 = int(s2l[k0])
+        E0 = float(prims["E"][s])
+        m = min(30, L - l0)
+        Y[s, :m] = res["layer_sum"][s, l0:l0 + m] / E0
+        th, ph = float(prims["theta"][s]), float(prims["phi"][s])
+        tx, ty = math.tan(th) * math.cos(ph), math.tan(th) * math.sin(ph)
+        x0, y0, z0 = float(prims["x0"][s]), float(prims["y0"][s]), k0 * geom.dz
+        er = np.zeros(30)
+        e = np.zeros(30)
+        for h in range(off[s], off[s + 1]):
+            j = int(s2l[int(round(res["z"][h] / geom.dz))]) - l0
+            if 0 <= j < 30:
+                dz = res["z"][h] - z0
+                r = math.hypot(res["x"][h] - x0 - dz * tx, res["y"][h] - y0 - dz * ty)
+                er[j] += res["E"][h] * r
+                e[j] += res["E"][h]
+        Y[s, 30:] = np.where(e > 0, er / np.where(e > 0, e, 1.0), 0.0)
+    return Y
 
 
 def normals(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
@@ -55,7 +114,7 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
     """Per diverted particle: the drawn deposits d [n_div, 30] and the hits.
     mode 0: d_j = E max(0, mu_j + exp(s_j/2) n_j); mode 1: d_j = E max(0, mu_j)."""
     X = features(div, geom, e_s)
-    out, _ = mlp.forward(params, X) if len(X) else (np.zeros((0, 60)), None)
+    out, _ = mlp.forward(params, X) if len(X) else (np.zeros((0, 90)), None)
     L = int(geom.n_layers)
     s2l = np.asarray(geom.slice_to_layer)
     zmid = np.array([geom.dz * (np.nonzero(s2l == l)[0].min() + np.nonzero(s2l == l)[0].max()) * 0.5
@@ -75,9 +134,13 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
         if tot > E:
             d[i] *= E / tot
         zk = div["k"][i] * geom.dz
+        mo = offset_normals(shower_id_base + int(div["shower"][i]), int(div["k"][i]), int(div["lineage"][i]), seed)
         for j in range(30):
             if d[i, j] > 0:
                 zm = zmid[l0 + j]
-                hits.append((int(div["shower"][i]), div["x"][i] + (zm - zk) * div["ux"][i] / div["uz"][i],
-                             div["y"][i] + (zm - zk) * div["uy"][i] / div["uz"][i], zm, d[i, j], l0 + j))
+                sig = max(0.0, out[i, 60 + j]) * math.sqrt(2.0 / math.pi)
+                hits.append((int(div["shower"][i]),
+                             div["x"][i] + (zm - zk) * div["ux"][i] / div["uz"][i] + sig * mo[j, 0],
+                             div["y"][i] + (zm - zk) * div["uy"][i] / div["uz"][i] + sig * mo[j, 1], zm, d[i, j],
+                             l0 + j))
     return dict(d=d, out=out, hits=np.array(hits).reshape(-1, 6))

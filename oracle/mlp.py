@@ -3,10 +3,15 @@
 The surrogate has no counterpart in the SUPA paper: it is a small MLP that
 stands in for the low-energy tail of a shower (sub-showers below a cutoff
 energy E_s).  Architecture: 6 inputs -> 3 hidden layers of 256 with GELU
-(exact form x * Phi(x)) -> 60 outputs = 30 means mu_j and 30 log-variances
-s_j of the per-layer deposit fractions, layers counted from the sub-shower's
-start layer.  Loss: Gaussian negative log-likelihood averaged over layers and
-samples, L = mean_b (1/30) sum_j [ (y_j - mu_j)^2 exp(-s_j) / 2 + s_j / 2 ].
+(exact form x * Phi(x)) -> 90 outputs = 30 means mu_j and 30 log-variances
+s_j of the per-layer deposit fractions, and 30 mean lateral distances rho_j
+of each layer's deposits from the sub-shower's axis, layers counted from the
+sub-shower's start layer.  Targets Y = [y_j, R_j]: deposit fractions and
+energy-weighted mean distances.  Loss: Gaussian negative log-likelihood of
+the fractions plus the fraction-weighted squared error of the distances,
+averaged over layers and samples,
+  L = mean_b (1/30) sum_j [ (y_j - mu_j)^2 exp(-s_j) / 2 + s_j / 2
+                            + LAMBDA_R y_j (rho_j - R_j)^2 / 2 ].
 Optimiser: Adam (Kingma & Ba 2015) with bias correction.
 
 Plain numpy float64, one matrix formula per step; no fusion or reordering.
@@ -18,8 +23,9 @@ import math
 import numpy as np
 from scipy.special import erf
 
-N_IN, N_HID, N_OUT, N_LAYERS_OUT = 6, 256, 60, 30
+N_IN, N_HID, N_OUT, N_LAYERS_OUT = 6, 256, 90, 30
 SHAPES = [(N_HID, N_IN), (N_HID, N_HID), (N_HID, N_HID), (N_OUT, N_HID)]
+LAMBDA_R = 1.0  # weight of the lateral term
 
 
 def gelu(z):
@@ -33,7 +39,7 @@ def gelu_grad(z):
 
 def forward(params, X):
     """params: list of (W [out, in], b [out]); X [B, 6].  Returns the output
-    [B, 60] and the cache needed by backward."""
+    [B, 90] and the cache needed by backward."""
     acts = [X]
     pre = []
     h = X
@@ -45,20 +51,26 @@ def forward(params, X):
     return h, (acts, pre)
 
 
-def nll(out, Y):
-    """Gaussian NLL, mean over samples and the 30 layers."""
-    mu, s = out[:, :N_LAYERS_OUT], out[:, N_LAYERS_OUT:]
-    return float(np.mean(0.5 * (Y - mu) ** 2 * np.exp(-s) + 0.5 * s))
+def _split(out, Y):
+    J = N_LAYERS_OUT
+    return out[:, :J], out[:, J:2 * J], out[:, 2 * J:3 * J], Y[:, :J], Y[:, J:2 * J]
 
 
-def nll_grad(out, Y):
-    """d loss / d out, [B, 60]."""
+def loss(out, Y):
+    """The loss L above: mean over samples and the 30 layers."""
+    mu, s, rho, y, R = _split(out, Y)
+    return float(np.mean(0.5 * (y - mu) ** 2 * np.exp(-s) + 0.5 * s + 0.5 * LAMBDA_R * y * (rho - R) ** 2))
+
+
+def loss_grad(out, Y):
+    """d L / d out, [B, 90]."""
     B = out.shape[0]
-    mu, s = out[:, :N_LAYERS_OUT], out[:, N_LAYERS_OUT:]
-    r = Y - mu
+    mu, s, rho, y, R = _split(out, Y)
+    r = y - mu
     g_mu = -r * np.exp(-s) / (B * N_LAYERS_OUT)
     g_s = (0.5 - 0.5 * r * r * np.exp(-s)) / (B * N_LAYERS_OUT)
-    return np.concatenate([g_mu, g_s], axis=1)
+    g_rho = LAMBDA_R * y * (rho - R) / (B * N_LAYERS_OUT)
+    return np.concatenate([g_mu, g_s, g_rho], axis=1)
 
 
 def backward(params, cache, g_out):
@@ -77,7 +89,7 @@ def backward(params, cache, g_out):
 
 def loss_and_grads(params, X, Y):
     out, cache = forward(params, X)
-    return nll(out, Y), backward(params, cache, nll_grad(out, Y))
+    return loss(out, Y), backward(params, cache, loss_grad(out, Y))
 
 
 class Adam:

@@ -497,6 +497,7 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     sp.count = b->d_sq_count;
     sp.cap = b->sq_cap;
     sp.out = b->inf.OUT;
+    sp.out_ld = b->inf.ld;
     sp.prim = b->d_prim;
     sp.geoms = b->d_geoms;
     sp.zmid = b->d_zmid;
@@ -571,6 +572,17 @@ int supa_build_training_set(supa_batch *b, float e_s, float *x_dev, float *y_dev
     SUPA_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
     SUPA_CUDA(launch_training_set(b->d_prim, b->last_n, b->d_geoms, b->d_s2l, b->d_linfo, b->d_lsum, b->max_layers,
                                   e_s, x_dev, y_dev, bad, st));
+    LateralParams lp{};
+    lp.src.pool = b->d_pool;
+    lp.src.page_next = b->d_page_next;
+    lp.src.hit_start = b->d_hit_start;
+    lp.src.hit_count = b->d_hit_count;
+    lp.prim = b->d_prim;
+    lp.geoms = b->d_geoms;
+    lp.s2l = b->d_s2l;
+    lp.n = b->last_n;
+    lp.y = y_dev;
+    SUPA_CUDA(launch_lateral_targets(lp, st));
     int h = 0;
     SUPA_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     SUPA_CUDA(cudaStreamSynchronize(st));

@@ -377,6 +377,58 @@ __global__ void __launch_bounds__(256) supa_profile_kernel(const ProfileParams p
         if (pbins[i] != 0.0f) atomicAdd(&p.lat[i], (double)pbins[i] * inv);
 }
 
+// Training targets of the surrogate's lateral outputs: for a sub-shower
+// entering on slice k0 at (x0, y0) with direction (theta, phi), each hit
+// (x, y, z, E) of layer l0 + j (j = 0..29) lies at distance
+//   r = |(x, y) - (x0, y0) - (z - k0 dz) (tan theta cos phi, tan theta sin phi)|
+// from the sub-shower's axis; R_j = sum E r / sum E over the layer's hits,
+// 0 for an empty layer.  One warp per sub-shower, FP32 sums in shared memory.
+__global__ void __launch_bounds__(256) lateral_targets_kernel(const LateralParams p) {
+    __shared__ float er[8][32], es[8][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t s = (int64_t)blockIdx.x * 8 + w; s < p.n; s += (int64_t)gridDim.x * 8) {
+        er[w][lane] = 0.0f;
+        es[w][lane] = 0.0f;
+        __syncwarp();
+        const supa_primary pr = p.prim[s];
+        const GeomDev &g = p.geoms[pr.geom & 0xFFFFu];
+        const int k0 = (int)(pr.geom >> 16);
+        const int l0 = k0 < g.n_slices ? (int)p.s2l[g.slice_off + k0] : -1;
+        if (l0 >= 0) {
+            const float t = tanf(pr.theta);
+            const float tx = t * cosf(pr.phi), ty = t * sinf(pr.phi);
+            const float z0 = (float)k0 * g.dz;
+            ShowerHits it;
+            it.init(p.src, s);
+            if (it.remaining > 0) {
+                do {
+                    for (int j = lane; j < it.seg_len; j += 32) {
+                        const float4 h = __ldg(it.seg_ptr + j);
+                        const int k = (int)rintf(h.z / g.dz);
+                        const int jj = (k >= 0 && k < g.n_slices) ? (int)p.s2l[g.slice_off + k] - l0 : -1;
+                        if (jj >= 0 && jj < kSurLayers) {
+                            const float dz = h.z - z0;
+                            const float r = hypotf(h.x - fmaf(dz, tx, pr.x0), h.y - fmaf(dz, ty, pr.y0));
+                            atomicAdd(&er[w][jj], h.w * r);
+                            atomicAdd(&es[w][jj], h.w);
+                        }
+                    }
+                } while (it.next());
+            }
+        }
+        __syncwarp();
+        if (lane < kSurLayers)
+            p.y[s * 2 * kSurLayers + kSurLayers + lane] = es[w][lane] > 0.0f ? er[w][lane] / es[w][lane] : 0.0f;
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_lateral_targets(const LateralParams &p, cudaStream_t st) {
+    if (p.n <= 0) return cudaSuccess;
+    lateral_targets_kernel<<<(unsigned)std::min<int64_t>((p.n + 7) / 8, 16384), 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_profiles(const ProfileParams &p, cudaStream_t st) {
     if (p.n_showers <= 0) return cudaSuccess;
     supa_profile_kernel<<<(unsigned)p.n_showers, 256, p.nbins * sizeof(float), st>>>(p);

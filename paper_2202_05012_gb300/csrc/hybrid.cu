@@ -43,6 +43,23 @@ __device__ float lane_normal(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_
     return (lane & 1) ? rad * sn : rad * cs;
 }
 
+// Standard normal pair (m1, m2) displacing the hit of layer j = lane: Box-
+// Muller on Philox block j / 2 of the stream with tag 2 (same key), words
+// (w0, w1) for even j and (w2, w3) for odd j.
+__device__ float2 lane_offset_normals(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed,
+                                      int lane) {
+    const int blk = lane >> 1, pr = lane & 1;
+    const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (2u << 16) | ((uint32_t)blk << 20), lin_lo, lin_hi),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint32_t w0 = pr ? r.z : r.x, w1 = pr ? r.w : r.y;
+    const float u1 = (float)((w0 >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
+    const float u2 = u24(w1);
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    return make_float2(rad * cs, rad * sn);
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -114,7 +131,7 @@ __global__ void sur_deposits(const SurParams p) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const bool ld = k0 + u < m && lane < kSurLayers;
-                const float *o = p.out + (size_t)(g0 + k0 + u) * 64;
+                const float *o = p.out + (size_t)(g0 + k0 + u) * p.out_ld;
                 mu[u] = ld ? o[lane] : 0.0f;
                 sg[u] = (ld && sample) ? o[kSurLayers + lane] : 0.0f;
             }
@@ -173,7 +190,10 @@ __global__ void sur_deposits(const SurParams p) {
 // Per group of 32 queue entries, one cursor atomic per run of one shower
 // (segmented scan of the per-particle counts), then one particle at a time
 // with lane j writing the hit of layer start + j when its deposit is > 0 --
-// a particle's hits are consecutive, in layer order.
+// a particle's hits are consecutive, in layer order.  The hit sits at the
+// layer's mid depth, displaced from the particle's straight line by
+// sigma_j (m1, m2), sigma_j = max(0, rho_j) sqrt(2 / pi): an isotropic 2-D
+// Gaussian whose mean distance is the predicted rho_j.
 __global__ void sur_hits(const SurParams p) {
     const unsigned n = min(*p.count, (unsigned)p.cap);
     const int lane = threadIdx.x & 31;
@@ -184,13 +204,17 @@ __global__ void sur_hits(const SurParams p) {
         const unsigned i = g0 + lane;
         const int m = (int)min(32u, i1 - g0);
         const bool valid = lane < m;
-        int sh = -1 - lane, r_loff = 0;
+        int sh = -1 - lane, r_loff = 0, r_k = 0;
         unsigned c = 0;
+        uint32_t r_lo = 0, r_hi = 0;
         float r_x = 0.f, r_y = 0.f, r_tx = 0.f, r_ty = 0.f, r_zk = 0.f;
         if (valid) {
             const SurRec r = p.rec[i];
             sh = (int)r.shower;
             c = p.pcnt[i];
+            r_k = r.k;
+            r_lo = r.lin_lo;
+            r_hi = r.lin_hi;
             const GeomDev &g = p.geoms[p.prim[r.shower].geom & 0xFFFFu];
             r_loff = g.layer_off + r.layer;
             r_zk = (float)r.k * g.dz;
@@ -220,16 +244,21 @@ __global__ void sur_hits(const SurParams p) {
         base = __shfl_sync(kFull, base, end);
         const int64_t at_lane = valid ? p.soff[sh] + (int64_t)(base + run_exc) : 0;
         for (int k0 = 0; k0 < m; k0 += 8) {
-            float d[8];
+            float d[8], rho[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                d[u] = (k0 + u < m && lane < kSurLayers) ? p.dep[(size_t)(g0 + k0 + u) * kSurLayers + lane] : 0.0f;
+            for (int u = 0; u < 8; ++u) {
+                const bool ld = k0 + u < m && lane < kSurLayers;
+                d[u] = ld ? p.dep[(size_t)(g0 + k0 + u) * kSurLayers + lane] : 0.0f;
+                rho[u] = ld ? p.out[(size_t)(g0 + k0 + u) * p.out_ld + 2 * kSurLayers + lane] : 0.0f;
+            }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int k = k0 + u;
                 if (k >= m) break;
                 const int64_t at = __shfl_sync(kFull, at_lane, k);
-                const int loff = __shfl_sync(kFull, r_loff, k);
+                const int loff = __shfl_sync(kFull, r_loff, k), kk = __shfl_sync(kFull, r_k, k);
+                const uint32_t lo = __shfl_sync(kFull, r_lo, k), hi = __shfl_sync(kFull, r_hi, k);
+                const int sh_k = __shfl_sync(kFull, sh, k);
                 const float zk = __shfl_sync(kFull, r_zk, k), x = __shfl_sync(kFull, r_x, k),
                             y = __shfl_sync(kFull, r_y, k), tx = __shfl_sync(kFull, r_tx, k),
                             ty = __shfl_sync(kFull, r_ty, k);
@@ -237,7 +266,11 @@ __global__ void sur_hits(const SurParams p) {
                 if (d[u] > 0.0f) {
                     const float zm = p.zmid[loff + lane];
                     const float dz = zm - zk;
-                    p.hits[at + __popc(nz & lt)] = make_float4(fmaf(dz, tx, x), fmaf(dz, ty, y), zm, d[u]);
+                    const float sig = fmaxf(0.0f, rho[u]) * 0.79788456080286536f;  // sqrt(2 / pi)
+                    const float2 m12 =
+                        lane_offset_normals((uint32_t)(p.shower_id_base + (uint32_t)sh_k), kk, lo, hi, p.seed, lane);
+                    p.hits[at + __popc(nz & lt)] =
+                        make_float4(fmaf(sig, m12.x, fmaf(dz, tx, x)), fmaf(sig, m12.y, fmaf(dz, ty, y)), zm, d[u]);
                 }
             }
         }
@@ -251,7 +284,8 @@ __global__ void add_counts(const uint32_t *a, const uint32_t *b, int64_t n, uint
 
 // Training set of the surrogate from a batch of sub-showers: features of
 // each sub-shower's start and its deposit fractions per layer from the start
-// layer on.
+// layer on (columns 0..29 of y [n][60]; the mean distances, columns 30..59,
+// come from launch_lateral_targets).
 __global__ void training_set(const supa_primary *prim, int64_t n, const GeomDev *geoms, const int8_t *s2l,
                              const LayerInfo *linfo, const double *lsum, int stride, float e_s, float *x, float *y,
                              int *bad) {
@@ -271,7 +305,7 @@ __global__ void training_set(const supa_primary *prim, int64_t n, const GeomDev 
         surrogate_features(pr.E, st * cp, st * sp, ct, k0, l0, g.n_layers, linfo[g.layer_off + l0], e_s, f);
         for (int i = 0; i < kSurIn; ++i) x[s * kSurIn + i] = f[i];
         for (int j = 0; j < kSurLayers; ++j)
-            y[s * kSurLayers + j] =
+            y[s * 2 * kSurLayers + j] =
                 (l0 + j < g.n_layers) ? (float)(lsum[(size_t)s * stride + l0 + j] / (double)pr.E) : 0.0f;
     }
 }

@@ -85,10 +85,11 @@ __host__ __device__ inline void surrogate_features(float E, float ux, float uy, 
 }
 
 // Inference buffers for a queue of up to `cap` diverted particles (owned by
-// a batch): the network's outputs [cap][64] (f32).
+// a batch): the network's outputs (f32).
 struct SurInfer {
     int cap = 0;
-    float *OUT = nullptr;  // network outputs [cap][64]
+    int ld = 0;            // row stride of OUT
+    float *OUT = nullptr;  // network outputs [cap][ld]: mu 0..29, s 30..59, rho 60..89
 };
 int surrogate_infer_init(supa_surrogate *s, int cap, SurInfer *inf);
 void surrogate_infer_free(SurInfer *inf);
@@ -101,7 +102,8 @@ struct SurParams {
     const SurRec *rec;
     const unsigned *count;  // queue length (device)
     int cap;
-    const float *out;       // network outputs [cap][64]
+    const float *out;       // network outputs [cap][out_ld]: mu, s, rho (30 each)
+    int out_ld;
     const supa_primary *prim;
     const GeomDev *geoms;
     const float *zmid;
@@ -249,6 +251,17 @@ struct ProfileParams {
     double *longi, *lat;
 };
 cudaError_t launch_profiles(const ProfileParams &p, cudaStream_t st);
+
+// Training targets R_j (mean lateral distances) of a batch of sub-showers.
+struct LateralParams {
+    HitSource src;
+    const supa_primary *prim;
+    const GeomDev *geoms;
+    const int8_t *s2l;
+    int64_t n;
+    float *y;  // [n][60]: columns 30..59 written
+};
+cudaError_t launch_lateral_targets(const LateralParams &p, cudaStream_t st);
 
 struct FetchParams {
     HitSource src;

@@ -1,6 +1,6 @@
 // sur_mlp.cu -- inference of the surrogate network 6 -> 256 -> 256 -> 256 ->
-// 64 in one persistent kernel: the activations of a 128-row tile never leave
-// the SM.
+// 128 (90 used) in one persistent kernel: the activations of a 128-row tile
+// never leave the SM.
 //
 // Per tile, layer l's accumulator lives in tensor memory (two 256-column
 // accumulators, alternating by layer), its epilogue (bias, GELU, BF16) writes
@@ -8,18 +8,19 @@
 // K-major layout the next layer's tcgen05.mma reads, one 64-column K-block
 // at a time, and the MMAs of layer l+1 start on each K-block as soon as it
 // is written -- so the tensor core works while the epilogue is still busy
-// with the rest of the layer.  Only the 6 inputs (24 B) and the 64 outputs
-// (256 B) of a row touch HBM.
+// with the rest of the layer.  Only the 6 inputs (24 B) and the outputs of a
+// row touch HBM.
 //
 // Shared memory (230,400 B with alignment slack):
 //   X   2 x 16 KB   inputs of two tiles (bf16, columns 0..15 used, K = 16)
 //   H   64 KB       hidden activation, 4 K-blocks of 128 rows x 64 columns
-//   W1  32 KB       resident: 256 rows x 64 columns (columns 0..15 used)
-//   W4  32 KB       resident: 4 K-blocks of 64 rows x 64 columns
-//   S   2 x 32 KB   ring of W2 / W3 K-blocks (256 rows x 64 columns), TMA
+//   W4  64 KB       resident: 4 K-blocks of 128 rows x 64 columns
+//   S   2 x 32 KB   ring of 256-row x 64-column weight blocks, TMA: per tile
+//                   W1 (columns 0..15 used), then the 4 K-blocks of W2 and W3
 // Warps: 0 TMA producer, 1 tensor-memory owner and MMA issuer, 2-3 pack the
 // inputs of each tile, 4-19 epilogue (warp w reads TMEM lanes 32(w%4)..+31
-// and columns 16((w-4)/4)..+15 of every K-block).
+// and columns 16((w-4)/4)..+15 of every K-block; 32((w-4)/4)..+31 of the
+// output layer).
 //
 // Every wait is bounded (about two seconds): on expiry the CTA sets the error
 // word, stops, lets its TMA loads and MMAs finish (bounded), frees tensor
@@ -42,8 +43,8 @@ constexpr int kRows = 128;
 constexpr uint32_t kXBytes = kRows * 128;    // one input tile
 constexpr uint32_t kHBlk = kRows * 128;      // one K-block of H
 constexpr uint32_t kWBlk = 256 * 128;        // one K-block of a 256-row weight
-constexpr uint32_t kW4Blk = 64 * 128;        // one K-block of W4
-constexpr uint32_t oX = 0, oH = 2 * kXBytes, oW1 = oH + 4 * kHBlk, oW4 = oW1 + kWBlk, oS = oW4 + 4 * kW4Blk;
+constexpr uint32_t kW4Blk = 128 * 128;       // one K-block of W4
+constexpr uint32_t oX = 0, oH = 2 * kXBytes, oW4 = oH + 4 * kHBlk, oS = oW4 + 4 * kW4Blk;
 constexpr uint32_t kMlpSmem = oS + 2 * kWBlk + 1024;
 constexpr int kEpiWarps = 16;
 
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                    const __grid_constant__ CUtensorMap tw3, const __grid_constant__ CUtensorMap tw4,
                    const MlpInferArgs g) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t w_res;       // W1 and W4 resident
+    __shared__ __align__(8) uint64_t w_res;       // W4 resident
     __shared__ __align__(8) uint64_t w_full[2];   // ring stage holds a K-block
     __shared__ __align__(8) uint64_t w_empty[2];  // the MMAs have read the stage
     __shared__ __align__(8) uint64_t x_full[2];   // input tile packed
@@ -105,23 +106,23 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     int issued = 0;  // ring loads issued by the producer
     if (warp == 0) {
         if (lane == 0) {
-            // ---- TMA producer: resident W1, W4; then W2, W3 K-blocks per tile ----
-            mbar_expect_tx(&w_res, kWBlk + 4 * kW4Blk);
-            tma_load_2d(base + oW1, &tw1, 0, 0, &w_res);
+            // ---- TMA producer: resident W4; then W1 and the W2, W3 K-blocks per tile ----
+            mbar_expect_tx(&w_res, 4 * kW4Blk);
             for (int kb = 0; kb < 4; ++kb) tma_load_2d(base + oW4 + kb * kW4Blk, &tw4, kb * 64, 0, &w_res);
             for (int t = 0; t < my_tiles && !*abort_v; ++t)
-                for (int layer = 2; layer <= 3 && !*abort_v; ++layer)
-                    for (int kb = 0; kb < 4; ++kb) {
-                        const int c = issued, s = c & 1;
-                        if (c >= 2 && !mbar_wait(&w_empty[s], ((c >> 1) - 1) & 1)) {
-                            fail();
-                            break;
-                        }
-                        if (*abort_v) break;
-                        mbar_expect_tx(&w_full[s], kWBlk);
-                        tma_load_2d(base + oS + s * kWBlk, layer == 2 ? &tw2 : &tw3, kb * 64, 0, &w_full[s]);
-                        issued = c + 1;
+                for (int blk = 0; blk < 9 && !*abort_v; ++blk) {
+                    const int c = issued, s = c & 1;
+                    if (c >= 2 && !mbar_wait(&w_empty[s], ((c >> 1) - 1) & 1)) {
+                        fail();
+                        break;
                     }
+                    if (*abort_v) break;
+                    const CUtensorMap *map = blk == 0 ? &tw1 : blk <= 4 ? &tw2 : &tw3;
+                    const int kb = blk == 0 ? 0 : (blk - 1) & 3;
+                    mbar_expect_tx(&w_full[s], kWBlk);
+                    tma_load_2d(base + oS + s * kWBlk, map, kb * 64, 0, &w_full[s]);
+                    issued = c + 1;
+                }
             if (*abort_v) {
                 // let the loads in flight land before the CTA exits
                 mbar_wait(&w_res, 0);
@@ -131,22 +132,24 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
-            constexpr uint32_t id256 = idesc_bf16(kRows, 256), id64 = idesc_bf16(kRows, 64);
-            const uint32_t sX = smem_u32(base + oX), sH = smem_u32(base + oH), sW1 = smem_u32(base + oW1),
-                           sW4 = smem_u32(base + oW4), sS = smem_u32(base + oS);
+            constexpr uint32_t id256 = idesc_bf16(kRows, 256), id128 = idesc_bf16(kRows, 128);
+            const uint32_t sX = smem_u32(base + oX), sH = smem_u32(base + oH), sW4 = smem_u32(base + oW4),
+                           sS = smem_u32(base + oS);
             bool ok = mbar_wait(&w_res, 0);
             if (!ok) fail();
             uint32_t hc = 0;  // completions of h_ready consumed (one per hidden layer)
             int wc = 0;       // ring stages consumed
             for (int t = 0; t < my_tiles && ok && !*abort_v; ++t) {
                 const int xb = t & 1;
-                if (!mbar_wait(&x_full[xb], (t >> 1) & 1)) {
+                if (!mbar_wait(&x_full[xb], (t >> 1) & 1) || !mbar_wait(&w_full[wc & 1], (wc >> 1) & 1)) {
                     fail();
                     break;
                 }
                 fence_after_sync();
-                // layer 1: K = 16 (6 inputs, zero padded), into accumulator 0
-                mma_bf16(acc0, sw128_desc(sX + xb * kXBytes), sw128_desc(sW1), id256, 0u);
+                // layer 1: K = 16 (6 inputs, zero padded), W1 from the ring, into accumulator 0
+                mma_bf16(acc0, sw128_desc(sX + xb * kXBytes), sw128_desc(sS + (wc & 1) * kWBlk), id256, 0u);
+                mma_commit(&w_empty[wc & 1]);
+                ++wc;
                 mma_commit(&x_empty[xb]);
                 mma_commit(&acc_full);
                 // layers 2 and 3 from H, weights through the ring
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                     if (ok) mma_commit(&acc_full);
                 }
                 if (!ok) break;
-                // layer 4: 64 outputs from H and the resident W4, into accumulator 1
+                // layer 4: 128 outputs from H and the resident W4, into accumulator 1
                 for (int kb = 0; kb < 4; ++kb) {
                     if (*abort_v || !mbar_wait(&h_ready[kb], hc & 1)) {
                         fail();
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         mma_bf16(acc1, sw128_desc(sH + kb * kHBlk + k * 32), sw128_desc(sW4 + kb * kW4Blk + k * 32),
-                                 id64, (kb > 0 || k > 0) ? 1u : 0u);
+                                 id128, (kb > 0 || k > 0) ? 1u : 0u);
                 }
                 ++hc;
                 if (!ok) break;
@@ -270,23 +273,23 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             }
             ++ac;
             fence_after_sync();
-            const int c0 = h * 16;
-            float v[16];
-            tmem_ld16(acc1 + lane_off + c0, v);
+            const int c0 = h * 32;
+            float v[32];
+            tmem_ld32(acc1 + lane_off + c0, v);
             fence_before_sync();
-            if (row < M) {
+            if (row < M && c0 < g.ncols) {
                 float *o = g.out + (size_t)row * g.ld + c0;
-                if (c0 + 16 <= g.ncols && (g.ld & 3) == 0 && ((uintptr_t)g.out & 15) == 0) {
+                if (c0 + 32 <= g.ncols && (g.ld & 3) == 0 && ((uintptr_t)g.out & 15) == 0) {
                     const float4 *b4 = reinterpret_cast<const float4 *>(g.b4 + c0);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < 8; ++i) {
                         const float4 bb = __ldg(b4 + i);
                         reinterpret_cast<float4 *>(o)[i] =
                             make_float4(v[4 * i] + bb.x, v[4 * i + 1] + bb.y, v[4 * i + 2] + bb.z, v[4 * i + 3] + bb.w);
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
+                    for (int j = 0; j < 32; ++j)
                         if (c0 + j < g.ncols) o[j] = v[j] + g.b4[c0 + j];
                 }
             }
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
 
 cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const CUtensorMap &w3,
                            const CUtensorMap &w4, const MlpInferArgs &a, cudaStream_t st) {
-    if (a.rows < 0 || a.ncols < 0 || a.ncols > 64 || a.ld < a.ncols || !a.x || !a.out || !a.error ||
+    if (a.rows < 0 || a.ncols < 0 || a.ncols > 128 || a.ld < a.ncols || !a.x || !a.out || !a.error ||
         ((uintptr_t)a.x & 7))
         return cudaErrorInvalidValue;
     if (a.rows == 0) return cudaSuccess;

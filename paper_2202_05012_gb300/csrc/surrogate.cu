@@ -1,13 +1,18 @@
 // surrogate.cu -- the BF16 tensor-core surrogate network of the hybrid path
-// (no counterpart in the SUPA paper): an MLP 6 -> 256 -> 256 -> 256 -> 60
-// with exact GELU, trained with a Gaussian negative log-likelihood and Adam,
-// evaluated in minibatches of `batch` rows.
+// (no counterpart in the SUPA paper): an MLP 6 -> 256 -> 256 -> 256 -> 90
+// with exact GELU -- per layer j = 0..29 from the start layer the mean mu_j
+// and log-variance s_j of the deposit fraction and the mean lateral distance
+// rho_j of the deposits from the particle's axis -- trained with Adam on
+//   L = mean (1/30) sum_j [(y_j - mu_j)^2 e^-s_j / 2 + s_j / 2
+//                          + y_j (rho_j - R_j)^2 / 2]
+// (targets: fractions y_j, energy-weighted mean distances R_j), evaluated
+// in minibatches of `batch` rows.
 //
 // Layout.  Every GEMM is C = A * B^T with both operands K-major (tc_gemm.cuh),
 // so the engine keeps each activation in both orientations (the forward
 // epilogue writes h and h^T) and each weight as W and W^T in BF16, next to
 // FP32 master weights and Adam moments.  The 6 inputs are padded to 64
-// columns and the 60 outputs to 64 rows; the padding stays exactly zero
+// columns and the 90 outputs to 128 rows; the padding stays exactly zero
 // (zero inputs and zero output gradients give zero updates).
 //
 // Training step: pack inputs -> 4 forward GEMMs (bias+GELU epilogues) ->
@@ -29,7 +34,10 @@ using namespace supa;
 
 namespace {
 
-constexpr int kIn = 6, kInPad = 64, kHid = 256, kOut = 60, kOutPad = 64, kLayersOut = 30;
+constexpr int kIn = 6, kInPad = 64, kHid = 256, kOut = 90, kOutPad = 128, kLayersOut = 30;
+constexpr int kY = 2 * kLayersOut;  // target columns: fractions, mean distances
+constexpr int kInferLd = 96;        // row stride of the inference outputs (>= kOut, multiple of 4)
+static_assert(kOutPad == kTileM, "d out^T is read as one full 128-row tile");
 // packed user parameter vector: W1, b1, W2, b2, W3, b3, W4, b4
 constexpr int kNParams = kHid * kIn + kHid + 2 * (kHid * kHid + kHid) + kOut * kHid + kOut;
 
@@ -66,7 +74,7 @@ __global__ void pack_inputs(const float *x, int64_t n, const unsigned *n_dev, in
         for (int j = 0; j < kInPad; ++j) X0T[(size_t)j * B + r] = __float2bfloat16_rn(j < kIn ? v[j] : 0.0f);
 }
 
-// Gaussian NLL over the 30 layers, mean over the batch: writes d loss / d out
+// The loss L over the 30 layers, mean over the batch: writes d L / d out
 // (bf16, both orientations; padding columns zero), adds the bias gradient of
 // the last layer and the loss sum.
 __global__ void nll_loss(const float *out, const float *y, int B, __nv_bfloat16 *G4, __nv_bfloat16 *G4T, float *gb4,
@@ -81,34 +89,40 @@ __global__ void nll_loss(const float *out, const float *y, int B, __nv_bfloat16 
     double l = 0.0;
     const float inv = 1.0f / (float)(B * kLayersOut);
     for (int j = 0; j < kLayersOut; ++j) {
-        float gmu = 0.0f, gs = 0.0f;
+        float gmu = 0.0f, gs = 0.0f, gr = 0.0f;
         if (live) {
-            const float mu = out[(size_t)r * kOutPad + j], s = out[(size_t)r * kOutPad + kLayersOut + j];
-            const float res = y[(size_t)r * kLayersOut + j] - mu;
+            const float *o = out + (size_t)r * kOutPad;
+            const float mu = o[j], s = o[kLayersOut + j], rho = o[2 * kLayersOut + j];
+            const float yj = y[(size_t)r * kY + j], dr = rho - y[(size_t)r * kY + kLayersOut + j];
+            const float res = yj - mu;
             const float e = expf(-s);
-            l += 0.5 * (double)(res * res * e) + 0.5 * (double)s;
+            l += 0.5 * (double)(res * res * e) + 0.5 * (double)s + 0.5 * (double)(yj * dr * dr);
             gmu = -res * e * inv;
             gs = (0.5f - 0.5f * res * res * e) * inv;
-            G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(gmu);
-            G4[(size_t)r * kOutPad + kLayersOut + j] = __float2bfloat16_rn(gs);
+            gr = yj * dr * inv;
+            __nv_bfloat16 *g4 = G4 + (size_t)r * kOutPad;
+            g4[j] = __float2bfloat16_rn(gmu);
+            g4[kLayersOut + j] = __float2bfloat16_rn(gs);
+            g4[2 * kLayersOut + j] = __float2bfloat16_rn(gr);
             G4T[(size_t)j * B + r] = __float2bfloat16_rn(gmu);
             G4T[(size_t)(kLayersOut + j) * B + r] = __float2bfloat16_rn(gs);
+            G4T[(size_t)(2 * kLayersOut + j) * B + r] = __float2bfloat16_rn(gr);
         }
         // bias gradient: column sums, one shared atomic per warp and column
         for (int o = 16; o > 0; o >>= 1) {
             gmu += __shfl_xor_sync(0xFFFFFFFFu, gmu, o);
             gs += __shfl_xor_sync(0xFFFFFFFFu, gs, o);
+            gr += __shfl_xor_sync(0xFFFFFFFFu, gr, o);
         }
         if (lane == 0) {
             atomicAdd(&colsum[j], gmu);
             atomicAdd(&colsum[kLayersOut + j], gs);
+            atomicAdd(&colsum[2 * kLayersOut + j], gr);
         }
     }
     if (live)
-        for (int j = kOut; j < kOutPad; ++j) {
-            G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(0.0f);
-            G4T[(size_t)j * B + r] = __float2bfloat16_rn(0.0f);
-        }
+        for (int j = kOut; j < kOutPad; ++j) G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(0.0f);
+    // (rows kOut.. of G4T are zero from creation and never written)
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
     __syncthreads();
@@ -133,14 +147,14 @@ __global__ void adam_update(float *p, float *m, float *v, const float *g, size_t
     }
 }
 
-// Rows (a i + c) mod n, i = i0 .. i0 + B - 1, of x [n][6] and y [n][30].
+// Rows (a i + c) mod n, i = i0 .. i0 + B - 1, of x [n][6] and y [n][60].
 __global__ void gather_rows(const float *x, const float *y, int64_t n, uint64_t a, uint64_t c, int64_t i0, int B,
                             float *xs, float *ys) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= B) return;
     const uint64_t src = (a * (uint64_t)(i0 + r) + c) % (uint64_t)n;
     for (int j = 0; j < kIn; ++j) xs[(size_t)r * kIn + j] = x[src * kIn + j];
-    for (int j = 0; j < kLayersOut; ++j) ys[(size_t)r * kLayersOut + j] = y[src * kLayersOut + j];
+    for (int j = 0; j < kY; ++j) ys[(size_t)r * kY + j] = y[src * kY + j];
 }
 
 // BF16 copies of a master weight [rows][cols]: W and (optionally) W^T.
@@ -324,7 +338,8 @@ void surrogate_infer_free(SurInfer *inf) {
 int surrogate_infer_init(supa_surrogate *s, int cap, SurInfer *inf) {
     (void)s;
     inf->cap = cap;
-    if (cudaMalloc((void **)&inf->OUT, (size_t)cap * kOutPad * 4) != cudaSuccess) {
+    inf->ld = kInferLd;
+    if (cudaMalloc((void **)&inf->OUT, (size_t)cap * kInferLd * 4) != cudaSuccess) {
         cudaGetLastError();
         surrogate_infer_free(inf);
         return set_last_error(SUPA_ERR_OOM, "surrogate queue buffers: out of device memory");
@@ -344,8 +359,8 @@ cudaError_t surrogate_infer_run(supa_surrogate *s, SurInfer *inf, const float *f
     a.b3 = s->master + Off::b3;
     a.b4 = s->master + Off::b4;
     a.out = inf->OUT;
-    a.ld = kOutPad;
-    a.ncols = kOutPad;
+    a.ld = kInferLd;
+    a.ncols = kOut;
     a.error = s->error;
     return launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4, a, st);
 }
@@ -379,11 +394,11 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
               grab(s, &s->X0, B * kInPad) && grab(s, &s->X0T, B * kInPad) && grab(s, &s->H1, B * kHid) &&
               grab(s, &s->H2, B * kHid) && grab(s, &s->H3, B * kHid) && grab(s, &s->H1T, B * kHid) &&
               grab(s, &s->H2T, B * kHid) && grab(s, &s->H3T, B * kHid) && grab(s, &s->G4, B * kOutPad) &&
-              grab(s, &s->G4T, B * kTileM) && grab(s, &s->G3, B * kHid) && grab(s, &s->G2, B * kHid) &&
+              grab(s, &s->G4T, B * kOutPad) && grab(s, &s->G3, B * kHid) && grab(s, &s->G2, B * kHid) &&
               grab(s, &s->G1, B * kHid) && grab(s, &s->G3T, B * kHid) && grab(s, &s->G2T, B * kHid) &&
               grab(s, &s->G1T, B * kHid) && grab(s, &s->Z1, B * kHid) && grab(s, &s->Z2, B * kHid) &&
               grab(s, &s->Z3, B * kHid) && grab(s, &s->OUT, B * kOutPad) && grab(s, &s->loss_tmp, 1) &&
-              grab(s, &s->error, 1) && grab(s, &s->Xs, B * kIn) && grab(s, &s->Ys, B * kLayersOut);
+              grab(s, &s->error, 1) && grab(s, &s->Xs, B * kIn) && grab(s, &s->Ys, B * kY);
     if (!ok) {
         supa_surrogate_destroy(s);
         return sfail(SUPA_ERR_OOM, "supa_surrogate_create: out of device memory");
@@ -397,9 +412,9 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
     rc |= make_bf16_map(&s->mG4, s->G4, B, kOutPad, 128);
     rc |= make_bf16_map(&s->mG3, s->G3, B, kHid, 128);
     rc |= make_bf16_map(&s->mG2, s->G2, B, kHid, 128);
-    // d out^T is read as the A operand of the 64-row weight gradient: it is
-    // kept 128 rows high (rows 64..127 stay zero) so every load is one full tile
-    rc |= make_bf16_map(&s->mG4T, s->G4T, kTileM, B, 128);
+    // d out^T is read as the A operand of the 128-row weight gradient (rows
+    // 90..127 stay zero)
+    rc |= make_bf16_map(&s->mG4T, s->G4T, kOutPad, B, 128);
     rc |= make_bf16_map(&s->mG3T, s->G3T, kHid, B, 128);
     rc |= make_bf16_map(&s->mG2T, s->G2T, kHid, B, 128);
     rc |= make_bf16_map(&s->mG1T, s->G1T, kHid, B, 128);
@@ -424,7 +439,7 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
     if (e == cudaSuccess) e = cudaMemset(s->m, 0, Off::total * 4);
     if (e == cudaSuccess) e = cudaMemset(s->v, 0, Off::total * 4);
     if (e == cudaSuccess) e = cudaMemset(s->error, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(s->G4T, 0, B * kTileM * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMemset(s->G4T, 0, B * kOutPad * sizeof(__nv_bfloat16));
     if (e != cudaSuccess || weight_copies(s, 0) != SUPA_OK || cudaDeviceSynchronize() != cudaSuccess) {
         supa_surrogate_destroy(s);
         return sfail(SUPA_ERR_CUDA, "supa_surrogate_create: upload failed");

@@ -115,7 +115,7 @@ def primaries(n: int, seed: int, *, e_lo: float, e_hi: float, log_uniform: bool 
     return p
 
 
-def mlp_init(seed: int, shapes=((256, 6), (256, 256), (256, 256), (60, 256))):
+def mlp_init(seed: int, shapes=((256, 6), (256, 256), (256, 256), (90, 256))):
     """Seeded initial parameters of the surrogate network: weights
     U(-1/sqrt(fan_in), 1/sqrt(fan_in)), biases zero; float64 [(W, b)]."""
     rng = np.random.Generator(np.random.PCG64(seed))

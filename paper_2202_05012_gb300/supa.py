@@ -353,7 +353,7 @@ def pack_mlp_params(params) -> np.ndarray:
                           ).astype(np.float32)
 
 
-def unpack_mlp_params(vec: np.ndarray, shapes=((256, 6), (256, 256), (256, 256), (60, 256))):
+def unpack_mlp_params(vec: np.ndarray, shapes=((256, 6), (256, 256), (256, 256), (90, 256))):
     out, o = [], 0
     for r, c in shapes:
         W = vec[o:o + r * c].reshape(r, c)

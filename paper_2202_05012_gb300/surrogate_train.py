@@ -9,8 +9,10 @@ runs in the library's kernels).
 
 Sub-showers start below E_s (energy log-uniform in [e_min, E_s], polar angle
 U[0, 45 deg], start layer uniform, start slice uniform within it) in the
-30-layer detector; targets are their per-layer deposit fractions from the
-start layer on.
+30-layer detector -- or, matched to a workload, from the particles its
+showers divert; targets are their per-layer deposit fractions from the start
+layer on and the mean lateral distances of those deposits from the
+sub-shower's axis.
 """
 from __future__ import annotations
 
@@ -21,10 +23,10 @@ import numpy as np
 from . import inputs
 from . import supa as S
 
-# Algorithmic FLOPs per sample of one training step of 6-256-256-256-60:
+# Algorithmic FLOPs per sample of one training step of 6-256-256-256-90:
 # forward 2 * sum(in * out), backward twice that (data and weight gradients,
 # minus the unused input gradient of the first layer).
-_LAYERS = [(6, 256), (256, 256), (256, 256), (256, 60)]
+_LAYERS = [(6, 256), (256, 256), (256, 256), (256, 90)]
 FWD_FLOPS = sum(2 * a * b for a, b in _LAYERS)
 TRAIN_FLOPS = FWD_FLOPS + 2 * FWD_FLOPS - 2 * 6 * 256
 
@@ -43,7 +45,7 @@ def training_set(n: int, e_s: float, seed: int, n_layers: int = 30, device="cuda
         S.supa_simulate(b, d, n, seed)
         info = S.supa_batch_get_info(b)
         x = torch.empty((n, 6), dtype=torch.float32, device=device)
-        y = torch.empty((n, 30), dtype=torch.float32, device=device)
+        y = torch.empty((n, 60), dtype=torch.float32, device=device)
         S.supa_build_training_set(b, e_s, x, y)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -96,7 +98,7 @@ def training_set_matched(geom, prims, e_s: float, n_max: int, seed: int, device=
         S.supa_simulate(b, sub, n, seed + 1)
         info = S.supa_batch_get_info(b)
         x = torch.empty((n, 6), dtype=torch.float32, device=device)
-        y = torch.empty((n, 30), dtype=torch.float32, device=device)
+        y = torch.empty((n, 60), dtype=torch.float32, device=device)
         S.supa_build_training_set(b, e_s, x, y)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -106,8 +108,11 @@ def training_set_matched(geom, prims, e_s: float, n_max: int, seed: int, device=
         S.supa_destroy_geometry(gh)
 
 
-def train(data: dict, epochs: int = 20, batch: int = 16384, lr: float = 1e-3, seed: int = 0, init_seed: int = 1):
-    """Adam epochs on the GPU; returns (network handle, log)."""
+def train(data: dict, epochs: int = 20, batch: int = 16384, lr: float = 1e-3, seed: int = 0, init_seed: int = 1,
+          lr_final: float | None = None):
+    """Adam epochs on the GPU; returns (network handle, log).  With lr_final
+    the learning rate decays geometrically from lr to lr_final over the
+    epochs."""
     import torch
     net = S.supa_surrogate_create(batch, S.pack_mlp_params(inputs.mlp_init(init_seed)))
     n = data["n"]
@@ -119,7 +124,8 @@ def train(data: dict, epochs: int = 20, batch: int = 16384, lr: float = 1e-3, se
     ev0.record()
     for ep in range(epochs):
         acc.zero_()
-        S.supa_surrogate_train_epoch(net, data["x"], data["y"], n, seed * 1000 + ep, lr, acc)
+        lr_ep = lr if lr_final is None or epochs < 2 else lr * (lr_final / lr) ** (ep / (epochs - 1))
+        S.supa_surrogate_train_epoch(net, data["x"], data["y"], n, seed * 1000 + ep, lr_ep, acc)
         losses.append(acc)  # read after the loop (no synchronisation per epoch)
         acc = torch.zeros(1, dtype=torch.float64, device="cuda")
     ev1.record()
@@ -128,6 +134,6 @@ def train(data: dict, epochs: int = 20, batch: int = 16384, lr: float = 1e-3, se
     ms = ev0.elapsed_time(ev1)
     per_epoch = [float(l.item()) / steps for l in losses]
     flops = TRAIN_FLOPS * steps * batch * epochs
-    return net, dict(epochs=epochs, batch=batch, lr=lr, steps_per_epoch=steps, seconds=ms / 1000.0,
+    return net, dict(epochs=epochs, batch=batch, lr=lr, lr_final=lr_final, steps_per_epoch=steps, seconds=ms / 1000.0,
                      seconds_per_epoch=ms / 1000.0 / epochs, loss_per_epoch=per_epoch,
                      tflops=flops / (ms / 1000.0) / 1e12, samples_per_s=steps * batch * epochs / (ms / 1000.0))

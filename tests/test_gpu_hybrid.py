@@ -47,7 +47,7 @@ def test_training_set_matches_oracle_targets():
         S.supa_simulate(b, S.primaries_to_device(p), n, 4)
         S.supa_batch_get_info(b)
         x = torch.zeros((n, 6), dtype=torch.float32, device="cuda")
-        y = torch.zeros((n, 30), dtype=torch.float32, device="cuda")
+        y = torch.zeros((n, 60), dtype=torch.float32, device="cuda")
         S.supa_build_training_set(b, E_S, x, y)
         X, Y = x.cpu().numpy(), y.cpu().numpy()
     finally:
@@ -55,15 +55,16 @@ def test_training_set_matches_oracle_targets():
         S.supa_destroy_geometry(gh)
     Xr, lay = _features_ref(p, start, g, E_S)
     np.testing.assert_allclose(X, Xr, rtol=1e-5, atol=1e-6)
+    from oracle import hybrid
     ora = oracle.simulate(g, p, 4, n_threads=8)
-    Yr = np.zeros((n, 30))
-    for s in range(n):
-        m = min(30, g.n_layers - lay[s])
-        Yr[s, :m] = ora["layer_sum"][s, lay[s]:lay[s] + m] / float(p["E"][s])
-    same = np.abs(Y - Yr).max(1) < 1e-4
+    Yr = hybrid.training_targets(g, p, ora)
+    same = np.abs(Y[:, :30] - Yr[:, :30]).max(1) < 1e-4
     assert same.mean() > 0.999
-    np.testing.assert_allclose(Y[same], Yr[same], rtol=1e-5, atol=1e-6)
-    np.testing.assert_allclose(Y.sum(1), Yr.sum(1), atol=2e-3)
+    np.testing.assert_allclose(Y[same, :30], Yr[same, :30], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(Y[:, :30].sum(1), Yr[:, :30].sum(1), atol=2e-3)
+    # mean lateral distances (FP32 sums on the device)
+    assert np.any(Yr[:, 30:] > 0.1)
+    np.testing.assert_allclose(Y[same, 30:], Yr[same, 30:], rtol=1e-4, atol=1e-5)
 
 
 def _surrogate(seed=1):
@@ -174,6 +175,31 @@ def test_hybrid_matches_oracle(mode):
     assert np.quantile(err, 0.99) < 3e-2, np.quantile(err, 0.99)
     np.testing.assert_allclose(arr["layer_sum"].sum(1), ls.sum(1), rtol=2e-2)
     assert abs((~stepped).sum() - len(dep["hits"])) <= 0.03 * len(dep["hits"])
+    # surrogate hits (tag 0): per shower, energy-weighted centre and spread
+    # around it (the displacements follow the network's rho_j and Philox)
+    oh = dep["hits"]
+    assert np.any(oh[:, 1:3] != 0)
+
+    def moments(s_idx, x, y, e):
+        W = np.bincount(s_idx, weights=e, minlength=n)
+        mx = np.bincount(s_idx, weights=e * x, minlength=n) / np.maximum(W, 1e-30)
+        my = np.bincount(s_idx, weights=e * y, minlength=n) / np.maximum(W, 1e-30)
+        q = np.bincount(s_idx, weights=e * ((x - mx[s_idx]) ** 2 + (y - my[s_idx]) ** 2), minlength=n)
+        return W, mx, my, q / np.maximum(W, 1e-30)
+
+    sur = ~stepped
+    Wg, mxg, myg, qg = moments(sh[sur], h[sur, 0].astype(np.float64), h[sur, 1].astype(np.float64),
+                               h[sur, 3].astype(np.float64))
+    Wo, mxo, myo, qo = moments(oh[:, 0].astype(int), oh[:, 1], oh[:, 2], oh[:, 4])
+    has = Wo > 0.05 * E0
+    assert has.sum() > n // 2
+    # deposits carry the BF16 network's error (a few per cent, more for the
+    # small ones near mu = 0), which moves an energy-weighted centre by about
+    # that error times the spread over the square root of the hits
+    dc = np.hypot(mxg - mxo, myg - myo)[has] / np.sqrt(qo[has])
+    dq = np.abs(qg - qo)[has] / qo[has]
+    assert np.quantile(dc, 0.99) < 5e-2, (np.quantile(dc, [0.5, 0.99]), np.median(np.sqrt(qo[has])))
+    assert np.quantile(dq, 0.99) < 5e-2, np.quantile(dq, [0.5, 0.99])
 
 
 def test_hybrid_queue_overflow_is_an_error():

@@ -15,7 +15,7 @@ def _batch(B, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     X = np.stack([rng.uniform(-3, 0, B), *rng.normal(0, 0.3, (2, B)), rng.uniform(0.7, 1, B), rng.uniform(0, 1, B),
                   rng.uniform(0, 1, B)], 1)
-    Y = np.abs(rng.normal(0.05, 0.05, (B, 30)))
+    Y = np.concatenate([np.abs(rng.normal(0.05, 0.05, (B, 30))), rng.uniform(0.0, 2.0, (B, 30))], 1)
     return X, Y
 
 
@@ -57,7 +57,7 @@ def test_forward_matches_fp64_oracle_including_ragged_tail():
     s = S.supa_surrogate_create(256, vec)
     try:
         xd = torch.from_numpy(X.astype(np.float32)).cuda()
-        out = torch.full((n, 60), np.nan, dtype=torch.float32, device="cuda")
+        out = torch.full((n, 90), np.nan, dtype=torch.float32, device="cuda")
         S.supa_surrogate_forward(s, xd, n, out)
         S.supa_surrogate_check(s)
         got = out.cpu().numpy().astype(np.float64)

@@ -1,8 +1,10 @@
 """Pins of the FP64 hybrid-path oracle (no counterpart in the paper; the
 rules are the library's): the normals are standard normal, a network with
-zero spread deposits exactly its means, sums above E are scaled to E, the
-hybrid stepping reduces to the plain one when nothing is set aside, and
-energy is conserved."""
+zero spread deposits exactly its means, sums above E are scaled to E, hits
+lie on the particle's straight line when the predicted distance is zero and
+at that mean distance otherwise, the hybrid stepping reduces to the plain
+one when nothing is set aside, energy is conserved, and the lateral
+training targets of a single symmetric split are its closed form."""
 import math
 
 import numpy as np
@@ -17,6 +19,14 @@ def test_box_muller_normals_are_standard():
     z = np.concatenate([hybrid.normals(s, 3 + s % 7, 2 * s + 1, 12345) for s in range(700)])
     assert stats.kstest(z, "norm").pvalue > 1e-3
     assert abs(z.mean()) < 0.03 and abs(z.std() - 1) < 0.03
+
+
+def test_offset_normals_are_standard_pairs():
+    m = np.concatenate([hybrid.offset_normals(s, 2 + s % 5, 3 * s + 1, 777) for s in range(500)])
+    assert stats.kstest(m.ravel(), "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(m[:, 0], m[:, 1])[0, 1]) < 0.05
+    # a different stream from the deposit normals
+    assert not np.allclose(m[:30, 0], hybrid.normals(0, 2, 1, 777)[:30])
 
 
 def test_plain_path_when_nothing_is_set_aside():
@@ -41,10 +51,10 @@ def test_energy_conservation_with_diversion():
     np.testing.assert_allclose(tot, p["E"].astype(np.float64), rtol=1e-12)
 
 
-def _const_net(mu, s):
+def _const_net(mu, s, rho=0.0):
     params = inputs.mlp_init(2)
-    W4 = np.zeros((60, 256))
-    b4 = np.concatenate([np.full(30, mu), np.full(30, s)])
+    W4 = np.zeros((90, 256))
+    b4 = np.concatenate([np.full(30, mu), np.full(30, s), np.full(30, rho)])
     return params[:3] + [(W4, b4)]
 
 
@@ -66,6 +76,69 @@ def test_zero_spread_deposits_the_means_and_scales_to_E():
     # hits sit on the particle's straight line at the layers' mid depths
     h = dep["hits"]
     assert np.all(np.isin(h[:, 3], 1.0 + 3.0 * np.arange(L)))
+    x, y = _straight_line(div, h, g)
+    np.testing.assert_allclose(h[:, 1], x, atol=1e-12)
+    np.testing.assert_allclose(h[:, 2], y, atol=1e-12)
+
+
+def _straight_line(div, h, g):
+    """Position of each hit's particle continued straight to the hit's depth."""
+    idx = {}
+    for i in range(len(div["E"])):
+        idx.setdefault(int(div["shower"][i]), []).append(i)
+    xs, ys = [], []
+    pos = {}
+    for row in h:
+        s, lay = int(row[0]), int(row[5])
+        # hits of one particle follow each other in layer order
+        key = (s, pos.get(s, 0))
+        i = idx[s][key[1]]
+        dz = row[3] - div["k"][i] * g.dz
+        xs.append(div["x"][i] + dz * div["ux"][i] / div["uz"][i])
+        ys.append(div["y"][i] + dz * div["uy"][i] / div["uz"][i])
+        last = lay == min(g.n_layers, div["layer"][i] + 30) - 1
+        if last:
+            pos[s] = key[1] + 1
+    return np.array(xs), np.array(ys)
+
+
+def test_hits_spread_at_the_predicted_mean_distance():
+    g = inputs.supa_d(30)
+    p = inputs.primaries(60, 9, e_lo=5, e_hi=20)
+    r = oracle.simulate(g, p, 3, e_s=1.0)
+    div = r["div"]
+    R = 0.7
+    dep = hybrid.deposits(div, _const_net(0.02, -80.0, R), g, 1.0, 3)
+    h = dep["hits"]
+    x, y = _straight_line(div, h, g)
+    dist = np.hypot(h[:, 1] - x, h[:, 2] - y)
+    # isotropic 2-D Gaussian with sigma = R sqrt(2/pi): distances are Rayleigh with mean R
+    assert len(dist) > 2000
+    sig = R * math.sqrt(2 / math.pi)
+    assert abs(dist.mean() - R) < 4 * sig * math.sqrt(2 - math.pi / 2) / math.sqrt(len(dist))
+    assert stats.kstest(dist, "rayleigh", args=(0, sig)).pvalue > 1e-3
+
+
+def test_training_targets_of_a_single_symmetric_split():
+    # one split on slice 0 with fixed theta and eps = 0: two halves of E
+    # deflected by theta/2 in opposite azimuths; every particle stops on
+    # slice 7 (layer 2), at distance 7 dz tan(theta/2) from the axis
+    g = inputs.supa_d(4, e_min=0.0)
+    g.p_split[:] = 0.0
+    g.p_stop[:] = 0.0
+    g.p_split[0] = 1.0
+    g.p_stop[7] = 1.0
+    g.theta_mode, g.theta_lo, g.theta_hi = inputs.THETA_FIXED, math.pi / 24, math.pi / 24
+    g.eps_mode = inputs.EPS_ZERO
+    p = inputs.primaries(5, 2, e_lo=0.5, e_hi=0.9)
+    p["theta"] = 0.0
+    r = oracle.simulate(g, p, 1)
+    Y = hybrid.training_targets(g, p, r)
+    assert np.all(r["offsets"][1:] - r["offsets"][:-1] == 2)
+    np.testing.assert_allclose(Y[:, 2], 1.0, rtol=1e-12)
+    np.testing.assert_allclose(Y[:, [0, 1, 3]], 0.0, atol=0)
+    np.testing.assert_allclose(Y[:, 32], 7.0 * math.tan(math.pi / 48), rtol=1e-9)
+    np.testing.assert_allclose(Y[:, [30, 31, 33]], 0.0, atol=0)
 
 
 def test_features_follow_their_definition():

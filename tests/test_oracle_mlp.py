@@ -13,7 +13,7 @@ from paper_2202_05012_gb300 import inputs
 def _data(B, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     X = rng.normal(0, 1, (B, 6))
-    Y = rng.uniform(0, 0.3, (B, 30))
+    Y = np.concatenate([rng.uniform(0, 0.3, (B, 30)), rng.uniform(0, 2.0, (B, 30))], 1)
     return X, Y
 
 
@@ -28,7 +28,7 @@ def test_gelu_and_its_derivative():
 
 
 def test_backward_matches_central_finite_differences():
-    params = inputs.mlp_init(3, shapes=((16, 6), (16, 16), (16, 16), (60, 16)))
+    params = inputs.mlp_init(3, shapes=((16, 6), (16, 16), (16, 16), (90, 16)))
     params = [(W, np.random.default_rng(i).normal(0, 0.1, b.shape)) for i, (W, b) in enumerate(params)]
     X, Y = _data(7, 1)
     loss, grads = mlp.loss_and_grads(params, X, Y)
@@ -41,7 +41,7 @@ def test_backward_matches_central_finite_differences():
                 def f(delta):
                     Q = [[W_.copy(), b_.copy()] for W_, b_ in params]
                     Q[li][which][ix] += delta
-                    return mlp.nll(mlp.forward([tuple(q) for q in Q], X)[0], Y)
+                    return mlp.loss(mlp.forward([tuple(q) for q in Q], X)[0], Y)
                 fd = (f(h) - f(-h)) / (2 * h)
                 assert abs(fd - G[ix]) <= 1e-6 * max(abs(fd), 1e-3), (li, which, ix, fd, G[ix])
 
@@ -64,9 +64,9 @@ def test_matches_torch_nn_float64():
         h = lin(h)
         if i < 3:
             h = torch.nn.functional.gelu(h, approximate="none")
-    mu, s = h[:, :30], h[:, 30:]
-    yt = torch.from_numpy(Y)
-    tl = torch.mean(0.5 * (yt - mu) ** 2 * torch.exp(-s) + 0.5 * s)
+    mu, s, rho = h[:, :30], h[:, 30:60], h[:, 60:]
+    yt, rt = torch.from_numpy(Y[:, :30]), torch.from_numpy(Y[:, 30:])
+    tl = torch.mean(0.5 * (yt - mu) ** 2 * torch.exp(-s) + 0.5 * s + 0.5 * mlp.LAMBDA_R * yt * (rho - rt) ** 2)
     tl.backward()
     assert abs(tl.item() - loss) < 1e-12
     for (gW, gb), lin in zip(grads, layers):
@@ -76,7 +76,7 @@ def test_matches_torch_nn_float64():
 
 def test_adam_matches_torch_optim():
     torch = pytest.importorskip("torch")
-    params = inputs.mlp_init(6, shapes=((8, 6), (8, 8), (8, 8), (60, 8)))
+    params = inputs.mlp_init(6, shapes=((8, 6), (8, 8), (8, 8), (90, 8)))
     X, Y = _data(16, 3)
     opt = mlp.Adam(params, lr=1e-2)
     tparams = [torch.tensor(a, requires_grad=True) for W, b in params for a in (W, b)]
