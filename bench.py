@@ -574,14 +574,18 @@ def profiles_of(S, b, n, L):
 
 def profile_errors(ref, got, thr=0.005):
     """Largest relative deviation over profile bins holding >= thr of the
-    energy, and the relative deviation of the mean total deposit."""
+    energy, and the relative deviation of the mean total deposit.  The
+    lateral profile is the regular radial bins (r < r_max, the imaged
+    region); the last bin (everything beyond) is reported as lateral_tail."""
     (rl, rr), (gl, gr) = ref, got
 
     def err(a, b):
         m = a >= thr
-        return float(np.max(np.abs(b[m] - a[m]) / a[m]))
+        return float(np.max(np.abs(b[m] - a[m]) / a[m])) if m.any() else 0.0
 
-    return {"longitudinal": err(rl, gl), "lateral": err(rr, gr),
+    return {"longitudinal": err(rl, gl), "lateral": err(rr[:-1], gr[:-1]),
+            "lateral_tail": float(abs(gr[-1] - rr[-1]) / rr[-1]) if rr[-1] > 0 else 0.0,
+            "lateral_tail_fraction": float(rr[-1]),
             "total_deposit": float(abs(gl.sum() - rl.sum()) / rl.sum()), "bin_threshold": thr}
 
 

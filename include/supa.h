@@ -303,8 +303,9 @@ int supa_surrogate_check(supa_surrogate *s);
  * up to more than E, are added to the layer sums and emitted as one hit per
  * non-empty layer after the shower's stepped hits: at the layer's mid depth,
  * displaced from the particle's straight line by sigma_j (m1, m2) with
- * sigma_j = max(0, rho_j) sqrt(2/pi) and standard normals m1, m2 (Philox
- * stream tag 2, same keys).  The energy left over is
+ * sigma_j = max(0, rho_j) sqrt(2/pi) and one pair of standard normals
+ * m1, m2 per particle (Philox stream tag 2, same keys).  The energy left
+ * over is
  * reported as sur_leak.  s = NULL or e_s <= 0 returns the batch to the plain
  * path.  s must outlive the batch.  Synchronous (allocates). */
 int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity, int32_t mode);

@@ -16,10 +16,11 @@ returns them):
      detector, scaled by E / sum d when the sum exceeds E;
   5. one hit per layer with d_j > 0 at the layer's mid depth, displaced
      from the particle's straight-line position by sigma_j (m1, m2):
-     sigma_j = max(0, rho_j) sqrt(2 / pi) (an isotropic 2-D Gaussian whose
-     mean distance is the predicted rho_j), (m1, m2) the Box-Muller pair of
-     Philox block j / 2 with counter (shower id, slice | 2 << 16 | block <<
-     20, lineage lo, lineage hi), words (w0, w1) for even j, (w2, w3) odd.
+     sigma_j = max(0, rho_j) sqrt(2 / pi), so that each layer's displacement
+     is an isotropic 2-D Gaussian whose mean distance is the predicted rho_j;
+     (m1, m2) is one Box-Muller pair per particle (all its layers: the
+     sub-shower drifts one way), from words (w0, w1) of the Philox block
+     with counter (shower id, slice | 2 << 16, lineage lo, lineage hi).
 
 training_targets() writes out the network's targets from a plain
 simulation of sub-showers: deposit fractions y_j of layers start + j and
@@ -54,15 +55,10 @@ def _box_muller(w0: int, w1: int):
 
 
 def offset_normals(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
-    """[30, 2] standard normal pairs of the lateral hit displacements."""
+    """The standard normal pair (m1, m2) of a particle's hit displacements."""
     key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
-    m = np.zeros((30, 2))
-    for blk in range(15):
-        w = philox(((shower_id) & 0xFFFFFFFF, k | (2 << 16) | (blk << 20), lineage & 0xFFFFFFFF,
-                    (lineage >> 32) & 0xFFFFFFFF), key)
-        m[2 * blk] = _box_muller(w[0], w[1])
-        m[2 * blk + 1] = _box_muller(w[2], w[3])
-    return m
+    w = philox(((shower_id) & 0xFFFFFFFF, k | (2 << 16), lineage & 0xFFFFFFFF, (lineage >> 32) & 0xFFFFFFFF), key)
+    return np.array(_box_muller(w[0], w[1]))
 
 
 def training_targets(geom, prims, res) -> np.ndarray:
@@ -140,7 +136,7 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
                 zm = zmid[l0 + j]
                 sig = max(0.0, out[i, 60 + j]) * math.sqrt(2.0 / math.pi)
                 hits.append((int(div["shower"][i]),
-                             div["x"][i] + (zm - zk) * div["ux"][i] / div["uz"][i] + sig * mo[j, 0],
-                             div["y"][i] + (zm - zk) * div["uy"][i] / div["uz"][i] + sig * mo[j, 1], zm, d[i, j],
+                             div["x"][i] + (zm - zk) * div["ux"][i] / div["uz"][i] + sig * mo[0],
+                             div["y"][i] + (zm - zk) * div["uy"][i] / div["uz"][i] + sig * mo[1], zm, d[i, j],
                              l0 + j))
     return dict(d=d, out=out, hits=np.array(hits).reshape(-1, 6))

@@ -43,20 +43,19 @@ __device__ float lane_normal(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_
     return (lane & 1) ? rad * sn : rad * cs;
 }
 
-// Standard normal pair (m1, m2) displacing the hit of layer j = lane: Box-
-// Muller on Philox block j / 2 of the stream with tag 2 (same key), words
-// (w0, w1) for even j and (w2, w3) for odd j.
-__device__ float2 lane_offset_normals(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed,
-                                      int lane) {
-    const int blk = lane >> 1, pr = lane & 1;
-    const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (2u << 16) | ((uint32_t)blk << 20), lin_lo, lin_hi),
-                                  (uint32_t)seed, (uint32_t)(seed >> 32));
-    const uint32_t w0 = pr ? r.z : r.x, w1 = pr ? r.w : r.y;
-    const float u1 = (float)((w0 >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
-    const float u2 = u24(w1);
-    const float rad = sqrtf(-2.0f * logf(u1));
+// The standard normal pair (m1, m2) displacing all hits of a diverted
+// particle: Box-Muller on words (w0, w1) of the Philox block with counter
+// (shower id, slice | 2 << 16, lineage lo, lineage hi), same key.  A
+// displacement needs no more than ~1e-6 relative accuracy, so the hardware
+// approximations of log, sin and cos serve.
+__device__ float2 offset_normals(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed) {
+    const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (2u << 16), lin_lo, lin_hi), (uint32_t)seed,
+                                  (uint32_t)(seed >> 32));
+    const float u1 = (float)((r.x >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
+    const float u2 = u24(r.y);
+    const float rad = sqrtf(-2.0f * __logf(u1));
     float sn, cs;
-    sincospif(2.0f * u2, &sn, &cs);
+    __sincosf(6.28318530717958648f * u2, &sn, &cs);
     return make_float2(rad * cs, rad * sn);
 }
 
@@ -192,8 +191,9 @@ __global__ void sur_deposits(const SurParams p) {
 // with lane j writing the hit of layer start + j when its deposit is > 0 --
 // a particle's hits are consecutive, in layer order.  The hit sits at the
 // layer's mid depth, displaced from the particle's straight line by
-// sigma_j (m1, m2), sigma_j = max(0, rho_j) sqrt(2 / pi): an isotropic 2-D
-// Gaussian whose mean distance is the predicted rho_j.
+// sigma_j (m1, m2), sigma_j = max(0, rho_j) sqrt(2 / pi): per layer an
+// isotropic 2-D Gaussian whose mean distance is the predicted rho_j, with
+// one normal pair per particle (drawn lane-per-particle for the group).
 __global__ void sur_hits(const SurParams p) {
     const unsigned n = min(*p.count, (unsigned)p.cap);
     const int lane = threadIdx.x & 31;
@@ -204,17 +204,15 @@ __global__ void sur_hits(const SurParams p) {
         const unsigned i = g0 + lane;
         const int m = (int)min(32u, i1 - g0);
         const bool valid = lane < m;
-        int sh = -1 - lane, r_loff = 0, r_k = 0;
+        int sh = -1 - lane, r_loff = 0;
         unsigned c = 0;
-        uint32_t r_lo = 0, r_hi = 0;
         float r_x = 0.f, r_y = 0.f, r_tx = 0.f, r_ty = 0.f, r_zk = 0.f;
+        float2 r_m = make_float2(0.f, 0.f);
         if (valid) {
             const SurRec r = p.rec[i];
             sh = (int)r.shower;
             c = p.pcnt[i];
-            r_k = r.k;
-            r_lo = r.lin_lo;
-            r_hi = r.lin_hi;
+            if (c) r_m = offset_normals((uint32_t)(p.shower_id_base + r.shower), r.k, r.lin_lo, r.lin_hi, p.seed);
             const GeomDev &g = p.geoms[p.prim[r.shower].geom & 0xFFFFu];
             r_loff = g.layer_off + r.layer;
             r_zk = (float)r.k * g.dz;
@@ -256,21 +254,18 @@ __global__ void sur_hits(const SurParams p) {
                 const int k = k0 + u;
                 if (k >= m) break;
                 const int64_t at = __shfl_sync(kFull, at_lane, k);
-                const int loff = __shfl_sync(kFull, r_loff, k), kk = __shfl_sync(kFull, r_k, k);
-                const uint32_t lo = __shfl_sync(kFull, r_lo, k), hi = __shfl_sync(kFull, r_hi, k);
-                const int sh_k = __shfl_sync(kFull, sh, k);
+                const int loff = __shfl_sync(kFull, r_loff, k);
                 const float zk = __shfl_sync(kFull, r_zk, k), x = __shfl_sync(kFull, r_x, k),
                             y = __shfl_sync(kFull, r_y, k), tx = __shfl_sync(kFull, r_tx, k),
-                            ty = __shfl_sync(kFull, r_ty, k);
+                            ty = __shfl_sync(kFull, r_ty, k), m1 = __shfl_sync(kFull, r_m.x, k),
+                            m2 = __shfl_sync(kFull, r_m.y, k);
                 const unsigned nz = __ballot_sync(kFull, d[u] > 0.0f);
                 if (d[u] > 0.0f) {
                     const float zm = p.zmid[loff + lane];
                     const float dz = zm - zk;
                     const float sig = fmaxf(0.0f, rho[u]) * 0.79788456080286536f;  // sqrt(2 / pi)
-                    const float2 m12 =
-                        lane_offset_normals((uint32_t)(p.shower_id_base + (uint32_t)sh_k), kk, lo, hi, p.seed, lane);
                     p.hits[at + __popc(nz & lt)] =
-                        make_float4(fmaf(sig, m12.x, fmaf(dz, tx, x)), fmaf(sig, m12.y, fmaf(dz, ty, y)), zm, d[u]);
+                        make_float4(fmaf(sig, m1, fmaf(dz, tx, x)), fmaf(sig, m2, fmaf(dz, ty, y)), zm, d[u]);
                 }
             }
         }

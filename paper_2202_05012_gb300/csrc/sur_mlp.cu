@@ -1,5 +1,5 @@
 // sur_mlp.cu -- inference of the surrogate network 6 -> 256 -> 256 -> 256 ->
-// 128 (90 used) in one persistent kernel: the activations of a 128-row tile
+// 96 (90 used) in one persistent kernel: the activations of a 128-row tile
 // never leave the SM.
 //
 // Per tile, layer l's accumulator lives in tensor memory (two 256-column
@@ -12,15 +12,17 @@
 // row touch HBM.
 //
 // Shared memory (230,400 B with alignment slack):
-//   X   2 x 16 KB   inputs of two tiles (bf16, columns 0..15 used, K = 16)
+//   X   16 KB       inputs of a tile (bf16, columns 0..15 used, K = 16); the
+//                   next tile is packed while the current one runs layers 2-4
 //   H   64 KB       hidden activation, 4 K-blocks of 128 rows x 64 columns
-//   W4  64 KB       resident: 4 K-blocks of 128 rows x 64 columns
-//   S   2 x 32 KB   ring of 256-row x 64-column weight blocks, TMA: per tile
-//                   W1 (columns 0..15 used), then the 4 K-blocks of W2 and W3
+//   W1  32 KB       resident: 256 rows x 64 columns (columns 0..15 used)
+//   W4  48 KB       resident: 4 K-blocks of 96 rows x 64 columns
+//   S   2 x 32 KB   ring of the 4 K-blocks of W2 and of W3 (256 rows x 64
+//                   columns each), TMA
 // Warps: 0 TMA producer, 1 tensor-memory owner and MMA issuer, 2-3 pack the
 // inputs of each tile, 4-19 epilogue (warp w reads TMEM lanes 32(w%4)..+31
 // and columns 16((w-4)/4)..+15 of every K-block; 32((w-4)/4)..+31 of the
-// output layer).
+// output layer, w < 16).
 //
 // Every wait is bounded (about two seconds): on expiry the CTA sets the error
 // word, stops, lets its TMA loads and MMAs finish (bounded), frees tensor
@@ -43,8 +45,9 @@ constexpr int kRows = 128;
 constexpr uint32_t kXBytes = kRows * 128;    // one input tile
 constexpr uint32_t kHBlk = kRows * 128;      // one K-block of H
 constexpr uint32_t kWBlk = 256 * 128;        // one K-block of a 256-row weight
-constexpr uint32_t kW4Blk = 128 * 128;       // one K-block of W4
-constexpr uint32_t oX = 0, oH = 2 * kXBytes, oW4 = oH + 4 * kHBlk, oS = oW4 + 4 * kW4Blk;
+constexpr int kOutN = 96;                    // output-layer width
+constexpr uint32_t kW4Blk = kOutN * 128;     // one K-block of W4
+constexpr uint32_t oX = 0, oH = kXBytes, oW1 = oH + 4 * kHBlk, oW4 = oW1 + kWBlk, oS = oW4 + 4 * kW4Blk;
 constexpr uint32_t kMlpSmem = oS + 2 * kWBlk + 1024;
 constexpr int kEpiWarps = 16;
 
@@ -53,11 +56,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                    const __grid_constant__ CUtensorMap tw3, const __grid_constant__ CUtensorMap tw4,
                    const MlpInferArgs g) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t w_res;       // W4 resident
+    __shared__ __align__(8) uint64_t w_res;       // W1 and W4 resident
     __shared__ __align__(8) uint64_t w_full[2];   // ring stage holds a K-block
     __shared__ __align__(8) uint64_t w_empty[2];  // the MMAs have read the stage
-    __shared__ __align__(8) uint64_t x_full[2];   // input tile packed
-    __shared__ __align__(8) uint64_t x_empty[2];  // layer-1 MMA has read it
+    __shared__ __align__(8) uint64_t x_full;      // input tile packed
+    __shared__ __align__(8) uint64_t x_empty;     // layer-1 MMA has read it
     __shared__ __align__(8) uint64_t h_ready[4];  // K-block kb of H written
     __shared__ __align__(8) uint64_t acc_full;    // a layer's accumulator is final
     __shared__ __align__(8) uint64_t drain;       // all MMAs of this CTA done
@@ -77,9 +80,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&w_full[i], 1);
             mbar_init(&w_empty[i], 1);
-            mbar_init(&x_full[i], 2);
-            mbar_init(&x_empty[i], 1);
         }
+        mbar_init(&x_full, 2);
+        mbar_init(&x_empty, 1);
         for (int i = 0; i < 4; ++i) mbar_init(&h_ready[i], kEpiWarps);
         mbar_init(&acc_full, 1);
         mbar_init(&drain, 1);
@@ -106,21 +109,20 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     int issued = 0;  // ring loads issued by the producer
     if (warp == 0) {
         if (lane == 0) {
-            // ---- TMA producer: resident W4; then W1 and the W2, W3 K-blocks per tile ----
-            mbar_expect_tx(&w_res, 4 * kW4Blk);
+            // ---- TMA producer: resident W1, W4; then the W2, W3 K-blocks per tile ----
+            mbar_expect_tx(&w_res, kWBlk + 4 * kW4Blk);
+            tma_load_2d(base + oW1, &tw1, 0, 0, &w_res);
             for (int kb = 0; kb < 4; ++kb) tma_load_2d(base + oW4 + kb * kW4Blk, &tw4, kb * 64, 0, &w_res);
             for (int t = 0; t < my_tiles && !*abort_v; ++t)
-                for (int blk = 0; blk < 9 && !*abort_v; ++blk) {
+                for (int blk = 0; blk < 8 && !*abort_v; ++blk) {
                     const int c = issued, s = c & 1;
                     if (c >= 2 && !mbar_wait(&w_empty[s], ((c >> 1) - 1) & 1)) {
                         fail();
                         break;
                     }
                     if (*abort_v) break;
-                    const CUtensorMap *map = blk == 0 ? &tw1 : blk <= 4 ? &tw2 : &tw3;
-                    const int kb = blk == 0 ? 0 : (blk - 1) & 3;
                     mbar_expect_tx(&w_full[s], kWBlk);
-                    tma_load_2d(base + oS + s * kWBlk, map, kb * 64, 0, &w_full[s]);
+                    tma_load_2d(base + oS + s * kWBlk, blk < 4 ? &tw2 : &tw3, (blk & 3) * 64, 0, &w_full[s]);
                     issued = c + 1;
                 }
             if (*abort_v) {
@@ -132,25 +134,22 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
-            constexpr uint32_t id256 = idesc_bf16(kRows, 256), id128 = idesc_bf16(kRows, 128);
-            const uint32_t sX = smem_u32(base + oX), sH = smem_u32(base + oH), sW4 = smem_u32(base + oW4),
-                           sS = smem_u32(base + oS);
+            constexpr uint32_t id256 = idesc_bf16(kRows, 256), idout = idesc_bf16(kRows, kOutN);
+            const uint32_t sX = smem_u32(base + oX), sH = smem_u32(base + oH), sW1 = smem_u32(base + oW1),
+                           sW4 = smem_u32(base + oW4), sS = smem_u32(base + oS);
             bool ok = mbar_wait(&w_res, 0);
             if (!ok) fail();
             uint32_t hc = 0;  // completions of h_ready consumed (one per hidden layer)
             int wc = 0;       // ring stages consumed
             for (int t = 0; t < my_tiles && ok && !*abort_v; ++t) {
-                const int xb = t & 1;
-                if (!mbar_wait(&x_full[xb], (t >> 1) & 1) || !mbar_wait(&w_full[wc & 1], (wc >> 1) & 1)) {
+                if (!mbar_wait(&x_full, t & 1)) {
                     fail();
                     break;
                 }
                 fence_after_sync();
-                // layer 1: K = 16 (6 inputs, zero padded), W1 from the ring, into accumulator 0
-                mma_bf16(acc0, sw128_desc(sX + xb * kXBytes), sw128_desc(sS + (wc & 1) * kWBlk), id256, 0u);
-                mma_commit(&w_empty[wc & 1]);
-                ++wc;
-                mma_commit(&x_empty[xb]);
+                // layer 1: K = 16 (6 inputs, zero padded), into accumulator 0
+                mma_bf16(acc0, sw128_desc(sX), sw128_desc(sW1), id256, 0u);
+                mma_commit(&x_empty);
                 mma_commit(&acc_full);
                 // layers 2 and 3 from H, weights through the ring
                 for (int layer = 2; layer <= 3 && ok; ++layer) {
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                     if (ok) mma_commit(&acc_full);
                 }
                 if (!ok) break;
-                // layer 4: 128 outputs from H and the resident W4, into accumulator 1
+                // layer 4: 96 outputs from H and the resident W4, into accumulator 1
                 for (int kb = 0; kb < 4; ++kb) {
                     if (*abort_v || !mbar_wait(&h_ready[kb], hc & 1)) {
                         fail();
@@ -185,7 +184,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         mma_bf16(acc1, sw128_desc(sH + kb * kHBlk + k * 32), sw128_desc(sW4 + kb * kW4Blk + k * 32),
-                                 id128, (kb > 0 || k > 0) ? 1u : 0u);
+                                 idout, (kb > 0 || k > 0) ? 1u : 0u);
                 }
                 ++hc;
                 if (!ok) break;
@@ -199,14 +198,13 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         // ---- input packing: 6 features -> bf16, columns 6..15 zero ----
         const int tid = threadIdx.x - 64;
         for (int t = 0; t < my_tiles; ++t) {
-            const int xb = t & 1;
             // warp-uniform decision (both warps of the packer take the same path)
-            if (!__all_sync(0xFFFFFFFFu, !*abort_v && (t < 2 || mbar_wait(&x_empty[xb], ((t >> 1) - 1) & 1)))) {
+            if (!__all_sync(0xFFFFFFFFu, !*abort_v && (t < 1 || mbar_wait(&x_empty, (t - 1) & 1)))) {
                 fail();
                 break;
             }
             const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kRows;
-            uint8_t *xs = base + oX + xb * kXBytes;
+            uint8_t *xs = base + oX;
             for (int r = tid; r < kRows; r += 64) {
                 const int row = m0 + r;
                 float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -221,7 +219,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             }
             fence_smem_to_async();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&x_full[xb]);
+            if (lane == 0) mbar_arrive(&x_full);
         }
     } else {
         // ---- epilogue: 16 warps; warp (q, h) owns rows 32q.. and columns 16h.. of each K-block ----
@@ -274,6 +272,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             ++ac;
             fence_after_sync();
             const int c0 = h * 32;
+            if (c0 >= kOutN) continue;
             float v[32];
             tmem_ld32(acc1 + lane_off + c0, v);
             fence_before_sync();
@@ -288,9 +287,12 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                             make_float4(v[4 * i] + bb.x, v[4 * i + 1] + bb.y, v[4 * i + 2] + bb.z, v[4 * i + 3] + bb.w);
                     }
                 } else {
+                    float bb[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) bb[j] = __ldg(g.b4 + c0 + j);
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (c0 + j < g.ncols) o[j] = v[j] + g.b4[c0 + j];
+                        if (c0 + j < g.ncols) o[j] = v[j] + bb[j];
                 }
             }
         }
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
 
 cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const CUtensorMap &w3,
                            const CUtensorMap &w4, const MlpInferArgs &a, cudaStream_t st) {
-    if (a.rows < 0 || a.ncols < 0 || a.ncols > 128 || a.ld < a.ncols || !a.x || !a.out || !a.error ||
+    if (a.rows < 0 || a.ncols < 0 || a.ncols > kOutN || a.ld < a.ncols || !a.x || !a.out || !a.error ||
         ((uintptr_t)a.x & 7))
         return cudaErrorInvalidValue;
     if (a.rows == 0) return cudaSuccess;

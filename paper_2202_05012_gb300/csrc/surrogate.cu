@@ -36,7 +36,7 @@ namespace {
 
 constexpr int kIn = 6, kInPad = 64, kHid = 256, kOut = 90, kOutPad = 128, kLayersOut = 30;
 constexpr int kY = 2 * kLayersOut;  // target columns: fractions, mean distances
-constexpr int kInferLd = 96;        // row stride of the inference outputs (>= kOut, multiple of 4)
+constexpr int kInferLd = 96;        // outputs written by the fused inference kernel (>= kOut; 90..95 are zero)
 static_assert(kOutPad == kTileM, "d out^T is read as one full 128-row tile");
 // packed user parameter vector: W1, b1, W2, b2, W3, b3, W4, b4
 constexpr int kNParams = kHid * kIn + kHid + 2 * (kHid * kHid + kHid) + kOut * kHid + kOut;
@@ -182,6 +182,7 @@ struct supa_surrogate {
     int *error = nullptr;
     CUtensorMap mX0, mH1, mH2, mH3, mG4, mG3, mG2, mG4T, mG3T, mG2T, mG1T;  // A operands (box 128 rows)
     CUtensorMap mW1, mW2, mW3, mW4, mW4T, mW3T, mW2T, mH3Tb, mH2Tb, mH1Tb, mX0Tb;  // B operands
+    CUtensorMap mW4i;  // W4 rows 0..95 for the fused inference kernel
     std::vector<void *> allocs;
 };
 
@@ -360,9 +361,9 @@ cudaError_t surrogate_infer_run(supa_surrogate *s, SurInfer *inf, const float *f
     a.b4 = s->master + Off::b4;
     a.out = inf->OUT;
     a.ld = kInferLd;
-    a.ncols = kOut;
+    a.ncols = kInferLd;  // all 96 columns: whole-vector stores (W4, b4 rows 90..95 are zero)
     a.error = s->error;
-    return launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4, a, st);
+    return launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4i, a, st);
 }
 
 }  // namespace supa
@@ -422,6 +423,7 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
     rc |= make_bf16_map(&s->mW2, s->W2b, kHid, kHid, kHid);
     rc |= make_bf16_map(&s->mW3, s->W3b, kHid, kHid, kHid);
     rc |= make_bf16_map(&s->mW4, s->W4b, kOutPad, kHid, kOutPad);
+    rc |= make_bf16_map(&s->mW4i, s->W4b, kOutPad, kHid, kInferLd);
     rc |= make_bf16_map(&s->mW4T, s->W4Tb, kHid, kOutPad, kHid);
     rc |= make_bf16_map(&s->mW3T, s->W3Tb, kHid, kHid, kHid);
     rc |= make_bf16_map(&s->mW2T, s->W2Tb, kHid, kHid, kHid);
@@ -545,7 +547,7 @@ int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, flo
     a.ld = kOut;
     a.ncols = kOut;
     a.error = s->error;
-    const cudaError_t e = launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4, a, (cudaStream_t)stream);
+    const cudaError_t e = launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4i, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));
     return SUPA_OK;
 }

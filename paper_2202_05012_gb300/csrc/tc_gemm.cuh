@@ -51,19 +51,19 @@ constexpr int kTileK = 64;
 
 size_t gemm_smem_bytes(int N);
 cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &a, int splits, cudaStream_t st);
-// The whole network 6 -> 256 -> 256 -> 256 -> 128 (GELU after the hidden
+// The whole network 6 -> 256 -> 256 -> 256 -> 96 (GELU after the hidden
 // layers) in one persistent kernel for inference (sur_mlp.cu).
 struct MlpInferArgs {
     const float *x;         // [rows][6] inputs
     int rows;               // rows present, or the capacity when `count` is set
     const unsigned *count;  // optional device row count: rows = min(rows, *count)
-    const float *b1, *b2, *b3, *b4;  // biases [256], [256], [256], [128]
-    float *out;             // [rows][ld] outputs, columns 0..ncols-1 written
+    const float *b1, *b2, *b3, *b4;  // biases [256], [256], [256], [96]
+    float *out;             // [rows][ld] outputs, columns 0..ncols-1 (ncols <= 96) written
     int ld, ncols;
     int *error;             // device error word (|= 8: a pipeline wait expired)
 };
 // w1: [256][64] in boxes of 256 rows; w2, w3: [256][256] in boxes of 256
-// rows; w4: [128][256] in boxes of 128 rows (make_bf16_map, K contiguous).
+// rows; w4: [>= 96][256] in boxes of 96 rows (make_bf16_map, K contiguous).
 cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const CUtensorMap &w3,
                            const CUtensorMap &w4, const MlpInferArgs &a, cudaStream_t st);
 
