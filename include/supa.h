@@ -291,8 +291,13 @@ int supa_surrogate_check(supa_surrogate *s);
 
 /* Deposit rule of the hybrid path for layer start + j of a particle of
  * energy E, from the network's mu_j and s_j. */
-#define SUPA_SURROGATE_SAMPLE 0 /* d_j = E max(0, mu_j + exp(s_j/2) n_j), n_j ~ N(0,1) */
-#define SUPA_SURROGATE_MEAN 1   /* d_j = E max(0, mu_j): the predicted mean   */
+/* MEAN: d_j = E max(0, mu_j).  SAMPLE: g_j = E mu_j exp(a_j n_j - a_j^2/2),
+ * n_j ~ N(0,1), a_j^2 = min(4, ln(1 + exp(s_j)/mu_j^2)) -- a log-normal draw
+ * with mean E mu_j (variance E^2 exp(s_j) below the cap), 0 for mu_j <= 0 --
+ * rescaled so that the particle's total equals the MEAN total: the shape of
+ * the deposits fluctuates, their sum does not. */
+#define SUPA_SURROGATE_SAMPLE 0
+#define SUPA_SURROGATE_MEAN 1
 
 /* Switch a batch to the hybrid path: from the next supa_simulate on, a
  * particle whose energy is below e_s when it reaches a slice of a readout

@@ -12,8 +12,12 @@ returns them):
      hi), block = 0..7, key = seed; from each block's words (w0, w1, w2, w3)
      the pairs (w0, w1) and (w2, w3) give u1 = ((w >> 8) + 1) 2^-24 and
      u2 = (w >> 8) 2^-24, z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2);
-  4. d_j = E max(0, mu_j + exp(s_j / 2) n_j) for layers inside the
-     detector, scaled by E / sum d when the sum exceeds E;
+  4. d_j = E f_j for layers inside the detector.  MEAN: f_j = max(0, mu_j).
+     SAMPLE: g_j = mu_j exp(a_j n_j - a_j^2 / 2), the log-normal with mean
+     mu_j and variance exp(s_j) (a_j^2 = ln(1 + exp(s_j) / mu_j^2), capped at
+     4 -- the mean stays mu_j), 0 when mu_j <= 0, then rescaled to the MEAN
+     total: f_j = g_j sum_i max(0, mu_i) / sum_i g_i (the shape fluctuates,
+     the total does not).  Both: scaled by E / sum d when the sum exceeds E;
   5. one hit per layer with d_j > 0 at the layer's mid depth, displaced
      from the particle's straight-line position by sigma_j (m1, m2):
      sigma_j = max(0, rho_j) sqrt(2 / pi), so that each layer's displacement
@@ -108,7 +112,7 @@ def normals(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
 
 def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int = 0, mode: int = 0) -> dict:
     """Per diverted particle: the drawn deposits d [n_div, 30] and the hits.
-    mode 0: d_j = E max(0, mu_j + exp(s_j/2) n_j); mode 1: d_j = E max(0, mu_j)."""
+    mode 0 (SAMPLE): moment-matched log-normal draws; mode 1 (MEAN): the means."""
     X = features(div, geom, e_s)
     out, _ = mlp.forward(params, X) if len(X) else (np.zeros((0, 90)), None)
     L = int(geom.n_layers)
@@ -124,8 +128,18 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
         E = div["E"][i]
         for j in range(30):
             if l0 + j < L:
-                f = out[i, j] if mode == 1 else out[i, j] + math.exp(0.5 * out[i, 30 + j]) * n[j]
-                d[i, j] = E * max(0.0, f)
+                mu = out[i, j]
+                if mode == 1 or mu <= 0.0:
+                    f = max(0.0, mu)
+                else:
+                    a2 = min(4.0, math.log1p(math.exp(out[i, 30 + j]) / (mu * mu)))
+                    f = mu * math.exp(math.sqrt(a2) * n[j] - 0.5 * a2)
+                d[i, j] = E * f
+        if mode != 1:
+            inside = l0 + np.arange(30) < L
+            mean_tot = E * np.maximum(0.0, out[i, :30][inside]).sum()
+            if d[i].sum() > 0:
+                d[i] *= mean_tot / d[i].sum()
         tot = d[i].sum()
         if tot > E:
             d[i] *= E / tot

@@ -4,12 +4,14 @@
 // After the step kernel has queued every particle that fell below E_s on a
 // readout slice, and the network has predicted per-layer deposit
 // distributions for the queue (means mu_j and log-variances s_j of the
-// deposit fraction of layer start + j), these kernels
-//   1. draw d_j = E max(0, mu_j + exp(s_j / 2) n_j) with standard normals n_j
-//      from Philox (stream tag 1, keyed by shower, slice and lineage, so the
-//      draw is replayable), truncated at the detector's back and scaled down
-//      when they add up to more than E; the rest of E is booked as
-//      surrogate leakage;
+// deposit fraction of layer start + j, mean lateral distances rho_j), these
+// kernels
+//   1. take d_j = E max(0, mu_j) (MEAN) or draw d_j from the log-normal with
+//      mean E mu_j and variance E^2 exp(s_j) and rescale the draws to the
+//      MEAN total (SAMPLE; standard normals from Philox stream tag 1, keyed
+//      by shower, slice and lineage, so the draw is replayable), truncated
+//      at the detector's back and scaled down when they add up to more than
+//      E; the rest of E is booked as surrogate leakage;
 //   2. add the deposits to the shower's FP64 layer sums and count one hit per
 //      non-empty layer;
 //   3. after a scan of the counts, write the hits -- one per layer, at the
@@ -153,15 +155,25 @@ __global__ void sur_deposits(const SurParams p) {
                     lo = __shfl_sync(kFull, r_lo, k);
                     hi = __shfl_sync(kFull, r_hi, k);
                 }
-                float v = 0.0f;
+                float v = 0.0f, vm = 0.0f;
                 if (lane < kSurLayers && layer + lane < nl) {
-                    float f = mu[u];
-                    if (sample)
-                        f = fmaf(expf(0.5f * sg[u]),
-                                 lane_normal((uint32_t)(p.shower_id_base + (uint32_t)sh), kk, lo, hi, p.seed, lane), f);
-                    v = E * fmaxf(0.0f, f);
+                    float f = fmaxf(0.0f, mu[u]);
+                    vm = E * f;
+                    if (sample && f > 0.0f) {
+                        // log-normal with mean mu and variance exp(s) (a^2 capped at 4)
+                        const float a2 = fminf(4.0f, log1pf(expf(sg[u]) / (f * f)));
+                        const float z =
+                            lane_normal((uint32_t)(p.shower_id_base + (uint32_t)sh), kk, lo, hi, p.seed, lane);
+                        f *= expf(fmaf(sqrtf(a2), z, -0.5f * a2));
+                    }
+                    v = E * f;
                 }
-                const float sum = warp_sum(v);
+                float sum = warp_sum(v);
+                if (sample) {  // uniform: the draws keep their shape and take the MEAN total
+                    const float sm = warp_sum(vm);
+                    if (sum > 0.0f) v *= sm / sum;
+                    sum = sm;
+                }
                 if (sum > E) v *= E / sum;
                 const unsigned i = g0 + (unsigned)k;
                 if (lane < kSurLayers) p.dep[(size_t)i * kSurLayers + lane] = v;

@@ -1,6 +1,8 @@
 """Pins of the FP64 hybrid-path oracle (no counterpart in the paper; the
 rules are the library's): the normals are standard normal, a network with
-zero spread deposits exactly its means, sums above E are scaled to E, hits
+zero spread deposits exactly its means, SAMPLE draws are log-normal with the
+predicted mean and variance, rescaled to the MEAN total, sums above E are
+scaled to E, hits
 lie on the particle's straight line when the predicted distance is zero and
 at that mean distance otherwise, the hybrid stepping reduces to the plain
 one when nothing is set aside, energy is conserved, and the lateral
@@ -146,6 +148,41 @@ def test_training_targets_of_a_single_symmetric_split():
     np.testing.assert_allclose(Y[:, [0, 1, 3]], 0.0, atol=0)
     np.testing.assert_allclose(Y[:, 32], 7.0 * math.tan(math.pi / 48), rtol=1e-9)
     np.testing.assert_allclose(Y[:, [30, 31, 33]], 0.0, atol=0)
+
+
+def test_sample_mode_is_the_moment_matched_log_normal():
+    g = inputs.supa_d(30)
+    p = inputs.primaries(150, 12, e_lo=5, e_hi=20)
+    r = oracle.simulate(g, p, 4, e_s=1.0)
+    div = r["div"]
+    mu, sd = 0.02, 0.01
+    net = _const_net(mu, math.log(sd * sd))
+    dep = hybrid.deposits(div, net, g, 1.0, 4, mode=0)
+    mean = hybrid.deposits(div, net, g, 1.0, 4, mode=1)
+    # the total of every particle is the MEAN total; the shape fluctuates
+    np.testing.assert_allclose(dep["d"].sum(1), mean["d"].sum(1), rtol=1e-12)
+    assert np.std(dep["d"][:, 0] / div["E"]) > 0.5 * sd
+    # before that rescaling the draws are log-normal with mean mu and
+    # variance sd^2 (a^2 = ln 1.25, below the cap): undo it per particle
+    inside = div["layer"][:, None] + np.arange(30) < g.n_layers  # [n, 30]
+    n_in = inside.sum(1)
+    raw = []
+    for i in range(len(div["E"])):
+        norm = hybrid.normals(int(div["shower"][i]), int(div["k"][i]), int(div["lineage"][i]), 4)[:n_in[i]]
+        raw.append(norm)
+    z = np.concatenate(raw)
+    assert z.size > 20000
+    a2 = math.log1p(sd * sd / (mu * mu))
+    g_draw = mu * np.exp(math.sqrt(a2) * z - 0.5 * a2)
+    assert abs(g_draw.mean() - mu) < 4 * sd / math.sqrt(g_draw.size)
+    assert abs(g_draw.var() / sd ** 2 - 1) < 0.05
+    ratio = np.concatenate([dep["d"][i, :n_in[i]] / div["E"][i] / (mu * np.exp(math.sqrt(a2) * raw[i] - 0.5 * a2))
+                            for i in range(len(raw))])
+    # one factor per particle: sum of means / sum of draws
+    for i in range(0, len(raw), 37):
+        r = dep["d"][i, :n_in[i]] / div["E"][i] / (mu * np.exp(math.sqrt(a2) * raw[i] - 0.5 * a2))
+        np.testing.assert_allclose(r, r[0], rtol=1e-12)
+    assert ratio.size == z.size
 
 
 def test_features_follow_their_definition():
