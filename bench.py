@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-hybrid", action="store_true", help="skip the plain-vs-surrogate comparison")
-    ap.add_argument("--e-s", type=float, default=1.0, help="surrogate cutoff energy E_s")
+    ap.add_argument("--e-s", type=float, default=2.0, help="surrogate cutoff energy E_s")
     ap.add_argument("--train-samples", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=2e-3, help="initial learning rate")
