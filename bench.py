@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="supa", choices=["supa", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5", "surrogate"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5", "surrogate", "hybrid"])
     ap.add_argument("--e-s-sweep", type=float, nargs="+", default=[0.2, 0.5, 1.0, 2.0, 5.0])
     ap.add_argument("--showers", type=int, default=0, help="override the batch size")
     ap.add_argument("--voxel-chunk", type=int, default=32768)
@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--lr-final", type=float, default=5e-5, help="learning rate of the last epoch (geometric decay)")
     ap.add_argument("--train-showers", type=int, default=0,
                     help="showers of the workload (another seed) whose diverted particles seed the training set")
+    ap.add_argument("--train-set", default="matched", choices=["matched", "generic"],
+                    help="hybrid workload: sub-showers from diverted particles, or generic starts (smaller)")
     ap.add_argument("--pipeline", type=int, default=1,
                     help="sub-batches per step; >1 overlaps simulation of one with downsampling of the previous")
     return ap.parse_args()
@@ -750,9 +752,11 @@ def run_surrogate(args):
 
 def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
     """Same metric through the public API with host buffers: primaries copied
-    from pinned host memory each step, the point cloud (all hits) and the
-    per-shower FP64 layer sums read back to pinned host memory.  Images stay
-    on the device, consumed chunk by chunk."""
+    from pinned host memory each step, the point cloud (all hits, fetched in
+    64M-hit chunks) and the per-shower FP64 layer sums read back to pinned
+    host memory.  The point cloud travels to the host on a second stream
+    (copy engines) while the images are made; images stay on the device,
+    consumed chunk by chunk."""
     import torch
     import torch.distributed as dist
     h_prim = torch.from_numpy(np.ascontiguousarray(prims).view(np.uint8)).pin_memory()
@@ -760,8 +764,10 @@ def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
     info = S.supa_batch_get_info(b)
     cap = int(info.n_hits * 1.05) + 1024
     h_hits = torch.empty((cap, 4), dtype=torch.float32, pin_memory=True)
+    d_hits = torch.empty((cap, 4), dtype=torch.float32, device="cuda")
     h_ls = torch.empty((n, geom.n_layers), dtype=torch.float64, pin_memory=True)
-    stream = torch.cuda.current_stream()
+    cur = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
     h2d = d2h = 0
 
     def step():
@@ -769,16 +775,19 @@ def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
         d_prim.copy_(h_prim, non_blocking=True)
         S.supa_simulate(b, d_prim, n, seed, base)
         inf = S.supa_batch_get_info(b)
-        for c0 in range(0, n, V):
-            S.supa_voxelize(b, c0, min(n, c0 + V), grid, oor)
         got = 0
         while got < inf.n_hits:
-            m = S.supa_fetch_hits(b, got, min(FETCH_CHUNK, cap - got), h_hits[got:], dst_is_device=False)
+            m = S.supa_fetch_hits(b, got, min(FETCH_CHUNK, cap - got), d_hits[got:])
             got += m
             if m == 0:
                 break
-        ls = S.info_arrays(inf)["layer_sum"]
-        h_ls.copy_(ls, non_blocking=True)
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            h_hits[:got].copy_(d_hits[:got], non_blocking=True)
+            h_ls.copy_(S.info_arrays(inf)["layer_sum"], non_blocking=True)
+        for c0 in range(0, n, V):
+            S.supa_voxelize(b, c0, min(n, c0 + V), grid, oor)
+        cur.wait_stream(side)
         torch.cuda.synchronize()
         h2d = h_prim.numel()
         d2h = inf.n_hits * 16 + h_ls.numel() * 8
@@ -874,6 +883,54 @@ def run_c3(args):
     print(json.dumps(out), flush=True)
 
 
+def run_hybrid(args):
+    """Hybrid simulation alone (C5 showers, stepping above E_s, the network
+    and its deposits and hits below it; no images), W warm-up and K timed
+    supa_simulate calls: the short workload the hybrid kernels are profiled
+    on."""
+    import torch
+
+    from paper_2202_05012_gb300 import inputs
+    from paper_2202_05012_gb300 import supa as S
+    from paper_2202_05012_gb300 import surrogate_train as T
+
+    torch.cuda.set_device(0)
+    n = args.showers or 20_000
+    g, p = inputs.workload_c5(n)
+    mean_e = float(p["E"].mean())
+    if args.train_set == "matched":
+        net, tlog = matched_training(args, T, lambda m: inputs.workload_c5(m, seed=14), args.e_s, mean_e)
+    else:
+        data = T.training_set(args.train_samples, args.e_s, seed=3, n_layers=30)
+        net, tlog = T.train(data, epochs=args.epochs, lr=args.lr, lr_final=args.lr_final)
+        tlog = {"samples": data["n"], "set": "generic sub-shower starts", **tlog}
+        del data
+    gh = S.supa_init_geometry(g)
+    d = S.primaries_to_device(p)
+    b = S.supa_batch_create([gh], n, {"max_hits": int(n * max(400, 40 * mean_e)) + (8 << 20), "lpt_order": 1})
+    S.supa_batch_set_surrogate(b, net, args.e_s, int(2.0 * mean_e / args.e_s * n) + (1 << 20),
+                               S.SUPA_SURROGATE_MEAN)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        S.supa_simulate(b, d, n, 4)
+        S.supa_batch_get_info(b)
+    ms = []
+    for _ in range(args.steps):
+        e0.record()
+        S.supa_simulate(b, d, n, 4)
+        e1.record()
+        info = S.supa_batch_get_info(b)
+        ms.append(e0.elapsed_time(e1))
+    S.supa_destroy_batch(b)
+    S.supa_destroy_geometry(gh)
+    S.supa_surrogate_destroy(net)
+    t = float(np.mean(ms))
+    print(json.dumps({"metric": "hybrid showers/s (simulate only)", "value": n / (t / 1000.0), "unit": "showers/s",
+                      "workload": f"C5 showers x {n}, E_s = {args.e_s} GeV, MEAN mode", "ms_per_call": ms,
+                      "diverted_per_shower": info.n_diverted / n, "particle_steps_per_shower": info.n_steps / n,
+                      "training": {k: v for k, v in tlog.items() if k != "loss_per_epoch"}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -882,6 +939,8 @@ def main():
         run_c3(args)
     elif args.workload == "surrogate":
         run_surrogate(args)
+    elif args.workload == "hybrid":
+        run_hybrid(args)
     else:
         run_supa(args)
 

@@ -185,7 +185,11 @@ int supa_batch_get_info(supa_batch *b, supa_batch_info *info, void *stream);
 /* Copy hits [first_hit, first_hit + max_hits) of the batch, in shower order
  * (the point cloud of Sec. 3: each hit is (x, y, z, E)), into dst, a device
  * buffer if dst_is_device else a host buffer.  *n_written receives the count
- * (fewer at the end of the batch).  Requires supa_batch_get_info first. */
+ * (fewer at the end of the batch).  Requires supa_batch_get_info first.
+ * Asynchronous on `stream` in both cases: a host destination (best pinned)
+ * is complete once the stream reaches this point; the hits pass through a
+ * batch-owned device staging buffer (grown to the largest host fetch, by a
+ * synchronising allocation) and one copy-engine transfer. */
 int supa_fetch_hits(supa_batch *b, int64_t first_hit, int64_t max_hits, void *dst, int32_t dst_is_device,
                     int64_t *n_written, void *stream);
 

@@ -782,25 +782,24 @@ static int fetch_common(supa_batch *b, int64_t first, int64_t max_hits, void *ds
         SUPA_CUDA(launch_fetch(p, st));
         return SUPA_OK;
     }
-    // host destination: gather into a device staging buffer, then copy out
-    const int64_t chunk = std::min<int64_t>(count, (int64_t)64 << 20);
-    if (b->stage_cap_hits < chunk) {
+    // host destination: one gather into the batch's device staging buffer,
+    // then one copy-engine transfer; both asynchronous on the stream, so the
+    // transfer can run beside other kernels (e.g. the images) on other
+    // streams.  The staging buffer is reused by the next host fetch of this
+    // batch, in stream order.
+    if (b->stage_cap_hits < count) {
         SUPA_CUDA(cudaStreamSynchronize(st));
         cudaFree(b->d_stage);
         b->d_stage = nullptr;
         b->stage_cap_hits = 0;
-        SUPA_CUDA(dalloc(&b->d_stage, (size_t)chunk));
-        b->stage_cap_hits = chunk;
+        SUPA_CUDA(dalloc(&b->d_stage, (size_t)count));
+        b->stage_cap_hits = count;
     }
-    for (int64_t done = 0; done < count; done += chunk) {
-        const int64_t m = std::min(chunk, count - done);
-        p.first = first + done;
-        p.count = m;
-        p.dst = b->d_stage;
-        SUPA_CUDA(launch_fetch(p, st));
-        SUPA_CUDA(cudaMemcpyAsync((char *)dst + done * 16, b->d_stage, m * 16, cudaMemcpyDeviceToHost, st));
-    }
-    SUPA_CUDA(cudaStreamSynchronize(st));
+    p.first = first;
+    p.count = count;
+    p.dst = b->d_stage;
+    SUPA_CUDA(launch_fetch(p, st));
+    SUPA_CUDA(cudaMemcpyAsync(dst, b->d_stage, (size_t)count * 16, cudaMemcpyDeviceToHost, st));
     return SUPA_OK;
 }
 

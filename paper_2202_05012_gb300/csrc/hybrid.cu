@@ -87,10 +87,11 @@ __device__ __forceinline__ void warp_range(unsigned n, unsigned &i0, unsigned &i
 // GPU is far too slow for a double add per deposit), converted to FP64 once
 // per run.  Queue records are read 32 at a time (lane k holds entry g0 + k)
 // and the network outputs of 8 entries are in flight at once.
+template <bool kSample>
 __global__ void sur_deposits(const SurParams p) {
     const unsigned n = min(*p.count, (unsigned)p.cap);
     const int lane = threadIdx.x & 31;
-    const bool sample = p.mode == SUPA_SURROGATE_SAMPLE;
+    constexpr bool sample = kSample;
     unsigned i0, i1;
     warp_range(n, i0, i1);
     int cur = -1;
@@ -134,7 +135,7 @@ __global__ void sur_deposits(const SurParams p) {
                 const bool ld = k0 + u < m && lane < kSurLayers;
                 const float *o = p.out + (size_t)(g0 + k0 + u) * p.out_ld;
                 mu[u] = ld ? o[lane] : 0.0f;
-                sg[u] = (ld && sample) ? o[kSurLayers + lane] : 0.0f;
+                if (sample) sg[u] = ld ? o[kSurLayers + lane] : 0.0f;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -150,7 +151,7 @@ __global__ void sur_deposits(const SurParams p) {
                 }
                 int kk = 0;
                 uint32_t lo = 0, hi = 0;
-                if (sample) {  // uniform
+                if (sample) {
                     kk = __shfl_sync(kFull, r_k, k);
                     lo = __shfl_sync(kFull, r_lo, k);
                     hi = __shfl_sync(kFull, r_hi, k);
@@ -158,7 +159,7 @@ __global__ void sur_deposits(const SurParams p) {
                 float v = 0.0f, vm = 0.0f;
                 if (lane < kSurLayers && layer + lane < nl) {
                     float f = fmaxf(0.0f, mu[u]);
-                    vm = E * f;
+                    if (sample) vm = E * f;
                     if (sample && f > 0.0f) {
                         // log-normal with mean mu and variance exp(s) (a^2 capped at 4)
                         const float a2 = fminf(4.0f, log1pf(expf(sg[u]) / (f * f)));
@@ -169,7 +170,7 @@ __global__ void sur_deposits(const SurParams p) {
                     v = E * f;
                 }
                 float sum = warp_sum(v);
-                if (sample) {  // uniform: the draws keep their shape and take the MEAN total
+                if (sample) {  // the draws keep their shape and take the MEAN total
                     const float sm = warp_sum(vm);
                     if (sum > 0.0f) v *= sm / sum;
                     sum = sm;
@@ -254,26 +255,31 @@ __global__ void sur_hits(const SurParams p) {
         base = __shfl_sync(kFull, base, end);
         const int64_t at_lane = valid ? p.soff[sh] + (int64_t)(base + run_exc) : 0;
         for (int k0 = 0; k0 < m; k0 += 8) {
-            float d[8], rho[8];
+            float d[8], rho[8], zmid[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const bool ld = k0 + u < m && lane < kSurLayers;
                 d[u] = ld ? p.dep[(size_t)(g0 + k0 + u) * kSurLayers + lane] : 0.0f;
                 rho[u] = ld ? p.out[(size_t)(g0 + k0 + u) * p.out_ld + 2 * kSurLayers + lane] : 0.0f;
             }
+            // mid depths of the layers that get a hit (a deposit > 0 lies inside the detector)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int loff = __shfl_sync(kFull, r_loff, (k0 + u) & 31);
+                zmid[u] = d[u] > 0.0f ? p.zmid[loff + lane] : 0.0f;
+            }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int k = k0 + u;
                 if (k >= m) break;
                 const int64_t at = __shfl_sync(kFull, at_lane, k);
-                const int loff = __shfl_sync(kFull, r_loff, k);
                 const float zk = __shfl_sync(kFull, r_zk, k), x = __shfl_sync(kFull, r_x, k),
                             y = __shfl_sync(kFull, r_y, k), tx = __shfl_sync(kFull, r_tx, k),
                             ty = __shfl_sync(kFull, r_ty, k), m1 = __shfl_sync(kFull, r_m.x, k),
                             m2 = __shfl_sync(kFull, r_m.y, k);
                 const unsigned nz = __ballot_sync(kFull, d[u] > 0.0f);
                 if (d[u] > 0.0f) {
-                    const float zm = p.zmid[loff + lane];
+                    const float zm = zmid[u];
                     const float dz = zm - zk;
                     const float sig = fmaxf(0.0f, rho[u]) * 0.79788456080286536f;  // sqrt(2 / pi)
                     p.hits[at + __popc(nz & lt)] =
@@ -342,7 +348,10 @@ cudaError_t launch_export_diverted(const SurRec *rec, int64_t n, const supa_prim
 }
 
 cudaError_t launch_sur_deposits(const SurParams &p, cudaStream_t st) {
-    sur_deposits<<<4096, 128, 0, st>>>(p);
+    if (p.mode == SUPA_SURROGATE_SAMPLE)
+        sur_deposits<true><<<4096, 128, 0, st>>>(p);
+    else
+        sur_deposits<false><<<4096, 128, 0, st>>>(p);
     return cudaGetLastError();
 }
 
