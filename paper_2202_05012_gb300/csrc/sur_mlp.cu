@@ -22,7 +22,7 @@
 // Warps: 0 TMA producer, 1 tensor-memory owner and MMA issuer, 2-3 pack the
 // inputs of each tile, 4-19 epilogue (warp w reads TMEM lanes 32(w%4)..+31
 // and columns 16((w-4)/4)..+15 of every K-block; 32((w-4)/4)..+31 of the
-// output layer, w < 16).
+// output layer, w < 16, which is staged in H and written out coalesced).
 //
 // Every wait is bounded (about two seconds): on expiry the CTA sets the error
 // word, stops, lets its TMA loads and MMAs finish (bounded), frees tensor
@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     __shared__ __align__(8) uint64_t h_ready[4];  // K-block kb of H written
     __shared__ __align__(8) uint64_t acc_full;    // a layer's accumulator is final
     __shared__ __align__(8) uint64_t drain;       // all MMAs of this CTA done
+    __shared__ __align__(8) uint64_t out_staged;  // every epilogue warp has staged its output block
+    __shared__ __align__(8) uint64_t out_done;    // every epilogue warp has written its share out
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -86,6 +88,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         for (int i = 0; i < 4; ++i) mbar_init(&h_ready[i], kEpiWarps);
         mbar_init(&acc_full, 1);
         mbar_init(&drain, 1);
+        mbar_init(&out_staged, kEpiWarps);
+        mbar_init(&out_done, kEpiWarps);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -271,29 +275,53 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             }
             ++ac;
             fence_after_sync();
+            // Output layer: stage the 128 x 96 tile in the H buffer (idle now:
+            // layer 4's MMAs are done and the next tile's layer-1 epilogue
+            // writes H only after every warp has passed out_done), then write
+            // it out row by row, coalesced.  Row pitch 100 floats: the float4
+            // stores of 8 consecutive rows hit distinct banks.
+            float *stage = reinterpret_cast<float *>(hs);
+            constexpr int kPitch = 100;
             const int c0 = h * 32;
-            if (c0 >= kOutN) continue;
-            float v[32];
-            tmem_ld32(acc1 + lane_off + c0, v);
-            fence_before_sync();
-            if (row < M && c0 < g.ncols) {
-                float *o = g.out + (size_t)row * g.ld + c0;
-                if (c0 + 32 <= g.ncols && (g.ld & 3) == 0 && ((uintptr_t)g.out & 15) == 0) {
-                    const float4 *b4 = reinterpret_cast<const float4 *>(g.b4 + c0);
+            if (c0 < kOutN) {
+                float v[32];
+                tmem_ld32(acc1 + lane_off + c0, v);
+                const float4 *b4 = reinterpret_cast<const float4 *>(g.b4 + c0);
+                float4 *dst = reinterpret_cast<float4 *>(stage + r * kPitch + c0);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 bb = __ldg(b4 + i);
-                        reinterpret_cast<float4 *>(o)[i] =
-                            make_float4(v[4 * i] + bb.x, v[4 * i + 1] + bb.y, v[4 * i + 2] + bb.z, v[4 * i + 3] + bb.w);
-                    }
-                } else {
-                    float bb[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) bb[j] = __ldg(g.b4 + c0 + j);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (c0 + j < g.ncols) o[j] = v[j] + bb[j];
+                for (int i = 0; i < 8; ++i) {
+                    const float4 bb = __ldg(b4 + i);
+                    dst[i] = make_float4(v[4 * i] + bb.x, v[4 * i + 1] + bb.y, v[4 * i + 2] + bb.z,
+                                         v[4 * i + 3] + bb.w);
                 }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&out_staged);
+            if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&out_staged, t & 1))) {
+                fail();
+                break;
+            }
+            const int m0 = row - r;
+            const int e = (warp - 4) * 32 + lane;  // 0..511 over the epilogue warps
+            const bool vec = (g.ld & 3) == 0 && ((uintptr_t)g.out & 15) == 0;
+            for (int idx = e; idx < kRows * (kOutN / 4); idx += kEpiWarps * 32) {
+                const int rr = idx / (kOutN / 4), c = (idx % (kOutN / 4)) * 4;
+                if (m0 + rr >= M || c >= g.ncols) continue;
+                const float4 val = *reinterpret_cast<const float4 *>(stage + rr * kPitch + c);
+                float *o = g.out + (size_t)(m0 + rr) * g.ld + c;
+                if (vec && c + 4 <= g.ncols) {
+                    *reinterpret_cast<float4 *>(o) = val;
+                } else {
+                    const float w4[4] = {val.x, val.y, val.z, val.w};
+                    for (int j = 0; j < 4 && c + j < g.ncols; ++j) o[j] = w4[j];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&out_done);
+            if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&out_done, t & 1))) {
+                fail();
+                break;
             }
         }
     }
