@@ -218,3 +218,58 @@ def test_hybrid_queue_overflow_is_an_error():
         S.supa_destroy_batch(b)
         S.supa_surrogate_destroy(sur)
         S.supa_destroy_geometry(gh)
+
+
+def test_exported_diverted_particles_match_the_oracles_set_aside():
+    """supa_export_diverted: every particle the hybrid run queued, as a
+    sub-shower primary (entry slice, energy, position, direction), equals the
+    oracle's set-aside record of the same shower (matched by slice and
+    energy; the queue order is not defined)."""
+    import torch
+    g = inputs.supa_d(30)
+    n = 150
+    p = inputs.primaries(n, 17, e_lo=5.0, e_hi=40.0, theta_max_deg=30.0)
+    gh = S.supa_init_geometry(g)
+    sur = _surrogate()
+    b = S.supa_batch_create([gh], n, {})
+    try:
+        S.supa_batch_set_surrogate(b, sur, E_S, 1_000_000, S.SUPA_SURROGATE_MEAN)
+        S.supa_simulate(b, S.primaries_to_device(p), n, 9)
+        info = S.supa_batch_get_info(b)
+        m = S.supa_export_diverted(b)
+        assert m == info.n_diverted > 0
+        buf = torch.zeros(m * 24, dtype=torch.uint8, device="cuda")
+        assert S.supa_export_diverted(b, buf) == m
+        ex = buf.cpu().numpy().view(inputs.PRIMARY_DTYPE)
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_surrogate_destroy(sur)
+        S.supa_destroy_geometry(gh)
+    div = oracle.simulate(g, p, 9, n_threads=8, e_s=E_S)["div"]
+    assert abs(len(div["E"]) - m) <= max(2, 1e-3 * m)
+    k_ex = ex["geom"] >> 16
+    assert np.all(ex["geom"] & 0xFFFF == 0)
+    assert np.all(ex["E"] < E_S) and np.all(g.slice_to_layer[k_ex] >= 0)
+    # match each exported particle to the oracle record of nearest energy
+    # (energies are continuous: distinct up to float32 rounding)
+    ux = np.sin(ex["theta"].astype(np.float64)) * np.cos(ex["phi"].astype(np.float64))
+    uz = np.cos(ex["theta"].astype(np.float64))
+    oe = np.argsort(div["E"])
+    Eo = div["E"][oe]
+    j = np.clip(np.searchsorted(Eo, ex["E"].astype(np.float64)), 1, len(Eo) - 1)
+    j = np.where(np.abs(Eo[j - 1] - ex["E"]) < np.abs(Eo[j] - ex["E"]), j - 1, j)
+    o = oe[j]
+    # float32 stepping keeps an energy within ~1e-6 of FP64 after the ~8
+    # splits from E0 down to E_s
+    close = np.abs(div["E"][o] - ex["E"]) <= 3e-6 * ex["E"]
+    assert close.mean() > 0.999
+    # a nearest-energy pair is unambiguous where no other oracle energy is
+    # within twice that
+    gap = np.minimum(np.abs(np.diff(Eo, prepend=-1.0)), np.abs(np.diff(Eo, append=1e30)))[j]
+    ok = close & (gap > 6e-6 * ex["E"])
+    assert ok.mean() > 0.8
+    assert np.array_equal(k_ex[ok], div["k"][o][ok])
+    np.testing.assert_allclose(ex["x0"][ok], div["x"][o][ok], rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(ex["y0"][ok], div["y"][o][ok], rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(ux[ok], div["ux"][o][ok], atol=1e-5)
+    np.testing.assert_allclose(uz[ok], div["uz"][o][ok], atol=1e-5)
