@@ -125,4 +125,12 @@ def compare(gpu, ora, geoms, prims, pos_rtol=RTOL):
     tot = gpu["layer_sum"].sum(1) + gpu["dead"] + gpu["leak"] + gpu["escape"]
     bound = (ora["n_splits"] + 1) * 2.0 ** -22 * E0 + 1e-12
     assert np.all(np.abs(tot - E0) <= bound), np.max(np.abs(tot - E0) / bound)
+    lo, lg = ora["layer_sum"][ok_keys], gpu["layer_sum"][ok_keys][:, :L]
+    nz = lo > 0
+    stats.update(
+        max_err_layer_sum=float((np.abs(lg - lo)[nz] / lo[nz]).max(initial=0)),
+        max_err_conservation=float((np.abs(tot - E0) / E0).max(initial=0)),
+        hit_counts_equal=float(np.mean(g_cnt == o_cnt)),
+        steps_equal=float(np.mean(gpu["steps"].astype(np.int64) == ora["steps"])),
+    )
     return stats

@@ -65,6 +65,39 @@ def test_c1_workload_parity():
     assert st["n_flip_showers"] <= 2
 
 
+def test_error_report_c2_shapes():
+    """The error of each output against the FP64 oracle on C2-shaped showers
+    (printed as one JSON line; the asserts are the stated tolerances)."""
+    import json
+
+    import torch
+    g = inputs.supa_d(30, grid=64, roi_mode=inputs.ROI_AXIS)
+    p = inputs.primaries(400, 41, e_lo=1.0, e_hi=100.0, theta_max_deg=30.0, entry_halfwidth=0.25)
+    st, gpu, ora = _check([g], p, seed=23)
+    rx, ry = oracle.roi_origins(g, p)
+    grid_o, oor_o = oracle.voxelize(ora["x"], ora["y"], ora["z"], ora["E"], ora["offsets"], g, rx, ry)
+    gh = S.supa_init_geometry(g)
+    b = S.supa_batch_create([gh], len(p), {})
+    try:
+        S.supa_simulate(b, S.primaries_to_device(p), len(p), 23)
+        S.supa_batch_get_info(b)
+        grid = torch.zeros((len(p), 30, 64, 64), dtype=torch.float32, device="cuda")
+        oor = torch.zeros(len(p), dtype=torch.float64, device="cuda")
+        S.supa_voxelize(b, 0, len(p), grid, oor)
+        grid_g = grid.cpu().numpy().astype(np.float64)
+        oor_g = oor.cpu().numpy()
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_destroy_geometry(gh)
+    on = (grid_o != 0) | (grid_g != 0)
+    cell_err = np.abs(grid_g - grid_o)[on] / np.maximum(np.abs(grid_o[on]), 1e-30)
+    st.update(cells_nonzero=int(on.sum()), cells_off_by_more_than_1e5=float(np.mean(cell_err > 1e-5)),
+              max_err_out_of_roi=float((np.abs(oor_g - oor_o) / np.maximum(oor_o, 1e-9)).max()))
+    print("ERROR_REPORT " + json.dumps(st))
+    assert st["cells_off_by_more_than_1e5"] < 1e-4
+    assert st["hit_counts_equal"] > 0.99 and st["steps_equal"] > 0.99
+
+
 def test_inclined_showers_axis_roi_parity():
     g = inputs.supa_d(30, grid=64, roi_mode=inputs.ROI_AXIS)
     p = inputs.primaries(300, 21, e_lo=1.0, e_hi=100.0, theta_max_deg=45.0, entry_halfwidth=0.25)
