@@ -541,6 +541,7 @@ def run_supa_serial(args):
         "roofline": roof, "gpu_launches": launches, "clocks": clk,
     }
 
+    out["shower_shapes"] = shape_timing(S, b, n, L, hits_per_shower)
     if not args.no_e2e:
         out["e2e"] = e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world)
     if world == 1 and args.workload == "c2" and not args.no_hybrid:
@@ -748,6 +749,28 @@ def run_surrogate(args):
         print(json.dumps(row), flush=True)
     S.supa_destroy_geometry(gh)
     print(json.dumps(out), flush=True)
+
+
+def shape_timing(S, b, n, L, hits_per_shower):
+    """The shower shape variables (Sec. 5.1, App. A.1) of every shower of the
+    last simulation, outside the timed step: showers/s and the achieved
+    bandwidth of algorithmic bytes (hits read once, FP64 layer sums, features
+    written)."""
+    import torch
+    lf = torch.empty((n, L, 18), dtype=torch.float32, device="cuda")
+    sf = torch.empty((n, 5), dtype=torch.float32, device="cuda")
+    S.supa_shower_shapes(b, 0, n, lf, sf)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 3
+    for _ in range(reps):
+        S.supa_shower_shapes(b, 0, n, lf, sf)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    per = 16 * hits_per_shower + 8 * L + 4 * (18 * L + 5)
+    return {"showers_per_s": n / (ms / 1000.0), "ms": ms, "bytes_per_shower": per,
+            "achieved_gbs": n * per / (ms / 1000.0) / 1e9, "kernel": "supa_shape_kernel"}
 
 
 def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):

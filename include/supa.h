@@ -237,6 +237,24 @@ int supa_profiles(supa_batch *b, int64_t shower_begin, int64_t shower_end, int32
  * without ordering) race and give wrong offsets.  Asynchronous on stream. */
 int supa_shower_offsets_noalloc(const uint32_t *counts_dev, int64_t n, int64_t *offsets_dev, void *stream);
 
+/* Shower shape variables (Sec. 5.1 "Shower Shape Variables", App. A.1
+ * "More shower shape variables") of showers [shower_begin, shower_end) of
+ * the last simulation, from its point clouds (stepped and surrogate hits)
+ * and FP64 layer sums.  Lateral coordinates of a point: (eta, phi) = (x, y)
+ * minus the incidence axis through the impact point at the point's depth,
+ * r = sqrt(eta^2 + phi^2).  layer_feats_dev float32 [n][L][18] with
+ * L = supa_batch_info.max_layers, per layer i (0-based):
+ *   n_i, Ebar_i, f_i = Ebar_i / E_tot, means of eta, phi, r, E over the
+ *   points, their standard deviations, the energy-weighted centroids of
+ *   eta, phi, r, the energy-weighted widths of eta, phi, r, and
+ *   E_ratio = (E[1] - E[2]) / (E[1] + E[2]) of the two largest point
+ *   energies (E[2] = 0 for one point); all 0 for an empty layer;
+ * shower_feats_dev float32 [n][5]: E_tot, depth d (deepest layer with
+ * energy, -1 if none), l_d = sum_i i Ebar_i, s_d = l_d / E_tot,
+ * sigma_sd = sqrt(sum_i i^2 Ebar_i / E_tot - s_d^2).  Asynchronous. */
+int supa_shower_shapes(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *layer_feats_dev,
+                       float *shower_feats_dev, void *stream);
+
 /* Downsample caller-provided hits: hits_dev float4 (x,y,z,E), shower s owns
  * hits [offsets_dev[s], offsets_dev[s+1]); a hit's layer is
  * slice_to_layer[rint(z/dz)] of geometry g; roi_x0_dev/roi_y0_dev are the low

@@ -895,6 +895,36 @@ int supa_profiles(supa_batch *b, int64_t shower_begin, int64_t shower_end, int32
     return SUPA_OK;
 }
 
+int supa_shower_shapes(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *layer_feats_dev,
+                       float *shower_feats_dev, void *stream) {
+    if (!b || !layer_feats_dev || !shower_feats_dev)
+        return fail(SUPA_ERR_INVALID_ARG, "supa_shower_shapes: null argument");
+    if (b->last_n < 0) return fail(SUPA_ERR_NOT_READY, "no simulation has been enqueued on this batch");
+    if (shower_begin < 0 || shower_end < shower_begin || shower_end > b->last_n)
+        return fail(SUPA_ERR_INVALID_ARG, "shower range outside the batch");
+    ShapeParams p{};
+    p.src.pool = b->d_pool;
+    p.src.page_next = b->d_page_next;
+    p.src.hit_start = b->d_hit_start;
+    p.src.hit_count = b->d_hit_count;
+    if (b->sur) {
+        p.src.sur_hits = b->d_sur_hits;
+        p.src.sur_off = b->d_soff;
+        p.src.sur_count = b->d_scount;
+    }
+    p.prim = b->d_prim;
+    p.geoms = b->d_geoms;
+    p.s2l = b->d_s2l;
+    p.lsum = b->d_lsum;
+    p.s_begin = shower_begin;
+    p.n_showers = shower_end - shower_begin;
+    p.L = b->max_layers;
+    p.layer_feats = layer_feats_dev;
+    p.shower_feats = shower_feats_dev;
+    SUPA_CUDA(launch_shower_shapes(p, (cudaStream_t)stream));
+    return SUPA_OK;
+}
+
 int supa_voxelize_hits(const supa_geometry *g, const float *hits_dev, const int64_t *offsets_dev, int64_t n_showers,
                        const float *roi_x0_dev, const float *roi_y0_dev, float *grid_dev, double *out_of_roi_dev,
                        void *stream) {

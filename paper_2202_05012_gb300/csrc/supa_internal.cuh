@@ -252,6 +252,21 @@ struct ProfileParams {
 };
 cudaError_t launch_profiles(const ProfileParams &p, cudaStream_t st);
 
+// Shower shape variables (Sec. 5.1, App. A.1) of a range of showers.
+constexpr int kShapeLayerFeats = 18, kShapeShowerFeats = 5;
+struct ShapeParams {
+    HitSource src;
+    const supa_primary *prim;
+    const GeomDev *geoms;
+    const int8_t *s2l;
+    const double *lsum;  // [n][L]
+    int64_t s_begin, n_showers;
+    int L;
+    float *layer_feats;   // [n_showers][L][18]
+    float *shower_feats;  // [n_showers][5]
+};
+cudaError_t launch_shower_shapes(const ShapeParams &p, cudaStream_t st);
+
 // Training targets R_j (mean lateral distances) of a batch of sub-showers.
 struct LateralParams {
     HitSource src;

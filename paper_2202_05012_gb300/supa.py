@@ -30,6 +30,7 @@ EXPORTED = (
     "supa_surrogate_destroy", "supa_surrogate_get_params", "supa_surrogate_gradients", "supa_surrogate_train_step",
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
     "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc", "supa_export_diverted",
+    "supa_shower_shapes",
 )
 
 
@@ -119,6 +120,7 @@ def lib(build_if_missing: bool = True):
         L.supa_profiles.argtypes = [_VP, _I64, _I64, ctypes.c_int32, ctypes.c_float, _VP, _VP, _VP]
         L.supa_shower_offsets_noalloc.argtypes = [_VP, _I64, _VP, _VP]
         L.supa_export_diverted.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I64), _VP]
+        L.supa_shower_shapes.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP]
         for name in EXPORTED[1:]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -334,6 +336,13 @@ def supa_shower_offsets_noalloc(counts_dev, n: int, offsets_dev, stream=None):
 def supa_build_training_set(b: int, e_s: float, x_dev, y_dev, stream=None):
     _check(lib().supa_build_training_set(b, float(e_s), _ptr(x_dev), _ptr(y_dev), _stream(stream)),
            "supa_build_training_set")
+
+
+def supa_shower_shapes(b: int, shower_begin: int, shower_end: int, layer_feats_dev, shower_feats_dev, stream=None):
+    """Shower shape variables: layer_feats_dev float32 [n][max_layers][18],
+    shower_feats_dev float32 [n][5] (see include/supa.h)."""
+    _check(lib().supa_shower_shapes(b, int(shower_begin), int(shower_end), _ptr(layer_feats_dev),
+                                    _ptr(shower_feats_dev), _stream(stream)), "supa_shower_shapes")
 
 
 def supa_export_diverted(b: int, out_dev=None, stream=None) -> int:
