@@ -91,6 +91,27 @@ def supa_v1() -> Geometry:
     )
 
 
+def supa_calogan() -> Geometry:
+    """A CaloGAN-like detector (Sec. 3.2, "Datasets and calorimeter
+    structure"; the grid experiments): three readout layers in proportion to
+    CaloGAN's 90, 347 and 43 mm, here 6, 22 and 3 slices of the SUPA-D model
+    (the paper does not give its slice split), over a 16 dz square region
+    with the cells of calogan_grids()."""
+    s2l = np.array([0] * 6 + [1] * 22 + [2] * 3, dtype=np.int32)
+    n = len(s2l)
+    return Geometry(
+        n_slices=n, dz=1.0, slice_to_layer=s2l, n_layers=3, p_stop=np.full(n, 0.02), p_split=np.full(n, 0.5),
+        nx=12, ny=12, wx=16.0 / 12, wy=16.0 / 12, roi_mode=ROI_FIXED,
+    )
+
+
+def calogan_grids(width: float = 16.0) -> list[tuple[int, int, float, float]]:
+    """Per-layer cells (nx, ny, wx, wy) of the CaloGAN-like detector at "1x":
+    3 x 96, 12 x 12 and 12 x 6 (rows x columns: ny x nx) over one square
+    region of side `width`."""
+    return [(nx, ny, width / nx, width / ny) for (ny, nx) in ((3, 96), (12, 12), (12, 6))]
+
+
 def primaries(n: int, seed: int, *, e_lo: float, e_hi: float, log_uniform: bool = False,
               theta_max_deg: float = 0.0, entry_halfwidth: float = 0.0, n_geoms: int = 1) -> np.ndarray:
     """Seeded primaries: energy U[e_lo, e_hi] (or log-uniform), polar angle
