@@ -542,6 +542,8 @@ def run_supa_serial(args):
     }
 
     out["shower_shapes"] = shape_timing(S, b, n, L, hits_per_shower)
+    if world == 1:
+        out["calogan_multires"] = calogan_timing(S)
     if not args.no_e2e:
         out["e2e"] = e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world)
     if world == 1 and args.workload == "c2" and not args.no_hybrid:
@@ -749,6 +751,44 @@ def run_surrogate(args):
         print(json.dumps(row), flush=True)
     S.supa_destroy_geometry(gh)
     print(json.dumps(out), flush=True)
+
+
+def calogan_timing(S, n=200_000):
+    """Per-layer grids at several resolutions: showers of the CaloGAN-like
+    detector (E U[1,100], normal incidence at the origin) imaged at 1x, 2x
+    and 3x (3x96 / 12x12 / 12x6 cells at 1x) from one pass over the hits;
+    showers/s and the achieved bandwidth of algorithmic bytes (hits read
+    once, images written)."""
+    import torch
+
+    from paper_2202_05012_gb300 import inputs
+    g = inputs.supa_calogan()
+    p = inputs.primaries(n, 71, e_lo=1.0, e_hi=100.0)
+    gh = S.supa_init_geometry(g)
+    b = S.supa_batch_create([gh], n, {"max_hits": n * 1500 + (8 << 20), "lpt_order": 1})
+    try:
+        S.supa_simulate(b, S.primaries_to_device(p), n, 71)
+        info = S.supa_batch_get_info(b)
+        grids, factors = inputs.calogan_grids(), [1, 2, 3]
+        C = S.supa_layer_images_cells(grids, factors)
+        img = torch.empty((n, C), dtype=torch.float32, device="cuda")
+        oor = torch.empty((n, len(factors)), dtype=torch.float64, device="cuda")
+        S.supa_voxelize_layers(b, 0, n, grids, factors, img, oor)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record()
+        for _ in range(reps):
+            S.supa_voxelize_layers(b, 0, n, grids, factors, img, oor)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        per = 4 * C + 16 * info.n_hits / n + 8 * len(factors)
+        return {"showers": n, "factors": factors, "cells_per_shower": C, "showers_per_s": n / (ms / 1000.0),
+                "ms": ms, "bytes_per_shower": per, "achieved_gbs": n * per / (ms / 1000.0) / 1e9,
+                "hits_per_shower": info.n_hits / n, "kernel": "supa_grid_kernel"}
+    finally:
+        S.supa_destroy_batch(b)
+        S.supa_destroy_geometry(gh)
 
 
 def shape_timing(S, b, n, L, hits_per_shower):

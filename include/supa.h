@@ -237,6 +237,36 @@ int supa_profiles(supa_batch *b, int64_t shower_begin, int64_t shower_end, int32
  * without ordering) race and give wrong offsets.  Asynchronous on stream. */
 int supa_shower_offsets_noalloc(const uint32_t *counts_dev, int64_t n, int64_t *offsets_dev, void *stream);
 
+/* Per-layer grids and resolutions (App. A.5 "Downsampling"; the grid
+ * experiments use a CaloGAN-like detector with 3 x 96, 12 x 12 and 12 x 6
+ * cells per layer at resolutions "1x", "2x", "3x").  Layer l has nx x ny
+ * cells of wx x wy (x fastest), over a region placed like the geometry's
+ * uniform grid (roi_mode).  At factor f every cell is split f times in both
+ * directions: cells of wx/f x wy/f (float32), nx f x ny f of them. */
+typedef struct supa_layer_grid {
+    int32_t nx, ny;
+    float wx, wy;
+} supa_layer_grid;
+
+/* Cells per shower of supa_voxelize_layers' output for these grids and
+ * factors (1 <= factor <= 16, at most 8 factors, one grid per layer), or
+ * SUPA_ERR_INVALID_ARG. */
+int64_t supa_layer_images_cells(const supa_layer_grid *grids, int32_t n_grids, const int32_t *factors,
+                                int32_t n_factors);
+
+/* Images of showers [shower_begin, shower_end) at every factor from one
+ * pass over their hits: images_dev float32 [n][cells] (16-byte aligned),
+ * per shower for each factor in the given order, for each layer, ny f rows
+ * of nx f cells; cell (i, j) sums the energy of the points with
+ * floor((x - lo) / (wx/f)) = i and floor((y - lo_y) / (wy/f)) = j, both in
+ * float32.  out_of_roi_dev (nullable) float64 [n][n_factors]: energy of the
+ * points outside their layer's region at that factor.  n_grids must cover
+ * supa_batch_info.max_layers; a shower's images must fit in shared memory
+ * (at most 51,200 cells).  Asynchronous. */
+int supa_voxelize_layers(supa_batch *b, int64_t shower_begin, int64_t shower_end, const supa_layer_grid *grids,
+                         int32_t n_grids, const int32_t *factors, int32_t n_factors, float *images_dev,
+                         double *out_of_roi_dev, void *stream);
+
 /* Shower shape variables (Sec. 5.1 "Shower Shape Variables", App. A.1
  * "More shower shape variables") of showers [shower_begin, shower_end) of
  * the last simulation, from its point clouds (stepped and surrogate hits)

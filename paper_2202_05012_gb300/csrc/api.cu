@@ -895,6 +895,82 @@ int supa_profiles(supa_batch *b, int64_t shower_begin, int64_t shower_end, int32
     return SUPA_OK;
 }
 
+// Cell layout of the per-layer, multi-resolution images (shared by the
+// size query and the call).
+static int64_t layer_grid_layout(const supa_layer_grid *grids, int32_t n_grids, const int32_t *factors,
+                                 int32_t n_factors, GridParams *p) {
+    if (!grids || !factors || n_grids < 1 || n_grids > SUPA_MAX_LAYERS || n_factors < 1 ||
+        n_factors > kMaxGridFactors)
+        return -1;
+    int64_t cells = 0;
+    for (int r = 0; r < n_factors; ++r) {
+        const int f = factors[r];
+        if (f < 1 || f > 16) return -1;
+        for (int l = 0; l < n_grids; ++l) {
+            const supa_layer_grid &g = grids[l];
+            if (g.nx < 1 || g.ny < 1 || g.nx > 4096 || g.ny > 4096 || !(g.wx > 0.0f) || !(g.wy > 0.0f) ||
+                !std::isfinite(g.wx) || !std::isfinite(g.wy))
+                return -1;
+            if (p) p->base[r][l] = (int)cells;
+            cells += (int64_t)g.nx * f * g.ny * f;
+            if (cells > ((int64_t)1 << 30)) return -1;
+        }
+    }
+    if (p) {
+        p->n_layers = n_grids;
+        p->n_res = n_factors;
+        for (int r = 0; r < n_factors; ++r) p->factor[r] = factors[r];
+        for (int l = 0; l < n_grids; ++l) p->grid[l] = {grids[l].nx, grids[l].ny, grids[l].wx, grids[l].wy};
+        p->cells = (int)cells;
+    }
+    return cells;
+}
+
+int64_t supa_layer_images_cells(const supa_layer_grid *grids, int32_t n_grids, const int32_t *factors,
+                                int32_t n_factors) {
+    const int64_t c = layer_grid_layout(grids, n_grids, factors, n_factors, nullptr);
+    if (c < 0) fail(SUPA_ERR_INVALID_ARG, "supa_layer_images_cells: bad grids or factors");
+    return c < 0 ? SUPA_ERR_INVALID_ARG : c;
+}
+
+int supa_voxelize_layers(supa_batch *b, int64_t shower_begin, int64_t shower_end, const supa_layer_grid *grids,
+                         int32_t n_grids, const int32_t *factors, int32_t n_factors, float *images_dev,
+                         double *out_of_roi_dev, void *stream) {
+    if (!b || !images_dev) return fail(SUPA_ERR_INVALID_ARG, "supa_voxelize_layers: null argument");
+    if (b->last_n < 0) return fail(SUPA_ERR_NOT_READY, "no simulation has been enqueued on this batch");
+    if (shower_begin < 0 || shower_end < shower_begin || shower_end > b->last_n)
+        return fail(SUPA_ERR_INVALID_ARG, "shower range outside the batch");
+    if ((uintptr_t)images_dev & 15) return fail(SUPA_ERR_INVALID_ARG, "images_dev must be 16-byte aligned");
+    GridParams p{};
+    const int64_t cells = layer_grid_layout(grids, n_grids, factors, n_factors, &p);
+    if (cells < 0) return fail(SUPA_ERR_INVALID_ARG, "supa_voxelize_layers: bad grids or factors");
+    if (n_grids < b->max_layers)
+        return fail(SUPA_ERR_INVALID_ARG, "supa_voxelize_layers: %d grids for %d layers", n_grids, b->max_layers);
+    if (grid_smem_bytes((int)cells) > 200 * 1024)
+        return fail(SUPA_ERR_INVALID_ARG, "supa_voxelize_layers: %lld cells per shower exceed shared memory",
+                    (long long)cells);
+    p.src.pool = b->d_pool;
+    p.src.page_next = b->d_page_next;
+    p.src.hit_start = b->d_hit_start;
+    p.src.hit_count = b->d_hit_count;
+    if (b->sur) {
+        p.src.sur_hits = b->d_sur_hits;
+        p.src.sur_off = b->d_soff;
+        p.src.sur_count = b->d_scount;
+    }
+    p.prim = b->d_prim;
+    p.geoms = b->d_geoms;
+    p.s2l = b->d_s2l;
+    p.zmid = b->d_zmid;
+    p.s_begin = shower_begin;
+    p.n_showers = shower_end - shower_begin;
+    p.single_geom = b->geoms.size() == 1 ? 1 : 0;
+    p.images = images_dev;
+    p.oor = out_of_roi_dev;
+    SUPA_CUDA(launch_voxelize_layers(p, (cudaStream_t)stream));
+    return SUPA_OK;
+}
+
 int supa_shower_shapes(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *layer_feats_dev,
                        float *shower_feats_dev, void *stream) {
     if (!b || !layer_feats_dev || !shower_feats_dev)

@@ -252,6 +252,32 @@ struct ProfileParams {
 };
 cudaError_t launch_profiles(const ProfileParams &p, cudaStream_t st);
 
+// Per-layer grids at several resolutions (grids.cu).
+constexpr int kMaxGridFactors = 8;
+struct LayerGridDev {
+    int nx, ny;
+    float wx, wy;
+};
+struct GridParams {
+    HitSource src;
+    const supa_primary *prim;
+    const GeomDev *geoms;
+    const int8_t *s2l;
+    const float *zmid;
+    int64_t s_begin, n_showers;
+    int single_geom;
+    int n_layers;  // grids given (layers at or past it: out of region)
+    LayerGridDev grid[SUPA_MAX_LAYERS];
+    int n_res;
+    int factor[kMaxGridFactors];
+    int base[kMaxGridFactors][SUPA_MAX_LAYERS];  // first cell of (factor, layer) in a shower's images
+    int cells;                                   // cells per shower
+    float *images;                               // [n_showers][cells]
+    double *oor;                                 // [n_showers][n_res], nullable
+};
+size_t grid_smem_bytes(int cells);
+cudaError_t launch_voxelize_layers(const GridParams &p, cudaStream_t st);
+
 // Shower shape variables (Sec. 5.1, App. A.1) of a range of showers.
 constexpr int kShapeLayerFeats = 18, kShapeShowerFeats = 5;
 struct ShapeParams {

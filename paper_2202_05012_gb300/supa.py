@@ -30,7 +30,7 @@ EXPORTED = (
     "supa_surrogate_destroy", "supa_surrogate_get_params", "supa_surrogate_gradients", "supa_surrogate_train_step",
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
     "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc", "supa_export_diverted",
-    "supa_shower_shapes",
+    "supa_shower_shapes", "supa_layer_images_cells", "supa_voxelize_layers",
 )
 
 
@@ -121,8 +121,12 @@ def lib(build_if_missing: bool = True):
         L.supa_shower_offsets_noalloc.argtypes = [_VP, _I64, _VP, _VP]
         L.supa_export_diverted.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I64), _VP]
         L.supa_shower_shapes.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP]
+        L.supa_layer_images_cells.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
+        L.supa_voxelize_layers.argtypes = [_VP, _I64, _I64, _VP, ctypes.c_int32, _VP, ctypes.c_int32, _VP, _VP,
+                                           _VP]
         for name in EXPORTED[1:]:
             getattr(L, name).restype = ctypes.c_int
+        L.supa_layer_images_cells.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -343,6 +347,36 @@ def supa_shower_shapes(b: int, shower_begin: int, shower_end: int, layer_feats_d
     shower_feats_dev float32 [n][5] (see include/supa.h)."""
     _check(lib().supa_shower_shapes(b, int(shower_begin), int(shower_end), _ptr(layer_feats_dev),
                                     _ptr(shower_feats_dev), _stream(stream)), "supa_shower_shapes")
+
+
+class supa_layer_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("wx", ctypes.c_float), ("wy", ctypes.c_float)]
+
+
+def _grid_args(grids, factors):
+    g = (supa_layer_grid * len(grids))(*[supa_layer_grid(int(nx), int(ny), float(wx), float(wy))
+                                         for (nx, ny, wx, wy) in grids])
+    f = (ctypes.c_int32 * len(factors))(*[int(x) for x in factors])
+    return g, f
+
+
+def supa_layer_images_cells(grids, factors) -> int:
+    """Cells per shower of supa_voxelize_layers for grids [(nx, ny, wx, wy)] per layer and factors."""
+    g, f = _grid_args(grids, factors)
+    c = lib().supa_layer_images_cells(g, len(grids), f, len(factors))
+    if c < 0:
+        _check(int(c), "supa_layer_images_cells")
+    return int(c)
+
+
+def supa_voxelize_layers(b: int, shower_begin: int, shower_end: int, grids, factors, images_dev,
+                         out_of_roi_dev=None, stream=None):
+    """Per-layer grids at every factor from one pass over the hits: images_dev
+    float32 [n][cells], out_of_roi_dev float64 [n][len(factors)] or None."""
+    g, f = _grid_args(grids, factors)
+    _check(lib().supa_voxelize_layers(b, int(shower_begin), int(shower_end), g, len(grids), f, len(factors),
+                                      _ptr(images_dev), _ptr(out_of_roi_dev), _stream(stream)),
+           "supa_voxelize_layers")
 
 
 def supa_export_diverted(b: int, out_dev=None, stream=None) -> int:

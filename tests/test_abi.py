@@ -90,3 +90,16 @@ def test_null_arguments_rejected_without_gpu():
     assert L.supa_voxelize(None, 0, 1, None, None, None) == S.SUPA_ERR_INVALID_ARG
     assert L.supa_simulate(None, None, 1, 0, 0, None) == S.SUPA_ERR_INVALID_ARG
     assert "null" in S.supa_last_error()
+
+
+def test_layer_image_sizes_and_their_validation():
+    grids = inputs.calogan_grids()
+    # 3x96 + 12x12 + 12x6 = 504 cells at 1x; x4 at 2x, x9 at 3x
+    assert S.supa_layer_images_cells(grids, [1]) == 504
+    assert S.supa_layer_images_cells(grids, [1, 2, 3]) == 504 * (1 + 4 + 9)
+    for bad_grids, bad_factors in (([(0, 12, 1.0, 1.0)], [1]), ([(12, 12, -1.0, 1.0)], [1]),
+                                   ([(12, 12, 1.0, float("nan"))], [1]), (grids, [0]), (grids, [17]),
+                                   (grids, [1] * 9)):
+        with pytest.raises(S.SupaError) as ei:
+            S.supa_layer_images_cells(bad_grids, bad_factors)
+        assert ei.value.code == S.SUPA_ERR_INVALID_ARG
