@@ -52,6 +52,10 @@ class _Geom(ctypes.Structure):
         ("eps_mode", ctypes.c_int), ("eps_frac", ctypes.c_double),
         ("split_mode", ctypes.c_int), ("e_min", ctypes.c_double), ("uz_min", ctypes.c_double),
         ("e_s", ctypes.c_double),
+        ("n_regions", ctypes.c_int), ("region_radius", ctypes.POINTER(ctypes.c_double)),
+        ("region_p_stop", ctypes.POINTER(ctypes.c_double)), ("region_p_split", ctypes.POINTER(ctypes.c_double)),
+        ("region_theta_lo", ctypes.POINTER(ctypes.c_double)), ("region_theta_hi", ctypes.POINTER(ctypes.c_double)),
+        ("region_eps_frac", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -128,6 +132,16 @@ def simulate(geom, prims: np.ndarray, seed: int, shower_id_base: int = 0, n_thre
               ps.ctypes.data_as(_P(ctypes.c_double)), pp.ctypes.data_as(_P(ctypes.c_double)),
               int(geom.theta_mode), float(geom.theta_lo), float(geom.theta_hi), int(geom.eps_mode),
               float(geom.eps_frac), int(geom.split_mode), float(geom.e_min), float(geom.uz_min), float(e_s))
+    keep = []
+    reg = getattr(geom, "regions", None)
+    if reg is not None and reg.n > 1:
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in
+                (reg.radius, reg.p_stop, reg.p_split, reg.theta_lo, reg.theta_hi, reg.eps_frac)]
+        keep.extend(arrs)
+        g.n_regions = reg.n
+        for name, a in zip(("region_radius", "region_p_stop", "region_p_split", "region_theta_lo",
+                            "region_theta_hi", "region_eps_frac"), arrs):
+            setattr(g, name, a.ctypes.data_as(_P(ctypes.c_double)))
     n = len(prims)
     assert ctypes.sizeof(_Primary) == _PRIMARY_NP.itemsize
     pr = np.zeros(max(n, 1), dtype=_PRIMARY_NP)

@@ -192,20 +192,41 @@ static int simulate_one(const ora_geom *g, const ora_primary *p, uint64_t seed,
         }
         acc->steps += 1;
 
+        /* The particle's lateral region at this slice (R26) selects the
+         * meta-parameters: r^2 = x^2 + y^2 against the squared radii, both in
+         * float32 (the kernel's precision). */
+        const double *p_stop = g->p_stop, *p_split = g->p_split;
+        double theta_lo = g->theta_lo, theta_hi = g->theta_hi, eps_frac = g->eps_frac;
+        if (g->n_regions > 1) {
+            const float xf = (float)q.x, yf = (float)q.y;
+            const float r2 = fmaf(xf, xf, yf * yf);
+            int reg = 0;
+            while (reg < g->n_regions - 1) {
+                const float b = (float)g->region_radius[reg];
+                if (r2 < b * b) break;
+                ++reg;
+            }
+            p_stop = g->region_p_stop + (size_t)reg * (size_t)g->n_slices;
+            p_split = g->region_p_split + (size_t)reg * (size_t)g->n_slices;
+            theta_lo = g->region_theta_lo[reg];
+            theta_hi = g->region_theta_hi[reg];
+            eps_frac = g->region_eps_frac[reg];
+        }
+
         /* Algorithm 1: draw theta, eps, alpha (and omega) for (shower, slice, lineage). */
         const uint32_t ctr[4] = {(uint32_t)shower_id, (uint32_t)k,
                                  (uint32_t)q.lineage, (uint32_t)(q.lineage >> 32)};
         uint32_t r[4];
         ora_philox4x32_10(ctr, key, r);
         const double alpha = (double)r[0] * (1.0 / 4294967296.0);
-        double theta = g->theta_lo;
+        double theta = theta_lo;
         if (g->theta_mode == ORA_THETA_UNIFORM)
-            theta = g->theta_lo + (g->theta_hi - g->theta_lo) * unif24(r[1]);
+            theta = theta_lo + (theta_hi - theta_lo) * unif24(r[1]);
         double eps = 0.0;
         if (g->eps_mode == ORA_EPS_UNIFORM)
-            eps = -g->eps_frac * theta + 2.0 * g->eps_frac * theta * unif24(r[2]);
+            eps = -eps_frac * theta + 2.0 * eps_frac * theta * unif24(r[2]);
 
-        const int stop = (alpha < g->p_stop[k]) || ((float)q.E < (float)g->e_min);
+        const int stop = (alpha < p_stop[k]) || ((float)q.E < (float)g->e_min);
         if (stop) {
             /* "Active <- False": the particle deposits its energy at slice k. */
             const int layer = g->slice_to_layer[k];
@@ -216,7 +237,7 @@ static int simulate_one(const ora_geom *g, const ora_primary *p, uint64_t seed,
                 if (push_hit(w, h)) return -1;
                 acc->layer_sum[layer] += q.E;
             }
-        } else if (alpha < g->p_stop[k] + g->p_split[k]) {
+        } else if (alpha < p_stop[k] + p_split[k]) {
             /* Split into two daughters (R2, R4). */
             const double omega = 2.0 * M_PI * unif24(r[3]);
             const double E0 = q.E * (theta / 2.0 + eps) / theta;

@@ -44,6 +44,19 @@ typedef struct {
     double e_s;                 /* hybrid path: a particle below e_s on a  */
                                 /* readout slice is set aside, not stepped */
                                 /* (0 = plain path)                        */
+    /* Lateral regions (Sec. 4.2: slices divided into regions with their own
+     * meta-parameters).  n_regions <= 1: none.  Otherwise region i holds
+     * the particles with region_radius[i-1] <= r < region_radius[i]
+     * (r^2 = x^2 + y^2 at the slice, compared in float32), and its
+     * p_stop / p_split (rows of [n_regions][n_slices]), theta range and
+     * eps_frac replace the geometry's. */
+    int n_regions;
+    const double *region_radius;    /* [n_regions - 1], increasing        */
+    const double *region_p_stop;    /* [n_regions][n_slices]              */
+    const double *region_p_split;   /* [n_regions][n_slices]              */
+    const double *region_theta_lo;  /* [n_regions]                        */
+    const double *region_theta_hi;  /* [n_regions]                        */
+    const double *region_eps_frac;  /* [n_regions]                        */
 } ora_geom;
 
 /* One primary: initial energy, impact position and incidence angles

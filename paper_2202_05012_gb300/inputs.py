@@ -54,10 +54,44 @@ class Geometry:
     wx: float = 0.5
     wy: float = 0.5
     roi_mode: int = ROI_FIXED
+    # lateral regions (Sec. 4.2): None, or a Regions record
+    regions: "Regions | None" = None
 
     def layer_slice_range(self, layer: int) -> tuple[int, int]:
         ks = np.nonzero(self.slice_to_layer == layer)[0]
         return int(ks.min()), int(ks.max())
+
+
+@dataclasses.dataclass
+class Regions:
+    """Concentric lateral regions around the z axis, each with its own
+    meta-parameters (Sec. 4.2): region i holds r in [radius[i-1], radius[i])
+    (radius[-1] = infinity); p_stop / p_split are [n_regions][n_slices]."""
+
+    radius: np.ndarray    # float64 [n_regions - 1], increasing
+    p_stop: np.ndarray    # float64 [n_regions][n_slices]
+    p_split: np.ndarray   # float64 [n_regions][n_slices]
+    theta_lo: np.ndarray  # float64 [n_regions]
+    theta_hi: np.ndarray  # float64 [n_regions]
+    eps_frac: np.ndarray  # float64 [n_regions]
+
+    @property
+    def n(self) -> int:
+        return len(self.theta_lo)
+
+
+def with_regions(g: Geometry, radius, p_stop, p_split, theta_lo, theta_hi, eps_frac) -> Geometry:
+    """Give geometry g lateral regions; scalar p_stop / p_split entries are
+    broadcast over the slices."""
+    R = len(theta_lo)
+    ps = np.array([np.full(g.n_slices, v, dtype=np.float64) if np.ndim(v) == 0 else np.asarray(v, np.float64)
+                   for v in p_stop])
+    pp = np.array([np.full(g.n_slices, v, dtype=np.float64) if np.ndim(v) == 0 else np.asarray(v, np.float64)
+                   for v in p_split])
+    g.regions = Regions(np.asarray(radius, np.float64), ps.reshape(R, g.n_slices), pp.reshape(R, g.n_slices),
+                        np.asarray(theta_lo, np.float64), np.asarray(theta_hi, np.float64),
+                        np.asarray(eps_frac, np.float64))
+    return g
 
 
 def supa_d(n_layers: int, slices_per_layer: int = 3, n_dead_front: int = 0, *, p_stop: float = 0.02,
