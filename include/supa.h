@@ -46,6 +46,7 @@ extern "C" {
 #define SUPA_MAX_SLICES 255
 #define SUPA_MAX_LAYERS 64
 #define SUPA_MAX_GEOMS 8
+#define SUPA_MAX_REGIONS 8
 
 /* Split-angle laws p_theta and p_eps (Algorithm 1 "Parameters"; Table 2). */
 #define SUPA_THETA_FIXED 0   /* theta = theta_lo                          */
@@ -65,7 +66,20 @@ extern "C" {
 #define SUPA_ROI_AXIS 1  /* centred on the incidence axis at mid-layer depth */
 
 /* Geometry and model parameters (Algorithm 1 "Parameters"; Sec. 4.2 dead
- * material).  All arrays are host arrays of n_slices entries, copied. */
+ * material).  All arrays are host arrays of n_slices entries, copied.
+ *
+ * Lateral regions (Sec. 4.2: the slices may be divided into regions, each
+ * with its own meta-parameters).  n_regions 0 or 1: none.  Otherwise
+ * (2..SUPA_MAX_REGIONS) concentric regions around the z axis: a particle at
+ * (x, y) on slice k is in region i when region_radius[i-1] <= r <
+ * region_radius[i] (region_radius[-1] = 0, region_radius[n_regions-1] =
+ * infinity), decided in float32 as x*x + y*y (one fma) < b*b with b the
+ * float32 radius.  Region i then takes region_p_stop / region_p_split row i
+ * ([n_regions][n_slices], row-major), region_theta_lo[i] / theta_hi[i] and
+ * region_eps_frac[i] in place of p_stop, p_split, theta_lo, theta_hi and
+ * eps_frac (theta_mode, eps_mode, split_mode, e_min and uz_min stay
+ * global).  The same range rules apply per region; radii must be positive
+ * and increasing. */
 typedef struct {
     int32_t n_slices;              /* slices z_k = k*dz, k = 0..n_slices-1 (1..255) */
     float dz;                      /* slice gap Delta z (> 0)                       */
@@ -83,6 +97,13 @@ typedef struct {
     int32_t nx, ny;                /* image cells per layer; nx*ny multiple of 4    */
     float wx, wy;                  /* cell size                                     */
     int32_t roi_mode;              /* SUPA_ROI_*                                    */
+    int32_t n_regions;             /* lateral regions (0/1: none)                   */
+    const double *region_radius;   /* [n_regions-1] increasing outer radii          */
+    const double *region_p_stop;   /* [n_regions][n_slices]                         */
+    const double *region_p_split;  /* [n_regions][n_slices]                         */
+    const double *region_theta_lo; /* [n_regions]                                   */
+    const double *region_theta_hi; /* [n_regions]                                   */
+    const double *region_eps_frac; /* [n_regions]                                   */
 } supa_geometry_desc;
 
 /* One primary particle (Sec. 3 initial particle; Sec. 4.2 conditioning on

@@ -61,7 +61,8 @@ int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
 struct supa_geometry {
     GeomDev rec;  // slice_off = layer_off = 0
-    std::vector<unsigned long long> t_stop, t_ss;
+    std::vector<unsigned long long> t_stop, t_ss;  // [regions][n_slices]
+    std::vector<RegionDev> regions;                // empty without lateral regions
     std::vector<int8_t> s2l;
     std::vector<float> zmid;
     std::vector<LayerInfo> linfo;
@@ -78,9 +79,11 @@ struct supa_batch {
     int64_t max_showers = 0;
     int max_layers = 1;
     bool tags = false, lpt = false;
+    bool regions = false;  // some geometry has lateral regions
     // tables
     GeomDev *d_geoms = nullptr;
     unsigned long long *d_tstop = nullptr, *d_tss = nullptr;
+    RegionDev *d_regions = nullptr;
     int8_t *d_s2l = nullptr;
     float *d_zmid = nullptr;
     LayerInfo *d_linfo = nullptr;
@@ -168,11 +171,32 @@ int supa_init_geometry(const supa_geometry_desc *d, supa_geometry **out) {
     // splits at most once per slice.
     if (d->n_slices > 62 && !(d->e_min > 0.0))
         return fail(SUPA_ERR_INVALID_ARG, "more than 62 slices needs e_min > 0 to bound the lineage depth");
+    const int n_reg = d->n_regions > 1 ? d->n_regions : 1;
+    double ef_max = ef;
+    if (n_reg > 1) {
+        if (n_reg > SUPA_MAX_REGIONS)
+            return fail(SUPA_ERR_INVALID_ARG, "n_regions must be <= %d, got %d", SUPA_MAX_REGIONS, n_reg);
+        if (!d->region_radius || !d->region_p_stop || !d->region_p_split || !d->region_theta_lo ||
+            !d->region_theta_hi || !d->region_eps_frac)
+            return fail(SUPA_ERR_INVALID_ARG, "lateral regions need every region_* array");
+        for (int i = 0; i < n_reg - 1; ++i)
+            if (!(d->region_radius[i] > (i ? d->region_radius[i - 1] : 0.0)) || !std::isfinite(d->region_radius[i]))
+                return fail(SUPA_ERR_INVALID_ARG, "region radii must be positive, finite and increasing");
+        for (int i = 0; i < n_reg; ++i) {
+            const double lo = d->region_theta_lo[i];
+            const double hi = d->theta_mode == SUPA_THETA_FIXED ? lo : d->region_theta_hi[i];
+            if (!(lo > 0.0) || !(hi >= lo) || !(hi < M_PI / 2))
+                return fail(SUPA_ERR_INVALID_ARG, "region %d: need 0 < theta_lo <= theta_hi < pi/2", i);
+            const double f = d->eps_mode == SUPA_EPS_UNIFORM ? d->region_eps_frac[i] : 0.0;
+            if (!(f >= 0.0 && f < 0.5)) return fail(SUPA_ERR_INVALID_ARG, "region %d: eps_frac must be in [0, 1/2)", i);
+            ef_max = std::max(ef_max, f);
+        }
+    }
 
     supa_geometry *g = new supa_geometry();
     const int n = d->n_slices;
-    g->t_stop.resize(n);
-    g->t_ss.resize(n);
+    g->t_stop.resize((size_t)n * n_reg);
+    g->t_ss.resize((size_t)n * n_reg);
     g->s2l.resize(n);
     std::vector<int> kmin(d->n_layers, 1 << 30), kmax(d->n_layers, -1);
     for (int k = 0; k < n; ++k) {
@@ -188,6 +212,15 @@ int supa_init_geometry(const supa_geometry_desc *d, supa_geometry **out) {
         }
         g->t_stop[k] = threshold(ps);
         g->t_ss[k] = threshold(ps + pp);
+        for (int i = 0; n_reg > 1 && i < n_reg; ++i) {
+            const double rs = d->region_p_stop[(size_t)i * n + k], rp = d->region_p_split[(size_t)i * n + k];
+            if (!(rs >= 0.0 && rs <= 1.0 && rp >= 0.0 && rp <= 1.0) || rs + rp > 1.0 + 1e-12) {
+                delete g;
+                return fail(SUPA_ERR_INVALID_ARG, "region %d, slice %d: need p_stop, p_split in [0,1] and sum <= 1", i, k);
+            }
+            g->t_stop[(size_t)i * n + k] = threshold(rs);
+            g->t_ss[(size_t)i * n + k] = threshold(rs + rp);
+        }
         g->s2l[k] = (int8_t)l;
         if (l >= 0) {
             kmin[l] = std::min(kmin[l], k);
@@ -228,17 +261,27 @@ int supa_init_geometry(const supa_geometry_desc *d, supa_geometry **out) {
     // Each split leaves a daughter at most q = 1/2 + eps_frac of its parent's
     // energy and only particles with E >= e_min split, so a primary below
     // e_min * q^-61 splits at most 62 times on any path.
-    r.e0_max = d->n_slices <= 62 ? INFINITY : (float)std::min(3.0e38, d->e_min * std::pow(0.5 + ef, -61.0));
+    r.e0_max = d->n_slices <= 62 ? INFINITY : (float)std::min(3.0e38, d->e_min * std::pow(0.5 + ef_max, -61.0));
+    r.thr_off = 0;
+    r.n_regions = n_reg;
+    r.region_off = 0;
+    for (int i = 0; n_reg > 1 && i < n_reg; ++i) {
+        const float b = i < n_reg - 1 ? (float)d->region_radius[i] : INFINITY;
+        const double lo = d->region_theta_lo[i];
+        const double span = d->theta_mode == SUPA_THETA_UNIFORM ? d->region_theta_hi[i] - lo : 0.0;
+        const double f = d->eps_mode == SUPA_EPS_UNIFORM ? d->region_eps_frac[i] : 0.0;
+        g->regions.push_back(make_float4(b * b, (float)lo, (float)span, (float)f));
+    }
 
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = dalloc(&g->d_rec, 1);
-    if (e == cudaSuccess) e = dalloc(&g->d_tstop, n);
-    if (e == cudaSuccess) e = dalloc(&g->d_tss, n);
+    if (e == cudaSuccess) e = dalloc(&g->d_tstop, g->t_stop.size());
+    if (e == cudaSuccess) e = dalloc(&g->d_tss, g->t_ss.size());
     if (e == cudaSuccess) e = dalloc(&g->d_s2l, n);
     if (e == cudaSuccess) e = dalloc(&g->d_zmid, d->n_layers);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_rec, &g->rec, sizeof(GeomDev), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_tstop, g->t_stop.data(), n * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_tss, g->t_ss.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_tstop, g->t_stop.data(), g->t_stop.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_tss, g->t_ss.data(), g->t_ss.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_s2l, g->s2l.data(), n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_zmid, g->zmid.data(), d->n_layers * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -283,7 +326,7 @@ int supa_destroy_batch(supa_batch *b) {
     if (!b) return SUPA_OK;
     free_hybrid(b);
     cudaFree(b->d_linfo);
-    void *ptrs[] = {b->d_geoms, b->d_tstop, b->d_tss, b->d_s2l, b->d_zmid, b->d_prim, b->d_queue,
+    void *ptrs[] = {b->d_geoms, b->d_tstop, b->d_tss, b->d_regions, b->d_s2l, b->d_zmid, b->d_prim, b->d_queue,
                     b->d_bucket, b->d_pool, b->d_tags, b->d_page_next, b->d_hit_start, b->d_hit_count,
                     b->d_steps, b->d_lsum, b->d_dead, b->d_leak, b->d_escape, b->d_offsets, b->d_scan_tmp,
                     b->d_ctrl, b->d_totals, b->d_spill, b->d_stage};
@@ -319,14 +362,18 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     // concatenated geometry tables
     std::vector<GeomDev> recs;
     std::vector<unsigned long long> ts, tss;
+    std::vector<RegionDev> regs;
     std::vector<int8_t> s2l;
     std::vector<float> zm;
     std::vector<LayerInfo> li;
     for (int i = 0; i < n_geoms; ++i) {
         GeomDev r = geoms[i]->rec;
-        r.slice_off = (int)ts.size();
+        r.slice_off = (int)s2l.size();
         r.layer_off = (int)zm.size();
+        r.thr_off = (int)ts.size();
+        r.region_off = (int)regs.size();
         recs.push_back(r);
+        regs.insert(regs.end(), geoms[i]->regions.begin(), geoms[i]->regions.end());
         ts.insert(ts.end(), geoms[i]->t_stop.begin(), geoms[i]->t_stop.end());
         tss.insert(tss.end(), geoms[i]->t_ss.begin(), geoms[i]->t_ss.end());
         s2l.insert(s2l.end(), geoms[i]->s2l.begin(), geoms[i]->s2l.end());
@@ -334,6 +381,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
         li.insert(li.end(), geoms[i]->linfo.begin(), geoms[i]->linfo.end());
         b->max_layers = std::max(b->max_layers, r.n_layers);
     }
+    b->regions = !regs.empty();
 
     // launch shape
     int sms = 0;
@@ -357,7 +405,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     b->warp_bytes = (int)warp_smem_bytes(b->stack_cap, b->stage_cap, b->tags);
     b->smem = (size_t)b->warp_bytes * wpb;
     int occ = 0;
-    e = step_kernel_attributes(b->minb, b->block, b->smem, &occ);
+    e = step_kernel_attributes(b->minb, b->regions, b->block, b->smem, &occ);
     if (e != cudaSuccess || occ < 1) {
         supa_destroy_batch(b);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel occupancy");
@@ -383,6 +431,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     if (e == cudaSuccess) e = dalloc(&b->d_geoms, n_geoms);
     if (e == cudaSuccess) e = dalloc(&b->d_tstop, ts.size());
     if (e == cudaSuccess) e = dalloc(&b->d_tss, tss.size());
+    if (e == cudaSuccess) e = dalloc(&b->d_regions, std::max<size_t>(regs.size(), 1));
     if (e == cudaSuccess) e = dalloc(&b->d_s2l, s2l.size());
     if (e == cudaSuccess) e = dalloc(&b->d_zmid, zm.size());
     if (e == cudaSuccess) e = dalloc(&b->d_linfo, li.size());
@@ -407,6 +456,8 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     if (e == cudaSuccess) e = cudaMemcpy(b->d_geoms, recs.data(), recs.size() * sizeof(GeomDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tstop, ts.data(), ts.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tss, tss.data(), tss.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !regs.empty())
+        e = cudaMemcpy(b->d_regions, regs.data(), regs.size() * sizeof(RegionDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_s2l, s2l.data(), s2l.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_zmid, zm.data(), zm.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -448,6 +499,7 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     p.geoms = b->d_geoms;
     p.t_stop = b->d_tstop;
     p.t_ss = b->d_tss;
+    p.regions = b->d_regions;
     p.s2l = b->d_s2l;
     p.pool = b->d_pool;
     p.tag_pool = b->d_tags;
@@ -484,7 +536,7 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
         SUPA_CUDA(cudaMemsetAsync(b->d_scursor, 0, (size_t)std::max<int64_t>(n, 1) * 4, st));
         SUPA_CUDA(cudaMemsetAsync(b->d_sur_leak, 0, (size_t)std::max<int64_t>(n, 1) * 8, st));
     }
-    if (n > 0) SUPA_CUDA(launch_step(b->minb, p, b->grid, b->block, b->smem, st));
+    if (n > 0) SUPA_CUDA(launch_step(b->minb, b->regions, p, b->grid, b->block, b->smem, st));
     if (!hybrid) {
         SUPA_CUDA(launch_scan_counts(b->d_hit_count, n, b->d_offsets, b->d_scan_tmp, st));
         return SUPA_OK;

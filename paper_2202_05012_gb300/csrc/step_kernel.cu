@@ -182,8 +182,9 @@ size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags) {
 }
 
 // MINB: resident 256-thread blocks per SM the register budget is cut for
-// (3: 80 registers, 4: 64).
-template <int MINB>
+// (3: 80 registers, 4: 64).  REGIONS: some geometry of the batch has lateral
+// regions (without, the threshold tables line up with the slice tables).
+template <int MINB, bool REGIONS>
 __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -323,8 +324,23 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
                 const uint4 r = philox4x32_10(
                     make_uint4(sid, (uint32_t)cur.k, (uint32_t)cur.lin, (uint32_t)(cur.lin >> 32)), key0, key1);
                 const int so = g.slice_off + cur.k;
+                int to = REGIONS ? g.thr_off + cur.k : so;
+                float th_lo = g.theta_lo, th_span = g.theta_span, eps_frac = g.eps_frac;
+                if (REGIONS && g.n_regions > 1) {
+                    // lateral region at this slice (Sec. 4.2): r^2 against the
+                    // squared outer radii, float32
+                    const float r2 = fmaf(cur.x, cur.x, __fmul_rn(cur.y, cur.y));
+                    const RegionDev *rt = p.regions + g.region_off;
+                    int reg = 0;
+                    RegionDev rv = __ldg(rt);
+                    while (reg < g.n_regions - 1 && !(r2 < rv.x)) rv = __ldg(rt + ++reg);
+                    to += reg * g.n_slices;
+                    th_lo = rv.y;
+                    th_span = rv.z;
+                    eps_frac = rv.w;
+                }
                 const unsigned long long r0 = r.x;
-                if (r0 < __ldg(p.t_stop + so) || cur.E < g.e_min) {
+                if (r0 < __ldg(p.t_stop + to) || cur.E < g.e_min) {
                     // stop: deposit the energy at slice k
                     const int layer = __ldg(p.s2l + so);
                     if (layer < 0) {
@@ -337,11 +353,11 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
                     }
                     have = false;
                 } else {
-                    if (r0 < __ldg(p.t_ss + so)) {
+                    if (r0 < __ldg(p.t_ss + to)) {
                         // split into two daughters
-                        const float theta = fmaf(g.theta_span, u24(r.y), g.theta_lo);
+                        const float theta = fmaf(th_span, u24(r.y), th_lo);
                         // E_0 / E = (theta/2 + eps)/theta = 1/2 + eps_frac (2U - 1)
-                        const float f = fmaf(g.eps_frac, fmaf(2.0f, u24(r.z), -1.0f), 0.5f);
+                        const float f = fmaf(eps_frac, fmaf(2.0f, u24(r.z), -1.0f), 0.5f);
                         const float d1 = theta * f;                               // theta/2 + eps
                         const float d0 = g.split_literal ? d1 : theta * (1.0f - f);  // theta/2 - eps
                         float sw, cw;
@@ -458,30 +474,36 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
 }
 
 namespace {
-template <int MINB>
+template <int MINB, bool REGIONS>
 cudaError_t attrs(int block, size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(supa_step_kernel<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(supa_step_kernel<MINB, REGIONS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     // largest shared-memory carve-out, so downsampling CTAs of another batch
     // can share the SM with these blocks
-    e = cudaFuncSetAttribute(supa_step_kernel<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(supa_step_kernel<MINB, REGIONS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, supa_step_kernel<MINB>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, supa_step_kernel<MINB, REGIONS>, block, smem);
 }
 }  // namespace
 
-cudaError_t launch_step(int minb, const StepParams &p, int grid, int block, size_t smem, cudaStream_t st) {
-    if (minb >= 4)
-        supa_step_kernel<4><<<grid, block, smem, st>>>(p);
+cudaError_t launch_step(int minb, bool regions, const StepParams &p, int grid, int block, size_t smem,
+                        cudaStream_t st) {
+    if (minb >= 4 && regions)
+        supa_step_kernel<4, true><<<grid, block, smem, st>>>(p);
+    else if (minb >= 4)
+        supa_step_kernel<4, false><<<grid, block, smem, st>>>(p);
+    else if (regions)
+        supa_step_kernel<3, true><<<grid, block, smem, st>>>(p);
     else
-        supa_step_kernel<3><<<grid, block, smem, st>>>(p);
+        supa_step_kernel<3, false><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t step_kernel_attributes(int minb, int block, size_t smem, int *blocks_per_sm) {
-    if (minb >= 4) return attrs<4>(block, smem, blocks_per_sm);
-    return attrs<3>(block, smem, blocks_per_sm);
+cudaError_t step_kernel_attributes(int minb, bool regions, int block, size_t smem, int *blocks_per_sm) {
+    if (minb >= 4) return regions ? attrs<4, true>(block, smem, blocks_per_sm) : attrs<4, false>(block, smem, blocks_per_sm);
+    return regions ? attrs<3, true>(block, smem, blocks_per_sm) : attrs<3, false>(block, smem, blocks_per_sm);
 }
 
 }  // namespace supa

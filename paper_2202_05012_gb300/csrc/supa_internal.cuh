@@ -29,7 +29,14 @@ struct GeomDev {
     float wx, wy;
     int roi_axis;
     float e0_max;  // largest primary energy whose lineage ids fit 64 bits
+    int thr_off;     // first entry of this geometry in the threshold tables
+    int n_regions;   // lateral regions (<= 1: none); region i thresholds at thr_off + i * n_slices
+    int region_off;  // first entry of this geometry in the region table
 };
+
+// One lateral region (Sec. 4.2): x = squared outer radius (float32, +inf for
+// the outermost), y = theta_lo, z = theta_span, w = eps_frac.
+using RegionDev = float4;
 
 // ---- hybrid path: particles below E_s handed to the surrogate network ----
 constexpr int kSurIn = 6;       // features
@@ -145,6 +152,7 @@ struct StepParams {
     const GeomDev *geoms;
     const unsigned long long *t_stop;  // [slices] stop iff r0 < t_stop
     const unsigned long long *t_ss;    // [slices] split iff t_stop <= r0 < t_ss
+    const RegionDev *regions;          // lateral regions of all geometries
     const int8_t *s2l;                 // [slices] layer or -1
     // hit pool
     float4 *pool;
@@ -193,8 +201,9 @@ size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags);
 // Kernel launchers (defined in the .cu files, called by the C ABI).
 // minb selects the register budget of the step kernel (3 or 4 resident
 // 256-thread blocks per SM: 80 or 64 registers).
-cudaError_t launch_step(int minb, const StepParams &p, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t step_kernel_attributes(int minb, int block, size_t smem, int *blocks_per_sm);
+cudaError_t launch_step(int minb, bool regions, const StepParams &p, int grid, int block, size_t smem,
+                        cudaStream_t st);
+cudaError_t step_kernel_attributes(int minb, bool regions, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_scan_counts(const uint32_t *counts, int64_t n, int64_t *offsets, unsigned long long *block_tmp,
                                cudaStream_t st);
 size_t scan_tmp_elems(int64_t n);

@@ -50,6 +50,10 @@ class supa_geometry_desc(ctypes.Structure):
         ("e_min", ctypes.c_double), ("uz_min", ctypes.c_double),
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("wx", ctypes.c_float), ("wy", ctypes.c_float),
         ("roi_mode", ctypes.c_int32),
+        ("n_regions", ctypes.c_int32), ("region_radius", ctypes.POINTER(ctypes.c_double)),
+        ("region_p_stop", ctypes.POINTER(ctypes.c_double)), ("region_p_split", ctypes.POINTER(ctypes.c_double)),
+        ("region_theta_lo", ctypes.POINTER(ctypes.c_double)), ("region_theta_hi", ctypes.POINTER(ctypes.c_double)),
+        ("region_eps_frac", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -174,8 +178,18 @@ def supa_init_geometry(geom) -> int:
         int(geom.theta_mode), float(geom.theta_lo), float(geom.theta_hi), int(geom.eps_mode), float(geom.eps_frac),
         int(geom.split_mode), float(geom.e_min), float(geom.uz_min), int(geom.nx), int(geom.ny), float(geom.wx),
         float(geom.wy), int(geom.roi_mode))
+    keep = []
+    reg = getattr(geom, "regions", None)
+    if reg is not None and reg.n > 1:
+        keep = [np.ascontiguousarray(a, dtype=np.float64) for a in
+                (reg.radius, reg.p_stop, reg.p_split, reg.theta_lo, reg.theta_hi, reg.eps_frac)]
+        d.n_regions = reg.n
+        for name, a in zip(("region_radius", "region_p_stop", "region_p_split", "region_theta_lo",
+                            "region_theta_hi", "region_eps_frac"), keep):
+            setattr(d, name, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     out = _VP()
     _check(lib().supa_init_geometry(ctypes.byref(d), ctypes.byref(out)), "supa_init_geometry")
+    del keep
     return out.value
 
 

@@ -4,6 +4,7 @@ from __future__ import annotations
 
 import numpy as np
 
+import oracle
 from paper_2202_05012_gb300 import supa as S
 
 # Tolerances (FP32 stepping against the FP64 oracle): positions within 1e-5
@@ -134,3 +135,24 @@ def compare(gpu, ora, geoms, prims, pos_rtol=RTOL):
         steps_equal=float(np.mean(gpu["steps"].astype(np.int64) == ora["steps"])),
     )
     return stats
+
+
+def oracle_multi(geoms, prims, seed, base):
+    """Oracle for a batch mixing geometries: each shower with its own geometry
+    and its global id (the random stream depends on nothing else)."""
+    parts = []
+    for i in range(len(prims)):
+        g = geoms[int(prims["geom"][i])]
+        parts.append(oracle.simulate(g, prims[i:i + 1], seed, shower_id_base=base + i))
+    Lmax = max(g.n_layers for g in geoms)
+    out = {}
+    for key in ("x", "y", "z", "E", "slice", "lineage"):
+        out[key] = np.concatenate([p[key] for p in parts])
+    out["offsets"] = np.concatenate([[0], np.cumsum([p["offsets"][-1] for p in parts])]).astype(np.int64)
+    for key in ("steps", "dead", "leak", "escape", "n_splits", "max_depth"):
+        out[key] = np.concatenate([p[key] for p in parts])
+    ls = np.zeros((len(prims), Lmax))
+    for i, p in enumerate(parts):
+        ls[i, :p["layer_sum"].shape[1]] = p["layer_sum"][0]
+    out["layer_sum"] = ls
+    return out

@@ -78,6 +78,36 @@ def test_lineage_bound_needs_energy_cut():
         S.supa_init_geometry(g)
 
 
+def _three_regions(**over):
+    g = inputs.supa_d(3)
+    kw = dict(radius=[1.0, 2.0], p_stop=[0.02, 0.1, 0.3], p_split=[0.5, 0.4, 0.2], theta_lo=[0.1, 0.2, 0.3],
+              theta_hi=[0.3, 0.4, 0.5], eps_frac=[0.25, 0.1, 0.0])
+    kw.update(over)
+    return inputs.with_regions(g, **kw)
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(radius=[2.0, 1.0]), "radii"),
+    (dict(radius=[0.0, 1.0]), "radii"),
+    (dict(radius=[1.0, math.inf]), "radii"),
+    (dict(eps_frac=[0.25, 0.5, 0.0]), "region 1: eps_frac"),
+    (dict(theta_lo=[0.1, 0.2, 1.6], theta_hi=[0.3, 0.4, 1.7]), "region 2: need 0 < theta_lo"),
+    (dict(p_stop=[0.02, 0.7, 0.3]), "region 1, slice 0"),
+])
+def test_region_validation_rejects(over, needle):
+    with pytest.raises(S.SupaError, match=needle) as ei:
+        S.supa_init_geometry(_three_regions(**over))
+    assert ei.value.code == S.SUPA_ERR_INVALID_ARG
+
+
+def test_too_many_regions_rejected():
+    R = 9
+    g = inputs.with_regions(inputs.supa_d(3), list(np.arange(1.0, R)), [0.02] * R, [0.5] * R, [0.1] * R,
+                            [0.3] * R, [0.25] * R)
+    with pytest.raises(S.SupaError, match="n_regions"):
+        S.supa_init_geometry(g)
+
+
 def test_null_arguments_rejected_without_gpu():
     L = S.lib()
     out = ctypes.c_void_p()

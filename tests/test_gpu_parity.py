@@ -9,7 +9,7 @@ import oracle
 from paper_2202_05012_gb300 import inputs
 from paper_2202_05012_gb300 import supa as S
 
-from gpu_helpers import compare, run_gpu
+from gpu_helpers import compare, oracle_multi, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -19,29 +19,8 @@ def _check(geoms, prims, seed, cfg=None, base=0, pos_rtol=1e-5):
     if len(geoms) == 1:
         ora = oracle.simulate(geoms[0], prims, seed, shower_id_base=base, n_threads=8)
     else:
-        ora = _oracle_multi(geoms, prims, seed, base)
+        ora = oracle_multi(geoms, prims, seed, base)
     return compare(gpu, ora, geoms, prims, pos_rtol=pos_rtol), gpu, ora
-
-
-def _oracle_multi(geoms, prims, seed, base):
-    """Oracle for a batch mixing geometries: each shower with its own geometry
-    and its global id (the random stream depends on nothing else)."""
-    parts = []
-    for i in range(len(prims)):
-        g = geoms[int(prims["geom"][i])]
-        parts.append(oracle.simulate(g, prims[i:i + 1], seed, shower_id_base=base + i))
-    Lmax = max(g.n_layers for g in geoms)
-    out = {}
-    for key in ("x", "y", "z", "E", "slice", "lineage"):
-        out[key] = np.concatenate([p[key] for p in parts])
-    out["offsets"] = np.concatenate([[0], np.cumsum([p["offsets"][-1] for p in parts])]).astype(np.int64)
-    for key in ("steps", "dead", "leak", "escape", "n_splits", "max_depth"):
-        out[key] = np.concatenate([p[key] for p in parts])
-    ls = np.zeros((len(prims), Lmax))
-    for i, p in enumerate(parts):
-        ls[i, :p["layer_sum"].shape[1]] = p["layer_sum"][0]
-    out["layer_sum"] = ls
-    return out
 
 
 def test_supav1_exact_on_gpu():
