@@ -817,46 +817,61 @@ def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
     """Same metric through the public API with host buffers: primaries copied
     from pinned host memory each step, the point cloud (all hits, fetched in
     64M-hit chunks) and the per-shower FP64 layer sums read back to pinned
-    host memory.  The point cloud travels to the host on a second stream
-    (copy engines) while the images are made; images stay on the device,
-    consumed chunk by chunk."""
+    host memory.  Each chunk travels to the host on a second stream (copy
+    engines) as soon as it is fetched, while the images are made and while
+    the next step simulates; two host buffers alternate, so a step's results
+    stay intact while the step after it runs.  Images stay on the device,
+    consumed chunk by chunk.  Every copy of the timed steps has finished when
+    the clock stops."""
     import torch
     import torch.distributed as dist
     h_prim = torch.from_numpy(np.ascontiguousarray(prims).view(np.uint8)).pin_memory()
     d_prim = torch.empty_like(h_prim, device="cuda")
     info = S.supa_batch_get_info(b)
     cap = int(info.n_hits * 1.05) + 1024
-    h_hits = torch.empty((cap, 4), dtype=torch.float32, pin_memory=True)
+    h_hits = [torch.empty((cap, 4), dtype=torch.float32, pin_memory=True) for _ in range(2)]
     d_hits = torch.empty((cap, 4), dtype=torch.float32, device="cuda")
-    h_ls = torch.empty((n, geom.n_layers), dtype=torch.float64, pin_memory=True)
+    h_ls = [torch.empty((n, geom.n_layers), dtype=torch.float64, pin_memory=True) for _ in range(2)]
     cur = torch.cuda.current_stream()
     side = torch.cuda.Stream()
+    ls_read = torch.cuda.Event()    # the batch's layer sums are on the host
+    hits_read = torch.cuda.Event()  # the device hit buffer is on the host
+    ls_read.record(side)
+    hits_read.record(side)
     h2d = d2h = 0
+    it = 0
 
     def step():
-        nonlocal h2d, d2h
+        nonlocal h2d, d2h, it
+        hh, hl = h_hits[it % 2], h_ls[it % 2]
+        it += 1
         d_prim.copy_(h_prim, non_blocking=True)
+        cur.wait_event(ls_read)  # the simulation rewrites the layer sums
         S.supa_simulate(b, d_prim, n, seed, base)
         inf = S.supa_batch_get_info(b)
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            hl.copy_(S.info_arrays(inf)["layer_sum"], non_blocking=True)
+            ls_read.record(side)
+        cur.wait_event(hits_read)  # the fetch rewrites the device hit buffer
         got = 0
         while got < inf.n_hits:
             m = S.supa_fetch_hits(b, got, min(FETCH_CHUNK, cap - got), d_hits[got:])
-            got += m
             if m == 0:
                 break
-        side.wait_stream(cur)
-        with torch.cuda.stream(side):
-            h_hits[:got].copy_(d_hits[:got], non_blocking=True)
-            h_ls.copy_(S.info_arrays(inf)["layer_sum"], non_blocking=True)
+            side.wait_stream(cur)
+            with torch.cuda.stream(side):
+                hh[got:got + m].copy_(d_hits[got:got + m], non_blocking=True)
+            got += m
+        hits_read.record(side)
         for c0 in range(0, n, V):
             S.supa_voxelize(b, c0, min(n, c0 + V), grid, oor)
-        cur.wait_stream(side)
-        torch.cuda.synchronize()
         h2d = h_prim.numel()
-        d2h = inf.n_hits * 16 + h_ls.numel() * 8
+        d2h = inf.n_hits * 16 + hl.numel() * 8
 
     for _ in range(max(1, args.warmup)):
         step()
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
