@@ -12,11 +12,11 @@
 //  * Stops are staged as float4 hits in shared memory and flushed with
 //    coalesced 16-byte stores to the warp's current page of the hit pool
 //    once flush_thr hits are staged.
-//  * Deposits are summed exactly in 64-bit fixed point (units of 2^-32) --
-//    per layer in shared memory, dead / leaked / escaped energy in lane
-//    registers -- on the integer pipe (GB300's FP64 rate is a small fraction
-//    of its FP32 rate), and delivered per shower as FP64.  Integer sums are
-//    exact and do not depend on the order of the additions.
+//  * Deposits are summed exactly in 64-bit fixed point (units of 2^-32) in
+//    shared memory -- per layer, and dead / leaked / escaped energy -- with
+//    32-bit shared-memory atomics on the integer pipe (GB300's FP64 rate is a
+//    small fraction of its FP32 rate), and delivered per shower as FP64.
+//    Integer sums are exact and do not depend on the order of the additions.
 // Every random draw is keyed by (seed; shower id, slice, lineage id), so the
 // result does not depend on which warp runs a shower or in which order.
 #include "philox.cuh"
@@ -32,7 +32,8 @@ struct WarpSmem {
     float4 *stage;
     unsigned long long *stage_tag;
     unsigned long long *slin;
-    unsigned long long *lsum;  // fixed point, units of 2^-32
+    unsigned long long *lsum;  // [SUPA_MAX_LAYERS] fixed point, units of 2^-32
+    unsigned long long *acc;   // [kAccDead, kAccLeak, kAccEscape], fixed point
     float *sx, *sy, *sux, *suy, *suz, *sE;
     uint8_t *sk;
 };
@@ -49,7 +50,8 @@ __device__ inline WarpSmem carve(unsigned char *base, int C, int H, bool tags) {
     w.slin = reinterpret_cast<unsigned long long *>(base + o);
     o += size_t(8) * C;
     w.lsum = reinterpret_cast<unsigned long long *>(base + o);
-    o += size_t(8) * SUPA_MAX_LAYERS;
+    w.acc = w.lsum + SUPA_MAX_LAYERS;
+    o += size_t(8) * (SUPA_MAX_LAYERS + 4);
     float *f = reinterpret_cast<float *>(base + o);
     w.sx = f;
     w.sy = f + C;
@@ -60,6 +62,19 @@ __device__ inline WarpSmem carve(unsigned char *base, int C, int H, bool tags) {
     o += size_t(24) * C;
     w.sk = base + o;
     return w;
+}
+
+constexpr int kAccDead = 0, kAccLeak = 1, kAccEscape = 2;
+
+// acc += v exactly, on a 64-bit fixed-point sum in shared memory, with 32-bit
+// shared-memory atomics: the low word's atomic returns the old value, so the
+// carry out of it is known and goes to the high word with v's high part.
+__device__ __forceinline__ void add_fixed(unsigned long long *acc, unsigned long long v) {
+    uint32_t *w = reinterpret_cast<uint32_t *>(acc);
+    const uint32_t lo = (uint32_t)v;
+    const uint32_t old = atomicAdd(w, lo);
+    const uint32_t hi = (uint32_t)(v >> 32) + (uint32_t)(old + lo < old);
+    if (hi) atomicAdd(w + 1, hi);
 }
 
 struct Particle {
@@ -109,10 +124,9 @@ __device__ __forceinline__ void deflect(float ux, float uy, float uz, float wx, 
 
 // A survivor of slice k either leaks (last slice), escapes (u_z too small)
 // or moves in a straight line to slice k+1.  Returns true if still alive.
-__device__ __forceinline__ bool advance(Particle &q, const GeomDev &g, unsigned long long &leak,
-                                        unsigned long long &esc) {
-    if (q.k == g.n_slices - 1) { leak += fixed32(q.E); return false; }
-    if (q.uz <= g.uz_min) { esc += fixed32(q.E); return false; }
+__device__ __forceinline__ bool advance(Particle &q, const GeomDev &g, unsigned long long *acc) {
+    if (q.k == g.n_slices - 1) { add_fixed(acc + kAccLeak, fixed32(q.E)); return false; }
+    if (q.uz <= g.uz_min) { add_fixed(acc + kAccEscape, fixed32(q.E)); return false; }
     const float r = __frcp_rn(q.uz);
     q.x = fmaf(g.dz, q.ux * r, q.x);
     q.y = fmaf(g.dz, q.uy * r, q.y);
@@ -177,7 +191,7 @@ __device__ __forceinline__ bool flush(const StepParams &p, const WarpSmem &w, in
 
 size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags) {
     size_t o = size_t(16) * stage_cap + (tags ? size_t(8) * stage_cap : 0) + size_t(8) * stack_cap +
-               size_t(8) * SUPA_MAX_LAYERS + size_t(24) * stack_cap + size_t(stack_cap);
+               size_t(8) * (SUPA_MAX_LAYERS + 4) + size_t(24) * stack_cap + size_t(stack_cap);
     return align16(o);
 }
 
@@ -227,6 +241,7 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
         const uint32_t sid = (uint32_t)(p.shower_id_base + (uint64_t)s);
 
         for (int l = lane; l < g.n_layers; l += 32) w.lsum[l] = 0ull;
+        if (lane < 3) w.acc[lane] = 0ull;
         if (pc.off == kPageHits && !next_page(p, pc, lane)) {
             if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
             break;
@@ -247,7 +262,6 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
         }
         int stack_n = 0, spill_n = 0, staged = 0;
         uint32_t n_hits = 0, n_steps = 0;
-        unsigned long long dead = 0, leak = 0, esc = 0;  // fixed point
         bool failed = false;
         __syncwarp();
 
@@ -344,12 +358,12 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
                     // stop: deposit the energy at slice k
                     const int layer = __ldg(p.s2l + so);
                     if (layer < 0) {
-                        dead += fixed32(cur.E);
+                        add_fixed(w.acc + kAccDead, fixed32(cur.E));
                     } else {
                         hit = true;
                         h = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
                         hit_lin = cur.lin;
-                        atomicAdd(&w.lsum[layer], fixed32(cur.E));
+                        add_fixed(&w.lsum[layer], fixed32(cur.E));
                     }
                     have = false;
                 } else {
@@ -381,9 +395,9 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
                         cur.E = E0;
                         dau.lin = 2ull * cur.lin + 1ull;
                         cur.lin = 2ull * cur.lin;
-                        push = advance(dau, g, leak, esc);
+                        push = advance(dau, g, w.acc);
                     }
-                    have = advance(cur, g, leak, esc);
+                    have = advance(cur, g, w.acc);
                 }
             }
 
@@ -448,9 +462,6 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
         // ---- per-shower records ----
         for (int o = 16; o > 0; o >>= 1) {
             n_steps += __shfl_xor_sync(kFull, n_steps, o);
-            dead += __shfl_xor_sync(kFull, dead, o);
-            leak += __shfl_xor_sync(kFull, leak, o);
-            esc += __shfl_xor_sync(kFull, esc, o);
         }
         __syncwarp();
         for (int l = lane; l < g.n_layers; l += 32) p.lsum[(size_t)s * p.lsum_stride + l] = from_fixed32(w.lsum[l]);
@@ -459,9 +470,9 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
             p.hit_start[s] = start;
             p.hit_count[s] = n_hits;
             p.steps[s] = n_steps;
-            p.dead[s] = from_fixed32(dead);
-            p.leak[s] = from_fixed32(leak);
-            p.escape[s] = from_fixed32(esc);
+            p.dead[s] = from_fixed32(w.acc[kAccDead]);
+            p.leak[s] = from_fixed32(w.acc[kAccLeak]);
+            p.escape[s] = from_fixed32(w.acc[kAccEscape]);
         }
         warp_steps += n_steps;
         warp_hits += n_hits;
