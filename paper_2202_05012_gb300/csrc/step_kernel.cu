@@ -127,7 +127,10 @@ __device__ __forceinline__ void deflect(float ux, float uy, float uz, float wx, 
 __device__ __forceinline__ bool advance(Particle &q, const GeomDev &g, unsigned long long *acc) {
     if (q.k == g.n_slices - 1) { add_fixed(acc + kAccLeak, fixed32(q.E)); return false; }
     if (q.uz <= g.uz_min) { add_fixed(acc + kAccEscape, fixed32(q.E)); return false; }
-    const float r = __frcp_rn(q.uz);
+    // 1/u_z from the SFU (one rounding of about an ulp; u_z > uz_min is a
+    // normal number)
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q.uz));
     q.x = fmaf(g.dz, q.ux * r, q.x);
     q.y = fmaf(g.dz, q.uy * r, q.y);
     q.k += 1;
@@ -331,8 +334,6 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
             // ---- one step of Algorithm 1 for every active lane ----
             bool push = false, hit = false;
             Particle dau;
-            float4 h;
-            unsigned long long hit_lin = 0;
             if (have) {
                 n_steps += 1;
                 const uint4 r = philox4x32_10(
@@ -360,9 +361,7 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
                     if (layer < 0) {
                         add_fixed(w.acc + kAccDead, fixed32(cur.E));
                     } else {
-                        hit = true;
-                        h = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
-                        hit_lin = cur.lin;
+                        hit = true;  // staged from cur below (a stopped lane keeps it)
                         add_fixed(&w.lsum[layer], fixed32(cur.E));
                     }
                     have = false;
@@ -375,7 +374,11 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
                         const float d1 = theta * f;                               // theta/2 + eps
                         const float d0 = g.split_literal ? d1 : theta * (1.0f - f);  // theta/2 - eps
                         float sw, cw;
-                        sincospif(2.0f * u24(r.w), &sw, &cw);  // omega = 2 pi U
+                        // omega = 2 pi U: sin and cos from the SFU over [-pi, pi)
+                        // (absolute error ~5e-7), sin(2 pi U) = -sin(2 pi (U - 1/2))
+                        __sincosf(6.28318531f * (u24(r.w) - 0.5f), &sw, &cw);
+                        sw = -sw;
+                        cw = -cw;
                         // orthonormal frame (e1, e2) perpendicular to u (Duff et al. 2017)
                         const float a = -1.0f / (1.0f + cur.uz);
                         const float b = cur.ux * cur.uy * a;
@@ -437,8 +440,8 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
             if (nh) {
                 if (hit) {
                     const int idx = staged + __popc(hm & lt_mask);
-                    w.stage[idx] = h;
-                    if (tags) w.stage_tag[idx] = hit_lin;
+                    w.stage[idx] = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
+                    if (tags) w.stage_tag[idx] = cur.lin;
                 }
                 staged += nh;
                 n_hits += nh;
