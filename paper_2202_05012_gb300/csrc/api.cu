@@ -123,7 +123,7 @@ struct supa_batch {
     SpillRec *d_spill = nullptr;
     int spill_cap = 0;
     // launch shape
-    int grid = 0, block = 0, stack_cap = 0, stage_cap = 0, flush_thr = 0, minb = 3, voxel_ctas = 0;
+    int grid = 0, block = 0, stack_cap = 0, minb = 3, voxel_ctas = 0;
     size_t smem = 0;
     int warp_bytes = 0;
     // state
@@ -400,9 +400,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
         supa_destroy_batch(b);
         return fail(SUPA_ERR_INVALID_ARG, "stack_depth must be an even number >= 64");
     }
-    b->flush_thr = cfg.flush_threshold > 0 ? cfg.flush_threshold : 128;
-    b->stage_cap = b->flush_thr + 32;
-    b->warp_bytes = (int)warp_smem_bytes(b->stack_cap, b->stage_cap, b->tags);
+    b->warp_bytes = (int)warp_smem_bytes(b->stack_cap);
     b->smem = (size_t)b->warp_bytes * wpb;
     int occ = 0;
     e = step_kernel_attributes(b->minb, b->regions, b->block, b->smem, &occ);
@@ -520,8 +518,6 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     p.spill = b->d_spill;
     p.spill_cap = b->spill_cap;
     p.stack_cap = b->stack_cap;
-    p.stage_cap = b->stage_cap;
-    p.flush_thr = b->flush_thr;
     p.warp_smem_bytes = b->warp_bytes;
     const bool hybrid = b->sur != nullptr;
     if (hybrid) {
@@ -683,7 +679,6 @@ int supa_autotune(const supa_geometry *const *geoms, int32_t n_geoms, const supa
     if (best.blocks_per_sm <= 0) best.blocks_per_sm = 3;
     if (best.warps_per_block <= 0) best.warps_per_block = 8;
     if (best.stack_depth <= 0) best.stack_depth = 128;
-    if (best.flush_threshold <= 0) best.flush_threshold = 128;
     cudaEvent_t e0, e1;
     SUPA_CUDA(cudaEventCreate(&e0));
     SUPA_CUDA(cudaEventCreate(&e1));
@@ -727,18 +722,12 @@ int supa_autotune(const supa_geometry *const *geoms, int32_t n_geoms, const supa
         c.stack_depth = depth;
         if (depth != best.stack_depth) consider(c);
     }
-    for (int ft : {32, 64, 128, 256}) {
-        supa_launch_config c = best;
-        c.flush_threshold = ft;
-        if (ft != best.flush_threshold) consider(c);
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!std::isfinite(best_t)) return fail(SUPA_ERR_CUDA, "supa_autotune: no candidate launch shape ran");
     cfg->blocks_per_sm = best.blocks_per_sm;
     cfg->warps_per_block = best.warps_per_block;
     cfg->stack_depth = best.stack_depth;
-    cfg->flush_threshold = best.flush_threshold;
     if (best_ms) *best_ms = best_t;
     g_last_error.clear();
     return SUPA_OK;

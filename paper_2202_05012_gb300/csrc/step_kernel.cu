@@ -9,9 +9,10 @@
 //    shared memory (ballot + popc compaction, no atomics); empty lanes refill
 //    from the stack.  A stack that outgrows shared memory spills its oldest
 //    half to a per-warp region of global scratch.
-//  * Stops are staged as float4 hits in shared memory and flushed with
-//    coalesced 16-byte stores to the warp's current page of the hit pool
-//    once flush_thr hits are staged.
+//  * Stops are written as float4 hits straight from the lanes to the warp's
+//    current page of the hit pool: the stopping lanes of one iteration
+//    write consecutive 16-byte slots (ballot + popc), so a warp's stores of
+//    one iteration are contiguous, and L2 merges them into full sectors.
 //  * Deposits are summed exactly in 64-bit fixed point (units of 2^-32) in
 //    shared memory -- per layer, and dead / leaked / escaped energy -- with
 //    32-bit shared-memory atomics on the integer pipe (GB300's FP64 rate is a
@@ -29,8 +30,6 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct WarpSmem {
-    float4 *stage;
-    unsigned long long *stage_tag;
     unsigned long long *slin;
     unsigned long long *lsum;  // [SUPA_MAX_LAYERS] fixed point, units of 2^-32
     unsigned long long *acc;   // [kAccDead, kAccLeak, kAccEscape], fixed point
@@ -40,13 +39,9 @@ struct WarpSmem {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-__device__ inline WarpSmem carve(unsigned char *base, int C, int H, bool tags) {
+__device__ inline WarpSmem carve(unsigned char *base, int C) {
     WarpSmem w;
     size_t o = 0;
-    w.stage = reinterpret_cast<float4 *>(base + o);
-    o += size_t(16) * H;
-    w.stage_tag = reinterpret_cast<unsigned long long *>(base + o);
-    if (tags) o += size_t(8) * H;
     w.slin = reinterpret_cast<unsigned long long *>(base + o);
     o += size_t(8) * C;
     w.lsum = reinterpret_cast<unsigned long long *>(base + o);
@@ -173,28 +168,11 @@ __device__ __forceinline__ bool next_page(const StepParams &p, PageCursor &pc, i
     return true;
 }
 
-// Write `count` staged hits to the page chain.  Lane-uniform.
-__device__ __forceinline__ bool flush(const StepParams &p, const WarpSmem &w, int count, PageCursor &pc, int lane) {
-    int done = 0;
-    while (done < count) {
-        if (pc.off == kPageHits && !next_page(p, pc, lane)) return false;
-        const int m = min(count - done, kPageHits - pc.off);
-        const size_t base = (size_t)pc.page * kPageHits + pc.off;
-        for (int j = lane; j < m; j += 32) p.pool[base + j] = w.stage[done + j];
-        if (p.tag_pool)
-            for (int j = lane; j < m; j += 32) p.tag_pool[base + j] = w.stage_tag[done + j];
-        pc.off += m;
-        done += m;
-    }
-    __syncwarp();
-    return true;
-}
-
 }  // namespace
 
-size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags) {
-    size_t o = size_t(16) * stage_cap + (tags ? size_t(8) * stage_cap : 0) + size_t(8) * stack_cap +
-               size_t(8) * (SUPA_MAX_LAYERS + 4) + size_t(24) * stack_cap + size_t(stack_cap);
+size_t warp_smem_bytes(int stack_cap) {
+    const size_t o = size_t(8) * stack_cap + size_t(8) * (SUPA_MAX_LAYERS + 4) + size_t(24) * stack_cap +
+                     size_t(stack_cap);
     return align16(o);
 }
 
@@ -210,7 +188,7 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
     const unsigned lt_mask = (1u << lane) - 1u;
     const int C = p.stack_cap;
     const bool tags = p.tag_pool != nullptr;
-    const WarpSmem w = carve(smem_raw + (size_t)wib * p.warp_smem_bytes, C, p.stage_cap, tags);
+    const WarpSmem w = carve(smem_raw + (size_t)wib * p.warp_smem_bytes, C);
     SpillRec *spill = p.spill + (size_t)warp_global * p.spill_cap;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
 
@@ -263,7 +241,7 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
             cur.ux = st * cp; cur.uy = st * sp; cur.uz = ct;
             cur.E = pr.E; cur.lin = 1ull; cur.k = k0;
         }
-        int stack_n = 0, spill_n = 0, staged = 0;
+        int stack_n = 0, spill_n = 0;
         uint32_t n_hits = 0, n_steps = 0;
         bool failed = false;
         __syncwarp();
@@ -361,7 +339,7 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
                     if (layer < 0) {
                         add_fixed(w.acc + kAccDead, fixed32(cur.E));
                     } else {
-                        hit = true;  // staged from cur below (a stopped lane keeps it)
+                        hit = true;  // written from cur below (a stopped lane keeps it)
                         add_fixed(&w.lsum[layer], fixed32(cur.E));
                     }
                     have = false;
@@ -434,33 +412,37 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
                 __syncwarp();
             }
 
-            // ---- stage hits, flush to the page chain past the threshold ----
+            // ---- write hits straight to the page chain ----
             const unsigned hm = __ballot_sync(kFull, hit);
             const int nh = __popc(hm);
             if (nh) {
-                if (hit) {
-                    const int idx = staged + __popc(hm & lt_mask);
-                    w.stage[idx] = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
-                    if (tags) w.stage_tag[idx] = cur.lin;
+                const int idx = __popc(hm & lt_mask);
+                const int room = kPageHits - pc.off;  // >= 1
+                if (hit && idx < room) {
+                    const size_t a = (size_t)pc.page * kPageHits + pc.off + idx;
+                    p.pool[a] = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
+                    if (tags) p.tag_pool[a] = cur.lin;
                 }
-                staged += nh;
-                n_hits += nh;
-                __syncwarp();
-                if (staged >= p.flush_thr) {
-                    if (!flush(p, w, staged, pc, lane)) {
+                if (nh >= room) {
+                    // the page is full: the rest go to a fresh page linked after it
+                    if (!next_page(p, pc, lane)) {
                         if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
                         failed = true;
                         break;
                     }
-                    staged = 0;
+                    if (hit && idx >= room) {
+                        const size_t a = (size_t)pc.page * kPageHits + (idx - room);
+                        p.pool[a] = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
+                        if (tags) p.tag_pool[a] = cur.lin;
+                    }
+                    pc.off = nh - room;
+                } else {
+                    pc.off += nh;
                 }
+                n_hits += nh;
             }
         }
         if (failed) break;
-        if (staged && !flush(p, w, staged, pc, lane)) {
-            if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
-            break;
-        }
 
         // ---- per-shower records ----
         for (int o = 16; o > 0; o >>= 1) {

@@ -175,8 +175,6 @@ struct StepParams {
     SpillRec *spill;
     int spill_cap;        // records per warp
     int stack_cap;        // particles per warp in shared memory
-    int stage_cap;        // staged hits per warp (>= flush_thr + 32)
-    int flush_thr;
     int warp_smem_bytes;  // shared memory per warp
     // hybrid path (e_s = 0: off)
     float e_s;
@@ -196,7 +194,7 @@ constexpr int kErrSpillOverflow = 2;
 constexpr int kErrBadPrimary = 4;
 constexpr int kErrQueueOverflow = 16;
 
-size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags);
+size_t warp_smem_bytes(int stack_cap);
 
 // Kernel launchers (defined in the .cu files, called by the C ABI).
 // minb selects the register budget of the step kernel (3 or 4 resident
