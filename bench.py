@@ -132,9 +132,11 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def stored_traffic(kernel: str, workload_key: str):
+def stored_traffic(kernel: str, workload_key: str, showers_per_launch: int):
     """DRAM bytes per launch from a committed ncu capture, valid only while the
-    kernel source is unchanged (sha256 of its translation unit)."""
+    kernel source is unchanged (sha256 of its translation unit), scaled from
+    the captured launch to one of `showers_per_launch` showers (the traffic
+    grows in proportion to the showers processed)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[kernel][workload_key]
@@ -142,7 +144,9 @@ def stored_traffic(kernel: str, workload_key: str):
         return None
     src = os.path.join(ROOT, "paper_2202_05012_gb300", "csrc", rec["source"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+    if sha != rec["sha256"]:
+        return None
+    return rec["bytes_per_launch"] * showers_per_launch / rec["showers_per_launch"]
 
 
 # ------------------------------------------------------------------ oracle ---
@@ -364,7 +368,7 @@ def run_supa(args):
     pk, pk_kind = peaks()
     bytes_per_shower = L * ny * nx * 4 + 16 * (info.n_hits / m) + 8
     achieved = V * bytes_per_shower / (avg_vox / 1000.0) / 1e9
-    traffic = stored_traffic("supa_voxel_kernel", args.workload)
+    traffic = stored_traffic("supa_voxel_kernel", args.workload, V)
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": "supa_voxel_kernel",
             "peak_source": pk_kind, "bytes_per_shower": bytes_per_shower, "showers_per_launch": V,
@@ -521,7 +525,7 @@ def run_supa_serial(args):
     avg_ms = sum(x for x, _ in full) / len(full)
     bytes_per_shower = L * ny * nx * 4 + 16 * hits_per_shower + 8
     achieved = full[0][1] * bytes_per_shower / (avg_ms / 1000.0) / 1e9
-    traffic = stored_traffic("supa_voxel_kernel", args.workload)
+    traffic = stored_traffic("supa_voxel_kernel", args.workload, full[0][1])
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": "supa_voxel_kernel",
             "peak_source": pk_kind, "bytes_per_shower": bytes_per_shower, "showers_per_launch": full[0][1]}
