@@ -6,8 +6,8 @@
 //    work queue (one atomicAdd per shower) and develops it completely.
 //  * Each lane holds one live particle in registers.  At a split the lane
 //    keeps daughter 0 and pushes daughter 1 onto the warp's particle stack in
-//    shared memory (ballot + popc compaction, no atomics); empty lanes refill
-//    from the stack.  A stack that outgrows shared memory spills its oldest
+//    shared memory (ballot + popc compaction, no atomics; two 16-byte words
+//    per particle); empty lanes refill from the stack.  A stack that outgrows shared memory spills its oldest
 //    half to a per-warp region of global scratch.
 //  * Stops are written as float4 hits straight from the lanes to the warp's
 //    current page of the hit pool: the stopping lanes of one iteration
@@ -30,10 +30,9 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct WarpSmem {
-    unsigned long long *slin;
+    float4 *sa, *sb;   // particle stack: (x, y, ux, uy), (uz, E, lin lo, lin hi)
     unsigned long long *lsum;  // [SUPA_MAX_LAYERS] fixed point, units of 2^-32
     unsigned long long *acc;   // [kAccDead, kAccLeak, kAccEscape], fixed point
-    float *sx, *sy, *sux, *suy, *suz, *sE;
     uint8_t *sk;
 };
 
@@ -42,19 +41,13 @@ __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(
 __device__ inline WarpSmem carve(unsigned char *base, int C) {
     WarpSmem w;
     size_t o = 0;
-    w.slin = reinterpret_cast<unsigned long long *>(base + o);
-    o += size_t(8) * C;
+    w.sa = reinterpret_cast<float4 *>(base + o);
+    o += size_t(16) * C;
+    w.sb = reinterpret_cast<float4 *>(base + o);
+    o += size_t(16) * C;
     w.lsum = reinterpret_cast<unsigned long long *>(base + o);
     w.acc = w.lsum + SUPA_MAX_LAYERS;
     o += size_t(8) * (SUPA_MAX_LAYERS + 4);
-    float *f = reinterpret_cast<float *>(base + o);
-    w.sx = f;
-    w.sy = f + C;
-    w.sux = f + 2 * C;
-    w.suy = f + 3 * C;
-    w.suz = f + 4 * C;
-    w.sE = f + 5 * C;
-    o += size_t(24) * C;
     w.sk = base + o;
     return w;
 }
@@ -79,15 +72,16 @@ struct Particle {
 };
 
 __device__ __forceinline__ void smem_store(const WarpSmem &w, int i, const Particle &q) {
-    w.sx[i] = q.x; w.sy[i] = q.y; w.sux[i] = q.ux; w.suy[i] = q.uy; w.suz[i] = q.uz; w.sE[i] = q.E;
-    w.slin[i] = q.lin;
+    w.sa[i] = make_float4(q.x, q.y, q.ux, q.uy);
+    w.sb[i] = make_float4(q.uz, q.E, __uint_as_float((uint32_t)q.lin), __uint_as_float((uint32_t)(q.lin >> 32)));
     w.sk[i] = (uint8_t)q.k;
 }
 
 __device__ __forceinline__ Particle smem_load(const WarpSmem &w, int i) {
     Particle q;
-    q.x = w.sx[i]; q.y = w.sy[i]; q.ux = w.sux[i]; q.uy = w.suy[i]; q.uz = w.suz[i]; q.E = w.sE[i];
-    q.lin = w.slin[i];
+    const float4 a = w.sa[i], b = w.sb[i];
+    q.x = a.x; q.y = a.y; q.ux = a.z; q.uy = a.w; q.uz = b.x; q.E = b.y;
+    q.lin = ((unsigned long long)__float_as_uint(b.w) << 32) | __float_as_uint(b.z);
     q.k = w.sk[i];
     return q;
 }
@@ -171,8 +165,8 @@ __device__ __forceinline__ bool next_page(const StepParams &p, PageCursor &pc, i
 }  // namespace
 
 size_t warp_smem_bytes(int stack_cap) {
-    const size_t o = size_t(8) * stack_cap + size_t(8) * (SUPA_MAX_LAYERS + 4) + size_t(24) * stack_cap +
-                     size_t(stack_cap);
+    // particle stack: 2 x 16 B + the slice byte per particle; fixed-point sums
+    const size_t o = size_t(32) * stack_cap + size_t(8) * (SUPA_MAX_LAYERS + 4) + size_t(stack_cap);
     return align16(o);
 }
 
