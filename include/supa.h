@@ -123,6 +123,10 @@ typedef struct {
     int32_t blocks_per_sm;   /* step-kernel blocks per SM (1..4; 4 selects a  */
                              /* 64-register build, fewer an 80-register one) */
     int32_t stack_depth;     /* particles held per warp in shared memory     */
+    int32_t flush_threshold; /* hits staged per warp in shared memory before */
+                             /* a coalesced flush to HBM (<= 1024; 0: 128);   */
+                             /* -1: each step's hits written straight from   */
+                             /* the lanes (no staging)                       */
     int32_t record_tags;     /* 1: also keep each hit's lineage id           */
     int32_t lpt_order;       /* 1: hand out showers by decreasing energy     */
     int32_t voxel_ctas_per_sm; /* downsampling CTAs per SM (0: as many as fit);

@@ -123,7 +123,7 @@ struct supa_batch {
     SpillRec *d_spill = nullptr;
     int spill_cap = 0;
     // launch shape
-    int grid = 0, block = 0, stack_cap = 0, minb = 3, voxel_ctas = 0;
+    int grid = 0, block = 0, stack_cap = 0, stage_cap = 0, flush_thr = 0, minb = 3, voxel_ctas = 0;
     size_t smem = 0;
     int warp_bytes = 0;
     // state
@@ -400,10 +400,16 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
         supa_destroy_batch(b);
         return fail(SUPA_ERR_INVALID_ARG, "stack_depth must be an even number >= 64");
     }
-    b->warp_bytes = (int)warp_smem_bytes(b->stack_cap);
+    if (cfg.flush_threshold < -1 || cfg.flush_threshold > 1024) {
+        supa_destroy_batch(b);
+        return fail(SUPA_ERR_INVALID_ARG, "flush_threshold must be -1 (direct hit writes) or in [0, 1024]");
+    }
+    b->flush_thr = cfg.flush_threshold == 0 ? 128 : std::max(0, cfg.flush_threshold);
+    b->stage_cap = b->flush_thr > 0 ? b->flush_thr + 32 : 0;
+    b->warp_bytes = (int)warp_smem_bytes(b->stack_cap, b->stage_cap, b->tags);
     b->smem = (size_t)b->warp_bytes * wpb;
     int occ = 0;
-    e = step_kernel_attributes(b->minb, b->regions, b->block, b->smem, &occ);
+    e = step_kernel_attributes(b->minb, b->regions, b->flush_thr > 0, b->block, b->smem, &occ);
     if (e != cudaSuccess || occ < 1) {
         supa_destroy_batch(b);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel occupancy");
@@ -498,6 +504,8 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     p.t_stop = b->d_tstop;
     p.t_ss = b->d_tss;
     p.regions = b->d_regions;
+    p.stage_cap = b->stage_cap;
+    p.flush_thr = b->flush_thr;
     p.s2l = b->d_s2l;
     p.pool = b->d_pool;
     p.tag_pool = b->d_tags;
@@ -532,7 +540,7 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
         SUPA_CUDA(cudaMemsetAsync(b->d_scursor, 0, (size_t)std::max<int64_t>(n, 1) * 4, st));
         SUPA_CUDA(cudaMemsetAsync(b->d_sur_leak, 0, (size_t)std::max<int64_t>(n, 1) * 8, st));
     }
-    if (n > 0) SUPA_CUDA(launch_step(b->minb, b->regions, p, b->grid, b->block, b->smem, st));
+    if (n > 0) SUPA_CUDA(launch_step(b->minb, b->regions, b->flush_thr > 0, p, b->grid, b->block, b->smem, st));
     if (!hybrid) {
         SUPA_CUDA(launch_scan_counts(b->d_hit_count, n, b->d_offsets, b->d_scan_tmp, st));
         return SUPA_OK;
@@ -722,12 +730,19 @@ int supa_autotune(const supa_geometry *const *geoms, int32_t n_geoms, const supa
         c.stack_depth = depth;
         if (depth != best.stack_depth) consider(c);
     }
+    if (best.flush_threshold == 0) best.flush_threshold = 128;
+    for (int ft : {-1, 64, 128, 256}) {
+        supa_launch_config c = best;
+        c.flush_threshold = ft;
+        if (ft != best.flush_threshold) consider(c);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!std::isfinite(best_t)) return fail(SUPA_ERR_CUDA, "supa_autotune: no candidate launch shape ran");
     cfg->blocks_per_sm = best.blocks_per_sm;
     cfg->warps_per_block = best.warps_per_block;
     cfg->stack_depth = best.stack_depth;
+    cfg->flush_threshold = best.flush_threshold;
     if (best_ms) *best_ms = best_t;
     g_last_error.clear();
     return SUPA_OK;

@@ -9,10 +9,13 @@
 //    shared memory (ballot + popc compaction, no atomics; two 16-byte words
 //    per particle); empty lanes refill from the stack.  A stack that outgrows shared memory spills its oldest
 //    half to a per-warp region of global scratch.
-//  * Stops are written as float4 hits straight from the lanes to the warp's
-//    current page of the hit pool: the stopping lanes of one iteration
-//    write consecutive 16-byte slots (ballot + popc), so a warp's stores of
-//    one iteration are contiguous, and L2 merges them into full sectors.
+//  * Stops become float4 hits in the warp's current page of the hit pool, in
+//    one of two builds.  STAGED (the default): hits are staged in shared
+//    memory (ballot + popc compaction) and flushed with coalesced 16-byte
+//    stores once flush_thr are staged.  Direct: the stopping lanes of one
+//    iteration write consecutive 16-byte slots straight from registers, so a
+//    warp's stores of one iteration are contiguous and L2 merges them into
+//    full sectors (on C2 about 1.5 % faster: no shared-memory round trip).
 //  * Deposits are summed exactly in 64-bit fixed point (units of 2^-32) in
 //    shared memory -- per layer, and dead / leaked / escaped energy -- with
 //    32-bit shared-memory atomics on the integer pipe (GB300's FP64 rate is a
@@ -30,6 +33,8 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct WarpSmem {
+    float4 *stage;                  // STAGED build: staged hits
+    unsigned long long *stage_tag;  // and their lineage ids (record_tags)
     float4 *sa, *sb;   // particle stack: (x, y, ux, uy), (uz, E, lin lo, lin hi)
     unsigned long long *lsum;  // [SUPA_MAX_LAYERS] fixed point, units of 2^-32
     unsigned long long *acc;   // [kAccDead, kAccLeak, kAccEscape], fixed point
@@ -38,7 +43,7 @@ struct WarpSmem {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-__device__ inline WarpSmem carve(unsigned char *base, int C) {
+__device__ inline WarpSmem carve(unsigned char *base, int C, int H, bool tags) {
     WarpSmem w;
     size_t o = 0;
     w.sa = reinterpret_cast<float4 *>(base + o);
@@ -49,6 +54,11 @@ __device__ inline WarpSmem carve(unsigned char *base, int C) {
     w.acc = w.lsum + SUPA_MAX_LAYERS;
     o += size_t(8) * (SUPA_MAX_LAYERS + 4);
     w.sk = base + o;
+    o = align16(o + size_t(C));
+    w.stage = reinterpret_cast<float4 *>(base + o);
+    o += size_t(16) * H;
+    w.stage_tag = reinterpret_cast<unsigned long long *>(base + o);
+    (void)tags;
     return w;
 }
 
@@ -162,18 +172,36 @@ __device__ __forceinline__ bool next_page(const StepParams &p, PageCursor &pc, i
     return true;
 }
 
+// STAGED build: write `count` staged hits to the page chain.  Lane-uniform.
+__device__ __forceinline__ bool flush(const StepParams &p, const WarpSmem &w, int count, PageCursor &pc, int lane) {
+    int done = 0;
+    while (done < count) {
+        if (pc.off == kPageHits && !next_page(p, pc, lane)) return false;
+        const int m = min(count - done, kPageHits - pc.off);
+        const size_t base = (size_t)pc.page * kPageHits + pc.off;
+        for (int j = lane; j < m; j += 32) p.pool[base + j] = w.stage[done + j];
+        if (p.tag_pool)
+            for (int j = lane; j < m; j += 32) p.tag_pool[base + j] = w.stage_tag[done + j];
+        pc.off += m;
+        done += m;
+    }
+    __syncwarp();
+    return true;
+}
+
 }  // namespace
 
-size_t warp_smem_bytes(int stack_cap) {
-    // particle stack: 2 x 16 B + the slice byte per particle; fixed-point sums
-    const size_t o = size_t(32) * stack_cap + size_t(8) * (SUPA_MAX_LAYERS + 4) + size_t(stack_cap);
-    return align16(o);
+size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags) {
+    // particle stack: 2 x 16 B + the slice byte per particle; fixed-point
+    // sums; the STAGED build's hit staging (16 B, + 8 B with tags, per slot)
+    const size_t o = align16(size_t(32) * stack_cap + size_t(8) * (SUPA_MAX_LAYERS + 4) + size_t(stack_cap));
+    return align16(o + size_t(16) * stage_cap + (tags ? size_t(8) * stage_cap : 0));
 }
 
 // MINB: resident 256-thread blocks per SM the register budget is cut for
 // (3: 80 registers, 4: 64).  REGIONS: some geometry of the batch has lateral
 // regions (without, the threshold tables line up with the slice tables).
-template <int MINB, bool REGIONS>
+template <int MINB, bool REGIONS, bool STAGED>
 __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -182,7 +210,7 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
     const unsigned lt_mask = (1u << lane) - 1u;
     const int C = p.stack_cap;
     const bool tags = p.tag_pool != nullptr;
-    const WarpSmem w = carve(smem_raw + (size_t)wib * p.warp_smem_bytes, C);
+    const WarpSmem w = carve(smem_raw + (size_t)wib * p.warp_smem_bytes, C, p.stage_cap, tags);
     SpillRec *spill = p.spill + (size_t)warp_global * p.spill_cap;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
 
@@ -235,7 +263,7 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
             cur.ux = st * cp; cur.uy = st * sp; cur.uz = ct;
             cur.E = pr.E; cur.lin = 1ull; cur.k = k0;
         }
-        int stack_n = 0, spill_n = 0;
+        int stack_n = 0, spill_n = 0, staged = 0;
         uint32_t n_hits = 0, n_steps = 0;
         bool failed = false;
         __syncwarp();
@@ -406,37 +434,65 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
                 __syncwarp();
             }
 
-            // ---- write hits straight to the page chain ----
-            const unsigned hm = __ballot_sync(kFull, hit);
-            const int nh = __popc(hm);
-            if (nh) {
-                const int idx = __popc(hm & lt_mask);
-                const int room = kPageHits - pc.off;  // >= 1
-                if (hit && idx < room) {
-                    const size_t a = (size_t)pc.page * kPageHits + pc.off + idx;
-                    p.pool[a] = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
-                    if (tags) p.tag_pool[a] = cur.lin;
-                }
-                if (nh >= room) {
-                    // the page is full: the rest go to a fresh page linked after it
-                    if (!next_page(p, pc, lane)) {
-                        if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
-                        failed = true;
-                        break;
+            // ---- hits: staged in shared memory and flushed past the threshold
+            //      (STAGED), or written straight to the page chain ----
+            if (STAGED) {
+                const unsigned hm = __ballot_sync(kFull, hit);
+                const int nh = __popc(hm);
+                if (nh) {
+                    if (hit) {
+                        const int idx = staged + __popc(hm & lt_mask);
+                        w.stage[idx] = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
+                        if (tags) w.stage_tag[idx] = cur.lin;
                     }
-                    if (hit && idx >= room) {
-                        const size_t a = (size_t)pc.page * kPageHits + (idx - room);
+                    staged += nh;
+                    n_hits += nh;
+                    __syncwarp();
+                    if (staged >= p.flush_thr) {
+                        if (!flush(p, w, staged, pc, lane)) {
+                            if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
+                            failed = true;
+                            break;
+                        }
+                        staged = 0;
+                    }
+                }
+            } else {
+                const unsigned hm = __ballot_sync(kFull, hit);
+                const int nh = __popc(hm);
+                if (nh) {
+                    const int idx = __popc(hm & lt_mask);
+                    const int room = kPageHits - pc.off;  // >= 1
+                    if (hit && idx < room) {
+                        const size_t a = (size_t)pc.page * kPageHits + pc.off + idx;
                         p.pool[a] = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
                         if (tags) p.tag_pool[a] = cur.lin;
                     }
-                    pc.off = nh - room;
-                } else {
-                    pc.off += nh;
+                    if (nh >= room) {
+                        // the page is full: the rest go to a fresh page linked after it
+                        if (!next_page(p, pc, lane)) {
+                            if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
+                            failed = true;
+                            break;
+                        }
+                        if (hit && idx >= room) {
+                            const size_t a = (size_t)pc.page * kPageHits + (idx - room);
+                            p.pool[a] = make_float4(cur.x, cur.y, (float)cur.k * g.dz, cur.E);
+                            if (tags) p.tag_pool[a] = cur.lin;
+                        }
+                        pc.off = nh - room;
+                    } else {
+                        pc.off += nh;
+                    }
+                    n_hits += nh;
                 }
-                n_hits += nh;
             }
         }
         if (failed) break;
+        if (STAGED && staged && !flush(p, w, staged, pc, lane)) {
+            if (lane == 0) atomicOr(p.error, kErrPoolOverflow);
+            break;
+        }
 
         // ---- per-shower records ----
         for (int o = 16; o > 0; o >>= 1) {
@@ -464,36 +520,36 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
 }
 
 namespace {
-template <int MINB, bool REGIONS>
-cudaError_t attrs(int block, size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(supa_step_kernel<MINB, REGIONS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    // largest shared-memory carve-out, so downsampling CTAs of another batch
-    // can share the SM with these blocks
-    e = cudaFuncSetAttribute(supa_step_kernel<MINB, REGIONS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, supa_step_kernel<MINB, REGIONS>, block, smem);
+using StepKernel = void (*)(const StepParams);
+
+// The builds of the step kernel: [64-register][lateral regions][staged hits].
+StepKernel pick(int minb, bool regions, bool staged) {
+    static const StepKernel k[2][2][2] = {
+        {{supa_step_kernel<3, false, false>, supa_step_kernel<3, false, true>},
+         {supa_step_kernel<3, true, false>, supa_step_kernel<3, true, true>}},
+        {{supa_step_kernel<4, false, false>, supa_step_kernel<4, false, true>},
+         {supa_step_kernel<4, true, false>, supa_step_kernel<4, true, true>}}};
+    return k[minb >= 4][regions][staged];
 }
 }  // namespace
 
-cudaError_t launch_step(int minb, bool regions, const StepParams &p, int grid, int block, size_t smem,
+cudaError_t launch_step(int minb, bool regions, bool staged, const StepParams &p, int grid, int block, size_t smem,
                         cudaStream_t st) {
-    if (minb >= 4 && regions)
-        supa_step_kernel<4, true><<<grid, block, smem, st>>>(p);
-    else if (minb >= 4)
-        supa_step_kernel<4, false><<<grid, block, smem, st>>>(p);
-    else if (regions)
-        supa_step_kernel<3, true><<<grid, block, smem, st>>>(p);
-    else
-        supa_step_kernel<3, false><<<grid, block, smem, st>>>(p);
+    pick(minb, regions, staged)<<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t step_kernel_attributes(int minb, bool regions, int block, size_t smem, int *blocks_per_sm) {
-    if (minb >= 4) return regions ? attrs<4, true>(block, smem, blocks_per_sm) : attrs<4, false>(block, smem, blocks_per_sm);
-    return regions ? attrs<3, true>(block, smem, blocks_per_sm) : attrs<3, false>(block, smem, blocks_per_sm);
+cudaError_t step_kernel_attributes(int minb, bool regions, bool staged, int block, size_t smem, int *blocks_per_sm) {
+    const StepKernel k = pick(minb, regions, staged);
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // largest shared-memory carve-out, so downsampling CTAs of another batch
+    // can share the SM with these blocks
+    e = cudaFuncSetAttribute(reinterpret_cast<const void *>(k), cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, smem);
 }
 
 }  // namespace supa

@@ -175,6 +175,8 @@ struct StepParams {
     SpillRec *spill;
     int spill_cap;        // records per warp
     int stack_cap;        // particles per warp in shared memory
+    int stage_cap;        // staged hits per warp (flush_thr + 32; 0: hits written directly)
+    int flush_thr;        // staged hits that trigger a flush
     int warp_smem_bytes;  // shared memory per warp
     // hybrid path (e_s = 0: off)
     float e_s;
@@ -194,14 +196,14 @@ constexpr int kErrSpillOverflow = 2;
 constexpr int kErrBadPrimary = 4;
 constexpr int kErrQueueOverflow = 16;
 
-size_t warp_smem_bytes(int stack_cap);
+size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags);
 
 // Kernel launchers (defined in the .cu files, called by the C ABI).
 // minb selects the register budget of the step kernel (3 or 4 resident
 // 256-thread blocks per SM: 80 or 64 registers).
-cudaError_t launch_step(int minb, bool regions, const StepParams &p, int grid, int block, size_t smem,
+cudaError_t launch_step(int minb, bool regions, bool staged, const StepParams &p, int grid, int block, size_t smem,
                         cudaStream_t st);
-cudaError_t step_kernel_attributes(int minb, bool regions, int block, size_t smem, int *blocks_per_sm);
+cudaError_t step_kernel_attributes(int minb, bool regions, bool staged, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_scan_counts(const uint32_t *counts, int64_t n, int64_t *offsets, unsigned long long *block_tmp,
                                cudaStream_t st);
 size_t scan_tmp_elems(int64_t n);

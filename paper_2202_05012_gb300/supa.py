@@ -60,7 +60,7 @@ class supa_geometry_desc(ctypes.Structure):
 class supa_launch_config(ctypes.Structure):
     _fields_ = [
         ("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
-        ("record_tags", ctypes.c_int32), ("lpt_order", ctypes.c_int32),
+        ("flush_threshold", ctypes.c_int32), ("record_tags", ctypes.c_int32), ("lpt_order", ctypes.c_int32),
         ("voxel_ctas_per_sm", ctypes.c_int32), ("max_hits", ctypes.c_int64),
     ]
 

@@ -103,12 +103,15 @@ def test_escape_and_leak_paths():
 
 
 @pytest.mark.parametrize("cfg", [
-    {"stack_depth": 64, "warps_per_block": 4},
-    {"stack_depth": 256, "warps_per_block": 8, "blocks_per_sm": 1},
+    {"stack_depth": 64, "flush_threshold": 32, "warps_per_block": 4},
+    {"stack_depth": 256, "flush_threshold": 256, "warps_per_block": 8, "blocks_per_sm": 1},
     {"lpt_order": 1},
+    {"flush_threshold": -1},
 ])
 def test_launch_shapes_do_not_change_results(cfg):
-    """Spills to global scratch (tiny stacks), one block per SM, LPT ordering."""
+    """Spills to global scratch (tiny stacks), small and large flush thresholds of
+    the hit staging, one block per SM, LPT ordering, hits written without
+    staging."""
     g = inputs.supa_d(50)
     p = inputs.primaries(60, 24, e_lo=100.0, e_hi=1000.0, log_uniform=True)
     _check([g], p, seed=3, cfg=cfg)

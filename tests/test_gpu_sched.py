@@ -27,10 +27,10 @@ def test_autotune_returns_a_valid_shape_with_identical_results():
         cfg, ms = S.supa_autotune(gh, d, len(p), seed=2, cfg={"lpt_order": 1, "max_hits": max_hits})
         assert ms > 0
         assert 2 <= cfg["blocks_per_sm"] <= 4 and cfg["warps_per_block"] in (4, 8)
-        assert cfg["stack_depth"] in (96, 128, 192, 256)
+        assert cfg["stack_depth"] in (96, 128, 192, 256) and cfg["flush_threshold"] in (-1, 64, 128, 256)
         assert cfg["max_hits"] == max_hits
         out = []
-        for c in (cfg, {"blocks_per_sm": 2, "warps_per_block": 4, "stack_depth": 64,
+        for c in (cfg, {"blocks_per_sm": 2, "warps_per_block": 4, "stack_depth": 64, "flush_threshold": 32,
                         "max_hits": max_hits}):
             b = S.supa_batch_create(gh, len(p), c)
             try:
