@@ -2,27 +2,29 @@
 // 96 (90 used) in one persistent kernel: the activations of a 128-row tile
 // never leave the SM.
 //
-// Per tile, layer l's accumulator lives in tensor memory (two 256-column
-// accumulators, alternating by layer), its epilogue (bias, GELU, BF16) writes
-// the activation straight into shared memory in the 128-byte-swizzled
-// K-major layout the next layer's tcgen05.mma reads, one 64-column K-block
-// at a time, and the MMAs of layer l+1 start on each K-block as soon as it
-// is written -- so the tensor core works while the epilogue is still busy
-// with the rest of the layer.  Only the 6 inputs (24 B) and the outputs of a
-// row touch HBM.
+// Two row tiles are in flight per CTA (slots A and B, each with its own
+// 256-column accumulator in tensor memory and its own activation buffer H),
+// and their layers alternate: while the epilogue warps turn slot A's layer-l
+// accumulator into activations (bias, GELU, BF16, written straight into
+// shared memory in the 128-byte-swizzled K-major layout the next MMA reads),
+// the tensor core runs slot B's layer, and the other way round.  A slot's
+// next layer starts once the epilogue has read all of its accumulator (the
+// layer overwrites it).  Only the 6 inputs (24 B) and the outputs of a row
+// touch HBM.
 //
-// Shared memory (230,400 B with alignment slack):
-//   X   16 KB       inputs of a tile (bf16, columns 0..15 used, K = 16); the
-//                   next tile is packed while the current one runs layers 2-4
-//   H   64 KB       hidden activation, 4 K-blocks of 128 rows x 64 columns
-//   W1  32 KB       resident: 256 rows x 64 columns (columns 0..15 used)
-//   W4  48 KB       resident: 4 K-blocks of 96 rows x 64 columns
-//   S   2 x 32 KB   ring of the 4 K-blocks of W2 and of W3 (256 rows x 64
-//                   columns each), TMA
+// Shared memory (209,920 B with alignment slack):
+//   X   16 KB       inputs of a tile (bf16, columns 0..15 used, K = 16), one
+//                   tile at a time: the next is packed once layer 1 read it
+//   H   2 x 64 KB   hidden activations of slots A and B, 4 K-blocks of 128
+//                   rows x 64 columns each; a slot's output tile is staged
+//                   in its H buffer and written out coalesced
+//   S   2 x 32 KB   ring of weight K-blocks, TMA, in the order the MMAs use
+//                   them: W1 (both slots), then per layer and slot the 4
+//                   K-blocks of W2, W3 (256 rows x 64 columns) or W4 (96 rows)
 // Warps: 0 TMA producer, 1 tensor-memory owner and MMA issuer, 2-3 pack the
 // inputs of each tile, 4-19 epilogue (warp w reads TMEM lanes 32(w%4)..+31
 // and columns 16((w-4)/4)..+15 of every K-block; 32((w-4)/4)..+31 of the
-// output layer, w < 16, which is staged in H and written out coalesced).
+// output layer, w < 16).
 //
 // Every wait is bounded (about two seconds): on expiry the CTA sets the error
 // word, stops, lets its TMA loads and MMAs finish (bounded), frees tensor
@@ -44,10 +46,11 @@ constexpr int kMlpThreads = 640;
 constexpr int kRows = 128;
 constexpr uint32_t kXBytes = kRows * 128;    // one input tile
 constexpr uint32_t kHBlk = kRows * 128;      // one K-block of H
-constexpr uint32_t kWBlk = 256 * 128;        // one K-block of a 256-row weight
+constexpr uint32_t kHBytes = 4 * kHBlk;      // one slot's H
+constexpr uint32_t kWBlk = 256 * 128;        // one K-block of a 256-row weight (a ring stage)
 constexpr int kOutN = 96;                    // output-layer width
 constexpr uint32_t kW4Blk = kOutN * 128;     // one K-block of W4
-constexpr uint32_t oX = 0, oH = kXBytes, oW1 = oH + 4 * kHBlk, oW4 = oW1 + kWBlk, oS = oW4 + 4 * kW4Blk;
+constexpr uint32_t oX = 0, oH = kXBytes, oS = oH + 2 * kHBytes;
 constexpr uint32_t kMlpSmem = oS + 2 * kWBlk + 1024;
 constexpr int kEpiWarps = 16;
 
@@ -56,16 +59,15 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                    const __grid_constant__ CUtensorMap tw3, const __grid_constant__ CUtensorMap tw4,
                    const MlpInferArgs g) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t w_res;       // W1 and W4 resident
-    __shared__ __align__(8) uint64_t w_full[2];   // ring stage holds a K-block
-    __shared__ __align__(8) uint64_t w_empty[2];  // the MMAs have read the stage
-    __shared__ __align__(8) uint64_t x_full;      // input tile packed
-    __shared__ __align__(8) uint64_t x_empty;     // layer-1 MMA has read it
-    __shared__ __align__(8) uint64_t h_ready[4];  // K-block kb of H written
-    __shared__ __align__(8) uint64_t acc_full;    // a layer's accumulator is final
-    __shared__ __align__(8) uint64_t drain;       // all MMAs of this CTA done
-    __shared__ __align__(8) uint64_t out_staged;  // every epilogue warp has staged its output block
-    __shared__ __align__(8) uint64_t out_done;    // every epilogue warp has written its share out
+    __shared__ __align__(8) uint64_t w_full[2];      // ring stage holds a K-block
+    __shared__ __align__(8) uint64_t w_empty[2];     // the MMAs have read the stage
+    __shared__ __align__(8) uint64_t x_full;         // input tile packed
+    __shared__ __align__(8) uint64_t x_empty;        // layer-1 MMA has read it
+    __shared__ __align__(8) uint64_t h_ready[2][4];  // slot: K-block kb of H written (accumulator read)
+    __shared__ __align__(8) uint64_t acc_full[2];    // slot: a layer's accumulator is final
+    __shared__ __align__(8) uint64_t drain;          // all MMAs of this CTA done
+    __shared__ __align__(8) uint64_t out_staged[2];  // slot: every epilogue warp staged its output block
+    __shared__ __align__(8) uint64_t out_done[2];    // slot: every epilogue warp wrote its share out
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -75,21 +77,21 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     const int tiles = (M + kRows - 1) / kRows;
     if ((int)blockIdx.x >= tiles) return;
     const int my_tiles = (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int my_pairs = (my_tiles + 1) / 2;  // tile 2p in slot A, tile 2p+1 (if any) in slot B
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
     if (threadIdx.x == 0) {
-        mbar_init(&w_res, 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&w_full[i], 1);
             mbar_init(&w_empty[i], 1);
+            for (int kb = 0; kb < 4; ++kb) mbar_init(&h_ready[i][kb], kEpiWarps);
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&out_staged[i], kEpiWarps);
+            mbar_init(&out_done[i], kEpiWarps);
         }
         mbar_init(&x_full, 2);
         mbar_init(&x_empty, 1);
-        for (int i = 0; i < 4; ++i) mbar_init(&h_ready[i], kEpiWarps);
-        mbar_init(&acc_full, 1);
         mbar_init(&drain, 1);
-        mbar_init(&out_staged, kEpiWarps);
-        mbar_init(&out_done, kEpiWarps);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -102,36 +104,42 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    const uint32_t tmem = tmem_slot;
-    const uint32_t acc0 = tmem, acc1 = tmem + 256;
+    const uint32_t tmem = tmem_slot;  // slot X's accumulator: columns 256 X .. 256 X + 255
     volatile int *abort_v = &abort_flag;
     auto fail = [&]() {
         if (!*abort_v) atomicOr(g.error, kErrTimeout);
         *abort_v = 1;
     };
 
-    int issued = 0;  // ring loads issued by the producer
     if (warp == 0) {
         if (lane == 0) {
-            // ---- TMA producer: resident W1, W4; then the W2, W3 K-blocks per tile ----
-            mbar_expect_tx(&w_res, kWBlk + 4 * kW4Blk);
-            tma_load_2d(base + oW1, &tw1, 0, 0, &w_res);
-            for (int kb = 0; kb < 4; ++kb) tma_load_2d(base + oW4 + kb * kW4Blk, &tw4, kb * 64, 0, &w_res);
-            for (int t = 0; t < my_tiles && !*abort_v; ++t)
-                for (int blk = 0; blk < 8 && !*abort_v; ++blk) {
-                    const int c = issued, s = c & 1;
-                    if (c >= 2 && !mbar_wait(&w_empty[s], ((c >> 1) - 1) & 1)) {
-                        fail();
-                        break;
-                    }
-                    if (*abort_v) break;
-                    mbar_expect_tx(&w_full[s], kWBlk);
-                    tma_load_2d(base + oS + s * kWBlk, blk < 4 ? &tw2 : &tw3, (blk & 3) * 64, 0, &w_full[s]);
-                    issued = c + 1;
+            // ---- TMA producer: the weight K-blocks in the order the MMAs use them ----
+            int issued = 0;
+            auto load = [&](const CUtensorMap *m, int kcol, uint32_t bytes) -> bool {
+                const int c = issued, s = c & 1;
+                if (c >= 2 && !mbar_wait(&w_empty[s], ((c >> 1) - 1) & 1)) {
+                    fail();
+                    return false;
                 }
+                if (*abort_v) return false;
+                mbar_expect_tx(&w_full[s], bytes);
+                tma_load_2d(base + oS + s * kWBlk, m, kcol, 0, &w_full[s]);
+                issued = c + 1;
+                return true;
+            };
+            bool ok = true;
+            for (int pr = 0; pr < my_pairs && ok && !*abort_v; ++pr) {
+                const int nx = 2 * pr + 1 < my_tiles ? 2 : 1;
+                ok = load(&tw1, 0, kWBlk);
+                for (int layer = 2; layer <= 4 && ok; ++layer)
+                    for (int x = 0; x < nx && ok; ++x)
+                        for (int kb = 0; kb < 4 && ok; ++kb)
+                            ok = layer == 2 ? load(&tw2, kb * 64, kWBlk)
+                                 : layer == 3 ? load(&tw3, kb * 64, kWBlk)
+                                              : load(&tw4, kb * 64, kW4Blk);
+            }
             if (*abort_v) {
                 // let the loads in flight land before the CTA exits
-                mbar_wait(&w_res, 0);
                 for (int i = max(0, issued - 2); i < issued; ++i) mbar_wait(&w_full[i & 1], (i >> 1) & 1);
             }
         }
@@ -139,60 +147,67 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         if (lane == 0) {
             // ---- MMA issuer ----
             constexpr uint32_t id256 = idesc_bf16(kRows, 256), idout = idesc_bf16(kRows, kOutN);
-            const uint32_t sX = smem_u32(base + oX), sH = smem_u32(base + oH), sW1 = smem_u32(base + oW1),
-                           sW4 = smem_u32(base + oW4), sS = smem_u32(base + oS);
-            bool ok = mbar_wait(&w_res, 0);
-            if (!ok) fail();
-            uint32_t hc = 0;  // completions of h_ready consumed (one per hidden layer)
-            int wc = 0;       // ring stages consumed
-            for (int t = 0; t < my_tiles && ok && !*abort_v; ++t) {
-                if (!mbar_wait(&x_full, t & 1)) {
+            const uint32_t sX = smem_u32(base + oX), sH = smem_u32(base + oH), sS = smem_u32(base + oS);
+            bool ok = true;
+            int wc = 0;                    // ring stages consumed
+            int xc = 0;                    // input tiles consumed
+            uint32_t hc[2] = {0u, 0u};     // completions of h_ready consumed, per slot
+            for (int pr = 0; pr < my_pairs && ok && !*abort_v; ++pr) {
+                const int nx = 2 * pr + 1 < my_tiles ? 2 : 1;
+                // layer 1: K = 16 (6 inputs, zero padded), W1 from the ring, both slots
+                int s = wc & 1;
+                if (!mbar_wait(&w_full[s], (wc >> 1) & 1)) {
                     fail();
                     break;
                 }
-                fence_after_sync();
-                // layer 1: K = 16 (6 inputs, zero padded), into accumulator 0
-                mma_bf16(acc0, sw128_desc(sX), sw128_desc(sW1), id256, 0u);
-                mma_commit(&x_empty);
-                mma_commit(&acc_full);
-                // layers 2 and 3 from H, weights through the ring
-                for (int layer = 2; layer <= 3 && ok; ++layer) {
-                    const uint32_t acc = layer == 2 ? acc1 : acc0;
-                    for (int kb = 0; kb < 4; ++kb) {
-                        const int s = wc & 1;
-                        if (*abort_v || !mbar_wait(&h_ready[kb], hc & 1) || !mbar_wait(&w_full[s], (wc >> 1) & 1)) {
-                            fail();
-                            ok = false;
-                            break;
-                        }
-                        fence_after_sync();
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            mma_bf16(acc, sw128_desc(sH + kb * kHBlk + k * 32), sw128_desc(sS + s * kWBlk + k * 32),
-                                     id256, (kb > 0 || k > 0) ? 1u : 0u);
-                        mma_commit(&w_empty[s]);
-                        ++wc;
-                    }
-                    ++hc;
-                    if (ok) mma_commit(&acc_full);
-                }
-                if (!ok) break;
-                // layer 4: 96 outputs from H and the resident W4, into accumulator 1
-                for (int kb = 0; kb < 4; ++kb) {
-                    if (*abort_v || !mbar_wait(&h_ready[kb], hc & 1)) {
+                for (int x = 0; x < nx && ok; ++x) {
+                    // the slot's accumulator is free once the previous tile's
+                    // output epilogue has read it
+                    if (!mbar_wait(&x_full, xc & 1) || (pr > 0 && !mbar_wait(&out_staged[x], (pr - 1) & 1))) {
                         fail();
                         ok = false;
                         break;
                     }
+                    ++xc;
                     fence_after_sync();
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        mma_bf16(acc1, sw128_desc(sH + kb * kHBlk + k * 32), sw128_desc(sW4 + kb * kW4Blk + k * 32),
-                                 idout, (kb > 0 || k > 0) ? 1u : 0u);
+                    mma_bf16(tmem + 256 * x, sw128_desc(sX), sw128_desc(sS + s * kWBlk), id256, 0u);
+                    mma_commit(&x_empty);
+                    mma_commit(&acc_full[x]);
                 }
-                ++hc;
                 if (!ok) break;
-                mma_commit(&acc_full);
+                mma_commit(&w_empty[s]);
+                ++wc;
+                // layers 2-4, alternating slots: a slot's layer starts once the
+                // epilogue has read all of its previous accumulator
+                for (int layer = 2; layer <= 4 && ok; ++layer) {
+                    for (int x = 0; x < nx && ok; ++x) {
+                        for (int kb = 0; kb < 4; ++kb)
+                            if (*abort_v || !mbar_wait(&h_ready[x][kb], hc[x] & 1)) {
+                                fail();
+                                ok = false;
+                                break;
+                            }
+                        if (!ok) break;
+                        ++hc[x];
+                        const uint32_t acc = tmem + 256 * x, hx = sH + x * kHBytes;
+                        for (int kb = 0; kb < 4; ++kb) {
+                            s = wc & 1;
+                            if (*abort_v || !mbar_wait(&w_full[s], (wc >> 1) & 1)) {
+                                fail();
+                                ok = false;
+                                break;
+                            }
+                            fence_after_sync();
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                mma_bf16(acc, sw128_desc(hx + kb * kHBlk + k * 32), sw128_desc(sS + s * kWBlk + k * 32),
+                                         layer == 4 ? idout : id256, (kb > 0 || k > 0) ? 1u : 0u);
+                            mma_commit(&w_empty[s]);
+                            ++wc;
+                        }
+                        if (ok) mma_commit(&acc_full[x]);
+                    }
+                }
             }
             // every MMA issued by this thread completes before tensor memory is freed
             mma_commit(&drain);
@@ -230,98 +245,106 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         const int q = warp & 3, h = (warp - 4) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        uint8_t *hs = base + oH;
-        uint32_t ac = 0;  // completions of acc_full consumed
-        for (int t = 0; t < my_tiles; ++t) {
-            const int row = ((int)blockIdx.x + t * (int)gridDim.x) * kRows + r;
-            bool ok = true;
-            for (int layer = 1; layer <= 3; ++layer) {
-                // warp-uniform, so that the .sync.aligned TMEM loads see the whole warp
-                if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full, ac & 1))) {
+        uint32_t ac[2] = {0u, 0u};  // completions of acc_full consumed, per slot
+        bool ok = true;
+        for (int pr = 0; pr < my_pairs && ok; ++pr) {
+            const int nx = 2 * pr + 1 < my_tiles ? 2 : 1;
+            for (int layer = 1; layer <= 3 && ok; ++layer) {
+                for (int x = 0; x < nx; ++x) {
+                    // warp-uniform, so that the .sync.aligned TMEM loads see the whole warp
+                    if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full[x], ac[x] & 1))) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    ++ac[x];
+                    fence_after_sync();
+                    const uint32_t acc = tmem + 256 * x + lane_off;
+                    const float *bias = layer == 1 ? g.b1 : layer == 2 ? g.b2 : g.b3;
+                    uint8_t *hs = base + oH + x * kHBytes;
+                    for (int kb = 0; kb < 4; ++kb) {
+                        const int c0 = kb * 64 + h * 16;
+                        float v[16];
+                        tmem_ld16(acc + c0, v);
+                        const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
+                        uint32_t p[8];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float4 bb = __ldg(b4 + i);
+                            p[2 * i] =
+                                gelu2_bf16(__fadd2_rn(make_float2(v[4 * i], v[4 * i + 1]), make_float2(bb.x, bb.y)));
+                            p[2 * i + 1] = gelu2_bf16(
+                                __fadd2_rn(make_float2(v[4 * i + 2], v[4 * i + 3]), make_float2(bb.z, bb.w)));
+                        }
+                        uint8_t *blk = hs + kb * kHBlk;
+                        *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
+                        *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) =
+                            make_uint4(p[4], p[5], p[6], p[7]);
+                        fence_smem_to_async();
+                        fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&h_ready[x][kb]);
+                    }
+                }
+            }
+            // Output layer of each slot: stage the 128 x 96 tile in the slot's H
+            // buffer (idle now: layer 4's MMAs are done, and the next tile of
+            // the slot writes H only after every warp has passed out_done),
+            // then write it out row by row, coalesced.  Row pitch 100 floats:
+            // the float4 stores of 8 consecutive rows hit distinct banks.
+            for (int x = 0; x < nx && ok; ++x) {
+                if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full[x], ac[x] & 1))) {
                     fail();
                     ok = false;
                     break;
                 }
-                ++ac;
+                ++ac[x];
                 fence_after_sync();
-                const uint32_t acc = (layer == 2 ? acc1 : acc0) + lane_off;
-                const float *bias = layer == 1 ? g.b1 : layer == 2 ? g.b2 : g.b3;
-                for (int kb = 0; kb < 4; ++kb) {
-                    const int c0 = kb * 64 + h * 16;
-                    float v[16];
-                    tmem_ld16(acc + c0, v);
-                    const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
-                    uint32_t p[8];
+                float *stage = reinterpret_cast<float *>(base + oH + x * kHBytes);
+                constexpr int kPitch = 100;
+                const int c0 = h * 32;
+                if (c0 < kOutN) {
+                    float v[32];
+                    tmem_ld32(tmem + 256 * x + lane_off + c0, v);
+                    const float4 *b4 = reinterpret_cast<const float4 *>(g.b4 + c0);
+                    float4 *dst = reinterpret_cast<float4 *>(stage + r * kPitch + c0);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < 8; ++i) {
                         const float4 bb = __ldg(b4 + i);
-                        p[2 * i] = gelu2_bf16(__fadd2_rn(make_float2(v[4 * i], v[4 * i + 1]), make_float2(bb.x, bb.y)));
-                        p[2 * i + 1] =
-                            gelu2_bf16(__fadd2_rn(make_float2(v[4 * i + 2], v[4 * i + 3]), make_float2(bb.z, bb.w)));
+                        dst[i] = make_float4(v[4 * i] + bb.x, v[4 * i + 1] + bb.y, v[4 * i + 2] + bb.z,
+                                             v[4 * i + 3] + bb.w);
                     }
-                    uint8_t *blk = hs + kb * kHBlk;
-                    *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
-                    *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) = make_uint4(p[4], p[5], p[6], p[7]);
-                    fence_smem_to_async();
-                    fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&h_ready[kb]);
                 }
-            }
-            if (!ok) break;
-            if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full, ac & 1))) {
-                fail();
-                break;
-            }
-            ++ac;
-            fence_after_sync();
-            // Output layer: stage the 128 x 96 tile in the H buffer (idle now:
-            // layer 4's MMAs are done and the next tile's layer-1 epilogue
-            // writes H only after every warp has passed out_done), then write
-            // it out row by row, coalesced.  Row pitch 100 floats: the float4
-            // stores of 8 consecutive rows hit distinct banks.
-            float *stage = reinterpret_cast<float *>(hs);
-            constexpr int kPitch = 100;
-            const int c0 = h * 32;
-            if (c0 < kOutN) {
-                float v[32];
-                tmem_ld32(acc1 + lane_off + c0, v);
-                const float4 *b4 = reinterpret_cast<const float4 *>(g.b4 + c0);
-                float4 *dst = reinterpret_cast<float4 *>(stage + r * kPitch + c0);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float4 bb = __ldg(b4 + i);
-                    dst[i] = make_float4(v[4 * i] + bb.x, v[4 * i + 1] + bb.y, v[4 * i + 2] + bb.z,
-                                         v[4 * i + 3] + bb.w);
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&out_staged[x]);
+                if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&out_staged[x], pr & 1))) {
+                    fail();
+                    ok = false;
+                    break;
                 }
-            }
-            fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&out_staged);
-            if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&out_staged, t & 1))) {
-                fail();
-                break;
-            }
-            const int m0 = row - r;
-            const int e = (warp - 4) * 32 + lane;  // 0..511 over the epilogue warps
-            const bool vec = (g.ld & 3) == 0 && ((uintptr_t)g.out & 15) == 0;
-            for (int idx = e; idx < kRows * (kOutN / 4); idx += kEpiWarps * 32) {
-                const int rr = idx / (kOutN / 4), c = (idx % (kOutN / 4)) * 4;
-                if (m0 + rr >= M || c >= g.ncols) continue;
-                const float4 val = *reinterpret_cast<const float4 *>(stage + rr * kPitch + c);
-                float *o = g.out + (size_t)(m0 + rr) * g.ld + c;
-                if (vec && c + 4 <= g.ncols) {
-                    *reinterpret_cast<float4 *>(o) = val;
-                } else {
-                    const float w4[4] = {val.x, val.y, val.z, val.w};
-                    for (int j = 0; j < 4 && c + j < g.ncols; ++j) o[j] = w4[j];
+                const int m0 = ((int)blockIdx.x + (2 * pr + x) * (int)gridDim.x) * kRows;
+                const int e = (warp - 4) * 32 + lane;  // 0..511 over the epilogue warps
+                const bool vec = (g.ld & 3) == 0 && ((uintptr_t)g.out & 15) == 0;
+                for (int idx = e; idx < kRows * (kOutN / 4); idx += kEpiWarps * 32) {
+                    const int rr = idx / (kOutN / 4), c = (idx % (kOutN / 4)) * 4;
+                    if (m0 + rr >= M || c >= g.ncols) continue;
+                    const float4 val = *reinterpret_cast<const float4 *>(stage + rr * kPitch + c);
+                    float *o = g.out + (size_t)(m0 + rr) * g.ld + c;
+                    if (vec && c + 4 <= g.ncols) {
+                        *reinterpret_cast<float4 *>(o) = val;
+                    } else {
+                        const float w4[4] = {val.x, val.y, val.z, val.w};
+                        for (int j = 0; j < 4 && c + j < g.ncols; ++j) o[j] = w4[j];
+                    }
                 }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&out_done);
-            if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&out_done, t & 1))) {
-                fail();
-                break;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&out_done[x]);
+                if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&out_done[x], pr & 1))) {
+                    fail();
+                    ok = false;
+                    break;
+                }
             }
         }
     }
