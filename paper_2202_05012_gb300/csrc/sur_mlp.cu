@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     __shared__ __align__(8) uint64_t w_empty[2];     // the MMAs have read the stage
     __shared__ __align__(8) uint64_t x_full;         // input tile packed
     __shared__ __align__(8) uint64_t x_empty;        // layer-1 MMA has read it
-    __shared__ __align__(8) uint64_t h_ready[2][4];  // slot: K-block kb of H written (accumulator read)
+    __shared__ __align__(8) uint64_t h_ready[2];     // slot: H written, accumulator read
     __shared__ __align__(8) uint64_t acc_full[2];    // slot: a layer's accumulator is final
     __shared__ __align__(8) uint64_t drain;          // all MMAs of this CTA done
     __shared__ __align__(8) uint64_t out_staged[2];  // slot: every epilogue warp staged its output block
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&w_full[i], 1);
             mbar_init(&w_empty[i], 1);
-            for (int kb = 0; kb < 4; ++kb) mbar_init(&h_ready[i][kb], kEpiWarps);
+            mbar_init(&h_ready[i], kEpiWarps);
             mbar_init(&acc_full[i], 1);
             mbar_init(&out_staged[i], kEpiWarps);
             mbar_init(&out_done[i], kEpiWarps);
@@ -181,13 +181,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                 // epilogue has read all of its previous accumulator
                 for (int layer = 2; layer <= 4 && ok; ++layer) {
                     for (int x = 0; x < nx && ok; ++x) {
-                        for (int kb = 0; kb < 4; ++kb)
-                            if (*abort_v || !mbar_wait(&h_ready[x][kb], hc[x] & 1)) {
-                                fail();
-                                ok = false;
-                                break;
-                            }
-                        if (!ok) break;
+                        if (*abort_v || !mbar_wait(&h_ready[x], hc[x] & 1)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
                         ++hc[x];
                         const uint32_t acc = tmem + 256 * x, hx = sH + x * kHBytes;
                         for (int kb = 0; kb < 4; ++kb) {
@@ -280,11 +278,13 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                         *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
                         *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) =
                             make_uint4(p[4], p[5], p[6], p[7]);
-                        fence_smem_to_async();
-                        fence_before_sync();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&h_ready[x][kb]);
                     }
+                    // the next layer's MMAs overwrite the whole accumulator, so
+                    // they wait for all of H: one hand-off per layer
+                    fence_smem_to_async();
+                    fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&h_ready[x]);
                 }
             }
             // Output layer of each slot: stage the 128 x 96 tile in the slot's H
