@@ -74,7 +74,7 @@ def workload(name: str, n: int):
         return g, p, 4, dict(workload="plain SUPA, E log-U[10,1000], 0-45 deg, 50 layers, 50x128x128", seed=4)
     g, p = inputs.workload_c2(n or 1_000_000)
     return g, p, 1, dict(workload="plain SUPA, 1M showers, E U[1,100], 0-30 deg, +-1 cell entry, 30 layers, "
-                                  "30x64x64 axis-centred images, 64M-hit chunks", seed=1)
+                                  "30x64x64 axis-centred images, point cloud written by the image pass", seed=1)
 
 
 class Clocks:
@@ -457,6 +457,8 @@ def run_supa_serial(args):
     oor = torch.empty(V, dtype=torch.float64, device="cuda")
     FC = args.fetch_chunk
     fbuf = torch.empty((FC, 4), dtype=torch.float32, device="cuda")
+    # the point cloud of a step, in shower order (written by the image pass)
+    hbuf = torch.empty((max_hits, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
@@ -473,14 +475,12 @@ def run_supa_serial(args):
             if ev is not None:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            S.supa_voxelize(b, c0, c1, grid, oor)
+            # images and point cloud of the chunk in one pass over its hits
+            S.supa_voxelize_fetch(b, c0, c1, grid, oor, hbuf)
             launches += 1
             if ev is not None:
                 e1.record(stream)
                 ev["vox"].append((e0, e1, c1 - c0))
-        for h0 in range(0, info.n_hits, FC):
-            S.supa_fetch_hits(b, h0, FC, fbuf)
-            launches += 1
         return info, launches
 
     for _ in range(args.warmup):
@@ -523,7 +523,8 @@ def run_supa_serial(args):
     pk, pk_kind = peaks()
     full = [(x, m) for x, m in vox_launch if m == V] or vox_launch
     avg_ms = sum(x for x, _ in full) / len(full)
-    bytes_per_shower = L * ny * nx * 4 + 16 * hits_per_shower + 8
+    # images written + hits read + hits written (point cloud) + out-of-region sum
+    bytes_per_shower = L * ny * nx * 4 + 32 * hits_per_shower + 8
     achieved = full[0][1] * bytes_per_shower / (avg_ms / 1000.0) / 1e9
     traffic = stored_traffic("supa_voxel_kernel", args.workload, full[0][1])
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -534,7 +535,7 @@ def run_supa_serial(args):
         "metric": METRIC, "value": value, "unit": "showers/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(conf, showers=n, layers=L, grid=[L, ny, nx], fetch_chunk_hits=FC,
+        "config": dict(conf, showers=n, layers=L, grid=[L, ny, nx],
                        voxel_chunk_showers=V, l2="inputs larger than L2 (hit pool and image chunks >> 129 MB)",
                        parallelism=f"replicas x{world}"),
         "particle_steps_per_s": n_steps * args.steps * world / (elapsed_ms / 1000.0),
@@ -601,12 +602,13 @@ def profile_errors(ref, got, thr=0.005):
 def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor, fbuf, L, profiles=False, mode=0,
                voxelize=True):
     """The whole path in hybrid mode over n showers in sub-batches: simulate
-    (stepping above E_s, network below), downsample, fetch.  Returns timings
+    (stepping above E_s, network below), images and point cloud in one pass.  Returns timings
     and (optionally) accumulated profiles."""
     import torch
     mean_e = float(prims["E"][:n].mean())
     cap = int(4.0 * mean_e / e_s * sub) + (1 << 20)
-    hb = S.supa_batch_create([gh], sub, {"max_hits": int(sub * max(400, 40 * mean_e)) + (8 << 20), "lpt_order": 1})
+    hb_hits = int(sub * max(400, 40 * mean_e)) + (8 << 20)
+    hb = S.supa_batch_create([gh], sub, {"max_hits": hb_hits, "lpt_order": 1})
     S.supa_batch_set_surrogate(hb, net, e_s, cap, mode)
     lo = torch.zeros(L, dtype=torch.float64, device="cuda")
     la = torch.zeros(PROFILE_BINS, dtype=torch.float64, device="cuda")
@@ -615,6 +617,7 @@ def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor,
     sim_ms = 0.0
     steps = diverted = hits = 0
     FC = fbuf.shape[0]
+    hbuf = torch.empty((hb_hits, 4), dtype=torch.float32, device="cuda") if voxelize else None  # point cloud
     torch.cuda.synchronize()
     ev[0].record(stream)
     for j in range(0, n, sub):
@@ -629,9 +632,10 @@ def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor,
         hits += info.n_hits
         if voxelize:
             for c0 in range(0, m, V):
-                S.supa_voxelize(hb, c0, min(m, c0 + V), grid, oor)
-        for h0 in range(0, info.n_hits, FC):
-            S.supa_fetch_hits(hb, h0, FC, fbuf)
+                S.supa_voxelize_fetch(hb, c0, min(m, c0 + V), grid, oor, hbuf)
+        else:
+            for h0 in range(0, info.n_hits, FC):
+                S.supa_fetch_hits(hb, h0, FC, fbuf)
         if profiles:
             S.supa_profiles(hb, 0, m, PROFILE_BINS, PROFILE_RMAX, lo, la)
     ev[1].record(stream)
@@ -819,14 +823,14 @@ def shape_timing(S, b, n, L, hits_per_shower):
 
 def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
     """Same metric through the public API with host buffers: primaries copied
-    from pinned host memory each step, the point cloud (all hits, fetched in
-    64M-hit chunks) and the per-shower FP64 layer sums read back to pinned
-    host memory.  Each chunk travels to the host on a second stream (copy
-    engines) as soon as it is fetched, while the images are made and while
-    the next step simulates; two host buffers alternate, so a step's results
-    stay intact while the step after it runs.  Images stay on the device,
-    consumed chunk by chunk.  Every copy of the timed steps has finished when
-    the clock stops."""
+    from pinned host memory each step, the point cloud (all hits, written by
+    the image pass chunk by chunk) and the per-shower FP64 layer sums read
+    back to pinned host memory.  Each chunk's hits travel to the host on a
+    second stream (copy engines) as soon as its images are made, while the
+    next chunks are made and while the next step simulates; two host
+    buffers alternate, so a step's results stay intact while the step after
+    it runs.  Images stay on the device, consumed chunk by chunk.  Every copy
+    of the timed steps has finished when the clock stops."""
     import torch
     import torch.distributed as dist
     h_prim = torch.from_numpy(np.ascontiguousarray(prims).view(np.uint8)).pin_memory()
@@ -844,6 +848,7 @@ def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
     hits_read.record(side)
     h2d = d2h = 0
     it = 0
+    chunk_idx = torch.tensor(list(range(0, n, V)) + [n], dtype=torch.int64, device="cuda")
 
     def step():
         nonlocal h2d, d2h, it
@@ -857,19 +862,17 @@ def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
         with torch.cuda.stream(side):
             hl.copy_(S.info_arrays(inf)["layer_sum"], non_blocking=True)
             ls_read.record(side)
-        cur.wait_event(hits_read)  # the fetch rewrites the device hit buffer
-        got = 0
-        while got < inf.n_hits:
-            m = S.supa_fetch_hits(b, got, min(FETCH_CHUNK, cap - got), d_hits[got:])
-            if m == 0:
-                break
-            side.wait_stream(cur)
-            with torch.cuda.stream(side):
-                hh[got:got + m].copy_(d_hits[got:got + m], non_blocking=True)
-            got += m
+        # first hit of each image chunk (and the end), for the chunks' copies
+        bnd = S.info_arrays(inf)["offsets"][chunk_idx].cpu().tolist()
+        cur.wait_event(hits_read)  # the image pass rewrites the device hit buffer
+        for j, c0 in enumerate(range(0, n, V)):
+            S.supa_voxelize_fetch(b, c0, min(n, c0 + V), grid, oor, d_hits)
+            a, z = bnd[j], bnd[j + 1]
+            if z > a:
+                side.wait_stream(cur)
+                with torch.cuda.stream(side):
+                    hh[a:z].copy_(d_hits[a:z], non_blocking=True)
         hits_read.record(side)
-        for c0 in range(0, n, V):
-            S.supa_voxelize(b, c0, min(n, c0 + V), grid, oor)
         h2d = h_prim.numel()
         d2h = inf.n_hits * 16 + hl.numel() * 8
 

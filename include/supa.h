@@ -235,6 +235,19 @@ int supa_fetch_hit_tags(supa_batch *b, int64_t first_hit, int64_t max_hits, uint
 int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev,
                   double *out_of_roi_dev, void *stream);
 
+/* supa_voxelize and the point cloud of the same showers in one pass over
+ * their hits (App. A.5 images and Sec. 3 point clouds): hit i of shower s,
+ * in the order of supa_fetch_hits, goes to float4 slot
+ * offsets[s] + i - hits_base of hits_dev (offsets as in
+ * supa_batch_info.offsets_dev; hits_dev device memory, 16-byte aligned,
+ * covering slots offsets[shower_begin] - hits_base up to
+ * offsets[shower_end] - hits_base, caller-owned).  The same result as
+ * supa_voxelize followed by supa_fetch_hits of those showers, with the hits
+ * read once instead of twice.  Asynchronous; may follow supa_simulate on the
+ * same stream directly. */
+int supa_voxelize_fetch(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev,
+                        double *out_of_roi_dev, float *hits_dev, int64_t hits_base, void *stream);
+
 /* Shower-shape profiles of showers [shower_begin, shower_end), added to the
  * caller's FP64 accumulators (Sec. 5.1 layer energies; lateral spread):
  * longi_dev[l] += layer energy / E0 per shower (max_layers entries);

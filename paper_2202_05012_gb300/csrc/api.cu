@@ -872,8 +872,8 @@ int supa_fetch_hit_tags(supa_batch *b, int64_t first_hit, int64_t max_hits, uint
 // Two image buffers of at least one layer each must fit in shared memory.
 static const size_t kMaxLayerBytes = 108 * 1024;
 
-int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev, double *out_of_roi_dev,
-                  void *stream) {
+static int voxelize_impl(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev,
+                         double *out_of_roi_dev, float4 *hits_dev, int64_t hits_base, void *stream) {
     if (!b || !grid_dev) return fail(SUPA_ERR_INVALID_ARG, "supa_voxelize: null argument");
     // Stream order is enough: the images read what the last supa_simulate on
     // this stream wrote, so both calls can sit in one captured graph.
@@ -917,8 +917,25 @@ int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float
     p.grid = grid_dev;
     p.oor = out_of_roi_dev;
     p.ctas_per_sm = b->voxel_ctas;
+    p.hits_out = hits_dev;
+    p.offsets = b->d_offsets;
+    p.hits_base = hits_base;
     SUPA_CUDA(launch_voxelize(p, st));
     return SUPA_OK;
+}
+
+int supa_voxelize(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev, double *out_of_roi_dev,
+                  void *stream) {
+    return voxelize_impl(b, shower_begin, shower_end, grid_dev, out_of_roi_dev, nullptr, 0, stream);
+}
+
+int supa_voxelize_fetch(supa_batch *b, int64_t shower_begin, int64_t shower_end, float *grid_dev,
+                        double *out_of_roi_dev, float *hits_dev, int64_t hits_base, void *stream) {
+    if (!hits_dev) return fail(SUPA_ERR_INVALID_ARG, "supa_voxelize_fetch: null hit buffer");
+    if ((size_t)hits_dev % 16 != 0) return fail(SUPA_ERR_INVALID_ARG, "hits_dev must be 16-byte aligned");
+    if (hits_base < 0) return fail(SUPA_ERR_INVALID_ARG, "hits_base must be >= 0");
+    return voxelize_impl(b, shower_begin, shower_end, grid_dev, out_of_roi_dev, reinterpret_cast<float4 *>(hits_dev),
+                         hits_base, stream);
 }
 
 int supa_profiles(supa_batch *b, int64_t shower_begin, int64_t shower_end, int32_t nbins, float r_max,

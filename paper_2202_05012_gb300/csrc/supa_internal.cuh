@@ -243,6 +243,11 @@ struct VoxParams {
     const float *roi_x0, *roi_y0;
     float *grid;
     double *oor;
+    // optional: the point cloud of the showers, hit i of shower s at
+    // hits_out[offsets[s] + i - hits_base], written in the same pass
+    float4 *hits_out;
+    const int64_t *offsets;
+    int64_t hits_base;
 };
 
 cudaError_t launch_voxelize(const VoxParams &p, cudaStream_t st);

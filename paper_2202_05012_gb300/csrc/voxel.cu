@@ -1,5 +1,6 @@
 // voxel.cu -- downsampling of the point clouds onto the uniform per-layer
-// grid (App. A.5 "Downsampling").
+// grid (App. A.5 "Downsampling"), optionally writing the point clouds out in
+// shower order in the same pass over the hits.
 #include <algorithm>
 
 #include "hits.cuh"
@@ -130,9 +131,11 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
         const bool listed = count <= p.list_cap;
         if (count > 0) {
             int64_t base = 0;
+            float4 *const out = p.hits_out ? p.hits_out + (p.offsets[s] - p.hits_base) : nullptr;
             do {
                 for (int j = threadIdx.x; j < it.seg_len; j += blockDim.x) {
                     const float4 h = __ldg(it.seg_ptr + j);
+                    if (out) out[base + j] = h;  // the point cloud, in shower order
                     bool dead;
                     const unsigned key = hit_key(h, g, p.s2l, roi_x, roi_y, p, dead);
                     if (key == kNoCell) oor += (double)h.w;

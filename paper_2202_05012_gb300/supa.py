@@ -30,7 +30,7 @@ EXPORTED = (
     "supa_surrogate_destroy", "supa_surrogate_get_params", "supa_surrogate_gradients", "supa_surrogate_train_step",
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
     "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc", "supa_export_diverted",
-    "supa_shower_shapes", "supa_layer_images_cells", "supa_voxelize_layers",
+    "supa_shower_shapes", "supa_layer_images_cells", "supa_voxelize_layers", "supa_voxelize_fetch",
 )
 
 
@@ -107,6 +107,7 @@ def lib(build_if_missing: bool = True):
         L.supa_fetch_hits.argtypes = [_VP, _I64, _I64, _VP, ctypes.c_int32, ctypes.POINTER(_I64), _VP]
         L.supa_fetch_hit_tags.argtypes = [_VP, _I64, _I64, _VP, ctypes.POINTER(_I64), _VP]
         L.supa_voxelize.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP]
+        L.supa_voxelize_fetch.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP, _I64, _VP]
         L.supa_voxelize_hits.argtypes = [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]
         L.supa_autotune.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, _VP, _I64, ctypes.c_uint64,
                                     ctypes.POINTER(supa_launch_config), ctypes.POINTER(ctypes.c_double), _VP]
@@ -259,6 +260,14 @@ def supa_fetch_hit_tags(b: int, first_hit: int, max_hits: int, dst_dev, stream=N
 def supa_voxelize(b: int, shower_begin: int, shower_end: int, grid_dev, out_of_roi_dev=None, stream=None):
     _check(lib().supa_voxelize(b, int(shower_begin), int(shower_end), _ptr(grid_dev), _ptr(out_of_roi_dev),
                                _stream(stream)), "supa_voxelize")
+
+
+def supa_voxelize_fetch(b: int, shower_begin: int, shower_end: int, grid_dev, out_of_roi_dev, hits_dev,
+                        hits_base: int = 0, stream=None):
+    """Images and point cloud of showers [shower_begin, shower_end) in one pass;
+    hit i of shower s lands in row offsets[s] + i - hits_base of hits_dev."""
+    _check(lib().supa_voxelize_fetch(b, int(shower_begin), int(shower_end), _ptr(grid_dev), _ptr(out_of_roi_dev),
+                                     _ptr(hits_dev), int(hits_base), _stream(stream)), "supa_voxelize_fetch")
 
 
 def supa_voxelize_hits(g: int, hits_dev, offsets_dev, n_showers: int, roi_x0_dev, roi_y0_dev, grid_dev,

@@ -142,3 +142,57 @@ def test_voxelize_rejects_bad_ranges():
     finally:
         S.supa_destroy_batch(b)
         S.supa_destroy_geometry(gh)
+
+
+@pytest.mark.parametrize("hybrid", [False, True])
+def test_voxelize_fetch_equals_voxelize_then_fetch(hybrid):
+    """One pass for images and point cloud gives what supa_voxelize followed by
+    supa_fetch_hits gives (the point cloud bit for bit), also in chunks with a
+    hit offset and with the surrogate's hits after the stepped ones."""
+    import torch
+    g = inputs.supa_d(20, grid=32, roi_mode=inputs.ROI_AXIS)
+    n = 3000
+    p = inputs.primaries(n, 17, e_lo=1.0, e_hi=60.0, theta_max_deg=25.0, entry_halfwidth=0.5)
+    gh = S.supa_init_geometry(g)
+    sur = S.supa_surrogate_create(1024, S.pack_mlp_params(inputs.mlp_init(3))) if hybrid else None
+    b = S.supa_batch_create([gh], n, {})
+    try:
+        if hybrid:
+            S.supa_batch_set_surrogate(b, sur, 1.0, 2_000_000, S.SUPA_SURROGATE_MEAN)
+        S.supa_simulate(b, S.primaries_to_device(p), n, 8)
+        info = S.supa_batch_get_info(b)
+        if hybrid:
+            assert info.n_diverted > 0
+        nh = info.n_hits
+        off = S.info_arrays(info)["offsets"].cpu().numpy()
+        L = info.max_layers
+        ref_img = torch.empty((n, L, 32, 32), device="cuda")
+        ref_oor = torch.empty(n, dtype=torch.float64, device="cuda")
+        S.supa_voxelize(b, 0, n, ref_img, ref_oor)
+        ref_hits = torch.empty((nh, 4), device="cuda")
+        assert S.supa_fetch_hits(b, 0, nh, ref_hits) == nh
+        img = torch.full((n, L, 32, 32), float("nan"), device="cuda")
+        oor = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        hits = torch.full((nh, 4), float("nan"), device="cuda")
+        S.supa_voxelize_fetch(b, 0, n, img, oor, hits)
+        torch.cuda.synchronize()
+        assert torch.equal(hits, ref_hits) and torch.equal(oor, ref_oor)
+        # cells sum in shared-memory float atomics: the order of the additions,
+        # and so the last bits, may differ from run to run
+        torch.testing.assert_close(img, ref_img, rtol=1e-5, atol=1e-6)
+        # two chunks into their own buffers, each indexed from its first hit
+        c = 1234
+        for s0, s1 in ((0, c), (c, n)):
+            m = int(off[s1] - off[s0])
+            part = torch.full((max(m, 1), 4), float("nan"), device="cuda")
+            S.supa_voxelize_fetch(b, s0, s1, img[s0:s1], oor[s0:s1], part, int(off[s0]))
+            torch.cuda.synchronize()
+            assert torch.equal(part[:m], ref_hits[off[s0]:off[s1]])
+        torch.testing.assert_close(img, ref_img, rtol=1e-5, atol=1e-6)
+        with pytest.raises(S.SupaError):
+            S.supa_voxelize_fetch(b, 0, n, img, oor, hits[:, 1:], 0)  # not 16-byte aligned
+    finally:
+        S.supa_destroy_batch(b)
+        if sur is not None:
+            S.supa_surrogate_destroy(sur)
+        S.supa_destroy_geometry(gh)
