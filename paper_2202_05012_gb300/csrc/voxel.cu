@@ -28,18 +28,26 @@ __device__ __forceinline__ double block_sum_double(double v, double *red) {
 // cells; each cell sums the energy of the points inside it).  Each CTA takes
 // whole showers in turn:
 //  1. one pass over the shower's hits computes each hit's layer and cell
-//     (float32, half-open cells) into a list in shared memory;
-//  2. for each group of G consecutive layers: zero an image buffer in shared
-//     memory, add the listed energies with shared-memory atomics, then copy
-//     the finished images to HBM with one bulk asynchronous copy
+//     (float32, half-open cells), sums the out-of-region energy and counts
+//     the hits per layer (the bucket sizes of a counting sort by layer);
+//  2. the layers are taken in windows of image groups whose hits fit a list
+//     in shared memory: a second read of the hits (L2-resident by now)
+//     scatters the window's (cell, energy) pairs into the list by layer --
+//     except for images of at most kScanGroups groups whose shower fits the
+//     list, where pass 1 writes the list unsorted and every group scans it;
+//  3. for each group of G consecutive layers: zero an image buffer in shared
+//     memory, add its own bucket of energies with shared-memory atomics,
+//     then copy the finished images to HBM with one bulk asynchronous copy
 //     (cp.async.bulk, TMA engine).  Two buffers alternate, so binning of one
 //     group overlaps the store of the previous one.
 // The images of consecutive layers of a shower are contiguous in the
-// [shower][layer][ny][nx] layout, so a group is one contiguous store.
-// Showers with more hits than the list holds re-read their hits per group.
+// [shower][layer][ny][nx] layout, so a group is one contiguous store.  A
+// single group with more hits than the list holds bins straight from the
+// hits.
 namespace {
 constexpr unsigned kNoCell = 0xFFFFFFFFu;
 constexpr int kTouchCap = 2048;  // touched cells remembered per image buffer
+constexpr int kScanGroups = 16;  // up to this many image groups a group scans the whole hit list
 
 // Add E to an image cell; the first deposit into a cell records it so that
 // the buffer can be reset cell by cell after its store.
@@ -79,6 +87,7 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
     __shared__ float roi_x[SUPA_MAX_LAYERS], roi_y[SUPA_MAX_LAYERS];
     __shared__ double red[32];
     __shared__ int touched_n[2];
+    __shared__ int lcount[SUPA_MAX_LAYERS], lstart[SUPA_MAX_LAYERS + 1], cursor[SUPA_MAX_LAYERS];
     const int cells = p.nx * p.ny;
     const int tile_floats = p.G * cells;
     float *const tile0 = reinterpret_cast<float *>(vsm);
@@ -96,6 +105,7 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
         float4 *t4 = reinterpret_cast<float4 *>(tile0);
         for (int i = threadIdx.x; i < 2 * tile_floats / 4; i += blockDim.x) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (threadIdx.x < 2) touched_n[threadIdx.x] = 0;
+        for (int l = threadIdx.x; l < SUPA_MAX_LAYERS; l += blockDim.x) lcount[l] = 0;
     }
 
     for (int64_t item = blockIdx.x; item < p.n_showers; item += gridDim.x) {
@@ -123,12 +133,15 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
         }
         __syncthreads();
 
-        // 1. classify every hit once
+        // 1. classify every hit once: out-of-region energy, per-layer counts
+        //    (and, in supa_voxelize_fetch, the point cloud)
         double oor = 0.0;
         ShowerHits it;
         it.init(p.src, s);
         const int64_t count = it.remaining;
-        const bool listed = count <= p.list_cap;
+        // few image groups and a list that holds every hit: each group scans
+        // the whole (unsorted) list; otherwise the counting sort by layer
+        const bool scan_all = count <= p.list_cap && p.n_groups <= kScanGroups;
         if (count > 0) {
             int64_t base = 0;
             float4 *const out = p.hits_out ? p.hits_out + (p.offsets[s] - p.hits_base) : nullptr;
@@ -138,60 +151,112 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
                     if (out) out[base + j] = h;  // the point cloud, in shower order
                     bool dead;
                     const unsigned key = hit_key(h, g, p.s2l, roi_x, roi_y, p, dead);
-                    if (key == kNoCell) oor += (double)h.w;
-                    if (listed) list[base + j] = make_uint2(key, __float_as_uint(h.w));
+                    if (key == kNoCell)
+                        oor += (double)h.w;
+                    if (scan_all)
+                        list[base + j] = make_uint2(key, __float_as_uint(h.w));
+                    else if (key != kNoCell)
+                        atomicAdd(&lcount[key >> 24], 1);
                 }
                 base += it.seg_len;
             } while (it.next());
         }
         const double tot = block_sum_double(oor, red);
         if (threadIdx.x == 0 && p.oor) p.oor[item] = tot;
-
-        // 2. one image group at a time, double-buffered bulk stores
-        for (int grp = 0; grp < p.n_groups; ++grp) {
-            const int l0 = grp * p.G;
-            const int G = min(p.G, p.L - l0);
-            float *tile = phase ? tile1 : tile0;
-            uint32_t *touched = phase ? touched1 : touched0;
-            // the store issued from this buffer two groups ago must have read it
-            if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
-            __syncthreads();
-            const int nt = touched_n[phase];
-            __syncthreads();
-            if (threadIdx.x == 0) touched_n[phase] = 0;
-            if (nt > kTouchCap) {
-                float4 *t4 = reinterpret_cast<float4 *>(tile);
-                for (int i = threadIdx.x; i < tile_floats / 4; i += blockDim.x) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
-                for (int i = threadIdx.x; i < nt; i += blockDim.x) tile[touched[i]] = 0.0f;
+        if (!scan_all && threadIdx.x == 0) {
+            // bucket starts of the counting sort by layer
+            int a = 0;
+            for (int l = 0; l < p.L; ++l) {
+                lstart[l] = a;
+                cursor[l] = a;
+                a += lcount[l];
+                lcount[l] = 0;
             }
-            __syncthreads();
-            if (listed) {
-                for (int j = threadIdx.x; j < count; j += blockDim.x) {
-                    const uint2 e = list[j];
-                    const int li = (int)(e.x >> 24) - l0;
-                    if (e.x != kNoCell && li >= 0 && li < G)
-                        deposit(tile, touched, &touched_n[phase], li * cells + (int)(e.x & 0xFFFFFFu),
-                                __uint_as_float(e.y));
-                }
-            } else if (count > 0) {
-                ShowerHits it2;
-                it2.init(p.src, s);
+            lstart[p.L] = a;
+        }
+        __syncthreads();
+
+        // 2. windows of consecutive image groups whose hits fit the list:
+        //    the window's hits are sorted into it by layer (a second read of
+        //    the shower's hits, from L2), then each group deposits only its
+        //    own bucket -- one image group at a time, double-buffered bulk
+        //    stores.  A single group with more hits than the list holds
+        //    deposits straight from the hits.
+        for (int gb = 0; gb < p.n_groups;) {
+            const int lb = gb * p.G;
+            int ge = scan_all ? p.n_groups : gb + 1;
+            while (ge < p.n_groups && lstart[min(p.L, (ge + 1) * p.G)] - lstart[lb] <= p.list_cap) ++ge;
+            const bool fits = scan_all || lstart[min(p.L, ge * p.G)] - lstart[lb] <= p.list_cap;
+            const int le = min(p.L, ge * p.G);
+            if (!scan_all && fits && lstart[le] > lstart[lb]) {
+                ShowerHits it1;
+                it1.init(p.src, s);
                 do {
-                    for (int j = threadIdx.x; j < it2.seg_len; j += blockDim.x) {
-                        const float4 h = __ldg(it2.seg_ptr + j);
+                    for (int j = threadIdx.x; j < it1.seg_len; j += blockDim.x) {
+                        const float4 h = __ldg(it1.seg_ptr + j);
                         bool dead;
                         const unsigned key = hit_key(h, g, p.s2l, roi_x, roi_y, p, dead);
-                        const int li = (int)(key >> 24) - l0;
-                        if (key != kNoCell && li >= 0 && li < G)
-                            deposit(tile, touched, &touched_n[phase], li * cells + (int)(key & 0xFFFFFFu), h.w);
+                        const int l = (int)(key >> 24);
+                        if (key != kNoCell && l >= lb && l < le)
+                            list[atomicAdd(&cursor[l], 1) - lstart[lb]] = make_uint2(key, __float_as_uint(h.w));
                     }
-                } while (it2.next());
+                } while (it1.next());
+                __syncthreads();
             }
-            __syncthreads();
-            if (threadIdx.x == 0)
-                bulk_store(p.grid + ((size_t)item * p.L + l0) * cells, tile, (unsigned)(G * cells) * 4u);
-            phase ^= 1;
+            for (int grp = gb; grp < ge; ++grp) {
+                const int l0 = grp * p.G;
+                const int G = min(p.G, p.L - l0);
+                float *tile = phase ? tile1 : tile0;
+                uint32_t *touched = phase ? touched1 : touched0;
+                // the store issued from this buffer two groups ago must have read it
+                if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                __syncthreads();
+                const int nt = touched_n[phase];
+                __syncthreads();
+                if (threadIdx.x == 0) touched_n[phase] = 0;
+                if (nt > kTouchCap) {
+                    float4 *t4 = reinterpret_cast<float4 *>(tile);
+                    for (int i = threadIdx.x; i < tile_floats / 4; i += blockDim.x)
+                        t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    for (int i = threadIdx.x; i < nt; i += blockDim.x) tile[touched[i]] = 0.0f;
+                }
+                __syncthreads();
+                if (scan_all) {
+                    for (int j = threadIdx.x; j < count; j += blockDim.x) {
+                        const uint2 e = list[j];
+                        const int li = (int)(e.x >> 24) - l0;
+                        if (e.x != kNoCell && li >= 0 && li < G)
+                            deposit(tile, touched, &touched_n[phase], li * cells + (int)(e.x & 0xFFFFFFu),
+                                    __uint_as_float(e.y));
+                    }
+                } else if (fits) {
+                    const int j1 = lstart[l0 + G] - lstart[lb];
+                    for (int j = lstart[l0] - lstart[lb] + threadIdx.x; j < j1; j += blockDim.x) {
+                        const uint2 e = list[j];
+                        deposit(tile, touched, &touched_n[phase], ((int)(e.x >> 24) - l0) * cells + (int)(e.x & 0xFFFFFFu),
+                                __uint_as_float(e.y));
+                    }
+                } else if (count > 0) {
+                    ShowerHits it2;
+                    it2.init(p.src, s);
+                    do {
+                        for (int j = threadIdx.x; j < it2.seg_len; j += blockDim.x) {
+                            const float4 h = __ldg(it2.seg_ptr + j);
+                            bool dead;
+                            const unsigned key = hit_key(h, g, p.s2l, roi_x, roi_y, p, dead);
+                            const int li = (int)(key >> 24) - l0;
+                            if (key != kNoCell && li >= 0 && li < G)
+                                deposit(tile, touched, &touched_n[phase], li * cells + (int)(key & 0xFFFFFFu), h.w);
+                        }
+                    } while (it2.next());
+                }
+                __syncthreads();
+                if (threadIdx.x == 0)
+                    bulk_store(p.grid + ((size_t)item * p.L + l0) * cells, tile, (unsigned)(G * cells) * 4u);
+                phase ^= 1;
+            }
+            gb = ge;
         }
     }
     // all bulk stores complete (written) before the CTA retires

@@ -196,3 +196,43 @@ def test_voxelize_fetch_equals_voxelize_then_fetch(hybrid):
         if sur is not None:
             S.supa_surrogate_destroy(sur)
         S.supa_destroy_geometry(gh)
+
+
+def test_voxelize_windows_and_oversized_layer_groups():
+    """Showers whose hits overflow the shared-memory list: layers taken in
+    several windows, a layer group with more hits than the list holds binned
+    straight from the hits, an empty shower -- all against the oracle."""
+    import torch
+    g = inputs.supa_d(6, grid=128, roi_mode=inputs.ROI_FIXED)  # 64 KB per layer: one layer per group
+    rng = np.random.Generator(np.random.PCG64(21))
+
+    def shower(n_hits, slices):
+        x = rng.normal(0, 3.0, n_hits).astype(np.float32)
+        y = rng.normal(0, 3.0, n_hits).astype(np.float32)
+        z = (rng.choice(slices, n_hits) * g.dz).astype(np.float32)
+        E = rng.exponential(1.0, n_hits).astype(np.float32)
+        return np.stack([x, y, z, E], 1)
+
+    parts = [shower(30000, np.arange(g.n_slices)),                 # ~5,000 per layer: one window per layer
+             np.concatenate([shower(12000, [3, 4, 5]), shower(300, np.arange(g.n_slices))]),  # one layer > list
+             np.zeros((0, 4), np.float32),
+             shower(100, np.arange(g.n_slices))]
+    hits = np.concatenate(parts)
+    off = np.concatenate([[0], np.cumsum([len(q) for q in parts])]).astype(np.int64)
+    n = len(parts)
+    prims = inputs.primaries(n, 5, e_lo=1, e_hi=1)
+    rx, ry = oracle.roi_origins(g, prims)
+    grid_o, oor_o = oracle.voxelize(hits[:, 0], hits[:, 1], hits[:, 2], hits[:, 3], off, g, rx, ry)
+    gh = S.supa_init_geometry(g)
+    try:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        out = torch.full((n, g.n_layers, g.ny, g.nx), -1.0, dtype=torch.float32, device="cuda")
+        oor = torch.zeros(n, dtype=torch.float64, device="cuda")
+        S.supa_voxelize_hits(gh, dev(hits), dev(off), n, dev(rx), dev(ry), out, oor)
+        grid_g = out.cpu().numpy().astype(np.float64)
+        assert np.array_equal(grid_g != 0, grid_o != 0)
+        np.testing.assert_allclose(grid_g, grid_o, rtol=2e-6, atol=1e-6)
+        np.testing.assert_allclose(oor.cpu().numpy(), oor_o, rtol=1e-12, atol=1e-12)
+        assert np.all(grid_g[2] == 0)
+    finally:
+        S.supa_destroy_geometry(gh)
