@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
     extern __shared__ __align__(128) unsigned char vsm[];
     __shared__ float roi_x[SUPA_MAX_LAYERS], roi_y[SUPA_MAX_LAYERS];
     __shared__ double red[32];
-    __shared__ int touched_n[2];
+    // touched-cell counts per image buffer, two per buffer alternating by use:
+    // a use adds to one while the next use still reads the other
+    __shared__ int touched_n[2][2];
     __shared__ int lcount[SUPA_MAX_LAYERS], lstart[SUPA_MAX_LAYERS + 1], cursor[SUPA_MAX_LAYERS];
     const int cells = p.nx * p.ny;
     const int tile_floats = p.G * cells;
@@ -97,14 +99,15 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
     uint2 *list = reinterpret_cast<uint2 *>(touched1 + kTouchCap);
     const float half_x = (float)p.nx * p.wx * 0.5f;
     const float half_y = (float)p.ny * p.wy * 0.5f;
-    int phase = 0;
+    int phase = 0;  // image buffer of the next group
+    int n_use = 0;  // groups binned so far (buffer uses: n_use >> 1 per buffer)
     // Both image buffers start zero and are kept zero between uses: after a
     // buffer's bulk store has been read, only the cells it touched (listed in
     // touched0/1; a full clear if that list overflowed) are reset.
     {
         float4 *t4 = reinterpret_cast<float4 *>(tile0);
         for (int i = threadIdx.x; i < 2 * tile_floats / 4; i += blockDim.x) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (threadIdx.x < 2) touched_n[threadIdx.x] = 0;
+        if (threadIdx.x < 4) touched_n[threadIdx.x >> 1][threadIdx.x & 1] = 0;
         for (int l = threadIdx.x; l < SUPA_MAX_LAYERS; l += blockDim.x) lcount[l] = 0;
     }
 
@@ -208,12 +211,18 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
                 const int G = min(p.G, p.L - l0);
                 float *tile = phase ? tile1 : tile0;
                 uint32_t *touched = phase ? touched1 : touched0;
-                // the store issued from this buffer two groups ago must have read it
-                if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                // this buffer's use number u = n_use >> 1: its deposits count
+                // in touched_n[phase][u & 1]; use u - 1 counted in the other
+                const int cu = (n_use >> 1) & 1;
+                int *const tn = &touched_n[phase][cu];
+                // the store issued from this buffer two groups ago must have
+                // read it; the counter of use u - 2 was read by use u - 1
+                if (threadIdx.x == 0) {
+                    asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                    *tn = 0;
+                }
                 __syncthreads();
-                const int nt = touched_n[phase];
-                __syncthreads();
-                if (threadIdx.x == 0) touched_n[phase] = 0;
+                const int nt = touched_n[phase][cu ^ 1];
                 if (nt > kTouchCap) {
                     float4 *t4 = reinterpret_cast<float4 *>(tile);
                     for (int i = threadIdx.x; i < tile_floats / 4; i += blockDim.x)
@@ -227,14 +236,14 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
                         const uint2 e = list[j];
                         const int li = (int)(e.x >> 24) - l0;
                         if (e.x != kNoCell && li >= 0 && li < G)
-                            deposit(tile, touched, &touched_n[phase], li * cells + (int)(e.x & 0xFFFFFFu),
+                            deposit(tile, touched, tn, li * cells + (int)(e.x & 0xFFFFFFu),
                                     __uint_as_float(e.y));
                     }
                 } else if (fits) {
                     const int j1 = lstart[l0 + G] - lstart[lb];
                     for (int j = lstart[l0] - lstart[lb] + threadIdx.x; j < j1; j += blockDim.x) {
                         const uint2 e = list[j];
-                        deposit(tile, touched, &touched_n[phase], ((int)(e.x >> 24) - l0) * cells + (int)(e.x & 0xFFFFFFu),
+                        deposit(tile, touched, tn, ((int)(e.x >> 24) - l0) * cells + (int)(e.x & 0xFFFFFFu),
                                 __uint_as_float(e.y));
                     }
                 } else if (count > 0) {
@@ -247,7 +256,7 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
                             const unsigned key = hit_key(h, g, p.s2l, roi_x, roi_y, p, dead);
                             const int li = (int)(key >> 24) - l0;
                             if (key != kNoCell && li >= 0 && li < G)
-                                deposit(tile, touched, &touched_n[phase], li * cells + (int)(key & 0xFFFFFFu), h.w);
+                                deposit(tile, touched, tn, li * cells + (int)(key & 0xFFFFFFu), h.w);
                         }
                     } while (it2.next());
                 }
@@ -255,6 +264,7 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
                 if (threadIdx.x == 0)
                     bulk_store(p.grid + ((size_t)item * p.L + l0) * cells, tile, (unsigned)(G * cells) * 4u);
                 phase ^= 1;
+                ++n_use;
             }
             gb = ge;
         }
