@@ -695,8 +695,8 @@ def hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor
 
 
 def run_surrogate(args):
-    """Surrogate training at the C4 sizes (10M plain-method sub-showers below
-    E_s, 20 epochs) and the hybrid run of C5 (50 layers, E log-uniform
+    """Surrogate training (10M plain-method sub-showers below E_s, 20 epochs)
+    and the hybrid run of the 50-layer workload (50 layers, E log-uniform
     [10,1000], 0-45 deg) against the plain run on the same seeds, for a sweep
     of E_s: showers/s (simulate only; images excluded to keep the sweep
     short) and profile errors."""
@@ -736,7 +736,7 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     plain_prof = (lo.cpu().numpy() / n5, la.cpu().numpy() / n5)
     S.supa_destroy_batch(pb)
-    out = {"metric": METRIC, "workload": "surrogate training (C4 sizes) + hybrid C5 vs plain, E_s sweep",
+    out = {"metric": METRIC, "workload": "surrogate training (10M samples x 20 epochs) + hybrid 50-layer showers vs plain, E_s sweep",
            "c5_showers": n5, "plain": {"simulate_showers_per_s": n5 / (plain_ms / 1000.0),
                                        "particle_steps_per_shower": plain_steps / n5}, "sweep": []}
     for e_s in args.e_s_sweep:
@@ -969,7 +969,7 @@ def run_c3(args):
 
 
 def run_hybrid(args):
-    """Hybrid simulation alone (C5 showers, stepping above E_s, the network
+    """Hybrid simulation alone (50-layer showers, stepping above E_s, the network
     and its deposits and hits below it; no images), W warm-up and K timed
     supa_simulate calls: the short workload the hybrid kernels are profiled
     on."""
@@ -1011,7 +1011,7 @@ def run_hybrid(args):
     S.supa_surrogate_destroy(net)
     t = float(np.mean(ms))
     print(json.dumps({"metric": "hybrid showers/s (simulate only)", "value": n / (t / 1000.0), "unit": "showers/s",
-                      "workload": f"C5 showers x {n}, E_s = {args.e_s} GeV, MEAN mode", "ms_per_call": ms,
+                      "workload": f"50-layer showers (E log-U[10,1000], 0-45 deg) x {n}, E_s = {args.e_s} GeV, MEAN mode", "ms_per_call": ms,
                       "diverted_per_shower": info.n_diverted / n, "particle_steps_per_shower": info.n_steps / n,
                       "training": {k: v for k, v in tlog.items() if k != "loss_per_epoch"}}), flush=True)
 

@@ -15,7 +15,8 @@
 //    stores once flush_thr are staged.  Direct: the stopping lanes of one
 //    iteration write consecutive 16-byte slots straight from registers, so a
 //    warp's stores of one iteration are contiguous and L2 merges them into
-//    full sectors (on C2 about 1.5 % faster: no shared-memory round trip).
+//    full sectors (about 1.5 % faster on 90-slice showers of 1-100 GeV: no
+//    shared-memory round trip).
 //  * Deposits are summed exactly in 64-bit fixed point (units of 2^-32) in
 //    shared memory -- per layer, and dead / leaked / escaped energy -- with
 //    32-bit shared-memory atomics on the integer pipe (GB300's FP64 rate is a

@@ -45,8 +45,8 @@ def test_c1_workload_parity():
 
 
 def test_error_report_c2_shapes():
-    """The error of each output against the FP64 oracle on C2-shaped showers
-    (printed as one JSON line; the asserts are the stated tolerances)."""
+    """The error of each output against the FP64 oracle on showers shaped
+    like the 30-layer workload (E U[1,100] GeV, 0-30 deg; printed as one JSON line; the asserts are the stated tolerances)."""
     import json
 
     import torch

@@ -1,5 +1,6 @@
 """GPU parity of the shower shape variables (Sec. 5.1, App. A.1) against the
-FP64 oracle on C2-shaped showers, and their consistency on the hybrid path
+FP64 oracle on showers shaped like the 30-layer workload (E U[1,100] GeV,
+0-30 deg), and their consistency on the hybrid path
 (stepped and surrogate points)."""
 import numpy as np
 import pytest

@@ -1,5 +1,5 @@
-"""What the trained surrogate gains over the method without it, on the C2
-workload at E_s = 2 GeV: the hybrid path steps a small fraction of the
+"""What the trained surrogate gains over the method without it, on the
+30-layer workload (E U[1,100] GeV, 0-30 deg) at E_s = 2 GeV: the hybrid path steps a small fraction of the
 particles the plain path steps, and its shower profiles stay within a few
 per cent of the plain ones -- which an untrained network of the same shape
 does not achieve."""
