@@ -137,9 +137,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 float v[32];
                 tmem_ld32(lane_addr + c0, v);
                 if (g.epi == EPI_ATOMIC_F32) {
-                    if (live)
+                    // split-K partial products: vector reductions of 4 floats
+                    if (live) {
+                        float *o = g.out_f32 + (size_t)row * g.ld + c0;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) atomicAdd(&g.out_f32[(size_t)row * g.ld + c0 + j], v[j]);
+                        for (int j = 0; j < 8; ++j)
+                            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(o + 4 * j),
+                                         "f"(v[4 * j]), "f"(v[4 * j + 1]), "f"(v[4 * j + 2]), "f"(v[4 * j + 3])
+                                         : "memory");
+                    }
                 } else if (g.epi == EPI_BIAS_F32) {
                     if (live) {
                         float4 *o = reinterpret_cast<float4 *>(g.out_f32 + (size_t)row * g.ld + c0);
@@ -173,9 +179,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     }
                 } else if (g.epi == EPI_GELU_BWD) {
                     float d[32];
+                    if (live) {
+                        const float4 *zi = reinterpret_cast<const float4 *>(g.z_in + (size_t)row * g.ld + c0);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        d[j] = live ? v[j] * gelu_grad(g.z_in[(size_t)row * g.ld + c0 + j]) : 0.0f;
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 z = zi[j];
+                            d[4 * j] = v[4 * j] * gelu_grad(z.x);
+                            d[4 * j + 1] = v[4 * j + 1] * gelu_grad(z.y);
+                            d[4 * j + 2] = v[4 * j + 2] * gelu_grad(z.z);
+                            d[4 * j + 3] = v[4 * j + 3] * gelu_grad(z.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) d[j] = 0.0f;
+                    }
                     if (live) {
                         uint4 *o = reinterpret_cast<uint4 *>(g.out_bf16 + (size_t)row * g.ld + c0);
 #pragma unroll
@@ -187,14 +204,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         for (int j = 0; j < 32; ++j)
                             g.outT_bf16[(size_t)(c0 + j) * g.ldT + row] = __float2bfloat16_rn(d[j]);
                     }
-                    // column sums over the 32 rows of this warp (bias gradient)
+                    // column sums over the 32 rows of this warp (bias gradient):
+                    // a butterfly that halves the columns a lane keeps at every
+                    // step, so lane j ends with the sum of column j
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        float s = d[j];
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const bool upper = (lane & o) != 0;
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-                        if (lane == 0) atomicAdd(&g.colsum[c0 + j], s);
+                        for (int i = 0; i < o; ++i) {
+                            const float give = upper ? d[i] : d[i + o];
+                            const float keep = upper ? d[i + o] : d[i];
+                            d[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, give, o);
+                        }
                     }
+                    atomicAdd(&g.colsum[c0 + lane], d[0]);
                 }
             }
             // hand the accumulator back to the MMA issuer
