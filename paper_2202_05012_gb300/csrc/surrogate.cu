@@ -76,19 +76,25 @@ __global__ void pack_inputs(const float *x, int64_t n, const unsigned *n_dev, in
 
 // The loss L over the 30 layers, mean over the batch: writes d L / d out
 // (bf16, both orientations; padding columns zero), adds the bias gradient of
-// the last layer and the loss sum.
-__global__ void nll_loss(const float *out, const float *y, int B, __nv_bfloat16 *G4, __nv_bfloat16 *G4T, float *gb4,
-                         double *loss_sum) {
+// the last layer and the loss sum.  A block takes 32 rows; thread (x, y)
+// handles row x of them for layers y, y + 8, ...: a warp covers 32
+// consecutive rows of one layer, so the transposed gradient is written
+// coalesced and the bias gradient is a warp sum.
+constexpr int kLossRows = 32, kLossLanesY = 8;
+
+__global__ void __launch_bounds__(kLossRows * kLossLanesY)
+    nll_loss(const float *out, const float *y, int B, __nv_bfloat16 *G4, __nv_bfloat16 *G4T, float *gb4,
+             double *loss_sum) {
     __shared__ float colsum[kOutPad];
-    __shared__ double red[32];
-    for (int j = threadIdx.x; j < kOutPad; j += blockDim.x) colsum[j] = 0.0f;
+    __shared__ double red[kLossLanesY];
+    const int tid = threadIdx.y * kLossRows + threadIdx.x;
+    for (int j = tid; j < kOutPad; j += kLossRows * kLossLanesY) colsum[j] = 0.0f;
     __syncthreads();
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.x * kLossRows + threadIdx.x;
     const bool live = r < B;
-    const unsigned lane = threadIdx.x & 31;
     double l = 0.0;
     const float inv = 1.0f / (float)(B * kLayersOut);
-    for (int j = 0; j < kLayersOut; ++j) {
+    for (int j = threadIdx.y; j < kLayersOut; j += kLossLanesY) {
         float gmu = 0.0f, gs = 0.0f, gr = 0.0f;
         if (live) {
             const float *o = out + (size_t)r * kOutPad;
@@ -108,30 +114,31 @@ __global__ void nll_loss(const float *out, const float *y, int B, __nv_bfloat16 
             G4T[(size_t)(kLayersOut + j) * B + r] = __float2bfloat16_rn(gs);
             G4T[(size_t)(2 * kLayersOut + j) * B + r] = __float2bfloat16_rn(gr);
         }
-        // bias gradient: column sums, one shared atomic per warp and column
+        // bias gradient: column sums over the warp's 32 rows
         for (int o = 16; o > 0; o >>= 1) {
             gmu += __shfl_xor_sync(0xFFFFFFFFu, gmu, o);
             gs += __shfl_xor_sync(0xFFFFFFFFu, gs, o);
             gr += __shfl_xor_sync(0xFFFFFFFFu, gr, o);
         }
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             atomicAdd(&colsum[j], gmu);
             atomicAdd(&colsum[kLayersOut + j], gs);
             atomicAdd(&colsum[2 * kLayersOut + j], gr);
         }
     }
     if (live)
-        for (int j = kOut; j < kOutPad; ++j) G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(0.0f);
+        for (int j = kOut + threadIdx.y; j < kOutPad; j += kLossLanesY)
+            G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(0.0f);
     // (rows kOut.. of G4T are zero from creation and never written)
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    if (threadIdx.x == 0) red[threadIdx.y] = l;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         double t = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        for (int i = 0; i < kLossLanesY; ++i) t += red[i];
         atomicAdd(loss_sum, t / (double)(B * kLayersOut));
     }
-    for (int j = threadIdx.x; j < kOut; j += blockDim.x) atomicAdd(&gb4[j], colsum[j]);
+    for (int j = tid; j < kOut; j += kLossRows * kLossLanesY) atomicAdd(&gb4[j], colsum[j]);
 }
 
 // Adam with bias correction (c1 = 1 - beta1^t, c2 = 1 - beta2^t).
@@ -260,7 +267,8 @@ cudaError_t backward(supa_surrogate *s, const float *y, cudaStream_t st) {
     const int B = s->B;
     cudaError_t e = cudaMemsetAsync(s->grad, 0, Off::total * sizeof(float), st);
     if (e != cudaSuccess) return e;
-    nll_loss<<<(B + 255) / 256, 256, 0, st>>>(s->OUT, y, B, s->G4, s->G4T, s->grad + Off::b4, s->loss_tmp);
+    nll_loss<<<(B + kLossRows - 1) / kLossRows, dim3(kLossRows, kLossLanesY), 0, st>>>(s->OUT, y, B, s->G4, s->G4T,
+                                                                                s->grad + Off::b4, s->loss_tmp);
     // layer 4
     GemmArgs a = gargs(kOutPad, kHid, B, EPI_ATOMIC_F32, s->error);
     a.out_f32 = s->grad + Off::W4; a.ld = kHid;
