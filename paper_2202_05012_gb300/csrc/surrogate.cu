@@ -76,40 +76,50 @@ __global__ void pack_inputs(const float *x, int64_t n, const unsigned *n_dev, in
 
 // The loss L over the 30 layers, mean over the batch: writes d L / d out
 // (bf16, both orientations; padding columns zero), adds the bias gradient of
-// the last layer and the loss sum.  A block takes 32 rows; thread (x, y)
-// handles row x of them for layers y, y + 8, ...: a warp covers 32
+// the last layer and the loss sum.  A block takes 32 rows: their outputs
+// and targets are staged in shared memory with coalesced loads, thread
+// (x, y) handles row x for layers y, y + 8, ... (a warp covers 32
 // consecutive rows of one layer, so the transposed gradient is written
-// coalesced and the bias gradient is a warp sum.
+// coalesced and the bias gradient is a warp sum), and the gradient rows
+// leave through shared memory as whole rows.
 constexpr int kLossRows = 32, kLossLanesY = 8;
 
 __global__ void __launch_bounds__(kLossRows * kLossLanesY)
     nll_loss(const float *out, const float *y, int B, __nv_bfloat16 *G4, __nv_bfloat16 *G4T, float *gb4,
              double *loss_sum) {
+    constexpr int kThreads = kLossRows * kLossLanesY;
     __shared__ float colsum[kOutPad];
     __shared__ double red[kLossLanesY];
+    __shared__ float so[kLossRows][kOut + 1];
+    __shared__ float sy[kLossRows][kY + 1];
+    __shared__ __align__(16) __nv_bfloat16 sg[kLossRows][kOutPad + 8];
     const int tid = threadIdx.y * kLossRows + threadIdx.x;
-    for (int j = tid; j < kOutPad; j += kLossRows * kLossLanesY) colsum[j] = 0.0f;
+    const int r0 = blockIdx.x * kLossRows;
+    const int rows = min(kLossRows, B - r0);
+    for (int j = tid; j < kOutPad; j += kThreads) colsum[j] = 0.0f;
+    for (int i = tid; i < rows * kOut; i += kThreads) so[i / kOut][i % kOut] = out[(size_t)(r0 + i / kOut) * kOutPad + i % kOut];
+    for (int i = tid; i < rows * kY; i += kThreads) sy[i / kY][i % kY] = y[(size_t)r0 * kY + i];
+    for (int i = tid; i < kLossRows * (kOutPad - kOut); i += kThreads)
+        sg[i / (kOutPad - kOut)][kOut + i % (kOutPad - kOut)] = __float2bfloat16_rn(0.0f);
     __syncthreads();
-    const int r = blockIdx.x * kLossRows + threadIdx.x;
-    const bool live = r < B;
+    const int rl = threadIdx.x, r = r0 + rl;
+    const bool live = rl < rows;
     double l = 0.0;
     const float inv = 1.0f / (float)(B * kLayersOut);
     for (int j = threadIdx.y; j < kLayersOut; j += kLossLanesY) {
         float gmu = 0.0f, gs = 0.0f, gr = 0.0f;
         if (live) {
-            const float *o = out + (size_t)r * kOutPad;
-            const float mu = o[j], s = o[kLayersOut + j], rho = o[2 * kLayersOut + j];
-            const float yj = y[(size_t)r * kY + j], dr = rho - y[(size_t)r * kY + kLayersOut + j];
+            const float mu = so[rl][j], s = so[rl][kLayersOut + j], rho = so[rl][2 * kLayersOut + j];
+            const float yj = sy[rl][j], dr = rho - sy[rl][kLayersOut + j];
             const float res = yj - mu;
             const float e = expf(-s);
             l += 0.5 * (double)(res * res * e) + 0.5 * (double)s + 0.5 * (double)(yj * dr * dr);
             gmu = -res * e * inv;
             gs = (0.5f - 0.5f * res * res * e) * inv;
             gr = yj * dr * inv;
-            __nv_bfloat16 *g4 = G4 + (size_t)r * kOutPad;
-            g4[j] = __float2bfloat16_rn(gmu);
-            g4[kLayersOut + j] = __float2bfloat16_rn(gs);
-            g4[2 * kLayersOut + j] = __float2bfloat16_rn(gr);
+            sg[rl][j] = __float2bfloat16_rn(gmu);
+            sg[rl][kLayersOut + j] = __float2bfloat16_rn(gs);
+            sg[rl][2 * kLayersOut + j] = __float2bfloat16_rn(gr);
             G4T[(size_t)j * B + r] = __float2bfloat16_rn(gmu);
             G4T[(size_t)(kLayersOut + j) * B + r] = __float2bfloat16_rn(gs);
             G4T[(size_t)(2 * kLayersOut + j) * B + r] = __float2bfloat16_rn(gr);
@@ -126,19 +136,21 @@ __global__ void __launch_bounds__(kLossRows * kLossLanesY)
             atomicAdd(&colsum[2 * kLayersOut + j], gr);
         }
     }
-    if (live)
-        for (int j = kOut + threadIdx.y; j < kOutPad; j += kLossLanesY)
-            G4[(size_t)r * kOutPad + j] = __float2bfloat16_rn(0.0f);
     // (rows kOut.. of G4T are zero from creation and never written)
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
     if (threadIdx.x == 0) red[threadIdx.y] = l;
     __syncthreads();
+    // gradient rows, 16 bytes at a time
+    for (int i = tid; i < rows * (kOutPad / 8); i += kThreads) {
+        const int rr = i / (kOutPad / 8), c = (i % (kOutPad / 8)) * 8;
+        *reinterpret_cast<uint4 *>(G4 + (size_t)(r0 + rr) * kOutPad + c) = *reinterpret_cast<const uint4 *>(&sg[rr][c]);
+    }
     if (tid == 0) {
         double t = 0.0;
         for (int i = 0; i < kLossLanesY; ++i) t += red[i];
         atomicAdd(loss_sum, t / (double)(B * kLayersOut));
     }
-    for (int j = tid; j < kOut; j += kLossRows * kLossLanesY) atomicAdd(&gb4[j], colsum[j]);
+    for (int j = tid; j < kOut; j += kThreads) atomicAdd(&gb4[j], colsum[j]);
 }
 
 // Adam with bias correction (c1 = 1 - beta1^t, c2 = 1 - beta2^t).
