@@ -166,14 +166,20 @@ __global__ void adam_update(float *p, float *m, float *v, const float *g, size_t
     }
 }
 
-// Rows (a i + c) mod n, i = i0 .. i0 + B - 1, of x [n][6] and y [n][60].
+// Rows (a i + c) mod n, i = i0 .. i0 + B - 1, of x [n][6] and y [n][60]:
+// one thread per value (a row's values are consecutive threads, so a row is
+// read and written coalesced).
 __global__ void gather_rows(const float *x, const float *y, int64_t n, uint64_t a, uint64_t c, int64_t i0, int B,
                             float *xs, float *ys) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= B) return;
+    constexpr int kRow = kIn + kY;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)B * kRow) return;
+    const int r = (int)(t / kRow), j = (int)(t % kRow);
     const uint64_t src = (a * (uint64_t)(i0 + r) + c) % (uint64_t)n;
-    for (int j = 0; j < kIn; ++j) xs[(size_t)r * kIn + j] = x[src * kIn + j];
-    for (int j = 0; j < kY; ++j) ys[(size_t)r * kY + j] = y[src * kY + j];
+    if (j < kIn)
+        xs[(size_t)r * kIn + j] = x[src * kIn + j];
+    else
+        ys[(size_t)r * kY + (j - kIn)] = y[src * kY + (j - kIn)];
 }
 
 // BF16 copies of a master weight [rows][cols]: W and (optionally) W^T.
@@ -544,7 +550,8 @@ int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const floa
     const uint64_t c = (seed ^ 0xD1B54A32D192ED03ull) % (uint64_t)n;
     const int64_t steps = n / s->B;
     for (int64_t k = 0; k < steps; ++k) {
-        gather_rows<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, y_dev, n, a, c, k * s->B, s->B, s->Xs, s->Ys);
+        gather_rows<<<(unsigned)(((int64_t)s->B * (kIn + kY) + 255) / 256), 256, 0, st>>>(x_dev, y_dev, n, a, c, k * s->B,
+                                                                                          s->B, s->Xs, s->Ys);
         const int rc = supa_surrogate_train_step(s, s->Xs, s->Ys, lr, loss_acc_dev, stream);
         if (rc != SUPA_OK) return rc;
     }
