@@ -28,12 +28,12 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Standard normal n_j of a diverted particle, j = lane (0..31): Box-Muller on
-// Philox block j / 4 of its stream (tag 1, keyed by shower, slice and
-// lineage); words 2p and 2p + 1 of a block give the pair (n_{4b+2p},
-// n_{4b+2p+1}) = rad (cos, sin)(2 pi u2), p = (j / 2) mod 2.
-__device__ float lane_normal(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed, int lane) {
-    const int blk = lane >> 2, pr = (lane >> 1) & 1;
+// Standard normal n_j of a diverted particle, j = 0..31 (the layer offset):
+// Box-Muller on Philox block j / 4 of its stream (tag 1, keyed by shower,
+// slice and lineage); words 2p and 2p + 1 of a block give the pair
+// (n_{4b+2p}, n_{4b+2p+1}) = rad (cos, sin)(2 pi u2), p = (j / 2) mod 2.
+__device__ float lane_normal(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed, int j) {
+    const int blk = j >> 2, pr = (j >> 1) & 1;
     const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (1u << 16) | ((uint32_t)blk << 20), lin_lo, lin_hi),
                                   (uint32_t)seed, (uint32_t)(seed >> 32));
     const uint32_t w0 = pr ? r.z : r.x, w1 = pr ? r.w : r.y;
@@ -42,7 +42,7 @@ __device__ float lane_normal(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_
     const float rad = sqrtf(-2.0f * logf(u1));
     float sn, cs;
     sincospif(2.0f * u2, &sn, &cs);
-    return (lane & 1) ? rad * sn : rad * cs;
+    return (j & 1) ? rad * sn : rad * cs;
 }
 
 // The standard normal pair (m1, m2) displacing all hits of a diverted
@@ -61,12 +61,6 @@ __device__ float2 offset_normals(uint32_t sid, int k, uint32_t lin_lo, uint32_t 
     return make_float2(rad * cs, rad * sn);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
 // Contiguous range of queue entries of this warp: consecutive entries mostly
 // belong to one shower (the step kernel queues a warp's diverted particles
 // together), so runs stay whole.
@@ -79,30 +73,37 @@ __device__ __forceinline__ void warp_range(unsigned n, unsigned &i0, unsigned &i
 
 }  // namespace
 
-// Pass 1, one warp per diverted particle (lane j = layer start + j): deposits,
-// hit count per particle, and -- summed over each run of consecutive queue
-// entries of one shower before the atomics -- layer sums, surrogate leakage
-// and hit counts per shower.  Lane L keeps the run's sums of absolute layers
-// L and L + 32, in 64-bit fixed point (integer adds: the FP64 unit of this
-// GPU is far too slow for a double add per deposit), converted to FP64 once
-// per run.  Queue records are read 32 at a time (lane k holds entry g0 + k)
-// and the network outputs of 8 entries are in flight at once.
+constexpr int kDepWarps = 4;
+
+// Pass 1: deposits d_j (j = 0..29, layer start + j), hit count per particle,
+// and per shower the layer sums, surrogate leakage and hit count.  A warp
+// walks a contiguous range of the queue 32 entries at a time.  First one
+// lane per particle: it reads the particle's network outputs as float4 rows,
+// forms its 30 deposits in registers, writes them and stages them in shared
+// memory.  Then one particle at a time, lane L adds the staged deposits of
+// absolute layers L and L + 32 to its run sums -- 64-bit fixed point (units
+// of 2^-32; integer adds: the FP64 unit of this GPU is far too slow for a
+// double add per deposit), summed over each run of consecutive queue
+// entries of one shower (consecutive entries mostly belong to one shower)
+// and converted to FP64 and added to the shower's sums once per run.
 template <bool kSample>
-__global__ void sur_deposits(const SurParams p) {
+__global__ void __launch_bounds__(kDepWarps * 32) sur_deposits(const SurParams p) {
+    __shared__ float s_dep[kDepWarps][32][kSurLayers + 1];
     const unsigned n = min(*p.count, (unsigned)p.cap);
-    const int lane = threadIdx.x & 31;
-    constexpr bool sample = kSample;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float(*stg)[kSurLayers + 1] = s_dep[wib];
     unsigned i0, i1;
     warp_range(n, i0, i1);
     int cur = -1;
     unsigned long long acc_lo = 0, acc_hi = 0;
     long long leak = 0;
     unsigned cnt = 0;
-    auto flush = [&]() {
+    auto flush = [&]() {  // warp-uniform
         if (cur < 0) return;
         double *ls = p.lsum + (size_t)cur * p.lsum_stride;
         if (acc_lo) atomicAdd(&ls[lane], from_fixed32(acc_lo));
         if (acc_hi) atomicAdd(&ls[lane + 32], from_fixed32(acc_hi));
+        // the run's leakage is spread over the lanes
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) leak += __shfl_xor_sync(kFull, leak, o);
         if (lane == 0) {
@@ -114,86 +115,85 @@ __global__ void sur_deposits(const SurParams p) {
         cnt = 0;
     };
     for (unsigned g0 = i0; g0 < i1; g0 += 32) {
+        const unsigned i = g0 + (unsigned)lane;
         const int m = (int)min(32u, i1 - g0);
-        uint32_t r_sh = 0, r_lo = 0, r_hi = 0;
-        int r_k = 0, r_layer = 0, r_nl = 0;
-        float r_E = 0.0f;
+        uint32_t sh = 0;
+        int layer = 0;
+        unsigned pc = 0;
+        long long pleak = 0;
         if (lane < m) {
-            const SurRec r = p.rec[g0 + lane];
-            r_sh = r.shower;
-            r_k = r.k;
-            r_layer = r.layer;
-            r_E = r.E;
-            r_lo = r.lin_lo;
-            r_hi = r.lin_hi;
-            r_nl = p.geoms[p.prim[r.shower].geom & 0xFFFFu].n_layers;
-        }
-        for (int k0 = 0; k0 < m; k0 += 8) {
-            float mu[8], sg[8];
+            const SurRec r = p.rec[i];
+            sh = r.shower;
+            layer = r.layer;
+            const float E = r.E;
+            const int nj = min(kSurLayers, p.geoms[p.prim[r.shower].geom & 0xFFFFu].n_layers - layer);
+            float v[kSurLayers];
+            const float4 *o4 = reinterpret_cast<const float4 *>(p.out + (size_t)i * p.out_ld);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const bool ld = k0 + u < m && lane < kSurLayers;
-                const float *o = p.out + (size_t)(g0 + k0 + u) * p.out_ld;
-                mu[u] = ld ? o[lane] : 0.0f;
-                if (sample) sg[u] = ld ? o[kSurLayers + lane] : 0.0f;
+            for (int q = 0; q < (kSurLayers + 3) / 4; ++q) {
+                const float4 mv = __ldg(o4 + q);
+                const float mq[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (4 * q + t < kSurLayers) v[4 * q + t] = mq[t];
             }
+            float sum = 0.0f, sum_mean = 0.0f;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int k = k0 + u;
-                if (k >= m) break;
-                const int sh = (int)__shfl_sync(kFull, r_sh, k);
-                const int layer = __shfl_sync(kFull, r_layer, k);
-                const int nl = __shfl_sync(kFull, r_nl, k);
-                const float E = __shfl_sync(kFull, r_E, k);
-                if (sh != cur) {
-                    flush();
-                    cur = sh;
-                }
-                int kk = 0;
-                uint32_t lo = 0, hi = 0;
-                if (sample) {
-                    kk = __shfl_sync(kFull, r_k, k);
-                    lo = __shfl_sync(kFull, r_lo, k);
-                    hi = __shfl_sync(kFull, r_hi, k);
-                }
-                float v = 0.0f, vm = 0.0f;
-                if (lane < kSurLayers && layer + lane < nl) {
-                    float f = fmaxf(0.0f, mu[u]);
-                    if (sample) vm = E * f;
-                    if (sample && f > 0.0f) {
+            for (int j = 0; j < kSurLayers; ++j) {
+                float f = j < nj ? fmaxf(0.0f, v[j]) : 0.0f;
+                if (kSample) {
+                    sum_mean += E * f;
+                    if (f > 0.0f) {
                         // log-normal with mean mu and variance exp(s) (a^2 capped at 4)
-                        const float a2 = fminf(4.0f, log1pf(expf(sg[u]) / (f * f)));
-                        const float z =
-                            lane_normal((uint32_t)(p.shower_id_base + (uint32_t)sh), kk, lo, hi, p.seed, lane);
+                        const float sg = __ldg(p.out + (size_t)i * p.out_ld + kSurLayers + j);
+                        const float a2 = fminf(4.0f, log1pf(expf(sg) / (f * f)));
+                        const float z = lane_normal((uint32_t)(p.shower_id_base + sh), r.k, r.lin_lo, r.lin_hi,
+                                                    p.seed, j);
                         f *= expf(fmaf(sqrtf(a2), z, -0.5f * a2));
                     }
-                    v = E * f;
                 }
-                float sum = warp_sum(v);
-                if (sample) {  // the draws keep their shape and take the MEAN total
-                    const float sm = warp_sum(vm);
-                    if (sum > 0.0f) v *= sm / sum;
-                    sum = sm;
-                }
-                if (sum > E) v *= E / sum;
-                const unsigned i = g0 + (unsigned)k;
-                if (lane < kSurLayers) p.dep[(size_t)i * kSurLayers + lane] = v;
-                const unsigned nz = __ballot_sync(kFull, v > 0.0f);
-                const unsigned long long fv = fixed32(v);
-                if (lane == 0) {
-                    p.pcnt[i] = (uint8_t)__popc(nz);
-                    cnt += (unsigned)__popc(nz);
-                    leak += (long long)fixed32(E);
-                }
-                leak -= (long long)fv;
-                // deposit of absolute layer a comes from lane a - layer
-                const int src_lo = lane - layer, src_hi = lane + 32 - layer;
-                const unsigned long long w_lo = __shfl_sync(kFull, fv, src_lo & 31),
-                                         w_hi = __shfl_sync(kFull, fv, src_hi & 31);
-                if (src_lo >= 0 && src_lo < kSurLayers) acc_lo += w_lo;
-                if (src_hi >= 0 && src_hi < kSurLayers) acc_hi += w_hi;
+                v[j] = E * f;
+                sum += v[j];
             }
+            float scale = 1.0f;
+            if (kSample) {  // the draws keep their shape and take the MEAN total
+                if (sum > 0.0f) scale = sum_mean / sum;
+                sum = sum_mean;
+            }
+            if (sum > E) scale *= E / sum;
+            float2 *d2 = reinterpret_cast<float2 *>(p.dep + (size_t)i * kSurLayers);
+            pleak = (long long)fixed32(E);
+#pragma unroll
+            for (int j = 0; j < kSurLayers; ++j) {
+                if (scale != 1.0f) v[j] *= scale;
+                pc += v[j] > 0.0f;
+                stg[lane][j] = v[j];
+            }
+#pragma unroll
+            for (int j = 0; j < kSurLayers; j += 2) d2[j / 2] = make_float2(v[j], v[j + 1]);
+            p.pcnt[i] = (uint8_t)pc;
         }
+        __syncwarp();
+        // one particle at a time: lane L takes absolute layers L and L + 32
+        for (int k = 0; k < m; ++k) {
+            const int sk = (int)__shfl_sync(kFull, sh, k);
+            const int lk = __shfl_sync(kFull, layer, k);
+            const unsigned ck = __shfl_sync(kFull, pc, k);
+            if (sk != cur) {
+                flush();
+                cur = sk;
+            }
+            const int j_lo = lane - lk, j_hi = lane + 32 - lk;
+            unsigned long long f_lo = 0, f_hi = 0;
+            if (j_lo >= 0 && j_lo < kSurLayers) f_lo = fixed32(stg[k][j_lo]);
+            if (j_hi >= 0 && j_hi < kSurLayers) f_hi = fixed32(stg[k][j_hi]);
+            acc_lo += f_lo;
+            acc_hi += f_hi;
+            leak -= (long long)(f_lo + f_hi);
+            cnt += ck;
+            if (lane == k) leak += pleak;  // the particle's energy, once (in its own lane)
+        }
+        __syncwarp();
     }
     flush();
 }
@@ -349,9 +349,9 @@ cudaError_t launch_export_diverted(const SurRec *rec, int64_t n, const supa_prim
 
 cudaError_t launch_sur_deposits(const SurParams &p, cudaStream_t st) {
     if (p.mode == SUPA_SURROGATE_SAMPLE)
-        sur_deposits<true><<<4096, 128, 0, st>>>(p);
+        sur_deposits<true><<<4096, kDepWarps * 32, 0, st>>>(p);
     else
-        sur_deposits<false><<<4096, 128, 0, st>>>(p);
+        sur_deposits<false><<<4096, kDepWarps * 32, 0, st>>>(p);
     return cudaGetLastError();
 }
 
