@@ -274,6 +274,16 @@ int supa_profiles(supa_batch *b, int64_t shower_begin, int64_t shower_end, int32
  * without ordering) race and give wrong offsets.  Asynchronous on stream. */
 int supa_shower_offsets_noalloc(const uint32_t *counts_dev, int64_t n, int64_t *offsets_dev, void *stream);
 
+/* Check of the failure path of the tensor-core pipelines (the paper has no
+ * counterpart): every pipeline wait in this library gives up after a bounded
+ * time, records SUPA_ERR_TIMEOUT and lets the kernel return, so that a stuck
+ * pipeline leaves a usable context instead of a hung GPU.  This call runs
+ * one such wait, bounded at limit_cycles SM cycles (1..2^40), on a barrier
+ * that nothing completes, synchronises `stream` and returns what the wait
+ * reported: SUPA_ERR_TIMEOUT when it gave up as it must, SUPA_OK if it
+ * completed, SUPA_ERR_CUDA on a CUDA error. */
+int supa_check_wait_expiry(int64_t limit_cycles, void *stream);
+
 /* Per-layer grids and resolutions (App. A.5 "Downsampling"; the grid
  * experiments use a CaloGAN-like detector with 3 x 96, 12 x 12 and 12 x 6
  * cells per layer at resolutions "1x", "2x", "3x").  Layer l has nx x ny

@@ -585,4 +585,20 @@ int supa_surrogate_check(supa_surrogate *s) {
     return check_error_word(s);
 }
 
+int supa_check_wait_expiry(int64_t limit_cycles, void *stream) {
+    if (limit_cycles < 1 || limit_cycles > (1ll << 40))
+        return sfail(SUPA_ERR_INVALID_ARG, "limit_cycles must be in [1, 2^40]");
+    cudaStream_t st = (cudaStream_t)stream;
+    int *d_status = nullptr;
+    int status = -1;
+    cudaError_t e = cudaMalloc(&d_status, sizeof(int));
+    if (e == cudaSuccess) e = launch_wait_expiry_probe((long long)limit_cycles, d_status, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_status);
+    if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, cudaGetErrorString(e));
+    if (status == 1) return sfail(SUPA_ERR_TIMEOUT, "the bounded wait gave up, as it must");
+    return SUPA_OK;
+}
+
 }  // extern "C"

@@ -290,4 +290,23 @@ int make_bf16_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t co
     return r == CUDA_SUCCESS ? 0 : -3;
 }
 
+namespace {
+// A wait on a barrier that nothing completes: the bounded wait must give up
+// after `limit` cycles and report it (the kernel returns normally).
+__global__ void wait_expiry_probe(long long limit, int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    const bool done = mbar_wait_for(&bar, 0, limit);
+    *status = done ? 0 : 1;
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&bar)) : "memory");
+}
+}  // namespace
+
+cudaError_t launch_wait_expiry_probe(long long limit_cycles, int *status, cudaStream_t st) {
+    wait_expiry_probe<<<1, 32, 0, st>>>(limit_cycles, status);
+    return cudaGetLastError();
+}
+
 }  // namespace supa

@@ -51,6 +51,9 @@ constexpr int kTileK = 64;
 
 size_t gemm_smem_bytes(int N);
 cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &a, int splits, cudaStream_t st);
+// One bounded mbarrier wait on a barrier nothing completes; *status (device)
+// receives 1 when the wait gave up after limit_cycles, else 0.
+cudaError_t launch_wait_expiry_probe(long long limit_cycles, int *status, cudaStream_t st);
 // The whole network 6 -> 256 -> 256 -> 256 -> 96 (GELU after the hidden
 // layers) in one persistent kernel for inference (sur_mlp.cu).
 struct MlpInferArgs {

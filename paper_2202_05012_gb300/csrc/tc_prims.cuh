@@ -29,8 +29,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 }
 
 // Wait until the phase of parity `parity` of the barrier has completed.
-// Bounded: returns false after about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded: returns false after `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     while (true) {
         uint32_t done;
@@ -40,8 +40,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+// The pipelines' wait: bounded at about two seconds.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, kWaitCycles);
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {

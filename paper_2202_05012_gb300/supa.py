@@ -31,6 +31,7 @@ EXPORTED = (
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
     "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc", "supa_export_diverted",
     "supa_shower_shapes", "supa_layer_images_cells", "supa_voxelize_layers", "supa_voxelize_fetch",
+    "supa_check_wait_expiry",
 )
 
 
@@ -108,6 +109,7 @@ def lib(build_if_missing: bool = True):
         L.supa_fetch_hit_tags.argtypes = [_VP, _I64, _I64, _VP, ctypes.POINTER(_I64), _VP]
         L.supa_voxelize.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP]
         L.supa_voxelize_fetch.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP, _I64, _VP]
+        L.supa_check_wait_expiry.argtypes = [_I64, _VP]
         L.supa_voxelize_hits.argtypes = [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]
         L.supa_autotune.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, _VP, _I64, ctypes.c_uint64,
                                     ctypes.POINTER(supa_launch_config), ctypes.POINTER(ctypes.c_double), _VP]
