@@ -467,7 +467,7 @@ def run_supa_serial(args):
         S.supa_simulate(b, d_prim, n, seed, base)
         if ev is not None:
             ev["sim1"].record(stream)
-        info = S.supa_batch_get_info(b)
+        # the images follow the simulation in stream order: no host synchronisation in the step
         launches = 1 + 3 + 3  # step kernel, offset scan, energy-ordered queue
         vox_ms = 0.0
         for c0 in range(0, n, V):
@@ -481,10 +481,11 @@ def run_supa_serial(args):
             if ev is not None:
                 e1.record(stream)
                 ev["vox"].append((e0, e1, c1 - c0))
-        return info, launches
+        return launches
 
     for _ in range(args.warmup):
-        info, _ = step()
+        step()
+    info = S.supa_batch_get_info(b)
     torch.cuda.synchronize()
     n_hits, n_steps = info.n_hits, info.n_steps
     hits_per_shower = n_hits / n
@@ -500,11 +501,11 @@ def run_supa_serial(args):
     launches = 0
     for _ in range(args.steps):
         ev = {"sim0": torch.cuda.Event(enable_timing=True), "sim1": torch.cuda.Event(enable_timing=True), "vox": []}
-        info, nl = step(ev)
-        launches += nl
+        launches += step(ev)
         evs.append(ev)
     t_end.record(stream)
     torch.cuda.synchronize()
+    info = S.supa_batch_get_info(b)  # status and totals of the last timed step
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
