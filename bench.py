@@ -171,6 +171,22 @@ def oracle_sample(geom, prims, seed, seconds, chunk=500):
     return done / dt, steps / dt, done, dt, threads
 
 
+def cpu_baseline_fresh(args):
+    """The oracle timed as the reference arm times it, in a fresh process: in
+    this one the host threads of the GPU run would compete with its threads
+    and slow it several-fold."""
+    import subprocess
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--workload", args.workload,
+           "--steps", "1", "--warmup", "1", "--cpu-seconds", str(args.cpu_seconds)]
+    if args.showers:
+        cmd += ["--showers", str(args.showers)]
+    res = subprocess.run(cmd, capture_output=True, text=True, check=True)
+    line = json.loads([l for l in res.stdout.splitlines() if l.startswith("{")][-1])
+    cb = dict(line["cpu_baseline"])
+    cb["sample"] += f"; {line['ms_per_step'] / 1000.0:.1f} s, timed in a fresh process"
+    return cb
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -416,11 +432,7 @@ def run_supa(args):
         out["e2e"] = {"value": args.steps * n * world / dt, "unit": "showers/s", "h2d_bytes_per_step": n * 24,
                       "d2h_bytes_per_step": hi * 16 + n * L * 8}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sps, done, dt, threads = oracle_sample(geom, prims, seed, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": v, "unit": "showers/s", "cores": threads, "kind": "oracle",
-                               "sample": f"first {done} showers of this workload in {dt:.1f} s (simulate on "
-                                         f"{threads} threads, downsample single-threaded)",
-                               "particle_steps_per_s": sps}
+        out["cpu_baseline"] = cpu_baseline_fresh(args)
     pipe.close()
     S.supa_destroy_geometry(gh)
     if rank == 0:
@@ -557,11 +569,7 @@ def run_supa_serial(args):
                  "profiles": profiles_of(S, b, n, L)}
         out["hybrid"] = hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor, fbuf, plain)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sps, done, dt, threads = oracle_sample(geom, prims, seed, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": v, "unit": "showers/s", "cores": threads, "kind": "oracle",
-                               "sample": f"first {done} showers of this workload in {dt:.1f} s (simulate on "
-                                         f"{threads} threads, downsample single-threaded)",
-                               "particle_steps_per_s": sps}
+        out["cpu_baseline"] = cpu_baseline_fresh(args)
     S.supa_destroy_batch(b)
     S.supa_destroy_geometry(gh)
     if rank == 0:
