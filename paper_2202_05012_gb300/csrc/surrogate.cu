@@ -154,15 +154,33 @@ __global__ void __launch_bounds__(kLossRows * kLossLanesY)
 }
 
 // Adam with bias correction (c1 = 1 - beta1^t, c2 = 1 - beta2^t).
+// The BF16 copies of the four weight matrices (W and, where set, W^T) that
+// the GEMMs read, refreshed by the Adam update itself.
+struct WeightCopies {
+    size_t off[4];
+    int rows[4], cols[4];
+    __nv_bfloat16 *Wb[4], *WTb[4];
+};
+
 __global__ void adam_update(float *p, float *m, float *v, const float *g, size_t n, float lr, float b1, float b2,
-                            float eps, float c1, float c2) {
+                            float eps, float c1, float c2, const WeightCopies wc) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.0f - b1) * gi;
         const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
         m[i] = mi;
         v[i] = vi;
-        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const size_t j = i - wc.off[w];
+            if (i >= wc.off[w] && j < (size_t)wc.rows[w] * wc.cols[w]) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(pi);
+                wc.Wb[w][j] = h;
+                if (wc.WTb[w]) wc.WTb[w][(j % wc.cols[w]) * wc.rows[w] + j / wc.cols[w]] = h;
+            }
+        }
     }
 }
 
@@ -524,9 +542,13 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
     s->t += 1;
     const float c1 = 1.0f - std::pow(s->beta1, (float)s->t), c2 = 1.0f - std::pow(s->beta2, (float)s->t);
+    const WeightCopies wc{{Off::W1, Off::W2, Off::W3, Off::W4},
+                          {kHid, kHid, kHid, kOutPad},
+                          {kInPad, kHid, kHid, kHid},
+                          {s->W1b, s->W2b, s->W3b, s->W4b},
+                          {nullptr, s->W2Tb, s->W3Tb, s->W4Tb}};
     adam_update<<<296, 256, 0, st>>>(s->master, s->m, s->v, s->grad, Off::total, lr, s->beta1, s->beta2, s->eps, c1,
-                                     c2);
-    if (weight_copies(s, st) != SUPA_OK) return sfail(SUPA_ERR_CUDA, "weight copies failed");
+                                     c2, wc);
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_step launch failed");
 }
 
