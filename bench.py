@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="supa", choices=["supa", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5", "surrogate", "hybrid"])
+    ap.add_argument("--workload", default="plain30", choices=["plain10", "plain30", "mixed4", "plain50", "surrogate", "hybrid"])
     ap.add_argument("--e-s-sweep", type=float, nargs="+", default=[0.2, 0.5, 1.0, 2.0, 5.0])
     ap.add_argument("--showers", type=int, default=0, help="override the batch size")
     ap.add_argument("--voxel-chunk", type=int, default=32768)
@@ -66,13 +66,13 @@ def parse():
 
 def workload(name: str, n: int):
     from paper_2202_05012_gb300 import inputs
-    if name == "c1":
-        g, p = inputs.workload_c1(n or 1000)
+    if name == "plain10":
+        g, p = inputs.workload_plain10(n or 1000)
         return g, p, 0, dict(workload="plain SUPA, 1k showers, E U[1,10], 10 layers, 10x32x32", seed=0)
-    if name == "c5":
-        g, p = inputs.workload_c5(n or 200_000)
+    if name == "plain50":
+        g, p = inputs.workload_plain50(n or 200_000)
         return g, p, 4, dict(workload="plain SUPA, E log-U[10,1000], 0-45 deg, 50 layers, 50x128x128", seed=4)
-    g, p = inputs.workload_c2(n or 1_000_000)
+    g, p = inputs.workload_plain30(n or 1_000_000)
     return g, p, 1, dict(workload="plain SUPA, 1M showers, E U[1,100], 0-30 deg, +-1 cell entry, 30 layers, "
                                   "30x64x64 axis-centred images, point cloud written by the image pass", seed=1)
 
@@ -321,7 +321,7 @@ def run_supa(args):
         prims = inputs.primaries(n, seed + 1000 * rank, e_lo=float(prims["E"].min()), e_hi=float(prims["E"].max()))
     L, ny, nx = geom.n_layers, geom.ny, geom.nx
     gh = S.supa_init_geometry(geom)
-    cap = {"c1": 400, "c2": 1500, "c5": 9000}[args.workload]
+    cap = {"plain10": 400, "plain30": 1500, "plain50": 9000}[args.workload]
     d_prim = S.primaries_to_device(prims)
     pipe = Pipeline(S, gh, d_prim, n, args.pipeline, seed, base, cap, args.voxel_chunk, L, ny, nx, args.fetch_chunk)
     stream = torch.cuda.current_stream()
@@ -461,7 +461,7 @@ def run_supa_serial(args):
         prims = inputs.primaries(n, seed + 1000 * rank, e_lo=float(prims["E"].min()), e_hi=float(prims["E"].max()))
     L, ny, nx = geom.n_layers, geom.ny, geom.nx
     gh = S.supa_init_geometry(geom)
-    max_hits = int(n * {"c1": 400, "c2": 1500, "c5": 9000}[args.workload]) + (8 << 20)
+    max_hits = int(n * {"plain10": 400, "plain30": 1500, "plain50": 9000}[args.workload]) + (8 << 20)
     b = S.supa_batch_create([gh], n, {"max_hits": max_hits, "lpt_order": 1})
     d_prim = S.primaries_to_device(prims)
     V = min(args.voxel_chunk, n)
@@ -564,7 +564,7 @@ def run_supa_serial(args):
         out["calogan_multires"] = calogan_timing(S)
     if not args.no_e2e:
         out["e2e"] = e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world)
-    if world == 1 and args.workload == "c2" and not args.no_hybrid:
+    if world == 1 and args.workload == "plain30" and not args.no_hybrid:
         plain = {"step_ms": elapsed_ms / args.steps, "simulate_ms": sim_ms, "steps": n_steps,
                  "profiles": profiles_of(S, b, n, L)}
         out["hybrid"] = hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor, fbuf, plain)
@@ -678,7 +678,7 @@ def hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor
     throughput and profiles with the plain run."""
     from paper_2202_05012_gb300 import inputs
     from paper_2202_05012_gb300 import surrogate_train as T
-    net, tlog = matched_training(args, T, lambda m: inputs.workload_c2(m, seed=11), args.e_s,
+    net, tlog = matched_training(args, T, lambda m: inputs.workload_plain30(m, seed=11), args.e_s,
                                  float(prims["E"].mean()))
     sub = 125_000
     L = geom.n_layers
@@ -717,7 +717,7 @@ def run_surrogate(args):
 
     torch.cuda.set_device(0)
     n5 = args.showers or 100_000
-    g5, p5 = inputs.workload_c5(n5)
+    g5, p5 = inputs.workload_plain50(n5)
     gh = S.supa_init_geometry(g5)
     d5 = S.primaries_to_device(p5)
     L = g5.n_layers
@@ -749,7 +749,7 @@ def run_surrogate(args):
            "c5_showers": n5, "plain": {"simulate_showers_per_s": n5 / (plain_ms / 1000.0),
                                        "particle_steps_per_shower": plain_steps / n5}, "sweep": []}
     for e_s in args.e_s_sweep:
-        net, tlog = matched_training(args, T, lambda m: inputs.workload_c5(m, seed=14), e_s, float(p5["E"].mean()))
+        net, tlog = matched_training(args, T, lambda m: inputs.workload_plain50(m, seed=14), e_s, float(p5["E"].mean()))
         row = {"e_s": e_s, "training": tlog}
         # sub-batches small enough that the queue (about 4 E / E_s particles
         # per shower, ~1 KB each with outputs, deposits and hits) stays < 32 GB
@@ -904,7 +904,7 @@ def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
             "d2h_bytes_per_step": d2h}
 
 
-def run_c3(args):
+def run_mixed4(args):
     """Uneven batch: 4M showers, E log-uniform [1,1000] (multiplicity spans
     ~1000x), geometries of 10/20/30/50 layers mixed in each persistent launch;
     launch shape chosen by the autotuner; each 1M-shower launch replayed from a
@@ -917,7 +917,7 @@ def run_c3(args):
     torch.cuda.set_device(0)
     n = args.showers or 4_000_000
     sub = min(n, 1_000_000)
-    geoms, prims = inputs.workload_c3(n)
+    geoms, prims = inputs.workload_mixed4(n)
     gh = [S.supa_init_geometry(g) for g in geoms]
     d_prim = S.primaries_to_device(prims)
     cfg = {"lpt_order": 1, "max_hits": int(sub * 5000) + (16 << 20)}
@@ -990,10 +990,10 @@ def run_hybrid(args):
 
     torch.cuda.set_device(0)
     n = args.showers or 20_000
-    g, p = inputs.workload_c5(n)
+    g, p = inputs.workload_plain50(n)
     mean_e = float(p["E"].mean())
     if args.train_set == "matched":
-        net, tlog = matched_training(args, T, lambda m: inputs.workload_c5(m, seed=14), args.e_s, mean_e)
+        net, tlog = matched_training(args, T, lambda m: inputs.workload_plain50(m, seed=14), args.e_s, mean_e)
     else:
         data = T.training_set(args.train_samples, args.e_s, seed=3, n_layers=30)
         net, tlog = T.train(data, epochs=args.epochs, lr=args.lr, lr_final=args.lr_final)
@@ -1029,8 +1029,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "c3":
-        run_c3(args)
+    elif args.workload == "mixed4":
+        run_mixed4(args)
     elif args.workload == "surrogate":
         run_surrogate(args)
     elif args.workload == "hybrid":

@@ -200,13 +200,13 @@ def subshower_primaries(n: int, seed: int, *, e_lo: float = 0.05, e_hi: float = 
 
 # ---- the workloads of the benchmark configurations ------------------------
 
-def workload_c1(n: int = 1000):
+def workload_plain10(n: int = 1000):
     """1,000 showers, seed 0: E ~ U[1,10], normal incidence at the origin,
     10 layers, 10 x 32 x 32 grid."""
     return supa_d(10, grid=32, roi_mode=ROI_FIXED), primaries(n, 0, e_lo=1.0, e_hi=10.0)
 
 
-def workload_c2(n: int = 1_000_000, seed: int = 1):
+def workload_plain30(n: int = 1_000_000, seed: int = 1):
     """1,000,000 showers, seed 1: E ~ U[1,100], polar angle U[0,30 deg],
     entry within +-1 cell, 30 layers, 30 x 64 x 64 grid centred on the
     nominal shower axis (another seed: more showers of the same kind)."""
@@ -214,14 +214,14 @@ def workload_c2(n: int = 1_000_000, seed: int = 1):
     return g, primaries(n, seed, e_lo=1.0, e_hi=100.0, theta_max_deg=30.0, entry_halfwidth=g.wx)
 
 
-def workload_c3(n: int = 4_000_000):
+def workload_mixed4(n: int = 4_000_000):
     """4,000,000 showers, seed 2: E log-uniform [1,1000], four geometries of
     10/20/30/50 layers mixed in one launch."""
     geoms = [supa_d(L, grid=64, roi_mode=ROI_AXIS) for L in (10, 20, 30, 50)]
     return geoms, primaries(n, 2, e_lo=1.0, e_hi=1000.0, log_uniform=True, n_geoms=4)
 
 
-def workload_c5(n: int = 10_000_000, seed: int = 4):
+def workload_plain50(n: int = 10_000_000, seed: int = 4):
     """10,000,000 showers, seed 4: E log-uniform [10,1000], polar angle
     U[0,45 deg], 50 layers, 50 x 128 x 128 grid (another seed: more showers
     of the same kind)."""

@@ -38,13 +38,13 @@ def test_supav1_exact_on_gpu():
 
 
 def test_c1_workload_parity():
-    g, p = inputs.workload_c1(1000)
+    g, p = inputs.workload_plain10(1000)
     st, gpu, ora = _check([g], p, seed=0)
     assert gpu["n_hits"] == ora["offsets"][-1] or st["n_flip_showers"] > 0
     assert st["n_flip_showers"] <= 2
 
 
-def test_error_report_c2_shapes():
+def test_error_report_30_layer_showers():
     """The error of each output against the FP64 oracle on showers shaped
     like the 30-layer workload (E U[1,100] GeV, 0-30 deg; printed as one JSON line; the asserts are the stated tolerances)."""
     import json
@@ -118,7 +118,7 @@ def test_launch_shapes_do_not_change_results(cfg):
 
 
 def test_mixed_geometries_in_one_launch():
-    geoms, p = inputs.workload_c3(240)
+    geoms, p = inputs.workload_mixed4(240)
     p["E"] = np.minimum(p["E"], 200.0)
     _check(geoms, p, seed=2)
 
@@ -137,7 +137,7 @@ def test_max_slices_and_layers():
 
 
 def test_determinism_and_replay():
-    g, p = inputs.workload_c1(200)
+    g, p = inputs.workload_plain10(200)
     a = run_gpu([g], p, seed=5)
     b = run_gpu([g], p, seed=5, cfg={"warps_per_block": 2})
     for key in ("counts", "steps"):
@@ -170,7 +170,7 @@ def test_hit_pool_overflow_is_an_error_not_a_fault():
 
 def test_fetch_chunks_and_host_destination():
     import torch
-    g, p = inputs.workload_c1(300)
+    g, p = inputs.workload_plain10(300)
     gh = S.supa_init_geometry(g)
     b = S.supa_batch_create([gh], 300, {"record_tags": 1})
     try:

@@ -19,7 +19,7 @@ def _results(b, n):
 
 def test_autotune_returns_a_valid_shape_with_identical_results():
     import torch
-    geoms, p = inputs.workload_c3(20_000)
+    geoms, p = inputs.workload_mixed4(20_000)
     gh = [S.supa_init_geometry(g) for g in geoms]
     try:
         d = S.primaries_to_device(p)
@@ -49,7 +49,7 @@ def test_autotune_returns_a_valid_shape_with_identical_results():
 
 def test_graph_captured_simulate_and_voxelize_match_eager():
     import torch
-    g, p = inputs.workload_c2(5000)
+    g, p = inputs.workload_plain30(5000)
     gh = S.supa_init_geometry(g)
     b = S.supa_batch_create([gh], len(p), {"lpt_order": 1})
     try:

@@ -22,7 +22,7 @@ def _gpu_shapes(b, n, L):
     return lf.cpu().numpy().astype(np.float64), sf.cpu().numpy().astype(np.float64)
 
 
-def test_shapes_match_oracle_c2_shapes():
+def test_shapes_match_oracle_30_layer_showers():
     g = inputs.supa_d(30, grid=64, roi_mode=inputs.ROI_AXIS)
     n = 300
     p = inputs.primaries(n, 51, e_lo=1.0, e_hi=100.0, theta_max_deg=30.0, entry_halfwidth=0.25)

@@ -40,8 +40,8 @@ def _worst(ref, got, thr=0.005):
 
 
 def test_trained_network_replaces_most_steps_at_small_profile_error():
-    g, p = inputs.workload_c2(N, seed=21)
-    gt, pt = inputs.workload_c2(150_000, seed=22)
+    g, p = inputs.workload_plain30(N, seed=21)
+    gt, pt = inputs.workload_plain30(150_000, seed=22)
     data = T.training_set_matched(gt, pt, E_S, 5_000_000, seed=5)
     net, log = T.train(data, epochs=15, lr=2e-3, lr_final=5e-5)
     del data

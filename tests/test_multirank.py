@@ -26,7 +26,7 @@ def _worker(rank, world, port, n_per_rank, out_q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        g, p = inputs.workload_c1(n_per_rank * world)
+        g, p = inputs.workload_plain10(n_per_rank * world)
         mine = p[rank * n_per_rank:(rank + 1) * n_per_rank]
         r = oracle.simulate(g, mine, seed=0, shower_id_base=rank * n_per_rank)
         ls = torch.from_numpy(np.ascontiguousarray(r["layer_sum"]))
@@ -60,7 +60,7 @@ def test_two_ranks_reproduce_one_run():
     for pr in procs:
         pr.join(timeout=60)
         assert pr.exitcode == 0
-    g, p = inputs.workload_c1(n * world)
+    g, p = inputs.workload_plain10(n * world)
     full = oracle.simulate(g, p, seed=0)
     assert np.array_equal(ls, full["layer_sum"])
     assert hits == len(full["E"])

@@ -364,7 +364,7 @@ def test_escape_and_leak_rules():
 
 
 def test_results_independent_of_partition_and_threads():
-    g, p = inputs.workload_c1(200)
+    g, p = inputs.workload_plain10(200)
     a = oracle.simulate(g, p, seed=0, n_threads=1)
     b = oracle.simulate(g, p, seed=0, n_threads=4)
     lo = oracle.simulate(g, p[:77], seed=0, shower_id_base=0)

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 def test_noalloc_offsets_equal_batch_offsets_twice():
     import torch
-    g, p = inputs.workload_c1(3000)
+    g, p = inputs.workload_plain10(3000)
     gh = S.supa_init_geometry(g)
     b = S.supa_batch_create([gh], len(p), {})
     try:
