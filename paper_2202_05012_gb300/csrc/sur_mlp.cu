@@ -12,7 +12,8 @@
 // layer overwrites it).  Only the 6 inputs (24 B) and the outputs of a row
 // touch HBM.
 //
-// Shared memory (209,920 B with alignment slack):
+// Shared memory (209,920 B with alignment slack, plus the 3 KB of hidden-layer
+// biases read by the epilogue):
 //   X   16 KB       inputs of a tile (bf16, columns 0..15 used, K = 16), one
 //                   tile at a time: the next is packed once layer 1 read it
 //   H   2 x 64 KB   hidden activations of slots A and B, 4 K-blocks of 128
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     __shared__ __align__(8) uint64_t out_staged[2];  // slot: every epilogue warp staged its output block
     __shared__ __align__(8) uint64_t out_done[2];    // slot: every epilogue warp wrote its share out
     __shared__ uint32_t tmem_slot;
+    __shared__ __align__(16) float sbias[3 * 256];
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -95,6 +97,10 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    // hidden-layer biases, read by the epilogue from shared memory (global
+    // loads in the GELU loop stalled it on their latency)
+    for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x)
+        sbias[i] = i < 256 ? g.b1[i] : i < 512 ? g.b2[i - 256] : g.b3[i - 512];
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
                      "r"(512)
@@ -258,26 +264,34 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                     ++ac[x];
                     fence_after_sync();
                     const uint32_t acc = tmem + 256 * x + lane_off;
-                    const float *bias = layer == 1 ? g.b1 : layer == 2 ? g.b2 : g.b3;
                     uint8_t *hs = base + oH + x * kHBytes;
+                    // the next K-block's columns load from tensor memory while
+                    // this one's GELU runs
+                    uint32_t rv[2][16];
+                    tmem_ld16_issue(acc + h * 16, rv[0]);
+                    tmem_ld_wait(rv[0]);
+#pragma unroll
                     for (int kb = 0; kb < 4; ++kb) {
                         const int c0 = kb * 64 + h * 16;
-                        float v[16];
-                        tmem_ld16(acc + c0, v);
-                        const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0);
+                        if (kb < 3) tmem_ld16_issue(acc + c0 + 64, rv[(kb + 1) & 1]);
+                        const float4 *b4 = reinterpret_cast<const float4 *>(sbias + (layer - 1) * 256 + c0);
+                        const uint32_t *u = rv[kb & 1];
                         uint32_t p[8];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const float4 bb = __ldg(b4 + i);
-                            p[2 * i] =
-                                gelu2_bf16(__fadd2_rn(make_float2(v[4 * i], v[4 * i + 1]), make_float2(bb.x, bb.y)));
-                            p[2 * i + 1] = gelu2_bf16(
-                                __fadd2_rn(make_float2(v[4 * i + 2], v[4 * i + 3]), make_float2(bb.z, bb.w)));
+                            const float4 bb = b4[i];
+                            p[2 * i] = gelu2_bf16(__fadd2_rn(
+                                make_float2(__uint_as_float(u[4 * i]), __uint_as_float(u[4 * i + 1])),
+                                make_float2(bb.x, bb.y)));
+                            p[2 * i + 1] = gelu2_bf16(__fadd2_rn(
+                                make_float2(__uint_as_float(u[4 * i + 2]), __uint_as_float(u[4 * i + 3])),
+                                make_float2(bb.z, bb.w)));
                         }
                         uint8_t *blk = hs + kb * kHBlk;
                         *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
                         *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) =
                             make_uint4(p[4], p[5], p[6], p[7]);
+                        if (kb < 3) tmem_ld_wait(rv[(kb + 1) & 1]);
                     }
                     // the next layer's MMAs overwrite the whole accumulator, so
                     // they wait for all of H: one hand-off per layer
