@@ -381,9 +381,16 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
 int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,
                                float lr, double *loss_acc_dev, void *stream);
 /* Inference: x_dev float32 [n][6] (8-byte aligned) -> out_dev float32
- * [n][90], 0 <= n < 2^31, in one launch of the fused network kernel
- * (asynchronous; a pipeline timeout shows in supa_surrogate_check). */
-int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, void *stream);
+ * [n][ld_out], 0 <= n < 2^31, 90 <= ld_out < 2^31, in one launch of the
+ * fused network kernel (asynchronous; a pipeline timeout shows in
+ * supa_surrogate_check).  Columns 0..89 of each row hold the outputs.  A
+ * pitch that is a multiple of 4 floats at a 16-byte aligned out_dev is
+ * written with TMA stores, which is faster; columns 90..min(ld_out, 96)-1
+ * then receive the network's padding outputs, which are zero.  Other pitches
+ * take plain coalesced stores and leave columns 90.. untouched.  Rows n..
+ * are never written. */
+int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, int64_t ld_out,
+                           void *stream);
 /* Synchronise and report a tensor-core pipeline that gave up waiting
  * (SUPA_ERR_TIMEOUT) since the last check. */
 int supa_surrogate_check(supa_surrogate *s);

@@ -55,10 +55,15 @@ constexpr uint32_t oX = 0, oH = kXBytes, oS = oH + 2 * kHBytes;
 constexpr uint32_t kMlpSmem = oS + 2 * kWBlk + 1024;
 constexpr int kEpiWarps = 16;
 
+// kTmaOut: the output rows are 16-byte aligned (ld a multiple of 4), and each
+// epilogue warp writes its 32 x 32 output block with one TMA store (tout);
+// otherwise the output tile is staged in shared memory and written out with
+// coalesced plain stores by all epilogue warps together.
+template <bool kTmaOut>
 __global__ void __launch_bounds__(kMlpThreads, 1)
     sur_mlp_kernel(const __grid_constant__ CUtensorMap tw1, const __grid_constant__ CUtensorMap tw2,
                    const __grid_constant__ CUtensorMap tw3, const __grid_constant__ CUtensorMap tw4,
-                   const MlpInferArgs g) {
+                   const __grid_constant__ CUtensorMap tout, const MlpInferArgs g) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t w_full[2];      // ring stage holds a K-block
     __shared__ __align__(8) uint64_t w_empty[2];     // the MMAs have read the stage
@@ -67,7 +72,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     __shared__ __align__(8) uint64_t h_ready[2];     // slot: H written, accumulator read
     __shared__ __align__(8) uint64_t acc_full[2];    // slot: a layer's accumulator is final
     __shared__ __align__(8) uint64_t drain;          // all MMAs of this CTA done
-    __shared__ __align__(8) uint64_t out_staged[2];  // slot: every epilogue warp staged its output block
+    __shared__ __align__(8) uint64_t out_staged[2];  // slot: every epilogue warp read its output block
     __shared__ __align__(8) uint64_t out_done[2];    // slot: every epilogue warp wrote its share out
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(16) float sbias[3 * 256];
@@ -301,11 +306,6 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                     if (lane == 0) mbar_arrive(&h_ready[x]);
                 }
             }
-            // Output layer of each slot: stage the 128 x 96 tile in the slot's H
-            // buffer (idle now: layer 4's MMAs are done, and the next tile of
-            // the slot writes H only after every warp has passed out_done),
-            // then write it out row by row, coalesced.  Row pitch 100 floats:
-            // the float4 stores of 8 consecutive rows hit distinct banks.
             for (int x = 0; x < nx && ok; ++x) {
                 if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full[x], ac[x] & 1))) {
                     fail();
@@ -314,6 +314,64 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                 }
                 ++ac[x];
                 fence_after_sync();
+                const int m0 = ((int)blockIdx.x + (2 * pr + x) * (int)gridDim.x) * kRows;
+                if constexpr (kTmaOut) {
+                    // Output layer, TMA path: warp (q, h < 3) holds rows 32q.. and
+                    // columns 32h.. of the tile; it stages them as one 4 KB block
+                    // in the 128-byte-swizzled layout of tout (inside the slot's
+                    // idle H buffer, its own block) and stores the block with
+                    // one TMA store.  Rows past M (a ragged last tile) go out
+                    // with plain stores; columns past ncols are clipped by tout.
+                    // The warp arrives on out_staged once the TMA engine has
+                    // read its block: the slot's next tile writes H only after
+                    // the MMA issuer has seen every warp arrive.
+                    const int c0 = h * 32, row0 = m0 + q * 32;
+                    if (c0 < kOutN && row0 < M) {
+                        float v[32];
+                        tmem_ld32(tmem + 256 * x + lane_off + c0, v);
+                        const float4 *b4 = reinterpret_cast<const float4 *>(g.b4 + c0);
+                        if (row0 + 32 <= M) {
+                            uint8_t *blk = base + oH + x * kHBytes + (h * 4 + q) * 4096;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const float4 bb = __ldg(b4 + i);
+                                *reinterpret_cast<float4 *>(blk + lane * 128 + ((i ^ (lane & 7)) << 4)) =
+                                    make_float4(v[4 * i] + bb.x, v[4 * i + 1] + bb.y, v[4 * i + 2] + bb.z,
+                                                v[4 * i + 3] + bb.w);
+                            }
+                            fence_smem_to_async();
+                            __syncwarp();
+                            if (lane == 0) {
+                                tma_store_2d(&tout, blk, c0, row0);
+                                bulk_commit();
+                                bulk_wait_read_all();
+                            }
+                            __syncwarp();
+                        } else if (row0 + lane < M) {
+                            float *o = g.out + (size_t)(row0 + lane) * g.ld + c0;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const float4 bb = __ldg(b4 + i);
+                                const float w4[4] = {v[4 * i] + bb.x, v[4 * i + 1] + bb.y, v[4 * i + 2] + bb.z,
+                                                     v[4 * i + 3] + bb.w};
+                                if (c0 + 4 * i + 4 <= g.ncols)
+                                    *reinterpret_cast<float4 *>(o + 4 * i) = make_float4(w4[0], w4[1], w4[2], w4[3]);
+                                else
+                                    for (int j = 0; j < 4 && c0 + 4 * i + j < g.ncols; ++j) o[4 * i + j] = w4[j];
+                            }
+                        }
+                    }
+                    fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&out_staged[x]);
+                    continue;
+                }
+                // Output layer, plain path: stage the 128 x 96 tile in the
+                // slot's H buffer (idle now: layer 4's MMAs are done, and the
+                // next tile of the slot writes H only after every warp has
+                // passed out_done), then write it out row by row, coalesced.
+                // Row pitch 100 floats: the float4 stores of 8 consecutive
+                // rows hit distinct banks.
                 float *stage = reinterpret_cast<float *>(base + oH + x * kHBytes);
                 constexpr int kPitch = 100;
                 const int c0 = h * 32;
@@ -337,7 +395,6 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                     ok = false;
                     break;
                 }
-                const int m0 = ((int)blockIdx.x + (2 * pr + x) * (int)gridDim.x) * kRows;
                 const int e = (warp - 4) * 32 + lane;  // 0..511 over the epilogue warps
                 const bool vec = (g.ld & 3) == 0 && ((uintptr_t)g.out & 15) == 0;
                 for (int idx = e; idx < kRows * (kOutN / 4); idx += kEpiWarps * 32) {
@@ -363,6 +420,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         }
     }
 
+    if constexpr (kTmaOut) {
+        if (warp >= 4 && lane == 0) bulk_wait_all();
+    }
     fence_before_sync();
     __syncthreads();
     if (warp == 1) {
@@ -379,13 +439,21 @@ cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const C
         ((uintptr_t)a.x & 7))
         return cudaErrorInvalidValue;
     if (a.rows == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(sur_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
+    // rows of a 16-byte multiple pitch at a 16-byte aligned base, whole
+    // 16-byte column groups written: TMA stores (a TMA store writes a 16-byte
+    // group that straddles the column bound whole)
+    CUtensorMap tout{};
+    const bool tma_out = (a.ld & 3) == 0 && ((uintptr_t)a.out & 15) == 0 && a.ncols > 0 && (a.ncols & 3) == 0;
+    if (tma_out && make_f32_store_map(&tout, a.out, (uint64_t)a.rows, (uint64_t)a.ncols, (uint64_t)a.ld) != 0)
+        return cudaErrorInvalidValue;
+    auto kernel = tma_out ? sur_mlp_kernel<true> : sur_mlp_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int tiles = (a.rows + kRows - 1) / kRows;
-    sur_mlp_kernel<<<std::max(1, std::min(tiles, sms)), kMlpThreads, kMlpSmem, st>>>(w1, w2, w3, w4, a);
+    kernel<<<std::max(1, std::min(tiles, sms)), kMlpThreads, kMlpSmem, st>>>(w1, w2, w3, w4, tout, a);
     return cudaGetLastError();
 }
 

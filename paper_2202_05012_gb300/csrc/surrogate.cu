@@ -580,11 +580,14 @@ int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const floa
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_epoch launch failed");
 }
 
-int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, void *stream) {
+int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, float *out_dev, int64_t ld_out,
+                           void *stream) {
     if (!s || (!x_dev && n > 0) || (!out_dev && n > 0))
         return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_forward: null argument");
     if (n < 0 || n > INT32_MAX) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_forward: n out of range");
     if ((uintptr_t)x_dev & 7) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_forward: x must be 8-byte aligned");
+    if (ld_out < kOut || ld_out > INT32_MAX)
+        return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_forward: ld_out must be in [90, 2^31)");
     MlpInferArgs a{};
     a.x = x_dev;
     a.rows = (int)n;
@@ -593,8 +596,10 @@ int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, flo
     a.b3 = s->master + Off::b3;
     a.b4 = s->master + Off::b4;
     a.out = out_dev;
-    a.ld = kOut;
-    a.ncols = kOut;
+    a.ld = (int)ld_out;
+    // a pitch of whole 16-byte groups takes the TMA stores, which write whole
+    // groups: then the padding outputs 90.. (zero) are written too, up to 96
+    a.ncols = ld_out % 4 == 0 ? (int)std::min<int64_t>(ld_out, kInferLd) : kOut;
     a.error = s->error;
     const cudaError_t e = launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4i, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));

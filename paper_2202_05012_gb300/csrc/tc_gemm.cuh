@@ -73,5 +73,10 @@ cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const C
 // Tensor map of a row-major bf16 matrix [rows][cols] (cols contiguous) read in
 // boxes of 64 columns x box_rows rows with the 128-byte swizzle.
 int make_bf16_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+// Tensor map of a row-major float32 matrix [rows][cols] with row pitch ld
+// floats (ld a multiple of 4, base 16-byte aligned), written in boxes of
+// 32 columns x 32 rows with the 128-byte swizzle; columns >= cols and rows
+// >= rows of a box are not written.
+int make_f32_store_map(CUtensorMap *map, void *base, uint64_t rows, uint64_t cols, uint64_t ld);
 
 }  // namespace supa

@@ -119,7 +119,7 @@ def lib(build_if_missing: bool = True):
         L.supa_surrogate_get_params.argtypes = [_VP, _VP]
         L.supa_surrogate_gradients.argtypes = [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _VP]
         L.supa_surrogate_train_step.argtypes = [_VP, _VP, _VP, ctypes.c_float, _VP, _VP]
-        L.supa_surrogate_forward.argtypes = [_VP, _VP, _I64, _VP, _VP]
+        L.supa_surrogate_forward.argtypes = [_VP, _VP, _I64, _VP, _I64, _VP]
         L.supa_surrogate_check.argtypes = [_VP]
         L.supa_surrogate_train_epoch.argtypes = [_VP, _VP, _VP, _I64, ctypes.c_uint64, ctypes.c_float, _VP, _VP]
         L.supa_batch_set_surrogate.argtypes = [_VP, _VP, ctypes.c_float, _I64, ctypes.c_int32]
@@ -327,8 +327,11 @@ def supa_surrogate_train_step(s: int, x_dev, y_dev, lr: float, loss_acc_dev=None
                                            _stream(stream)), "supa_surrogate_train_step")
 
 
-def supa_surrogate_forward(s: int, x_dev, n: int, out_dev, stream=None):
-    _check(lib().supa_surrogate_forward(s, _ptr(x_dev), int(n), _ptr(out_dev), _stream(stream)),
+def supa_surrogate_forward(s: int, x_dev, n: int, out_dev, ld_out=None, stream=None):
+    """ld_out: the row pitch of out_dev in floats (default: the tensor's row stride, else 90)."""
+    if ld_out is None:
+        ld_out = out_dev.stride(0) if hasattr(out_dev, "stride") and out_dev.dim() == 2 else 90
+    _check(lib().supa_surrogate_forward(s, _ptr(x_dev), int(n), _ptr(out_dev), int(ld_out), _stream(stream)),
            "supa_surrogate_forward")
 
 

@@ -49,23 +49,39 @@ def test_gradients_match_fp64_oracle():
         S.supa_surrogate_destroy(s)
 
 
-def test_forward_matches_fp64_oracle_including_ragged_tail():
+@pytest.mark.parametrize("n,ld", [(1000, 90), (1000, 96), (1000, 93), (40_013, 96), (40_013, 90)])
+def test_forward_matches_fp64_oracle_including_ragged_tail(n, ld):
+    """Row pitches of 90 and 93 floats take the plain stores, 96 the TMA
+    stores; n = 1000 ends in a tile whose last 32-row block is partial, and
+    40,013 rows give every CTA two row tiles in flight and more than one pair.
+    The rows past n stay untouched, and so do columns 90.. of the plain
+    stores; the TMA stores write the zero padding outputs 90..95."""
     import torch
     vec, params = _f32_params(8)
-    n = 1000  # not a multiple of the minibatch: the last chunk is ragged
     X, _ = _batch(n, 2)
     s = S.supa_surrogate_create(256, vec)
     try:
         xd = torch.from_numpy(X.astype(np.float32)).cuda()
-        out = torch.full((n, 90), np.nan, dtype=torch.float32, device="cuda")
+        out = torch.full((n + 3, ld), np.nan, dtype=torch.float32, device="cuda")
         S.supa_surrogate_forward(s, xd, n, out)
         S.supa_surrogate_check(s)
-        got = out.cpu().numpy().astype(np.float64)
+        o = out.cpu().numpy()
+        assert np.all(np.isnan(o[n:]))
+        if ld % 4 == 0:
+            assert np.all(o[:n, 90:] == 0)
+        else:
+            assert np.all(np.isnan(o[:, 90:]))
+        got = o[:n, :90].astype(np.float64)
         ref, _ = mlp.forward(params, X)
         scale = np.abs(ref).max()
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref)) < 2e-2 * scale
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-2
+        if ld != 90:  # the two store paths give the same numbers
+            out90 = torch.empty((n, 90), dtype=torch.float32, device="cuda")
+            S.supa_surrogate_forward(s, xd, n, out90)
+            S.supa_surrogate_check(s)
+            assert np.array_equal(out90.cpu().numpy(), o[:n, :90])
     finally:
         S.supa_surrogate_destroy(s)
 
