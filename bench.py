@@ -746,7 +746,7 @@ def run_surrogate(args):
     plain_prof = (lo.cpu().numpy() / n5, la.cpu().numpy() / n5)
     S.supa_destroy_batch(pb)
     out = {"metric": METRIC, "workload": "surrogate training (10M samples x 20 epochs) + hybrid 50-layer showers vs plain, E_s sweep",
-           "c5_showers": n5, "plain": {"simulate_showers_per_s": n5 / (plain_ms / 1000.0),
+           "showers": n5, "plain": {"simulate_showers_per_s": n5 / (plain_ms / 1000.0),
                                        "particle_steps_per_shower": plain_steps / n5}, "sweep": []}
     for e_s in args.e_s_sweep:
         net, tlog = matched_training(args, T, lambda m: inputs.workload_plain50(m, seed=14), e_s, float(p5["E"].mean()))
