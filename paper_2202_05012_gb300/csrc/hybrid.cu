@@ -28,21 +28,27 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Standard normal n_j of a diverted particle, j = 0..31 (the layer offset):
+// Standard normals n_j of a diverted particle, j = 0..31 (the layer offset):
 // Box-Muller on Philox block j / 4 of its stream (tag 1, keyed by shower,
-// slice and lineage); words 2p and 2p + 1 of a block give the pair
-// (n_{4b+2p}, n_{4b+2p+1}) = rad (cos, sin)(2 pi u2), p = (j / 2) mod 2.
-__device__ float lane_normal(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed, int j) {
-    const int blk = j >> 2, pr = (j >> 1) & 1;
-    const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (1u << 16) | ((uint32_t)blk << 20), lin_lo, lin_hi),
+// slice and lineage); words 2p and 2p + 1 of block b give the pair
+// (n_{4b+2p}, n_{4b+2p+1}) = rad (cos, sin)(2 pi u2).  block_normals forms
+// the pairs of block b that `want` names (bit p: pair p) from one Philox call.
+__device__ void block_normals(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed, int b,
+                              unsigned want, float (&n)[4]) {
+    const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (1u << 16) | ((uint32_t)b << 20), lin_lo, lin_hi),
                                   (uint32_t)seed, (uint32_t)(seed >> 32));
-    const uint32_t w0 = pr ? r.z : r.x, w1 = pr ? r.w : r.y;
-    const float u1 = (float)((w0 >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
-    const float u2 = u24(w1);
-    const float rad = sqrtf(-2.0f * logf(u1));
-    float sn, cs;
-    sincospif(2.0f * u2, &sn, &cs);
-    return (j & 1) ? rad * sn : rad * cs;
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+        if (!(want & (1u << pr))) continue;
+        const uint32_t w0 = pr ? r.z : r.x, w1 = pr ? r.w : r.y;
+        const float u1 = (float)((w0 >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
+        const float u2 = u24(w1);
+        const float rad = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        n[2 * pr] = rad * cs;
+        n[2 * pr + 1] = rad * sn;
+    }
 }
 
 // The standard normal pair (m1, m2) displacing all hits of a diverted
@@ -139,21 +145,35 @@ __global__ void __launch_bounds__(kDepWarps * 32) sur_deposits(const SurParams p
             }
             float sum = 0.0f, sum_mean = 0.0f;
 #pragma unroll
-            for (int j = 0; j < kSurLayers; ++j) {
-                float f = j < nj ? fmaxf(0.0f, v[j]) : 0.0f;
+            for (int b = 0; b < (kSurLayers + 3) / 4; ++b) {
+                // the normals of this block of 4 layers, one Philox block and
+                // one Box-Muller pair per 2 layers that draw
+                float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                 if (kSample) {
-                    sum_mean += E * f;
-                    if (f > 0.0f) {
-                        // log-normal with mean mu and variance exp(s) (a^2 capped at 4)
-                        const float sg = __ldg(p.out + (size_t)i * p.out_ld + kSurLayers + j);
-                        const float a2 = fminf(4.0f, log1pf(expf(sg) / (f * f)));
-                        const float z = lane_normal((uint32_t)(p.shower_id_base + sh), r.k, r.lin_lo, r.lin_hi,
-                                                    p.seed, j);
-                        f *= expf(fmaf(sqrtf(a2), z, -0.5f * a2));
-                    }
+                    unsigned want = 0u;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (4 * b + t < kSurLayers && 4 * b + t < nj && v[4 * b + t] > 0.0f) want |= 1u << (t >> 1);
+                    if (want)
+                        block_normals((uint32_t)(p.shower_id_base + sh), r.k, r.lin_lo, r.lin_hi, p.seed, b, want, z);
                 }
-                v[j] = E * f;
-                sum += v[j];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int j = 4 * b + t;
+                    if (j >= kSurLayers) break;
+                    float f = j < nj ? fmaxf(0.0f, v[j]) : 0.0f;
+                    if (kSample) {
+                        sum_mean += E * f;
+                        if (f > 0.0f) {
+                            // log-normal with mean mu and variance exp(s) (a^2 capped at 4)
+                            const float sg = __ldg(p.out + (size_t)i * p.out_ld + kSurLayers + j);
+                            const float a2 = fminf(4.0f, log1pf(expf(sg) / (f * f)));
+                            f *= expf(fmaf(sqrtf(a2), z[t], -0.5f * a2));
+                        }
+                    }
+                    v[j] = E * f;
+                    sum += v[j];
+                }
             }
             float scale = 1.0f;
             if (kSample) {  // the draws keep their shape and take the MEAN total
