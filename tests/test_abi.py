@@ -24,6 +24,27 @@ def test_header_and_binding_agree():
     assert declared_entry_points() == sorted(S.EXPORTED)
 
 
+def declared_parameter_counts():
+    src = open(os.path.join(ROOT, "include", "supa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(supa_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        params = " ".join(params.split())
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every prototype's parameter count equals the argtypes the binding sets."""
+    L = S.lib()
+    counts = declared_parameter_counts()
+    assert set(counts) == set(declared_entry_points())
+    for name, n in counts.items():
+        argtypes = getattr(L, name).argtypes
+        assert (len(argtypes) if argtypes is not None else 0) == n, (name, n, argtypes)
+        assert argtypes is not None or n == 0, name
+
+
 def test_library_exports_every_declared_symbol():
     L = S.lib()
     for name in declared_entry_points():
