@@ -141,6 +141,7 @@ def test_null_arguments_rejected_without_gpu():
     assert L.supa_voxelize(None, 0, 1, None, None, None) == S.SUPA_ERR_INVALID_ARG
     assert L.supa_voxelize_fetch(None, 0, 1, None, None, None, 0, None) == S.SUPA_ERR_INVALID_ARG
     assert L.supa_check_wait_expiry(0, None) == S.SUPA_ERR_INVALID_ARG
+    assert L.supa_surrogate_forward(None, None, 1, None, 96, None) == S.SUPA_ERR_INVALID_ARG
     assert L.supa_simulate(None, None, 1, 0, 0, None) == S.SUPA_ERR_INVALID_ARG
     assert "null" in S.supa_last_error()
 
