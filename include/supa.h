@@ -269,7 +269,11 @@ int supa_profiles(supa_batch *b, int64_t shower_begin, int64_t shower_end, int32
  * the library until the process exits; n may be at most 16,769,024
  * (larger n: SUPA_ERR_INVALID_ARG, nothing launched).  The first call on a
  * device looks up the array's device address, so make that first call
- * before capturing a stream into a graph.  All calls share the one array:
+ * before capturing a stream into a graph; the address is kept per device
+ * and context, and the first call in a new context (after cudaDeviceReset)
+ * looks it up again, so that call too belongs before any capture.  Entries
+ * of the array are written before they are read within each call, so what
+ * an earlier call left there does not matter.  All calls share the one array:
  * calls that overlap on the GPU (different streams, or different threads
  * without ordering) race and give wrong offsets.  Asynchronous on stream. */
 int supa_shower_offsets_noalloc(const uint32_t *counts_dev, int64_t n, int64_t *offsets_dev, void *stream);

@@ -447,10 +447,6 @@ cudaError_t launch_profiles(const ProfileParams &p, cudaStream_t st) {
 // Exclusive scan of per-shower hit counts into int64 offsets [n+1]:
 // per-block totals, a single-block scan of the totals, then the final pass.
 namespace {
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
-
 __device__ __forceinline__ long long block_exclusive_scan(long long v, long long *warp_tot, long long &total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     long long inc = v;

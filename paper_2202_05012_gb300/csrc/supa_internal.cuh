@@ -204,6 +204,12 @@ size_t warp_smem_bytes(int stack_cap, int stage_cap, bool tags);
 cudaError_t launch_step(int minb, bool regions, bool staged, const StepParams &p, int grid, int block, size_t smem,
                         cudaStream_t st);
 cudaError_t step_kernel_attributes(int minb, bool regions, bool staged, int block, size_t smem, int *blocks_per_sm);
+// Exclusive scan of per-shower counts: kScanTile showers per block of the
+// first and last pass; scratch of scan_tmp_elems(n) = ceil(n / kScanTile) + 1
+// per-block totals.
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
 cudaError_t launch_scan_counts(const uint32_t *counts, int64_t n, int64_t *offsets, unsigned long long *block_tmp,
                                cudaStream_t st);
 size_t scan_tmp_elems(int64_t n);

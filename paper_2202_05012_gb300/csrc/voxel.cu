@@ -260,6 +260,9 @@ __global__ void __launch_bounds__(512) supa_voxel_kernel(const VoxParams p) {
                         }
                     } while (it2.next());
                 }
+                // each thread orders its own shared-memory writes of the tile
+                // before the async-proxy read of the bulk copy
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 __syncthreads();
                 if (threadIdx.x == 0)
                     bulk_store(p.grid + ((size_t)item * p.L + l0) * cells, tile, (unsigned)(G * cells) * 4u);
