@@ -7,17 +7,34 @@ returns them):
      layer (k - first slice) / slices in the layer, layers left from the
      particle's layer to the back over 30 (capped at 1);
   2. the FP64 network (oracle.mlp) gives mu_j and s_j, j = 0..29;
-  3. n_j: standard normals by Box-Muller from Philox4x32-10 blocks with
-     counter (shower id, slice | 1 << 16 | block << 20, lineage lo, lineage
-     hi), block = 0..7, key = seed; from each block's words (w0, w1, w2, w3)
-     the pairs (w0, w1) and (w2, w3) give u1 = ((w >> 8) + 1) 2^-24 and
-     u2 = (w >> 8) 2^-24, z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2);
+  3. SAMPLE draws: gamma variates by Marsaglia and Tsang's method ("A
+     simple method for generating gamma variables", ACM TOMS 26(3), 2000)
+     for shape a = alpha (alpha >= 1) or a = alpha + 1 (alpha < 1, then
+     multiplied by U^(1/alpha)): d = a - 1/3, c = 1 / sqrt(9 d); attempt t
+     (t = 0..3) of layer j takes the Philox4x32-10 block with counter
+     (shower id, slice | 3 << 16 | (4 j + t) << 20, lineage lo, lineage
+     hi), key = seed, words (w0, w1, w2, w3): a standard normal
+     x = sqrt(-2 ln u1) cos(2 pi u2) with u1 = ((w0 >> 8) + 1) 2^-24,
+     u2 = (w1 >> 8) 2^-24; v = (1 + c x)^3; accepted when 1 + c x > 0 and
+     ln u < x^2 / 2 + d (1 - v + ln v), u = ((w2 >> 8) + 1) 2^-24, giving
+     d v (times u3^(1/alpha), u3 = ((w3 >> 8) + 1) 2^-24, when alpha < 1).
+     Four rejections in a row (probability below 10^-5 for a >= 1) give the
+     mean alpha.  The accept test is taken in float32 with the operations in
+     the order written (the precision the library takes it in); the value is
+     formed in FP64;
   4. d_j = E f_j for layers inside the detector.  MEAN: f_j = max(0, mu_j).
-     SAMPLE: g_j = mu_j exp(a_j n_j - a_j^2 / 2), the log-normal with mean
-     mu_j and variance exp(s_j) (a_j^2 = ln(1 + exp(s_j) / mu_j^2), capped at
-     4 -- the mean stays mu_j), 0 when mu_j <= 0, then rescaled to the MEAN
-     total: f_j = g_j sum_i max(0, mu_i) / sum_i g_i (the shape fluctuates,
-     the total does not).  Both: scaled by E / sum d when the sum exceeds E;
+     SAMPLE: the total T = sum_j max(0, mu_j) is kept and its split over the
+     layers is drawn from a Dirichlet distribution whose means are the MEAN
+     shares m_j = max(0, mu_j) / T, so every layer's expected deposit is
+     exactly its MEAN deposit: f_j = T G_j / sum_i G_i with independent
+     G_j ~ Gamma(alpha_j = c m_j) (gamma_variate).  The concentration c is
+     matched to the predicted spreads: a Dirichlet share has variance
+     m_j (1 - m_j) / (c + 1), so T^2 (1 - sum m_j^2) / (c + 1) is set equal
+     to V = sum exp(s_j) over the layers with mu_j > 0 (the predicted
+     variances of their deposit fractions), c raised to 1 where it falls
+     below; where c exceeds 10^4 (V = 0 included) the spread is negligible
+     and the MEAN fractions are taken without a draw.  Both: scaled by
+     E / sum d when the sum exceeds E;
   5. one hit per layer with d_j > 0 at the layer's mid depth, displaced
      from the particle's straight-line position by sigma_j (m1, m2):
      sigma_j = max(0, rho_j) sqrt(2 / pi), so that each layer's displacement
@@ -95,26 +112,91 @@ def training_targets(geom, prims, res) -> np.ndarray:
     return Y
 
 
-def normals(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
+def _u24p(w: int) -> float:
+    """((w >> 8) + 1) 2^-24, a uniform on (0, 1]."""
+    return ((int(w) >> 8) + 1) * 2.0 ** -24
+
+
+def gamma_variate(alpha: float, shower_id: int, k: int, lineage: int, j: int, seed: int) -> float:
+    """Gamma(alpha, 1) variate of layer j of a diverted particle (step 3 of
+    the module's rule); alpha is taken at float32 precision."""
+    f32 = np.float32
     key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
-    z = []
-    for blk in range(8):
-        w = philox(((shower_id) & 0xFFFFFFFF, k | (1 << 16) | (blk << 20), lineage & 0xFFFFFFFF,
+    al = f32(alpha)
+    boost = al < f32(1.0)
+    a = f32(al + f32(1.0)) if boost else al
+    d = f32(a - f32(1.0 / 3.0))
+    c = f32(f32(1.0) / f32(np.sqrt(f32(f32(9.0) * d))))
+    for t in range(4):
+        w = philox((shower_id & 0xFFFFFFFF, k | (3 << 16) | ((4 * j + t) << 20), lineage & 0xFFFFFFFF,
                     (lineage >> 32) & 0xFFFFFFFF), key)
-        for p in range(2):
-            u1 = ((int(w[2 * p]) >> 8) + 1) * 2.0 ** -24
-            u2 = (int(w[2 * p + 1]) >> 8) * 2.0 ** -24
-            rad = math.sqrt(-2.0 * math.log(u1))
-            z.append(rad * math.cos(2 * math.pi * u2))
-            z.append(rad * math.sin(2 * math.pi * u2))
-    return np.array(z)
+        u1, u2, u, u3 = _u24p(w[0]), (int(w[1]) >> 8) * 2.0 ** -24, _u24p(w[2]), _u24p(w[3])
+        # the decision in float32, the operations in the order written
+        rad = f32(np.sqrt(f32(f32(-2.0) * f32(math.log(u1)))))
+        x = f32(rad * f32(math.cos(2.0 * math.pi * u2)))
+        t1 = f32(f32(1.0) + f32(c * x))
+        if not t1 > f32(0.0):
+            continue
+        v = f32(f32(t1 * t1) * t1)
+        rhs = f32(f32(f32(0.5) * f32(x * x)) + f32(d * f32(f32(f32(1.0) - v) + f32(math.log(float(v))))))
+        if not f32(math.log(u)) < rhs:
+            continue
+        # the value in FP64 from the same draws
+        x64 = math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+        d64 = float(a) - 1.0 / 3.0
+        g = d64 * (1.0 + x64 / math.sqrt(9.0 * d64)) ** 3
+        if boost:
+            g *= u3 ** (1.0 / float(al))
+        return g
+    return float(al)
 
 
-def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int = 0, mode: int = 0) -> dict:
+SAMPLE_C_MIN, SAMPLE_C_MAX = 1.0, 1.0e4
+
+
+def sample_concentration(f: np.ndarray, s: np.ndarray) -> float:
+    """Dirichlet concentration c of step 4 from the MEAN fractions f_j
+    (>= 0) and the predicted log-variances s_j; math.inf where the MEAN
+    fractions are taken without a draw (c above SAMPLE_C_MAX)."""
+    T = float(f.sum())
+    pos = f > 0
+    V = float(np.exp(s[pos]).sum())
+    if T <= 0:
+        return math.inf
+    m = f / T
+    num = T * T * (1.0 - float((m * m).sum()))
+    if V <= 0 or num > (SAMPLE_C_MAX + 1.0) * V:
+        return math.inf
+    return max(SAMPLE_C_MIN, num / V - 1.0)
+
+
+def sample_fractions(f: np.ndarray, s: np.ndarray, shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
+    """SAMPLE fractions: the MEAN total T = sum f split by a Dirichlet draw
+    with means f / T (step 4)."""
+    T = float(f.sum())
+    if T <= 0:
+        return np.zeros_like(f)
+    c = sample_concentration(f, s)
+    if math.isinf(c):
+        return f.copy()
+    G = np.zeros_like(f)
+    for j in np.nonzero(f > 0)[0]:
+        G[j] = gamma_variate(c * f[j] / T, shower_id, k, lineage, int(j), seed)
+    tot = G.sum()
+    if tot <= 0:
+        return f.copy()
+    return T * G / tot
+
+
+def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int = 0, mode: int = 0,
+             out=None) -> dict:
     """Per diverted particle: the drawn deposits d [n_div, 30] and the hits.
-    mode 0 (SAMPLE): moment-matched log-normal draws; mode 1 (MEAN): the means."""
+    mode 0 (SAMPLE): Dirichlet split of the MEAN total; mode 1 (MEAN): the
+    means.  `out` [n_div, 90] replaces the FP64 network's outputs when given
+    (to apply the rule to another implementation's network outputs)."""
     X = features(div, geom, e_s)
-    out, _ = mlp.forward(params, X) if len(X) else (np.zeros((0, 90)), None)
+    if out is None:
+        out, _ = mlp.forward(params, X) if len(X) else (np.zeros((0, 90)), None)
     L = int(geom.n_layers)
     s2l = np.asarray(geom.slice_to_layer)
     zmid = np.array([geom.dz * (np.nonzero(s2l == l)[0].min() + np.nonzero(s2l == l)[0].max()) * 0.5
@@ -123,23 +205,14 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
     d = np.zeros((nd, 30))
     hits = []
     for i in range(nd):
-        n = normals(shower_id_base + int(div["shower"][i]), int(div["k"][i]), int(div["lineage"][i]), seed)
         l0 = int(div["layer"][i])
         E = div["E"][i]
-        for j in range(30):
-            if l0 + j < L:
-                mu = out[i, j]
-                if mode == 1 or mu <= 0.0:
-                    f = max(0.0, mu)
-                else:
-                    a2 = min(4.0, math.log1p(math.exp(out[i, 30 + j]) / (mu * mu)))
-                    f = mu * math.exp(math.sqrt(a2) * n[j] - 0.5 * a2)
-                d[i, j] = E * f
+        inside = l0 + np.arange(30) < L
+        f = np.where(inside, np.maximum(0.0, out[i, :30]), 0.0)
         if mode != 1:
-            inside = l0 + np.arange(30) < L
-            mean_tot = E * np.maximum(0.0, out[i, :30][inside]).sum()
-            if d[i].sum() > 0:
-                d[i] *= mean_tot / d[i].sum()
+            f = sample_fractions(f, out[i, 30:60], shower_id_base + int(div["shower"][i]), int(div["k"][i]),
+                                 int(div["lineage"][i]), seed)
+        d[i] = E * f
         tot = d[i].sum()
         if tot > E:
             d[i] *= E / tot

@@ -1,7 +1,8 @@
 """Pins of the FP64 hybrid-path oracle (no counterpart in the paper; the
-rules are the library's): the normals are standard normal, a network with
-zero spread deposits exactly its means, SAMPLE draws are log-normal with the
-predicted mean and variance, rescaled to the MEAN total, sums above E are
+rules are the library's): the gamma variates follow the gamma law
+(scipy.stats), a network with zero spread deposits exactly its means, SAMPLE
+splits the MEAN total by a Dirichlet draw whose means are the MEAN shares
+and whose spread matches the predicted variances, sums above E are
 scaled to E, hits
 lie on the particle's straight line when the predicted distance is zero and
 at that mean distance otherwise, the hybrid stepping reduces to the plain
@@ -10,6 +11,7 @@ training targets of a single symmetric split are its closed form."""
 import math
 
 import numpy as np
+import pytest
 from scipy import stats
 
 import oracle
@@ -17,18 +19,34 @@ from oracle import hybrid
 from paper_2202_05012_gb300 import inputs
 
 
-def test_box_muller_normals_are_standard():
-    z = np.concatenate([hybrid.normals(s, 3 + s % 7, 2 * s + 1, 12345) for s in range(700)])
-    assert stats.kstest(z, "norm").pvalue > 1e-3
-    assert abs(z.mean()) < 0.03 and abs(z.std() - 1) < 0.03
+@pytest.mark.parametrize("alpha", [0.05, 0.3, 1.0, 2.5, 40.0])
+def test_gamma_variates_follow_the_gamma_law(alpha):
+    """Marsaglia-Tsang with the alpha < 1 boost against scipy's gamma law,
+    over independent counters (showers) and two layers' streams."""
+    g = np.array([hybrid.gamma_variate(alpha, s, 5, 2 * s + 1, s % 2, 4242) for s in range(4000)])
+    assert np.all(g >= 0)
+    assert stats.kstest(g, "gamma", args=(alpha,)).pvalue > 1e-3
+    assert abs(g.mean() - alpha) < 4 * math.sqrt(alpha / len(g))
+    assert abs(g.var() / alpha - 1) < 0.25
+
+
+def test_gamma_streams_differ_by_layer_and_attempt():
+    a = [hybrid.gamma_variate(2.0, 7, 3, 9, j, 1) for j in range(30)]
+    assert len(set(a)) == 30
+    # a layer's draw depends on the shower, slice and lineage of its particle
+    assert hybrid.gamma_variate(2.0, 8, 3, 9, 0, 1) != a[0]
+    assert hybrid.gamma_variate(2.0, 7, 4, 9, 0, 1) != a[0]
+    assert hybrid.gamma_variate(2.0, 7, 3, 10, 0, 1) != a[0]
 
 
 def test_offset_normals_are_standard_pairs():
     m = np.array([hybrid.offset_normals(s, 2 + s % 5, 3 * s + 1, 777) for s in range(6000)])
     assert stats.kstest(m.ravel(), "norm").pvalue > 1e-3
     assert abs(np.corrcoef(m[:, 0], m[:, 1])[0, 1]) < 0.05
-    # a different stream from the deposit normals
-    assert not np.isclose(m[0, 0], hybrid.normals(0, 2, 1, 777)[0])
+    # a different stream (tag 2) from the decision block (tag 0) of the same particle
+    w0 = oracle.philox((0, 2, 1, 0), (777, 0))
+    w2 = oracle.philox((0, 2 | (2 << 16), 1, 0), (777, 0))
+    assert not np.array_equal(w0, w2)
 
 
 def test_plain_path_when_nothing_is_set_aside():
@@ -150,39 +168,91 @@ def test_training_targets_of_a_single_symmetric_split():
     np.testing.assert_allclose(Y[:, [30, 31, 33]], 0.0, atol=0)
 
 
-def test_sample_mode_is_the_moment_matched_log_normal():
-    g = inputs.supa_d(30)
-    p = inputs.primaries(150, 12, e_lo=5, e_hi=20)
-    r = oracle.simulate(g, p, 4, e_s=1.0)
-    div = r["div"]
+def _layer_net(mu, s, rho=0.0):
+    """A network whose outputs are the given per-layer mu_j, s_j (and rho)
+    whatever its inputs."""
+    params = inputs.mlp_init(2)
+    W4 = np.zeros((90, 256))
+    b4 = np.concatenate([np.asarray(mu, float), np.asarray(s, float), np.full(30, rho)])
+    return params[:3] + [(W4, b4)]
+
+
+def _diverted_on_layer0(n, E=0.5):
+    """n diverted particles at the front of a 30-layer detector (all 30
+    predicted layers inside), distinct showers and lineages."""
+    return dict(shower=np.arange(n), k=np.zeros(n, int), lineage=2 * np.arange(n) + 3, layer=np.zeros(n, int),
+                E=np.full(n, E), x=np.zeros(n), y=np.zeros(n), ux=np.zeros(n), uy=np.zeros(n), uz=np.ones(n))
+
+
+def test_sample_concentration_matches_the_predicted_variance():
+    # equal layers: T = 30 mu, m = 1/30, V = 30 sd^2 -> c + 1 = T^2 (1 - 1/30) / V
     mu, sd = 0.02, 0.01
-    net = _const_net(mu, math.log(sd * sd))
+    f = np.full(30, mu)
+    c = hybrid.sample_concentration(f, np.full(30, math.log(sd * sd)))
+    T = 30 * mu
+    assert c == pytest.approx(T * T * (1 - 1 / 30) / (30 * sd * sd) - 1, rel=1e-12)
+    # a Dirichlet share then has variance T^2 m (1 - m) / (c + 1) = sd^2
+    assert T * T * (1 / 30) * (1 - 1 / 30) / (c + 1) == pytest.approx(sd * sd, rel=1e-12)
+    # a negligible spread takes the means (no draw); a huge one the lowest c
+    assert math.isinf(hybrid.sample_concentration(f, np.full(30, -200.0)))
+    tiny = T * T * (1 - 1 / 30) / (30 * (hybrid.SAMPLE_C_MAX + 1)) * 1.01
+    assert hybrid.sample_concentration(f, np.full(30, math.log(tiny))) == pytest.approx(hybrid.SAMPLE_C_MAX / 1.01, rel=1e-3)
+    assert math.isinf(hybrid.sample_concentration(f, np.full(30, math.log(tiny / 1.02))))
+    assert hybrid.sample_concentration(f, np.full(30, 5.0)) == hybrid.SAMPLE_C_MIN
+    assert math.isinf(hybrid.sample_concentration(np.zeros(30), np.zeros(30)))
+    # layers without a mean deposit do not count towards V
+    f2 = f.copy()
+    f2[10:] = 0.0
+    s2 = np.full(30, math.log(sd * sd))
+    s2[10:] = 3.0
+    T2 = 10 * mu
+    assert hybrid.sample_concentration(f2, s2) == pytest.approx(T2 * T2 * 0.9 / (10 * sd * sd) - 1, rel=1e-12)
+
+
+def test_sample_mode_is_an_unbiased_dirichlet_split():
+    g = inputs.supa_d(30)
+    n = 3000
+    div = _diverted_on_layer0(n)
+    # uneven means (a peak and a long tail, two layers empty) and spreads
+    j = np.arange(30)
+    mu = 0.08 * np.exp(-0.5 * ((j - 6) / 3.0) ** 2) + 0.002  # total 0.65: no scaling to E
+    mu[[20, 25]] = -0.01
+    sd = 0.4 * np.abs(mu)
+    net = _layer_net(mu, np.log(sd * sd))
     dep = hybrid.deposits(div, net, g, 1.0, 4, mode=0)
     mean = hybrid.deposits(div, net, g, 1.0, 4, mode=1)
-    # the total of every particle is the MEAN total; the shape fluctuates
+    E = div["E"][:, None]
+    fr = dep["d"] / E
+    # every particle keeps the MEAN total; layers without a mean get nothing
     np.testing.assert_allclose(dep["d"].sum(1), mean["d"].sum(1), rtol=1e-12)
-    assert np.std(dep["d"][:, 0] / div["E"]) > 0.5 * sd
-    # before that rescaling the draws are log-normal with mean mu and
-    # variance sd^2 (a^2 = ln 1.25, below the cap): undo it per particle
-    inside = div["layer"][:, None] + np.arange(30) < g.n_layers  # [n, 30]
-    n_in = inside.sum(1)
-    raw = []
-    for i in range(len(div["E"])):
-        norm = hybrid.normals(int(div["shower"][i]), int(div["k"][i]), int(div["lineage"][i]), 4)[:n_in[i]]
-        raw.append(norm)
-    z = np.concatenate(raw)
-    assert z.size > 20000
-    a2 = math.log1p(sd * sd / (mu * mu))
-    g_draw = mu * np.exp(math.sqrt(a2) * z - 0.5 * a2)
-    assert abs(g_draw.mean() - mu) < 4 * sd / math.sqrt(g_draw.size)
-    assert abs(g_draw.var() / sd ** 2 - 1) < 0.05
-    ratio = np.concatenate([dep["d"][i, :n_in[i]] / div["E"][i] / (mu * np.exp(math.sqrt(a2) * raw[i] - 0.5 * a2))
-                            for i in range(len(raw))])
-    # one factor per particle: sum of means / sum of draws
-    for i in range(0, len(raw), 37):
-        r = dep["d"][i, :n_in[i]] / div["E"][i] / (mu * np.exp(math.sqrt(a2) * raw[i] - 0.5 * a2))
-        np.testing.assert_allclose(r, r[0], rtol=1e-12)
-    assert ratio.size == z.size
+    assert np.all(dep["d"][:, [20, 25]] == 0)
+    f = np.maximum(0.0, mu)
+    T = f.sum()
+    m = f / T
+    c = hybrid.sample_concentration(f, np.log(sd * sd))
+    # each layer's mean fraction is its MEAN fraction (Dirichlet means), its
+    # variance T^2 m (1 - m) / (c + 1)
+    var = T * T * m * (1 - m) / (c + 1)
+    se = np.sqrt(var / n)
+    ok = f > 0
+    assert np.all(np.abs(fr.mean(0)[ok] - f[ok]) < 4.5 * se[ok])
+    np.testing.assert_allclose(fr.var(0)[ok], var[ok], rtol=0.2)
+    # and the spread summed over the layers is the predicted one
+    assert abs((fr.var(0)[ok]).sum() / (sd[ok] ** 2).sum() - 1) < 0.1
+    # replayable: the same counters give the same draws
+    again = hybrid.deposits({k: v[:50] for k, v in div.items()}, net, g, 1.0, 4, mode=0)
+    np.testing.assert_array_equal(again["d"], dep["d"][:50])
+
+
+def test_sample_mode_is_truncated_at_the_back():
+    g = inputs.supa_d(30)
+    div = _diverted_on_layer0(200)
+    div["layer"][:] = 25  # five layers inside
+    div["k"][:] = 75
+    net = _layer_net(np.full(30, 0.05), np.full(30, math.log(1e-4)))
+    dep = hybrid.deposits(div, net, g, 1.0, 4, mode=0)
+    assert np.all(dep["d"][:, 5:] == 0)
+    np.testing.assert_allclose(dep["d"].sum(1), 0.25 * div["E"], rtol=1e-12)
 
 
 def test_features_follow_their_definition():
