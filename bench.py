@@ -578,34 +578,32 @@ def run_supa_serial(args):
         dist.destroy_process_group()
 
 
-PROFILE_BINS, PROFILE_RMAX = 64, 8.0
-
-
 def profiles_of(S, b, n, L):
     """Mean longitudinal (per-layer energy / E0) and lateral (energy / E0 per
-    0.125-wide ring around the incidence axis) profiles of the batch."""
+    ring around the incidence axis, the last ring open) profiles of the
+    batch."""
     import torch
+    from paper_2202_05012_gb300.surrogate_train import PROFILE_BINS, PROFILE_RMAX
     lo = torch.zeros(L, dtype=torch.float64, device="cuda")
     la = torch.zeros(PROFILE_BINS, dtype=torch.float64, device="cuda")
     S.supa_profiles(b, 0, n, PROFILE_BINS, PROFILE_RMAX, lo, la)
     return lo.cpu().numpy() / n, la.cpu().numpy() / n
 
 
-def profile_errors(ref, got, thr=0.005):
-    """Largest relative deviation over profile bins holding >= thr of the
-    energy, and the relative deviation of the mean total deposit.  The
-    lateral profile is the regular radial bins (r < r_max, the imaged
-    region); the last bin (everything beyond) is reported as lateral_tail."""
-    (rl, rr), (gl, gr) = ref, got
+def profile_errors(ref, got):
+    """Largest relative profile deviations over groups of bins holding >= 2 %
+    of the plain run's energy each, covering all of it (see
+    surrogate_train.profile_errors)."""
+    from paper_2202_05012_gb300.surrogate_train import profile_errors as pe
+    return pe(ref, got)
 
-    def err(a, b):
-        m = a >= thr
-        return float(np.max(np.abs(b[m] - a[m]) / a[m])) if m.any() else 0.0
 
-    return {"longitudinal": err(rl, gl), "lateral": err(rr[:-1], gr[:-1]),
-            "lateral_tail": float(abs(gr[-1] - rr[-1]) / rr[-1]) if rr[-1] > 0 else 0.0,
-            "lateral_tail_fraction": float(rr[-1]),
-            "total_deposit": float(abs(gl.sum() - rl.sum()) / rl.sum()), "bin_threshold": thr}
+def profile_binning():
+    from paper_2202_05012_gb300.surrogate_train import PROFILE_BINS, PROFILE_GROUP, PROFILE_RMAX
+    return {"lateral_rings": PROFILE_BINS, "ring_width": PROFILE_RMAX / PROFILE_BINS,
+            "last_ring": f"r >= {PROFILE_RMAX * (PROFILE_BINS - 1) / PROFILE_BINS:g} (open)",
+            "error": f"largest relative deviation over groups of consecutive bins holding >= "
+                     f"{PROFILE_GROUP:.0%} of the plain run's energy each (all bins: 100 % of the energy)"}
 
 
 def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor, fbuf, L, profiles=False, mode=0,
@@ -619,6 +617,7 @@ def hybrid_run(S, gh, prims, d_prim, n, seed, base, net, e_s, sub, V, grid, oor,
     hb_hits = int(sub * max(400, 40 * mean_e)) + (8 << 20)
     hb = S.supa_batch_create([gh], sub, {"max_hits": hb_hits, "lpt_order": 1})
     S.supa_batch_set_surrogate(hb, net, e_s, cap, mode)
+    from paper_2202_05012_gb300.surrogate_train import PROFILE_BINS, PROFILE_RMAX
     lo = torch.zeros(L, dtype=torch.float64, device="cuda")
     la = torch.zeros(PROFILE_BINS, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -685,7 +684,7 @@ def hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor
     out = {"e_s": args.e_s, "plain_showers_per_s": n / (plain["step_ms"] / 1000.0),
            "plain_simulate_showers_per_s": n / (plain["simulate_ms"] / 1000.0),
            "plain_particle_steps_per_shower": plain["steps"] / n,
-           "profile_binning": {"lateral_bins": PROFILE_BINS, "r_max": PROFILE_RMAX},
+           "profile_binning": profile_binning(),
            "training": tlog,
            "note": "hybrid timed in 125k-shower sub-batches (network over each sub-batch's queue); plain as one "
                    "batch; same showers and seeds"}
@@ -714,6 +713,7 @@ def run_surrogate(args):
     from paper_2202_05012_gb300 import inputs
     from paper_2202_05012_gb300 import supa as S
     from paper_2202_05012_gb300 import surrogate_train as T
+    from paper_2202_05012_gb300.surrogate_train import PROFILE_BINS, PROFILE_RMAX
 
     torch.cuda.set_device(0)
     n5 = args.showers or 100_000

@@ -218,7 +218,9 @@ int supa_fetch_hits(supa_batch *b, int64_t first_hit, int64_t max_hits, void *ds
                     int64_t *n_written, void *stream);
 
 /* Same ranges as supa_fetch_hits, lineage ids (uint64) of the hits; needs
- * record_tags = 1 at batch creation. */
+ * record_tags = 1 at batch creation.  On the hybrid path a surrogate hit
+ * carries the lineage id of the diverted particle that emitted it with bit 63
+ * set (stepped hits never have bit 63: lineage ids stay below 2^63). */
 int supa_fetch_hit_tags(supa_batch *b, int64_t first_hit, int64_t max_hits, uint64_t *dst_dev,
                         int64_t *n_written, void *stream);
 
@@ -401,11 +403,19 @@ int supa_surrogate_check(supa_surrogate *s);
 
 /* Deposit rule of the hybrid path for layer start + j of a particle of
  * energy E, from the network's mu_j and s_j. */
-/* MEAN: d_j = E max(0, mu_j).  SAMPLE: g_j = E mu_j exp(a_j n_j - a_j^2/2),
- * n_j ~ N(0,1), a_j^2 = min(4, ln(1 + exp(s_j)/mu_j^2)) -- a log-normal draw
- * with mean E mu_j (variance E^2 exp(s_j) below the cap), 0 for mu_j <= 0 --
- * rescaled so that the particle's total equals the MEAN total: the shape of
- * the deposits fluctuates, their sum does not. */
+/* MEAN: d_j = E max(0, mu_j).  SAMPLE: the MEAN total E T, T = sum_j
+ * max(0, mu_j), split over the layers by a Dirichlet draw whose means are the
+ * MEAN shares m_j = max(0, mu_j) / T: d_j = E T G_j / sum_i G_i with
+ * independent G_j ~ Gamma(c m_j), so every layer's expected deposit is its
+ * MEAN deposit and the particle's total is the MEAN total.  The
+ * concentration c matches the predicted variances: T^2 (1 - sum m_j^2) /
+ * (c + 1) = sum of exp(s_j) over the layers with mu_j > 0, c >= 1; where c
+ * would exceed 10^4 the MEAN deposits are taken; a layer whose G_j is below
+ * 10^-9 of sum_i G_i gets nothing (the others' sum normalises).  The gamma
+ * variates follow
+ * Marsaglia and Tsang (ACM TOMS 26(3), 2000) on Philox stream tag 3 (counter
+ * (shower id, slice | 3 << 16 | (4 j + attempt) << 20, lineage), key =
+ * seed), at most four attempts per layer (then the mean c m_j). */
 #define SUPA_SURROGATE_SAMPLE 0
 #define SUPA_SURROGATE_MEAN 1
 
@@ -441,6 +451,35 @@ int supa_build_training_set(supa_batch *b, float e_s, float *x_dev, float *y_dev
  * Like the surrogate itself this has no counterpart in the SUPA paper.
  * Synchronous. */
 int supa_export_diverted(supa_batch *b, supa_primary *out_dev, int64_t capacity, int64_t *n_out, void *stream);
+
+/* Everything the surrogate did for one diverted particle of the last hybrid
+ * simulation: its key and state when it was set aside, the network's outputs
+ * and its drawn deposits (no counterpart in the SUPA paper). */
+typedef struct supa_diverted_record {
+    uint32_t shower;  /* index of the shower in the batch                 */
+    int32_t slice;    /* slice of diversion k                             */
+    int32_t layer;    /* readout layer of slice k                         */
+    float x, y;       /* position on slice k                              */
+    float tx, ty;     /* slopes u_x / u_z, u_y / u_z                      */
+    float E;          /* energy                                           */
+    uint64_t lineage; /* lineage id                                       */
+    float mu[30];     /* network outputs for layers layer + j:            */
+    float s[30];      /*   deposit-fraction means, log-variances and mean */
+    float rho[30];    /*   lateral distances                              */
+    float dep[30];    /* deposits of layers layer + j (0 past the back)    */
+    uint32_t n_hits;  /* hits emitted (layers with a deposit > 0)         */
+    uint32_t reserved;
+} supa_diverted_record;
+
+/* Writes the records of min(n, capacity) diverted particles of the last
+ * hybrid simulation of b to out_dev (device memory, 528 bytes each, in queue
+ * order, which is not defined) and the queue length n to *n_out; capacity 0
+ * with out_dev NULL only reports n.  The deposit rule and the hit rule can be
+ * checked particle by particle from these records.  SUPA_ERR_INVALID_ARG if
+ * b is not in hybrid mode, SUPA_ERR_NOT_READY before its first simulation.
+ * Synchronous. */
+int supa_export_surrogate(supa_batch *b, supa_diverted_record *out_dev, int64_t capacity, int64_t *n_out,
+                          void *stream);
 
 #ifdef __cplusplus
 }

@@ -33,8 +33,10 @@ returns them):
      to V = sum exp(s_j) over the layers with mu_j > 0 (the predicted
      variances of their deposit fractions), c raised to 1 where it falls
      below; where c exceeds 10^4 (V = 0 included) the spread is negligible
-     and the MEAN fractions are taken without a draw.  Both: scaled by
-     E / sum d when the sum exceeds E;
+     and the MEAN fractions are taken without a draw.  A layer whose G_j is
+     below 10^-9 of sum_i G_i gets nothing (the sum over the others
+     normalises; such shares lie where float32 gamma variates underflow).
+     Both: scaled by E / sum d when the sum exceeds E;
   5. one hit per layer with d_j > 0 at the layer's mid depth, displaced
      from the particle's straight-line position by sigma_j (m1, m2):
      sigma_j = max(0, rho_j) sqrt(2 / pi), so that each layer's displacement
@@ -152,6 +154,7 @@ def gamma_variate(alpha: float, shower_id: int, k: int, lineage: int, j: int, se
 
 
 SAMPLE_C_MIN, SAMPLE_C_MAX = 1.0, 1.0e4
+SAMPLE_SHARE_MIN = 1.0e-9
 
 
 def sample_concentration(f: np.ndarray, s: np.ndarray) -> float:
@@ -185,12 +188,14 @@ def sample_fractions(f: np.ndarray, s: np.ndarray, shower_id: int, k: int, linea
     tot = G.sum()
     if tot <= 0:
         return f.copy()
-    return T * G / tot
+    G[G < SAMPLE_SHARE_MIN * tot] = 0.0
+    return T * G / G.sum()
 
 
 def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int = 0, mode: int = 0,
              out=None) -> dict:
-    """Per diverted particle: the drawn deposits d [n_div, 30] and the hits.
+    """Per diverted particle: the drawn deposits d [n_div, 30] and the hits
+    [n_hits, 7] (shower, x, y, z, E, layer, index of the particle in div).
     mode 0 (SAMPLE): Dirichlet split of the MEAN total; mode 1 (MEAN): the
     means.  `out` [n_div, 90] replaces the FP64 network's outputs when given
     (to apply the rule to another implementation's network outputs)."""
@@ -225,5 +230,5 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
                 hits.append((int(div["shower"][i]),
                              div["x"][i] + (zm - zk) * div["ux"][i] / div["uz"][i] + sig * mo[0],
                              div["y"][i] + (zm - zk) * div["uy"][i] / div["uz"][i] + sig * mo[1], zm, d[i, j],
-                             l0 + j))
-    return dict(d=d, out=out, hits=np.array(hits).reshape(-1, 6))
+                             l0 + j, i))
+    return dict(d=d, out=out, hits=np.array(hits).reshape(-1, 7))

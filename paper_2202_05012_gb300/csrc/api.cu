@@ -100,6 +100,7 @@ struct supa_batch {
     uint32_t *d_scount = nullptr, *d_scursor = nullptr, *d_tot = nullptr;
     int64_t *d_soff = nullptr;
     float4 *d_sur_hits = nullptr;
+    unsigned long long *d_sur_tags = nullptr;  // lineage tags of the surrogate hits (record_tags)
     double *d_sur_leak = nullptr;
     unsigned long long *d_scan_tmp2 = nullptr;
     int64_t n_diverted = 0;
@@ -305,7 +306,7 @@ int supa_destroy_geometry(supa_geometry *g) {
 
 static void free_hybrid(supa_batch *b) {
     void *ptrs[] = {b->d_sq_rec, b->d_sq_feat, b->d_dep, b->d_pcnt, b->d_sq_count, b->d_scount, b->d_scursor, b->d_tot,
-                    b->d_soff, b->d_sur_hits, b->d_sur_leak, b->d_scan_tmp2};
+                    b->d_soff, b->d_sur_hits, b->d_sur_tags, b->d_sur_leak, b->d_scan_tmp2};
     for (void *p : ptrs) cudaFree(p);
     surrogate_infer_free(&b->inf);
     b->d_sq_rec = nullptr;
@@ -315,6 +316,7 @@ static void free_hybrid(supa_batch *b) {
     b->d_scount = b->d_scursor = b->d_tot = nullptr;
     b->d_soff = nullptr;
     b->d_sur_hits = nullptr;
+    b->d_sur_tags = nullptr;
     b->d_sur_leak = nullptr;
     b->d_scan_tmp2 = nullptr;
     b->sur = nullptr;
@@ -478,6 +480,8 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     return SUPA_OK;
 }
 
+static SurParams sur_params(const supa_batch *b, uint64_t seed, uint64_t shower_id_base);
+
 int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64_t seed, uint64_t shower_id_base,
                   void *stream) {
     if (!b || (!prim_dev && n > 0)) return fail(SUPA_ERR_INVALID_ARG, "supa_simulate: null argument");
@@ -547,6 +551,17 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     }
     // hybrid: network over the queue, deposits, surrogate hit segments
     SUPA_CUDA(surrogate_infer_run(b->sur, &b->inf, b->d_sq_feat, b->d_sq_count, st));
+    const SurParams sp = sur_params(b, seed, shower_id_base);
+    SUPA_CUDA(launch_sur_deposits(sp, st));
+    SUPA_CUDA(launch_scan_counts(b->d_scount, n, b->d_soff, b->d_scan_tmp2, st));
+    SUPA_CUDA(launch_sur_hits(sp, st));
+    SUPA_CUDA(launch_add_counts(b->d_hit_count, b->d_scount, n, b->d_tot, st));
+    SUPA_CUDA(launch_scan_counts(b->d_tot, n, b->d_offsets, b->d_scan_tmp, st));
+    return SUPA_OK;
+}
+
+// Kernel arguments of the surrogate side of a hybrid batch.
+static SurParams sur_params(const supa_batch *b, uint64_t seed, uint64_t shower_id_base) {
     SurParams sp{};
     sp.mode = b->sur_mode;
     sp.rec = b->d_sq_rec;
@@ -568,12 +583,8 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     sp.soff = b->d_soff;
     sp.scursor = b->d_scursor;
     sp.hits = b->d_sur_hits;
-    SUPA_CUDA(launch_sur_deposits(sp, st));
-    SUPA_CUDA(launch_scan_counts(b->d_scount, n, b->d_soff, b->d_scan_tmp2, st));
-    SUPA_CUDA(launch_sur_hits(sp, st));
-    SUPA_CUDA(launch_add_counts(b->d_hit_count, b->d_scount, n, b->d_tot, st));
-    SUPA_CUDA(launch_scan_counts(b->d_tot, n, b->d_offsets, b->d_scan_tmp, st));
-    return SUPA_OK;
+    sp.tags = b->d_sur_tags;
+    return sp;
 }
 
 int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity, int32_t mode) {
@@ -599,6 +610,7 @@ int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_
     if (e == cudaSuccess) e = dalloc(&b->d_tot, n);
     if (e == cudaSuccess) e = dalloc(&b->d_soff, n + 1);
     if (e == cudaSuccess) e = dalloc(&b->d_sur_hits, (size_t)cap * kSurLayers);
+    if (e == cudaSuccess && b->tags) e = dalloc(&b->d_sur_tags, (size_t)cap * kSurLayers);
     if (e == cudaSuccess) e = dalloc(&b->d_sur_leak, n);
     if (e == cudaSuccess) e = dalloc(&b->d_scan_tmp2, scan_tmp_elems(n) + 1);
     if (e != cudaSuccess) {
@@ -658,6 +670,24 @@ int supa_export_diverted(supa_batch *b, supa_primary *out_dev, int64_t capacity,
     SUPA_CUDA(cudaStreamSynchronize(st));
     const int64_t n = std::min<int64_t>((int64_t)h, (int64_t)b->sq_cap);
     SUPA_CUDA(launch_export_diverted(b->d_sq_rec, std::min(n, capacity), b->d_prim, out_dev, st));
+    SUPA_CUDA(cudaStreamSynchronize(st));
+    *n_out = n;
+    return SUPA_OK;
+}
+
+int supa_export_surrogate(supa_batch *b, supa_diverted_record *out_dev, int64_t capacity, int64_t *n_out,
+                          void *stream) {
+    if (!b || !n_out || capacity < 0 || (capacity > 0 && !out_dev))
+        return fail(SUPA_ERR_INVALID_ARG, "supa_export_surrogate: bad argument");
+    *n_out = 0;
+    if (!b->sur) return fail(SUPA_ERR_INVALID_ARG, "supa_export_surrogate: the batch is not in hybrid mode");
+    if (b->last_n < 0) return fail(SUPA_ERR_NOT_READY, "no simulation has been enqueued on this batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    SUPA_CUDA(cudaMemcpyAsync(&h, b->d_sq_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SUPA_CUDA(cudaStreamSynchronize(st));
+    const int64_t n = std::min<int64_t>((int64_t)h, (int64_t)b->sq_cap);
+    SUPA_CUDA(launch_export_surrogate(sur_params(b, 0, 0), std::min(n, capacity), out_dev, st));
     SUPA_CUDA(cudaStreamSynchronize(st));
     *n_out = n;
     return SUPA_OK;
@@ -829,6 +859,7 @@ static int fetch_common(supa_batch *b, int64_t first, int64_t max_hits, void *ds
         p.src.sur_count = b->d_scount;
     }
     p.tag_pool = tags ? b->d_tags : nullptr;
+    p.sur_tags = tags && b->sur ? b->d_sur_tags : nullptr;
     p.n_showers = b->last_n;
     if (dev) {
         p.first = first;

@@ -37,9 +37,10 @@ __global__ void supa_fetch_kernel(const FetchParams p, const int64_t *canon) {
             for (int j = lane; j < it.seg_len; j += 32) {
                 const int64_t gidx = s0 + i0 + j;
                 if (gidx < lo_hit || gidx >= hi_hit) continue;
-                if (p.dst_tags)  // surrogate hits carry no lineage: tag 0
+                if (p.dst_tags)
                     p.dst_tags[gidx - lo_hit] =
-                        it.phase == 0 ? p.tag_pool[(size_t)(it.seg_ptr - p.src.pool) + j] : 0ull;
+                        it.phase == 0 ? p.tag_pool[(size_t)(it.seg_ptr - p.src.pool) + j]
+                                      : (p.sur_tags ? p.sur_tags[(size_t)(it.seg_ptr - p.src.sur_hits) + j] : 0ull);
                 else
                     p.dst[gidx - lo_hit] = it.seg_ptr[j];
             }

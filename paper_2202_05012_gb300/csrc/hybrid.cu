@@ -6,12 +6,15 @@
 // distributions for the queue (means mu_j and log-variances s_j of the
 // deposit fraction of layer start + j, mean lateral distances rho_j), these
 // kernels
-//   1. take d_j = E max(0, mu_j) (MEAN) or draw d_j from the log-normal with
-//      mean E mu_j and variance E^2 exp(s_j) and rescale the draws to the
-//      MEAN total (SAMPLE; standard normals from Philox stream tag 1, keyed
-//      by shower, slice and lineage, so the draw is replayable), truncated
-//      at the detector's back and scaled down when they add up to more than
-//      E; the rest of E is booked as surrogate leakage;
+//   1. take d_j = E max(0, mu_j) (MEAN), or split the MEAN total
+//      T = sum_j max(0, mu_j) over the layers by a Dirichlet draw whose means
+//      are the MEAN shares and whose concentration c matches the predicted
+//      variances exp(s_j) (SAMPLE: d_j = E T G_j / sum G, G_j ~ Gamma(c m_j)
+//      by Marsaglia and Tsang's method on Philox stream tag 3, keyed by
+//      shower, slice and lineage, so the draw is replayable; every layer's
+//      expected deposit is its MEAN deposit), truncated at the detector's
+//      back and scaled down when they add up to more than E; the rest of E
+//      is booked as surrogate leakage;
 //   2. add the deposits to the shower's FP64 layer sums and count one hit per
 //      non-empty layer;
 //   3. after a scan of the counts, write the hits -- one per layer, at the
@@ -28,28 +31,55 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Standard normals n_j of a diverted particle, j = 0..31 (the layer offset):
-// Box-Muller on Philox block j / 4 of its stream (tag 1, keyed by shower,
-// slice and lineage); words 2p and 2p + 1 of block b give the pair
-// (n_{4b+2p}, n_{4b+2p+1}) = rad (cos, sin)(2 pi u2).  block_normals forms
-// the pairs of block b that `want` names (bit p: pair p) from one Philox call.
-__device__ void block_normals(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed, int b,
-                              unsigned want, float (&n)[4]) {
-    const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (1u << 16) | ((uint32_t)b << 20), lin_lo, lin_hi),
-                                  (uint32_t)seed, (uint32_t)(seed >> 32));
-#pragma unroll
-    for (int pr = 0; pr < 2; ++pr) {
-        if (!(want & (1u << pr))) continue;
-        const uint32_t w0 = pr ? r.z : r.x, w1 = pr ? r.w : r.y;
-        const float u1 = (float)((w0 >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
-        const float u2 = u24(w1);
-        const float rad = sqrtf(-2.0f * logf(u1));
-        float sn, cs;
-        sincospif(2.0f * u2, &sn, &cs);
-        n[2 * pr] = rad * cs;
-        n[2 * pr + 1] = rad * sn;
+// Gamma(alpha, 1) variate of layer j of a diverted particle: Marsaglia and
+// Tsang, "A simple method for generating gamma variables" (ACM TOMS 26(3),
+// 2000), for shape a = alpha, or a = alpha + 1 times u3^(1/alpha) when
+// alpha < 1.  Attempt t (0..3) takes the Philox block with counter
+// (shower id, slice | 3 << 16 | (4 j + t) << 20, lineage lo, lineage hi):
+// a standard normal x from words 0 and 1 (Box-Muller), the uniform of the
+// accept test from word 2, u3 from word 3.  The accept test is evaluated
+// with explicitly rounded float32 operations in a fixed order (no
+// contraction into fused multiply-adds), so that another implementation
+// can take the same decision; four rejections in a row give the mean alpha.
+__device__ float gamma_variate(float alpha, uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed,
+                               int j) {
+    const bool boost = alpha < 1.0f;
+    const float a = boost ? __fadd_rn(alpha, 1.0f) : alpha;
+    const float d = __fsub_rn(a, 0.333333343f);  // float32(1/3)
+    const float c = __fdiv_rn(1.0f, __fsqrt_rn(__fmul_rn(9.0f, d)));
+    for (int t = 0; t < 4; ++t) {
+        const uint4 r = philox4x32_10(
+            make_uint4(sid, (uint32_t)k | (3u << 16) | ((uint32_t)(4 * j + t) << 20), lin_lo, lin_hi),
+            (uint32_t)seed, (uint32_t)(seed >> 32));
+        const float u1 = (float)((r.x >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
+        const float u2 = u24(r.y);
+        const float rad = __fsqrt_rn(__fmul_rn(-2.0f, logf(u1)));
+        const float x = __fmul_rn(rad, cospif(__fmul_rn(2.0f, u2)));
+        const float t1 = __fadd_rn(1.0f, __fmul_rn(c, x));
+        if (!(t1 > 0.0f)) continue;
+        const float v = __fmul_rn(__fmul_rn(t1, t1), t1);
+        const float u = (float)((r.z >> 8) + 1u) * (1.0f / 16777216.0f);
+        const float rhs = __fadd_rn(__fmul_rn(0.5f, __fmul_rn(x, x)),
+                                    __fmul_rn(d, __fadd_rn(__fsub_rn(1.0f, v), logf(v))));
+        if (!(logf(u) < rhs)) continue;
+        float g = __fmul_rn(d, v);
+        if (boost) {
+            const float u3 = (float)((r.w >> 8) + 1u) * (1.0f / 16777216.0f);
+            g *= powf(u3, __fdiv_rn(1.0f, alpha));
+        }
+        return g;
     }
+    return alpha;
 }
+
+// Dirichlet concentration bounds of the SAMPLE split: below kSampleCMin the
+// concentration is raised to it; above kSampleCMax the spread is negligible
+// and the MEAN shares are taken without a draw.
+constexpr float kSampleCMin = 1.0f, kSampleCMax = 1.0e4f;
+// A layer whose gamma variate is below this fraction of the particle's sum
+// of variates gets no deposit (such shares are where float32 variates
+// underflow).
+constexpr float kShareMin = 1.0e-9f;
 
 // The standard normal pair (m1, m2) displacing all hits of a diverted
 // particle: Box-Muller on words (w0, w1) of the Philox block with counter
@@ -143,44 +173,66 @@ __global__ void __launch_bounds__(kDepWarps * 32) sur_deposits(const SurParams p
                 for (int t = 0; t < 4; ++t)
                     if (4 * q + t < kSurLayers) v[4 * q + t] = mq[t];
             }
-            float sum = 0.0f, sum_mean = 0.0f;
+            // MEAN fractions of the layers inside the detector
+            float T = 0.0f;
 #pragma unroll
-            for (int b = 0; b < (kSurLayers + 3) / 4; ++b) {
-                // the normals of this block of 4 layers, one Philox block and
-                // one Box-Muller pair per 2 layers that draw
-                float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                if (kSample) {
-                    unsigned want = 0u;
+            for (int j = 0; j < kSurLayers; ++j) {
+                v[j] = j < nj ? fmaxf(0.0f, v[j]) : 0.0f;
+                T += v[j];
+            }
+            if (kSample && T > 0.0f) {
+                // concentration matched to the predicted variances of the layers with a mean
+                const float rT = 1.0f / T;
+                float q = 0.0f, V = 0.0f;
 #pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        if (4 * b + t < kSurLayers && 4 * b + t < nj && v[4 * b + t] > 0.0f) want |= 1u << (t >> 1);
-                    if (want)
-                        block_normals((uint32_t)(p.shower_id_base + sh), r.k, r.lin_lo, r.lin_hi, p.seed, b, want, z);
-                }
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int j = 4 * b + t;
-                    if (j >= kSurLayers) break;
-                    float f = j < nj ? fmaxf(0.0f, v[j]) : 0.0f;
-                    if (kSample) {
-                        sum_mean += E * f;
-                        if (f > 0.0f) {
-                            // log-normal with mean mu and variance exp(s) (a^2 capped at 4)
-                            const float sg = __ldg(p.out + (size_t)i * p.out_ld + kSurLayers + j);
-                            const float a2 = fminf(4.0f, log1pf(expf(sg) / (f * f)));
-                            f *= expf(fmaf(sqrtf(a2), z[t], -0.5f * a2));
-                        }
+                for (int j = 0; j < kSurLayers; ++j) {
+                    if (v[j] > 0.0f) {
+                        const float m = v[j] * rT;
+                        q = fmaf(m, m, q);
+                        V += expf(__ldg(p.out + (size_t)i * p.out_ld + kSurLayers + j));
                     }
-                    v[j] = E * f;
-                    sum += v[j];
                 }
+                const float num = T * T * (1.0f - q);
+                if (V > 0.0f && num <= (kSampleCMax + 1.0f) * V) {
+                    const float cm = fmaxf(kSampleCMin, num / V - 1.0f) * rT;
+                    // one layer at a time, the variates staged in this lane's
+                    // row of shared memory (one copy of the sampler's code:
+                    // unrolled over 30 layers it overflows the instruction cache)
+                    float gs = 0.0f;
+#pragma unroll 1
+                    for (int j = 0; j < nj; ++j) {
+                        const float mu = __ldg(p.out + (size_t)i * p.out_ld + j);
+                        const float G = mu > 0.0f ? gamma_variate(cm * mu, (uint32_t)(p.shower_id_base + sh), r.k,
+                                                                  r.lin_lo, r.lin_hi, p.seed, j)
+                                                  : 0.0f;
+                        stg[lane][j] = G;
+                        gs += G;
+                    }
+                    if (gs > 0.0f) {
+                        // shares below kShareMin of the sum get nothing
+                        const float gmin = kShareMin * gs;
+                        float gk = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < kSurLayers; ++j) {
+                            float G = j < nj ? stg[lane][j] : 0.0f;
+                            if (G < gmin) G = 0.0f;
+                            v[j] = G;
+                            gk += G;
+                        }
+                        const float sc = T / gk;
+#pragma unroll
+                        for (int j = 0; j < kSurLayers; ++j) v[j] *= sc;
+                    }
+                }
+            }
+            float sum = 0.0f;
+#pragma unroll
+            for (int j = 0; j < kSurLayers; ++j) {
+                v[j] *= E;
+                sum += v[j];
             }
             float scale = 1.0f;
-            if (kSample) {  // the draws keep their shape and take the MEAN total
-                if (sum > 0.0f) scale = sum_mean / sum;
-                sum = sum_mean;
-            }
-            if (sum > E) scale *= E / sum;
+            if (sum > E) scale = E / sum;
             float2 *d2 = reinterpret_cast<float2 *>(p.dep + (size_t)i * kSurLayers);
             pleak = (long long)fixed32(E);
 #pragma unroll
@@ -241,9 +293,11 @@ __global__ void sur_hits(const SurParams p) {
         unsigned c = 0;
         float r_x = 0.f, r_y = 0.f, r_tx = 0.f, r_ty = 0.f, r_zk = 0.f;
         float2 r_m = make_float2(0.f, 0.f);
+        unsigned long long r_tag = 0;
         if (valid) {
             const SurRec r = p.rec[i];
             sh = (int)r.shower;
+            r_tag = (1ull << 63) | ((unsigned long long)r.lin_hi << 32) | r.lin_lo;
             c = p.pcnt[i];
             if (c) r_m = offset_normals((uint32_t)(p.shower_id_base + r.shower), r.k, r.lin_lo, r.lin_hi, p.seed);
             const GeomDev &g = p.geoms[p.prim[r.shower].geom & 0xFFFFu];
@@ -298,12 +352,14 @@ __global__ void sur_hits(const SurParams p) {
                             ty = __shfl_sync(kFull, r_ty, k), m1 = __shfl_sync(kFull, r_m.x, k),
                             m2 = __shfl_sync(kFull, r_m.y, k);
                 const unsigned nz = __ballot_sync(kFull, d[u] > 0.0f);
+                const unsigned long long tag = p.tags ? __shfl_sync(kFull, r_tag, k) : 0ull;
                 if (d[u] > 0.0f) {
                     const float zm = zmid[u];
                     const float dz = zm - zk;
                     const float sig = fmaxf(0.0f, rho[u]) * 0.79788456080286536f;  // sqrt(2 / pi)
                     p.hits[at + __popc(nz & lt)] =
                         make_float4(fmaf(sig, m1, fmaf(dz, tx, x)), fmaf(sig, m2, fmaf(dz, ty, y)), zm, d[u]);
+                    if (p.tags) p.tags[at + __popc(nz & lt)] = tag;
                 }
             }
         }
@@ -358,6 +414,39 @@ __global__ void export_diverted(const SurRec *rec, int64_t n, const supa_primary
         q.geom = (prim[r.shower].geom & 0xFFFFu) | ((uint32_t)r.k << 16);
         out[i] = q;
     }
+}
+
+// Per diverted particle: its queue record, network outputs, deposits and
+// hit count as one supa_diverted_record.
+__global__ void export_surrogate(const SurParams p, int64_t n, supa_diverted_record *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const SurRec r = p.rec[i];
+        supa_diverted_record &o = out[i];
+        o.shower = r.shower;
+        o.slice = r.k;
+        o.layer = r.layer;
+        o.x = r.x;
+        o.y = r.y;
+        o.tx = r.tx;
+        o.ty = r.ty;
+        o.E = r.E;
+        o.lineage = ((uint64_t)r.lin_hi << 32) | r.lin_lo;
+        const float *row = p.out + (size_t)i * p.out_ld;
+        for (int j = 0; j < kSurLayers; ++j) {
+            o.mu[j] = row[j];
+            o.s[j] = row[kSurLayers + j];
+            o.rho[j] = row[2 * kSurLayers + j];
+            o.dep[j] = p.dep[(size_t)i * kSurLayers + j];
+        }
+        o.n_hits = p.pcnt[i];
+        o.reserved = 0;
+    }
+}
+
+cudaError_t launch_export_surrogate(const SurParams &p, int64_t n, supa_diverted_record *out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    export_surrogate<<<(unsigned)std::min<int64_t>((n + 127) / 128, 8192), 128, 0, st>>>(p, n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_export_diverted(const SurRec *rec, int64_t n, const supa_primary *prim, supa_primary *out,

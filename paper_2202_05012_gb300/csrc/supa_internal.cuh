@@ -124,11 +124,13 @@ struct SurParams {
     const int64_t *soff;    // [n+1] exclusive scan of scount
     uint32_t *scursor;      // [n]
     float4 *hits;           // surrogate hit segments
+    unsigned long long *tags;  // their lineage tags (bit 63 set), or null
 };
 cudaError_t launch_sur_deposits(const SurParams &p, cudaStream_t st);
 cudaError_t launch_sur_hits(const SurParams &p, cudaStream_t st);
 cudaError_t launch_export_diverted(const SurRec *rec, int64_t n, const supa_primary *prim, supa_primary *out,
                                    cudaStream_t st);
+cudaError_t launch_export_surrogate(const SurParams &p, int64_t n, supa_diverted_record *out, cudaStream_t st);
 cudaError_t launch_add_counts(const uint32_t *a, const uint32_t *b, int64_t n, uint32_t *out, cudaStream_t st);
 cudaError_t launch_training_set(const supa_primary *prim, int64_t n, const GeomDev *geoms, const int8_t *s2l,
                                 const LayerInfo *linfo, const double *lsum, int stride, float e_s, float *x, float *y,
@@ -331,6 +333,7 @@ struct FetchParams {
     int64_t first, count;
     float4 *dst;
     unsigned long long *dst_tags;
+    const unsigned long long *sur_tags;  // tags of the surrogate hits (hybrid path with record_tags)
 };
 cudaError_t launch_fetch(const FetchParams &p, cudaStream_t st);
 

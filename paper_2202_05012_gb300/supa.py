@@ -31,7 +31,7 @@ EXPORTED = (
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
     "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc", "supa_export_diverted",
     "supa_shower_shapes", "supa_layer_images_cells", "supa_voxelize_layers", "supa_voxelize_fetch",
-    "supa_check_wait_expiry",
+    "supa_check_wait_expiry", "supa_export_surrogate",
 )
 
 
@@ -127,6 +127,7 @@ def lib(build_if_missing: bool = True):
         L.supa_profiles.argtypes = [_VP, _I64, _I64, ctypes.c_int32, ctypes.c_float, _VP, _VP, _VP]
         L.supa_shower_offsets_noalloc.argtypes = [_VP, _I64, _VP, _VP]
         L.supa_export_diverted.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I64), _VP]
+        L.supa_export_surrogate.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I64), _VP]
         L.supa_shower_shapes.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP]
         L.supa_layer_images_cells.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
         L.supa_voxelize_layers.argtypes = [_VP, _I64, _I64, _VP, ctypes.c_int32, _VP, ctypes.c_int32, _VP, _VP,
@@ -415,6 +416,27 @@ def supa_export_diverted(b: int, out_dev=None, stream=None) -> int:
     cap = 0 if out_dev is None else out_dev.numel() * out_dev.element_size() // 24
     _check(lib().supa_export_diverted(b, _ptr(out_dev) if cap else None, cap, ctypes.byref(n), _stream(stream)),
            "supa_export_diverted")
+    return int(n.value)
+
+
+# supa_diverted_record of include/supa.h (528 bytes)
+DIVERTED_RECORD_DTYPE = np.dtype([
+    ("shower", "<u4"), ("slice", "<i4"), ("layer", "<i4"), ("x", "<f4"), ("y", "<f4"), ("tx", "<f4"),
+    ("ty", "<f4"), ("E", "<f4"), ("lineage", "<u8"), ("mu", "<f4", 30), ("s", "<f4", 30), ("rho", "<f4", 30),
+    ("dep", "<f4", 30), ("n_hits", "<u4"), ("reserved", "<u4")])
+assert DIVERTED_RECORD_DTYPE.itemsize == 528
+
+
+def supa_export_surrogate(b: int, out_dev=None, stream=None) -> int:
+    """Per diverted particle of the last hybrid run: key, state, network
+    outputs and deposits (supa_diverted_record) into out_dev (a uint8 tensor
+    of 528-byte records, or None to only count); returns how many the queue
+    held."""
+    n = _I64(0)
+    size = DIVERTED_RECORD_DTYPE.itemsize
+    cap = 0 if out_dev is None else out_dev.numel() * out_dev.element_size() // size
+    _check(lib().supa_export_surrogate(b, _ptr(out_dev) if cap else None, cap, ctypes.byref(n), _stream(stream)),
+           "supa_export_surrogate")
     return int(n.value)
 
 

@@ -137,3 +137,54 @@ def train(data: dict, epochs: int = 20, batch: int = 16384, lr: float = 1e-3, se
     return net, dict(epochs=epochs, batch=batch, lr=lr, lr_final=lr_final, steps_per_epoch=steps, seconds=ms / 1000.0,
                      seconds_per_epoch=ms / 1000.0 / epochs, loss_per_epoch=per_epoch,
                      tflops=flops / (ms / 1000.0) / 1e12, samples_per_s=steps * batch * epochs / (ms / 1000.0))
+
+
+# Profile comparison of a hybrid run against the plain run on the same
+# showers.  Lateral profiles are taken in PROFILE_BINS rings of width
+# PROFILE_RMAX / PROFILE_BINS around the incidence axis, the last ring open
+# to infinity, so that every deposit is counted.
+PROFILE_BINS, PROFILE_RMAX = 129, 16.0
+PROFILE_GROUP = 0.02
+
+
+def energy_groups(ref, frac: float = PROFILE_GROUP):
+    """Consecutive bins of the reference profile merged into groups that each
+    hold at least `frac` of its total (greedily from the first bin; the
+    remainder joins the last group): returns the group index of every bin.
+    The groups cover every bin, so an error taken over them covers all the
+    energy."""
+    ref = np.asarray(ref, dtype=np.float64)
+    tot = ref.sum()
+    gid = np.zeros(len(ref), dtype=np.int64)
+    g, acc = 0, 0.0
+    for i, v in enumerate(ref):
+        gid[i] = g
+        acc += v
+        if acc >= frac * tot and i < len(ref) - 1:
+            g, acc = g + 1, 0.0
+    if acc < frac * tot and g > 0:  # the remainder joins the last full group
+        gid[gid == g] = g - 1
+    return gid
+
+
+def profile_errors(ref, got, frac: float = PROFILE_GROUP) -> dict:
+    """Largest relative deviation of a profile from the reference over groups
+    of consecutive bins holding >= frac of the reference's energy each (all
+    bins, all the energy), for the longitudinal (per layer) and the lateral
+    (per ring, last ring open) mean profiles; the relative deviation of the
+    mean total deposit; and, for reference, the largest per-bin deviation
+    over single layers holding >= 0.5 % of the energy."""
+    (rl, rr), (gl, gr) = ref, got
+
+    def grouped(a, b):
+        gid = energy_groups(a, frac)
+        sa = np.bincount(gid, weights=a)
+        sb = np.bincount(gid, weights=b)
+        return float(np.max(np.abs(sb - sa) / sa)), int(gid.max() + 1)
+
+    lo, n_lo = grouped(rl, gl)
+    la, n_la = grouped(rr, gr)
+    m = rl >= 0.005 * rl.sum()
+    return {"longitudinal": lo, "lateral": la, "total_deposit": float(abs(gl.sum() - rl.sum()) / rl.sum()),
+            "group_fraction": frac, "groups": [n_lo, n_la], "energy_covered": 1.0,
+            "longitudinal_per_layer": float(np.max(np.abs(gl[m] - rl[m]) / rl[m]))}

@@ -1,9 +1,10 @@
 """What the trained surrogate gains over the method without it, on the
 30-layer workload (E U[1,100] GeV, 0-30 deg) at E_s = 2 GeV: the hybrid path steps a small fraction of the
-particles the plain path steps, and its shower profiles stay within a few
-per cent of the plain ones -- which an untrained network of the same shape
-does not achieve."""
-import numpy as np
+particles the plain path steps, and its longitudinal and lateral shower
+profiles stay within 2 % of the plain ones in both modes (lateral: largest
+deviation over groups of rings holding >= 2 % of the energy each, every ring
+included; longitudinal: over the layers holding >= 0.5 % of the energy) --
+which an untrained network of the same shape does not achieve."""
 import pytest
 
 from paper_2202_05012_gb300 import inputs
@@ -14,15 +15,15 @@ pytestmark = pytest.mark.gpu
 
 E_S = 2.0
 N = 20_000
-BINS, R_MAX = 64, 8.0
+BINS, R_MAX = T.PROFILE_BINS, T.PROFILE_RMAX
 
 
-def _run(gh, d, mean_e, net):
+def _run(gh, d, mean_e, net, mode=S.SUPA_SURROGATE_MEAN):
     import torch
     b = S.supa_batch_create([gh], N, {"max_hits": int(N * 60 * mean_e) + (8 << 20), "lpt_order": 1})
     try:
         if net is not None:
-            S.supa_batch_set_surrogate(b, net, E_S, int(4 * mean_e / E_S * N) + (1 << 20), S.SUPA_SURROGATE_MEAN)
+            S.supa_batch_set_surrogate(b, net, E_S, int(4 * mean_e / E_S * N) + (1 << 20), mode)
         S.supa_simulate(b, d, N, 7)
         info = S.supa_batch_get_info(b)
         lo = torch.zeros(30, dtype=torch.float64, device="cuda")
@@ -32,11 +33,6 @@ def _run(gh, d, mean_e, net):
         return info.n_steps, lo.cpu().numpy() / N, la.cpu().numpy() / N
     finally:
         S.supa_destroy_batch(b)
-
-
-def _worst(ref, got, thr=0.005):
-    m = ref >= thr
-    return float(np.max(np.abs(got[m] - ref[m]) / ref[m]))
 
 
 def test_trained_network_replaces_most_steps_at_small_profile_error():
@@ -52,6 +48,7 @@ def test_trained_network_replaces_most_steps_at_small_profile_error():
         mean_e = float(p["E"].mean())
         steps_plain, lo_p, la_p = _run(gh, d, mean_e, None)
         steps_h, lo_h, la_h = _run(gh, d, mean_e, net)
+        _, lo_s, la_s = _run(gh, d, mean_e, net, S.SUPA_SURROGATE_SAMPLE)
         _, lo_u, la_u = _run(gh, d, mean_e, untrained)
     finally:
         S.supa_destroy_geometry(gh)
@@ -59,8 +56,10 @@ def test_trained_network_replaces_most_steps_at_small_profile_error():
         S.supa_surrogate_destroy(untrained)
     # the network replaces most of the stepping
     assert steps_h < 0.2 * steps_plain, (steps_h, steps_plain)
-    # ... at small profile error (lateral over the imaged radius, last bin = beyond)
-    errs = (_worst(lo_p, lo_h), _worst(la_p[:-1], la_h[:-1]), abs(lo_h.sum() / lo_p.sum() - 1))
-    assert errs[0] < 0.03 and errs[1] < 0.03 and errs[2] < 0.005, errs
+    # ... at small profile error, in both modes
+    for lo, la in ((lo_h, la_h), (lo_s, la_s)):
+        e = T.profile_errors((lo_p, la_p), (lo, la))
+        assert e["longitudinal_per_layer"] < 0.02 and e["lateral"] < 0.02 and e["total_deposit"] < 0.005, e
     # which the same network untrained is far from
-    assert _worst(lo_p, lo_u) > 0.1 or _worst(la_p[:-1], la_u[:-1]) > 0.1
+    e = T.profile_errors((lo_p, la_p), (lo_u, la_u))
+    assert e["longitudinal"] > 0.1 or e["lateral"] > 0.1, e
