@@ -6,7 +6,9 @@ returns them):
   1. features: log(E / E_s), direction cosines, position of the slice in its
      layer (k - first slice) / slices in the layer, layers left from the
      particle's layer to the back over 30 (capped at 1);
-  2. the FP64 network (oracle.mlp) gives mu_j and s_j, j = 0..29;
+  2. the FP64 network (oracle.mlp) gives o_j, s_j and rho_j, j = 0..29;
+     the mean deposit fraction of layer start + j is mu_j = exp(o_j - 4)
+     (oracle.mlp.deposit_means);
   3. SAMPLE draws: gamma variates by Marsaglia and Tsang's method ("A
      simple method for generating gamma variables", ACM TOMS 26(3), 2000)
      for shape a = alpha (alpha >= 1) or a = alpha + 1 (alpha < 1, then
@@ -22,21 +24,24 @@ returns them):
      mean alpha.  The accept test is taken in float32 with the operations in
      the order written (the precision the library takes it in); the value is
      formed in FP64;
-  4. d_j = E f_j for layers inside the detector.  MEAN: f_j = max(0, mu_j).
-     SAMPLE: the total T = sum_j max(0, mu_j) is kept and its split over the
-     layers is drawn from a Dirichlet distribution whose means are the MEAN
-     shares m_j = max(0, mu_j) / T, so every layer's expected deposit is
-     exactly its MEAN deposit: f_j = T G_j / sum_i G_i with independent
-     G_j ~ Gamma(alpha_j = c m_j) (gamma_variate).  The concentration c is
+  4. d_j = E f_j for layers inside the detector.  MEAN: f_j = mu_j, and
+     0 where mu_j < 10^-6 (a layer that would get less than a millionth of
+     the particle's energy gets no hit).  SAMPLE: the total T = sum_j f_j of
+     the MEAN fractions is kept and its split over their layers is drawn
+     from a Dirichlet distribution whose means are the MEAN shares
+     m_j = f_j / T, so every layer's expected deposit is its MEAN deposit:
+     f_j = T G_j / sum_i G_i with independent G_j ~ Gamma(alpha_j = c m_j)
+     (gamma_variate); a layer whose drawn share T G_j / sum_i G_i is below
+     10^-6 gets nothing and the sum over the others normalises (the draws'
+     only departure from the MEAN expectation, at most 3 10^-5 of E per
+     particle moved between layers).  The concentration c is
      matched to the predicted spreads: a Dirichlet share has variance
      m_j (1 - m_j) / (c + 1), so T^2 (1 - sum m_j^2) / (c + 1) is set equal
-     to V = sum exp(s_j) over the layers with mu_j > 0 (the predicted
+     to V = sum exp(s_j) over the layers with f_j > 0 (the predicted
      variances of their deposit fractions), c raised to 1 where it falls
      below; where c exceeds 10^4 (V = 0 included) the spread is negligible
-     and the MEAN fractions are taken without a draw.  A layer whose G_j is
-     below 10^-9 of sum_i G_i gets nothing (the sum over the others
-     normalises; such shares lie where float32 gamma variates underflow).
-     Both: scaled by E / sum d when the sum exceeds E;
+     and the MEAN fractions are taken without a draw.  Both: scaled by
+     E / sum d when the sum exceeds E;
   5. one hit per layer with d_j > 0 at the layer's mid depth, displaced
      from the particle's straight-line position by sigma_j (m1, m2):
      sigma_j = max(0, rho_j) sqrt(2 / pi), so that each layer's displacement
@@ -154,7 +159,7 @@ def gamma_variate(alpha: float, shower_id: int, k: int, lineage: int, j: int, se
 
 
 SAMPLE_C_MIN, SAMPLE_C_MAX = 1.0, 1.0e4
-SAMPLE_SHARE_MIN = 1.0e-9
+FRACTION_MIN = 1.0e-6
 
 
 def sample_concentration(f: np.ndarray, s: np.ndarray) -> float:
@@ -188,8 +193,11 @@ def sample_fractions(f: np.ndarray, s: np.ndarray, shower_id: int, k: int, linea
     tot = G.sum()
     if tot <= 0:
         return f.copy()
-    G[G < SAMPLE_SHARE_MIN * tot] = 0.0
-    return T * G / G.sum()
+    G[T * G / tot < FRACTION_MIN] = 0.0
+    kept = G.sum()
+    if kept <= 0:
+        return f.copy()
+    return T * G / kept
 
 
 def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int = 0, mode: int = 0,
@@ -213,7 +221,8 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
         l0 = int(div["layer"][i])
         E = div["E"][i]
         inside = l0 + np.arange(30) < L
-        f = np.where(inside, np.maximum(0.0, out[i, :30]), 0.0)
+        mu = mlp.deposit_means(out[i:i + 1])[0]
+        f = np.where(inside & (mu >= FRACTION_MIN), mu, 0.0)
         if mode != 1:
             f = sample_fractions(f, out[i, 30:60], shower_id_base + int(div["shower"][i]), int(div["k"][i]),
                                  int(div["lineage"][i]), seed)

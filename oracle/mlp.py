@@ -3,10 +3,13 @@
 The surrogate has no counterpart in the SUPA paper: it is a small MLP that
 stands in for the low-energy tail of a shower (sub-showers below a cutoff
 energy E_s).  Architecture: 6 inputs -> 3 hidden layers of 256 with GELU
-(exact form x * Phi(x)) -> 90 outputs = 30 means mu_j and 30 log-variances
-s_j of the per-layer deposit fractions, and 30 mean lateral distances rho_j
-of each layer's deposits from the sub-shower's axis, layers counted from the
-sub-shower's start layer.  Targets Y = [y_j, R_j]: deposit fractions and
+(exact form x * Phi(x)) -> 90 outputs o = 30 log-link outputs o_j of the
+means mu_j = exp(o_j - MU_SHIFT) and 30 log-variances s_j of the per-layer
+deposit fractions, and 30 mean lateral distances rho_j of each layer's
+deposits from the sub-shower's axis, layers counted from the sub-shower's
+start layer.  The log link keeps every mean positive and makes a rounding
+error of o_j a relative error of mu_j, so layers a sub-shower does not
+reach get means that go to zero instead of a rounding-noise floor.  Targets Y = [y_j, R_j]: deposit fractions and
 energy-weighted mean distances.  Loss: Gaussian negative log-likelihood of
 the fractions plus the fraction-weighted squared error of the distances,
 averaged over layers and samples,
@@ -24,6 +27,7 @@ import numpy as np
 from scipy.special import erf
 
 N_IN, N_HID, N_OUT, N_LAYERS_OUT = 6, 256, 90, 30
+MU_SHIFT = 4.0  # mu_j = exp(o_j - MU_SHIFT): outputs near 0 at initialisation give means near 1/55
 SHAPES = [(N_HID, N_IN), (N_HID, N_HID), (N_HID, N_HID), (N_OUT, N_HID)]
 LAMBDA_R = 1.0  # weight of the lateral term
 
@@ -51,9 +55,14 @@ def forward(params, X):
     return h, (acts, pre)
 
 
+def deposit_means(out):
+    """mu_j = exp(o_j - MU_SHIFT) of the first 30 outputs, [B, 30]."""
+    return np.exp(out[:, :N_LAYERS_OUT] - MU_SHIFT)
+
+
 def _split(out, Y):
     J = N_LAYERS_OUT
-    return out[:, :J], out[:, J:2 * J], out[:, 2 * J:3 * J], Y[:, :J], Y[:, J:2 * J]
+    return deposit_means(out), out[:, J:2 * J], out[:, 2 * J:3 * J], Y[:, :J], Y[:, J:2 * J]
 
 
 def loss(out, Y):
@@ -63,11 +72,11 @@ def loss(out, Y):
 
 
 def loss_grad(out, Y):
-    """d L / d out, [B, 90]."""
+    """d L / d out, [B, 90] (the first 30 columns through the log link)."""
     B = out.shape[0]
     mu, s, rho, y, R = _split(out, Y)
     r = y - mu
-    g_mu = -r * np.exp(-s) / (B * N_LAYERS_OUT)
+    g_mu = -r * np.exp(-s) * mu / (B * N_LAYERS_OUT)  # d mu / d o = mu
     g_s = (0.5 - 0.5 * r * r * np.exp(-s)) / (B * N_LAYERS_OUT)
     g_rho = LAMBDA_R * y * (rho - R) / (B * N_LAYERS_OUT)
     return np.concatenate([g_mu, g_s, g_rho], axis=1)

@@ -15,7 +15,7 @@ import pytest
 from scipy import stats
 
 import oracle
-from oracle import hybrid
+from oracle import hybrid, mlp
 from paper_2202_05012_gb300 import inputs
 
 
@@ -71,10 +71,17 @@ def test_energy_conservation_with_diversion():
     np.testing.assert_allclose(tot, p["E"].astype(np.float64), rtol=1e-12)
 
 
+def _raw_mu(mu):
+    """Network outputs o_j that give the means mu_j = exp(o_j - 4) (a very
+    negative output for mu <= 0: a mean far below every cut)."""
+    mu = np.asarray(mu, dtype=float)
+    return np.where(mu > 0, np.log(np.where(mu > 0, mu, 1.0)) + mlp.MU_SHIFT, -100.0)
+
+
 def _const_net(mu, s, rho=0.0):
     params = inputs.mlp_init(2)
     W4 = np.zeros((90, 256))
-    b4 = np.concatenate([np.full(30, mu), np.full(30, s), np.full(30, rho)])
+    b4 = np.concatenate([np.full(30, _raw_mu(mu)), np.full(30, s), np.full(30, rho)])
     return params[:3] + [(W4, b4)]
 
 
@@ -173,7 +180,7 @@ def _layer_net(mu, s, rho=0.0):
     whatever its inputs."""
     params = inputs.mlp_init(2)
     W4 = np.zeros((90, 256))
-    b4 = np.concatenate([np.asarray(mu, float), np.asarray(s, float), np.full(30, rho)])
+    b4 = np.concatenate([_raw_mu(mu), np.asarray(s, float), np.full(30, rho)])
     return params[:3] + [(W4, b4)]
 
 
@@ -262,3 +269,20 @@ def test_features_follow_their_definition():
     f = hybrid.features(div, g, 1.0)
     np.testing.assert_allclose(f[0], [math.log(0.5), 0.1, 0.2, math.sqrt(0.95), 1 / 3, 29 / 30])
     np.testing.assert_allclose(f[1], [math.log(0.05), 0, 0, 1, 2 / 3, 1 / 30])
+
+
+def test_log_link_means_and_the_millionth_cut():
+    """mu_j = exp(o_j - 4); a layer whose mean fraction is below 10^-6 gets
+    no deposit and no hit in either mode, one just above it does."""
+    out = np.zeros((1, 90))
+    out[0, :3] = [4.0, 4.0 + math.log(0.5), 0.0]
+    np.testing.assert_allclose(mlp.deposit_means(out)[0, :3], [1.0, 0.5, math.exp(-4.0)], rtol=1e-15)
+    g = inputs.supa_d(30)
+    div = _diverted_on_layer0(40)
+    mu = np.full(30, 0.02)
+    mu[3], mu[4] = 0.99e-6, 1.01e-6
+    for mode in (0, 1):
+        dep = hybrid.deposits(div, _layer_net(mu, np.full(30, math.log(1e-10))), g, 1.0, 4, mode=mode)
+        assert np.all(dep["d"][:, 3] == 0) and np.all(dep["d"][:, 4] > 0)
+        assert not np.any(dep["hits"][:, 5] == 3)
+        assert np.sum(dep["hits"][:, 5] == 4) == len(div["E"])

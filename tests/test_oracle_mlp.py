@@ -64,7 +64,7 @@ def test_matches_torch_nn_float64():
         h = lin(h)
         if i < 3:
             h = torch.nn.functional.gelu(h, approximate="none")
-    mu, s, rho = h[:, :30], h[:, 30:60], h[:, 60:]
+    mu, s, rho = torch.exp(h[:, :30] - mlp.MU_SHIFT), h[:, 30:60], h[:, 60:]
     yt, rt = torch.from_numpy(Y[:, :30]), torch.from_numpy(Y[:, 30:])
     tl = torch.mean(0.5 * (yt - mu) ** 2 * torch.exp(-s) + 0.5 * s + 0.5 * mlp.LAMBDA_R * yt * (rho - rt) ** 2)
     tl.backward()
