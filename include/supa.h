@@ -403,16 +403,18 @@ int supa_surrogate_check(supa_surrogate *s);
 
 /* Deposit rule of the hybrid path for layer start + j of a particle of
  * energy E, from the network's mu_j and s_j. */
-/* MEAN: d_j = E max(0, mu_j).  SAMPLE: the MEAN total E T, T = sum_j
- * max(0, mu_j), split over the layers by a Dirichlet draw whose means are the
- * MEAN shares m_j = max(0, mu_j) / T: d_j = E T G_j / sum_i G_i with
- * independent G_j ~ Gamma(c m_j), so every layer's expected deposit is its
- * MEAN deposit and the particle's total is the MEAN total.  The
- * concentration c matches the predicted variances: T^2 (1 - sum m_j^2) /
- * (c + 1) = sum of exp(s_j) over the layers with mu_j > 0, c >= 1; where c
- * would exceed 10^4 the MEAN deposits are taken; a layer whose G_j is below
- * 10^-9 of sum_i G_i gets nothing (the others' sum normalises).  The gamma
- * variates follow
+/* The network's first 30 outputs o_j give the deposit-fraction means
+ * through a log link, mu_j = exp(o_j - 4).  MEAN: d_j = E f_j, f_j = mu_j,
+ * and 0 where mu_j < 10^-6.  SAMPLE: the MEAN total E T, T = sum_j f_j,
+ * split over the layers with f_j > 0 by a Dirichlet draw whose means are the
+ * MEAN shares m_j = f_j / T: d_j = E T G_j / sum_i G_i with independent
+ * G_j ~ Gamma(c m_j), so every layer's expected deposit is its MEAN deposit
+ * and the particle's total is the MEAN total.  The concentration c matches
+ * the predicted variances: T^2 (1 - sum m_j^2) / (c + 1) = sum of exp(s_j)
+ * over the layers with f_j > 0, c >= 1; where c would exceed 10^4 the MEAN
+ * deposits are taken; a layer whose drawn share T G_j / sum_i G_i is below
+ * 10^-6 gets nothing (the others' sum normalises).  The gamma variates
+ * follow
  * Marsaglia and Tsang (ACM TOMS 26(3), 2000) on Philox stream tag 3 (counter
  * (shower id, slice | 3 << 16 | (4 j + attempt) << 20, lineage), key =
  * seed), at most four attempts per layer (then the mean c m_j). */
@@ -463,8 +465,10 @@ typedef struct supa_diverted_record {
     float tx, ty;     /* slopes u_x / u_z, u_y / u_z                      */
     float E;          /* energy                                           */
     uint64_t lineage; /* lineage id                                       */
-    float mu[30];     /* network outputs for layers layer + j:            */
-    float s[30];      /*   deposit-fraction means, log-variances and mean */
+    float lmu[30];    /* network outputs for layers layer + j: log-link   */
+                      /*   output o_j of the deposit-fraction mean        */
+                      /*   mu_j = exp(o_j - 4),                           */
+    float s[30];      /*   log-variances of the fractions and the mean    */
     float rho[30];    /*   lateral distances                              */
     float dep[30];    /* deposits of layers layer + j (0 past the back)    */
     uint32_t n_hits;  /* hits emitted (layers with a deposit > 0)         */

@@ -37,8 +37,9 @@ returns them):
      particle moved between layers).  The concentration c is
      matched to the predicted spreads: a Dirichlet share has variance
      m_j (1 - m_j) / (c + 1), so T^2 (1 - sum m_j^2) / (c + 1) is set equal
-     to V = sum exp(s_j) over the layers with f_j > 0 (the predicted
-     variances of their deposit fractions), c raised to 1 where it falls
+     to V = sum (exp(s_j) + 10^-8) over the layers with f_j > 0 (the
+     predicted variances of their deposit fractions, with the network's
+     variance floor), c raised to 1 where it falls
      below; where c exceeds 10^4 (V = 0 included) the spread is negligible
      and the MEAN fractions are taken without a draw.  Both: scaled by
      E / sum d when the sum exceeds E;
@@ -168,7 +169,7 @@ def sample_concentration(f: np.ndarray, s: np.ndarray) -> float:
     fractions are taken without a draw (c above SAMPLE_C_MAX)."""
     T = float(f.sum())
     pos = f > 0
-    V = float(np.exp(s[pos]).sum())
+    V = float((np.exp(s[pos]) + mlp.VAR_FLOOR).sum())
     if T <= 0:
         return math.inf
     m = f / T

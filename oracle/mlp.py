@@ -13,8 +13,12 @@ reach get means that go to zero instead of a rounding-noise floor.  Targets Y = 
 energy-weighted mean distances.  Loss: Gaussian negative log-likelihood of
 the fractions plus the fraction-weighted squared error of the distances,
 averaged over layers and samples,
-  L = mean_b (1/30) sum_j [ (y_j - mu_j)^2 exp(-s_j) / 2 + s_j / 2
-                            + LAMBDA_R y_j (rho_j - R_j)^2 / 2 ].
+  L = mean_b (1/30) sum_j [ (y_j - mu_j)^2 / (2 v_j) + ln(v_j) / 2
+                            + LAMBDA_R y_j (rho_j - R_j)^2 / 2 ],
+  v_j = exp(s_j) + VAR_FLOOR,
+the predicted variance of the fraction with a floor of 10^-8 (a standard
+deviation of 10^-4): without it a layer whose target is always 0 drives
+mu_j and v_j to 0 together and (y - mu)^2 / v overflows.
 Optimiser: Adam (Kingma & Ba 2015) with bias correction.
 
 Plain numpy float64, one matrix formula per step; no fusion or reordering.
@@ -28,6 +32,7 @@ from scipy.special import erf
 
 N_IN, N_HID, N_OUT, N_LAYERS_OUT = 6, 256, 90, 30
 MU_SHIFT = 4.0  # mu_j = exp(o_j - MU_SHIFT): outputs near 0 at initialisation give means near 1/55
+VAR_FLOOR = 1.0e-8
 SHAPES = [(N_HID, N_IN), (N_HID, N_HID), (N_HID, N_HID), (N_OUT, N_HID)]
 LAMBDA_R = 1.0  # weight of the lateral term
 
@@ -68,7 +73,8 @@ def _split(out, Y):
 def loss(out, Y):
     """The loss L above: mean over samples and the 30 layers."""
     mu, s, rho, y, R = _split(out, Y)
-    return float(np.mean(0.5 * (y - mu) ** 2 * np.exp(-s) + 0.5 * s + 0.5 * LAMBDA_R * y * (rho - R) ** 2))
+    v = np.exp(s) + VAR_FLOOR
+    return float(np.mean(0.5 * (y - mu) ** 2 / v + 0.5 * np.log(v) + 0.5 * LAMBDA_R * y * (rho - R) ** 2))
 
 
 def loss_grad(out, Y):
@@ -76,8 +82,10 @@ def loss_grad(out, Y):
     B = out.shape[0]
     mu, s, rho, y, R = _split(out, Y)
     r = y - mu
-    g_mu = -r * np.exp(-s) * mu / (B * N_LAYERS_OUT)  # d mu / d o = mu
-    g_s = (0.5 - 0.5 * r * r * np.exp(-s)) / (B * N_LAYERS_OUT)
+    es = np.exp(s)
+    v = es + VAR_FLOOR
+    g_mu = -r * mu / v / (B * N_LAYERS_OUT)  # d mu / d o = mu
+    g_s = 0.5 * es / v * (1.0 - r * r / v) / (B * N_LAYERS_OUT)  # d v / d s = exp(s)
     g_rho = LAMBDA_R * y * (rho - R) / (B * N_LAYERS_OUT)
     return np.concatenate([g_mu, g_s, g_rho], axis=1)
 

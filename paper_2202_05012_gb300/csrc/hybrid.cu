@@ -6,8 +6,9 @@
 // distributions for the queue (means mu_j and log-variances s_j of the
 // deposit fraction of layer start + j, mean lateral distances rho_j), these
 // kernels
-//   1. take d_j = E max(0, mu_j) (MEAN), or split the MEAN total
-//      T = sum_j max(0, mu_j) over the layers by a Dirichlet draw whose means
+//   1. take d_j = E mu_j, mu_j = exp(o_j - 4) (MEAN; 0 below a millionth),
+//      or split the MEAN total T = sum_j f_j of those fractions over their
+//      layers by a Dirichlet draw whose means
 //      are the MEAN shares and whose concentration c matches the predicted
 //      variances exp(s_j) (SAMPLE: d_j = E T G_j / sum G, G_j ~ Gamma(c m_j)
 //      by Marsaglia and Tsang's method on Philox stream tag 3, keyed by
@@ -76,10 +77,6 @@ __device__ float gamma_variate(float alpha, uint32_t sid, int k, uint32_t lin_lo
 // concentration is raised to it; above kSampleCMax the spread is negligible
 // and the MEAN shares are taken without a draw.
 constexpr float kSampleCMin = 1.0f, kSampleCMax = 1.0e4f;
-// A layer whose gamma variate is below this fraction of the particle's sum
-// of variates gets no deposit (such shares are where float32 variates
-// underflow).
-constexpr float kShareMin = 1.0e-9f;
 
 // The standard normal pair (m1, m2) displacing all hits of a diverted
 // particle: Box-Muller on words (w0, w1) of the Philox block with counter
@@ -173,11 +170,13 @@ __global__ void __launch_bounds__(kDepWarps * 32) sur_deposits(const SurParams p
                 for (int t = 0; t < 4; ++t)
                     if (4 * q + t < kSurLayers) v[4 * q + t] = mq[t];
             }
-            // MEAN fractions of the layers inside the detector
+            // MEAN fractions of the layers inside the detector (log link;
+            // none below a millionth)
             float T = 0.0f;
 #pragma unroll
             for (int j = 0; j < kSurLayers; ++j) {
-                v[j] = j < nj ? fmaxf(0.0f, v[j]) : 0.0f;
+                const float mu = expf(v[j] - kMuShift);
+                v[j] = j < nj && mu >= kFractionMin ? mu : 0.0f;
                 T += v[j];
             }
             if (kSample && T > 0.0f) {
@@ -201,27 +200,30 @@ __global__ void __launch_bounds__(kDepWarps * 32) sur_deposits(const SurParams p
                     float gs = 0.0f;
 #pragma unroll 1
                     for (int j = 0; j < nj; ++j) {
-                        const float mu = __ldg(p.out + (size_t)i * p.out_ld + j);
-                        const float G = mu > 0.0f ? gamma_variate(cm * mu, (uint32_t)(p.shower_id_base + sh), r.k,
-                                                                  r.lin_lo, r.lin_hi, p.seed, j)
-                                                  : 0.0f;
+                        const float mu = expf(__ldg(p.out + (size_t)i * p.out_ld + j) - kMuShift);
+                        const float G = mu >= kFractionMin
+                                            ? gamma_variate(cm * mu, (uint32_t)(p.shower_id_base + sh), r.k, r.lin_lo,
+                                                            r.lin_hi, p.seed, j)
+                                            : 0.0f;
                         stg[lane][j] = G;
                         gs += G;
                     }
                     if (gs > 0.0f) {
-                        // shares below kShareMin of the sum get nothing
-                        const float gmin = kShareMin * gs;
+                        // drawn shares below a millionth of E get nothing; the rest normalises
+                        const float tg = T / gs;
                         float gk = 0.0f;
 #pragma unroll
                         for (int j = 0; j < kSurLayers; ++j) {
                             float G = j < nj ? stg[lane][j] : 0.0f;
-                            if (G < gmin) G = 0.0f;
-                            v[j] = G;
+                            if (tg * G < kFractionMin) G = 0.0f;
+                            stg[lane][j] = G;
                             gk += G;
                         }
-                        const float sc = T / gk;
+                        if (gk > 0.0f) {
+                            const float sc = T / gk;
 #pragma unroll
-                        for (int j = 0; j < kSurLayers; ++j) v[j] *= sc;
+                            for (int j = 0; j < kSurLayers; ++j) v[j] = stg[lane][j] * sc;
+                        }
                     }
                 }
             }
@@ -433,7 +435,7 @@ __global__ void export_surrogate(const SurParams p, int64_t n, supa_diverted_rec
         o.lineage = ((uint64_t)r.lin_hi << 32) | r.lin_lo;
         const float *row = p.out + (size_t)i * p.out_ld;
         for (int j = 0; j < kSurLayers; ++j) {
-            o.mu[j] = row[j];
+            o.lmu[j] = row[j];
             o.s[j] = row[kSurLayers + j];
             o.rho[j] = row[2 * kSurLayers + j];
             o.dep[j] = p.dep[(size_t)i * kSurLayers + j];

@@ -62,6 +62,13 @@ __device__ __forceinline__ double from_fixed32(unsigned long long v) {
 }
 
 // A diverted particle: where it is and what it carries.
+// Surrogate network outputs per layer j: o_j (log link: deposit-fraction
+// mean mu_j = exp(o_j - kMuShift)), s_j (log-variance), rho_j (mean lateral
+// distance); a layer whose mean or drawn fraction is below kFractionMin of the
+// particle's energy gets no deposit.
+constexpr float kMuShift = 4.0f;
+constexpr float kFractionMin = 1.0e-6f;
+
 struct SurRec {
     uint32_t shower;  // index in the batch
     int16_t k;        // slice of diversion

@@ -1,8 +1,9 @@
 // surrogate.cu -- the BF16 tensor-core surrogate network of the hybrid path
 // (no counterpart in the SUPA paper): an MLP 6 -> 256 -> 256 -> 256 -> 90
-// with exact GELU -- per layer j = 0..29 from the start layer the mean mu_j
-// and log-variance s_j of the deposit fraction and the mean lateral distance
-// rho_j of the deposits from the particle's axis -- trained with Adam on
+// with exact GELU -- per layer j = 0..29 from the start layer the mean
+// mu_j = exp(o_j - 4) (log link: output o_j) and log-variance s_j of the
+// deposit fraction and the mean lateral distance rho_j of the deposits from
+// the particle's axis -- trained with Adam on
 //   L = mean (1/30) sum_j [(y_j - mu_j)^2 e^-s_j / 2 + s_j / 2
 //                          + y_j (rho_j - R_j)^2 / 2]
 // (targets: fractions y_j, energy-weighted mean distances R_j), evaluated
@@ -109,12 +110,13 @@ __global__ void __launch_bounds__(kLossRows * kLossLanesY)
     for (int j = threadIdx.y; j < kLayersOut; j += kLossLanesY) {
         float gmu = 0.0f, gs = 0.0f, gr = 0.0f;
         if (live) {
-            const float mu = so[rl][j], s = so[rl][kLayersOut + j], rho = so[rl][2 * kLayersOut + j];
+            const float mu = expf(so[rl][j] - kMuShift), s = so[rl][kLayersOut + j],
+                        rho = so[rl][2 * kLayersOut + j];
             const float yj = sy[rl][j], dr = rho - sy[rl][kLayersOut + j];
             const float res = yj - mu;
             const float e = expf(-s);
             l += 0.5 * (double)(res * res * e) + 0.5 * (double)s + 0.5 * (double)(yj * dr * dr);
-            gmu = -res * e * inv;
+            gmu = -res * e * mu * inv;  // through the log link: d mu / d o = mu
             gs = (0.5f - 0.5f * res * res * e) * inv;
             gr = yj * dr * inv;
             sg[rl][j] = __float2bfloat16_rn(gmu);

@@ -192,19 +192,24 @@ def _diverted_on_layer0(n, E=0.5):
 
 
 def test_sample_concentration_matches_the_predicted_variance():
-    # equal layers: T = 30 mu, m = 1/30, V = 30 sd^2 -> c + 1 = T^2 (1 - 1/30) / V
+    # equal layers: T = 30 mu, m = 1/30, V = 30 v with v = sd^2 + the
+    # network's variance floor -> c + 1 = T^2 (1 - 1/30) / V
     mu, sd = 0.02, 0.01
+    v = sd * sd + mlp.VAR_FLOOR
     f = np.full(30, mu)
     c = hybrid.sample_concentration(f, np.full(30, math.log(sd * sd)))
     T = 30 * mu
-    assert c == pytest.approx(T * T * (1 - 1 / 30) / (30 * sd * sd) - 1, rel=1e-12)
-    # a Dirichlet share then has variance T^2 m (1 - m) / (c + 1) = sd^2
-    assert T * T * (1 / 30) * (1 - 1 / 30) / (c + 1) == pytest.approx(sd * sd, rel=1e-12)
+    assert c == pytest.approx(T * T * (1 - 1 / 30) / (30 * v) - 1, rel=1e-12)
+    # a Dirichlet share then has variance T^2 m (1 - m) / (c + 1) = v
+    assert T * T * (1 / 30) * (1 - 1 / 30) / (c + 1) == pytest.approx(v, rel=1e-12)
     # a negligible spread takes the means (no draw); a huge one the lowest c
     assert math.isinf(hybrid.sample_concentration(f, np.full(30, -200.0)))
-    tiny = T * T * (1 - 1 / 30) / (30 * (hybrid.SAMPLE_C_MAX + 1)) * 1.01
-    assert hybrid.sample_concentration(f, np.full(30, math.log(tiny))) == pytest.approx(hybrid.SAMPLE_C_MAX / 1.01, rel=1e-3)
-    assert math.isinf(hybrid.sample_concentration(f, np.full(30, math.log(tiny / 1.02))))
+    v_edge = T * T * (1 - 1 / 30) / (30 * (hybrid.SAMPLE_C_MAX + 1))  # c = C_MAX exactly
+    s_just_below = math.log(1.01 * v_edge - mlp.VAR_FLOOR)  # c slightly below C_MAX
+    assert hybrid.sample_concentration(f, np.full(30, s_just_below)) == pytest.approx(
+        (hybrid.SAMPLE_C_MAX + 1) / 1.01 - 1, rel=1e-9)
+    s_just_above = math.log(0.99 * v_edge - mlp.VAR_FLOOR)
+    assert math.isinf(hybrid.sample_concentration(f, np.full(30, s_just_above)))
     assert hybrid.sample_concentration(f, np.full(30, 5.0)) == hybrid.SAMPLE_C_MIN
     assert math.isinf(hybrid.sample_concentration(np.zeros(30), np.zeros(30)))
     # layers without a mean deposit do not count towards V
@@ -213,7 +218,7 @@ def test_sample_concentration_matches_the_predicted_variance():
     s2 = np.full(30, math.log(sd * sd))
     s2[10:] = 3.0
     T2 = 10 * mu
-    assert hybrid.sample_concentration(f2, s2) == pytest.approx(T2 * T2 * 0.9 / (10 * sd * sd) - 1, rel=1e-12)
+    assert hybrid.sample_concentration(f2, s2) == pytest.approx(T2 * T2 * 0.9 / (10 * v) - 1, rel=1e-12)
 
 
 def test_sample_mode_is_an_unbiased_dirichlet_split():
@@ -245,7 +250,7 @@ def test_sample_mode_is_an_unbiased_dirichlet_split():
     assert np.all(np.abs(fr.mean(0)[ok] - f[ok]) < 4.5 * se[ok])
     np.testing.assert_allclose(fr.var(0)[ok], var[ok], rtol=0.2)
     # and the spread summed over the layers is the predicted one
-    assert abs((fr.var(0)[ok]).sum() / (sd[ok] ** 2).sum() - 1) < 0.1
+    assert abs((fr.var(0)[ok]).sum() / (sd[ok] ** 2 + mlp.VAR_FLOOR).sum() - 1) < 0.1
     # replayable: the same counters give the same draws
     again = hybrid.deposits({k: v[:50] for k, v in div.items()}, net, g, 1.0, 4, mode=0)
     np.testing.assert_array_equal(again["d"], dep["d"][:50])

@@ -66,7 +66,8 @@ def test_matches_torch_nn_float64():
             h = torch.nn.functional.gelu(h, approximate="none")
     mu, s, rho = torch.exp(h[:, :30] - mlp.MU_SHIFT), h[:, 30:60], h[:, 60:]
     yt, rt = torch.from_numpy(Y[:, :30]), torch.from_numpy(Y[:, 30:])
-    tl = torch.mean(0.5 * (yt - mu) ** 2 * torch.exp(-s) + 0.5 * s + 0.5 * mlp.LAMBDA_R * yt * (rho - rt) ** 2)
+    v = torch.exp(s) + mlp.VAR_FLOOR
+    tl = torch.mean(0.5 * (yt - mu) ** 2 / v + 0.5 * torch.log(v) + 0.5 * mlp.LAMBDA_R * yt * (rho - rt) ** 2)
     tl.backward()
     assert abs(tl.item() - loss) < 1e-12
     for (gW, gb), lin in zip(grads, layers):
