@@ -410,8 +410,9 @@ int supa_surrogate_check(supa_surrogate *s);
  * MEAN shares m_j = f_j / T: d_j = E T G_j / sum_i G_i with independent
  * G_j ~ Gamma(c m_j), so every layer's expected deposit is its MEAN deposit
  * and the particle's total is the MEAN total.  The concentration c matches
- * the predicted variances: T^2 (1 - sum m_j^2) / (c + 1) = sum of exp(s_j)
- * over the layers with f_j > 0, c >= 1; where c would exceed 10^4 the MEAN
+ * the predicted variances: T^2 (1 - sum m_j^2) / (c + 1) = sum of
+ * exp(s_j) + 10^-8 (the training loss's variance floor) over the layers with
+ * f_j > 0, c >= 1; where c would exceed 10^4 the MEAN
  * deposits are taken; a layer whose drawn share T G_j / sum_i G_i is below
  * 10^-6 gets nothing (the others' sum normalises).  The gamma variates
  * follow

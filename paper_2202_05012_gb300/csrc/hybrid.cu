@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kDepWarps * 32) sur_deposits(const SurParams p
                     if (v[j] > 0.0f) {
                         const float m = v[j] * rT;
                         q = fmaf(m, m, q);
-                        V += expf(__ldg(p.out + (size_t)i * p.out_ld + kSurLayers + j));
+                        V += expf(__ldg(p.out + (size_t)i * p.out_ld + kSurLayers + j)) + kVarFloor;
                     }
                 }
                 const float num = T * T * (1.0f - q);

@@ -67,6 +67,8 @@ __device__ __forceinline__ double from_fixed32(unsigned long long v) {
 // distance); a layer whose mean or drawn fraction is below kFractionMin of the
 // particle's energy gets no deposit.
 constexpr float kMuShift = 4.0f;
+// Floor of the predicted variance of a deposit fraction, e^s_j + kVarFloor.
+constexpr float kVarFloor = 1.0e-8f;
 constexpr float kFractionMin = 1.0e-6f;
 
 struct SurRec {

@@ -4,8 +4,8 @@
 // mu_j = exp(o_j - 4) (log link: output o_j) and log-variance s_j of the
 // deposit fraction and the mean lateral distance rho_j of the deposits from
 // the particle's axis -- trained with Adam on
-//   L = mean (1/30) sum_j [(y_j - mu_j)^2 e^-s_j / 2 + s_j / 2
-//                          + y_j (rho_j - R_j)^2 / 2]
+//   L = mean (1/30) sum_j [(y_j - mu_j)^2 / (2 v_j) + ln(v_j) / 2
+//                          + y_j (rho_j - R_j)^2 / 2],  v_j = e^s_j + 1e-8
 // (targets: fractions y_j, energy-weighted mean distances R_j), evaluated
 // in minibatches of `batch` rows.
 //
@@ -114,10 +114,11 @@ __global__ void __launch_bounds__(kLossRows * kLossLanesY)
                         rho = so[rl][2 * kLayersOut + j];
             const float yj = sy[rl][j], dr = rho - sy[rl][kLayersOut + j];
             const float res = yj - mu;
-            const float e = expf(-s);
-            l += 0.5 * (double)(res * res * e) + 0.5 * (double)s + 0.5 * (double)(yj * dr * dr);
-            gmu = -res * e * mu * inv;  // through the log link: d mu / d o = mu
-            gs = (0.5f - 0.5f * res * res * e) * inv;
+            const float es = expf(s);
+            const float iv = 1.0f / (es + kVarFloor);  // floored variance
+            l += 0.5 * (double)(res * res * iv) - 0.5 * log((double)iv) + 0.5 * (double)(yj * dr * dr);
+            gmu = -res * iv * mu * inv;  // through the log link: d mu / d o = mu
+            gs = 0.5f * es * iv * (1.0f - res * res * iv) * inv;
             gr = yj * dr * inv;
             sg[rl][j] = __float2bfloat16_rn(gmu);
             sg[rl][kLayersOut + j] = __float2bfloat16_rn(gs);

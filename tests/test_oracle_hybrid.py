@@ -4,10 +4,11 @@ rules are the library's): the gamma variates follow the gamma law
 splits the MEAN total by a Dirichlet draw whose means are the MEAN shares
 and whose spread matches the predicted variances, sums above E are
 scaled to E, hits
-lie on the particle's straight line when the predicted distance is zero and
-at that mean distance otherwise, the hybrid stepping reduces to the plain
-one when nothing is set aside, energy is conserved, and the lateral
-training targets of a single symmetric split are its closed form."""
+lie on the particle's straight line when the predicted mean squared distance
+is zero and at Rayleigh distances with that mean square otherwise, the
+hybrid stepping reduces to the plain one when nothing is set aside, energy
+is conserved, and the lateral training targets (mean squared distances) of a
+single symmetric split are their closed form."""
 import math
 
 import numpy as np
@@ -129,28 +130,29 @@ def _straight_line(div, h, g):
     return np.array(xs), np.array(ys)
 
 
-def test_hits_spread_at_the_predicted_mean_distance():
+def test_hits_spread_at_the_predicted_mean_squared_distance():
     g = inputs.supa_d(30)
     p = inputs.primaries(60, 9, e_lo=5, e_hi=20)
     r = oracle.simulate(g, p, 3, e_s=1.0)
     div = r["div"]
-    R = 0.7
-    dep = hybrid.deposits(div, _const_net(0.02, -80.0, R), g, 1.0, 3)
+    Q = 0.49
+    dep = hybrid.deposits(div, _const_net(0.02, -80.0, Q), g, 1.0, 3)
     h = dep["hits"]
     x, y = _straight_line(div, h, g)
     dist = np.hypot(h[:, 1] - x, h[:, 2] - y)
-    # per layer an isotropic 2-D Gaussian with sigma = R sqrt(2/pi): the
-    # distances are Rayleigh with mean R; one pair per particle, so test the
-    # first layer of each particle (independent draws)
+    # per layer an isotropic 2-D Gaussian with sigma = sqrt(Q / 2): the
+    # distances are Rayleigh with mean squared distance Q; one pair per
+    # particle, so test the first layer of each particle (independent draws)
     first = np.concatenate([[True], (h[1:, 0] != h[:-1, 0]) | (h[1:, 5] <= h[:-1, 5])])
     d1 = dist[first]
     assert len(d1) > 300
-    sig = R * math.sqrt(2 / math.pi)
-    assert abs(d1.mean() - R) < 4 * sig * math.sqrt(2 - math.pi / 2) / math.sqrt(len(d1))
+    sig = math.sqrt(Q / 2)
+    # r^2 is exponential with mean Q (standard deviation Q)
+    assert abs((d1 ** 2).mean() - Q) < 4 * Q / math.sqrt(len(d1))
     assert stats.kstest(d1, "rayleigh", args=(0, sig)).pvalue > 1e-3
-    # all layers of a particle share the direction of the displacement
-    assert np.allclose(dist[~first], R * math.sqrt(2 / math.pi) * np.repeat(
-        d1 / sig, np.diff(np.append(np.nonzero(first)[0], len(first))))[~first], rtol=1e-9)
+    # all layers of a particle share the direction and size of the displacement
+    assert np.allclose(dist[~first], np.repeat(d1, np.diff(np.append(np.nonzero(first)[0], len(first))))[~first],
+                       rtol=1e-9)
 
 
 def test_training_targets_of_a_single_symmetric_split():
@@ -171,7 +173,7 @@ def test_training_targets_of_a_single_symmetric_split():
     assert np.all(r["offsets"][1:] - r["offsets"][:-1] == 2)
     np.testing.assert_allclose(Y[:, 2], 1.0, rtol=1e-12)
     np.testing.assert_allclose(Y[:, [0, 1, 3]], 0.0, atol=0)
-    np.testing.assert_allclose(Y[:, 32], 7.0 * math.tan(math.pi / 48), rtol=1e-9)
+    np.testing.assert_allclose(Y[:, 32], (7.0 * math.tan(math.pi / 48)) ** 2, rtol=1e-9)
     np.testing.assert_allclose(Y[:, [30, 31, 33]], 0.0, atol=0)
 
 
