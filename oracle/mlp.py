@@ -5,16 +5,16 @@ stands in for the low-energy tail of a shower (sub-showers below a cutoff
 energy E_s).  Architecture: 6 inputs -> 3 hidden layers of 256 with GELU
 (exact form x * Phi(x)) -> 90 outputs o = 30 log-link outputs o_j of the
 means mu_j = exp(o_j - MU_SHIFT) and 30 log-variances s_j of the per-layer
-deposit fractions, and 30 mean squared lateral distances q_j of each layer's
+deposit fractions, and 30 mean lateral distances rho_j of each layer's
 deposits from the sub-shower's axis, layers counted from the sub-shower's
 start layer.  The log link keeps every mean positive and makes a rounding
 error of o_j a relative error of mu_j, so layers a sub-shower does not
-reach get means that go to zero instead of a rounding-noise floor.  Targets Y = [y_j, Q_j]: deposit fractions and
-energy-weighted mean squared distances.  Loss: Gaussian negative log-likelihood of
+reach get means that go to zero instead of a rounding-noise floor.  Targets Y = [y_j, R_j]: deposit fractions and
+energy-weighted mean distances.  Loss: Gaussian negative log-likelihood of
 the fractions plus the fraction-weighted squared error of the distances,
 averaged over layers and samples,
   L = mean_b (1/30) sum_j [ (y_j - mu_j)^2 / (2 v_j) + ln(v_j) / 2
-                            + LAMBDA_R y_j (q_j - Q_j)^2 / 2 ],
+                            + LAMBDA_R y_j (rho_j - R_j)^2 / 2 ],
   v_j = exp(s_j) + VAR_FLOOR,
 the predicted variance of the fraction with a floor of 10^-8 (a standard
 deviation of 10^-4): without it a layer whose target is always 0 drives

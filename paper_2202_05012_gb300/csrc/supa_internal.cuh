@@ -63,7 +63,7 @@ __device__ __forceinline__ double from_fixed32(unsigned long long v) {
 
 // A diverted particle: where it is and what it carries.
 // Surrogate network outputs per layer j: o_j (log link: deposit-fraction
-// mean mu_j = exp(o_j - kMuShift)), s_j (log-variance), rho_j (mean lateral
+// mean mu_j = exp(o_j - kMuShift)), s_j (log-variance), q_j (mean squared lateral
 // distance); a layer whose mean or drawn fraction is below kFractionMin of the
 // particle's energy gets no deposit.
 constexpr float kMuShift = 4.0f;
@@ -105,7 +105,7 @@ __host__ __device__ inline void surrogate_features(float E, float ux, float uy, 
 struct SurInfer {
     int cap = 0;
     int ld = 0;            // row stride of OUT
-    float *OUT = nullptr;  // network outputs [cap][ld]: mu 0..29, s 30..59, rho 60..89
+    float *OUT = nullptr;  // network outputs [cap][ld]: o 0..29, s 30..59, q 60..89
 };
 int surrogate_infer_init(supa_surrogate *s, int cap, SurInfer *inf);
 void surrogate_infer_free(SurInfer *inf);
@@ -118,7 +118,7 @@ struct SurParams {
     const SurRec *rec;
     const unsigned *count;  // queue length (device)
     int cap;
-    const float *out;       // network outputs [cap][out_ld]: mu, s, rho (30 each)
+    const float *out;       // network outputs [cap][out_ld]: o, s, q (30 each)
     int out_ld;
     const supa_primary *prim;
     const GeomDev *geoms;
@@ -324,7 +324,7 @@ struct ShapeParams {
 };
 cudaError_t launch_shower_shapes(const ShapeParams &p, cudaStream_t st);
 
-// Training targets R_j (mean lateral distances) of a batch of sub-showers.
+// Training targets Q_j (mean squared lateral distances) of a batch of sub-showers.
 struct LateralParams {
     HitSource src;
     const supa_primary *prim;

@@ -4,11 +4,11 @@ rules are the library's): the gamma variates follow the gamma law
 splits the MEAN total by a Dirichlet draw whose means are the MEAN shares
 and whose spread matches the predicted variances, sums above E are
 scaled to E, hits
-lie on the particle's straight line when the predicted mean squared distance
-is zero and at Rayleigh distances with that mean square otherwise, the
-hybrid stepping reduces to the plain one when nothing is set aside, energy
-is conserved, and the lateral training targets (mean squared distances) of a
-single symmetric split are their closed form."""
+lie on the particle's straight line when the predicted mean distance is zero
+and at Rayleigh distances whose mean square is 1.41 times its square
+otherwise, the hybrid stepping reduces to the plain one when nothing is set
+aside, energy is conserved, and the lateral training targets (mean
+distances) of a single symmetric split are their closed form."""
 import math
 
 import numpy as np
@@ -130,22 +130,23 @@ def _straight_line(div, h, g):
     return np.array(xs), np.array(ys)
 
 
-def test_hits_spread_at_the_predicted_mean_squared_distance():
+def test_hits_spread_with_the_stated_second_moment_about_the_mean_distance():
     g = inputs.supa_d(30)
     p = inputs.primaries(60, 9, e_lo=5, e_hi=20)
     r = oracle.simulate(g, p, 3, e_s=1.0)
     div = r["div"]
-    Q = 0.49
-    dep = hybrid.deposits(div, _const_net(0.02, -80.0, Q), g, 1.0, 3)
+    R = 0.7
+    dep = hybrid.deposits(div, _const_net(0.02, -80.0, R), g, 1.0, 3)
     h = dep["hits"]
     x, y = _straight_line(div, h, g)
     dist = np.hypot(h[:, 1] - x, h[:, 2] - y)
-    # per layer an isotropic 2-D Gaussian with sigma = sqrt(Q / 2): the
-    # distances are Rayleigh with mean squared distance Q; one pair per
-    # particle, so test the first layer of each particle (independent draws)
+    # per layer an isotropic 2-D Gaussian with mean squared distance
+    # 1.41 R^2: the distances are Rayleigh with sigma = R sqrt(1.41 / 2); one
+    # pair per particle, so test the first layer of each particle
     first = np.concatenate([[True], (h[1:, 0] != h[:-1, 0]) | (h[1:, 5] <= h[:-1, 5])])
     d1 = dist[first]
     assert len(d1) > 300
+    Q = 1.41 * R * R
     sig = math.sqrt(Q / 2)
     # r^2 is exponential with mean Q (standard deviation Q)
     assert abs((d1 ** 2).mean() - Q) < 4 * Q / math.sqrt(len(d1))
@@ -173,7 +174,7 @@ def test_training_targets_of_a_single_symmetric_split():
     assert np.all(r["offsets"][1:] - r["offsets"][:-1] == 2)
     np.testing.assert_allclose(Y[:, 2], 1.0, rtol=1e-12)
     np.testing.assert_allclose(Y[:, [0, 1, 3]], 0.0, atol=0)
-    np.testing.assert_allclose(Y[:, 32], (7.0 * math.tan(math.pi / 48)) ** 2, rtol=1e-9)
+    np.testing.assert_allclose(Y[:, 32], 7.0 * math.tan(math.pi / 48), rtol=1e-9)
     np.testing.assert_allclose(Y[:, [30, 31, 33]], 0.0, atol=0)
 
 
@@ -293,3 +294,29 @@ def test_log_link_means_and_the_millionth_cut():
         assert np.all(dep["d"][:, 3] == 0) and np.all(dep["d"][:, 4] > 0)
         assert not np.any(dep["hits"][:, 5] == 3)
         assert np.sum(dep["hits"][:, 5] == 4) == len(div["E"])
+
+
+def test_lateral_second_moment_factor_is_the_plain_sub_showers():
+    """LATERAL_M2 restates a measurement: the energy-weighted <r^2> / <r>^2
+    of plain sub-showers' hit distances from their axis, r taken relative to
+    the mean distance of sub-showers alike in energy (8 bins over 0.5-2 GeV),
+    start slice and layer offset, at normal incidence."""
+    g = inputs.supa_d(30)
+    p, _ = inputs.subshower_primaries(8000, 5, e_lo=0.5, e_hi=2.0)
+    p["theta"] = 0.0
+    r = oracle.simulate(g, p, 3, n_threads=8)
+    s2l = np.asarray(g.slice_to_layer)
+    sh = np.repeat(np.arange(len(p)), np.diff(r["offsets"]))
+    k0 = (p["geom"].astype(np.int64) >> 16)[sh]
+    first = np.array([np.nonzero(s2l == l)[0].min() for l in range(g.n_layers)])
+    j = s2l[np.rint(r["z"] / g.dz).astype(int)] - s2l[k0]
+    d = np.hypot(r["x"] - p["x0"][sh], r["y"] - p["y0"][sh])
+    ebin = np.clip((np.log(p["E"][sh] / 0.5) / np.log(4.0) * 8).astype(int), 0, 7)
+    key = (ebin * 3 + (k0 - first[s2l[k0]])) * 30 + j
+    w = r["E"]
+    mean_d = np.bincount(key, weights=w * d) / np.maximum(np.bincount(key, weights=w), 1e-300)
+    ok = mean_d[key] > 0
+    q = d[ok] / mean_d[key][ok]
+    m2 = float((w[ok] * q * q).sum() / w[ok].sum())
+    assert abs(m2 - hybrid.LATERAL_M2) < 0.04, m2
+    assert m2 > 4 / math.pi + 0.08  # wider than a 2-D Gaussian fitted to the mean distance
