@@ -355,11 +355,11 @@ int supa_voxelize_hits(const supa_geometry *g, const float *hits_dev, const int6
  * the number of layers left behind the start layer) through three hidden
  * layers of 256 with GELU to 90 outputs: log-link outputs o_j of the means
  * mu_j = exp(o_j - 4) and log-variances s_j of the deposit fractions of
- * layers start + j, j = 0..29, and the mean squared lateral distances q_j
- * of those deposits from the particle's axis.  Targets: fractions y_j and
- * energy-weighted mean squared distances Q_j ([.][60]).  Loss, mean over
- * samples and layers: (y_j - mu_j)^2 / (2 v_j) + ln(v_j) / 2
- * + y_j (q_j - Q_j)^2 / 2 with v_j = exp(s_j) + 10^-8.  Compute: BF16
+ * layers start + j, j = 0..29, and the mean lateral distances rho_j of
+ * those deposits from the particle's axis.  Targets: fractions y_j and
+ * energy-weighted mean distances R_j ([.][60]).  Loss, mean over samples and
+ * layers: (y_j - mu_j)^2 / (2 v_j) + ln(v_j) / 2 + y_j (rho_j - R_j)^2 / 2
+ * with v_j = exp(s_j) + 10^-8.  Compute: BF16
  * tensor-core GEMMs (tcgen05, TMA) with FP32 accumulation, FP32 master
  * weights and Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  * Parameters are exchanged as a packed float32 vector of
@@ -432,8 +432,9 @@ int supa_surrogate_check(supa_surrogate *s);
  * up to more than E, are added to the layer sums and emitted as one hit per
  * non-empty layer after the shower's stepped hits: at the layer's mid depth,
  * displaced from the particle's straight line by sigma_j (m1, m2) with
- * sigma_j = sqrt(max(0, q_j) / 2) (mean squared displacement q_j) and one
- * pair of standard normals
+ * sigma_j = max(0, rho_j) sqrt(1.41 / 2) (mean squared displacement
+ * 1.41 rho_j^2, the plain sub-showers' <r^2> / <r>^2 about their mean
+ * distance) and one pair of standard normals
  * m1, m2 per particle (Philox stream tag 2, same keys).  The energy left
  * over is
  * reported as sur_leak.  s = NULL or e_s <= 0 returns the batch to the plain
@@ -444,8 +445,8 @@ int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_
  * primary entering on its start slice, see supa_primary.geom): x_dev float32
  * [n][6] features of the start; y_dev float32 [n][60]: deposit fractions of
  * layers start + 0..29 (FP64 layer sums / E), then the energy-weighted mean
- * squared distance of each of those layers' hits from the sub-shower's axis
- * (0 for an empty layer).  Synchronous. */
+ * distance of each of those layers' hits from the sub-shower's axis (0 for
+ * an empty layer).  Synchronous. */
 int supa_build_training_set(supa_batch *b, float e_s, float *x_dev, float *y_dev, void *stream);
 
 /* The particles the last hybrid simulation of b diverted to the network, as
@@ -472,7 +473,7 @@ typedef struct supa_diverted_record {
                       /*   output o_j of the deposit-fraction mean        */
                       /*   mu_j = exp(o_j - 4),                           */
     float s[30];      /*   log-variances of the fractions and the mean    */
-    float q2[30];     /*   squared lateral distances                      */
+    float rho[30];    /*   lateral distances                              */
     float dep[30];    /* deposits of layers layer + j (0 past the back)    */
     uint32_t n_hits;  /* hits emitted (layers with a deposit > 0)         */
     uint32_t reserved;

@@ -390,9 +390,8 @@ cudaError_t launch_shower_shapes(const ShapeParams &p, cudaStream_t st) {
 // entering on slice k0 at (x0, y0) with direction (theta, phi), each hit
 // (x, y, z, E) of layer l0 + j (j = 0..29) lies at distance
 //   r = |(x, y) - (x0, y0) - (z - k0 dz) (tan theta cos phi, tan theta sin phi)|
-// from the sub-shower's axis; Q_j = sum E r^2 / sum E over the layer's hits
-// (the energy-weighted mean squared distance), 0 for an empty layer.  One
-// warp per sub-shower, FP32 sums in shared memory.
+// from the sub-shower's axis; R_j = sum E r / sum E over the layer's hits,
+// 0 for an empty layer.  One warp per sub-shower, FP32 sums in shared memory.
 __global__ void __launch_bounds__(256) lateral_targets_kernel(const LateralParams p) {
     __shared__ float er[8][32], es[8][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -418,8 +417,8 @@ __global__ void __launch_bounds__(256) lateral_targets_kernel(const LateralParam
                         const int jj = (k >= 0 && k < g.n_slices) ? (int)p.s2l[g.slice_off + k] - l0 : -1;
                         if (jj >= 0 && jj < kSurLayers) {
                             const float dz = h.z - z0;
-                            const float ex = h.x - fmaf(dz, tx, pr.x0), ey = h.y - fmaf(dz, ty, pr.y0);
-                            atomicAdd(&er[w][jj], h.w * fmaf(ex, ex, ey * ey));
+                            const float r = hypotf(h.x - fmaf(dz, tx, pr.x0), h.y - fmaf(dz, ty, pr.y0));
+                            atomicAdd(&er[w][jj], h.w * r);
                             atomicAdd(&es[w][jj], h.w);
                         }
                     }

@@ -4,7 +4,7 @@
 // After the step kernel has queued every particle that fell below E_s on a
 // readout slice, and the network has predicted per-layer deposit
 // distributions for the queue (means mu_j and log-variances s_j of the
-// deposit fraction of layer start + j, mean squared lateral distances q_j), these
+// deposit fraction of layer start + j, mean lateral distances rho_j), these
 // kernels
 //   1. take d_j = E mu_j, mu_j = exp(o_j - 4) (MEAN; 0 below a millionth),
 //      or split the MEAN total T = sum_j f_j of those fractions over their
@@ -278,9 +278,10 @@ __global__ void __launch_bounds__(kDepWarps * 32) sur_deposits(const SurParams p
 // with lane j writing the hit of layer start + j when its deposit is > 0 --
 // a particle's hits are consecutive, in layer order.  The hit sits at the
 // layer's mid depth, displaced from the particle's straight line by
-// sigma_j (m1, m2), sigma_j = sqrt(max(0, q_j) / 2): per layer an isotropic
-// 2-D Gaussian whose mean squared distance is the predicted q_j, with one
-// normal pair per particle (drawn lane-per-particle for the group).
+// sigma_j (m1, m2), sigma_j = max(0, rho_j) sqrt(kLateralM2 / 2): per layer
+// an isotropic 2-D Gaussian whose mean squared distance is kLateralM2 times
+// the square of the predicted mean distance rho_j, with one normal pair per
+// particle (drawn lane-per-particle for the group).
 __global__ void sur_hits(const SurParams p) {
     const unsigned n = min(*p.count, (unsigned)p.cap);
     const int lane = threadIdx.x & 31;
@@ -331,12 +332,12 @@ __global__ void sur_hits(const SurParams p) {
         base = __shfl_sync(kFull, base, end);
         const int64_t at_lane = valid ? p.soff[sh] + (int64_t)(base + run_exc) : 0;
         for (int k0 = 0; k0 < m; k0 += 8) {
-            float d[8], q2[8], zmid[8];
+            float d[8], rho[8], zmid[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const bool ld = k0 + u < m && lane < kSurLayers;
                 d[u] = ld ? p.dep[(size_t)(g0 + k0 + u) * kSurLayers + lane] : 0.0f;
-                q2[u] = ld ? p.out[(size_t)(g0 + k0 + u) * p.out_ld + 2 * kSurLayers + lane] : 0.0f;
+                rho[u] = ld ? p.out[(size_t)(g0 + k0 + u) * p.out_ld + 2 * kSurLayers + lane] : 0.0f;
             }
             // mid depths of the layers that get a hit (a deposit > 0 lies inside the detector)
 #pragma unroll
@@ -358,7 +359,7 @@ __global__ void sur_hits(const SurParams p) {
                 if (d[u] > 0.0f) {
                     const float zm = zmid[u];
                     const float dz = zm - zk;
-                    const float sig = sqrtf(0.5f * fmaxf(0.0f, q2[u]));
+                    const float sig = fmaxf(0.0f, rho[u]) * kLateralSigma;
                     p.hits[at + __popc(nz & lt)] =
                         make_float4(fmaf(sig, m1, fmaf(dz, tx, x)), fmaf(sig, m2, fmaf(dz, ty, y)), zm, d[u]);
                     if (p.tags) p.tags[at + __popc(nz & lt)] = tag;
@@ -375,7 +376,7 @@ __global__ void add_counts(const uint32_t *a, const uint32_t *b, int64_t n, uint
 
 // Training set of the surrogate from a batch of sub-showers: features of
 // each sub-shower's start and its deposit fractions per layer from the start
-// layer on (columns 0..29 of y [n][60]; the mean squared distances, columns 30..59,
+// layer on (columns 0..29 of y [n][60]; the mean distances, columns 30..59,
 // come from launch_lateral_targets).
 __global__ void training_set(const supa_primary *prim, int64_t n, const GeomDev *geoms, const int8_t *s2l,
                              const LayerInfo *linfo, const double *lsum, int stride, float e_s, float *x, float *y,
@@ -437,7 +438,7 @@ __global__ void export_surrogate(const SurParams p, int64_t n, supa_diverted_rec
         for (int j = 0; j < kSurLayers; ++j) {
             o.lmu[j] = row[j];
             o.s[j] = row[kSurLayers + j];
-            o.q2[j] = row[2 * kSurLayers + j];
+            o.rho[j] = row[2 * kSurLayers + j];
             o.dep[j] = p.dep[(size_t)i * kSurLayers + j];
         }
         o.n_hits = p.pcnt[i];

@@ -63,12 +63,18 @@ __device__ __forceinline__ double from_fixed32(unsigned long long v) {
 
 // A diverted particle: where it is and what it carries.
 // Surrogate network outputs per layer j: o_j (log link: deposit-fraction
-// mean mu_j = exp(o_j - kMuShift)), s_j (log-variance), q_j (mean squared lateral
+// mean mu_j = exp(o_j - kMuShift)), s_j (log-variance), rho_j (mean lateral
 // distance); a layer whose mean or drawn fraction is below kFractionMin of the
 // particle's energy gets no deposit.
 constexpr float kMuShift = 4.0f;
 // Floor of the predicted variance of a deposit fraction, e^s_j + kVarFloor.
 constexpr float kVarFloor = 1.0e-8f;
+// A surrogate hit's displacement is a 2-D Gaussian with mean squared distance
+// kLateralM2 rho_j^2 (sigma = rho_j sqrt(kLateralM2 / 2)): the plain
+// sub-showers' energy-weighted <r^2> / <r>^2 about their conditional mean
+// distance.
+constexpr float kLateralM2 = 1.41f;
+constexpr float kLateralSigma = 0.83964278f;  // sqrt(1.41 / 2)
 constexpr float kFractionMin = 1.0e-6f;
 
 struct SurRec {
@@ -105,7 +111,7 @@ __host__ __device__ inline void surrogate_features(float E, float ux, float uy, 
 struct SurInfer {
     int cap = 0;
     int ld = 0;            // row stride of OUT
-    float *OUT = nullptr;  // network outputs [cap][ld]: o 0..29, s 30..59, q 60..89
+    float *OUT = nullptr;  // network outputs [cap][ld]: o 0..29, s 30..59, rho 60..89
 };
 int surrogate_infer_init(supa_surrogate *s, int cap, SurInfer *inf);
 void surrogate_infer_free(SurInfer *inf);
@@ -118,7 +124,7 @@ struct SurParams {
     const SurRec *rec;
     const unsigned *count;  // queue length (device)
     int cap;
-    const float *out;       // network outputs [cap][out_ld]: o, s, q (30 each)
+    const float *out;       // network outputs [cap][out_ld]: o, s, rho (30 each)
     int out_ld;
     const supa_primary *prim;
     const GeomDev *geoms;
@@ -324,7 +330,7 @@ struct ShapeParams {
 };
 cudaError_t launch_shower_shapes(const ShapeParams &p, cudaStream_t st);
 
-// Training targets Q_j (mean squared lateral distances) of a batch of sub-showers.
+// Training targets R_j (mean lateral distances) of a batch of sub-showers.
 struct LateralParams {
     HitSource src;
     const supa_primary *prim;

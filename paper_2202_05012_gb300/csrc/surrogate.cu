@@ -2,11 +2,11 @@
 // (no counterpart in the SUPA paper): an MLP 6 -> 256 -> 256 -> 256 -> 90
 // with exact GELU -- per layer j = 0..29 from the start layer the mean
 // mu_j = exp(o_j - 4) (log link: output o_j) and log-variance s_j of the
-// deposit fraction and the mean squared lateral distance q_j of the deposits
-// from the particle's axis -- trained with Adam on
+// deposit fraction and the mean lateral distance rho_j of the deposits from
+// the particle's axis -- trained with Adam on
 //   L = mean (1/30) sum_j [(y_j - mu_j)^2 / (2 v_j) + ln(v_j) / 2
-//                          + y_j (q_j - Q_j)^2 / 2],  v_j = e^s_j + 1e-8
-// (targets: fractions y_j, energy-weighted mean squared distances Q_j), evaluated
+//                          + y_j (rho_j - R_j)^2 / 2],  v_j = e^s_j + 1e-8
+// (targets: fractions y_j, energy-weighted mean distances R_j), evaluated
 // in minibatches of `batch` rows.
 //
 // Layout.  Every GEMM is C = A * B^T with both operands K-major (tc_gemm.cuh),
@@ -36,7 +36,7 @@ using namespace supa;
 namespace {
 
 constexpr int kIn = 6, kInPad = 64, kHid = 256, kOut = 90, kOutPad = 128, kLayersOut = 30;
-constexpr int kY = 2 * kLayersOut;  // target columns: fractions, mean squared distances
+constexpr int kY = 2 * kLayersOut;  // target columns: fractions, mean distances
 constexpr int kInferLd = 96;        // outputs written by the fused inference kernel (>= kOut; 90..95 are zero)
 static_assert(kOutPad == kTileM, "d out^T is read as one full 128-row tile");
 // packed user parameter vector: W1, b1, W2, b2, W3, b3, W4, b4
@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(kLossRows * kLossLanesY)
         float gmu = 0.0f, gs = 0.0f, gr = 0.0f;
         if (live) {
             const float mu = expf(so[rl][j] - kMuShift), s = so[rl][kLayersOut + j],
-                        q2 = so[rl][2 * kLayersOut + j];
-            const float yj = sy[rl][j], dr = q2 - sy[rl][kLayersOut + j];
+                        rho = so[rl][2 * kLayersOut + j];
+            const float yj = sy[rl][j], dr = rho - sy[rl][kLayersOut + j];
             const float res = yj - mu;
             const float es = expf(s);
             const float iv = 1.0f / (es + kVarFloor);  // floored variance

@@ -422,7 +422,7 @@ def supa_export_diverted(b: int, out_dev=None, stream=None) -> int:
 # supa_diverted_record of include/supa.h (528 bytes)
 DIVERTED_RECORD_DTYPE = np.dtype([
     ("shower", "<u4"), ("slice", "<i4"), ("layer", "<i4"), ("x", "<f4"), ("y", "<f4"), ("tx", "<f4"),
-    ("ty", "<f4"), ("E", "<f4"), ("lineage", "<u8"), ("lmu", "<f4", 30), ("s", "<f4", 30), ("q2", "<f4", 30),
+    ("ty", "<f4"), ("E", "<f4"), ("lineage", "<u8"), ("lmu", "<f4", 30), ("s", "<f4", 30), ("rho", "<f4", 30),
     ("dep", "<f4", 30), ("n_hits", "<u4"), ("reserved", "<u4")])
 assert DIVERTED_RECORD_DTYPE.itemsize == 528
 

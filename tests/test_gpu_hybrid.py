@@ -214,7 +214,7 @@ def test_hybrid_matches_oracle_particle_by_particle(mode):
     #    GPU's own state, within the derived BF16 bound
     st = _state_of_records(rec)
     ref, bound = bf16_forward_bound(params64, hybrid.features(st, g, E_S))
-    got = np.concatenate([rec["lmu"], rec["s"], rec["q2"]], 1).astype(np.float64)
+    got = np.concatenate([rec["lmu"], rec["s"], rec["rho"]], 1).astype(np.float64)
     err = np.abs(got - ref)
     assert np.all(err <= bound), (err / bound).max()
     assert np.sqrt(np.mean((err / bound) ** 2)) < 0.25  # far inside the worst case
