@@ -59,6 +59,9 @@ def parse():
                     help="showers of the workload (another seed) whose diverted particles seed the training set")
     ap.add_argument("--train-set", default="matched", choices=["matched", "generic"],
                     help="hybrid workload: sub-showers from diverted particles, or generic starts (smaller)")
+    ap.add_argument("--c5-showers", type=int, default=10_000_000,
+                    help="showers of the 50-layer hybrid comparison in the default run (0: skip it)")
+    ap.add_argument("--no-mixed4", action="store_true", help="skip the uneven-batch measurement in the default run")
     ap.add_argument("--pipeline", type=int, default=1,
                     help="sub-batches per step; >1 overlaps simulation of one with downsampling of the previous")
     return ap.parse_args()
@@ -568,9 +571,20 @@ def run_supa_serial(args):
         plain = {"step_ms": elapsed_ms / args.steps, "simulate_ms": sim_ms, "steps": n_steps,
                  "profiles": profiles_of(S, b, n, L)}
         out["hybrid"] = hybrid_compare(args, S, gh, geom, prims, d_prim, n, seed, base, V, grid, oor, fbuf, plain)
+    if world == 1 and args.workload == "plain30" and (not args.no_mixed4 or (not args.no_hybrid and args.c5_showers)):
+        # free the 1M-shower batch and its buffers for the larger workloads
+        S.supa_destroy_batch(b)
+        b = None
+        del grid, oor, fbuf, hbuf
+        torch.cuda.empty_cache()
+        if not args.no_mixed4:
+            out["mixed4"] = mixed4_measure(S, 4_000_000, steps=3, warmup=1)
+        if not args.no_hybrid and args.c5_showers:
+            out["hybrid_c5"] = hybrid_c5(args, S)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_fresh(args)
-    S.supa_destroy_batch(b)
+    if b is not None:
+        S.supa_destroy_batch(b)
     S.supa_destroy_geometry(gh)
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -904,25 +918,39 @@ def e2e(args, S, b, geom, prims, seed, base, n, V, grid, oor, world):
             "d2h_bytes_per_step": d2h}
 
 
-def run_mixed4(args):
-    """Uneven batch: 4M showers, E log-uniform [1,1000] (multiplicity spans
-    ~1000x), geometries of 10/20/30/50 layers mixed in each persistent launch;
-    launch shape chosen by the autotuner; each 1M-shower launch replayed from a
-    captured CUDA graph.  Simulation only (hits and FP64 layer sums)."""
+def tail_metrics(t) -> dict:
+    """Load balance of one persistent launch from its warps' (start, end)
+    global times: the launch span, the time from the last-but-one warp
+    running out of showers to the last one, and the fraction of warp time
+    idle in the last 10 % of the span."""
+    t = np.asarray(t, dtype=np.int64)
+    t0, t1 = int(t[:, 0].min()), int(t[:, 1].max())
+    span = max(1, t1 - t0)
+    ends = np.sort(t[:, 1])
+    w0 = t1 - 0.1 * span
+    busy = np.clip(np.minimum(t[:, 1], t1) - np.maximum(t[:, 0], w0), 0, None).sum()
+    return {"launch_ms": span / 1e6, "tail_last_but_one_ms": (t1 - int(ends[-2])) / 1e6,
+            "idle_fraction_last_10pct": float(1.0 - busy / (len(t) * 0.1 * span)), "warps": int(len(t))}
+
+
+def mixed4_measure(S, n: int, steps: int, warmup: int, clocks: Clocks | None = None) -> dict:
+    """Uneven batch: n showers, E log-uniform [1,1000] (multiplicity spans
+    ~1000x), geometries of 10/20/30/50 layers mixed in each persistent
+    launch; launch shape chosen by the autotuner; each 1M-shower launch
+    replayed from a captured CUDA graph.  Simulation only (hits and FP64
+    layer sums).  The tail comes from the warps' start and end times of one
+    untimed replay of every launch."""
     import torch
 
     from paper_2202_05012_gb300 import inputs
-    from paper_2202_05012_gb300 import supa as S
 
-    torch.cuda.set_device(0)
-    n = args.showers or 4_000_000
     sub = min(n, 1_000_000)
     geoms, prims = inputs.workload_mixed4(n)
     gh = [S.supa_init_geometry(g) for g in geoms]
     d_prim = S.primaries_to_device(prims)
     cfg = {"lpt_order": 1, "max_hits": int(sub * 5000) + (16 << 20)}
     tuned, tune_ms = S.supa_autotune(gh, d_prim, sub, seed=2, cfg=cfg)
-    b = S.supa_batch_create(gh, sub, tuned)
+    b = S.supa_batch_create(gh, sub, dict(tuned, record_warp_times=1))
     graphs = []
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -940,41 +968,163 @@ def run_mixed4(args):
     torch.cuda.synchronize()
 
     def step():
-        steps = hits = 0
+        st = hi = 0
         for g in graphs:
             g.replay()
             info = S.supa_batch_get_info(b)
-            steps += info.n_steps
-            hits += info.n_hits
-        return steps, hits
+            st += info.n_steps
+            hi += info.n_hits
+        return st, hi
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
-    clocks = Clocks(0)
     torch.cuda.synchronize()
-    clocks.start()
+    if clocks is not None:
+        clocks.start()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
-    for _ in range(args.steps):
-        steps, hits = step()
+    for _ in range(steps):
+        n_steps, n_hits = step()
     t1.record()
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks is not None else None
     ms = t0.elapsed_time(t1)
-    out = {
-        "metric": METRIC, "value": args.steps * n / (ms / 1000.0), "unit": "showers/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "uneven batch: 4M showers, E log-U[1,1000], 10/20/30/50-layer geometries mixed per "
-                               "launch, graph-captured 1M-shower launches, autotuned", "showers": n,
-                   "showers_per_launch": sub, "launch_config": tuned, "autotune_sample_ms": tune_ms},
-        "particle_steps_per_s": args.steps * steps / (ms / 1000.0), "hits_per_shower": hits / n,
-        "steps_per_shower": steps / n, "gpu_launches": args.steps * len(graphs) * (1 + 3 + 3), "clocks": clk,
-    }
+    tails = []
+    for g in graphs:
+        g.replay()
+        S.supa_batch_get_info(b)
+        tails.append(tail_metrics(S.supa_batch_warp_times(b)))
     S.supa_destroy_batch(b)
     for g in gh:
         S.supa_destroy_geometry(g)
+    return {"workload": "uneven batch: 4M showers, E log-U[1,1000], 10/20/30/50-layer geometries mixed per "
+                        "launch, graph-captured 1M-shower launches, autotuned", "showers": n,
+            "showers_per_launch": sub, "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
+            "showers_per_s": steps * n / (ms / 1000.0), "particle_steps_per_s": steps * n_steps / (ms / 1000.0),
+            "hits_per_shower": n_hits / n, "steps_per_shower": n_steps / n,
+            "launch_config": {k: v for k, v in tuned.items() if k != "record_warp_times"},
+            "autotune_sample_ms": tune_ms, "gpu_launches": steps * len(graphs) * (1 + 3 + 3),
+            "tail_per_launch": tails,
+            "tail_mean": {k: float(np.mean([t[k] for t in tails])) for k in tails[0]}, "clocks": clk}
+
+
+def run_mixed4(args):
+    """The uneven batch (see mixed4_measure) as the JSON line."""
+    import torch
+
+    from paper_2202_05012_gb300 import supa as S
+
+    torch.cuda.set_device(0)
+    n = args.showers or 4_000_000
+    m = mixed4_measure(S, n, args.steps, args.warmup, Clocks(0))
+    out = {
+        "metric": METRIC, "value": m["showers_per_s"], "unit": "showers/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": m["workload"], "showers": n, "showers_per_launch": m["showers_per_launch"],
+                   "launch_config": m["launch_config"], "autotune_sample_ms": m["autotune_sample_ms"]},
+        "particle_steps_per_s": m["particle_steps_per_s"], "hits_per_shower": m["hits_per_shower"],
+        "steps_per_shower": m["steps_per_shower"], "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
+        "tail_mean": m["tail_mean"],
+    }
     print(json.dumps(out), flush=True)
+
+
+def c5_pass(S, gh, p, d, n, seed, sub, V, grid, oor, hits_per_shower, net=None, e_s=0.0, mode=1):
+    """The whole path over n showers of the 50-layer workload in sub-batches
+    of `sub`: simulate (plain, or hybrid with `net` below e_s), then images
+    and point cloud of every chunk of V showers in one pass.  Each
+    sub-batch's work is bracketed by CUDA events (the whole path, and the
+    simulation alone); the profiles are accumulated between sub-batches,
+    outside the events."""
+    import torch
+
+    from paper_2202_05012_gb300.surrogate_train import PROFILE_BINS, PROFILE_RMAX
+    L = grid.shape[1]
+    mean_e = float(p["E"][:n].mean())
+    max_hits = int(sub * hits_per_shower) + (8 << 20)
+    hb = S.supa_batch_create([gh], sub, {"max_hits": max_hits, "lpt_order": 1})
+    try:
+        if net is not None:
+            S.supa_batch_set_surrogate(hb, net, e_s, int(4.0 * mean_e / e_s * sub) + (1 << 20), mode)
+        hbuf = torch.empty((max_hits, 4), dtype=torch.float32, device="cuda")
+        lo = torch.zeros(L, dtype=torch.float64, device="cuda")
+        la = torch.zeros(PROFILE_BINS, dtype=torch.float64, device="cuda")
+        evs = []
+        steps = diverted = hits = 0
+        for j in range(0, n, sub):
+            m = min(sub, n - j)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
+            S.supa_simulate(hb, d[j * 24:(j + m) * 24], m, seed, j)
+            ev[1].record()
+            for c0 in range(0, m, V):
+                S.supa_voxelize_fetch(hb, c0, min(m, c0 + V), grid, oor, hbuf)
+            ev[2].record()
+            evs.append(ev)
+            info = S.supa_batch_get_info(hb)
+            steps += info.n_steps
+            diverted += info.n_diverted
+            hits += info.n_hits
+            S.supa_profiles(hb, 0, m, PROFILE_BINS, PROFILE_RMAX, lo, la)
+        torch.cuda.synchronize()
+        total_ms = sum(e[0].elapsed_time(e[2]) for e in evs)
+        sim_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+        return {"showers_per_s": n / (total_ms / 1000.0), "simulate_showers_per_s": n / (sim_ms / 1000.0),
+                "particle_steps_per_s": steps / (sim_ms / 1000.0), "particle_steps_per_shower": steps / n,
+                "diverted_per_shower": diverted / n, "hits_per_shower": hits / n, "ms": total_ms,
+                "simulate_ms": sim_ms, "sub_batch_showers": sub,
+                "profiles": (lo.cpu().numpy() / n, la.cpu().numpy() / n)}
+    finally:
+        S.supa_destroy_batch(hb)
+
+
+def hybrid_c5(args, S) -> dict:
+    """The surrogate on its own workload: 10M showers, seed 4, E log-uniform
+    [10,1000], 0-45 deg, 50 layers, 50 x 128 x 128 images (written chunk by
+    chunk with the point cloud), run plainly and with the network below E_s
+    in both modes on the same seeds; the network is trained first on 10M
+    sub-showers started from the particles showers of the same workload
+    (another seed) divert, 20 epochs."""
+    import torch
+
+    from paper_2202_05012_gb300 import inputs
+    from paper_2202_05012_gb300 import surrogate_train as T
+    n = args.c5_showers
+    g5, p5 = inputs.workload_plain50(n)
+    gh = S.supa_init_geometry(g5)
+    d5 = S.primaries_to_device(p5)
+    L = g5.n_layers
+    V = 2048
+    grid = torch.empty((V, L, g5.ny, g5.nx), dtype=torch.float32, device="cuda")
+    oor = torch.empty(V, dtype=torch.float64, device="cuda")
+    mean_e = float(p5["E"].mean())
+    net, tlog = matched_training(args, T, lambda m: inputs.workload_plain50(m, seed=14), args.e_s, mean_e)
+    out = {"workload": f"hybrid 50-layer showers: {n} showers, seed 4, E log-U[10,1000], 0-45 deg, 50 layers, "
+                       "50x128x128 images and point cloud, plain vs surrogate on the same seeds",
+           "showers": n, "e_s": args.e_s, "profile_binning": profile_binning(),
+           "training": {k: v for k, v in tlog.items() if k != "loss_per_epoch"},
+           "training_loss_last_epoch": tlog["loss_per_epoch"][-1]}
+    try:
+        # a short pass of each kind first (launch paths, allocations)
+        c5_pass(S, gh, p5, d5, 20_000, 4, 20_000, V, grid, oor, 9000)
+        plain = c5_pass(S, gh, p5, d5, n, 4, 250_000, V, grid, oor, 9000)
+        ref = plain.pop("profiles")
+        out["plain"] = plain
+        sub_h = 100_000
+        for mode, name in ((S.SUPA_SURROGATE_MEAN, "mean"), (S.SUPA_SURROGATE_SAMPLE, "sample")):
+            c5_pass(S, gh, p5, d5, 20_000, 4, 20_000, V, grid, oor, max(400, 40 * mean_e), net, args.e_s, mode)
+            r = c5_pass(S, gh, p5, d5, n, 4, sub_h, V, grid, oor, max(400, 40 * mean_e), net, args.e_s, mode)
+            r["profile_error"] = profile_errors(ref, r.pop("profiles"))
+            r["vs_plain"] = {"showers_per_s": r["showers_per_s"] / plain["showers_per_s"],
+                             "simulate_showers_per_s": r["simulate_showers_per_s"] / plain["simulate_showers_per_s"]}
+            out[name] = r
+    finally:
+        S.supa_surrogate_destroy(net)
+        S.supa_destroy_geometry(gh)
+        del grid, oor, d5
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_hybrid(args):

@@ -133,6 +133,9 @@ typedef struct {
                                   1 leaves room on every SM for step-kernel
                                   blocks of another batch to run alongside  */
     int64_t max_hits;        /* hit pool capacity (0: sized from free memory)*/
+    int32_t record_warp_times; /* 1: every step-kernel warp records when it
+                                  starts and when it runs out of showers
+                                  (supa_batch_warp_times)                    */
 } supa_launch_config;
 
 /* Per-batch results after a simulation (device pointers stay owned by the
@@ -205,6 +208,16 @@ int supa_autotune(const supa_geometry *const *geoms, int32_t n_geoms, const supa
  * result pointers.  Returns SUPA_ERR_OVERFLOW if the hit pool or a particle
  * stack overflowed (re-run with a smaller batch or a larger max_hits). */
 int supa_batch_get_info(supa_batch *b, supa_batch_info *info, void *stream);
+
+/* Load balance of the last simulation of a batch created with
+ * record_warp_times = 1 (no counterpart in the paper; the scheduling of an
+ * uneven batch): for each warp of the persistent step kernel the GPU's
+ * global timer (ns) when it started and when it found the shower queue
+ * empty, [n_warps][2] uint64 into host memory dst (capacity warps).  Writes
+ * min(n_warps, capacity) pairs and n_warps to *n_warps.  SUPA_ERR_INVALID_ARG
+ * without record_warp_times, SUPA_ERR_NOT_READY before a simulation.
+ * Synchronous. */
+int supa_batch_warp_times(supa_batch *b, uint64_t *dst, int64_t capacity, int64_t *n_warps);
 
 /* Copy hits [first_hit, first_hit + max_hits) of the batch, in shower order
  * (the point cloud of Sec. 3: each hit is (x, y, z, E)), into dst, a device

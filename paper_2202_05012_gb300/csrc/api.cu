@@ -122,6 +122,7 @@ struct supa_batch {
     int *d_ctrl = nullptr;
     unsigned long long *d_totals = nullptr;
     SpillRec *d_spill = nullptr;
+    unsigned long long *d_warp_times = nullptr;  // [warps][2] (record_warp_times)
     int spill_cap = 0;
     // launch shape
     int grid = 0, block = 0, stack_cap = 0, stage_cap = 0, flush_thr = 0, minb = 3, voxel_ctas = 0;
@@ -331,7 +332,7 @@ int supa_destroy_batch(supa_batch *b) {
     void *ptrs[] = {b->d_geoms, b->d_tstop, b->d_tss, b->d_regions, b->d_s2l, b->d_zmid, b->d_prim, b->d_queue,
                     b->d_bucket, b->d_pool, b->d_tags, b->d_page_next, b->d_hit_start, b->d_hit_count,
                     b->d_steps, b->d_lsum, b->d_dead, b->d_leak, b->d_escape, b->d_offsets, b->d_scan_tmp,
-                    b->d_ctrl, b->d_totals, b->d_spill, b->d_stage};
+                    b->d_ctrl, b->d_totals, b->d_spill, b->d_stage, b->d_warp_times};
     for (void *p : ptrs) cudaFree(p);
     delete b;
     return SUPA_OK;
@@ -459,6 +460,7 @@ int supa_batch_create(const supa_geometry *const *geoms, int32_t n_geoms, int64_
     if (e == cudaSuccess) e = dalloc(&b->d_ctrl, 4);
     if (e == cudaSuccess) e = dalloc(&b->d_totals, 2);
     if (e == cudaSuccess) e = dalloc(&b->d_spill, (size_t)n_warps * b->spill_cap);
+    if (e == cudaSuccess && cfg.record_warp_times) e = dalloc(&b->d_warp_times, (size_t)n_warps * 2);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_geoms, recs.data(), recs.size() * sizeof(GeomDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tstop, ts.data(), ts.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tss, tss.data(), tss.size() * 8, cudaMemcpyHostToDevice);
@@ -528,6 +530,7 @@ int supa_simulate(supa_batch *b, const supa_primary *prim_dev, int64_t n, uint64
     p.error = b->d_ctrl + 2;
     p.totals = b->d_totals;
     p.spill = b->d_spill;
+    p.warp_times = b->d_warp_times;
     p.spill_cap = b->spill_cap;
     p.stack_cap = b->stack_cap;
     p.warp_smem_bytes = b->warp_bytes;
@@ -672,6 +675,20 @@ int supa_export_diverted(supa_batch *b, supa_primary *out_dev, int64_t capacity,
     SUPA_CUDA(launch_export_diverted(b->d_sq_rec, std::min(n, capacity), b->d_prim, out_dev, st));
     SUPA_CUDA(cudaStreamSynchronize(st));
     *n_out = n;
+    return SUPA_OK;
+}
+
+int supa_batch_warp_times(supa_batch *b, uint64_t *dst, int64_t capacity, int64_t *n_warps) {
+    if (!b || !n_warps || capacity < 0 || (capacity > 0 && !dst))
+        return fail(SUPA_ERR_INVALID_ARG, "supa_batch_warp_times: bad argument");
+    *n_warps = 0;
+    if (!b->d_warp_times) return fail(SUPA_ERR_INVALID_ARG, "the batch was created without record_warp_times");
+    if (b->last_n < 0) return fail(SUPA_ERR_NOT_READY, "no simulation has been enqueued on this batch");
+    const int64_t nw = (int64_t)b->grid * (b->block / 32);
+    SUPA_CUDA(cudaDeviceSynchronize());
+    if (capacity > 0)
+        SUPA_CUDA(cudaMemcpy(dst, b->d_warp_times, (size_t)std::min(nw, capacity) * 16, cudaMemcpyDeviceToHost));
+    *n_warps = nw;
     return SUPA_OK;
 }
 

@@ -217,6 +217,8 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
 
     PageCursor pc{-1, kPageHits};
     unsigned long long warp_steps = 0, warp_hits = 0;
+    unsigned long long t_start = 0;
+    if (p.warp_times && lane == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
 
     while (true) {
         int q = 0;
@@ -517,6 +519,12 @@ __global__ void __launch_bounds__(256, MINB) supa_step_kernel(const StepParams p
     if (lane == 0 && (warp_steps | warp_hits)) {
         atomicAdd(&p.totals[0], warp_steps);
         atomicAdd(&p.totals[1], warp_hits);
+    }
+    if (p.warp_times && lane == 0) {
+        unsigned long long t_end;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+        p.warp_times[2 * warp_global] = t_start;
+        p.warp_times[2 * warp_global + 1] = t_end;
     }
 }
 

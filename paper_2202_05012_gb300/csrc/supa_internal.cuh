@@ -195,6 +195,7 @@ struct StepParams {
     int stage_cap;        // staged hits per warp (flush_thr + 32; 0: hits written directly)
     int flush_thr;        // staged hits that trigger a flush
     int warp_smem_bytes;  // shared memory per warp
+    unsigned long long *warp_times;  // [warps][2] start / end global time (ns), or null
     // hybrid path (e_s = 0: off)
     float e_s;
     const LayerInfo *linfo;  // per geometry layer (layer_off + l)

@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(kLossRows * kLossLanesY)
             const float yj = sy[rl][j], dr = rho - sy[rl][kLayersOut + j];
             const float res = yj - mu;
             const float es = expf(s);
-            const float iv = 1.0f / (es + kVarFloor);  // floored variance
-            l += 0.5 * (double)(res * res * iv) - 0.5 * log((double)iv) + 0.5 * (double)(yj * dr * dr);
+            const float v = es + kVarFloor;  // floored variance
+            const float iv = 1.0f / v;
+            l += 0.5 * (double)(res * res * iv) + 0.5 * (double)logf(v) + 0.5 * (double)(yj * dr * dr);
             gmu = -res * iv * mu * inv;  // through the log link: d mu / d o = mu
             gs = 0.5f * es * iv * (1.0f - res * res * iv) * inv;
             gr = yj * dr * inv;

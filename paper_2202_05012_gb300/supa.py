@@ -31,7 +31,7 @@ EXPORTED = (
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
     "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc", "supa_export_diverted",
     "supa_shower_shapes", "supa_layer_images_cells", "supa_voxelize_layers", "supa_voxelize_fetch",
-    "supa_check_wait_expiry", "supa_export_surrogate",
+    "supa_check_wait_expiry", "supa_export_surrogate", "supa_batch_warp_times",
 )
 
 
@@ -62,7 +62,7 @@ class supa_launch_config(ctypes.Structure):
     _fields_ = [
         ("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
         ("flush_threshold", ctypes.c_int32), ("record_tags", ctypes.c_int32), ("lpt_order", ctypes.c_int32),
-        ("voxel_ctas_per_sm", ctypes.c_int32), ("max_hits", ctypes.c_int64),
+        ("voxel_ctas_per_sm", ctypes.c_int32), ("max_hits", ctypes.c_int64), ("record_warp_times", ctypes.c_int32),
     ]
 
 
@@ -128,6 +128,7 @@ def lib(build_if_missing: bool = True):
         L.supa_shower_offsets_noalloc.argtypes = [_VP, _I64, _VP, _VP]
         L.supa_export_diverted.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I64), _VP]
         L.supa_export_surrogate.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I64), _VP]
+        L.supa_batch_warp_times.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I64)]
         L.supa_shower_shapes.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP]
         L.supa_layer_images_cells.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32]
         L.supa_voxelize_layers.argtypes = [_VP, _I64, _I64, _VP, ctypes.c_int32, _VP, ctypes.c_int32, _VP, _VP,
@@ -216,6 +217,16 @@ def supa_batch_create(geoms: list[int], max_showers: int, cfg: dict | None = Non
     _check(lib().supa_batch_create(arr, len(geoms), int(max_showers), _cfg(cfg), ctypes.byref(out)),
            "supa_batch_create")
     return out.value
+
+
+def supa_batch_warp_times(b: int) -> np.ndarray:
+    """[n_warps, 2] uint64 start / end times (ns, the GPU's global timer) of
+    every step-kernel warp in the last simulation (record_warp_times)."""
+    n = _I64(0)
+    _check(lib().supa_batch_warp_times(b, None, 0, ctypes.byref(n)), "supa_batch_warp_times")
+    out = np.zeros((n.value, 2), dtype=np.uint64)
+    _check(lib().supa_batch_warp_times(b, out.ctypes.data, n.value, ctypes.byref(n)), "supa_batch_warp_times")
+    return out
 
 
 def supa_destroy_batch(b: int):

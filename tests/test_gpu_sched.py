@@ -82,3 +82,43 @@ def test_graph_captured_simulate_and_voxelize_match_eager():
     finally:
         S.supa_destroy_batch(b)
         S.supa_destroy_geometry(gh)
+
+
+def test_warp_timeline_brackets_the_launch_and_changes_nothing():
+    """record_warp_times: one (start, end) pair per warp of the persistent
+    launch, every end after its start, all inside the launch as CUDA events
+    time it; the results equal those of a batch without the timeline."""
+    import torch
+    geoms, p = inputs.workload_mixed4(30_000)
+    gh = [S.supa_init_geometry(g) for g in geoms]
+    try:
+        d = S.primaries_to_device(p)
+        cfg = {"lpt_order": 1, "max_hits": len(p) * 5000, "blocks_per_sm": 3, "warps_per_block": 8}
+        res = []
+        for rec in (1, 0):
+            b = S.supa_batch_create(gh, len(p), dict(cfg, record_warp_times=rec))
+            try:
+                S.supa_simulate(b, d, len(p), 2)  # warm
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                S.supa_simulate(b, d, len(p), 2)
+                e1.record()
+                res.append(_results(b, len(p))[1])
+                if rec:
+                    t = S.supa_batch_warp_times(b).astype(np.int64)
+                    sms = torch.cuda.get_device_properties(0).multi_processor_count
+                    assert t.shape == (3 * sms * 8, 2)
+                    assert np.all(t[:, 1] >= t[:, 0]) and np.all(t[:, 0] > 0)
+                    span_ms = (t[:, 1].max() - t[:, 0].min()) / 1e6
+                    assert 0 < span_ms <= e0.elapsed_time(e1) * 1.05 + 0.05
+                else:
+                    with pytest.raises(S.SupaError) as ei:
+                        S.supa_batch_warp_times(b)
+                    assert ei.value.code == S.SUPA_ERR_INVALID_ARG
+            finally:
+                S.supa_destroy_batch(b)
+        for k in ("counts", "layer_sum", "steps"):
+            assert np.array_equal(res[0][k], res[1][k]), k
+    finally:
+        for g in gh:
+            S.supa_destroy_geometry(g)
