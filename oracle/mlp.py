@@ -3,7 +3,8 @@
 The surrogate has no counterpart in the SUPA paper: it is a small MLP that
 stands in for the low-energy tail of a shower (sub-showers below a cutoff
 energy E_s).  Architecture: 6 inputs -> 3 hidden layers of 256 with GELU
-(exact form x * Phi(x)) -> 90 outputs o = 30 log-link outputs o_j of the
+(the tanh form of Hendrycks and Gimpel, "Gaussian Error Linear Units",
+2016: 0.5 z (1 + tanh(sqrt(2 / pi) (z + 0.044715 z^3)))) -> 90 outputs o = 30 log-link outputs o_j of the
 means mu_j = exp(o_j - MU_SHIFT) and 30 log-variances s_j of the per-layer
 deposit fractions, and 30 mean lateral distances rho_j of each layer's
 deposits from the sub-shower's axis, layers counted from the sub-shower's
@@ -28,7 +29,6 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.special import erf
 
 N_IN, N_HID, N_OUT, N_LAYERS_OUT = 6, 256, 90, 30
 MU_SHIFT = 4.0  # mu_j = exp(o_j - MU_SHIFT): outputs near 0 at initialisation give means near 1/55
@@ -37,13 +37,18 @@ SHAPES = [(N_HID, N_IN), (N_HID, N_HID), (N_HID, N_HID), (N_OUT, N_HID)]
 LAMBDA_R = 1.0  # weight of the lateral term
 
 
+GELU_C = math.sqrt(2.0 / math.pi)
+GELU_A = 0.044715
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(GELU_C * (z + GELU_A * z ** 3)))
 
 
 def gelu_grad(z):
-    # d/dz [z Phi(z)] = Phi(z) + z phi(z)
-    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+    # d/dz: 0.5 (1 + t) + 0.5 z (1 - t^2) w'(z), t = tanh(w), w = c (z + a z^3)
+    t = np.tanh(GELU_C * (z + GELU_A * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * GELU_C * (1.0 + 3.0 * GELU_A * z * z)
 
 
 def forward(params, X):

@@ -27,6 +27,18 @@ def test_gelu_and_its_derivative():
     np.testing.assert_allclose(mlp.gelu_grad(z), fd, rtol=1e-7, atol=1e-9)
 
 
+def test_gelu_is_the_tanh_form():
+    """The tanh form of GELU (torch's approximate="tanh", a library routine),
+    within 5e-4 of the erf form z Phi(z)."""
+    torch = pytest.importorskip("torch")
+    from scipy.special import erf
+    z = np.linspace(-9, 9, 3601)
+    ref = torch.nn.functional.gelu(torch.from_numpy(z), approximate="tanh").numpy()
+    np.testing.assert_allclose(mlp.gelu(z), ref, rtol=1e-14, atol=1e-15)
+    exact = 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+    assert 4e-4 < np.abs(mlp.gelu(z) - exact).max() < 5e-4
+
+
 def test_backward_matches_central_finite_differences():
     params = inputs.mlp_init(3, shapes=((16, 6), (16, 16), (16, 16), (90, 16)))
     params = [(W, np.random.default_rng(i).normal(0, 0.1, b.shape)) for i, (W, b) in enumerate(params)]
@@ -63,7 +75,7 @@ def test_matches_torch_nn_float64():
     for i, lin in enumerate(layers):
         h = lin(h)
         if i < 3:
-            h = torch.nn.functional.gelu(h, approximate="none")
+            h = torch.nn.functional.gelu(h, approximate="tanh")
     mu, s, rho = torch.exp(h[:, :30] - mlp.MU_SHIFT), h[:, 30:60], h[:, 60:]
     yt, rt = torch.from_numpy(Y[:, :30]), torch.from_numpy(Y[:, 30:])
     v = torch.exp(s) + mlp.VAR_FLOOR
