@@ -366,7 +366,8 @@ int supa_voxelize_hits(const supa_geometry *g, const float *hits_dev, const int6
  * per-layer deposits.  The network maps 6 features (log E, the direction
  * cosines u_x, u_y, u_z, the position of the start slice within its layer,
  * the number of layers left behind the start layer) through three hidden
- * layers of 256 with GELU to 90 outputs: log-link outputs o_j of the means
+ * layers of 256 with GELU (its tanh form, z (1 + tanh(sqrt(2 / pi) (z +
+ * 0.044715 z^3))) / 2) to 90 outputs: log-link outputs o_j of the means
  * mu_j = exp(o_j - 4) and log-variances s_j of the deposit fractions of
  * layers start + j, j = 0..29, and the mean lateral distances rho_j of
  * those deposits from the particle's axis.  Targets: fractions y_j and

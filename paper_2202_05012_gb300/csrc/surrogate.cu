@@ -1,6 +1,6 @@
 // surrogate.cu -- the BF16 tensor-core surrogate network of the hybrid path
 // (no counterpart in the SUPA paper): an MLP 6 -> 256 -> 256 -> 256 -> 90
-// with exact GELU -- per layer j = 0..29 from the start layer the mean
+// with GELU (tanh form) -- per layer j = 0..29 from the start layer the mean
 // mu_j = exp(o_j - 4) (log link: output o_j) and log-variance s_j of the
 // deposit fraction and the mean lateral distance rho_j of the deposits from
 // the particle's axis -- trained with Adam on

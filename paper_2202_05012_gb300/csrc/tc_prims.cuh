@@ -166,27 +166,29 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[16]) {
                  : "memory");
 }
 
-// erf for the GELU epilogues: the rational approximation of Abramowitz &
-// Stegun, Handbook of Mathematical Functions (1964), formula 7.1.26 (after
-// Hastings), |error| <= 1.5e-7 for x >= 0, extended by odd symmetry -- far
-// below the BF16 resolution of the stored activations.  The reciprocal is
-// the hardware approximation (at most 1 ulp off), which moves the result by
-// less than 1e-7.
-__device__ __forceinline__ float erf_as(float x) {
-    const float a = fabsf(x);
+// GELU in its tanh form (Hendrycks and Gimpel, "Gaussian Error Linear
+// Units", 2016): GELU(z) = z (1 + t) / 2, t = tanh(w), w = c (z + a z^3),
+// c = sqrt(2 / pi), a = 0.044715.  tanh from the SFU (tanh.approx.f32,
+// relative error below 2^-10.9: GELU off by less than 2.5e-4 |z|, below the
+// BF16 rounding of a stored activation z > 0).  Its derivative is
+// (1 + t) / 2 + z (1 - t^2) c (1 + 3 a z^2) / 2.
+constexpr float kGeluC = 0.7978845608028654f, kGeluA = 0.044715f;
+
+__device__ __forceinline__ float tanh_sfu(float x) {
     float t;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, a, 1.0f)));
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-    return copysignf(1.0f - poly * __expf(-a * a), x);
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(x));
+    return t;
 }
 
-// GELU(z) = z Phi(z) with Phi(z) = (1 + erf(z / sqrt 2)) / 2; its derivative
-// Phi(z) + z phi(z), phi the standard normal density.
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu(float z) {
+    const float t = tanh_sfu(kGeluC * fmaf(kGeluA * z, z * z, z));
+    return 0.5f * fmaf(z, t, z);
+}
 
 __device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * __expf(-0.5f * z * z) * 0.39894228040143268f;
+    const float z2 = z * z;
+    const float t = tanh_sfu(kGeluC * fmaf(kGeluA * z, z2, z));
+    return 0.5f * (1.0f + t) + 0.5f * z * fmaf(-t, t, 1.0f) * kGeluC * fmaf(3.0f * kGeluA, z2, 1.0f);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -195,31 +197,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // The same GELU for two values at once, as BF16, with packed FP32x2
-// arithmetic.  With Phi(z) = 1 - erfc(a) / 2 for z >= 0 and erfc(a) / 2 for
-// z < 0 (a = |z| / sqrt 2), GELU(z) = z Phi(z) = max(z, 0) - |z| erfc(a) / 2,
-// and formula 7.1.26 gives erfc(a) = t P(t) exp(-a^2), t = 1 / (1 + p a),
-// with the same constants as erf_as (here folded: -P / 2, p / sqrt 2, and
-// exp(-a^2) = 2^(-z^2 log2(e) / 2)).
+// arithmetic: w = z (c + c a z^2), then z (1 + t) / 2.
 __device__ __forceinline__ uint32_t gelu2_bf16(float2 z) {
-    constexpr float kP = 0.3275911f * 0.70710678118654752f;
-    const float2 az = make_float2(fabsf(z.x), fabsf(z.y));
-    const float2 d = __ffma2_rn(az, make_float2(kP, kP), make_float2(1.0f, 1.0f));
-    float2 t;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t.x) : "f"(d.x));
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t.y) : "f"(d.y));
-    float2 p = __ffma2_rn(t, make_float2(-0.5f * 1.061405429f, -0.5f * 1.061405429f),
-                          make_float2(0.5f * 1.453152027f, 0.5f * 1.453152027f));
-    p = __ffma2_rn(t, p, make_float2(-0.5f * 1.421413741f, -0.5f * 1.421413741f));
-    p = __ffma2_rn(t, p, make_float2(0.5f * 0.284496736f, 0.5f * 0.284496736f));
-    p = __ffma2_rn(t, p, make_float2(-0.5f * 0.254829592f, -0.5f * 0.254829592f));
-    p = __fmul2_rn(t, p);  // -t P(t) / 2
-    constexpr float kE = -0.5f * 1.4426950408889634f;
-    const float2 w = __fmul2_rn(__fmul2_rn(z, make_float2(kE, kE)), z);
-    float2 e;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(w.x));
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(w.y));
-    const float2 hq = __fmul2_rn(p, e);  // -erfc(a) / 2
-    const float2 h = __ffma2_rn(az, hq, make_float2(fmaxf(z.x, 0.0f), fmaxf(z.y, 0.0f)));
+    constexpr float kC3 = kGeluC * kGeluA;
+    const float2 u = __fmul2_rn(z, z);
+    const float2 w = __fmul2_rn(z, __ffma2_rn(u, make_float2(kC3, kC3), make_float2(kGeluC, kGeluC)));
+    const float2 t = make_float2(tanh_sfu(w.x), tanh_sfu(w.y));
+    const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
+    const float2 h = __ffma2_rn(hz, t, hz);
     return pack_bf16(h.x, h.y);
 }
 
