@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="supa", choices=["supa", "reference"])
-    ap.add_argument("--workload", default="plain30", choices=["plain10", "plain30", "mixed4", "plain50", "surrogate", "hybrid"])
+    ap.add_argument("--workload", default="plain30",
+                    choices=["plain10", "plain30", "mixed4", "plain50", "surrogate", "hybrid", "forward"])
     ap.add_argument("--e-s-sweep", type=float, nargs="+", default=[0.2, 0.5, 1.0, 2.0, 5.0])
     ap.add_argument("--showers", type=int, default=0, help="override the batch size")
     ap.add_argument("--voxel-chunk", type=int, default=32768)
@@ -1175,6 +1176,46 @@ def run_hybrid(args):
                       "training": {k: v for k, v in tlog.items() if k != "loss_per_epoch"}}), flush=True)
 
 
+def run_forward(args):
+    """The surrogate network's inference kernel alone: W warm-up and K timed
+    supa_surrogate_forward calls on n random feature rows (default 4.5M, the
+    queue of about 40k 50-layer showers at E_s = 1), 96-float output rows as
+    the hybrid path writes them; TFLOP/s of algorithmic flops (311,296 per
+    row) against the measured BF16 peak."""
+    import torch
+
+    from paper_2202_05012_gb300 import inputs
+    from paper_2202_05012_gb300 import supa as S
+    torch.cuda.set_device(0)
+    n = args.showers or 4_500_000
+    s = S.supa_surrogate_create(256, S.pack_mlp_params(inputs.mlp_init(8)))
+    rng = np.random.default_rng(2)
+    X = np.stack([rng.uniform(-3, 0, n), *rng.normal(0, 0.3, (2, n)), rng.uniform(0.7, 1, n), rng.uniform(0, 1, n),
+                  rng.uniform(0, 1, n)], 1).astype(np.float32)
+    xd = torch.from_numpy(X).cuda()
+    out = torch.empty((n, 96), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        S.supa_surrogate_forward(s, xd, n, out)
+    S.supa_surrogate_check(s)
+    ms = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        e0.record()
+        S.supa_surrogate_forward(s, xd, n, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    S.supa_surrogate_check(s)
+    S.supa_surrogate_destroy(s)
+    flops = 2 * (6 * 256 + 2 * 256 * 256 + 256 * 90) * n
+    pk, pk_kind = peaks()
+    best = min(ms)
+    print(json.dumps({"metric": "surrogate inference TFLOP/s (algorithmic)", "value": flops / (best / 1000) / 1e12,
+                      "unit": "TFLOP/s", "rows": n, "ms_per_call": ms, "ms_best": best,
+                      "frac_of_bf16_burst": flops / (best / 1000) / 1e12 / pk["bf16_tflops"], "peak_source": pk_kind,
+                      "kernel": "sur_mlp_kernel"}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1185,6 +1226,8 @@ def main():
         run_surrogate(args)
     elif args.workload == "hybrid":
         run_hybrid(args)
+    elif args.workload == "forward":
+        run_forward(args)
     else:
         run_supa(args)
 
