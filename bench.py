@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--train-samples", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=2e-3, help="initial learning rate")
+    ap.add_argument("--batch", type=int, default=16384, help="training minibatch rows (a multiple of 128)")
     ap.add_argument("--lr-final", type=float, default=5e-5, help="learning rate of the last epoch (geometric decay)")
     ap.add_argument("--train-showers", type=int, default=0,
                     help="showers of the workload (another seed) whose diverted particles seed the training set")
@@ -680,7 +681,7 @@ def matched_training(args, T, make, e_s, mean_e):
     n_show = args.train_showers or int(min(2_000_000, max(50_000, 2.5 * args.train_samples * e_s / mean_e)))
     g_t, p_t = make(n_show)
     data = T.training_set_matched(g_t, p_t, e_s, args.train_samples, seed=5)
-    net, log = T.train(data, epochs=args.epochs, lr=args.lr, lr_final=args.lr_final)
+    net, log = T.train(data, epochs=args.epochs, batch=args.batch, lr=args.lr, lr_final=args.lr_final)
     return net, {"samples": data["n"], "data_seconds": data["seconds"], "training_showers": n_show,
                  "set": "matched: diverted particles of the workload's showers (seed 11/14), stepped plainly",
                  **log}
