@@ -336,6 +336,45 @@ cudaError_t backward(supa_surrogate *s, const float *y, cudaStream_t st) {
     return gemm(s->mG1T, s->mX0Tb, a, st);
 }
 
+// One minibatch (packed inputs in X0/X0T, targets y) up to the gradients in
+// s->grad (zeroed first) and the loss added to *s->loss_tmp: the fused pass
+// per 128-row tile (forward, loss gradient, data-gradient chain; bias
+// gradients), then the four weight gradients dW = G^T H as split-K GEMMs
+// over the rows.
+cudaError_t train_pass(supa_surrogate *s, const float *y, cudaStream_t st) {
+    const int B = s->B;
+    cudaError_t e = cudaMemsetAsync(s->grad, 0, Off::total * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    TrainPassArgs t{};
+    t.B = B;
+    t.b1 = s->master + Off::b1;
+    t.b2 = s->master + Off::b2;
+    t.b3 = s->master + Off::b3;
+    t.b4 = s->master + Off::b4;
+    t.y = y;
+    t.Z1 = s->Z1; t.Z2 = s->Z2; t.Z3 = s->Z3;
+    t.H1T = s->H1T; t.H2T = s->H2T; t.H3T = s->H3T;
+    t.G4T = s->G4T; t.G3T = s->G3T; t.G2T = s->G2T; t.G1T = s->G1T;
+    t.gb1 = s->grad + Off::b1; t.gb2 = s->grad + Off::b2; t.gb3 = s->grad + Off::b3; t.gb4 = s->grad + Off::b4;
+    t.loss_sum = s->loss_tmp;
+    t.error = s->error;
+    if ((e = launch_train_pass(s->mX0, s->mW1, s->mW2, s->mW3, s->mW4, s->mW4T, s->mW3T, s->mW2T, t, st)) !=
+        cudaSuccess)
+        return e;
+    GemmArgs a = gargs(kOutPad, kHid, B, EPI_ATOMIC_F32, s->error);
+    a.out_f32 = s->grad + Off::W4; a.ld = kHid;
+    if ((e = gemm(s->mG4T, s->mH3Tb, a, st)) != cudaSuccess) return e;
+    a = gargs(kHid, kHid, B, EPI_ATOMIC_F32, s->error);
+    a.out_f32 = s->grad + Off::W3; a.ld = kHid;
+    if ((e = gemm(s->mG3T, s->mH2Tb, a, st)) != cudaSuccess) return e;
+    a = gargs(kHid, kHid, B, EPI_ATOMIC_F32, s->error);
+    a.out_f32 = s->grad + Off::W2; a.ld = kHid;
+    if ((e = gemm(s->mG2T, s->mH1Tb, a, st)) != cudaSuccess) return e;
+    a = gargs(kHid, kInPad, B, EPI_ATOMIC_F32, s->error);
+    a.out_f32 = s->grad + Off::W1; a.ld = kInPad;
+    return gemm(s->mG1T, s->mX0Tb, a, st);
+}
+
 int check_error_word(supa_surrogate *s) {
     int h = 0;
     if (cudaMemcpy(&h, s->error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SUPA_ERR_CUDA;
@@ -514,8 +553,7 @@ int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float 
     if (cudaMemsetAsync(s->loss_tmp, 0, sizeof(double), st) != cudaSuccess)
         return sfail(SUPA_ERR_CUDA, "memset failed");
     pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, nullptr, s->B, s->X0, s->X0T);
-    cudaError_t e = forward(s, st);
-    if (e == cudaSuccess) e = backward(s, y_dev, st);
+    cudaError_t e = train_pass(s, y_dev, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("gradients: ") + cudaGetErrorString(e));
     int rc = check_error_word(s);
@@ -535,14 +573,11 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
     cudaStream_t st = (cudaStream_t)stream;
     double *loss = loss_acc_dev ? loss_acc_dev : s->loss_tmp;
     pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, nullptr, s->B, s->X0, s->X0T);
-    cudaError_t e = forward(s, st);
-    if (e == cudaSuccess) {
-        // backward() writes the minibatch loss into s->loss_tmp; point it at the accumulator
-        double *keep = s->loss_tmp;
-        s->loss_tmp = loss;
-        e = backward(s, y_dev, st);
-        s->loss_tmp = keep;
-    }
+    // train_pass() adds the minibatch loss to s->loss_tmp; point it at the accumulator
+    double *keep = s->loss_tmp;
+    s->loss_tmp = loss;
+    cudaError_t e = train_pass(s, y_dev, st);
+    s->loss_tmp = keep;
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
     s->t += 1;
     const float c1 = 1.0f - std::pow(s->beta1, (float)s->t), c2 = 1.0f - std::pow(s->beta2, (float)s->t);

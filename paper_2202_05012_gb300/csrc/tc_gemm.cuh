@@ -70,6 +70,27 @@ struct MlpInferArgs {
 cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const CUtensorMap &w3,
                            const CUtensorMap &w4, const MlpInferArgs &a, cudaStream_t st);
 
+// One training pass of a minibatch up to the weight gradients (train_mlp.cu):
+// per 128-row tile the forward, the loss gradient and the data-gradient chain
+// in one kernel.  Inputs through the x0 map ([B][64] bf16, 128-row boxes),
+// weights through w1 ([256][64]), w2, w3 ([256][256]), w4 ([128][256], 128-row
+// boxes), w4t ([256][128]), w3t, w2t ([256][256]) -- 256-row boxes otherwise.
+struct TrainPassArgs {
+    int B;                           // rows, a multiple of 128
+    const float *b1, *b2, *b3, *b4;  // biases [256] x 3, [128]
+    const float *y;                  // [B][60] targets
+    float *Z1, *Z2, *Z3;             // [256][B] pre-activations, transposed (written)
+    __nv_bfloat16 *H1T, *H2T, *H3T;  // [256][B] transposed activations (written)
+    __nv_bfloat16 *G4T;              // [128][B] transposed output gradient (rows 90.. left alone)
+    __nv_bfloat16 *G3T, *G2T, *G1T;  // [256][B] transposed hidden gradients (written)
+    float *gb1, *gb2, *gb3, *gb4;    // bias gradients (added to)
+    double *loss_sum;                // minibatch loss (added to)
+    int *error;                      // device error word (|= 8: a pipeline wait expired)
+};
+cudaError_t launch_train_pass(const CUtensorMap &x0, const CUtensorMap &w1, const CUtensorMap &w2,
+                              const CUtensorMap &w3, const CUtensorMap &w4, const CUtensorMap &w4t,
+                              const CUtensorMap &w3t, const CUtensorMap &w2t, const TrainPassArgs &a, cudaStream_t st);
+
 // Tensor map of a row-major bf16 matrix [rows][cols] (cols contiguous) read in
 // boxes of 64 columns x box_rows rows with the 128-byte swizzle.
 int make_bf16_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);

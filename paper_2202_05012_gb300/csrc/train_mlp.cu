@@ -1,0 +1,430 @@
+// train_mlp.cu -- the surrogate network's training pass up to the weight
+// gradients, one 128-row tile per CTA in one kernel: the forward through the
+// four layers, the loss gradient, and the data-gradient chain back through
+// layers 4, 3 and 2, with the tile's activations (and then its gradients)
+// kept in shared memory as the A operand of the next tcgen05 MMA.  Per layer
+// and tile the tensor core takes the operand from shared memory, the 16
+// epilogue warps turn its TMEM accumulator into the next operand.
+//
+// Writes what the weight-gradient GEMMs and the optimiser need: the
+// pre-activations Z1..Z3 (float32, transposed [256][B] so that a warp's 32
+// rows are one coalesced 128-byte access, read back by the GELU backward of
+// the same thread), the transposed activations H1^T..H3^T and gradients G4^T..G1^T
+// (bf16, [features][rows], K-major operands of dW = G^T H over the rows), the
+// bias gradients (column sums) and the minibatch loss.  The per-layer
+// launches it replaces each gave every CTA one 128-row tile and spent most
+// of their 15-20 us on the latency of one tile's loads, MMAs and stores.
+//
+// Loss (mean over rows and the 30 layers), network outputs o_j, s_j, rho_j:
+//   (y_j - mu_j)^2 / (2 v_j) + ln(v_j) / 2 + y_j (rho_j - R_j)^2 / 2,
+//   mu_j = exp(o_j - 4), v_j = exp(s_j) + 1e-8.
+//
+// Shared memory (213 KB): X 16 KB (the tile's inputs, bf16, K = 64 with 6
+// used), A 64 KB (activations or gradients, 4 K-blocks of 128 rows x 64
+// columns, 128-byte swizzle; during the loss it holds the float32 outputs),
+// G 32 KB (the output gradient, K = 128, columns 90.. zero), and a 3-stage
+// ring of 32 KB weight K-blocks in the order the MMAs use them: W1, W2 (4),
+// W3 (4), W4 (4, 128 rows), W4^T (2), W3^T (4), W2^T (4).
+// Warps: 0 TMA producer, 1 TMEM owner and MMA issuer, 4-19 epilogue (warp w
+// reads TMEM lanes 32 (w % 4).. and columns 16 ((w - 4) / 4).. of each
+// 64-column block).  Every wait is bounded; on expiry the CTA sets the error
+// word, stops, lets its loads and MMAs finish (bounded), frees TMEM, returns.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "supa_internal.cuh"
+#include "tc_gemm.cuh"
+#include "tc_prims.cuh"
+
+namespace supa {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kTThreads = 640;
+constexpr int kTRows = 128;
+constexpr int kLayersOut = 30;
+constexpr int kOutPitch = 97;                 // float32 row pitch of the staged outputs
+constexpr uint32_t kXBytes = kTRows * 128;    // input tile
+constexpr uint32_t kABlk = kTRows * 128;      // one K-block of a 128-row operand
+constexpr uint32_t kABytes = 4 * kABlk;
+constexpr uint32_t kGBytes = 2 * kABlk;
+constexpr uint32_t kStageBytes = 256 * 128;   // one weight K-block (256 rows x 64 columns)
+constexpr int kRing = 3;
+constexpr uint32_t oX = 0, oA = kXBytes, oG = oA + kABytes, oS = oG + kGBytes;
+constexpr uint32_t kTrainSmem = oS + kRing * kStageBytes + 1024;
+constexpr int kEpi = 16;
+
+struct TrainMaps {
+    CUtensorMap x0, w1, w2, w3, w4, w4t, w3t, w2t;
+};
+
+// The weight K-block loads of one tile, in MMA order.
+struct LoadPlan {
+    int map;     // 0 w1, 1 w2, 2 w3, 3 w4, 4 w4t, 5 w3t, 6 w2t
+    int kb;      // column block
+    uint32_t bytes;
+};
+__device__ __forceinline__ LoadPlan plan(int i) {
+    if (i == 0) return {0, 0, 256 * 128};
+    if (i < 5) return {1, i - 1, 256 * 128};
+    if (i < 9) return {2, i - 5, 256 * 128};
+    if (i < 13) return {3, i - 9, 128 * 128};
+    if (i < 15) return {4, i - 13, 256 * 128};
+    if (i < 19) return {5, i - 15, 256 * 128};
+    return {6, i - 19, 256 * 128};
+}
+constexpr int kLoads = 23;
+
+__global__ void __launch_bounds__(kTThreads, 1)
+    train_mlp_kernel(const __grid_constant__ TrainMaps mp, const TrainPassArgs g) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t w_full[kRing], w_empty[kRing];
+    __shared__ __align__(8) uint64_t x_full, x_empty;
+    __shared__ __align__(8) uint64_t acc_full;  // a layer's accumulator is final
+    __shared__ __align__(8) uint64_t a_ready;   // the next operand is written, the accumulator read
+    __shared__ __align__(8) uint64_t drain;
+    __shared__ __align__(8) uint64_t epi_bar;   // all epilogue warps reached the same point
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(16) float sbias[3 * 256 + 128];
+    __shared__ float colsum4[128];
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = g.B / kTRows;
+    if ((int)blockIdx.x >= tiles) return;
+    const int my_tiles = (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            mbar_init(&w_full[i], 1);
+            mbar_init(&w_empty[i], 1);
+        }
+        mbar_init(&x_full, 1);
+        mbar_init(&x_empty, 1);
+        mbar_init(&acc_full, 1);
+        mbar_init(&a_ready, kEpi);
+        mbar_init(&drain, 1);
+        mbar_init(&epi_bar, kEpi);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < 3 * 256 + 128; i += blockDim.x)
+        sbias[i] = i < 256 ? g.b1[i] : i < 512 ? g.b2[i - 256] : i < 768 ? g.b3[i - 512] : g.b4[i - 768];
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) colsum4[i] = 0.0f;
+    // the output-gradient operand: columns 90..127 stay zero
+    for (uint32_t i = threadIdx.x; i < kGBytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(base + oG)[i] = make_uint4(0u, 0u, 0u, 0u);
+    fence_smem_to_async();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    volatile int *abort_v = &abort_flag;
+    auto fail = [&]() {
+        if (!*abort_v) atomicOr(g.error, kErrTimeout);
+        *abort_v = 1;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer: each tile's input block, then its 23 weight K-blocks ----
+            int issued = 0, x_issued = 0;
+            bool ok = true;
+            for (int t = 0; t < my_tiles && ok && !*abort_v; ++t) {
+                const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
+                if (t > 0 && !mbar_wait(&x_empty, (t - 1) & 1)) {
+                    fail();
+                    break;
+                }
+                mbar_expect_tx(&x_full, kXBytes);
+                tma_load_2d(base + oX, &mp.x0, 0, m0, &x_full);
+                x_issued = t + 1;
+                for (int i = 0; i < kLoads && ok; ++i) {
+                    const int c = t * kLoads + i, s = c % kRing;
+                    if (c >= kRing && !mbar_wait(&w_empty[s], ((c / kRing) - 1) & 1)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    if (*abort_v) {
+                        ok = false;
+                        break;
+                    }
+                    const LoadPlan pl = plan(i);
+                    const CUtensorMap *m = pl.map == 0   ? &mp.w1
+                                           : pl.map == 1 ? &mp.w2
+                                           : pl.map == 2 ? &mp.w3
+                                           : pl.map == 3 ? &mp.w4
+                                           : pl.map == 4 ? &mp.w4t
+                                           : pl.map == 5 ? &mp.w3t
+                                                         : &mp.w2t;
+                    mbar_expect_tx(&w_full[s], pl.bytes);
+                    tma_load_2d(base + oS + s * kStageBytes, m, pl.kb * 64, 0, &w_full[s]);
+                    issued = c + 1;
+                }
+            }
+            if (*abort_v) {
+                // let the loads in flight land before the CTA exits
+                for (int i = max(0, issued - kRing); i < issued; ++i) mbar_wait(&w_full[i % kRing], (i / kRing) & 1);
+                if (x_issued > 0) mbar_wait(&x_full, (x_issued - 1) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            constexpr uint32_t id256 = idesc_bf16(kTRows, 256), id128 = idesc_bf16(kTRows, 128);
+            const uint32_t sX = smem_u32(base + oX), sA = smem_u32(base + oA), sG = smem_u32(base + oG),
+                           sS = smem_u32(base + oS);
+            bool ok = true;
+            uint32_t ar = 0;  // a_ready completions consumed
+            int c = 0;        // weight stages consumed
+            // one layer: `nkb` K-blocks of the operand at `a_base` against the next ring stages
+            auto layer = [&](uint32_t a_base, int nkb, uint32_t idesc, int k_steps_first) -> bool {
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int s = c % kRing;
+                    if (*abort_v || !mbar_wait(&w_full[s], (c / kRing) & 1)) return false;
+                    fence_after_sync();
+                    const int ks = kb == 0 ? k_steps_first : 4;
+                    for (int k = 0; k < ks; ++k)
+                        mma_bf16(tmem, sw128_desc(a_base + kb * kABlk + k * 32), sw128_desc(sS + s * kStageBytes + k * 32),
+                                 idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    mma_commit(&w_empty[s]);
+                    ++c;
+                }
+                mma_commit(&acc_full);
+                return true;
+            };
+            auto wait_operand = [&]() -> bool {
+                if (*abort_v || !mbar_wait(&a_ready, ar & 1)) return false;
+                ++ar;
+                fence_after_sync();
+                return true;
+            };
+            for (int t = 0; t < my_tiles && ok; ++t) {
+                // the accumulator is free once the previous tile's last epilogue read it
+                if (t > 0 && !wait_operand()) { ok = false; break; }
+                if (*abort_v || !mbar_wait(&x_full, t & 1)) { ok = false; break; }
+                fence_after_sync();
+                // layer 1: K = 16 (6 inputs, zero padded)
+                ok = layer(sX, 1, id256, 1);
+                if (!ok) break;
+                mma_commit(&x_empty);
+                ok = wait_operand() && layer(sA, 4, id256, 4)      // layer 2
+                     && wait_operand() && layer(sA, 4, id256, 4)   // layer 3
+                     && wait_operand() && layer(sA, 4, id128, 4)   // layer 4 (128 output columns)
+                     && wait_operand() && layer(sG, 2, id256, 4)   // d out W4: K = 128
+                     && wait_operand() && layer(sA, 4, id256, 4)   // d H3 W3
+                     && wait_operand() && layer(sA, 4, id256, 4);  // d H2 W2
+            }
+            if (!ok) fail();
+            // every MMA issued by this thread completes before tensor memory is freed
+            mma_commit(&drain);
+            mbar_wait(&drain, 0);
+        }
+    } else if (warp >= 4) {
+        // ---- epilogue: warp (q, h) owns rows 32q.. and columns 16h.. of each K-block ----
+        const int q = warp & 3, h = (warp - 4) >> 2;
+        const int r = q * 32 + lane;
+        const int e = (warp - 4) * 32 + lane;  // 0..511
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const float inv = 1.0f / (float)(g.B * kLayersOut);
+        uint8_t *A = base + oA;
+        uint8_t *G = base + oG;
+        int ph = 0;  // acc_full completions consumed
+        int eph = 0; // epi_bar completions consumed
+        bool ok = true;
+        // a bounded barrier among the 16 epilogue warps (a plain named barrier
+        // would wait forever for a warp that gave up)
+        auto epi_sync = [&]() -> bool {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&epi_bar);
+            const bool w = __all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&epi_bar, eph & 1));
+            ++eph;
+            return w;
+        };
+        auto wait_acc = [&]() -> bool {
+            // warp-uniform, so that the .sync.aligned TMEM loads see the whole warp
+            const bool w = __all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full, ph & 1));
+            ++ph;
+            fence_after_sync();
+            return w;
+        };
+        auto hand_off = [&]() {
+            fence_smem_to_async();
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_ready);
+        };
+        for (int t = 0; t < my_tiles && ok; ++t) {
+            const int row = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows + r;
+            // ---- forward: z = acc + b, Z stored, GELU(z) to the operand and transposed ----
+            for (int l = 0; l < 3 && ok; ++l) {
+                if (!wait_acc()) { ok = false; break; }
+                float *Z = l == 0 ? g.Z1 : l == 1 ? g.Z2 : g.Z3;
+                __nv_bfloat16 *HT = l == 0 ? g.H1T : l == 1 ? g.H2T : g.H3T;
+#pragma unroll 1
+                for (int kb = 0; kb < 4; ++kb) {
+                    const int c0 = kb * 64 + h * 16;
+                    float v[16];
+                    tmem_ld16(tmem + lane_off + c0, v);
+                    const float *bb = sbias + l * 256 + c0;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += bb[i];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) Z[(size_t)(c0 + i) * g.B + row] = v[i];
+                    uint32_t p[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) p[i] = gelu2_bf16(make_float2(v[2 * i], v[2 * i + 1]));
+                    uint8_t *blk = A + kb * kABlk;
+                    *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
+                    *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) = make_uint4(p[4], p[5], p[6], p[7]);
+                    const __nv_bfloat16 *hb = reinterpret_cast<const __nv_bfloat16 *>(p);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) HT[(size_t)(c0 + i) * g.B + row] = hb[i];
+                }
+                hand_off();
+            }
+            if (!ok) break;
+            // ---- output layer: stage out = acc + b4 (float32) in the A buffer ----
+            if (!wait_acc()) { ok = false; break; }
+            float *outs = reinterpret_cast<float *>(A);
+#pragma unroll 1
+            for (int kb = 0; kb < 2; ++kb) {
+                const int c0 = kb * 64 + h * 16;
+                float v[16];
+                tmem_ld16(tmem + lane_off + c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (c0 + i < 96) outs[r * kOutPitch + c0 + i] = v[i] + sbias[768 + c0 + i];
+            }
+            if (!epi_sync()) { ok = false; break; }
+            // ---- loss gradient: warp w takes rows 8 (w - 4) .. + 7, lane j layer j (< 30):
+            //      coalesced target reads, one shared atomic per element for the bias gradient ----
+            {
+                const int wr = warp - 4, j = lane;
+                double l = 0.0;
+                if (j < kLayersOut) {
+                    for (int it = 0; it < 8; ++it) {
+                        const int lr = wr * 8 + it;
+                        const int grow = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows + lr;
+                        const float *o = outs + lr * kOutPitch;
+                        const float *y = g.y + (size_t)grow * (2 * kLayersOut);
+                        const float mu = expf(o[j] - kMuShift), sv = o[kLayersOut + j], rho = o[2 * kLayersOut + j];
+                        const float yj = __ldg(y + j), dr = rho - __ldg(y + kLayersOut + j);
+                        const float res = yj - mu;
+                        const float es = expf(sv);
+                        const float vv = es + kVarFloor;
+                        const float iv = 1.0f / vv;
+                        l += 0.5 * (double)(res * res * iv) + 0.5 * (double)logf(vv) + 0.5 * (double)(yj * dr * dr);
+                        const float gv[3] = {-res * iv * mu * inv, 0.5f * es * iv * (1.0f - res * res * iv) * inv,
+                                             yj * dr * inv};
+#pragma unroll
+                        for (int w3 = 0; w3 < 3; ++w3) {
+                            const int col = w3 * kLayersOut + j;
+                            *reinterpret_cast<__nv_bfloat16 *>(G + (col >> 6) * kABlk +
+                                                               sw128_offset(lr, (col & 63) >> 3) + (col & 7) * 2) =
+                                __float2bfloat16_rn(gv[w3]);
+                            atomicAdd(&colsum4[col], gv[w3]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o2 = 16; o2 > 0; o2 >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o2);
+                if (lane == 0) atomicAdd(g.loss_sum, l / (double)(g.B * kLayersOut));
+            }
+            if (!epi_sync()) { ok = false; break; }
+            // G4^T from the operand buffer: lanes take consecutive rows of one column
+            {
+                const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
+                for (int idx = e; idx < 3 * kLayersOut * kTRows; idx += kEpi * 32) {
+                    const int col = idx >> 7, lr = idx & 127;
+                    g.G4T[(size_t)col * g.B + m0 + lr] = *reinterpret_cast<const __nv_bfloat16 *>(
+                        G + (col >> 6) * kABlk + sw128_offset(lr, (col & 63) >> 3) + (col & 7) * 2);
+                }
+            }
+            if (e < 3 * kLayersOut) {
+                atomicAdd(&g.gb4[e], colsum4[e]);
+                colsum4[e] = 0.0f;
+            }
+            hand_off();
+            // ---- backward: g = acc * GELU'(z), to the operand (layers 3, 2), transposed, column sums ----
+            for (int l = 2; l >= 0 && ok; --l) {
+                if (!wait_acc()) { ok = false; break; }
+                const float *Z = l == 0 ? g.Z1 : l == 1 ? g.Z2 : g.Z3;
+                __nv_bfloat16 *GT = l == 0 ? g.G1T : l == 1 ? g.G2T : g.G3T;
+                float *gb = l == 0 ? g.gb1 : l == 1 ? g.gb2 : g.gb3;
+#pragma unroll 1
+                for (int kb = 0; kb < 4; ++kb) {
+                    const int c0 = kb * 64 + h * 16;
+                    float d[16];
+                    tmem_ld16(tmem + lane_off + c0, d);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) d[i] *= gelu_grad(Z[(size_t)(c0 + i) * g.B + row]);
+                    uint32_t p[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) p[i] = pack_bf16(d[2 * i], d[2 * i + 1]);
+                    if (l > 0) {
+                        uint8_t *blk = A + kb * kABlk;
+                        *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
+                        *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) =
+                            make_uint4(p[4], p[5], p[6], p[7]);
+                    }
+                    const __nv_bfloat16 *hb = reinterpret_cast<const __nv_bfloat16 *>(p);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) GT[(size_t)(c0 + i) * g.B + row] = hb[i];
+                    // column sums over the warp's 32 rows: lane i < 16 ends with column c0 + i
+#pragma unroll
+                    for (int o2 = 8; o2 > 0; o2 >>= 1) {
+                        const bool upper = (lane & o2) != 0;
+#pragma unroll
+                        for (int i = 0; i < o2; ++i) {
+                            const float give = upper ? d[i] : d[i + o2];
+                            const float keep = upper ? d[i + o2] : d[i];
+                            d[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, give, o2);
+                        }
+                    }
+                    d[0] += __shfl_xor_sync(0xFFFFFFFFu, d[0], 16);
+                    if (lane < 16) atomicAdd(&gb[c0 + lane], d[0]);
+                }
+                hand_off();
+            }
+        }
+        if (!ok) fail();
+    }
+
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256) : "memory");
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_train_pass(const CUtensorMap &x0, const CUtensorMap &w1, const CUtensorMap &w2,
+                              const CUtensorMap &w3, const CUtensorMap &w4, const CUtensorMap &w4t,
+                              const CUtensorMap &w3t, const CUtensorMap &w2t, const TrainPassArgs &a, cudaStream_t st) {
+    if (a.B < kTRows || a.B % kTRows) return cudaErrorInvalidValue;
+    TrainMaps m{x0, w1, w2, w3, w4, w4t, w3t, w2t};
+    cudaError_t e = cudaFuncSetAttribute(train_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = a.B / kTRows;
+    train_mlp_kernel<<<std::min(tiles, sms), kTThreads, kTrainSmem, st>>>(m, a);
+    return cudaGetLastError();
+}
+
+}  // namespace supa
