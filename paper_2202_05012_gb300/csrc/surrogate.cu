@@ -9,17 +9,20 @@
 // (targets: fractions y_j, energy-weighted mean distances R_j), evaluated
 // in minibatches of `batch` rows.
 //
-// Layout.  Every GEMM is C = A * B^T with both operands K-major (tc_gemm.cuh),
-// so the engine keeps each activation in both orientations (the forward
-// epilogue writes h and h^T) and each weight as W and W^T in BF16, next to
-// FP32 master weights and Adam moments.  The 6 inputs are padded to 64
-// columns and the 90 outputs to 128 rows; the padding stays exactly zero
-// (zero inputs and zero output gradients give zero updates).
+// Layout.  The training pass (train_mlp.cu) keeps a 128-row tile's
+// activations in shared memory as the next layer's operand and writes them,
+// and the gradients of the backward, row-major in BF16; the weight gradients
+// dW = G^T H read those as MN-major operands (tc_gemm.cu).  Each weight is
+// kept as W and W^T in BF16 (the backward multiplies by W^T), next to FP32
+// master weights and Adam moments.  The 6 inputs are padded to 64 columns
+// and the 90 outputs to 128 rows; the padding stays exactly zero (zero inputs
+// and zero output gradients give zero updates).
 //
-// Training step: pack inputs -> 4 forward GEMMs (bias+GELU epilogues) ->
-// loss kernel (NLL, d loss / d out) -> per layer a data-gradient GEMM
-// (GELU-backward epilogue, bias gradient by column sums) and a split-K
-// weight-gradient GEMM (float atomics) -> Adam -> BF16 weight copies.
+// Training step: gather the minibatch -> pack inputs -> training pass
+// (forward, loss gradient, data-gradient chain, bias gradients) -> the four
+// weight gradients in one grouped launch -> Adam, which also refreshes the
+// BF16 weight copies.
+
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -38,7 +41,6 @@ namespace {
 constexpr int kIn = 6, kInPad = 64, kHid = 256, kOut = 90, kOutPad = 128, kLayersOut = 30;
 constexpr int kY = 2 * kLayersOut;  // target columns: fractions, mean distances
 constexpr int kInferLd = 96;        // outputs written by the fused inference kernel (>= kOut; 90..95 are zero)
-static_assert(kOutPad == kTileM, "d out^T is read as one full 128-row tile");
 // packed user parameter vector: W1, b1, W2, b2, W3, b3, W4, b4
 constexpr int kNParams = kHid * kIn + kHid + 2 * (kHid * kHid + kHid) + kOut * kHid + kOut;
 
@@ -54,14 +56,10 @@ cudaError_t dalloc(T **p, size_t n) {
     return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
 }
 
-// Inputs [n][6] float32 -> X0 [B][64] bf16 (and its transpose when X0T is
-// not null); rows past n are zero, rows past *n_dev are not written (the
-// GEMMs skip them).
-__global__ void pack_inputs(const float *x, int64_t n, const unsigned *n_dev, int B, __nv_bfloat16 *X0,
-                            __nv_bfloat16 *X0T) {
+// Inputs [n][6] float32 -> X0 [B][64] bf16; rows past n are zero.
+__global__ void pack_inputs(const float *x, int64_t n, int B, __nv_bfloat16 *X0) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= B) return;
-    if (n_dev && r >= (int64_t)*n_dev) return;
     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (r < n)
         for (int j = 0; j < kIn; ++j) v[j] = x[(size_t)r * kIn + j];
@@ -71,90 +69,6 @@ __global__ void pack_inputs(const float *x, int64_t n, const unsigned *n_dev, in
     for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
     row[0] = *reinterpret_cast<const uint4 *>(h);
     for (int j = 1; j < kInPad / 8; ++j) row[j] = make_uint4(0u, 0u, 0u, 0u);
-    if (X0T)
-        for (int j = 0; j < kInPad; ++j) X0T[(size_t)j * B + r] = __float2bfloat16_rn(j < kIn ? v[j] : 0.0f);
-}
-
-// The loss L over the 30 layers, mean over the batch: writes d L / d out
-// (bf16, both orientations; padding columns zero), adds the bias gradient of
-// the last layer and the loss sum.  A block takes 32 rows: their outputs
-// and targets are staged in shared memory with coalesced loads, thread
-// (x, y) handles row x for layers y, y + 8, ... (a warp covers 32
-// consecutive rows of one layer, so the transposed gradient is written
-// coalesced and the bias gradient is a warp sum), and the gradient rows
-// leave through shared memory as whole rows.
-constexpr int kLossRows = 32, kLossLanesY = 8;
-
-__global__ void __launch_bounds__(kLossRows * kLossLanesY)
-    nll_loss(const float *out, const float *y, int B, __nv_bfloat16 *G4, __nv_bfloat16 *G4T, float *gb4,
-             double *loss_sum) {
-    constexpr int kThreads = kLossRows * kLossLanesY;
-    __shared__ float colsum[kOutPad];
-    __shared__ double red[kLossLanesY];
-    __shared__ float so[kLossRows][kOut + 1];
-    __shared__ float sy[kLossRows][kY + 1];
-    __shared__ __align__(16) __nv_bfloat16 sg[kLossRows][kOutPad + 8];
-    const int tid = threadIdx.y * kLossRows + threadIdx.x;
-    const int r0 = blockIdx.x * kLossRows;
-    const int rows = min(kLossRows, B - r0);
-    for (int j = tid; j < kOutPad; j += kThreads) colsum[j] = 0.0f;
-    for (int i = tid; i < rows * kOut; i += kThreads) so[i / kOut][i % kOut] = out[(size_t)(r0 + i / kOut) * kOutPad + i % kOut];
-    for (int i = tid; i < rows * kY; i += kThreads) sy[i / kY][i % kY] = y[(size_t)r0 * kY + i];
-    for (int i = tid; i < kLossRows * (kOutPad - kOut); i += kThreads)
-        sg[i / (kOutPad - kOut)][kOut + i % (kOutPad - kOut)] = __float2bfloat16_rn(0.0f);
-    __syncthreads();
-    const int rl = threadIdx.x, r = r0 + rl;
-    const bool live = rl < rows;
-    double l = 0.0;
-    const float inv = 1.0f / (float)(B * kLayersOut);
-    for (int j = threadIdx.y; j < kLayersOut; j += kLossLanesY) {
-        float gmu = 0.0f, gs = 0.0f, gr = 0.0f;
-        if (live) {
-            const float mu = expf(so[rl][j] - kMuShift), s = so[rl][kLayersOut + j],
-                        rho = so[rl][2 * kLayersOut + j];
-            const float yj = sy[rl][j], dr = rho - sy[rl][kLayersOut + j];
-            const float res = yj - mu;
-            const float es = expf(s);
-            const float v = es + kVarFloor;  // floored variance
-            const float iv = 1.0f / v;
-            l += 0.5 * (double)(res * res * iv) + 0.5 * (double)logf(v) + 0.5 * (double)(yj * dr * dr);
-            gmu = -res * iv * mu * inv;  // through the log link: d mu / d o = mu
-            gs = 0.5f * es * iv * (1.0f - res * res * iv) * inv;
-            gr = yj * dr * inv;
-            sg[rl][j] = __float2bfloat16_rn(gmu);
-            sg[rl][kLayersOut + j] = __float2bfloat16_rn(gs);
-            sg[rl][2 * kLayersOut + j] = __float2bfloat16_rn(gr);
-            G4T[(size_t)j * B + r] = __float2bfloat16_rn(gmu);
-            G4T[(size_t)(kLayersOut + j) * B + r] = __float2bfloat16_rn(gs);
-            G4T[(size_t)(2 * kLayersOut + j) * B + r] = __float2bfloat16_rn(gr);
-        }
-        // bias gradient: column sums over the warp's 32 rows
-        for (int o = 16; o > 0; o >>= 1) {
-            gmu += __shfl_xor_sync(0xFFFFFFFFu, gmu, o);
-            gs += __shfl_xor_sync(0xFFFFFFFFu, gs, o);
-            gr += __shfl_xor_sync(0xFFFFFFFFu, gr, o);
-        }
-        if (threadIdx.x == 0) {
-            atomicAdd(&colsum[j], gmu);
-            atomicAdd(&colsum[kLayersOut + j], gs);
-            atomicAdd(&colsum[2 * kLayersOut + j], gr);
-        }
-    }
-    // (rows kOut.. of G4T are zero from creation and never written)
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
-    if (threadIdx.x == 0) red[threadIdx.y] = l;
-    __syncthreads();
-    // gradient rows, 16 bytes at a time
-    for (int i = tid; i < rows * (kOutPad / 8); i += kThreads) {
-        const int rr = i / (kOutPad / 8), c = (i % (kOutPad / 8)) * 8;
-        *reinterpret_cast<uint4 *>(G4 + (size_t)(r0 + rr) * kOutPad + c) = *reinterpret_cast<const uint4 *>(&sg[rr][c]);
-    }
-    if (tid == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kLossLanesY; ++i) t += red[i];
-        atomicAdd(loss_sum, t / (double)(B * kLayersOut));
-    }
-    for (int j = tid; j < kOut; j += kThreads) atomicAdd(&gb4[j], colsum[j]);
 }
 
 // Adam with bias correction (c1 = 1 - beta1^t, c2 = 1 - beta2^t).
@@ -222,13 +136,13 @@ struct supa_surrogate {
     float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
     float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     __nv_bfloat16 *W1b, *W2b, *W3b, *W4b, *W2Tb, *W3Tb, *W4Tb;
-    __nv_bfloat16 *X0, *X0T, *H1, *H2, *H3, *H1T, *H2T, *H3T, *G4, *G4T, *G3, *G2, *G1, *G3T, *G2T, *G1T;
-    float *Z1, *Z2, *Z3, *OUT;
+    __nv_bfloat16 *X0, *H1, *H2, *H3, *G4, *G3, *G2, *G1;  // row-major operands of the weight gradients
+    __nv_bfloat16 *GP1, *GP2, *GP3;                           // GELU'(z) of the hidden layers
     float *Xs = nullptr, *Ys = nullptr;  // gathered minibatch (epoch training)
     double *loss_tmp = nullptr;
     int *error = nullptr;
-    CUtensorMap mX0, mH1, mH2, mH3, mG4, mG3, mG2, mG4T, mG3T, mG2T, mG1T;  // A operands (box 128 rows)
-    CUtensorMap mW1, mW2, mW3, mW4, mW4T, mW3T, mW2T, mH3Tb, mH2Tb, mH1Tb, mX0Tb;  // B operands
+    TrainMapSet tm;                                  // the training pass's loads and stores
+    CUtensorMap dG[kWgradMax], dH[kWgradMax];        // weight-gradient operands (64-row boxes)
     CUtensorMap mW4i;  // W4 rows 0..95 for the fused inference kernel
     std::vector<void *> allocs;
 };
@@ -258,89 +172,11 @@ int weight_copies(supa_surrogate *s, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : SUPA_ERR_CUDA;
 }
 
-GemmArgs gargs(int M, int N, int K, int epi, int *err) {
-    GemmArgs a{};
-    a.M = M;
-    a.N = N;
-    a.K = K;
-    a.k_blocks_per_split = K / kTileK;
-    a.epi = epi;
-    a.error = err;
-    return a;
-}
-
-cudaError_t gemm(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs a, cudaStream_t st, int m_tiles_target = 0) {
-    int splits = 1;
-    if (a.epi == EPI_ATOMIC_F32) {
-        const int kb = a.K / kTileK;
-        const int m_tiles = (a.M + kTileM - 1) / kTileM;
-        const int want = std::max(1, std::min(kb, 152 / m_tiles));
-        a.k_blocks_per_split = (kb + want - 1) / want;
-        splits = (kb + a.k_blocks_per_split - 1) / a.k_blocks_per_split;
-    }
-    (void)m_tiles_target;
-    return launch_gemm(ta, tb, a, splits, st);
-}
-
-// Forward pass of one training minibatch whose packed inputs are in X0/X0T,
-// keeping pre-activations and transposed activations for the backward.
-cudaError_t forward(supa_surrogate *s, cudaStream_t st) {
-    const int B = s->B;
-    const int ep = EPI_BIAS_GELU;
-    GemmArgs a = gargs(B, kHid, kInPad, ep, s->error);
-    a.bias = s->master + Off::b1; a.out_f32 = s->Z1; a.out_bf16 = s->H1; a.outT_bf16 = s->H1T; a.ld = kHid; a.ldT = B;
-    cudaError_t e = gemm(s->mX0, s->mW1, a, st);
-    if (e != cudaSuccess) return e;
-    a = gargs(B, kHid, kHid, ep, s->error);
-    a.bias = s->master + Off::b2; a.out_f32 = s->Z2; a.out_bf16 = s->H2; a.outT_bf16 = s->H2T; a.ld = kHid; a.ldT = B;
-    if ((e = gemm(s->mH1, s->mW2, a, st)) != cudaSuccess) return e;
-    a = gargs(B, kHid, kHid, ep, s->error);
-    a.bias = s->master + Off::b3; a.out_f32 = s->Z3; a.out_bf16 = s->H3; a.outT_bf16 = s->H3T; a.ld = kHid; a.ldT = B;
-    if ((e = gemm(s->mH2, s->mW3, a, st)) != cudaSuccess) return e;
-    a = gargs(B, kOutPad, kHid, EPI_BIAS_F32, s->error);
-    a.bias = s->master + Off::b4; a.out_f32 = s->OUT; a.ld = kOutPad;
-    return gemm(s->mH3, s->mW4, a, st);
-}
-
-// Loss and gradients of the minibatch in X0 with targets y (grad zeroed first).
-cudaError_t backward(supa_surrogate *s, const float *y, cudaStream_t st) {
-    const int B = s->B;
-    cudaError_t e = cudaMemsetAsync(s->grad, 0, Off::total * sizeof(float), st);
-    if (e != cudaSuccess) return e;
-    nll_loss<<<(B + kLossRows - 1) / kLossRows, dim3(kLossRows, kLossLanesY), 0, st>>>(s->OUT, y, B, s->G4, s->G4T,
-                                                                                s->grad + Off::b4, s->loss_tmp);
-    // layer 4
-    GemmArgs a = gargs(kOutPad, kHid, B, EPI_ATOMIC_F32, s->error);
-    a.out_f32 = s->grad + Off::W4; a.ld = kHid;
-    if ((e = gemm(s->mG4T, s->mH3Tb, a, st)) != cudaSuccess) return e;
-    a = gargs(B, kHid, kOutPad, EPI_GELU_BWD, s->error);
-    a.z_in = s->Z3; a.out_bf16 = s->G3; a.outT_bf16 = s->G3T; a.colsum = s->grad + Off::b3; a.ld = kHid; a.ldT = B;
-    if ((e = gemm(s->mG4, s->mW4T, a, st)) != cudaSuccess) return e;
-    // layer 3
-    a = gargs(kHid, kHid, B, EPI_ATOMIC_F32, s->error);
-    a.out_f32 = s->grad + Off::W3; a.ld = kHid;
-    if ((e = gemm(s->mG3T, s->mH2Tb, a, st)) != cudaSuccess) return e;
-    a = gargs(B, kHid, kHid, EPI_GELU_BWD, s->error);
-    a.z_in = s->Z2; a.out_bf16 = s->G2; a.outT_bf16 = s->G2T; a.colsum = s->grad + Off::b2; a.ld = kHid; a.ldT = B;
-    if ((e = gemm(s->mG3, s->mW3T, a, st)) != cudaSuccess) return e;
-    // layer 2
-    a = gargs(kHid, kHid, B, EPI_ATOMIC_F32, s->error);
-    a.out_f32 = s->grad + Off::W2; a.ld = kHid;
-    if ((e = gemm(s->mG2T, s->mH1Tb, a, st)) != cudaSuccess) return e;
-    a = gargs(B, kHid, kHid, EPI_GELU_BWD, s->error);
-    a.z_in = s->Z1; a.out_bf16 = s->G1; a.outT_bf16 = s->G1T; a.colsum = s->grad + Off::b1; a.ld = kHid; a.ldT = B;
-    if ((e = gemm(s->mG2, s->mW2T, a, st)) != cudaSuccess) return e;
-    // layer 1
-    a = gargs(kHid, kInPad, B, EPI_ATOMIC_F32, s->error);
-    a.out_f32 = s->grad + Off::W1; a.ld = kInPad;
-    return gemm(s->mG1T, s->mX0Tb, a, st);
-}
-
-// One minibatch (packed inputs in X0/X0T, targets y) up to the gradients in
-// s->grad (zeroed first) and the loss added to *s->loss_tmp: the fused pass
-// per 128-row tile (forward, loss gradient, data-gradient chain; bias
-// gradients), then the four weight gradients dW = G^T H as split-K GEMMs
-// over the rows.
+// One minibatch (packed inputs in X0, targets y) up to the gradients in
+// s->grad (zeroed first) and the loss added to *s->loss_tmp: the training
+// pass per 128-row tile (forward, loss gradient, data-gradient chain; bias
+// gradients), then dW4 = G4^T H3, dW3 = G3^T H2, dW2 = G2^T H1, dW1 = G1^T X0
+// over the rows in one grouped launch.
 cudaError_t train_pass(supa_surrogate *s, const float *y, cudaStream_t st) {
     const int B = s->B;
     cudaError_t e = cudaMemsetAsync(s->grad, 0, Off::total * sizeof(float), st);
@@ -352,27 +188,20 @@ cudaError_t train_pass(supa_surrogate *s, const float *y, cudaStream_t st) {
     t.b3 = s->master + Off::b3;
     t.b4 = s->master + Off::b4;
     t.y = y;
-    t.Z1 = s->Z1; t.Z2 = s->Z2; t.Z3 = s->Z3;
-    t.H1T = s->H1T; t.H2T = s->H2T; t.H3T = s->H3T;
-    t.G4T = s->G4T; t.G3T = s->G3T; t.G2T = s->G2T; t.G1T = s->G1T;
+    t.GP1 = s->GP1; t.GP2 = s->GP2; t.GP3 = s->GP3;
     t.gb1 = s->grad + Off::b1; t.gb2 = s->grad + Off::b2; t.gb3 = s->grad + Off::b3; t.gb4 = s->grad + Off::b4;
     t.loss_sum = s->loss_tmp;
     t.error = s->error;
-    if ((e = launch_train_pass(s->mX0, s->mW1, s->mW2, s->mW3, s->mW4, s->mW4T, s->mW3T, s->mW2T, t, st)) !=
-        cudaSuccess)
-        return e;
-    GemmArgs a = gargs(kOutPad, kHid, B, EPI_ATOMIC_F32, s->error);
-    a.out_f32 = s->grad + Off::W4; a.ld = kHid;
-    if ((e = gemm(s->mG4T, s->mH3Tb, a, st)) != cudaSuccess) return e;
-    a = gargs(kHid, kHid, B, EPI_ATOMIC_F32, s->error);
-    a.out_f32 = s->grad + Off::W3; a.ld = kHid;
-    if ((e = gemm(s->mG3T, s->mH2Tb, a, st)) != cudaSuccess) return e;
-    a = gargs(kHid, kHid, B, EPI_ATOMIC_F32, s->error);
-    a.out_f32 = s->grad + Off::W2; a.ld = kHid;
-    if ((e = gemm(s->mG2T, s->mH1Tb, a, st)) != cudaSuccess) return e;
-    a = gargs(kHid, kInPad, B, EPI_ATOMIC_F32, s->error);
-    a.out_f32 = s->grad + Off::W1; a.ld = kInPad;
-    return gemm(s->mG1T, s->mX0Tb, a, st);
+    if ((e = launch_train_pass(s->tm, t, st)) != cudaSuccess) return e;
+    WgradArgs w{};
+    w.B = B;
+    w.nprob = 4;
+    w.p[0] = {kOutPad, kHid, s->grad + Off::W4, kHid};
+    w.p[1] = {kHid, kHid, s->grad + Off::W3, kHid};
+    w.p[2] = {kHid, kHid, s->grad + Off::W2, kHid};
+    w.p[3] = {kHid, kInPad, s->grad + Off::W1, kInPad};
+    w.error = s->error;
+    return launch_weight_grads(s->dG, s->dH, w, st);
 }
 
 int check_error_word(supa_surrogate *s) {
@@ -450,7 +279,7 @@ cudaError_t surrogate_infer_run(supa_surrogate *s, SurInfer *inf, const float *f
     a.ld = kInferLd;
     a.ncols = kInferLd;  // all 96 columns: whole-vector stores (W4, b4 rows 90..95 are zero)
     a.error = s->error;
-    return launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4i, a, st);
+    return launch_sur_mlp(s->tm.w1, s->tm.w2, s->tm.w3, s->mW4i, a, st);
 }
 
 }  // namespace supa
@@ -479,45 +308,43 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
               grab(s, &s->W2b, (size_t)kHid * kHid) && grab(s, &s->W3b, (size_t)kHid * kHid) &&
               grab(s, &s->W4b, (size_t)kOutPad * kHid) && grab(s, &s->W2Tb, (size_t)kHid * kHid) &&
               grab(s, &s->W3Tb, (size_t)kHid * kHid) && grab(s, &s->W4Tb, (size_t)kHid * kOutPad) &&
-              grab(s, &s->X0, B * kInPad) && grab(s, &s->X0T, B * kInPad) && grab(s, &s->H1, B * kHid) &&
-              grab(s, &s->H2, B * kHid) && grab(s, &s->H3, B * kHid) && grab(s, &s->H1T, B * kHid) &&
-              grab(s, &s->H2T, B * kHid) && grab(s, &s->H3T, B * kHid) && grab(s, &s->G4, B * kOutPad) &&
-              grab(s, &s->G4T, B * kOutPad) && grab(s, &s->G3, B * kHid) && grab(s, &s->G2, B * kHid) &&
-              grab(s, &s->G1, B * kHid) && grab(s, &s->G3T, B * kHid) && grab(s, &s->G2T, B * kHid) &&
-              grab(s, &s->G1T, B * kHid) && grab(s, &s->Z1, B * kHid) && grab(s, &s->Z2, B * kHid) &&
-              grab(s, &s->Z3, B * kHid) && grab(s, &s->OUT, B * kOutPad) && grab(s, &s->loss_tmp, 1) &&
+              grab(s, &s->X0, B * kInPad) && grab(s, &s->H1, B * kHid) && grab(s, &s->H2, B * kHid) &&
+              grab(s, &s->H3, B * kHid) && grab(s, &s->G4, B * kOutPad) && grab(s, &s->G3, B * kHid) &&
+              grab(s, &s->G2, B * kHid) && grab(s, &s->G1, B * kHid) && grab(s, &s->GP1, B * kHid) &&
+              grab(s, &s->GP2, B * kHid) && grab(s, &s->GP3, B * kHid) && grab(s, &s->loss_tmp, 1) &&
               grab(s, &s->error, 1) && grab(s, &s->Xs, B * kIn) && grab(s, &s->Ys, B * kY);
     if (!ok) {
         supa_surrogate_destroy(s);
         return sfail(SUPA_ERR_OOM, "supa_surrogate_create: out of device memory");
     }
-    // tensor maps: A operands read 128-row boxes, B operands N-row boxes
+    // tensor maps of the training pass: the input tile and its stores in
+    // 128-row boxes, the weights (W and W^T) in boxes of all their rows
     int rc = 0;
-    rc |= make_bf16_map(&s->mX0, s->X0, B, kInPad, 128);
-    rc |= make_bf16_map(&s->mH1, s->H1, B, kHid, 128);
-    rc |= make_bf16_map(&s->mH2, s->H2, B, kHid, 128);
-    rc |= make_bf16_map(&s->mH3, s->H3, B, kHid, 128);
-    rc |= make_bf16_map(&s->mG4, s->G4, B, kOutPad, 128);
-    rc |= make_bf16_map(&s->mG3, s->G3, B, kHid, 128);
-    rc |= make_bf16_map(&s->mG2, s->G2, B, kHid, 128);
-    // d out^T is read as the A operand of the 128-row weight gradient (rows
-    // 90..127 stay zero)
-    rc |= make_bf16_map(&s->mG4T, s->G4T, kOutPad, B, 128);
-    rc |= make_bf16_map(&s->mG3T, s->G3T, kHid, B, 128);
-    rc |= make_bf16_map(&s->mG2T, s->G2T, kHid, B, 128);
-    rc |= make_bf16_map(&s->mG1T, s->G1T, kHid, B, 128);
-    rc |= make_bf16_map(&s->mW1, s->W1b, kHid, kInPad, kHid);
-    rc |= make_bf16_map(&s->mW2, s->W2b, kHid, kHid, kHid);
-    rc |= make_bf16_map(&s->mW3, s->W3b, kHid, kHid, kHid);
-    rc |= make_bf16_map(&s->mW4, s->W4b, kOutPad, kHid, kOutPad);
+    TrainMapSet &tm = s->tm;
+    rc |= make_bf16_map(&tm.x0, s->X0, B, kInPad, 128);
+    rc |= make_bf16_map(&tm.w1, s->W1b, kHid, kInPad, kHid);
+    rc |= make_bf16_map(&tm.w2, s->W2b, kHid, kHid, kHid);
+    rc |= make_bf16_map(&tm.w3, s->W3b, kHid, kHid, kHid);
+    rc |= make_bf16_map(&tm.w4, s->W4b, kOutPad, kHid, kOutPad);
+    rc |= make_bf16_map(&tm.w4t, s->W4Tb, kHid, kOutPad, kHid);
+    rc |= make_bf16_map(&tm.w3t, s->W3Tb, kHid, kHid, kHid);
+    rc |= make_bf16_map(&tm.w2t, s->W2Tb, kHid, kHid, kHid);
+    rc |= make_bf16_map(&tm.h1, s->H1, B, kHid, 128);
+    rc |= make_bf16_map(&tm.h2, s->H2, B, kHid, 128);
+    rc |= make_bf16_map(&tm.h3, s->H3, B, kHid, 128);
+    rc |= make_bf16_map(&tm.g4, s->G4, B, kOutPad, 128);
+    rc |= make_bf16_map(&tm.g3, s->G3, B, kHid, 128);
+    rc |= make_bf16_map(&tm.g2, s->G2, B, kHid, 128);
+    rc |= make_bf16_map(&tm.g1, s->G1, B, kHid, 128);
     rc |= make_bf16_map(&s->mW4i, s->W4b, kOutPad, kHid, kInferLd);
-    rc |= make_bf16_map(&s->mW4T, s->W4Tb, kHid, kOutPad, kHid);
-    rc |= make_bf16_map(&s->mW3T, s->W3Tb, kHid, kHid, kHid);
-    rc |= make_bf16_map(&s->mW2T, s->W2Tb, kHid, kHid, kHid);
-    rc |= make_bf16_map(&s->mH3Tb, s->H3T, kHid, B, kHid);
-    rc |= make_bf16_map(&s->mH2Tb, s->H2T, kHid, B, kHid);
-    rc |= make_bf16_map(&s->mH1Tb, s->H1T, kHid, B, kHid);
-    rc |= make_bf16_map(&s->mX0Tb, s->X0T, kInPad, B, kInPad);
+    // the weight gradients read the same matrices in 64-row boxes
+    const __nv_bfloat16 *gsrc[kWgradMax] = {s->G4, s->G3, s->G2, s->G1};
+    const __nv_bfloat16 *hsrc[kWgradMax] = {s->H3, s->H2, s->H1, s->X0};
+    const int gcols[kWgradMax] = {kOutPad, kHid, kHid, kHid}, hcols[kWgradMax] = {kHid, kHid, kHid, kInPad};
+    for (int i = 0; i < kWgradMax; ++i) {
+        rc |= make_bf16_map(&s->dG[i], gsrc[i], B, gcols[i], 64);
+        rc |= make_bf16_map(&s->dH[i], hsrc[i], B, hcols[i], 64);
+    }
     if (rc != 0) {
         supa_surrogate_destroy(s);
         return sfail(SUPA_ERR_CUDA, "supa_surrogate_create: cuTensorMapEncodeTiled failed");
@@ -528,7 +355,6 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
     if (e == cudaSuccess) e = cudaMemset(s->m, 0, Off::total * 4);
     if (e == cudaSuccess) e = cudaMemset(s->v, 0, Off::total * 4);
     if (e == cudaSuccess) e = cudaMemset(s->error, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(s->G4T, 0, B * kOutPad * sizeof(__nv_bfloat16));
     if (e != cudaSuccess || weight_copies(s, 0) != SUPA_OK || cudaDeviceSynchronize() != cudaSuccess) {
         supa_surrogate_destroy(s);
         return sfail(SUPA_ERR_CUDA, "supa_surrogate_create: upload failed");
@@ -552,7 +378,7 @@ int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float 
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(s->loss_tmp, 0, sizeof(double), st) != cudaSuccess)
         return sfail(SUPA_ERR_CUDA, "memset failed");
-    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, nullptr, s->B, s->X0, s->X0T);
+    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0);
     cudaError_t e = train_pass(s, y_dev, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("gradients: ") + cudaGetErrorString(e));
@@ -572,7 +398,7 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
     if (!s || !x_dev || !y_dev) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_step: null argument");
     cudaStream_t st = (cudaStream_t)stream;
     double *loss = loss_acc_dev ? loss_acc_dev : s->loss_tmp;
-    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, nullptr, s->B, s->X0, s->X0T);
+    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0);
     // train_pass() adds the minibatch loss to s->loss_tmp; point it at the accumulator
     double *keep = s->loss_tmp;
     s->loss_tmp = loss;
@@ -640,7 +466,7 @@ int supa_surrogate_forward(supa_surrogate *s, const float *x_dev, int64_t n, flo
     // groups: then the padding outputs 90.. (zero) are written too, up to 96
     a.ncols = ld_out % 4 == 0 ? (int)std::min<int64_t>(ld_out, kInferLd) : kOut;
     a.error = s->error;
-    const cudaError_t e = launch_sur_mlp(s->mW1, s->mW2, s->mW3, s->mW4i, a, (cudaStream_t)stream);
+    const cudaError_t e = launch_sur_mlp(s->tm.w1, s->tm.w2, s->tm.w3, s->mW4i, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));
     return SUPA_OK;
 }

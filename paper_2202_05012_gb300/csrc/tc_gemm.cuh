@@ -1,17 +1,7 @@
-// tc_gemm.cuh -- BF16 tensor-core GEMM for the surrogate network on sm_103a:
+// tc_gemm.cuh -- tensor-core kernels of the surrogate network on sm_103a:
 // tcgen05.mma with FP32 accumulation in tensor memory (TMEM), operands staged
 // in shared memory by TMA (cp.async.bulk.tensor, 128-byte swizzle), stages
-// released through mbarriers, fused epilogues.
-//
-//   C[M x N] = A[M x K] * B[N x K]^T      (A, B bf16, K contiguous)
-//
-// A persistent CTA walks 128-row tiles of C (all N <= 256 columns each)
-// with two TMEM accumulators, so the epilogue of one tile overlaps the MMAs
-// of the next; blockIdx.y splits K (split-K partial products are added with
-// float atomics).  Warp 0 lane 0 issues TMA loads, warp 1 owns the TMEM
-// allocation and its lane 0 issues the MMAs, warps 4..11 run the epilogue
-// (warps 4+q and 8+q read TMEM lanes 32q..32q+31 = rows of the tile, one
-// half of the columns each).
+// released through mbarriers.
 //
 // Every mbarrier wait is bounded: on expiry the CTA records an error code,
 // stops issuing work, drains what it issued (again bounded), frees its TMEM
@@ -23,34 +13,29 @@
 
 namespace supa {
 
-enum GemmEpilogue : int {
-    EPI_BIAS_GELU = 0,  // z = acc + bias; store z (f32), gelu(z) (bf16) and its transpose (bf16)
-    EPI_BIAS_F32 = 1,   // acc + bias -> f32
-    EPI_GELU_BWD = 2,   // g = acc * gelu'(z); store g (bf16), its transpose, column sums (bias gradient)
-    EPI_ATOMIC_F32 = 3, // out += acc (split-K partial products)
+// Weight gradients of a training minibatch, up to four problems in one launch
+// (tc_gemm.cu): dW_p[M_p][N_p] += sum over the B rows r of G_p[r][m] H_p[r][n],
+// G_p [B][>= M_p] and H_p [B][N_p] row-major bf16 (the layout the training
+// pass writes), read through tensor maps with boxes of 64 columns x 64 rows
+// (make_bf16_map(..., 64)).  Each CTA takes one (problem, 128-row block of
+// dW_p, run of 64-row K-blocks) and adds its partial product to out_p with
+// float vector reductions; the runs are sized so that there is about one CTA
+// per SM.
+constexpr int kWgradMax = 4;
+struct WgradProblem {
+    int M;       // dW rows, a multiple of 128
+    int N;       // dW columns: 64, 128 or 256
+    float *out;  // [M][ld] (16-byte aligned, ld a multiple of 4), added to
+    int ld;
 };
-
-struct GemmArgs {
-    int M, N, K;        // N in {64, 128, 256}; K multiple of 64
-    int k_blocks_per_split;
-    int epi;
-    const float *bias;  // [N]
-    float *out_f32;     // [M][ld] (BIAS_F32, ATOMIC_F32) or z (BIAS_GELU)
-    __nv_bfloat16 *out_bf16;   // [M][ld]
-    __nv_bfloat16 *outT_bf16;  // [N][ldT]
-    const float *z_in;  // [M][ld] (GELU_BWD)
-    float *colsum;      // [N] (GELU_BWD)
-    int ld, ldT;
-    int *error;         // device error word
-    const unsigned *m_dev;  // optional device row count: rows >= min(M, *m_dev) are skipped
+struct WgradArgs {
+    int B;       // rows contracted over, a multiple of 64
+    int nprob;   // 1..kWgradMax
+    WgradProblem p[kWgradMax];
+    int *error;  // device error word (|= 8: a pipeline wait expired)
 };
-
-constexpr int kGemmStages = 4;
-constexpr int kTileM = 128;
-constexpr int kTileK = 64;
-
-size_t gemm_smem_bytes(int N);
-cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &a, int splits, cudaStream_t st);
+cudaError_t launch_weight_grads(const CUtensorMap *g_maps, const CUtensorMap *h_maps, const WgradArgs &a,
+                                cudaStream_t st);
 // One bounded mbarrier wait on a barrier nothing completes; *status (device)
 // receives 1 when the wait gave up after limit_cycles, else 0.
 cudaError_t launch_wait_expiry_probe(long long limit_cycles, int *status, cudaStream_t st);
@@ -75,21 +60,23 @@ cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const C
 // in one kernel.  Inputs through the x0 map ([B][64] bf16, 128-row boxes),
 // weights through w1 ([256][64]), w2, w3 ([256][256]), w4 ([128][256], 128-row
 // boxes), w4t ([256][128]), w3t, w2t ([256][256]) -- 256-row boxes otherwise.
+// The activations H1..H3 ([B][256]) and the gradients d out (G4, [B][128],
+// columns 90.. zero) and G3..G1 ([B][256]), all row-major bf16, leave through
+// the store maps h1..h3, g4, g3..g1 (boxes of 64 columns x 128 rows).
 struct TrainPassArgs {
-    int B;                           // rows, a multiple of 128
-    const float *b1, *b2, *b3, *b4;  // biases [256] x 3, [128]
-    const float *y;                  // [B][60] targets
-    float *Z1, *Z2, *Z3;             // [256][B] pre-activations, transposed (written)
-    __nv_bfloat16 *H1T, *H2T, *H3T;  // [256][B] transposed activations (written)
-    __nv_bfloat16 *G4T;              // [128][B] transposed output gradient (rows 90.. left alone)
-    __nv_bfloat16 *G3T, *G2T, *G1T;  // [256][B] transposed hidden gradients (written)
-    float *gb1, *gb2, *gb3, *gb4;    // bias gradients (added to)
-    double *loss_sum;                // minibatch loss (added to)
-    int *error;                      // device error word (|= 8: a pipeline wait expired)
+    int B;                              // rows, a multiple of 128
+    const float *b1, *b2, *b3, *b4;     // biases [256] x 3, [128]
+    const float *y;                     // [B][60] targets
+    __nv_bfloat16 *GP1, *GP2, *GP3;     // [B][256] GELU'(z) of the hidden layers (written, read back)
+    float *gb1, *gb2, *gb3, *gb4;       // bias gradients (added to)
+    double *loss_sum;                   // minibatch loss (added to)
+    int *error;                         // device error word (|= 8: a pipeline wait expired)
 };
-cudaError_t launch_train_pass(const CUtensorMap &x0, const CUtensorMap &w1, const CUtensorMap &w2,
-                              const CUtensorMap &w3, const CUtensorMap &w4, const CUtensorMap &w4t,
-                              const CUtensorMap &w3t, const CUtensorMap &w2t, const TrainPassArgs &a, cudaStream_t st);
+struct TrainMapSet {
+    CUtensorMap x0, w1, w2, w3, w4, w4t, w3t, w2t;  // loads
+    CUtensorMap h1, h2, h3, g4, g3, g2, g1;         // stores
+};
+cudaError_t launch_train_pass(const TrainMapSet &maps, const TrainPassArgs &a, cudaStream_t st);
 
 // Tensor map of a row-major bf16 matrix [rows][cols] (cols contiguous) read in
 // boxes of 64 columns x box_rows rows with the 128-byte swizzle.

@@ -85,7 +85,23 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Byte offset of the 16-byte unit `u` (0..7) of row `r` inside such a tile.
+// Shared-memory matrix descriptor of an MN-major operand: TMA boxes of 64 K
+// rows x 64 MN elements (128-byte rows, 128-byte swizzle), the box of the
+// next 64 MN elements `lbo` bytes further (leading byte offset), 8-row K
+// groups 1024 bytes apart (stride byte offset).  An operand whose rows are
+// its K index -- a row-major activation [rows][features] contracted over the
+// rows -- is read this way without a transpose.
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr, uint32_t lbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Byte offset of the 16-byte unit `u` (0..7) of row `r` inside a tile of
+// 128-byte rows with the 128-byte swizzle (either operand layout above).
 __device__ __forceinline__ uint32_t sw128_offset(int r, int u) {
     return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((u ^ (r & 7)) << 4));
 }
@@ -94,6 +110,11 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int u) {
 // operands K-major, M x N tile.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with both operands MN-major (the transpose bits of A and B).
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
+    return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -206,6 +227,24 @@ __device__ __forceinline__ uint32_t gelu2_bf16(float2 z) {
     const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
     const float2 h = __ffma2_rn(hz, t, hz);
     return pack_bf16(h.x, h.y);
+}
+
+// GELU and its derivative for two values at once, both as BF16 pairs, from
+// one tanh each: h = z (1 + t) / 2 and
+// h' = (1 + t) / 2 + (z / 2) (1 - t^2) (c + 3 c a z^2).
+__device__ __forceinline__ void gelu2_grad2_bf16(float2 z, uint32_t &h, uint32_t &hp) {
+    constexpr float kC3 = kGeluC * kGeluA;
+    const float2 u = __fmul2_rn(z, z);
+    const float2 w = __fmul2_rn(z, __ffma2_rn(u, make_float2(kC3, kC3), make_float2(kGeluC, kGeluC)));
+    const float2 t = make_float2(tanh_sfu(w.x), tanh_sfu(w.y));
+    const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
+    const float2 g = __ffma2_rn(hz, t, hz);
+    const float2 dw = __ffma2_rn(u, make_float2(3.0f * kC3, 3.0f * kC3), make_float2(kGeluC, kGeluC));
+    const float2 sech2 = __ffma2_rn(make_float2(-t.x, -t.y), t, make_float2(1.0f, 1.0f));
+    const float2 half1t = __ffma2_rn(t, make_float2(0.5f, 0.5f), make_float2(0.5f, 0.5f));
+    const float2 gp = __ffma2_rn(__fmul2_rn(hz, sech2), dw, half1t);
+    h = pack_bf16(g.x, g.y);
+    hp = pack_bf16(gp.x, gp.y);
 }
 
 }  // namespace tc

@@ -1,34 +1,41 @@
 // train_mlp.cu -- the surrogate network's training pass up to the weight
-// gradients, one 128-row tile per CTA in one kernel: the forward through the
-// four layers, the loss gradient, and the data-gradient chain back through
-// layers 4, 3 and 2, with the tile's activations (and then its gradients)
-// kept in shared memory as the A operand of the next tcgen05 MMA.  Per layer
-// and tile the tensor core takes the operand from shared memory, the 16
-// epilogue warps turn its TMEM accumulator into the next operand.
+// gradients, one 128-row tile at a time per CTA in one kernel: the forward
+// through the four layers, the loss gradient, and the data-gradient chain
+// back through layers 4, 3 and 2, with the tile's activations (and then its
+// gradients) kept in shared memory as the A operand of the next tcgen05 MMA.
+// Per layer and tile the tensor core takes the operand from shared memory,
+// the 16 epilogue warps turn its TMEM accumulator into the next operand.
 //
-// Writes what the weight-gradient GEMMs and the optimiser need: the
-// pre-activations Z1..Z3 (float32, transposed [256][B] so that a warp's 32
-// rows are one coalesced 128-byte access, read back by the GELU backward of
-// the same thread), the transposed activations H1^T..H3^T and gradients G4^T..G1^T
-// (bf16, [features][rows], K-major operands of dW = G^T H over the rows), the
-// bias gradients (column sums) and the minibatch loss.  The per-layer
-// launches it replaces each gave every CTA one 128-row tile and spent most
-// of their 15-20 us on the latency of one tile's loads, MMAs and stores.
+// Writes what the weight-gradient GEMM and the optimiser need: every operand
+// tile it builds -- the activations H1..H3, the output gradient d out and the
+// hidden gradients G3..G1 -- leaves shared memory row-major through TMA
+// stores issued by one thread (the weight-gradient GEMM reads them as
+// MN-major operands, so no transposed copy is written); GELU'(z) of the
+// hidden layers (bf16 [B][256], two 16-byte stores per thread and K-block,
+// read back by the same thread in the backward); the bias gradients (column
+// sums) and the minibatch loss.  The per-layer launches it replaces each gave
+// every CTA one 128-row tile and spent most of their 15-20 us on the latency
+// of one tile's loads, MMAs and stores.
 //
 // Loss (mean over rows and the 30 layers), network outputs o_j, s_j, rho_j:
 //   (y_j - mu_j)^2 / (2 v_j) + ln(v_j) / 2 + y_j (rho_j - R_j)^2 / 2,
 //   mu_j = exp(o_j - 4), v_j = exp(s_j) + 1e-8.
 //
-// Shared memory (213 KB): X 16 KB (the tile's inputs, bf16, K = 64 with 6
+// Shared memory (209 KB): X 16 KB (the tile's inputs, bf16, K = 64 with 6
 // used), A 64 KB (activations or gradients, 4 K-blocks of 128 rows x 64
 // columns, 128-byte swizzle; during the loss it holds the float32 outputs),
 // G 32 KB (the output gradient, K = 128, columns 90.. zero), and a 3-stage
 // ring of 32 KB weight K-blocks in the order the MMAs use them: W1, W2 (4),
 // W3 (4), W4 (4, 128 rows), W4^T (2), W3^T (4), W2^T (4).
-// Warps: 0 TMA producer, 1 TMEM owner and MMA issuer, 4-19 epilogue (warp w
-// reads TMEM lanes 32 (w % 4).. and columns 16 ((w - 4) / 4).. of each
-// 64-column block).  Every wait is bounded; on expiry the CTA sets the error
-// word, stops, lets its loads and MMAs finish (bounded), frees TMEM, returns.
+// Warps: 0 TMA producer, 1 TMEM owner and MMA issuer, 2 TMA stores of the
+// operand tiles, 4-19 epilogue (warp w reads TMEM lanes 32 (w % 4).. and
+// columns 16 ((w - 4) / 4).. of each 64-column block).
+// Barriers per tile: acc_full completes once per MMA layer (7); a_ready once
+// per epilogue phase (7: the operand is written and the accumulator read);
+// a_free once per phase after the stores of its operand have read shared
+// memory, before the next phase overwrites it.
+// Every wait is bounded; on expiry the CTA sets the error word, stops, lets
+// its loads, MMAs and stores finish (bounded), frees TMEM, returns.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -56,10 +63,7 @@ constexpr int kRing = 3;
 constexpr uint32_t oX = 0, oA = kXBytes, oG = oA + kABytes, oS = oG + kGBytes;
 constexpr uint32_t kTrainSmem = oS + kRing * kStageBytes + 1024;
 constexpr int kEpi = 16;
-
-struct TrainMaps {
-    CUtensorMap x0, w1, w2, w3, w4, w4t, w3t, w2t;
-};
+constexpr int kPhases = 7;  // epilogue phases per tile: H1, H2, H3, d out, G3, G2, G1
 
 // The weight K-block loads of one tile, in MMA order.
 struct LoadPlan {
@@ -79,12 +83,13 @@ __device__ __forceinline__ LoadPlan plan(int i) {
 constexpr int kLoads = 23;
 
 __global__ void __launch_bounds__(kTThreads, 1)
-    train_mlp_kernel(const __grid_constant__ TrainMaps mp, const TrainPassArgs g) {
+    train_mlp_kernel(const __grid_constant__ TrainMapSet mp, const TrainPassArgs g) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t w_full[kRing], w_empty[kRing];
     __shared__ __align__(8) uint64_t x_full, x_empty;
     __shared__ __align__(8) uint64_t acc_full;  // a layer's accumulator is final
     __shared__ __align__(8) uint64_t a_ready;   // the next operand is written, the accumulator read
+    __shared__ __align__(8) uint64_t a_free;    // the stores of that operand have read it
     __shared__ __align__(8) uint64_t drain;
     __shared__ __align__(8) uint64_t epi_bar;   // all epilogue warps reached the same point
     __shared__ uint32_t tmem_slot;
@@ -107,6 +112,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
         mbar_init(&x_empty, 1);
         mbar_init(&acc_full, 1);
         mbar_init(&a_ready, kEpi);
+        mbar_init(&a_free, 1);
         mbar_init(&drain, 1);
         mbar_init(&epi_bar, kEpi);
         abort_flag = 0;
@@ -231,6 +237,36 @@ __global__ void __launch_bounds__(kTThreads, 1)
             mma_commit(&drain);
             mbar_wait(&drain, 0);
         }
+    } else if (warp == 2) {
+        if (lane == 0) {
+            // ---- stores: each phase's operand tile to its row-major matrix ----
+            uint32_t n = 0;  // a_ready completions seen
+            bool ok = true;
+            for (int t = 0; t < my_tiles && ok; ++t) {
+                const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
+                for (int ph = 0; ph < kPhases; ++ph, ++n) {
+                    if (*abort_v || !mbar_wait(&a_ready, n & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    if (ph == 3) {
+                        tma_store_2d(&mp.g4, base + oG, 0, m0);
+                        tma_store_2d(&mp.g4, base + oG + kABlk, 64, m0);
+                    } else {
+                        const CUtensorMap *m = ph == 0 ? &mp.h1 : ph == 1 ? &mp.h2 : ph == 2 ? &mp.h3
+                                             : ph == 4 ? &mp.g3 : ph == 5 ? &mp.g2 : &mp.g1;
+#pragma unroll 1
+                        for (int kb = 0; kb < 4; ++kb) tma_store_2d(m, base + oA + kb * kABlk, kb * 64, m0);
+                    }
+                    bulk_commit();
+                    bulk_wait_read_all();
+                    mbar_arrive(&a_free);
+                }
+            }
+            if (!ok) fail();
+            // the stores complete before the CTA (and its shared memory) goes away
+            bulk_wait_all();
+        }
     } else if (warp >= 4) {
         // ---- epilogue: warp (q, h) owns rows 32q.. and columns 16h.. of each K-block ----
         const int q = warp & 3, h = (warp - 4) >> 2;
@@ -240,8 +276,9 @@ __global__ void __launch_bounds__(kTThreads, 1)
         const float inv = 1.0f / (float)(g.B * kLayersOut);
         uint8_t *A = base + oA;
         uint8_t *G = base + oG;
-        int ph = 0;  // acc_full completions consumed
-        int eph = 0; // epi_bar completions consumed
+        int ph = 0;   // acc_full completions consumed
+        int eph = 0;  // epi_bar completions consumed
+        int np = 0;   // phases handed off (a_free completions to come)
         bool ok = true;
         // a bounded barrier among the 16 epilogue warps (a plain named barrier
         // would wait forever for a warp that gave up)
@@ -252,9 +289,12 @@ __global__ void __launch_bounds__(kTThreads, 1)
             ++eph;
             return w;
         };
+        // the accumulator of the next layer is final, and the previous phase's
+        // operand has been read by its stores (warp-uniform, so that the
+        // .sync.aligned TMEM loads see the whole warp)
         auto wait_acc = [&]() -> bool {
-            // warp-uniform, so that the .sync.aligned TMEM loads see the whole warp
-            const bool w = __all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full, ph & 1));
+            const bool w = __all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&acc_full, ph & 1) &&
+                                                       (np == 0 || mbar_wait(&a_free, (np - 1) & 1)));
             ++ph;
             fence_after_sync();
             return w;
@@ -264,14 +304,14 @@ __global__ void __launch_bounds__(kTThreads, 1)
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&a_ready);
+            ++np;
         };
         for (int t = 0; t < my_tiles && ok; ++t) {
             const int row = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows + r;
-            // ---- forward: z = acc + b, Z stored, GELU(z) to the operand and transposed ----
+            // ---- forward: z = acc + b; GELU(z) to the operand, GELU'(z) kept for the backward ----
             for (int l = 0; l < 3 && ok; ++l) {
                 if (!wait_acc()) { ok = false; break; }
-                float *Z = l == 0 ? g.Z1 : l == 1 ? g.Z2 : g.Z3;
-                __nv_bfloat16 *HT = l == 0 ? g.H1T : l == 1 ? g.H2T : g.H3T;
+                __nv_bfloat16 *GP = (l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + (size_t)row * 256;
 #pragma unroll 1
                 for (int kb = 0; kb < 4; ++kb) {
                     const int c0 = kb * 64 + h * 16;
@@ -280,17 +320,15 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     const float *bb = sbias + l * 256 + c0;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] += bb[i];
+                    uint32_t p[8], d[8];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) Z[(size_t)(c0 + i) * g.B + row] = v[i];
-                    uint32_t p[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) p[i] = gelu2_bf16(make_float2(v[2 * i], v[2 * i + 1]));
+                    for (int i = 0; i < 8; ++i) gelu2_grad2_bf16(make_float2(v[2 * i], v[2 * i + 1]), p[i], d[i]);
                     uint8_t *blk = A + kb * kABlk;
                     *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
                     *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) = make_uint4(p[4], p[5], p[6], p[7]);
-                    const __nv_bfloat16 *hb = reinterpret_cast<const __nv_bfloat16 *>(p);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) HT[(size_t)(c0 + i) * g.B + row] = hb[i];
+                    uint4 *gp = reinterpret_cast<uint4 *>(GP + c0);
+                    gp[0] = make_uint4(d[0], d[1], d[2], d[3]);
+                    gp[1] = make_uint4(d[4], d[5], d[6], d[7]);
                 }
                 hand_off();
             }
@@ -343,45 +381,35 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 if (lane == 0) atomicAdd(g.loss_sum, l / (double)(g.B * kLayersOut));
             }
             if (!epi_sync()) { ok = false; break; }
-            // G4^T from the operand buffer: lanes take consecutive rows of one column
-            {
-                const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
-                for (int idx = e; idx < 3 * kLayersOut * kTRows; idx += kEpi * 32) {
-                    const int col = idx >> 7, lr = idx & 127;
-                    g.G4T[(size_t)col * g.B + m0 + lr] = *reinterpret_cast<const __nv_bfloat16 *>(
-                        G + (col >> 6) * kABlk + sw128_offset(lr, (col & 63) >> 3) + (col & 7) * 2);
-                }
-            }
             if (e < 3 * kLayersOut) {
                 atomicAdd(&g.gb4[e], colsum4[e]);
                 colsum4[e] = 0.0f;
             }
             hand_off();
-            // ---- backward: g = acc * GELU'(z), to the operand (layers 3, 2), transposed, column sums ----
+            // ---- backward: g = acc * GELU'(z), to the operand, column sums ----
             for (int l = 2; l >= 0 && ok; --l) {
-                if (!wait_acc()) { ok = false; break; }
-                const float *Z = l == 0 ? g.Z1 : l == 1 ? g.Z2 : g.Z3;
-                __nv_bfloat16 *GT = l == 0 ? g.G1T : l == 1 ? g.G2T : g.G3T;
+                const __nv_bfloat16 *GP = (l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + (size_t)row * 256;
                 float *gb = l == 0 ? g.gb1 : l == 1 ? g.gb2 : g.gb3;
+                if (!wait_acc()) { ok = false; break; }
 #pragma unroll 1
                 for (int kb = 0; kb < 4; ++kb) {
                     const int c0 = kb * 64 + h * 16;
+                    const uint4 *gpv = reinterpret_cast<const uint4 *>(GP + c0);
+                    const uint4 gp0 = gpv[0], gp1 = gpv[1];
                     float d[16];
                     tmem_ld16(tmem + lane_off + c0, d);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) d[i] *= gelu_grad(Z[(size_t)(c0 + i) * g.B + row]);
+                    const uint32_t gw[8] = {gp0.x, gp0.y, gp0.z, gp0.w, gp1.x, gp1.y, gp1.z, gp1.w};
                     uint32_t p[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) p[i] = pack_bf16(d[2 * i], d[2 * i + 1]);
-                    if (l > 0) {
-                        uint8_t *blk = A + kb * kABlk;
-                        *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
-                        *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) =
-                            make_uint4(p[4], p[5], p[6], p[7]);
+                    for (int i = 0; i < 8; ++i) {
+                        const float2 s = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&gw[i]));
+                        d[2 * i] *= s.x;
+                        d[2 * i + 1] *= s.y;
+                        p[i] = pack_bf16(d[2 * i], d[2 * i + 1]);
                     }
-                    const __nv_bfloat16 *hb = reinterpret_cast<const __nv_bfloat16 *>(p);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) GT[(size_t)(c0 + i) * g.B + row] = hb[i];
+                    uint8_t *blk = A + kb * kABlk;
+                    *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
+                    *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) = make_uint4(p[4], p[5], p[6], p[7]);
                     // column sums over the warp's 32 rows: lane i < 16 ends with column c0 + i
 #pragma unroll
                     for (int o2 = 8; o2 > 0; o2 >>= 1) {
@@ -412,18 +440,15 @@ __global__ void __launch_bounds__(kTThreads, 1)
 
 }  // namespace
 
-cudaError_t launch_train_pass(const CUtensorMap &x0, const CUtensorMap &w1, const CUtensorMap &w2,
-                              const CUtensorMap &w3, const CUtensorMap &w4, const CUtensorMap &w4t,
-                              const CUtensorMap &w3t, const CUtensorMap &w2t, const TrainPassArgs &a, cudaStream_t st) {
+cudaError_t launch_train_pass(const TrainMapSet &maps, const TrainPassArgs &a, cudaStream_t st) {
     if (a.B < kTRows || a.B % kTRows) return cudaErrorInvalidValue;
-    TrainMaps m{x0, w1, w2, w3, w4, w4t, w3t, w2t};
     cudaError_t e = cudaFuncSetAttribute(train_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int tiles = a.B / kTRows;
-    train_mlp_kernel<<<std::min(tiles, sms), kTThreads, kTrainSmem, st>>>(m, a);
+    train_mlp_kernel<<<std::min(tiles, sms), kTThreads, kTrainSmem, st>>>(maps, a);
     return cudaGetLastError();
 }
 
