@@ -80,42 +80,45 @@ struct WeightCopies {
     __nv_bfloat16 *Wb[4], *WTb[4];
 };
 
-__global__ void adam_update(float *p, float *m, float *v, const float *g, size_t n, float lr, float b1, float b2,
+__global__ void adam_update(float *p, float *m, float *v, const float *g, int n, float lr, float b1, float b2,
                             float eps, float c1, float c2, const WeightCopies wc) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.0f - b1) * gi;
-        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        p[i] = pi;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const size_t j = i - wc.off[w];
-            if (i >= wc.off[w] && j < (size_t)wc.rows[w] * wc.cols[w]) {
-                const __nv_bfloat16 h = __float2bfloat16_rn(pi);
-                wc.Wb[w][j] = h;
-                if (wc.WTb[w]) wc.WTb[w][(j % wc.cols[w]) * wc.rows[w] + j / wc.cols[w]] = h;
-            }
+    for (int w = 0; w < 4; ++w) {
+        const int j = i - (int)wc.off[w];
+        if (j >= 0 && j < wc.rows[w] * wc.cols[w]) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(pi);
+            wc.Wb[w][j] = h;
+            if (wc.WTb[w]) wc.WTb[w][(j % wc.cols[w]) * wc.rows[w] + j / wc.cols[w]] = h;
         }
     }
 }
 
 // Rows (a i + c) mod n, i = i0 .. i0 + B - 1, of x [n][6] and y [n][60]:
-// one thread per value (a row's values are consecutive threads, so a row is
-// read and written coalesced).
-__global__ void gather_rows(const float *x, const float *y, int64_t n, uint64_t a, uint64_t c, int64_t i0, int B,
-                            float *xs, float *ys) {
-    constexpr int kRow = kIn + kY;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)B * kRow) return;
-    const int r = (int)(t / kRow), j = (int)(t % kRow);
+// the targets to ys [B][60], the inputs packed as X0 [B][64] bf16 (the 6
+// features, then zeros).  One warp per row: the row's 66 floats are read and
+// its 240 + 128 bytes written by consecutive lanes.
+__global__ void gather_pack(const float *x, const float *y, int64_t n, uint64_t a, uint64_t c, int64_t i0, int B,
+                            float *ys, __nv_bfloat16 *X0) {
+    const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (r >= B) return;
     const uint64_t src = (a * (uint64_t)(i0 + r) + c) % (uint64_t)n;
-    if (j < kIn)
-        xs[(size_t)r * kIn + j] = x[src * kIn + j];
-    else
-        ys[(size_t)r * kY + (j - kIn)] = y[src * kY + (j - kIn)];
+    const float *yr = y + src * kY;
+    const float y0 = yr[lane], y1 = lane + 32 < kY ? yr[lane + 32] : 0.0f;
+    const float xv = lane < kIn ? x[src * kIn + lane] : 0.0f;
+    ys[(size_t)r * kY + lane] = y0;
+    if (lane + 32 < kY) ys[(size_t)r * kY + lane + 32] = y1;
+    const float lo = __shfl_sync(0xFFFFFFFFu, xv, (2 * lane) & 31), hi = __shfl_sync(0xFFFFFFFFu, xv, (2 * lane + 1) & 31);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(2 * lane < kIn ? lo : 0.0f, 2 * lane + 1 < kIn ? hi : 0.0f);
+    reinterpret_cast<__nv_bfloat162 *>(X0 + (size_t)r * kInPad)[lane] = h;
 }
 
 // BF16 copies of a master weight [rows][cols]: W and (optionally) W^T.
@@ -138,7 +141,7 @@ struct supa_surrogate {
     __nv_bfloat16 *W1b, *W2b, *W3b, *W4b, *W2Tb, *W3Tb, *W4Tb;
     __nv_bfloat16 *X0, *H1, *H2, *H3, *G4, *G3, *G2, *G1;  // row-major operands of the weight gradients
     __nv_bfloat16 *GP1, *GP2, *GP3;                           // GELU'(z) of the hidden layers
-    float *Xs = nullptr, *Ys = nullptr;  // gathered minibatch (epoch training)
+    float *Ys = nullptr;  // gathered minibatch targets (epoch training)
     double *loss_tmp = nullptr;
     int *error = nullptr;
     TrainMapSet tm;                                  // the training pass's loads and stores
@@ -312,7 +315,7 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
               grab(s, &s->H3, B * kHid) && grab(s, &s->G4, B * kOutPad) && grab(s, &s->G3, B * kHid) &&
               grab(s, &s->G2, B * kHid) && grab(s, &s->G1, B * kHid) && grab(s, &s->GP1, B * kHid) &&
               grab(s, &s->GP2, B * kHid) && grab(s, &s->GP3, B * kHid) && grab(s, &s->loss_tmp, 1) &&
-              grab(s, &s->error, 1) && grab(s, &s->Xs, B * kIn) && grab(s, &s->Ys, B * kY);
+              grab(s, &s->error, 1) && grab(s, &s->Ys, B * kY);
     if (!ok) {
         supa_surrogate_destroy(s);
         return sfail(SUPA_ERR_OOM, "supa_surrogate_create: out of device memory");
@@ -393,12 +396,12 @@ int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float 
     return SUPA_OK;
 }
 
-int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float *y_dev, float lr,
-                              double *loss_acc_dev, void *stream) {
-    if (!s || !x_dev || !y_dev) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_step: null argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    double *loss = loss_acc_dev ? loss_acc_dev : s->loss_tmp;
-    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0);
+}  // extern "C"
+
+namespace {
+// The training pass of the packed minibatch in X0 with targets y (loss added
+// to *loss), then the Adam update.
+int train_on_packed(supa_surrogate *s, const float *y_dev, float lr, double *loss, cudaStream_t st) {
     // train_pass() adds the minibatch loss to s->loss_tmp; point it at the accumulator
     double *keep = s->loss_tmp;
     s->loss_tmp = loss;
@@ -412,9 +415,20 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
                           {kInPad, kHid, kHid, kHid},
                           {s->W1b, s->W2b, s->W3b, s->W4b},
                           {nullptr, s->W2Tb, s->W3Tb, s->W4Tb}};
-    adam_update<<<296, 256, 0, st>>>(s->master, s->m, s->v, s->grad, Off::total, lr, s->beta1, s->beta2, s->eps, c1,
-                                     c2, wc);
+    adam_update<<<(unsigned)((Off::total + 255) / 256), 256, 0, st>>>(s->master, s->m, s->v, s->grad, (int)Off::total,
+                                                                      lr, s->beta1, s->beta2, s->eps, c1, c2, wc);
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_step launch failed");
+}
+}  // namespace
+
+extern "C" {
+
+int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float *y_dev, float lr,
+                              double *loss_acc_dev, void *stream) {
+    if (!s || !x_dev || !y_dev) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_step: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0);
+    return train_on_packed(s, y_dev, lr, loss_acc_dev ? loss_acc_dev : s->loss_tmp, st);
 }
 
 int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,
@@ -436,10 +450,10 @@ int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const floa
     while (gcd(a, (uint64_t)n) != 1) a = (a + 1) % (uint64_t)n == 0 ? 1 : a + 1;
     const uint64_t c = (seed ^ 0xD1B54A32D192ED03ull) % (uint64_t)n;
     const int64_t steps = n / s->B;
+    double *loss = loss_acc_dev ? loss_acc_dev : s->loss_tmp;
     for (int64_t k = 0; k < steps; ++k) {
-        gather_rows<<<(unsigned)(((int64_t)s->B * (kIn + kY) + 255) / 256), 256, 0, st>>>(x_dev, y_dev, n, a, c, k * s->B,
-                                                                                          s->B, s->Xs, s->Ys);
-        const int rc = supa_surrogate_train_step(s, s->Xs, s->Ys, lr, loss_acc_dev, stream);
+        gather_pack<<<(unsigned)((s->B + 7) / 8), 256, 0, st>>>(x_dev, y_dev, n, a, c, k * s->B, s->B, s->Ys, s->X0);
+        const int rc = train_on_packed(s, s->Ys, lr, loss, st);
         if (rc != SUPA_OK) return rc;
     }
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_epoch launch failed");

@@ -312,14 +312,18 @@ __global__ void __launch_bounds__(kTThreads, 1)
             for (int l = 0; l < 3 && ok; ++l) {
                 if (!wait_acc()) { ok = false; break; }
                 __nv_bfloat16 *GP = (l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + (size_t)row * 256;
-#pragma unroll 1
+                // the next K-block's accumulator columns load while this one is processed
+                uint32_t raw[16], nxt[16];
+                tmem_ld16_issue(tmem + lane_off + h * 16, raw);
+                tmem_ld_wait(raw);
+#pragma unroll
                 for (int kb = 0; kb < 4; ++kb) {
                     const int c0 = kb * 64 + h * 16;
+                    if (kb < 3) tmem_ld16_issue(tmem + lane_off + c0 + 64, nxt);
                     float v[16];
-                    tmem_ld16(tmem + lane_off + c0, v);
                     const float *bb = sbias + l * 256 + c0;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += bb[i];
+                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(raw[i]) + bb[i];
                     uint32_t p[8], d[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) gelu2_grad2_bf16(make_float2(v[2 * i], v[2 * i + 1]), p[i], d[i]);
@@ -329,6 +333,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     uint4 *gp = reinterpret_cast<uint4 *>(GP + c0);
                     gp[0] = make_uint4(d[0], d[1], d[2], d[3]);
                     gp[1] = make_uint4(d[4], d[5], d[6], d[7]);
+                    if (kb < 3) {
+                        tmem_ld_wait(nxt);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) raw[i] = nxt[i];
+                    }
                 }
                 hand_off();
             }
@@ -347,23 +356,31 @@ __global__ void __launch_bounds__(kTThreads, 1)
             }
             if (!epi_sync()) { ok = false; break; }
             // ---- loss gradient: warp w takes rows 8 (w - 4) .. + 7, lane j layer j (< 30):
-            //      coalesced target reads, one shared atomic per element for the bias gradient ----
+            //      the 16 target loads issued together (coalesced), one shared atomic per
+            //      element for the bias gradient, the loss summed in float per warp ----
             {
                 const int wr = warp - 4, j = lane;
-                double l = 0.0;
+                float l = 0.0f;
                 if (j < kLayersOut) {
+                    const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
+                    float yv[8], yr[8];
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const float *y = g.y + (size_t)(m0 + wr * 8 + it) * (2 * kLayersOut);
+                        yv[it] = __ldg(y + j);
+                        yr[it] = __ldg(y + kLayersOut + j);
+                    }
+#pragma unroll
                     for (int it = 0; it < 8; ++it) {
                         const int lr = wr * 8 + it;
-                        const int grow = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows + lr;
                         const float *o = outs + lr * kOutPitch;
-                        const float *y = g.y + (size_t)grow * (2 * kLayersOut);
                         const float mu = expf(o[j] - kMuShift), sv = o[kLayersOut + j], rho = o[2 * kLayersOut + j];
-                        const float yj = __ldg(y + j), dr = rho - __ldg(y + kLayersOut + j);
+                        const float yj = yv[it], dr = rho - yr[it];
                         const float res = yj - mu;
                         const float es = expf(sv);
                         const float vv = es + kVarFloor;
                         const float iv = 1.0f / vv;
-                        l += 0.5 * (double)(res * res * iv) + 0.5 * (double)logf(vv) + 0.5 * (double)(yj * dr * dr);
+                        l += 0.5f * (res * res * iv + logf(vv) + yj * dr * dr);
                         const float gv[3] = {-res * iv * mu * inv, 0.5f * es * iv * (1.0f - res * res * iv) * inv,
                                              yj * dr * inv};
 #pragma unroll
@@ -378,7 +395,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 }
 #pragma unroll
                 for (int o2 = 16; o2 > 0; o2 >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o2);
-                if (lane == 0) atomicAdd(g.loss_sum, l / (double)(g.B * kLayersOut));
+                if (lane == 0) atomicAdd(g.loss_sum, (double)l / (double)(g.B * kLayersOut));
             }
             if (!epi_sync()) { ok = false; break; }
             if (e < 3 * kLayersOut) {
@@ -391,20 +408,30 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 const __nv_bfloat16 *GP = (l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + (size_t)row * 256;
                 float *gb = l == 0 ? g.gb1 : l == 1 ? g.gb2 : g.gb3;
                 if (!wait_acc()) { ok = false; break; }
-#pragma unroll 1
+                // GELU'(z) and the accumulator columns of the next K-block load
+                // while this one is processed
+                const uint4 *gpv = reinterpret_cast<const uint4 *>(GP + h * 16);
+                uint4 gp0 = gpv[0], gp1 = gpv[1];
+                uint32_t raw[16], nxt[16];
+                tmem_ld16_issue(tmem + lane_off + h * 16, raw);
+                tmem_ld_wait(raw);
+#pragma unroll
                 for (int kb = 0; kb < 4; ++kb) {
                     const int c0 = kb * 64 + h * 16;
-                    const uint4 *gpv = reinterpret_cast<const uint4 *>(GP + c0);
-                    const uint4 gp0 = gpv[0], gp1 = gpv[1];
+                    uint4 np0 = gp0, np1 = gp1;
+                    if (kb < 3) {
+                        tmem_ld16_issue(tmem + lane_off + c0 + 64, nxt);
+                        np0 = gpv[8 * (kb + 1)];  // 64 bf16 columns = 8 x 16 bytes
+                        np1 = gpv[8 * (kb + 1) + 1];
+                    }
                     float d[16];
-                    tmem_ld16(tmem + lane_off + c0, d);
                     const uint32_t gw[8] = {gp0.x, gp0.y, gp0.z, gp0.w, gp1.x, gp1.y, gp1.z, gp1.w};
                     uint32_t p[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const float2 s = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&gw[i]));
-                        d[2 * i] *= s.x;
-                        d[2 * i + 1] *= s.y;
+                        d[2 * i] = __uint_as_float(raw[2 * i]) * s.x;
+                        d[2 * i + 1] = __uint_as_float(raw[2 * i + 1]) * s.y;
                         p[i] = pack_bf16(d[2 * i], d[2 * i + 1]);
                     }
                     uint8_t *blk = A + kb * kABlk;
@@ -423,6 +450,13 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     }
                     d[0] += __shfl_xor_sync(0xFFFFFFFFu, d[0], 16);
                     if (lane < 16) atomicAdd(&gb[c0 + lane], d[0]);
+                    if (kb < 3) {
+                        tmem_ld_wait(nxt);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) raw[i] = nxt[i];
+                        gp0 = np0;
+                        gp1 = np1;
+                    }
                 }
                 hand_off();
             }
