@@ -388,11 +388,13 @@ int supa_surrogate_destroy(supa_surrogate *s);
 /* Current FP32 master parameters (synchronous). */
 int supa_surrogate_get_params(supa_surrogate *s, float *params_host);
 /* Loss and gradients of one minibatch without an update (synchronous):
- * x_dev float32 [batch][6], y_dev float32 [batch][60]. */
+ * x_dev float32 [batch][6] (4-byte aligned), y_dev float32 [batch][60]
+ * (8-byte aligned); a misaligned pointer is SUPA_ERR_INVALID_ARG. */
 int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float *y_dev, float *grads_host,
                              double *loss_host, void *stream);
-/* One Adam step on one minibatch (asynchronous); adds the minibatch loss to
- * *loss_acc_dev (device FP64) when it is not NULL. */
+/* One Adam step on one minibatch (asynchronous; x_dev, y_dev as for
+ * supa_surrogate_gradients); adds the minibatch loss to *loss_acc_dev
+ * (device FP64) when it is not NULL. */
 int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float *y_dev, float lr,
                               double *loss_acc_dev, void *stream);
 /* One epoch over a training set of n samples (x_dev [n][6], y_dev [n][60]):

@@ -80,7 +80,7 @@ struct WeightCopies {
     __nv_bfloat16 *Wb[4], *WTb[4];
 };
 
-__global__ void adam_update(float *p, float *m, float *v, const float *g, int n, float lr, float b1, float b2,
+__global__ void adam_update(float *p, float *m, float *v, float *g, int n, float lr, float b1, float b2,
                             float eps, float c1, float c2, const WeightCopies wc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -91,6 +91,7 @@ __global__ void adam_update(float *p, float *m, float *v, const float *g, int n,
     v[i] = vi;
     const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     p[i] = pi;
+    g[i] = 0.0f;  // ready for the next minibatch's gradients
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
         const int j = i - (int)wc.off[w];
@@ -136,6 +137,7 @@ __global__ void cast_weight(const float *W, int rows, int cols, __nv_bfloat16 *W
 struct supa_surrogate {
     int B = 0;
     int t = 0;  // Adam step count
+    bool grad_zero = false;  // the gradient block holds zeros (the Adam update clears it)
     float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
     float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     __nv_bfloat16 *W1b, *W2b, *W3b, *W4b, *W2Tb, *W3Tb, *W4Tb;
@@ -182,8 +184,9 @@ int weight_copies(supa_surrogate *s, cudaStream_t st) {
 // over the rows in one grouped launch.
 cudaError_t train_pass(supa_surrogate *s, const float *y, cudaStream_t st) {
     const int B = s->B;
-    cudaError_t e = cudaMemsetAsync(s->grad, 0, Off::total * sizeof(float), st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!s->grad_zero && (e = cudaMemsetAsync(s->grad, 0, Off::total * sizeof(float), st)) != cudaSuccess) return e;
+    s->grad_zero = false;
     TrainPassArgs t{};
     t.B = B;
     t.b1 = s->master + Off::b1;
@@ -378,6 +381,8 @@ int supa_surrogate_get_params(supa_surrogate *s, float *params_host) {
 int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float *y_dev, float *grads_host,
                              double *loss_host, void *stream) {
     if (!s || !x_dev || !y_dev || !grads_host) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_gradients: null");
+    if (((uintptr_t)x_dev & 3) || ((uintptr_t)y_dev & 7))
+        return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_gradients: x must be 4-byte and y 8-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(s->loss_tmp, 0, sizeof(double), st) != cudaSuccess)
         return sfail(SUPA_ERR_CUDA, "memset failed");
@@ -417,7 +422,9 @@ int train_on_packed(supa_surrogate *s, const float *y_dev, float lr, double *los
                           {nullptr, s->W2Tb, s->W3Tb, s->W4Tb}};
     adam_update<<<(unsigned)((Off::total + 255) / 256), 256, 0, st>>>(s->master, s->m, s->v, s->grad, (int)Off::total,
                                                                       lr, s->beta1, s->beta2, s->eps, c1, c2, wc);
-    return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_step launch failed");
+    if (cudaGetLastError() != cudaSuccess) return sfail(SUPA_ERR_CUDA, "train_step launch failed");
+    s->grad_zero = true;
+    return SUPA_OK;
 }
 }  // namespace
 
@@ -426,6 +433,8 @@ extern "C" {
 int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float *y_dev, float lr,
                               double *loss_acc_dev, void *stream) {
     if (!s || !x_dev || !y_dev) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_step: null argument");
+    if (((uintptr_t)x_dev & 3) || ((uintptr_t)y_dev & 7))
+        return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_step: x must be 4-byte and y 8-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0);
     return train_on_packed(s, y_dev, lr, loss_acc_dev ? loss_acc_dev : s->loss_tmp, st);

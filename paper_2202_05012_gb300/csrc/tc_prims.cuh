@@ -169,6 +169,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 8 consecutive columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // A TMEM load of 32 lanes x 16 columns whose completion is awaited later: the
 // wait names the destination registers, so that no use of them moves above it.
 __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
@@ -227,6 +238,28 @@ __device__ __forceinline__ uint32_t gelu2_bf16(float2 z) {
     const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
     const float2 h = __ffma2_rn(hz, t, hz);
     return pack_bf16(h.x, h.y);
+}
+
+// Column sums of a warp's 32 x N block (lane = row, d[i] = column i, N a
+// power of two <= 32): a butterfly that halves the columns a lane keeps at
+// every step, then sums across the remaining lane groups.  Returns the sum of
+// column lane % N over the 32 rows (d is overwritten).
+template <int N>
+__device__ __forceinline__ float warp_column_sums(float (&d)[N], int lane) {
+#pragma unroll
+    for (int o = N / 2; o > 0; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float give = upper ? d[i] : d[i + o];
+            const float keep = upper ? d[i + o] : d[i];
+            d[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, give, o);
+        }
+    }
+    float s = d[0];
+#pragma unroll
+    for (int o = N; o < 32; o <<= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    return s;
 }
 
 // GELU and its derivative for two values at once, both as BF16 pairs, from

@@ -23,10 +23,11 @@
 //
 // Shared memory (209 KB): X 16 KB (the tile's inputs, bf16, K = 64 with 6
 // used), A 64 KB (activations or gradients, 4 K-blocks of 128 rows x 64
-// columns, 128-byte swizzle; during the loss it holds the float32 outputs),
-// G 32 KB (the output gradient, K = 128, columns 90.. zero), and a 3-stage
-// ring of 32 KB weight K-blocks in the order the MMAs use them: W1, W2 (4),
-// W3 (4), W4 (4, 128 rows), W4^T (2), W3^T (4), W2^T (4).
+// columns, 128-byte swizzle; after the output layer it holds d out, K = 128,
+// columns 90.. zero), and a 4-stage ring of 32 KB weight K-blocks -- one
+// hidden layer's weights, loaded during the epilogue before the layer -- in
+// the order the MMAs use them: W1, W2 (4), W3 (4), W4 (4, 128 rows), W4^T
+// (2), W3^T (4), W2^T (4).  The loss reads the outputs straight from TMEM.
 // Warps: 0 TMA producer, 1 TMEM owner and MMA issuer, 2 TMA stores of the
 // operand tiles, 4-19 epilogue (warp w reads TMEM lanes 32 (w % 4).. and
 // columns 16 ((w - 4) / 4).. of each 64-column block).
@@ -53,14 +54,12 @@ using namespace tc;
 constexpr int kTThreads = 640;
 constexpr int kTRows = 128;
 constexpr int kLayersOut = 30;
-constexpr int kOutPitch = 97;                 // float32 row pitch of the staged outputs
 constexpr uint32_t kXBytes = kTRows * 128;    // input tile
 constexpr uint32_t kABlk = kTRows * 128;      // one K-block of a 128-row operand
 constexpr uint32_t kABytes = 4 * kABlk;
-constexpr uint32_t kGBytes = 2 * kABlk;
 constexpr uint32_t kStageBytes = 256 * 128;   // one weight K-block (256 rows x 64 columns)
-constexpr int kRing = 3;
-constexpr uint32_t oX = 0, oA = kXBytes, oG = oA + kABytes, oS = oG + kGBytes;
+constexpr int kRing = 4;
+constexpr uint32_t oX = 0, oA = kXBytes, oS = oA + kABytes;
 constexpr uint32_t kTrainSmem = oS + kRing * kStageBytes + 1024;
 constexpr int kEpi = 16;
 constexpr int kPhases = 7;  // epilogue phases per tile: H1, H2, H3, d out, G3, G2, G1
@@ -91,10 +90,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
     __shared__ __align__(8) uint64_t a_ready;   // the next operand is written, the accumulator read
     __shared__ __align__(8) uint64_t a_free;    // the stores of that operand have read it
     __shared__ __align__(8) uint64_t drain;
-    __shared__ __align__(8) uint64_t epi_bar;   // all epilogue warps reached the same point
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(16) float sbias[3 * 256 + 128];
-    __shared__ float colsum4[128];
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -114,17 +111,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
         mbar_init(&a_ready, kEpi);
         mbar_init(&a_free, 1);
         mbar_init(&drain, 1);
-        mbar_init(&epi_bar, kEpi);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     for (int i = threadIdx.x; i < 3 * 256 + 128; i += blockDim.x)
         sbias[i] = i < 256 ? g.b1[i] : i < 512 ? g.b2[i - 256] : i < 768 ? g.b3[i - 512] : g.b4[i - 768];
-    for (int i = threadIdx.x; i < 128; i += blockDim.x) colsum4[i] = 0.0f;
-    // the output-gradient operand: columns 90..127 stay zero
-    for (uint32_t i = threadIdx.x; i < kGBytes / 16; i += blockDim.x)
-        reinterpret_cast<uint4 *>(base + oG)[i] = make_uint4(0u, 0u, 0u, 0u);
-    fence_smem_to_async();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
                      "r"(256)
@@ -189,8 +180,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
         if (lane == 0) {
             // ---- MMA issuer ----
             constexpr uint32_t id256 = idesc_bf16(kTRows, 256), id128 = idesc_bf16(kTRows, 128);
-            const uint32_t sX = smem_u32(base + oX), sA = smem_u32(base + oA), sG = smem_u32(base + oG),
-                           sS = smem_u32(base + oS);
+            const uint32_t sX = smem_u32(base + oX), sA = smem_u32(base + oA), sS = smem_u32(base + oS);
             bool ok = true;
             uint32_t ar = 0;  // a_ready completions consumed
             int c = 0;        // weight stages consumed
@@ -228,7 +218,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 ok = wait_operand() && layer(sA, 4, id256, 4)      // layer 2
                      && wait_operand() && layer(sA, 4, id256, 4)   // layer 3
                      && wait_operand() && layer(sA, 4, id128, 4)   // layer 4 (128 output columns)
-                     && wait_operand() && layer(sG, 2, id256, 4)   // d out W4: K = 128
+                     && wait_operand() && layer(sA, 2, id256, 4)   // d out W4: K = 128
                      && wait_operand() && layer(sA, 4, id256, 4)   // d H3 W3
                      && wait_operand() && layer(sA, 4, id256, 4);  // d H2 W2
             }
@@ -250,8 +240,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
                         break;
                     }
                     if (ph == 3) {
-                        tma_store_2d(&mp.g4, base + oG, 0, m0);
-                        tma_store_2d(&mp.g4, base + oG + kABlk, 64, m0);
+                        tma_store_2d(&mp.g4, base + oA, 0, m0);
+                        tma_store_2d(&mp.g4, base + oA + kABlk, 64, m0);
                     } else {
                         const CUtensorMap *m = ph == 0 ? &mp.h1 : ph == 1 ? &mp.h2 : ph == 2 ? &mp.h3
                                              : ph == 4 ? &mp.g3 : ph == 5 ? &mp.g2 : &mp.g1;
@@ -275,20 +265,9 @@ __global__ void __launch_bounds__(kTThreads, 1)
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const float inv = 1.0f / (float)(g.B * kLayersOut);
         uint8_t *A = base + oA;
-        uint8_t *G = base + oG;
         int ph = 0;   // acc_full completions consumed
-        int eph = 0;  // epi_bar completions consumed
         int np = 0;   // phases handed off (a_free completions to come)
         bool ok = true;
-        // a bounded barrier among the 16 epilogue warps (a plain named barrier
-        // would wait forever for a warp that gave up)
-        auto epi_sync = [&]() -> bool {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&epi_bar);
-            const bool w = __all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&epi_bar, eph & 1));
-            ++eph;
-            return w;
-        };
         // the accumulator of the next layer is final, and the previous phase's
         // operand has been read by its stores (warp-uniform, so that the
         // .sync.aligned TMEM loads see the whole warp)
@@ -342,65 +321,82 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 hand_off();
             }
             if (!ok) break;
-            // ---- output layer: stage out = acc + b4 (float32) in the A buffer ----
+            // ---- output layer and loss gradient: thread (q, h) takes row r and layers
+            //      j = 8h .. 8h + 7 (< 30), its outputs o_j, s_j, rho_j read from TMEM, and
+            //      writes d out (bf16) into the A buffer as the operand of d out W4 ----
             if (!wait_acc()) { ok = false; break; }
-            float *outs = reinterpret_cast<float *>(A);
-#pragma unroll 1
-            for (int kb = 0; kb < 2; ++kb) {
-                const int c0 = kb * 64 + h * 16;
-                float v[16];
-                tmem_ld16(tmem + lane_off + c0, v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (c0 + i < 96) outs[r * kOutPitch + c0 + i] = v[i] + sbias[768 + c0 + i];
-            }
-            if (!epi_sync()) { ok = false; break; }
-            // ---- loss gradient: warp w takes rows 8 (w - 4) .. + 7, lane j layer j (< 30):
-            //      the 16 target loads issued together (coalesced), one shared atomic per
-            //      element for the bias gradient, the loss summed in float per warp ----
             {
-                const int wr = warp - 4, j = lane;
-                float l = 0.0f;
-                if (j < kLayersOut) {
-                    const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
-                    float yv[8], yr[8];
+                const int j0 = 8 * h, nj = h < 3 ? 8 : kLayersOut - 24;
+                float om[8], os[8], orh[8];
+                tmem_ld8(tmem + lane_off + j0, om);
+                tmem_ld8(tmem + lane_off + kLayersOut + j0, os);
+                tmem_ld8(tmem + lane_off + 2 * kLayersOut + j0, orh);
+                const float *yrow = g.y + (size_t)row * (2 * kLayersOut);
+                float yv[8], yr[8];
 #pragma unroll
-                    for (int it = 0; it < 8; ++it) {
-                        const float *y = g.y + (size_t)(m0 + wr * 8 + it) * (2 * kLayersOut);
-                        yv[it] = __ldg(y + j);
-                        yr[it] = __ldg(y + kLayersOut + j);
+                for (int i = 0; i < 8; i += 2) {
+                    if (i < nj) {
+                        const float2 a = *reinterpret_cast<const float2 *>(yrow + j0 + i);
+                        const float2 b = *reinterpret_cast<const float2 *>(yrow + kLayersOut + j0 + i);
+                        yv[i] = a.x; yv[i + 1] = a.y;
+                        yr[i] = b.x; yr[i + 1] = b.y;
+                    } else {
+                        yv[i] = yv[i + 1] = yr[i] = yr[i + 1] = 0.0f;
                     }
+                }
+                float gd[16], gr[8];  // d out of the means and log-variances, of the distances
+                float l = 0.0f;
 #pragma unroll
-                    for (int it = 0; it < 8; ++it) {
-                        const int lr = wr * 8 + it;
-                        const float *o = outs + lr * kOutPitch;
-                        const float mu = expf(o[j] - kMuShift), sv = o[kLayersOut + j], rho = o[2 * kLayersOut + j];
-                        const float yj = yv[it], dr = rho - yr[it];
-                        const float res = yj - mu;
-                        const float es = expf(sv);
+                for (int i = 0; i < 8; ++i) {
+                    gd[i] = gd[8 + i] = gr[i] = 0.0f;
+                    if (i < nj) {
+                        const int j = j0 + i;
+                        const float mu = expf(om[i] + sbias[768 + j] - kMuShift);
+                        const float es = expf(os[i] + sbias[768 + kLayersOut + j]);
+                        const float dr = orh[i] + sbias[768 + 2 * kLayersOut + j] - yr[i];
+                        const float res = yv[i] - mu;
                         const float vv = es + kVarFloor;
                         const float iv = 1.0f / vv;
-                        l += 0.5f * (res * res * iv + logf(vv) + yj * dr * dr);
-                        const float gv[3] = {-res * iv * mu * inv, 0.5f * es * iv * (1.0f - res * res * iv) * inv,
-                                             yj * dr * inv};
+                        l += 0.5f * (res * res * iv + logf(vv) + yv[i] * dr * dr);
+                        gd[i] = -res * iv * mu * inv;
+                        gd[8 + i] = 0.5f * es * iv * (1.0f - res * res * iv) * inv;
+                        gr[i] = yv[i] * dr * inv;
+                    }
+                }
+                // d out into the operand: row r, columns j, 30 + j, 60 + j (2-byte stores);
+                // the padding columns 90..127 are zeroed by the h = 3 threads
+                uint8_t *Arow = A;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (i < nj) {
 #pragma unroll
                         for (int w3 = 0; w3 < 3; ++w3) {
-                            const int col = w3 * kLayersOut + j;
-                            *reinterpret_cast<__nv_bfloat16 *>(G + (col >> 6) * kABlk +
-                                                               sw128_offset(lr, (col & 63) >> 3) + (col & 7) * 2) =
-                                __float2bfloat16_rn(gv[w3]);
-                            atomicAdd(&colsum4[col], gv[w3]);
+                            const int col = w3 * kLayersOut + j0 + i;
+                            const float v = w3 == 0 ? gd[i] : w3 == 1 ? gd[8 + i] : gr[i];
+                            *reinterpret_cast<__nv_bfloat16 *>(Arow + (col >> 6) * kABlk +
+                                                               sw128_offset(r, (col & 63) >> 3) + (col & 7) * 2) =
+                                __float2bfloat16_rn(v);
                         }
                     }
                 }
+                if (h == 3) {
+                    uint8_t *blk = Arow + kABlk;  // columns 64..127
+#pragma unroll
+                    for (int col = 90; col < 96; ++col)
+                        *reinterpret_cast<__nv_bfloat16 *>(blk + sw128_offset(r, (col - 64) >> 3) + (col & 7) * 2) =
+                            __float2bfloat16_rn(0.0f);
+#pragma unroll
+                    for (int u = 4; u < 8; ++u) *reinterpret_cast<uint4 *>(blk + sw128_offset(r, u)) = make_uint4(0u, 0u, 0u, 0u);
+                }
+                // bias gradient of the output layer: column sums over the warp's rows
+                const float s16 = warp_column_sums<16>(gd, lane);
+                const float s8 = warp_column_sums<8>(gr, lane);
+                if (lane < 16 && (lane & 7) < nj)
+                    atomicAdd(&g.gb4[(lane < 8 ? 0 : kLayersOut) + j0 + (lane & 7)], s16);
+                if (lane < 8 && lane < nj) atomicAdd(&g.gb4[2 * kLayersOut + j0 + lane], s8);
 #pragma unroll
                 for (int o2 = 16; o2 > 0; o2 >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o2);
                 if (lane == 0) atomicAdd(g.loss_sum, (double)l / (double)(g.B * kLayersOut));
-            }
-            if (!epi_sync()) { ok = false; break; }
-            if (e < 3 * kLayersOut) {
-                atomicAdd(&g.gb4[e], colsum4[e]);
-                colsum4[e] = 0.0f;
             }
             hand_off();
             // ---- backward: g = acc * GELU'(z), to the operand, column sums ----
@@ -437,19 +433,9 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     uint8_t *blk = A + kb * kABlk;
                     *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
                     *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) = make_uint4(p[4], p[5], p[6], p[7]);
-                    // column sums over the warp's 32 rows: lane i < 16 ends with column c0 + i
-#pragma unroll
-                    for (int o2 = 8; o2 > 0; o2 >>= 1) {
-                        const bool upper = (lane & o2) != 0;
-#pragma unroll
-                        for (int i = 0; i < o2; ++i) {
-                            const float give = upper ? d[i] : d[i + o2];
-                            const float keep = upper ? d[i + o2] : d[i];
-                            d[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, give, o2);
-                        }
-                    }
-                    d[0] += __shfl_xor_sync(0xFFFFFFFFu, d[0], 16);
-                    if (lane < 16) atomicAdd(&gb[c0 + lane], d[0]);
+                    // column sums over the warp's 32 rows (bias gradient)
+                    const float cs = warp_column_sums<16>(d, lane);
+                    if (lane < 16) atomicAdd(&gb[c0 + lane], cs);
                     if (kb < 3) {
                         tmem_ld_wait(nxt);
 #pragma unroll
