@@ -44,18 +44,21 @@ returns them):
      and the MEAN fractions are taken without a draw.  Both: scaled by
      E / sum d when the sum exceeds E;
   5. one hit per layer with d_j > 0 at the layer's mid depth, displaced
-     from the particle's straight-line position by sigma_j (m1, m2):
-     sigma_j = max(0, rho_j) sqrt(LATERAL_M2 / 2), so that each layer's
-     displacement is an isotropic 2-D Gaussian whose mean squared distance
-     is LATERAL_M2 rho_j^2.  LATERAL_M2 = 1.41 is the energy-weighted
-     <r^2> / <r>^2 of the plain sub-showers' hit distances about the mean
-     distance of sub-showers alike in energy, start slice and layer
-     (measured with this oracle on 40,000 sub-showers of 0.5-2 GeV; a 2-D
-     Gaussian fitted to the mean distance alone has 4 / pi = 1.27 and left
-     the outer rings of the shower's lateral profile short);
-     (m1, m2) is one Box-Muller pair per particle (all its layers: the
+     from the particle's straight-line position by max(0, rho_j) q
+     (cos phi, sin phi), one (q, phi) per particle (all its layers: the
      sub-shower drifts one way), from words (w0, w1) of the Philox block
-     with counter (shower id, slice | 2 << 16, lineage lo, lineage hi).
+     with counter (shower id, slice | 2 << 16, lineage lo, lineage hi):
+     phi = 2 pi (w1 >> 8) 2^-24 and q = lateral_quantile(u), u = (w0 >> 8)
+     2^-24, the quantile function of the lateral law LATERAL_Q.  The law is
+     measured with this oracle (tests/golden/lateral_law.py): the
+     energy-weighted distribution of plain sub-showers' hit distances from
+     their axis divided by the mean distance of sub-showers alike in energy,
+     start slice and layer offset -- the quantity rho_j estimates -- with
+     mean 1, so each layer's mean displacement is rho_j.  It has a spike at
+     0 (a sub-shower's first deposits lie on its axis), a core narrower and
+     a tail longer than a 2-D Gaussian's (E q^2 = 1.38 against 4 / pi =
+     1.27); a Gaussian of either moment left the shower's lateral profile
+     2-3 % off in its rings.
 
 training_targets() writes out the network's targets from a plain
 simulation of sub-showers: deposit fractions y_j of layers start + j and
@@ -82,18 +85,37 @@ def features(div: dict, geom, e_s: float) -> np.ndarray:
                      (div["k"] - first[lay]) / count[lay], np.minimum(1.0, (L - lay) / 30.0)], 1)
 
 
-def _box_muller(w0: int, w1: int):
-    u1 = ((int(w0) >> 8) + 1) * 2.0 ** -24
-    u2 = (int(w1) >> 8) * 2.0 ** -24
-    rad = math.sqrt(-2.0 * math.log(u1))
-    return rad * math.cos(2 * math.pi * u2), rad * math.sin(2 * math.pi * u2)
+# The lateral law: its quantile function at u = i / 64, i = 0..64 (the last
+# value is the measured quantile at u = 0.998, which leaves the far 0.2 % of
+# the tail short), linear in between, scaled to mean 1.  Written by
+# tests/golden/lateral_law.py (80,000 sub-showers, seed 5).
+LATERAL_Q = np.array([
+    0.00000, 0.00000, 0.00000, 0.13168, 0.19840, 0.24732, 0.28922, 0.32671,
+    0.36028, 0.39115, 0.42114, 0.44900, 0.47602, 0.50152, 0.52699, 0.55146,
+    0.57525, 0.59910, 0.62231, 0.64475, 0.66703, 0.68907, 0.71090, 0.73253,
+    0.75422, 0.77610, 0.79778, 0.81916, 0.84060, 0.86253, 0.88486, 0.90712,
+    0.92884, 0.95082, 0.97305, 0.99593, 1.01889, 1.04247, 1.06618, 1.09030,
+    1.11503, 1.14011, 1.16589, 1.19201, 1.21890, 1.24660, 1.27561, 1.30556,
+    1.33609, 1.36810, 1.40167, 1.43705, 1.47402, 1.51349, 1.55558, 1.60084,
+    1.65098, 1.70647, 1.77006, 1.84258, 1.92934, 2.03901, 2.19413, 2.48104,
+    4.43834])
 
 
-def offset_normals(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
-    """The standard normal pair (m1, m2) of a particle's hit displacements."""
+def lateral_quantile(u: float) -> float:
+    """q(u), u in [0, 1), of the lateral law: linear between LATERAL_Q[i] at
+    u = i / 64 and LATERAL_Q[i + 1]."""
+    x = u * 64.0
+    i = min(63, int(x))
+    return float(LATERAL_Q[i] + (x - i) * (LATERAL_Q[i + 1] - LATERAL_Q[i]))
+
+
+def lateral_offset(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarray:
+    """(q cos phi, q sin phi) of a particle's hit displacements (step 5)."""
     key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
     w = philox(((shower_id) & 0xFFFFFFFF, k | (2 << 16), lineage & 0xFFFFFFFF, (lineage >> 32) & 0xFFFFFFFF), key)
-    return np.array(_box_muller(w[0], w[1]))
+    q = lateral_quantile((int(w[0]) >> 8) * 2.0 ** -24)
+    phi = 2 * math.pi * (int(w[1]) >> 8) * 2.0 ** -24
+    return np.array([q * math.cos(phi), q * math.sin(phi)])
 
 
 def training_targets(geom, prims, res) -> np.ndarray:
@@ -167,7 +189,6 @@ def gamma_variate(alpha: float, shower_id: int, k: int, lineage: int, j: int, se
 
 SAMPLE_C_MIN, SAMPLE_C_MAX = 1.0, 1.0e4
 FRACTION_MIN = 1.0e-6
-LATERAL_M2 = 1.41
 
 
 def sample_concentration(f: np.ndarray, s: np.ndarray) -> float:
@@ -239,11 +260,11 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
         if tot > E:
             d[i] *= E / tot
         zk = div["k"][i] * geom.dz
-        mo = offset_normals(shower_id_base + int(div["shower"][i]), int(div["k"][i]), int(div["lineage"][i]), seed)
+        mo = lateral_offset(shower_id_base + int(div["shower"][i]), int(div["k"][i]), int(div["lineage"][i]), seed)
         for j in range(30):
             if d[i, j] > 0:
                 zm = zmid[l0 + j]
-                sig = max(0.0, out[i, 60 + j]) * math.sqrt(LATERAL_M2 / 2.0)
+                sig = max(0.0, out[i, 60 + j])
                 hits.append((int(div["shower"][i]),
                              div["x"][i] + (zm - zk) * div["ux"][i] / div["uz"][i] + sig * mo[0],
                              div["y"][i] + (zm - zk) * div["uy"][i] / div["uz"][i] + sig * mo[1], zm, d[i, j],
