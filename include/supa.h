@@ -447,13 +447,11 @@ int supa_surrogate_check(supa_surrogate *s);
  * Philox keyed by shower, slice and lineage) and, scaled down when they add
  * up to more than E, are added to the layer sums and emitted as one hit per
  * non-empty layer after the shower's stepped hits: at the layer's mid depth,
- * displaced from the particle's straight line by sigma_j (m1, m2) with
- * sigma_j = max(0, rho_j) sqrt(1.41 / 2) (mean squared displacement
- * 1.41 rho_j^2, the plain sub-showers' <r^2> / <r>^2 about their mean
- * distance) and one pair of standard normals
- * m1, m2 per particle (Philox stream tag 2, same keys).  The energy left
- * over is
- * reported as sur_leak.  s = NULL or e_s <= 0 returns the batch to the plain
+ * displaced from the particle's straight line by max(0, rho_j) q (cos phi,
+ * sin phi), one (q, phi) per particle (Philox stream tag 2, same keys): phi
+ * uniform, q from the measured lateral law of plain sub-showers (their hits'
+ * distances from the axis over the mean distance, a 65-point quantile
+ * table, mean 1).  The energy left over is reported as sur_leak.  s = NULL or e_s <= 0 returns the batch to the plain
  * path.  s must outlive the batch.  Synchronous (allocates). */
 int supa_batch_set_surrogate(supa_batch *b, supa_surrogate *s, float e_s, int64_t queue_capacity, int32_t mode);
 

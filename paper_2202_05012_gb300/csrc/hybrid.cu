@@ -78,20 +78,39 @@ __device__ float gamma_variate(float alpha, uint32_t sid, int k, uint32_t lin_lo
 // and the MEAN shares are taken without a draw.
 constexpr float kSampleCMin = 1.0f, kSampleCMax = 1.0e4f;
 
-// The standard normal pair (m1, m2) displacing all hits of a diverted
-// particle: Box-Muller on words (w0, w1) of the Philox block with counter
-// (shower id, slice | 2 << 16, lineage lo, lineage hi), same key.  A
-// displacement needs no more than ~1e-6 relative accuracy, so the hardware
-// approximations of log, sin and cos serve.
-__device__ float2 offset_normals(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed) {
+// The lateral law of the surrogate hits: the quantile function of q, a hit's
+// distance from its sub-shower's axis over the mean distance rho_j, at u =
+// i / 64 (i = 0..64; the last point is the quantile at u = 0.998), linear in
+// between, mean 1.  Measured from plain sub-showers (energy-weighted hit
+// distances about the mean distance of sub-showers alike in energy, start
+// slice and layer offset, 0.05-2 GeV): an atom at 0, a core narrower and a
+// tail longer than a 2-D Gaussian's.
+__constant__ float c_lateral_q[65] = {
+    0.00000f, 0.00000f, 0.00000f, 0.13168f, 0.19840f, 0.24732f, 0.28922f, 0.32671f,
+    0.36028f, 0.39115f, 0.42114f, 0.44900f, 0.47602f, 0.50152f, 0.52699f, 0.55146f,
+    0.57525f, 0.59910f, 0.62231f, 0.64475f, 0.66703f, 0.68907f, 0.71090f, 0.73253f,
+    0.75422f, 0.77610f, 0.79778f, 0.81916f, 0.84060f, 0.86253f, 0.88486f, 0.90712f,
+    0.92884f, 0.95082f, 0.97305f, 0.99593f, 1.01889f, 1.04247f, 1.06618f, 1.09030f,
+    1.11503f, 1.14011f, 1.16589f, 1.19201f, 1.21890f, 1.24660f, 1.27561f, 1.30556f,
+    1.33609f, 1.36810f, 1.40167f, 1.43705f, 1.47402f, 1.51349f, 1.55558f, 1.60084f,
+    1.65098f, 1.70647f, 1.77006f, 1.84258f, 1.92934f, 2.03901f, 2.19413f, 2.48104f,
+    4.43834f};
+
+// The displacement (q cos phi, q sin phi) of all hits of a diverted particle,
+// in units of each layer's rho_j: from words (w0, w1) of the Philox block with
+// counter (shower id, slice | 2 << 16, lineage lo, lineage hi), same key,
+// q = the law's quantile at u = (w0 >> 8) 2^-24, phi = 2 pi (w1 >> 8) 2^-24.
+// A displacement needs no more than ~1e-6 relative accuracy, so the hardware
+// sine and cosine serve.
+__device__ float2 lateral_offset(uint32_t sid, int k, uint32_t lin_lo, uint32_t lin_hi, uint64_t seed) {
     const uint4 r = philox4x32_10(make_uint4(sid, (uint32_t)k | (2u << 16), lin_lo, lin_hi), (uint32_t)seed,
                                   (uint32_t)(seed >> 32));
-    const float u1 = (float)((r.x >> 8) + 1u) * (1.0f / 16777216.0f);  // (0, 1]
-    const float u2 = u24(r.y);
-    const float rad = sqrtf(-2.0f * __logf(u1));
+    const float x = (float)(r.x >> 8) * (64.0f / 16777216.0f);  // exact: u * 64 in [0, 64)
+    const int i = min(63, (int)x);
+    const float q = fmaf(x - (float)i, c_lateral_q[i + 1] - c_lateral_q[i], c_lateral_q[i]);
     float sn, cs;
-    __sincosf(6.28318530717958648f * u2, &sn, &cs);
-    return make_float2(rad * cs, rad * sn);
+    __sincosf(6.28318530717958648f * u24(r.y), &sn, &cs);
+    return make_float2(q * cs, q * sn);
 }
 
 // Contiguous range of queue entries of this warp: consecutive entries mostly
@@ -278,10 +297,9 @@ __global__ void __launch_bounds__(kDepWarps * 32) sur_deposits(const SurParams p
 // with lane j writing the hit of layer start + j when its deposit is > 0 --
 // a particle's hits are consecutive, in layer order.  The hit sits at the
 // layer's mid depth, displaced from the particle's straight line by
-// sigma_j (m1, m2), sigma_j = max(0, rho_j) sqrt(kLateralM2 / 2): per layer
-// an isotropic 2-D Gaussian whose mean squared distance is kLateralM2 times
-// the square of the predicted mean distance rho_j, with one normal pair per
-// particle (drawn lane-per-particle for the group).
+// max(0, rho_j) (m1, m2), one lateral-law draw (m1, m2) per particle (drawn
+// lane-per-particle for the group): the mean displacement of a layer's hit
+// is the predicted mean distance rho_j.
 __global__ void sur_hits(const SurParams p) {
     const unsigned n = min(*p.count, (unsigned)p.cap);
     const int lane = threadIdx.x & 31;
@@ -302,7 +320,7 @@ __global__ void sur_hits(const SurParams p) {
             sh = (int)r.shower;
             r_tag = (1ull << 63) | ((unsigned long long)r.lin_hi << 32) | r.lin_lo;
             c = p.pcnt[i];
-            if (c) r_m = offset_normals((uint32_t)(p.shower_id_base + r.shower), r.k, r.lin_lo, r.lin_hi, p.seed);
+            if (c) r_m = lateral_offset((uint32_t)(p.shower_id_base + r.shower), r.k, r.lin_lo, r.lin_hi, p.seed);
             const GeomDev &g = p.geoms[p.prim[r.shower].geom & 0xFFFFu];
             r_loff = g.layer_off + r.layer;
             r_zk = (float)r.k * g.dz;
@@ -359,7 +377,7 @@ __global__ void sur_hits(const SurParams p) {
                 if (d[u] > 0.0f) {
                     const float zm = zmid[u];
                     const float dz = zm - zk;
-                    const float sig = fmaxf(0.0f, rho[u]) * kLateralSigma;
+                    const float sig = fmaxf(0.0f, rho[u]);
                     p.hits[at + __popc(nz & lt)] =
                         make_float4(fmaf(sig, m1, fmaf(dz, tx, x)), fmaf(sig, m2, fmaf(dz, ty, y)), zm, d[u]);
                     if (p.tags) p.tags[at + __popc(nz & lt)] = tag;

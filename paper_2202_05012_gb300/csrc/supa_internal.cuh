@@ -69,12 +69,6 @@ __device__ __forceinline__ double from_fixed32(unsigned long long v) {
 constexpr float kMuShift = 4.0f;
 // Floor of the predicted variance of a deposit fraction, e^s_j + kVarFloor.
 constexpr float kVarFloor = 1.0e-8f;
-// A surrogate hit's displacement is a 2-D Gaussian with mean squared distance
-// kLateralM2 rho_j^2 (sigma = rho_j sqrt(kLateralM2 / 2)): the plain
-// sub-showers' energy-weighted <r^2> / <r>^2 about their conditional mean
-// distance.
-constexpr float kLateralM2 = 1.41f;
-constexpr float kLateralSigma = 0.83964278f;  // sqrt(1.41 / 2)
 constexpr float kFractionMin = 1.0e-6f;
 
 struct SurRec {
