@@ -29,10 +29,15 @@
 // the order the MMAs use them: W1, W2 (4), W3 (4), W4 (4, 128 rows), W4^T
 // (2), W3^T (4), W2^T (4).  The loss reads the outputs straight from TMEM.
 // Warps: 0 TMA producer, 1 TMEM owner and MMA issuer, 2 TMA stores of the
-// operand tiles, 4-19 epilogue (warp w reads TMEM lanes 32 (w % 4).. and
-// columns 16 ((w - 4) / 4).. of each 64-column block).
-// Barriers per tile: acc_full completes once per MMA layer (7); a_ready once
-// per epilogue phase (7: the operand is written and the accumulator read);
+// operand tiles, 3-18 epilogue (warp w reads TMEM lanes 32 (w % 4).. and
+// columns 16 ((w - 3) / 4).. of each 64-column block).
+// Two TMEM accumulators (512 columns) alternate between consecutive layers,
+// and each 64-column K-block of an operand is handed to the MMA issuer (and
+// to the stores) as soon as the epilogue has written it: the next layer's
+// MMAs run while the epilogue finishes the current one.
+// Barriers: acc_full completes once per MMA layer (7 per tile); a_ready[kb]
+// once per epilogue phase (7 per tile: K-block kb of the operand is written,
+// and the epilogue is past reading the accumulator before the current one);
 // a_free once per phase after the stores of its operand have read shared
 // memory, before the next phase overwrites it.
 // Every wait is bounded; on expiry the CTA sets the error word, stops, lets
@@ -51,7 +56,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kTThreads = 640;
+constexpr int kTThreads = 608;  // 19 warps (5 on some schedulers: 96 registers a thread)
 constexpr int kTRows = 128;
 constexpr int kLayersOut = 30;
 constexpr uint32_t kXBytes = kTRows * 128;    // input tile
@@ -62,7 +67,8 @@ constexpr int kRing = 4;
 constexpr uint32_t oX = 0, oA = kXBytes, oS = oA + kABytes;
 constexpr uint32_t kTrainSmem = oS + kRing * kStageBytes + 1024;
 constexpr int kEpi = 16;
-constexpr int kPhases = 7;  // epilogue phases per tile: H1, H2, H3, d out, G3, G2, G1
+constexpr int kPhases = 7;    // epilogue phases per tile: H1, H2, H3, d out, G3, G2, G1
+constexpr int kHandOff = 2;  // K-blocks per hand-off of an operand to the MMAs (1, 2 or 4)
 
 // The weight K-block loads of one tile, in MMA order.
 struct LoadPlan {
@@ -87,7 +93,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
     __shared__ __align__(8) uint64_t w_full[kRing], w_empty[kRing];
     __shared__ __align__(8) uint64_t x_full, x_empty;
     __shared__ __align__(8) uint64_t acc_full;  // a layer's accumulator is final
-    __shared__ __align__(8) uint64_t a_ready;   // the next operand is written, the accumulator read
+    __shared__ __align__(8) uint64_t a_ready[4];  // K-block kb of the next operand is written
     __shared__ __align__(8) uint64_t a_free;    // the stores of that operand have read it
     __shared__ __align__(8) uint64_t drain;
     __shared__ uint32_t tmem_slot;
@@ -108,7 +114,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
         mbar_init(&x_full, 1);
         mbar_init(&x_empty, 1);
         mbar_init(&acc_full, 1);
-        mbar_init(&a_ready, kEpi);
+        for (int kb = 0; kb < 4; ++kb) mbar_init(&a_ready[kb], kEpi);
         mbar_init(&a_free, 1);
         mbar_init(&drain, 1);
         abort_flag = 0;
@@ -118,7 +124,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
         sbias[i] = i < 256 ? g.b1[i] : i < 512 ? g.b2[i - 256] : i < 768 ? g.b3[i - 512] : g.b4[i - 768];
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(256)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -182,45 +188,45 @@ __global__ void __launch_bounds__(kTThreads, 1)
             constexpr uint32_t id256 = idesc_bf16(kTRows, 256), id128 = idesc_bf16(kTRows, 128);
             const uint32_t sX = smem_u32(base + oX), sA = smem_u32(base + oA), sS = smem_u32(base + oS);
             bool ok = true;
-            uint32_t ar = 0;  // a_ready completions consumed
-            int c = 0;        // weight stages consumed
-            // one layer: `nkb` K-blocks of the operand at `a_base` against the next ring stages
-            auto layer = [&](uint32_t a_base, int nkb, uint32_t idesc, int k_steps_first) -> bool {
+            uint32_t m = 0;  // MMA layers issued: layer m accumulates in TMEM columns 256 (m % 2)..
+            int c = 0;       // weight stages consumed
+            // one layer: `nkb` K-blocks of the operand at `a_base` against the next ring
+            // stages; with `wait_op`, K-block kb waits until the epilogue of the previous
+            // layer has written it (which also means that epilogue is past reading the
+            // accumulator this layer overwrites)
+            auto layer = [&](uint32_t a_base, int nkb, uint32_t idesc, int k_steps_first, bool wait_op) -> bool {
+                const uint32_t acc = tmem + (m & 1u) * 256u;
                 for (int kb = 0; kb < nkb; ++kb) {
+                    if (wait_op && (*abort_v || !mbar_wait(&a_ready[kb], (m - 1) & 1))) return false;
                     const int s = c % kRing;
                     if (*abort_v || !mbar_wait(&w_full[s], (c / kRing) & 1)) return false;
                     fence_after_sync();
                     const int ks = kb == 0 ? k_steps_first : 4;
                     for (int k = 0; k < ks; ++k)
-                        mma_bf16(tmem, sw128_desc(a_base + kb * kABlk + k * 32), sw128_desc(sS + s * kStageBytes + k * 32),
+                        mma_bf16(acc, sw128_desc(a_base + kb * kABlk + k * 32), sw128_desc(sS + s * kStageBytes + k * 32),
                                  idesc, (kb > 0 || k > 0) ? 1u : 0u);
                     mma_commit(&w_empty[s]);
                     ++c;
                 }
                 mma_commit(&acc_full);
-                return true;
-            };
-            auto wait_operand = [&]() -> bool {
-                if (*abort_v || !mbar_wait(&a_ready, ar & 1)) return false;
-                ++ar;
-                fence_after_sync();
+                ++m;
                 return true;
             };
             for (int t = 0; t < my_tiles && ok; ++t) {
-                // the accumulator is free once the previous tile's last epilogue read it
-                if (t > 0 && !wait_operand()) { ok = false; break; }
+                // layer 1 (K = 16: 6 inputs, zero padded) reads the input tile; its
+                // accumulator is free once the previous tile's last epilogue has begun
+                if (t > 0 && (*abort_v || !mbar_wait(&a_ready[0], (m - 1) & 1))) { ok = false; break; }
                 if (*abort_v || !mbar_wait(&x_full, t & 1)) { ok = false; break; }
                 fence_after_sync();
-                // layer 1: K = 16 (6 inputs, zero padded)
-                ok = layer(sX, 1, id256, 1);
+                ok = layer(sX, 1, id256, 1, false);
                 if (!ok) break;
                 mma_commit(&x_empty);
-                ok = wait_operand() && layer(sA, 4, id256, 4)      // layer 2
-                     && wait_operand() && layer(sA, 4, id256, 4)   // layer 3
-                     && wait_operand() && layer(sA, 4, id128, 4)   // layer 4 (128 output columns)
-                     && wait_operand() && layer(sA, 2, id256, 4)   // d out W4: K = 128
-                     && wait_operand() && layer(sA, 4, id256, 4)   // d H3 W3
-                     && wait_operand() && layer(sA, 4, id256, 4);  // d H2 W2
+                ok = layer(sA, 4, id256, 4, true)      // layer 2
+                     && layer(sA, 4, id256, 4, true)   // layer 3
+                     && layer(sA, 4, id128, 4, true)   // layer 4 (128 output columns)
+                     && layer(sA, 2, id256, 4, true)   // d out W4: K = 128
+                     && layer(sA, 4, id256, 4, true)   // d H3 W3
+                     && layer(sA, 4, id256, 4, true);  // d H2 W2
             }
             if (!ok) fail();
             // every MMA issued by this thread completes before tensor memory is freed
@@ -230,24 +236,23 @@ __global__ void __launch_bounds__(kTThreads, 1)
     } else if (warp == 2) {
         if (lane == 0) {
             // ---- stores: each phase's operand tile to its row-major matrix ----
-            uint32_t n = 0;  // a_ready completions seen
+            uint32_t n = 0;  // epilogue phases seen
             bool ok = true;
             for (int t = 0; t < my_tiles && ok; ++t) {
                 const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
-                for (int ph = 0; ph < kPhases; ++ph, ++n) {
-                    if (*abort_v || !mbar_wait(&a_ready, n & 1)) {
-                        ok = false;
-                        break;
-                    }
-                    if (ph == 3) {
-                        tma_store_2d(&mp.g4, base + oA, 0, m0);
-                        tma_store_2d(&mp.g4, base + oA + kABlk, 64, m0);
-                    } else {
-                        const CUtensorMap *m = ph == 0 ? &mp.h1 : ph == 1 ? &mp.h2 : ph == 2 ? &mp.h3
-                                             : ph == 4 ? &mp.g3 : ph == 5 ? &mp.g2 : &mp.g1;
+                for (int ph = 0; ph < kPhases && ok; ++ph, ++n) {
+                    const CUtensorMap *m = ph == 0 ? &mp.h1 : ph == 1 ? &mp.h2 : ph == 2 ? &mp.h3 : ph == 3 ? &mp.g4
+                                         : ph == 4 ? &mp.g3 : ph == 5 ? &mp.g2 : &mp.g1;
+                    // each K-block leaves as soon as it is written (d out has two)
 #pragma unroll 1
-                        for (int kb = 0; kb < 4; ++kb) tma_store_2d(m, base + oA + kb * kABlk, kb * 64, m0);
+                    for (int kb = 0; kb < 4; ++kb) {
+                        if (*abort_v || !mbar_wait(&a_ready[kb], n & 1)) {
+                            ok = false;
+                            break;
+                        }
+                        if (ph != 3 || kb < 2) tma_store_2d(m, base + oA + kb * kABlk, kb * 64, m0);
                     }
+                    if (!ok) break;
                     bulk_commit();
                     bulk_wait_read_all();
                     mbar_arrive(&a_free);
@@ -257,11 +262,10 @@ __global__ void __launch_bounds__(kTThreads, 1)
             // the stores complete before the CTA (and its shared memory) goes away
             bulk_wait_all();
         }
-    } else if (warp >= 4) {
+    } else if (warp >= 3) {
         // ---- epilogue: warp (q, h) owns rows 32q.. and columns 16h.. of each K-block ----
-        const int q = warp & 3, h = (warp - 4) >> 2;
+        const int q = warp & 3, h = (warp - 3) >> 2;
         const int r = q * 32 + lane;
-        const int e = (warp - 4) * 32 + lane;  // 0..511
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const float inv = 1.0f / (float)(g.B * kLayersOut);
         uint8_t *A = base + oA;
@@ -278,12 +282,16 @@ __global__ void __launch_bounds__(kTThreads, 1)
             fence_after_sync();
             return w;
         };
-        auto hand_off = [&]() {
+        // K-blocks up to kb of the next operand are written (and this warp is
+        // past its reads of the previous accumulator): every kHandOff K-blocks,
+        // one fence for the group
+        auto hand_off_kb = [&](int kb) {
+            if ((kb + 1) % kHandOff != 0) return;
             fence_smem_to_async();
             fence_before_sync();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&a_ready);
-            ++np;
+            if (lane == 0)
+                for (int k = kb + 1 - kHandOff; k <= kb; ++k) mbar_arrive(&a_ready[k]);
         };
         for (int t = 0; t < my_tiles && ok; ++t) {
             const int row = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows + r;
@@ -291,14 +299,15 @@ __global__ void __launch_bounds__(kTThreads, 1)
             for (int l = 0; l < 3 && ok; ++l) {
                 if (!wait_acc()) { ok = false; break; }
                 __nv_bfloat16 *GP = (l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + (size_t)row * 256;
+                const uint32_t acc = tmem + lane_off + (uint32_t)(np & 1) * 256u;
                 // the next K-block's accumulator columns load while this one is processed
                 uint32_t raw[16], nxt[16];
-                tmem_ld16_issue(tmem + lane_off + h * 16, raw);
+                tmem_ld16_issue(acc + h * 16, raw);
                 tmem_ld_wait(raw);
 #pragma unroll
                 for (int kb = 0; kb < 4; ++kb) {
                     const int c0 = kb * 64 + h * 16;
-                    if (kb < 3) tmem_ld16_issue(tmem + lane_off + c0 + 64, nxt);
+                    if (kb < 3) tmem_ld16_issue(acc + c0 + 64, nxt);
                     float v[16];
                     const float *bb = sbias + l * 256 + c0;
 #pragma unroll
@@ -312,25 +321,22 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     uint4 *gp = reinterpret_cast<uint4 *>(GP + c0);
                     gp[0] = make_uint4(d[0], d[1], d[2], d[3]);
                     gp[1] = make_uint4(d[4], d[5], d[6], d[7]);
+                    hand_off_kb(kb);
                     if (kb < 3) {
                         tmem_ld_wait(nxt);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) raw[i] = nxt[i];
                     }
                 }
-                hand_off();
+                ++np;
             }
             if (!ok) break;
             // ---- output layer and loss gradient: thread (q, h) takes row r and layers
             //      j = 8h .. 8h + 7 (< 30), its outputs o_j, s_j, rho_j read from TMEM, and
             //      writes d out (bf16) into the A buffer as the operand of d out W4 ----
-            if (!wait_acc()) { ok = false; break; }
             {
                 const int j0 = 8 * h, nj = h < 3 ? 8 : kLayersOut - 24;
-                float om[8], os[8], orh[8];
-                tmem_ld8(tmem + lane_off + j0, om);
-                tmem_ld8(tmem + lane_off + kLayersOut + j0, os);
-                tmem_ld8(tmem + lane_off + 2 * kLayersOut + j0, orh);
+                // the targets load while the output layer's MMAs run
                 const float *yrow = g.y + (size_t)row * (2 * kLayersOut);
                 float yv[8], yr[8];
 #pragma unroll
@@ -344,6 +350,10 @@ __global__ void __launch_bounds__(kTThreads, 1)
                         yv[i] = yv[i + 1] = yr[i] = yr[i + 1] = 0.0f;
                     }
                 }
+                if (!wait_acc()) { ok = false; break; }
+                const uint32_t acc = tmem + lane_off + (uint32_t)(np & 1) * 256u;
+                float om[8], os[8], orh[8];
+                tmem_ld8x3(acc + j0, acc + kLayersOut + j0, acc + 2 * kLayersOut + j0, om, os, orh);
                 float gd[16], gr[8];  // d out of the means and log-variances, of the distances
                 float l = 0.0f;
 #pragma unroll
@@ -398,7 +408,9 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 for (int o2 = 16; o2 > 0; o2 >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o2);
                 if (lane == 0) atomicAdd(g.loss_sum, (double)l / (double)(g.B * kLayersOut));
             }
-            hand_off();
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) hand_off_kb(kb);
+            ++np;
             // ---- backward: g = acc * GELU'(z), to the operand, column sums ----
             for (int l = 2; l >= 0 && ok; --l) {
                 const __nv_bfloat16 *GP = (l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + (size_t)row * 256;
@@ -408,15 +420,16 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 // while this one is processed
                 const uint4 *gpv = reinterpret_cast<const uint4 *>(GP + h * 16);
                 uint4 gp0 = gpv[0], gp1 = gpv[1];
+                const uint32_t acc = tmem + lane_off + (uint32_t)(np & 1) * 256u;
                 uint32_t raw[16], nxt[16];
-                tmem_ld16_issue(tmem + lane_off + h * 16, raw);
+                tmem_ld16_issue(acc + h * 16, raw);
                 tmem_ld_wait(raw);
 #pragma unroll
                 for (int kb = 0; kb < 4; ++kb) {
                     const int c0 = kb * 64 + h * 16;
                     uint4 np0 = gp0, np1 = gp1;
                     if (kb < 3) {
-                        tmem_ld16_issue(tmem + lane_off + c0 + 64, nxt);
+                        tmem_ld16_issue(acc + c0 + 64, nxt);
                         np0 = gpv[8 * (kb + 1)];  // 64 bf16 columns = 8 x 16 bytes
                         np1 = gpv[8 * (kb + 1) + 1];
                     }
@@ -436,6 +449,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     // column sums over the warp's 32 rows (bias gradient)
                     const float cs = warp_column_sums<16>(d, lane);
                     if (lane < 16) atomicAdd(&gb[c0 + lane], cs);
+                    hand_off_kb(kb);
                     if (kb < 3) {
                         tmem_ld_wait(nxt);
 #pragma unroll
@@ -444,7 +458,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
                         gp1 = np1;
                     }
                 }
-                hand_off();
+                ++np;
             }
         }
         if (!ok) fail();
@@ -454,7 +468,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
     __syncthreads();
     if (warp == 1) {
         fence_after_sync();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512) : "memory");
     }
 }
 
