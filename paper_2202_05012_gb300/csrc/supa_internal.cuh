@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/supa.h"
 
 namespace supa {
@@ -219,6 +221,31 @@ cudaError_t step_kernel_attributes(int minb, bool regions, bool staged, int bloc
 // Exclusive scan of per-shower counts: kScanTile showers per block of the
 // first and last pass; scratch of scan_tmp_elems(n) = ceil(n / kScanTile) + 1
 // per-block totals.
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while the kernel before it in the stream is still running; it runs its
+// set-up (barriers, tensor memory) and then pdl_wait()s, which returns once
+// every earlier kernel of the stream has completed and its writes are
+// visible, before it touches their results or overwrites what they read.
+// pdl_trigger() lets the next such kernel be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;

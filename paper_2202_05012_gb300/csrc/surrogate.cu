@@ -18,10 +18,10 @@
 // and the 90 outputs to 128 rows; the padding stays exactly zero (zero inputs
 // and zero output gradients give zero updates).
 //
-// Training step: gather the minibatch -> pack inputs -> training pass
-// (forward, loss gradient, data-gradient chain, bias gradients) -> the four
-// weight gradients in one grouped launch -> Adam, which also refreshes the
-// BF16 weight copies.
+// Training step: the training pass (gathers its minibatch rows, forward,
+// loss gradient, data-gradient chain, bias gradients) -> the four weight
+// gradients in one grouped launch -> Adam, which also refreshes the BF16
+// weight copies and clears the gradients.
 
 #include <cuda_bf16.h>
 
@@ -56,21 +56,6 @@ cudaError_t dalloc(T **p, size_t n) {
     return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
 }
 
-// Inputs [n][6] float32 -> X0 [B][64] bf16; rows past n are zero.
-__global__ void pack_inputs(const float *x, int64_t n, int B, __nv_bfloat16 *X0) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= B) return;
-    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (r < n)
-        for (int j = 0; j < kIn; ++j) v[j] = x[(size_t)r * kIn + j];
-    // one 128-byte row: the 6 features, then zeros
-    uint4 *row = reinterpret_cast<uint4 *>(X0 + (size_t)r * kInPad);
-    __nv_bfloat162 h[4];
-    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-    row[0] = *reinterpret_cast<const uint4 *>(h);
-    for (int j = 1; j < kInPad / 8; ++j) row[j] = make_uint4(0u, 0u, 0u, 0u);
-}
-
 // Adam with bias correction (c1 = 1 - beta1^t, c2 = 1 - beta2^t).
 // The BF16 copies of the four weight matrices (W and, where set, W^T) that
 // the GEMMs read, refreshed by the Adam update itself.
@@ -82,6 +67,8 @@ struct WeightCopies {
 
 __global__ void adam_update(float *p, float *m, float *v, float *g, int n, float lr, float b1, float b2,
                             float eps, float c1, float c2, const WeightCopies wc) {
+    pdl_wait();  // the weight gradients are complete
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -101,25 +88,6 @@ __global__ void adam_update(float *p, float *m, float *v, float *g, int n, float
             if (wc.WTb[w]) wc.WTb[w][(j % wc.cols[w]) * wc.rows[w] + j / wc.cols[w]] = h;
         }
     }
-}
-
-// Rows (a i + c) mod n, i = i0 .. i0 + B - 1, of x [n][6] and y [n][60]:
-// the targets to ys [B][60], the inputs packed as X0 [B][64] bf16 (the 6
-// features, then zeros).  One warp per row: the row's 66 floats are read and
-// its 240 + 128 bytes written by consecutive lanes.
-__global__ void gather_pack(const float *x, const float *y, int64_t n, uint64_t a, uint64_t c, int64_t i0, int B,
-                            float *ys, __nv_bfloat16 *X0) {
-    const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (r >= B) return;
-    const uint64_t src = (a * (uint64_t)(i0 + r) + c) % (uint64_t)n;
-    const float *yr = y + src * kY;
-    const float y0 = yr[lane], y1 = lane + 32 < kY ? yr[lane + 32] : 0.0f;
-    const float xv = lane < kIn ? x[src * kIn + lane] : 0.0f;
-    ys[(size_t)r * kY + lane] = y0;
-    if (lane + 32 < kY) ys[(size_t)r * kY + lane + 32] = y1;
-    const float lo = __shfl_sync(0xFFFFFFFFu, xv, (2 * lane) & 31), hi = __shfl_sync(0xFFFFFFFFu, xv, (2 * lane + 1) & 31);
-    const __nv_bfloat162 h = __floats2bfloat162_rn(2 * lane < kIn ? lo : 0.0f, 2 * lane + 1 < kIn ? hi : 0.0f);
-    reinterpret_cast<__nv_bfloat162 *>(X0 + (size_t)r * kInPad)[lane] = h;
 }
 
 // BF16 copies of a master weight [rows][cols]: W and (optionally) W^T.
@@ -143,7 +111,6 @@ struct supa_surrogate {
     __nv_bfloat16 *W1b, *W2b, *W3b, *W4b, *W2Tb, *W3Tb, *W4Tb;
     __nv_bfloat16 *X0, *H1, *H2, *H3, *G4, *G3, *G2, *G1;  // row-major operands of the weight gradients
     __nv_bfloat16 *GP1, *GP2, *GP3;                           // GELU'(z) of the hidden layers
-    float *Ys = nullptr;  // gathered minibatch targets (epoch training)
     double *loss_tmp = nullptr;
     int *error = nullptr;
     TrainMapSet tm;                                  // the training pass's loads and stores
@@ -177,12 +144,14 @@ int weight_copies(supa_surrogate *s, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : SUPA_ERR_CUDA;
 }
 
-// One minibatch (packed inputs in X0, targets y) up to the gradients in
-// s->grad (zeroed first) and the loss added to *s->loss_tmp: the training
-// pass per 128-row tile (forward, loss gradient, data-gradient chain; bias
-// gradients), then dW4 = G4^T H3, dW3 = G3^T H2, dW2 = G2^T H1, dW1 = G1^T X0
-// over the rows in one grouped launch.
-cudaError_t train_pass(supa_surrogate *s, const float *y, cudaStream_t st) {
+// One minibatch -- rows (a (i0 + r) + c) mod n of the inputs x [n][6] and
+// targets y [n][60] -- up to the gradients in s->grad (zeroed unless the last
+// Adam update left it zero) and the loss added to *s->loss_tmp: the training
+// pass per 128-row tile (gather, forward, loss gradient, data-gradient chain;
+// bias gradients), then dW4 = G4^T H3, dW3 = G3^T H2, dW2 = G2^T H1,
+// dW1 = G1^T X0 over the rows in one grouped launch.
+cudaError_t train_pass(supa_surrogate *s, const float *x, const float *y, int64_t n, uint64_t a, uint64_t c,
+                       int64_t i0, cudaStream_t st) {
     const int B = s->B;
     cudaError_t e = cudaSuccess;
     if (!s->grad_zero && (e = cudaMemsetAsync(s->grad, 0, Off::total * sizeof(float), st)) != cudaSuccess) return e;
@@ -193,7 +162,12 @@ cudaError_t train_pass(supa_surrogate *s, const float *y, cudaStream_t st) {
     t.b2 = s->master + Off::b2;
     t.b3 = s->master + Off::b3;
     t.b4 = s->master + Off::b4;
+    t.x = x;
     t.y = y;
+    t.n = n;
+    t.i0 = i0;
+    t.perm_a = a;
+    t.perm_c = c;
     t.GP1 = s->GP1; t.GP2 = s->GP2; t.GP3 = s->GP3;
     t.gb1 = s->grad + Off::b1; t.gb2 = s->grad + Off::b2; t.gb3 = s->grad + Off::b3; t.gb4 = s->grad + Off::b4;
     t.loss_sum = s->loss_tmp;
@@ -318,7 +292,7 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
               grab(s, &s->H3, B * kHid) && grab(s, &s->G4, B * kOutPad) && grab(s, &s->G3, B * kHid) &&
               grab(s, &s->G2, B * kHid) && grab(s, &s->G1, B * kHid) && grab(s, &s->GP1, B * kHid) &&
               grab(s, &s->GP2, B * kHid) && grab(s, &s->GP3, B * kHid) && grab(s, &s->loss_tmp, 1) &&
-              grab(s, &s->error, 1) && grab(s, &s->Ys, B * kY);
+              grab(s, &s->error, 1);
     if (!ok) {
         supa_surrogate_destroy(s);
         return sfail(SUPA_ERR_OOM, "supa_surrogate_create: out of device memory");
@@ -386,8 +360,7 @@ int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float 
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(s->loss_tmp, 0, sizeof(double), st) != cudaSuccess)
         return sfail(SUPA_ERR_CUDA, "memset failed");
-    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0);
-    cudaError_t e = train_pass(s, y_dev, st);
+    cudaError_t e = train_pass(s, x_dev, y_dev, s->B, 1, 0, 0, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("gradients: ") + cudaGetErrorString(e));
     int rc = check_error_word(s);
@@ -404,13 +377,14 @@ int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float 
 }  // extern "C"
 
 namespace {
-// The training pass of the packed minibatch in X0 with targets y (loss added
-// to *loss), then the Adam update.
-int train_on_packed(supa_surrogate *s, const float *y_dev, float lr, double *loss, cudaStream_t st) {
+// The training pass of the minibatch (see train_pass; loss added to *loss),
+// then the Adam update.
+int train_minibatch(supa_surrogate *s, const float *x, const float *y, int64_t n, uint64_t a, uint64_t c, int64_t i0,
+                    float lr, double *loss, cudaStream_t st) {
     // train_pass() adds the minibatch loss to s->loss_tmp; point it at the accumulator
     double *keep = s->loss_tmp;
     s->loss_tmp = loss;
-    cudaError_t e = train_pass(s, y_dev, st);
+    cudaError_t e = train_pass(s, x, y, n, a, c, i0, st);
     s->loss_tmp = keep;
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
     s->t += 1;
@@ -420,9 +394,9 @@ int train_on_packed(supa_surrogate *s, const float *y_dev, float lr, double *los
                           {kInPad, kHid, kHid, kHid},
                           {s->W1b, s->W2b, s->W3b, s->W4b},
                           {nullptr, s->W2Tb, s->W3Tb, s->W4Tb}};
-    adam_update<<<(unsigned)((Off::total + 255) / 256), 256, 0, st>>>(s->master, s->m, s->v, s->grad, (int)Off::total,
-                                                                      lr, s->beta1, s->beta2, s->eps, c1, c2, wc);
-    if (cudaGetLastError() != cudaSuccess) return sfail(SUPA_ERR_CUDA, "train_step launch failed");
+    if (launch_pdl(adam_update, dim3((unsigned)((Off::total + 255) / 256)), dim3(256), 0, st, s->master, s->m, s->v,
+                   s->grad, (int)Off::total, lr, s->beta1, s->beta2, s->eps, c1, c2, wc) != cudaSuccess)
+        return sfail(SUPA_ERR_CUDA, "train_step launch failed");
     s->grad_zero = true;
     return SUPA_OK;
 }
@@ -436,8 +410,7 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
     if (((uintptr_t)x_dev & 3) || ((uintptr_t)y_dev & 7))
         return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_step: x must be 4-byte and y 8-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
-    pack_inputs<<<(s->B + 255) / 256, 256, 0, st>>>(x_dev, s->B, s->B, s->X0);
-    return train_on_packed(s, y_dev, lr, loss_acc_dev ? loss_acc_dev : s->loss_tmp, st);
+    return train_minibatch(s, x_dev, y_dev, s->B, 1, 0, 0, lr, loss_acc_dev ? loss_acc_dev : s->loss_tmp, st);
 }
 
 int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,
@@ -461,8 +434,7 @@ int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const floa
     const int64_t steps = n / s->B;
     double *loss = loss_acc_dev ? loss_acc_dev : s->loss_tmp;
     for (int64_t k = 0; k < steps; ++k) {
-        gather_pack<<<(unsigned)((s->B + 7) / 8), 256, 0, st>>>(x_dev, y_dev, n, a, c, k * s->B, s->B, s->Ys, s->X0);
-        const int rc = train_on_packed(s, s->Ys, lr, loss, st);
+        const int rc = train_minibatch(s, x_dev, y_dev, n, a, c, k * s->B, lr, loss, st);
         if (rc != SUPA_OK) return rc;
     }
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_epoch launch failed");

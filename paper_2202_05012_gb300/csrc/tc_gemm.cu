@@ -5,6 +5,7 @@
 
 #include <algorithm>
 
+#include "supa_internal.cuh"
 #include "tc_gemm.cuh"
 #include "tc_prims.cuh"
 
@@ -89,6 +90,10 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
+    // the training pass that wrote the operands (and the Adam update that
+    // cleared the gradients) are done from here on
+    pdl_wait();
+    pdl_trigger();
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -212,8 +217,7 @@ cudaError_t launch_weight_grads(const CUtensorMap *g_maps, const CUtensorMap *h_
     pl.item0[a.nprob] = items;
     cudaError_t e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
     if (e != cudaSuccess) return e;
-    wgrad_kernel<<<items, kWgThreads, kWgSmem, st>>>(m, a, pl);
-    return cudaGetLastError();
+    return launch_pdl(wgrad_kernel, dim3(items), dim3(kWgThreads), kWgSmem, st, m, a, pl);
 }
 
 namespace {

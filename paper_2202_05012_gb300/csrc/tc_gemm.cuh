@@ -57,16 +57,22 @@ cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const C
 
 // One training pass of a minibatch up to the weight gradients (train_mlp.cu):
 // per 128-row tile the forward, the loss gradient and the data-gradient chain
-// in one kernel.  Inputs through the x0 map ([B][64] bf16, 128-row boxes),
-// weights through w1 ([256][64]), w2, w3 ([256][256]), w4 ([128][256], 128-row
-// boxes), w4t ([256][128]), w3t, w2t ([256][256]) -- 256-row boxes otherwise.
+// in one kernel.  The kernel gathers the minibatch rows itself; the packed
+// inputs leave through the x0 map ([B][64] bf16, 128-row boxes, columns 6..
+// zero: the B operand of dW1).  Weights through w1 ([256][64]), w2, w3
+// ([256][256]), w4 ([128][256], 128-row boxes), w4t ([256][128]), w3t, w2t
+// ([256][256]) -- 256-row boxes otherwise.
 // The activations H1..H3 ([B][256]) and the gradients d out (G4, [B][128],
 // columns 90.. zero) and G3..G1 ([B][256]), all row-major bf16, leave through
 // the store maps h1..h3, g4, g3..g1 (boxes of 64 columns x 128 rows).
 struct TrainPassArgs {
     int B;                              // rows, a multiple of 128
     const float *b1, *b2, *b3, *b4;     // biases [256] x 3, [128]
-    const float *y;                     // [B][60] targets
+    // the minibatch: row r is row (perm_a (i0 + r) + perm_c) mod n of the
+    // inputs x [n][6] and the targets y [n][60] (gathered by the kernel)
+    const float *x, *y;
+    int64_t n, i0;
+    uint64_t perm_a, perm_c;
     __nv_bfloat16 *GP1, *GP2, *GP3;     // [B][256] GELU'(z) of the hidden layers (written, read back)
     float *gb1, *gb2, *gb3, *gb4;       // bias gradients (added to)
     double *loss_sum;                   // minibatch loss (added to)

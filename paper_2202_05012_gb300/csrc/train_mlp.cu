@@ -6,16 +6,18 @@
 // Per layer and tile the tensor core takes the operand from shared memory,
 // the 16 epilogue warps turn its TMEM accumulator into the next operand.
 //
-// Writes what the weight-gradient GEMM and the optimiser need: every operand
-// tile it builds -- the activations H1..H3, the output gradient d out and the
-// hidden gradients G3..G1 -- leaves shared memory row-major through TMA
-// stores issued by one thread (the weight-gradient GEMM reads them as
-// MN-major operands, so no transposed copy is written); GELU'(z) of the
-// hidden layers (bf16 [B][256], two 16-byte stores per thread and K-block,
-// read back by the same thread in the backward); the bias gradients (column
-// sums) and the minibatch loss.  The per-layer launches it replaces each gave
-// every CTA one 128-row tile and spent most of their 15-20 us on the latency
-// of one tile's loads, MMAs and stores.
+// Gathers its minibatch rows itself (one warp packs the rows of x into the
+// input tile), and writes what the weight-gradient GEMM and the optimiser
+// need: every operand tile it builds -- the packed inputs, the activations
+// H1..H3, the output gradient d out and the hidden gradients G3..G1 -- leaves
+// shared memory row-major through TMA stores issued by one thread (the
+// weight-gradient GEMM reads them as MN-major operands, so no transposed copy
+// is written); GELU'(z) of the hidden layers (bf16 [B][256], two 16-byte
+// stores per thread and K-block, read back by the same thread in the
+// backward); the bias gradients (column sums) and the minibatch loss.  The
+// per-layer launches it replaces each gave every CTA one 128-row tile and
+// spent most of their 15-20 us on the latency of one tile's loads, MMAs and
+// stores.
 //
 // Loss (mean over rows and the 30 layers), network outputs o_j, s_j, rho_j:
 //   (y_j - mu_j)^2 / (2 v_j) + ln(v_j) / 2 + y_j (rho_j - R_j)^2 / 2,
@@ -29,8 +31,9 @@
 // the order the MMAs use them: W1, W2 (4), W3 (4), W4 (4, 128 rows), W4^T
 // (2), W3^T (4), W2^T (4).  The loss reads the outputs straight from TMEM.
 // Warps: 0 TMA producer, 1 TMEM owner and MMA issuer, 2 TMA stores of the
-// operand tiles, 3-18 epilogue (warp w reads TMEM lanes 32 (w % 4).. and
-// columns 16 ((w - 3) / 4).. of each 64-column block).
+// operand tiles, 3 gathers the minibatch rows of the inputs into the input
+// tile, 4-19 epilogue (warp w reads TMEM lanes 32 (w % 4).. and columns
+// 16 ((w - 4) / 4).. of each 64-column block).
 // Two TMEM accumulators (512 columns) alternate between consecutive layers,
 // and each 64-column K-block of an operand is handed to the MMA issuer (and
 // to the stores) as soon as the epilogue has written it: the next layer's
@@ -56,7 +59,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kTThreads = 608;  // 19 warps (5 on some schedulers: 96 registers a thread)
+constexpr int kTThreads = 640;  // 20 warps (5 per scheduler: 96 registers a thread)
 constexpr int kTRows = 128;
 constexpr int kLayersOut = 30;
 constexpr uint32_t kXBytes = kTRows * 128;    // input tile
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
     train_mlp_kernel(const __grid_constant__ TrainMapSet mp, const TrainPassArgs g) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t w_full[kRing], w_empty[kRing];
-    __shared__ __align__(8) uint64_t x_full, x_empty;
+    __shared__ __align__(8) uint64_t x_full, x_empty, x_read;  // input tile: gathered, read by layer 1, stored
     __shared__ __align__(8) uint64_t acc_full;  // a layer's accumulator is final
     __shared__ __align__(8) uint64_t a_ready[4];  // K-block kb of the next operand is written
     __shared__ __align__(8) uint64_t a_free;    // the stores of that operand have read it
@@ -113,6 +116,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
         }
         mbar_init(&x_full, 1);
         mbar_init(&x_empty, 1);
+        mbar_init(&x_read, 1);
         mbar_init(&acc_full, 1);
         for (int kb = 0; kb < 4; ++kb) mbar_init(&a_ready[kb], kEpi);
         mbar_init(&a_free, 1);
@@ -120,14 +124,23 @@ __global__ void __launch_bounds__(kTThreads, 1)
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    for (int i = threadIdx.x; i < 3 * 256 + 128; i += blockDim.x)
-        sbias[i] = i < 256 ? g.b1[i] : i < 512 ? g.b2[i - 256] : i < 768 ? g.b3[i - 512] : g.b4[i - 768];
+    // the input tile's columns 8..63 stay zero (the gather writes columns 0..7)
+    for (uint32_t i = threadIdx.x; i < kXBytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(base + oX)[i] = make_uint4(0u, 0u, 0u, 0u);
+    fence_smem_to_async();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
                      "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
+    // the earlier kernels of the stream (the last Adam update: weights and
+    // biases; the last weight gradients: readers of the buffers written here)
+    // are done from here on
+    pdl_wait();
+    pdl_trigger();
+    for (int i = threadIdx.x; i < 3 * 256 + 128; i += blockDim.x)
+        sbias[i] = i < 256 ? g.b1[i] : i < 512 ? g.b2[i - 256] : i < 768 ? g.b3[i - 512] : g.b4[i - 768];
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -140,18 +153,10 @@ __global__ void __launch_bounds__(kTThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---- TMA producer: each tile's input block, then its 23 weight K-blocks ----
-            int issued = 0, x_issued = 0;
+            // ---- TMA producer: each tile's 23 weight K-blocks ----
+            int issued = 0;
             bool ok = true;
             for (int t = 0; t < my_tiles && ok && !*abort_v; ++t) {
-                const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
-                if (t > 0 && !mbar_wait(&x_empty, (t - 1) & 1)) {
-                    fail();
-                    break;
-                }
-                mbar_expect_tx(&x_full, kXBytes);
-                tma_load_2d(base + oX, &mp.x0, 0, m0, &x_full);
-                x_issued = t + 1;
                 for (int i = 0; i < kLoads && ok; ++i) {
                     const int c = t * kLoads + i, s = c % kRing;
                     if (c >= kRing && !mbar_wait(&w_empty[s], ((c / kRing) - 1) & 1)) {
@@ -179,7 +184,6 @@ __global__ void __launch_bounds__(kTThreads, 1)
             if (*abort_v) {
                 // let the loads in flight land before the CTA exits
                 for (int i = max(0, issued - kRing); i < issued; ++i) mbar_wait(&w_full[i % kRing], (i / kRing) & 1);
-                if (x_issued > 0) mbar_wait(&x_full, (x_issued - 1) & 1);
             }
         }
     } else if (warp == 1) {
@@ -240,6 +244,15 @@ __global__ void __launch_bounds__(kTThreads, 1)
             bool ok = true;
             for (int t = 0; t < my_tiles && ok; ++t) {
                 const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
+                // the packed input tile (the B operand of dW1)
+                if (*abort_v || !mbar_wait(&x_full, t & 1)) {
+                    ok = false;
+                    break;
+                }
+                tma_store_2d(&mp.x0, base + oX, 0, m0);
+                bulk_commit();
+                bulk_wait_read_all();
+                mbar_arrive(&x_read);
                 for (int ph = 0; ph < kPhases && ok; ++ph, ++n) {
                     const CUtensorMap *m = ph == 0 ? &mp.h1 : ph == 1 ? &mp.h2 : ph == 2 ? &mp.h3 : ph == 3 ? &mp.g4
                                          : ph == 4 ? &mp.g3 : ph == 5 ? &mp.g2 : &mp.g1;
@@ -262,9 +275,37 @@ __global__ void __launch_bounds__(kTThreads, 1)
             // the stores complete before the CTA (and its shared memory) goes away
             bulk_wait_all();
         }
-    } else if (warp >= 3) {
+    } else if (warp == 3) {
+        // ---- gather: the tile's rows of x, packed to bf16 in the input tile ----
+        bool ok = true;
+        for (int t = 0; t < my_tiles && ok; ++t) {
+            const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
+            // the previous tile's input was read by layer 1 and by its store
+            if (t > 0 && !__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&x_empty, (t - 1) & 1) &&
+                                                      mbar_wait(&x_read, (t - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            float v[4][6];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t src = (int64_t)((g.perm_a * (uint64_t)(g.i0 + m0 + lane + 32 * k) + g.perm_c) %
+                                              (uint64_t)g.n);
+#pragma unroll
+                for (int j = 0; j < 6; ++j) v[k][j] = __ldg(g.x + src * 6 + j);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                *reinterpret_cast<uint4 *>(base + oX + sw128_offset(lane + 32 * k, 0)) =
+                    make_uint4(pack_bf16(v[k][0], v[k][1]), pack_bf16(v[k][2], v[k][3]), pack_bf16(v[k][4], v[k][5]), 0u);
+            fence_smem_to_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&x_full);
+        }
+        if (!ok) fail();
+    } else if (warp >= 4) {
         // ---- epilogue: warp (q, h) owns rows 32q.. and columns 16h.. of each K-block ----
-        const int q = warp & 3, h = (warp - 3) >> 2;
+        const int q = warp & 3, h = (warp - 4) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const float inv = 1.0f / (float)(g.B * kLayersOut);
@@ -337,7 +378,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
             {
                 const int j0 = 8 * h, nj = h < 3 ? 8 : kLayersOut - 24;
                 // the targets load while the output layer's MMAs run
-                const float *yrow = g.y + (size_t)row * (2 * kLayersOut);
+                const int64_t src = (int64_t)((g.perm_a * (uint64_t)(g.i0 + row) + g.perm_c) % (uint64_t)g.n);
+                const float *yrow = g.y + src * (2 * kLayersOut);
                 float yv[8], yr[8];
 #pragma unroll
                 for (int i = 0; i < 8; i += 2) {
@@ -476,14 +518,13 @@ __global__ void __launch_bounds__(kTThreads, 1)
 
 cudaError_t launch_train_pass(const TrainMapSet &maps, const TrainPassArgs &a, cudaStream_t st) {
     if (a.B < kTRows || a.B % kTRows) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(train_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
-    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaFuncSetAttribute(train_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+    if (e != cudaSuccess) return e;
     const int tiles = a.B / kTRows;
-    train_mlp_kernel<<<std::min(tiles, sms), kTThreads, kTrainSmem, st>>>(maps, a);
-    return cudaGetLastError();
+    return launch_pdl(train_mlp_kernel, dim3(std::min(tiles, sms)), dim3(kTThreads), kTrainSmem, st, maps, a);
 }
 
 }  // namespace supa
