@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
+    __syncwarp();  // lanes that ran a one-lane role rejoin: the block barrier is warp-aligned
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -423,6 +424,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     if constexpr (kTmaOut) {
         if (warp >= 4 && lane == 0) bulk_wait_all();
     }
+    __syncwarp();  // lanes that ran a one-lane role rejoin: the block barrier is warp-aligned
     fence_before_sync();
     __syncthreads();
     if (warp == 1) {

@@ -13,8 +13,8 @@
 // activations in shared memory as the next layer's operand and writes them,
 // and the gradients of the backward, row-major in BF16; the weight gradients
 // dW = G^T H read those as MN-major operands (tc_gemm.cu).  Each weight is
-// kept as W and W^T in BF16 (the backward multiplies by W^T), next to FP32
-// master weights and Adam moments.  The 6 inputs are padded to 64 columns
+// kept in BF16 (the backward's products with W^T read W as an MN-major
+// operand), next to FP32 master weights and Adam moments.  The 6 inputs are padded to 64 columns
 // and the 90 outputs to 128 rows; the padding stays exactly zero (zero inputs
 // and zero output gradients give zero updates).
 //
@@ -57,16 +57,18 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 // Adam with bias correction (c1 = 1 - beta1^t, c2 = 1 - beta2^t).
-// The BF16 copies of the four weight matrices (W and, where set, W^T) that
-// the GEMMs read, refreshed by the Adam update itself.
+// The BF16 copies of the four weight matrices that the tensor-core kernels
+// read, refreshed by the Adam update itself.
 struct WeightCopies {
-    size_t off[4];
-    int rows[4], cols[4];
-    __nv_bfloat16 *Wb[4], *WTb[4];
+    int off[4];   // offset of W in the master block
+    int size[4];  // rows x columns
+    __nv_bfloat16 *Wb[4];
 };
 
+// inv_c1 = 1 / c1, inv_sqrt_c2 = 1 / sqrt(c2): the step is
+// lr (m / c1) / (sqrt(v / c2) + eps) = lr m inv_c1 / (sqrt(v) inv_sqrt_c2 + eps).
 __global__ void adam_update(float *p, float *m, float *v, float *g, int n, float lr, float b1, float b2,
-                            float eps, float c1, float c2, const WeightCopies wc) {
+                            float eps, float inv_c1, float inv_sqrt_c2, const WeightCopies wc) {
     pdl_wait();  // the weight gradients are complete
     pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,28 +78,20 @@ __global__ void adam_update(float *p, float *m, float *v, float *g, int n, float
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float pi = p[i] - __fdividef(lr * mi * inv_c1, fmaf(sqrtf(vi), inv_sqrt_c2, eps));
     p[i] = pi;
     g[i] = 0.0f;  // ready for the next minibatch's gradients
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const int j = i - (int)wc.off[w];
-        if (j >= 0 && j < wc.rows[w] * wc.cols[w]) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(pi);
-            wc.Wb[w][j] = h;
-            if (wc.WTb[w]) wc.WTb[w][(j % wc.cols[w]) * wc.rows[w] + j / wc.cols[w]] = h;
-        }
+        const int j = i - wc.off[w];
+        if (j >= 0 && j < wc.size[w]) wc.Wb[w][j] = __float2bfloat16_rn(pi);
     }
 }
 
-// BF16 copies of a master weight [rows][cols]: W and (optionally) W^T.
-__global__ void cast_weight(const float *W, int rows, int cols, __nv_bfloat16 *Wb, __nv_bfloat16 *WTb) {
+// BF16 copy of a master weight [rows][cols].
+__global__ void cast_weight(const float *W, int n, __nv_bfloat16 *Wb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows * cols) return;
-    const int r = i / cols, c = i % cols;
-    const __nv_bfloat16 h = __float2bfloat16_rn(W[i]);
-    Wb[i] = h;
-    if (WTb) WTb[(size_t)c * rows + r] = h;
+    if (i < n) Wb[i] = __float2bfloat16_rn(W[i]);
 }
 
 }  // namespace
@@ -108,13 +102,14 @@ struct supa_surrogate {
     bool grad_zero = false;  // the gradient block holds zeros (the Adam update clears it)
     float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
     float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
-    __nv_bfloat16 *W1b, *W2b, *W3b, *W4b, *W2Tb, *W3Tb, *W4Tb;
+    __nv_bfloat16 *W1b, *W2b, *W3b, *W4b;
     __nv_bfloat16 *X0, *H1, *H2, *H3, *G4, *G3, *G2, *G1;  // row-major operands of the weight gradients
     __nv_bfloat16 *GP1, *GP2, *GP3;                           // GELU'(z) of the hidden layers
     double *loss_tmp = nullptr;
     int *error = nullptr;
     TrainMapSet tm;                                  // the training pass's loads and stores
     CUtensorMap dG[kWgradMax], dH[kWgradMax];        // weight-gradient operands (64-row boxes)
+    CUtensorMap dO[kWgradMax];                       // weight gradients (f32, reduced into by TMA)
     CUtensorMap mW4i;  // W4 rows 0..95 for the fused inference kernel
     std::vector<void *> allocs;
 };
@@ -137,10 +132,10 @@ void free_all(supa_surrogate *s) {
 
 int weight_copies(supa_surrogate *s, cudaStream_t st) {
     const int T = 256;
-    cast_weight<<<(kHid * kInPad + T - 1) / T, T, 0, st>>>(s->master + Off::W1, kHid, kInPad, s->W1b, nullptr);
-    cast_weight<<<(kHid * kHid + T - 1) / T, T, 0, st>>>(s->master + Off::W2, kHid, kHid, s->W2b, s->W2Tb);
-    cast_weight<<<(kHid * kHid + T - 1) / T, T, 0, st>>>(s->master + Off::W3, kHid, kHid, s->W3b, s->W3Tb);
-    cast_weight<<<(kOutPad * kHid + T - 1) / T, T, 0, st>>>(s->master + Off::W4, kOutPad, kHid, s->W4b, s->W4Tb);
+    cast_weight<<<(kHid * kInPad + T - 1) / T, T, 0, st>>>(s->master + Off::W1, kHid * kInPad, s->W1b);
+    cast_weight<<<(kHid * kHid + T - 1) / T, T, 0, st>>>(s->master + Off::W2, kHid * kHid, s->W2b);
+    cast_weight<<<(kHid * kHid + T - 1) / T, T, 0, st>>>(s->master + Off::W3, kHid * kHid, s->W3b);
+    cast_weight<<<(kOutPad * kHid + T - 1) / T, T, 0, st>>>(s->master + Off::W4, kOutPad * kHid, s->W4b);
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : SUPA_ERR_CUDA;
 }
 
@@ -181,7 +176,7 @@ cudaError_t train_pass(supa_surrogate *s, const float *x, const float *y, int64_
     w.p[2] = {kHid, kHid, s->grad + Off::W2, kHid};
     w.p[3] = {kHid, kInPad, s->grad + Off::W1, kInPad};
     w.error = s->error;
-    return launch_weight_grads(s->dG, s->dH, w, st);
+    return launch_weight_grads(s->dG, s->dH, s->dO, w, st);
 }
 
 int check_error_word(supa_surrogate *s) {
@@ -286,8 +281,7 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
     bool ok = grab(s, &s->master, Off::total) && grab(s, &s->m, Off::total) && grab(s, &s->v, Off::total) &&
               grab(s, &s->grad, Off::total) && grab(s, &s->W1b, (size_t)kHid * kInPad) &&
               grab(s, &s->W2b, (size_t)kHid * kHid) && grab(s, &s->W3b, (size_t)kHid * kHid) &&
-              grab(s, &s->W4b, (size_t)kOutPad * kHid) && grab(s, &s->W2Tb, (size_t)kHid * kHid) &&
-              grab(s, &s->W3Tb, (size_t)kHid * kHid) && grab(s, &s->W4Tb, (size_t)kHid * kOutPad) &&
+              grab(s, &s->W4b, (size_t)kOutPad * kHid) &&
               grab(s, &s->X0, B * kInPad) && grab(s, &s->H1, B * kHid) && grab(s, &s->H2, B * kHid) &&
               grab(s, &s->H3, B * kHid) && grab(s, &s->G4, B * kOutPad) && grab(s, &s->G3, B * kHid) &&
               grab(s, &s->G2, B * kHid) && grab(s, &s->G1, B * kHid) && grab(s, &s->GP1, B * kHid) &&
@@ -298,7 +292,8 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
         return sfail(SUPA_ERR_OOM, "supa_surrogate_create: out of device memory");
     }
     // tensor maps of the training pass: the input tile and its stores in
-    // 128-row boxes, the weights (W and W^T) in boxes of all their rows
+    // 128-row boxes, the weights in boxes of all their rows (forward) and of
+    // 64 x 64 (backward)
     int rc = 0;
     TrainMapSet &tm = s->tm;
     rc |= make_bf16_map(&tm.x0, s->X0, B, kInPad, 128);
@@ -306,9 +301,9 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
     rc |= make_bf16_map(&tm.w2, s->W2b, kHid, kHid, kHid);
     rc |= make_bf16_map(&tm.w3, s->W3b, kHid, kHid, kHid);
     rc |= make_bf16_map(&tm.w4, s->W4b, kOutPad, kHid, kOutPad);
-    rc |= make_bf16_map(&tm.w4t, s->W4Tb, kHid, kOutPad, kHid);
-    rc |= make_bf16_map(&tm.w3t, s->W3Tb, kHid, kHid, kHid);
-    rc |= make_bf16_map(&tm.w2t, s->W2Tb, kHid, kHid, kHid);
+    rc |= make_bf16_map(&tm.w4m, s->W4b, kOutPad, kHid, 64);
+    rc |= make_bf16_map(&tm.w3m, s->W3b, kHid, kHid, 64);
+    rc |= make_bf16_map(&tm.w2m, s->W2b, kHid, kHid, 64);
     rc |= make_bf16_map(&tm.h1, s->H1, B, kHid, 128);
     rc |= make_bf16_map(&tm.h2, s->H2, B, kHid, 128);
     rc |= make_bf16_map(&tm.h3, s->H3, B, kHid, 128);
@@ -321,9 +316,12 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
     const __nv_bfloat16 *gsrc[kWgradMax] = {s->G4, s->G3, s->G2, s->G1};
     const __nv_bfloat16 *hsrc[kWgradMax] = {s->H3, s->H2, s->H1, s->X0};
     const int gcols[kWgradMax] = {kOutPad, kHid, kHid, kHid}, hcols[kWgradMax] = {kHid, kHid, kHid, kInPad};
+    float *gout[kWgradMax] = {s->grad + Off::W4, s->grad + Off::W3, s->grad + Off::W2, s->grad + Off::W1};
+    const int orows[kWgradMax] = {kOutPad, kHid, kHid, kHid};
     for (int i = 0; i < kWgradMax; ++i) {
         rc |= make_bf16_map(&s->dG[i], gsrc[i], B, gcols[i], 64);
         rc |= make_bf16_map(&s->dH[i], hsrc[i], B, hcols[i], 64);
+        rc |= make_f32_store_map(&s->dO[i], gout[i], orows[i], hcols[i], hcols[i]);
     }
     if (rc != 0) {
         supa_surrogate_destroy(s);
@@ -389,13 +387,12 @@ int train_minibatch(supa_surrogate *s, const float *x, const float *y, int64_t n
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
     s->t += 1;
     const float c1 = 1.0f - std::pow(s->beta1, (float)s->t), c2 = 1.0f - std::pow(s->beta2, (float)s->t);
-    const WeightCopies wc{{Off::W1, Off::W2, Off::W3, Off::W4},
-                          {kHid, kHid, kHid, kOutPad},
-                          {kInPad, kHid, kHid, kHid},
-                          {s->W1b, s->W2b, s->W3b, s->W4b},
-                          {nullptr, s->W2Tb, s->W3Tb, s->W4Tb}};
+    const WeightCopies wc{{(int)Off::W1, (int)Off::W2, (int)Off::W3, (int)Off::W4},
+                          {kHid * kInPad, kHid * kHid, kHid * kHid, kOutPad * kHid},
+                          {s->W1b, s->W2b, s->W3b, s->W4b}};
     if (launch_pdl(adam_update, dim3((unsigned)((Off::total + 255) / 256)), dim3(256), 0, st, s->master, s->m, s->v,
-                   s->grad, (int)Off::total, lr, s->beta1, s->beta2, s->eps, c1, c2, wc) != cudaSuccess)
+                   s->grad, (int)Off::total, lr, s->beta1, s->beta2, s->eps, 1.0f / c1, 1.0f / std::sqrt(c2), wc) !=
+        cudaSuccess)
         return sfail(SUPA_ERR_CUDA, "train_step launch failed");
     s->grad_zero = true;
     return SUPA_OK;

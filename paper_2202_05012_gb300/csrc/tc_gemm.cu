@@ -25,7 +25,7 @@ constexpr uint32_t kWgA = 2 * kWgBox;          // 128 columns of G
 constexpr uint32_t kWgStage = kWgA + 4 * kWgBox;  // + up to 256 columns of H
 
 struct WgradMaps {
-    CUtensorMap g[kWgradMax], h[kWgradMax];
+    CUtensorMap g[kWgradMax], h[kWgradMax], o[kWgradMax];
 };
 struct WgradPlan {
     int splits[kWgradMax];      // K splits of each problem
@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     // cleared the gradients) are done from here on
     pdl_wait();
     pdl_trigger();
+    __syncwarp();  // lanes that ran a one-lane role rejoin: the block barrier is warp-aligned
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -149,19 +150,34 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             if (lane == 0 && nkb > 0) atomicOr(g.error, kErrTimeout);
             *abort_v = 1;
         } else {
-            const int row = mt * 128 + q * 32 + lane;
+            // The partial product leaves by TMA reductions: each warp stages its
+            // 32-row x 32-column blocks in the 128-byte-swizzled layout of the
+            // output map (16 KB a warp in the idle stage buffers) and one lane
+            // adds them to dW_p -- whole lines per request, where per-thread
+            // vector reductions sent one 16-byte request per row.
             const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-            float *out = out_base + (size_t)row * ld;
+            uint8_t *wbuf = base + (warp - 4) * 4 * 4096;
+            const int chunks = N / 64;
 #pragma unroll 1
-            for (int c0 = h * (N / 2); c0 < (h + 1) * (N / 2); c0 += 32) {
+            for (int ci = 0; ci < chunks; ++ci) {
+                const int c0 = h * (N / 2) + ci * 32;
                 float v[32];
                 tmem_ld32(lane_addr + c0, v);
+                uint8_t *blk = wbuf + ci * 4096;
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(out + c0 + 4 * j), "f"(v[4 * j]),
-                                 "f"(v[4 * j + 1]), "f"(v[4 * j + 2]), "f"(v[4 * j + 3])
-                                 : "memory");
+                for (int i = 0; i < 8; ++i)
+                    *reinterpret_cast<float4 *>(blk + lane * 128 + ((i ^ (lane & 7)) << 4)) =
+                        make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             }
+            fence_smem_to_async();
+            __syncwarp();
+            if (lane == 0) {
+                for (int ci = 0; ci < chunks; ++ci)
+                    tma_reduce_add_2d(&mp.o[p], wbuf + ci * 4096, h * (N / 2) + ci * 32, mt * 128 + q * 32);
+                bulk_commit();
+                bulk_wait_all();
+            }
+            __syncwarp();
         }
     }
 
@@ -169,6 +185,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     if (warp == 0 && lane == 0 && *abort_v)
         for (int i = max(0, issued - kWgStages); i < issued; ++i)
             mbar_wait(&full_bar[i % kWgStages], (i / kWgStages) & 1);
+    __syncwarp();  // lanes that ran a one-lane role rejoin: the block barrier is warp-aligned
     fence_before_sync();
     __syncthreads();
     if (warp == 1) {
@@ -181,8 +198,8 @@ constexpr size_t kWgSmem = (size_t)kWgStages * kWgStage + 1024;
 
 }  // namespace
 
-cudaError_t launch_weight_grads(const CUtensorMap *g_maps, const CUtensorMap *h_maps, const WgradArgs &a,
-                                cudaStream_t st) {
+cudaError_t launch_weight_grads(const CUtensorMap *g_maps, const CUtensorMap *h_maps, const CUtensorMap *out_maps,
+                                const WgradArgs &a, cudaStream_t st) {
     if (a.B < 64 || a.B % 64 != 0 || a.nprob < 1 || a.nprob > kWgradMax) return cudaErrorInvalidValue;
     const int kbt = a.B / 64;
     WgradMaps m;
@@ -213,6 +230,7 @@ cudaError_t launch_weight_grads(const CUtensorMap *g_maps, const CUtensorMap *h_
         items += (q.M / 128) * splits;
         m.g[i] = g_maps[i];
         m.h[i] = h_maps[i];
+        m.o[i] = out_maps[i];
     }
     pl.item0[a.nprob] = items;
     cudaError_t e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);

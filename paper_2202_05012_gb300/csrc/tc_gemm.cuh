@@ -18,9 +18,9 @@ namespace supa {
 // G_p [B][>= M_p] and H_p [B][N_p] row-major bf16 (the layout the training
 // pass writes), read through tensor maps with boxes of 64 columns x 64 rows
 // (make_bf16_map(..., 64)).  Each CTA takes one (problem, 128-row block of
-// dW_p, run of 64-row K-blocks) and adds its partial product to out_p with
-// float vector reductions; the runs are sized so that there is about one CTA
-// per SM.
+// dW_p, run of 64-row K-blocks) and adds its partial product to out_p with TMA
+// reductions through out_maps[p] (make_f32_store_map over out_p: 32 x 32
+// boxes); the runs are sized so that there is about one CTA per SM.
 constexpr int kWgradMax = 4;
 struct WgradProblem {
     int M;       // dW rows, a multiple of 128
@@ -34,8 +34,8 @@ struct WgradArgs {
     WgradProblem p[kWgradMax];
     int *error;  // device error word (|= 8: a pipeline wait expired)
 };
-cudaError_t launch_weight_grads(const CUtensorMap *g_maps, const CUtensorMap *h_maps, const WgradArgs &a,
-                                cudaStream_t st);
+cudaError_t launch_weight_grads(const CUtensorMap *g_maps, const CUtensorMap *h_maps, const CUtensorMap *out_maps,
+                                const WgradArgs &a, cudaStream_t st);
 // One bounded mbarrier wait on a barrier nothing completes; *status (device)
 // receives 1 when the wait gave up after limit_cycles, else 0.
 cudaError_t launch_wait_expiry_probe(long long limit_cycles, int *status, cudaStream_t st);
@@ -59,9 +59,10 @@ cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const C
 // per 128-row tile the forward, the loss gradient and the data-gradient chain
 // in one kernel.  The kernel gathers the minibatch rows itself; the packed
 // inputs leave through the x0 map ([B][64] bf16, 128-row boxes, columns 6..
-// zero: the B operand of dW1).  Weights through w1 ([256][64]), w2, w3
-// ([256][256]), w4 ([128][256], 128-row boxes), w4t ([256][128]), w3t, w2t
-// ([256][256]) -- 256-row boxes otherwise.
+// zero: the B operand of dW1).  Weights (bf16, row-major [out][in]) through
+// w1 ([256][64]), w2, w3 ([256][256]) in 256-row boxes and w4 ([128][256])
+// in 128-row boxes for the forward, and through w4m, w3m, w2m (the same W4,
+// W3, W2 in boxes of 64 x 64) for the backward.
 // The activations H1..H3 ([B][256]) and the gradients d out (G4, [B][128],
 // columns 90.. zero) and G3..G1 ([B][256]), all row-major bf16, leave through
 // the store maps h1..h3, g4, g3..g1 (boxes of 64 columns x 128 rows).
@@ -79,7 +80,7 @@ struct TrainPassArgs {
     int *error;                         // device error word (|= 8: a pipeline wait expired)
 };
 struct TrainMapSet {
-    CUtensorMap x0, w1, w2, w3, w4, w4t, w3t, w2t;  // loads
+    CUtensorMap x0, w1, w2, w3, w4, w4m, w3m, w2m;  // loads (x0: store)
     CUtensorMap h1, h2, h3, g4, g3, g2, g1;         // stores
 };
 cudaError_t launch_train_pass(const TrainMapSet &maps, const TrainPassArgs &a, cudaStream_t st);

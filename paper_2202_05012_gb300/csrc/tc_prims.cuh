@@ -65,6 +65,14 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void 
                  "r"(x), "r"(y), "r"(smem_u32(src))
                  : "memory");
 }
+// TMA reduction of one box from shared memory into global memory: the
+// tensor's elements add the box's (f32 add), tracked like a bulk store.
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                     (uint64_t)map),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 // The source of every committed bulk store of this thread has been read.
 __device__ __forceinline__ void bulk_wait_read_all() {

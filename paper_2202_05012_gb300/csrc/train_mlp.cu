@@ -28,8 +28,10 @@
 // columns, 128-byte swizzle; after the output layer it holds d out, K = 128,
 // columns 90.. zero), and a 4-stage ring of 32 KB weight K-blocks -- one
 // hidden layer's weights, loaded during the epilogue before the layer -- in
-// the order the MMAs use them: W1, W2 (4), W3 (4), W4 (4, 128 rows), W4^T
-// (2), W3^T (4), W2^T (4).  The loss reads the outputs straight from TMEM.
+// the order the MMAs use them: W1, W2 (4), W3 (4), W4 (4, 128 rows), then
+// for the backward W4 (2), W3 (4), W2 (4) again as MN-major B operands (the
+// transposes W^T without a transposed copy: 64 rows of W, the K block, in
+// four boxes of 64 columns).  The loss reads the outputs straight from TMEM.
 // Warps: 0 TMA producer, 1 TMEM owner and MMA issuer, 2 TMA stores of the
 // operand tiles, 3 gathers the minibatch rows of the inputs into the input
 // tile, 4-19 epilogue (warp w reads TMEM lanes 32 (w % 4).. and columns
@@ -75,7 +77,7 @@ constexpr int kHandOff = 2;  // K-blocks per hand-off of an operand to the MMAs 
 
 // The weight K-block loads of one tile, in MMA order.
 struct LoadPlan {
-    int map;     // 0 w1, 1 w2, 2 w3, 3 w4, 4 w4t, 5 w3t, 6 w2t
+    int map;     // 0 w1, 1 w2, 2 w3, 3 w4 (K-major B operands), 4 w4, 5 w3, 6 w2 (MN-major, backward)
     int kb;      // column block
     uint32_t bytes;
 };
@@ -125,8 +127,28 @@ __global__ void __launch_bounds__(kTThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     // the input tile's columns 8..63 stay zero (the gather writes columns 0..7)
-    for (uint32_t i = threadIdx.x; i < kXBytes / 16; i += blockDim.x)
-        reinterpret_cast<uint4 *>(base + oX)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = threadIdx.x; i < kTRows * 7; i += blockDim.x)
+        *reinterpret_cast<uint4 *>(base + oX + sw128_offset(i / 7, 1 + i % 7)) = make_uint4(0u, 0u, 0u, 0u);
+    // the rows of x of tile t packed to bf16 into columns 0..7 of the input
+    // tile (x is not written by the kernels before this one: the first tile is
+    // gathered before waiting for them)
+    auto gather_tile = [&](int t) {
+        const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
+        float v[4][6];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t src =
+                (int64_t)((g.perm_a * (uint64_t)(g.i0 + m0 + lane + 32 * k) + g.perm_c) % (uint64_t)g.n);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) v[k][j] = __ldg(g.x + src * 6 + j);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            *reinterpret_cast<uint4 *>(base + oX + sw128_offset(lane + 32 * k, 0)) =
+                make_uint4(pack_bf16(v[k][0], v[k][1]), pack_bf16(v[k][2], v[k][3]), pack_bf16(v[k][4], v[k][5]), 0u);
+        fence_smem_to_async();
+    };
+    if (warp == 3) gather_tile(0);
     fence_smem_to_async();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
@@ -141,6 +163,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
     pdl_trigger();
     for (int i = threadIdx.x; i < 3 * 256 + 128; i += blockDim.x)
         sbias[i] = i < 256 ? g.b1[i] : i < 512 ? g.b2[i - 256] : i < 768 ? g.b3[i - 512] : g.b4[i - 768];
+    __syncwarp();  // lanes that ran a one-lane role rejoin: the block barrier is warp-aligned
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -169,15 +192,17 @@ __global__ void __launch_bounds__(kTThreads, 1)
                         break;
                     }
                     const LoadPlan pl = plan(i);
-                    const CUtensorMap *m = pl.map == 0   ? &mp.w1
-                                           : pl.map == 1 ? &mp.w2
-                                           : pl.map == 2 ? &mp.w3
-                                           : pl.map == 3 ? &mp.w4
-                                           : pl.map == 4 ? &mp.w4t
-                                           : pl.map == 5 ? &mp.w3t
-                                                         : &mp.w2t;
                     mbar_expect_tx(&w_full[s], pl.bytes);
-                    tma_load_2d(base + oS + s * kStageBytes, m, pl.kb * 64, 0, &w_full[s]);
+                    if (pl.map < 4) {
+                        // forward: 64 columns (K) of all rows (N) of W
+                        const CUtensorMap *m = pl.map == 0 ? &mp.w1 : pl.map == 1 ? &mp.w2 : pl.map == 2 ? &mp.w3 : &mp.w4;
+                        tma_load_2d(base + oS + s * kStageBytes, m, pl.kb * 64, 0, &w_full[s]);
+                    } else {
+                        // backward: 64 rows (K) of W, all 256 columns (N) in four boxes
+                        const CUtensorMap *m = pl.map == 4 ? &mp.w4m : pl.map == 5 ? &mp.w3m : &mp.w2m;
+                        for (int j = 0; j < 4; ++j)
+                            tma_load_2d(base + oS + s * kStageBytes + j * 8192, m, j * 64, pl.kb * 64, &w_full[s]);
+                    }
                     issued = c + 1;
                 }
             }
@@ -190,6 +215,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
         if (lane == 0) {
             // ---- MMA issuer ----
             constexpr uint32_t id256 = idesc_bf16(kTRows, 256), id128 = idesc_bf16(kTRows, 128);
+            constexpr uint32_t id256m = idesc_bf16(kTRows, 256) | (1u << 16);  // B MN-major
             const uint32_t sX = smem_u32(base + oX), sA = smem_u32(base + oA), sS = smem_u32(base + oS);
             bool ok = true;
             uint32_t m = 0;  // MMA layers issued: layer m accumulates in TMEM columns 256 (m % 2)..
@@ -198,7 +224,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
             // stages; with `wait_op`, K-block kb waits until the epilogue of the previous
             // layer has written it (which also means that epilogue is past reading the
             // accumulator this layer overwrites)
-            auto layer = [&](uint32_t a_base, int nkb, uint32_t idesc, int k_steps_first, bool wait_op) -> bool {
+            auto layer = [&](uint32_t a_base, int nkb, uint32_t idesc, int k_steps_first, bool wait_op,
+                             bool b_mn = false) -> bool {
                 const uint32_t acc = tmem + (m & 1u) * 256u;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (wait_op && (*abort_v || !mbar_wait(&a_ready[kb], (m - 1) & 1))) return false;
@@ -206,9 +233,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     if (*abort_v || !mbar_wait(&w_full[s], (c / kRing) & 1)) return false;
                     fence_after_sync();
                     const int ks = kb == 0 ? k_steps_first : 4;
+                    const uint32_t sb = sS + s * kStageBytes;
                     for (int k = 0; k < ks; ++k)
-                        mma_bf16(acc, sw128_desc(a_base + kb * kABlk + k * 32), sw128_desc(sS + s * kStageBytes + k * 32),
-                                 idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        mma_bf16(acc, sw128_desc(a_base + kb * kABlk + k * 32),
+                                 b_mn ? sw128_mn_desc(sb + k * 2048, 8192) : sw128_desc(sb + k * 32), idesc,
+                                 (kb > 0 || k > 0) ? 1u : 0u);
                     mma_commit(&w_empty[s]);
                     ++c;
                 }
@@ -228,9 +257,9 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 ok = layer(sA, 4, id256, 4, true)      // layer 2
                      && layer(sA, 4, id256, 4, true)   // layer 3
                      && layer(sA, 4, id128, 4, true)   // layer 4 (128 output columns)
-                     && layer(sA, 2, id256, 4, true)   // d out W4: K = 128
-                     && layer(sA, 4, id256, 4, true)   // d H3 W3
-                     && layer(sA, 4, id256, 4, true);  // d H2 W2
+                     && layer(sA, 2, id256m, 4, true, true)   // d out W4: K = 128
+                     && layer(sA, 4, id256m, 4, true, true)   // d H3 W3
+                     && layer(sA, 4, id256m, 4, true, true);  // d H2 W2
             }
             if (!ok) fail();
             // every MMA issued by this thread completes before tensor memory is freed
@@ -276,29 +305,18 @@ __global__ void __launch_bounds__(kTThreads, 1)
             bulk_wait_all();
         }
     } else if (warp == 3) {
-        // ---- gather: the tile's rows of x, packed to bf16 in the input tile ----
+        // ---- gather: each tile's rows of x into the input tile (the first one is there) ----
         bool ok = true;
         for (int t = 0; t < my_tiles && ok; ++t) {
-            const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows;
-            // the previous tile's input was read by layer 1 and by its store
-            if (t > 0 && !__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&x_empty, (t - 1) & 1) &&
-                                                      mbar_wait(&x_read, (t - 1) & 1))) {
-                ok = false;
-                break;
+            if (t > 0) {
+                // the previous tile's input was read by layer 1 and by its store
+                if (!__all_sync(0xFFFFFFFFu, !*abort_v && mbar_wait(&x_empty, (t - 1) & 1) &&
+                                                 mbar_wait(&x_read, (t - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                gather_tile(t);
             }
-            float v[4][6];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t src = (int64_t)((g.perm_a * (uint64_t)(g.i0 + m0 + lane + 32 * k) + g.perm_c) %
-                                              (uint64_t)g.n);
-#pragma unroll
-                for (int j = 0; j < 6; ++j) v[k][j] = __ldg(g.x + src * 6 + j);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                *reinterpret_cast<uint4 *>(base + oX + sw128_offset(lane + 32 * k, 0)) =
-                    make_uint4(pack_bf16(v[k][0], v[k][1]), pack_bf16(v[k][2], v[k][3]), pack_bf16(v[k][4], v[k][5]), 0u);
-            fence_smem_to_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&x_full);
         }
@@ -506,6 +524,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
         if (!ok) fail();
     }
 
+    __syncwarp();  // lanes that ran a one-lane role rejoin: the block barrier is warp-aligned
     fence_before_sync();
     __syncthreads();
     if (warp == 1) {
