@@ -44,31 +44,21 @@ returns them):
      and the MEAN fractions are taken without a draw.  Both: scaled by
      E / sum d when the sum exceeds E;
   5. one hit per layer with d_j > 0 at the layer's mid depth, displaced
-     from the particle's straight-line position by max(0, rho_j) D, one D
-     per particle (all its layers: the sub-shower drifts one way), from
-     words (w0, w1) of the Philox block with counter (shower id, slice |
-     2 << 16, lineage lo, lineage hi): q = lateral_quantile(u), u = (w0 >>
-     8) 2^-24, the quantile function of the lateral law LATERAL_Q, and phi =
-     2 pi (w1 >> 8) 2^-24, and
-       D = (q / M(u_z)) (cos(phi) e_par / u_z + sin(phi) e_perp),
-     e_par the unit vector of the particle's direction projected on the
-     layer plane ((1, 0) at normal incidence), e_perp = e_par turned by 90
-     degrees, M(c) = (2 / pi) E(1 - c^2) / c the mean radius of the ellipse
-     with semi-axes 1 / c and 1 (E the complete elliptic integral of the
-     second kind).  A spread perpendicular to an inclined sub-shower's axis
-     lands on the layer plane stretched by 1 / u_z along the projected
-     direction (the plain sub-showers' in-plane spread along / across it:
-     1.09, 1.26, 1.47 at 20, 35, 45 degrees, against 1 / cos = 1.06, 1.22,
-     1.41); dividing by M keeps each layer's mean displacement at rho_j.
-     The law is measured with this oracle (tests/golden/lateral_law.py):
-     the energy-weighted distribution of plain sub-showers' hit distances
-     from their axis over the mean distance of sub-showers alike in energy,
-     start slice and layer offset -- the quantity rho_j estimates -- at
-     normal incidence, with mean 1.  It has an atom at 0 (a sub-shower's
-     first deposits lie on its axis), a core narrower and a tail longer
-     than a 2-D Gaussian's (E q^2 = 1.38 against 4 / pi = 1.27); a Gaussian
-     of either moment left the shower's lateral profile 2-3 % off in its
-     rings.
+     from the particle's straight-line position by max(0, rho_j) q
+     (cos phi, sin phi), one (q, phi) per particle (all its layers: the
+     sub-shower drifts one way), from words (w0, w1) of the Philox block
+     with counter (shower id, slice | 2 << 16, lineage lo, lineage hi):
+     phi = 2 pi (w1 >> 8) 2^-24 and q = lateral_quantile(u), u = (w0 >> 8)
+     2^-24, the quantile function of the lateral law LATERAL_Q.  The law is
+     measured with this oracle (tests/golden/lateral_law.py): the
+     energy-weighted distribution of plain sub-showers' hit distances from
+     their axis divided by the mean distance of sub-showers alike in energy,
+     start slice and layer offset -- the quantity rho_j estimates -- with
+     mean 1, so each layer's mean displacement is rho_j.  It has a spike at
+     0 (a sub-shower's first deposits lie on its axis), a core narrower and
+     a tail longer than a 2-D Gaussian's (E q^2 = 1.38 against 4 / pi =
+     1.27); a Gaussian of either moment left the shower's lateral profile
+     2-3 % off in its rings.
 
 training_targets() writes out the network's targets from a plain
 simulation of sub-showers: deposit fractions y_j of layers start + j and
@@ -126,24 +116,6 @@ def lateral_offset(shower_id: int, k: int, lineage: int, seed: int) -> np.ndarra
     q = lateral_quantile((int(w[0]) >> 8) * 2.0 ** -24)
     phi = 2 * math.pi * (int(w[1]) >> 8) * 2.0 ** -24
     return np.array([q * math.cos(phi), q * math.sin(phi)])
-
-
-def ellipse_mean_radius(c: float) -> float:
-    """M(c) = (2 / pi) E(1 - c^2) / c, the mean over the angle of the radius
-    of the ellipse with semi-axes 1 / c and 1 (0 < c <= 1); M(1) = 1."""
-    from scipy.special import ellipe
-    return 2.0 / math.pi * float(ellipe(1.0 - c * c)) / c
-
-
-def lateral_displacement(off, ux: float, uy: float, uz: float) -> np.ndarray:
-    """D of step 5 (per unit rho_j) from lateral_offset's (q cos phi,
-    q sin phi) and the particle's direction."""
-    s = math.hypot(ux, uy)
-    ex, ey = (ux / s, uy / s) if s > 0 else (1.0, 0.0)
-    a = off[0] / uz  # along the projected direction, stretched by 1 / u_z
-    b = off[1]
-    m = ellipse_mean_radius(uz)
-    return np.array([(a * ex - b * ey) / m, (a * ey + b * ex) / m])
 
 
 def training_targets(geom, prims, res) -> np.ndarray:
@@ -288,9 +260,7 @@ def deposits(div: dict, params, geom, e_s: float, seed: int, shower_id_base: int
         if tot > E:
             d[i] *= E / tot
         zk = div["k"][i] * geom.dz
-        mo = lateral_displacement(
-            lateral_offset(shower_id_base + int(div["shower"][i]), int(div["k"][i]), int(div["lineage"][i]), seed),
-            div["ux"][i], div["uy"][i], div["uz"][i])
+        mo = lateral_offset(shower_id_base + int(div["shower"][i]), int(div["k"][i]), int(div["lineage"][i]), seed)
         for j in range(30):
             if d[i, j] > 0:
                 zm = zmid[l0 + j]
