@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="supa", choices=["supa", "reference"])
     ap.add_argument("--workload", default="plain30",
-                    choices=["plain10", "plain30", "mixed4", "plain50", "surrogate", "hybrid", "forward"])
+                    choices=["plain10", "plain30", "mixed4", "plain50", "surrogate", "hybrid", "forward", "train"])
     ap.add_argument("--e-s-sweep", type=float, nargs="+", default=[0.2, 0.5, 1.0, 2.0, 5.0])
     ap.add_argument("--showers", type=int, default=0, help="override the batch size")
     ap.add_argument("--voxel-chunk", type=int, default=32768)
@@ -1217,6 +1217,33 @@ def run_forward(args):
                       "kernel": "sur_mlp_kernel"}), flush=True)
 
 
+def run_train(args):
+    """The surrogate's training alone: a generic training set of
+    --train-samples sub-showers (E log-uniform [e_min, E_s], plain method,
+    E_s = --e-s), then --epochs Adam epochs in --batch-row minibatches, each
+    step the training pass, the grouped weight gradients and the Adam update;
+    W warm-up epochs first (not timed).  TFLOP/s of algorithmic flops
+    (forward + backward, 3 x 311,296 per sample) by CUDA events."""
+    import torch
+
+    from paper_2202_05012_gb300 import surrogate_train as T
+    torch.cuda.set_device(0)
+    data = T.training_set(args.train_samples, args.e_s, 5)
+    if args.warmup:
+        net, _ = T.train(data, epochs=args.warmup, batch=args.batch, lr=args.lr, lr_final=args.lr_final)
+        from paper_2202_05012_gb300 import supa as S
+        S.supa_surrogate_destroy(net)
+    net, log = T.train(data, epochs=args.epochs, batch=args.batch, lr=args.lr, lr_final=args.lr_final)
+    from paper_2202_05012_gb300 import supa as S
+    S.supa_surrogate_destroy(net)
+    steps = log["steps_per_epoch"] * log["epochs"]
+    print(json.dumps({"metric": "surrogate training TFLOP/s (algorithmic)", "value": log["tflops"], "unit": "TFLOP/s",
+                      "samples": args.train_samples, "epochs": args.epochs, "batch": args.batch,
+                      "us_per_step": log["seconds"] / steps * 1e6, "samples_per_s": log["samples_per_s"],
+                      "seconds": log["seconds"], "loss_last_epoch": log["loss_per_epoch"][-1],
+                      "kernels": ["train_mlp_kernel", "wgrad_kernel", "adam_update"]}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1229,6 +1256,8 @@ def main():
         run_hybrid(args)
     elif args.workload == "forward":
         run_forward(args)
+    elif args.workload == "train":
+        run_train(args)
     else:
         run_supa(args)
 
