@@ -397,6 +397,17 @@ int supa_surrogate_gradients(supa_surrogate *s, const float *x_dev, const float 
  * (device FP64) when it is not NULL. */
 int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float *y_dev, float lr,
                               double *loss_acc_dev, void *stream);
+/* Iterate averaging (Polyak-Ruppert) of the training: mode
+ * SUPA_AVERAGE_START resets the average and from the next Adam step on adds
+ * every step's FP32 parameters to it with equal weight; SUPA_AVERAGE_STOP
+ * stops adding; SUPA_AVERAGE_APPLY replaces the parameters (and the BF16
+ * copies the kernels read) by the average of the steps added so far (no
+ * change if none was).  The Adam moments are kept.  Asynchronous on `stream`;
+ * SUPA_ERR_INVALID_ARG for another mode. */
+#define SUPA_AVERAGE_STOP 0
+#define SUPA_AVERAGE_START 1
+#define SUPA_AVERAGE_APPLY 2
+int supa_surrogate_average(supa_surrogate *s, int32_t mode, void *stream);
 /* One epoch over a training set of n samples (x_dev [n][6], y_dev [n][60]):
  * floor(n / batch) Adam steps on minibatches gathered in the order of the
  * permutation i -> (a i + c) mod n that `seed` picks.  Asynchronous; adds

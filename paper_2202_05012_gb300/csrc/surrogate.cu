@@ -67,8 +67,10 @@ struct WeightCopies {
 
 // inv_c1 = 1 / c1, inv_sqrt_c2 = 1 / sqrt(c2): the step is
 // lr (m / c1) / (sqrt(v / c2) + eps) = lr m inv_c1 / (sqrt(v) inv_sqrt_c2 + eps).
+// With avg set, the updated parameters are also added to the running
+// average avg with weight w (1 / (steps averaged + 1)).
 __global__ void adam_update(float *p, float *m, float *v, float *g, int n, float lr, float b1, float b2,
-                            float eps, float inv_c1, float inv_sqrt_c2, const WeightCopies wc) {
+                            float eps, float inv_c1, float inv_sqrt_c2, const WeightCopies wc, float *avg, float w) {
     pdl_wait();  // the weight gradients are complete
     pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -81,6 +83,7 @@ __global__ void adam_update(float *p, float *m, float *v, float *g, int n, float
     const float pi = p[i] - __fdividef(lr * mi * inv_c1, fmaf(sqrtf(vi), inv_sqrt_c2, eps));
     p[i] = pi;
     g[i] = 0.0f;  // ready for the next minibatch's gradients
+    if (avg) avg[i] = fmaf(w, pi - avg[i], avg[i]);
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
         const int j = i - wc.off[w];
@@ -100,6 +103,9 @@ struct supa_surrogate {
     int B = 0;
     int t = 0;  // Adam step count
     bool grad_zero = false;  // the gradient block holds zeros (the Adam update clears it)
+    bool avg_on = false;     // iterate averaging: Adam steps are added to avg
+    int64_t avg_n = 0;       // steps in the average
+    float *avg = nullptr;    // running average of the master parameters
     float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
     float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     __nv_bfloat16 *W1b, *W2b, *W3b, *W4b;
@@ -286,6 +292,7 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
               grab(s, &s->H3, B * kHid) && grab(s, &s->G4, B * kOutPad) && grab(s, &s->G3, B * kHid) &&
               grab(s, &s->G2, B * kHid) && grab(s, &s->G1, B * kHid) && grab(s, &s->GP1, B * kHid) &&
               grab(s, &s->GP2, B * kHid) && grab(s, &s->GP3, B * kHid) && grab(s, &s->loss_tmp, 1) &&
+              grab(s, &s->avg, Off::total) &&
               grab(s, &s->error, 1);
     if (!ok) {
         supa_surrogate_destroy(s);
@@ -391,10 +398,12 @@ int train_minibatch(supa_surrogate *s, const float *x, const float *y, int64_t n
                           {kHid * kInPad, kHid * kHid, kHid * kHid, kOutPad * kHid},
                           {s->W1b, s->W2b, s->W3b, s->W4b}};
     if (launch_pdl(adam_update, dim3((unsigned)((Off::total + 255) / 256)), dim3(256), 0, st, s->master, s->m, s->v,
-                   s->grad, (int)Off::total, lr, s->beta1, s->beta2, s->eps, 1.0f / c1, 1.0f / std::sqrt(c2), wc) !=
+                   s->grad, (int)Off::total, lr, s->beta1, s->beta2, s->eps, 1.0f / c1, 1.0f / std::sqrt(c2), wc,
+                   s->avg_on ? s->avg : (float *)nullptr, s->avg_on ? 1.0f / (float)(s->avg_n + 1) : 0.0f) !=
         cudaSuccess)
         return sfail(SUPA_ERR_CUDA, "train_step launch failed");
     s->grad_zero = true;
+    if (s->avg_on) ++s->avg_n;
     return SUPA_OK;
 }
 }  // namespace
@@ -408,6 +417,29 @@ int supa_surrogate_train_step(supa_surrogate *s, const float *x_dev, const float
         return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_step: x must be 4-byte and y 8-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     return train_minibatch(s, x_dev, y_dev, s->B, 1, 0, 0, lr, loss_acc_dev ? loss_acc_dev : s->loss_tmp, st);
+}
+
+int supa_surrogate_average(supa_surrogate *s, int32_t mode, void *stream) {
+    if (!s) return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_average: null surrogate");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode == SUPA_AVERAGE_START) {
+        // zeroed, so that the first step added (weight 1) gives exactly its parameters
+        if (cudaMemsetAsync(s->avg, 0, Off::total * sizeof(float), st) != cudaSuccess)
+            return sfail(SUPA_ERR_CUDA, "supa_surrogate_average: memset failed");
+        s->avg_on = true;
+        s->avg_n = 0;
+    } else if (mode == SUPA_AVERAGE_STOP) {
+        s->avg_on = false;
+    } else if (mode == SUPA_AVERAGE_APPLY) {
+        if (s->avg_n > 0 &&
+            (cudaMemcpyAsync(s->master, s->avg, Off::total * sizeof(float), cudaMemcpyDeviceToDevice, st) !=
+                 cudaSuccess ||
+             weight_copies(s, st) != SUPA_OK))
+            return sfail(SUPA_ERR_CUDA, "supa_surrogate_average: apply failed");
+    } else {
+        return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_average: mode must be 0, 1 or 2");
+    }
+    return SUPA_OK;
 }
 
 int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,

@@ -31,7 +31,7 @@ EXPORTED = (
     "supa_surrogate_forward", "supa_surrogate_check", "supa_surrogate_train_epoch", "supa_batch_set_surrogate",
     "supa_build_training_set", "supa_profiles", "supa_shower_offsets_noalloc", "supa_export_diverted",
     "supa_shower_shapes", "supa_layer_images_cells", "supa_voxelize_layers", "supa_voxelize_fetch",
-    "supa_check_wait_expiry", "supa_export_surrogate", "supa_batch_warp_times",
+    "supa_check_wait_expiry", "supa_export_surrogate", "supa_batch_warp_times", "supa_surrogate_average",
 )
 
 
@@ -122,6 +122,7 @@ def lib(build_if_missing: bool = True):
         L.supa_surrogate_forward.argtypes = [_VP, _VP, _I64, _VP, _I64, _VP]
         L.supa_surrogate_check.argtypes = [_VP]
         L.supa_surrogate_train_epoch.argtypes = [_VP, _VP, _VP, _I64, ctypes.c_uint64, ctypes.c_float, _VP, _VP]
+        L.supa_surrogate_average.argtypes = [_VP, ctypes.c_int32, _VP]
         L.supa_batch_set_surrogate.argtypes = [_VP, _VP, ctypes.c_float, _I64, ctypes.c_int32]
         L.supa_build_training_set.argtypes = [_VP, ctypes.c_float, _VP, _VP, _VP]
         L.supa_profiles.argtypes = [_VP, _I64, _I64, ctypes.c_int32, ctypes.c_float, _VP, _VP, _VP]
@@ -349,6 +350,16 @@ def supa_surrogate_forward(s: int, x_dev, n: int, out_dev, ld_out=None, stream=N
 
 def supa_surrogate_check(s: int):
     _check(lib().supa_surrogate_check(s), "supa_surrogate_check")
+
+
+SUPA_AVERAGE_STOP, SUPA_AVERAGE_START, SUPA_AVERAGE_APPLY = 0, 1, 2
+
+
+def supa_surrogate_average(s: int, mode: int, stream=None):
+    """Iterate averaging of the training (SUPA_AVERAGE_*): start adding the
+    Adam steps that follow to a uniform average, stop, or replace the
+    parameters by the average."""
+    _check(lib().supa_surrogate_average(s, int(mode), _stream(stream)), "supa_surrogate_average")
 
 
 def supa_surrogate_train_epoch(s: int, x_dev, y_dev, n: int, seed: int, lr: float, loss_acc_dev=None, stream=None):

@@ -109,10 +109,12 @@ def training_set_matched(geom, prims, e_s: float, n_max: int, seed: int, device=
 
 
 def train(data: dict, epochs: int = 20, batch: int = 16384, lr: float = 1e-3, seed: int = 0, init_seed: int = 1,
-          lr_final: float | None = None):
+          lr_final: float | None = None, average_from: int | None = None):
     """Adam epochs on the GPU; returns (network handle, log).  With lr_final
     the learning rate decays geometrically from lr to lr_final over the
-    epochs."""
+    epochs; with average_from the network's final parameters are the average
+    of the parameters after every Adam step from that epoch on (iterate
+    averaging)."""
     import torch
     net = S.supa_surrogate_create(batch, S.pack_mlp_params(inputs.mlp_init(init_seed)))
     n = data["n"]
@@ -125,16 +127,22 @@ def train(data: dict, epochs: int = 20, batch: int = 16384, lr: float = 1e-3, se
     for ep in range(epochs):
         acc.zero_()
         lr_ep = lr if lr_final is None or epochs < 2 else lr * (lr_final / lr) ** (ep / (epochs - 1))
+        if average_from is not None and ep == average_from:
+            S.supa_surrogate_average(net, S.SUPA_AVERAGE_START)
         S.supa_surrogate_train_epoch(net, data["x"], data["y"], n, seed * 1000 + ep, lr_ep, acc)
         losses.append(acc)  # read after the loop (no synchronisation per epoch)
         acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+    if average_from is not None and average_from < epochs:
+        S.supa_surrogate_average(net, S.SUPA_AVERAGE_APPLY)
+        S.supa_surrogate_average(net, S.SUPA_AVERAGE_STOP)
     ev1.record()
     torch.cuda.synchronize()
     S.supa_surrogate_check(net)
     ms = ev0.elapsed_time(ev1)
     per_epoch = [float(l.item()) / steps for l in losses]
     flops = TRAIN_FLOPS * steps * batch * epochs
-    return net, dict(epochs=epochs, batch=batch, lr=lr, lr_final=lr_final, steps_per_epoch=steps, seconds=ms / 1000.0,
+    return net, dict(epochs=epochs, batch=batch, lr=lr, lr_final=lr_final, average_from=average_from,
+                     steps_per_epoch=steps, seconds=ms / 1000.0,
                      seconds_per_epoch=ms / 1000.0 / epochs, loss_per_epoch=per_epoch,
                      tflops=flops / (ms / 1000.0) / 1e12, samples_per_s=steps * batch * epochs / (ms / 1000.0))
 

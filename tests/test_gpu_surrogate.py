@@ -114,3 +114,48 @@ def test_adam_trajectory_follows_oracle():
             assert np.linalg.norm(W - rW) / np.linalg.norm(rW) < 2e-2
     finally:
         S.supa_surrogate_destroy(s)
+
+
+def test_iterate_average_is_the_mean_of_the_steps_parameters():
+    """supa_surrogate_average: after START, every Adam step's parameters
+    enter a uniform average; APPLY makes the network that average (checked
+    against the mean of the parameters read after each step) and the
+    inference kernel then uses it."""
+    import torch
+    B = 256
+    vec, _ = _f32_params(11)
+    X, Y = _batch(B, 4)
+    s = S.supa_surrogate_create(B, vec)
+    try:
+        xd = torch.from_numpy(X.astype(np.float32)).cuda()
+        yd = torch.from_numpy(Y.astype(np.float32)).cuda()
+        for _ in range(2):
+            S.supa_surrogate_train_step(s, xd, yd, 1e-3)
+        S.supa_surrogate_average(s, S.SUPA_AVERAGE_START)
+        seen = []
+        for _ in range(5):
+            S.supa_surrogate_train_step(s, xd, yd, 1e-3)
+            seen.append(S.supa_surrogate_get_params(s).astype(np.float64))
+        S.supa_surrogate_average(s, S.SUPA_AVERAGE_STOP)
+        S.supa_surrogate_train_step(s, xd, yd, 1e-3)  # not averaged
+        last = S.supa_surrogate_get_params(s)
+        S.supa_surrogate_average(s, S.SUPA_AVERAGE_APPLY)
+        got = S.supa_surrogate_get_params(s).astype(np.float64)
+        ref = np.mean(seen, axis=0)
+        np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-7)
+        assert np.abs(got - last).max() > 1e-6  # the steps did move the parameters
+        # the BF16 copies follow: the forward equals a network built from the average
+        t = S.supa_surrogate_create(B, got.astype(np.float32))
+        try:
+            o1 = torch.empty((B, 96), dtype=torch.float32, device="cuda")
+            o2 = torch.empty((B, 96), dtype=torch.float32, device="cuda")
+            S.supa_surrogate_forward(s, xd, B, o1)
+            S.supa_surrogate_forward(t, xd, B, o2)
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(o1.cpu().numpy()[:, :90], o2.cpu().numpy()[:, :90], rtol=0, atol=1e-6)
+        finally:
+            S.supa_surrogate_destroy(t)
+        with pytest.raises(S.SupaError):
+            S.supa_surrogate_average(s, 7)
+    finally:
+        S.supa_surrogate_destroy(s)
