@@ -159,3 +159,38 @@ def test_iterate_average_is_the_mean_of_the_steps_parameters():
             S.supa_surrogate_average(s, 7)
     finally:
         S.supa_surrogate_destroy(s)
+
+
+def test_gradients_with_several_tiles_per_cta():
+    """A minibatch of 40,960 rows: 320 row tiles, more than the GPU has SMs,
+    so CTAs of the training pass take two or three tiles one after another
+    (input tile, operand buffers, barriers and TMEM accumulators reused) and
+    the weight gradients contract over 640 K-blocks.  Same check as for 1,024
+    rows against the FP64 oracle."""
+    import torch
+    B = 40_960
+    vec, params = _f32_params(9)
+    X, Y = _batch(B, 6)
+    s = S.supa_surrogate_create(B, vec)
+    try:
+        xd = torch.from_numpy(X.astype(np.float32)).cuda()
+        yd = torch.from_numpy(Y.astype(np.float32)).cuda()
+        g, loss = S.supa_surrogate_gradients(s, xd, yd)
+        ref_loss, ref = mlp.loss_and_grads(params, X, Y)
+        assert abs(loss - ref_loss) <= 1e-2 * abs(ref_loss) + 1e-4
+        gg = S.unpack_mlp_params(g.astype(np.float64))
+        for i, ((gW, gb), (rW, rb)) in enumerate(zip(gg, ref)):
+            for a, r, name in ((gW, rW, f"W{i + 1}"), (gb, rb, f"b{i + 1}")):
+                rel = np.linalg.norm(a - r) / np.linalg.norm(r)
+                cos = np.dot(a.ravel(), r.ravel()) / (np.linalg.norm(a) * np.linalg.norm(r))
+                assert rel < 2e-2 and cos > 0.999, (name, rel, cos)
+        # the same rows in another order give the same gradients (sums over rows)
+        perm = np.random.default_rng(1).permutation(B)
+        g2, loss2 = S.supa_surrogate_gradients(s, torch.from_numpy(X[perm].astype(np.float32)).cuda(),
+                                               torch.from_numpy(Y[perm].astype(np.float32)).cuda())
+        for (a1, b1), (a2, b2) in zip(gg, S.unpack_mlp_params(g2.astype(np.float64))):
+            for u, v in ((a1, a2), (b1, b2)):
+                assert np.linalg.norm(u - v) <= 1e-4 * np.linalg.norm(u)
+        assert abs(loss2 - loss) <= 1e-5 * abs(loss)
+    finally:
+        S.supa_surrogate_destroy(s)
