@@ -421,13 +421,15 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     gd[i] = gd[8 + i] = gr[i] = 0.0f;
                     if (i < nj) {
                         const int j = j0 + i;
-                        const float mu = expf(om[i] + sbias[768 + j] - kMuShift);
-                        const float es = expf(os[i] + sbias[768 + kLayersOut + j]);
+                        // hardware exp2 / log2 based exp and log: a relative error of a few
+                        // ulp, far below the BF16 rounding of the gradient
+                        const float mu = __expf(om[i] + sbias[768 + j] - kMuShift);
+                        const float es = __expf(os[i] + sbias[768 + kLayersOut + j]);
                         const float dr = orh[i] + sbias[768 + 2 * kLayersOut + j] - yr[i];
                         const float res = yv[i] - mu;
                         const float vv = es + kVarFloor;
-                        const float iv = 1.0f / vv;
-                        l += 0.5f * (res * res * iv + logf(vv) + yv[i] * dr * dr);
+                        const float iv = __frcp_rn(vv);
+                        l += 0.5f * (res * res * iv + __logf(vv) + yv[i] * dr * dr);
                         gd[i] = -res * iv * mu * inv;
                         gd[8 + i] = 0.5f * es * iv * (1.0f - res * res * iv) * inv;
                         gr[i] = yv[i] * dr * inv;
