@@ -2,10 +2,12 @@
 30-layer workload (E U[1,100] GeV, 0-30 deg) at E_s = 2 GeV: the hybrid path steps a small fraction of the
 particles the plain path steps, and its shower profiles stay close to the
 plain ones in both modes: every layer holding >= 0.5 % of the energy within
-2 %, and within 3 % the largest deviation over groups of consecutive layers,
-or of rings around the shower axis, holding >= 2 % of the energy each (every
-layer and ring included) -- which an untrained network of the same shape
-does not achieve."""
+2 %, and the largest deviation over groups of consecutive layers (within
+3 %), or of rings around the shower axis (within 2.5 %), holding >= 2 % of
+the energy each (every layer and ring included) -- which an untrained
+network of the same shape does not achieve.  (Four trainings gave lateral
+errors of 1.55-2.13 % and longitudinal errors of 0.67-1.55 % on 100,000
+showers.)"""
 import numpy as np
 import pytest
 
@@ -16,23 +18,24 @@ from paper_2202_05012_gb300 import surrogate_train as T
 pytestmark = pytest.mark.gpu
 
 E_S = 2.0
-N = 20_000
+N = 20_000          # showers of the distribution comparison
+N_PROFILE = 100_000  # showers of the profile comparison (its sampling noise about 0.5 % at 20,000)
 BINS, R_MAX = T.PROFILE_BINS, T.PROFILE_RMAX
 
 
-def _run(gh, d, mean_e, net, mode=S.SUPA_SURROGATE_MEAN):
+def _run(gh, d, mean_e, net, mode=S.SUPA_SURROGATE_MEAN, n=N_PROFILE):
     import torch
-    b = S.supa_batch_create([gh], N, {"max_hits": int(N * 60 * mean_e) + (8 << 20), "lpt_order": 1})
+    b = S.supa_batch_create([gh], n, {"max_hits": int(n * 60 * mean_e) + (8 << 20), "lpt_order": 1})
     try:
         if net is not None:
-            S.supa_batch_set_surrogate(b, net, E_S, int(4 * mean_e / E_S * N) + (1 << 20), mode)
-        S.supa_simulate(b, d, N, 7)
+            S.supa_batch_set_surrogate(b, net, E_S, int(4 * mean_e / E_S * n) + (1 << 20), mode)
+        S.supa_simulate(b, d, n, 7)
         info = S.supa_batch_get_info(b)
         lo = torch.zeros(30, dtype=torch.float64, device="cuda")
         la = torch.zeros(BINS, dtype=torch.float64, device="cuda")
-        S.supa_profiles(b, 0, N, BINS, R_MAX, lo, la)
+        S.supa_profiles(b, 0, n, BINS, R_MAX, lo, la)
         torch.cuda.synchronize()
-        return info.n_steps, lo.cpu().numpy() / N, la.cpu().numpy() / N
+        return info.n_steps, lo.cpu().numpy() / n, la.cpu().numpy() / n
     finally:
         S.supa_destroy_batch(b)
 
@@ -52,7 +55,7 @@ def trained():
 
 def test_trained_network_replaces_most_steps_at_small_profile_error(trained):
     net = trained
-    g, p = inputs.workload_plain30(N, seed=21)
+    g, p = inputs.workload_plain30(N_PROFILE, seed=21)
     untrained = S.supa_surrogate_create(16384, S.pack_mlp_params(inputs.mlp_init(1)))
     gh = S.supa_init_geometry(g)
     try:
@@ -71,7 +74,7 @@ def test_trained_network_replaces_most_steps_at_small_profile_error(trained):
     for lo, la in ((lo_h, la_h), (lo_s, la_s)):
         e = T.profile_errors((lo_p, la_p), (lo, la))
         assert e["longitudinal_per_layer"] < 0.02 and e["longitudinal"] < 0.03, e
-        assert e["lateral"] < 0.03 and e["total_deposit"] < 0.006, e
+        assert e["lateral"] < 0.025 and e["total_deposit"] < 0.006, e
     # which the same network untrained is far from
     e = T.profile_errors((lo_p, la_p), (lo_u, la_u))
     assert e["longitudinal"] > 0.1 or e["lateral"] > 0.1, e
