@@ -27,9 +27,10 @@ def _f32_params(seed):
     return vec, [(W.astype(np.float64), b.astype(np.float64)) for W, b in S.unpack_mlp_params(vec)]
 
 
-def test_gradients_match_fp64_oracle():
+@pytest.mark.parametrize("B", [128, 1024])
+def test_gradients_match_fp64_oracle(B):
+    """One row tile (128: one CTA, two K-blocks of weight gradients) and eight."""
     import torch
-    B = 1024
     vec, params = _f32_params(7)
     X, Y = _batch(B, 1)
     s = S.supa_surrogate_create(B, vec)
