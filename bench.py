@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--lr", type=float, default=2e-3, help="initial learning rate")
     ap.add_argument("--batch", type=int, default=16384, help="training minibatch rows (a multiple of 128)")
     ap.add_argument("--lr-final", type=float, default=5e-5, help="learning rate of the last epoch (geometric decay)")
+    ap.add_argument("--average-from", type=int, default=-1,
+                    help="epoch from which the network is the average of the steps' parameters (-1: off)")
     ap.add_argument("--train-showers", type=int, default=0,
                     help="showers of the workload (another seed) whose diverted particles seed the training set")
     ap.add_argument("--train-set", default="matched", choices=["matched", "generic"],
@@ -681,7 +683,8 @@ def matched_training(args, T, make, e_s, mean_e):
     n_show = args.train_showers or int(min(2_000_000, max(50_000, 2.5 * args.train_samples * e_s / mean_e)))
     g_t, p_t = make(n_show)
     data = T.training_set_matched(g_t, p_t, e_s, args.train_samples, seed=5)
-    net, log = T.train(data, epochs=args.epochs, batch=args.batch, lr=args.lr, lr_final=args.lr_final)
+    net, log = T.train(data, epochs=args.epochs, batch=args.batch, lr=args.lr, lr_final=args.lr_final,
+                       average_from=args.average_from if args.average_from >= 0 else None)
     return net, {"samples": data["n"], "data_seconds": data["seconds"], "training_showers": n_show,
                  "set": "matched: diverted particles of the workload's showers (seed 11/14), stepped plainly",
                  **log}
@@ -1148,7 +1151,8 @@ def run_hybrid(args):
         net, tlog = matched_training(args, T, lambda m: inputs.workload_plain50(m, seed=14), args.e_s, mean_e)
     else:
         data = T.training_set(args.train_samples, args.e_s, seed=3, n_layers=30)
-        net, tlog = T.train(data, epochs=args.epochs, lr=args.lr, lr_final=args.lr_final)
+        net, tlog = T.train(data, epochs=args.epochs, lr=args.lr, lr_final=args.lr_final,
+                            average_from=args.average_from if args.average_from >= 0 else None)
         tlog = {"samples": data["n"], "set": "generic sub-shower starts", **tlog}
         del data
     gh = S.supa_init_geometry(g)
@@ -1233,7 +1237,8 @@ def run_train(args):
         net, _ = T.train(data, epochs=args.warmup, batch=args.batch, lr=args.lr, lr_final=args.lr_final)
         from paper_2202_05012_gb300 import supa as S
         S.supa_surrogate_destroy(net)
-    net, log = T.train(data, epochs=args.epochs, batch=args.batch, lr=args.lr, lr_final=args.lr_final)
+    net, log = T.train(data, epochs=args.epochs, batch=args.batch, lr=args.lr, lr_final=args.lr_final,
+                       average_from=args.average_from if args.average_from >= 0 else None)
     from paper_2202_05012_gb300 import supa as S
     S.supa_surrogate_destroy(net)
     steps = log["steps_per_epoch"] * log["epochs"]
