@@ -61,7 +61,8 @@ def training_set_matched(geom, prims, e_s: float, n_max: int, seed: int, device=
     `prims` of a workload run in hybrid mode (any network: only the queue of
     particles diverted below e_s is used), those particles become sub-shower
     primaries (supa_export_diverted), and each is simulated by the plain
-    method in the same geometry.  At most n_max samples."""
+    method in the same geometry.  At most n_max samples; the set does not
+    depend on the order the particles were diverted in."""
     import torch
     gh = S.supa_init_geometry(geom)
     net = S.supa_surrogate_create(128, S.pack_mlp_params(inputs.mlp_init(0)))
@@ -79,10 +80,21 @@ def training_set_matched(geom, prims, e_s: float, n_max: int, seed: int, device=
             m = min(shower_batch, len(prims) - j)
             S.supa_simulate(hb, d[j * 24:(j + m) * 24], m, seed, j)
             S.supa_batch_get_info(hb)
-            k = min(S.supa_export_diverted(hb), n_max - got)
-            buf = torch.empty(k * 24, dtype=torch.uint8, device=device)
+            k_all = S.supa_export_diverted(hb)
+            buf = torch.empty(k_all * 24, dtype=torch.uint8, device=device)
             S.supa_export_diverted(hb, buf)
-            chunks.append(buf)
+            # the queue's order depends on which warp diverted first: sort the
+            # records by their bytes, so that the set (and the Philox streams of
+            # its plain simulation, keyed by position) is the same every run,
+            # then keep a seeded random subset where the set is full
+            rec = buf.view(torch.int32).view(k_all, 6)
+            for col in range(5, -1, -1):
+                rec = rec[torch.sort(rec[:, col], stable=True).indices]
+            k = min(k_all, n_max - got)
+            if k < k_all:
+                gen = torch.Generator().manual_seed(seed * 7919 + j)
+                rec = rec[torch.randperm(k_all, generator=gen)[:k].to(device)]
+            chunks.append(rec.contiguous().view(torch.uint8).view(-1))
             got += k
             if got >= n_max:
                 break

@@ -5,10 +5,9 @@ plain ones in both modes: every layer holding >= 0.5 % of the energy within
 2 %, and within 3 % the largest deviation over groups of consecutive
 layers, or of rings around the shower axis, holding >= 2 % of the energy
 each (every layer and ring included) -- which an untrained network of the
-same shape does not achieve.  The lateral figure depends on the training
-run: 1.2-2.4 % on 100,000 showers over trainings in separate processes
-(each draws its own matched training set), once 3.4 % with iterate
-averaging, which the recipe does not use."""
+same shape does not achieve.  (The matched training set no longer depends
+on the order particles were diverted in: three runs in separate processes
+gave lateral errors of 1.20-1.39 % and longitudinal 0.97-1.10 %.)"""
 import numpy as np
 import pytest
 
