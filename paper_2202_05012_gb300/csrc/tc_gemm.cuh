@@ -74,7 +74,7 @@ struct TrainPassArgs {
     const float *x, *y;
     int64_t n, i0;
     uint64_t perm_a, perm_c;
-    __nv_bfloat16 *GP1, *GP2, *GP3;     // [B][256] GELU'(z) of the hidden layers (written, read back)
+    __nv_bfloat16 *GP1, *GP2, *GP3;     // B x 256 GELU'(z) of the hidden layers, in the pass's thread order (written, read back)
     float *gb1, *gb2, *gb3, *gb4;       // bias gradients (added to)
     double *loss_sum;                   // minibatch loss (added to)
     int *error;                         // device error word (|= 8: a pipeline wait expired)

@@ -353,11 +353,16 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 for (int k = kb + 1 - kHandOff; k <= kb; ++k) mbar_arrive(&a_ready[k]);
         };
         for (int t = 0; t < my_tiles && ok; ++t) {
-            const int row = ((int)blockIdx.x + t * (int)gridDim.x) * kTRows + r;
+            const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+            const int row = tile * kTRows + r;
+            // GELU'(z) is kept in thread order, so that each warp's stores and loads of it are
+            // whole 512-byte runs: per layer and tile 64 KB, [epilogue warp][K-block][half][lane]
+            // x 16 bytes (the same thread reads back what it wrote)
+            const size_t gp_at = (size_t)tile * (kTRows * 256 / 8) + (size_t)(warp - 4) * 256 + lane;
             // ---- forward: z = acc + b; GELU(z) to the operand, GELU'(z) kept for the backward ----
             for (int l = 0; l < 3 && ok; ++l) {
                 if (!wait_acc()) { ok = false; break; }
-                __nv_bfloat16 *GP = (l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + (size_t)row * 256;
+                uint4 *gp = reinterpret_cast<uint4 *>(l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + gp_at;
                 const uint32_t acc = tmem + lane_off + (uint32_t)(np & 1) * 256u;
                 // the next K-block's accumulator columns load while this one is processed
                 uint32_t raw[16], nxt[16];
@@ -377,9 +382,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     uint8_t *blk = A + kb * kABlk;
                     *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h)) = make_uint4(p[0], p[1], p[2], p[3]);
                     *reinterpret_cast<uint4 *>(blk + sw128_offset(r, 2 * h + 1)) = make_uint4(p[4], p[5], p[6], p[7]);
-                    uint4 *gp = reinterpret_cast<uint4 *>(GP + c0);
-                    gp[0] = make_uint4(d[0], d[1], d[2], d[3]);
-                    gp[1] = make_uint4(d[4], d[5], d[6], d[7]);
+                    gp[kb * 64] = make_uint4(d[0], d[1], d[2], d[3]);
+                    gp[kb * 64 + 32] = make_uint4(d[4], d[5], d[6], d[7]);
                     hand_off_kb(kb);
                     if (kb < 3) {
                         tmem_ld_wait(nxt);
@@ -475,13 +479,12 @@ __global__ void __launch_bounds__(kTThreads, 1)
             ++np;
             // ---- backward: g = acc * GELU'(z), to the operand, column sums ----
             for (int l = 2; l >= 0 && ok; --l) {
-                const __nv_bfloat16 *GP = (l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + (size_t)row * 256;
+                const uint4 *gpv = reinterpret_cast<const uint4 *>(l == 0 ? g.GP1 : l == 1 ? g.GP2 : g.GP3) + gp_at;
                 float *gb = l == 0 ? g.gb1 : l == 1 ? g.gb2 : g.gb3;
                 if (!wait_acc()) { ok = false; break; }
                 // GELU'(z) and the accumulator columns of the next K-block load
                 // while this one is processed
-                const uint4 *gpv = reinterpret_cast<const uint4 *>(GP + h * 16);
-                uint4 gp0 = gpv[0], gp1 = gpv[1];
+                uint4 gp0 = gpv[0], gp1 = gpv[32];
                 const uint32_t acc = tmem + lane_off + (uint32_t)(np & 1) * 256u;
                 uint32_t raw[16], nxt[16];
                 tmem_ld16_issue(acc + h * 16, raw);
@@ -492,8 +495,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     uint4 np0 = gp0, np1 = gp1;
                     if (kb < 3) {
                         tmem_ld16_issue(acc + c0 + 64, nxt);
-                        np0 = gpv[8 * (kb + 1)];  // 64 bf16 columns = 8 x 16 bytes
-                        np1 = gpv[8 * (kb + 1) + 1];
+                        np0 = gpv[64 * (kb + 1)];
+                        np1 = gpv[64 * (kb + 1) + 32];
                     }
                     float d[16];
                     const uint32_t gw[8] = {gp0.x, gp0.y, gp0.z, gp0.w, gp1.x, gp1.y, gp1.z, gp1.w};
