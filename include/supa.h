@@ -411,7 +411,8 @@ int supa_surrogate_average(supa_surrogate *s, int32_t mode, void *stream);
 /* One epoch over a training set of n samples (x_dev [n][6], y_dev [n][60]):
  * floor(n / batch) Adam steps on minibatches gathered in the order of the
  * permutation i -> (a i + c) mod n that `seed` picks.  Asynchronous; adds
- * each minibatch loss to *loss_acc_dev when it is not NULL. */
+ * each minibatch loss to *loss_acc_dev when it is not NULL.  x_dev 4-byte and
+ * y_dev 8-byte aligned, else SUPA_ERR_INVALID_ARG. */
 int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,
                                float lr, double *loss_acc_dev, void *stream);
 /* Inference: x_dev float32 [n][6] (8-byte aligned) -> out_dev float32

@@ -38,8 +38,7 @@ using namespace supa;
 
 namespace {
 
-constexpr int kIn = 6, kInPad = 64, kHid = 256, kOut = 90, kOutPad = 128, kLayersOut = 30;
-constexpr int kY = 2 * kLayersOut;  // target columns: fractions, mean distances
+constexpr int kIn = 6, kInPad = 64, kHid = 256, kOut = 90, kOutPad = 128;
 constexpr int kInferLd = 96;        // outputs written by the fused inference kernel (>= kOut; 90..95 are zero)
 // packed user parameter vector: W1, b1, W2, b2, W3, b3, W4, b4
 constexpr int kNParams = kHid * kIn + kHid + 2 * (kHid * kHid + kHid) + kOut * kHid + kOut;
@@ -446,6 +445,8 @@ int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const floa
                                float lr, double *loss_acc_dev, void *stream) {
     if (!s || !x_dev || !y_dev || n < s->B)
         return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_epoch: need at least one full minibatch");
+    if (((uintptr_t)x_dev & 3) || ((uintptr_t)y_dev & 7))
+        return sfail(SUPA_ERR_INVALID_ARG, "supa_surrogate_train_epoch: x must be 4-byte and y 8-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     // permutation i -> (a i + c) mod n with gcd(a, n) = 1
     uint64_t a = (seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull) % (uint64_t)n;
