@@ -1224,8 +1224,9 @@ def run_forward(args):
 def run_train(args):
     """The surrogate's training alone: a generic training set of
     --train-samples sub-showers (E log-uniform [e_min, E_s], plain method,
-    E_s = --e-s), then --epochs Adam epochs in --batch-row minibatches, each
-    step the training pass, the grouped weight gradients and the Adam update;
+    E_s = --e-s), then --epochs Adam epochs in --batch-row minibatches (per
+    epoch the targets staged once in the training pass's order; each step the
+    training pass, the grouped weight gradients and the Adam update);
     W warm-up epochs first (not timed).  TFLOP/s of algorithmic flops
     (forward + backward, 3 x 311,296 per sample) by CUDA events."""
     import torch
@@ -1246,7 +1247,8 @@ def run_train(args):
                       "samples": args.train_samples, "epochs": args.epochs, "batch": args.batch,
                       "us_per_step": log["seconds"] / steps * 1e6, "samples_per_s": log["samples_per_s"],
                       "seconds": log["seconds"], "loss_last_epoch": log["loss_per_epoch"][-1],
-                      "kernels": ["train_mlp_kernel", "wgrad_kernel", "adam_update"]}), flush=True)
+                      "kernels": ["stage_targets (once an epoch)", "train_mlp_kernel", "wgrad_kernel",
+                                  "adam_update"]}), flush=True)
 
 
 def main():

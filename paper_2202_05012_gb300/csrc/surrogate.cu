@@ -110,6 +110,9 @@ struct supa_surrogate {
     __nv_bfloat16 *W1b, *W2b, *W3b, *W4b;
     __nv_bfloat16 *X0, *H1, *H2, *H3, *G4, *G3, *G2, *G1;  // row-major operands of the weight gradients
     __nv_bfloat16 *GP1, *GP2, *GP3;                           // GELU'(z) of the hidden layers
+    float4 *yt = nullptr;       // one minibatch's targets in the training pass's order
+    float4 *yt_epoch = nullptr;  // an epoch's, staged once before its first step
+    int64_t yt_epoch_tiles = 0;
     double *loss_tmp = nullptr;
     int *error = nullptr;
     TrainMapSet tm;                                  // the training pass's loads and stores
@@ -133,6 +136,9 @@ bool grab(supa_surrogate *s, T **p, size_t n) {
 void free_all(supa_surrogate *s) {
     for (void *p : s->allocs) cudaFree(p);
     s->allocs.clear();
+    cudaFree(s->yt_epoch);
+    s->yt_epoch = nullptr;
+    s->yt_epoch_tiles = 0;
 }
 
 int weight_copies(supa_surrogate *s, cudaStream_t st) {
@@ -149,9 +155,10 @@ int weight_copies(supa_surrogate *s, cudaStream_t st) {
 // Adam update left it zero) and the loss added to *s->loss_tmp: the training
 // pass per 128-row tile (gather, forward, loss gradient, data-gradient chain;
 // bias gradients), then dW4 = G4^T H3, dW3 = G3^T H2, dW2 = G2^T H1,
-// dW1 = G1^T X0 over the rows in one grouped launch.
+// dW1 = G1^T X0 over the rows in one grouped launch.  The targets come staged
+// (launch_stage_targets) at yt, or are staged here when yt is null.
 cudaError_t train_pass(supa_surrogate *s, const float *x, const float *y, int64_t n, uint64_t a, uint64_t c,
-                       int64_t i0, cudaStream_t st) {
+                       int64_t i0, cudaStream_t st, const float4 *yt = nullptr) {
     const int B = s->B;
     cudaError_t e = cudaSuccess;
     if (!s->grad_zero && (e = cudaMemsetAsync(s->grad, 0, Off::total * sizeof(float), st)) != cudaSuccess) return e;
@@ -162,8 +169,12 @@ cudaError_t train_pass(supa_surrogate *s, const float *x, const float *y, int64_
     t.b2 = s->master + Off::b2;
     t.b3 = s->master + Off::b3;
     t.b4 = s->master + Off::b4;
+    if (!yt) {
+        if ((e = launch_stage_targets(y, n, i0, a, c, B / 128, s->yt, st)) != cudaSuccess) return e;
+        yt = s->yt;
+    }
     t.x = x;
-    t.y = y;
+    t.yt = yt;
     t.n = n;
     t.i0 = i0;
     t.perm_a = a;
@@ -290,7 +301,8 @@ int supa_surrogate_create(int32_t batch, const float *params_host, supa_surrogat
               grab(s, &s->X0, B * kInPad) && grab(s, &s->H1, B * kHid) && grab(s, &s->H2, B * kHid) &&
               grab(s, &s->H3, B * kHid) && grab(s, &s->G4, B * kOutPad) && grab(s, &s->G3, B * kHid) &&
               grab(s, &s->G2, B * kHid) && grab(s, &s->G1, B * kHid) && grab(s, &s->GP1, B * kHid) &&
-              grab(s, &s->GP2, B * kHid) && grab(s, &s->GP3, B * kHid) && grab(s, &s->loss_tmp, 1) &&
+              grab(s, &s->GP2, B * kHid) && grab(s, &s->GP3, B * kHid) && grab(s, &s->yt, B * 16) &&
+              grab(s, &s->loss_tmp, 1) &&
               grab(s, &s->avg, Off::total) &&
               grab(s, &s->error, 1);
     if (!ok) {
@@ -384,11 +396,11 @@ namespace {
 // The training pass of the minibatch (see train_pass; loss added to *loss),
 // then the Adam update.
 int train_minibatch(supa_surrogate *s, const float *x, const float *y, int64_t n, uint64_t a, uint64_t c, int64_t i0,
-                    float lr, double *loss, cudaStream_t st) {
+                    float lr, double *loss, cudaStream_t st, const float4 *yt = nullptr) {
     // train_pass() adds the minibatch loss to s->loss_tmp; point it at the accumulator
     double *keep = s->loss_tmp;
     s->loss_tmp = loss;
-    cudaError_t e = train_pass(s, x, y, n, a, c, i0, st);
+    cudaError_t e = train_pass(s, x, y, n, a, c, i0, st, yt);
     s->loss_tmp = keep;
     if (e != cudaSuccess) return sfail(SUPA_ERR_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
     s->t += 1;
@@ -463,8 +475,23 @@ int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const floa
     const uint64_t c = (seed ^ 0xD1B54A32D192ED03ull) % (uint64_t)n;
     const int64_t steps = n / s->B;
     double *loss = loss_acc_dev ? loss_acc_dev : s->loss_tmp;
+    // the epoch's targets in the training pass's order, staged once (the
+    // gather of random rows is then off the passes' critical path)
+    const int64_t tiles = steps * (s->B / 128);
+    if (tiles > s->yt_epoch_tiles) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return sfail(SUPA_ERR_CUDA, "train_epoch: stream failed");
+        cudaFree(s->yt_epoch);
+        s->yt_epoch = nullptr;
+        s->yt_epoch_tiles = 0;
+        if (cudaMalloc((void **)&s->yt_epoch, (size_t)tiles * 2048 * sizeof(float4)) != cudaSuccess)
+            return sfail(SUPA_ERR_OOM, "supa_surrogate_train_epoch: out of device memory for the staged targets");
+        s->yt_epoch_tiles = tiles;
+    }
+    if (launch_stage_targets(y_dev, n, 0, a, c, tiles, s->yt_epoch, st) != cudaSuccess)
+        return sfail(SUPA_ERR_CUDA, "train_epoch: staging launch failed");
     for (int64_t k = 0; k < steps; ++k) {
-        const int rc = train_minibatch(s, x_dev, y_dev, n, a, c, k * s->B, lr, loss, st);
+        const int rc = train_minibatch(s, x_dev, y_dev, n, a, c, k * s->B, lr, loss, st,
+                                       s->yt_epoch + (size_t)k * (s->B / 128) * 2048);
         if (rc != SUPA_OK) return rc;
     }
     return cudaGetLastError() == cudaSuccess ? SUPA_OK : sfail(SUPA_ERR_CUDA, "train_epoch launch failed");

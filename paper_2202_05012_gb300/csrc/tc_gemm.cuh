@@ -55,6 +55,15 @@ struct MlpInferArgs {
 cudaError_t launch_sur_mlp(const CUtensorMap &w1, const CUtensorMap &w2, const CUtensorMap &w3,
                            const CUtensorMap &w4, const MlpInferArgs &a, cudaStream_t st);
 
+// Targets in the order the training pass's loss phase reads them: for tiles
+// t < `tiles` of 128 rows, rows (a (i0 + 128 t + r) + c) mod n of y [n][60]
+// (8-byte aligned) as 2048 float4 each at yt + 2048 t, [h][q][k][lane] for
+// row 32 q + lane of the tile: k = 0, 1 the deposit fractions of layers
+// 8 h + 4 k .. + 3, k = 2, 3 the mean distances of the same layers (layers
+// past 29: unused).  A plain launch: it follows all earlier work on `st`.
+cudaError_t launch_stage_targets(const float *y, int64_t n, int64_t i0, uint64_t a, uint64_t c, int64_t tiles,
+                                 float4 *yt, cudaStream_t st);
+
 // One training pass of a minibatch up to the weight gradients (train_mlp.cu):
 // per 128-row tile the forward, the loss gradient and the data-gradient chain
 // in one kernel.  The kernel gathers the minibatch rows itself; the packed
@@ -70,10 +79,12 @@ struct TrainPassArgs {
     int B;                              // rows, a multiple of 128
     const float *b1, *b2, *b3, *b4;     // biases [256] x 3, [128]
     // the minibatch: row r is row (perm_a (i0 + r) + perm_c) mod n of the
-    // inputs x [n][6] and the targets y [n][60] (gathered by the kernel)
-    const float *x, *y;
+    // inputs x [n][6] (gathered by the kernel) and of the targets, staged by
+    // launch_stage_targets: yt is the minibatch's first tile
+    const float *x;
     int64_t n, i0;
     uint64_t perm_a, perm_c;
+    const float4 *yt;
     __nv_bfloat16 *GP1, *GP2, *GP3;     // B x 256 GELU'(z) of the hidden layers, in the pass's thread order (written, read back)
     float *gb1, *gb2, *gb3, *gb4;       // bias gradients (added to)
     double *loss_sum;                   // minibatch loss (added to)

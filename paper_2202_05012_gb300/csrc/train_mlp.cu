@@ -64,6 +64,7 @@ using namespace tc;
 constexpr int kTThreads = 640;  // 20 warps (5 per scheduler: 96 registers a thread)
 constexpr int kTRows = 128;
 constexpr int kLayersOut = 30;
+constexpr int kStagedPerTile = 2048;  // float4 of staged targets per 128-row tile
 constexpr uint32_t kXBytes = kTRows * 128;    // input tile
 constexpr uint32_t kABlk = kTRows * 128;      // one K-block of a 128-row operand
 constexpr uint32_t kABytes = 4 * kABlk;
@@ -91,6 +92,41 @@ __device__ __forceinline__ LoadPlan plan(int i) {
     return {6, i - 19, 256 * 128};
 }
 constexpr int kLoads = 23;
+
+// Targets in the loss phase's thread order (layout with launch_stage_targets):
+// per tile the 128 rows are read whole (30 lanes x 8 bytes a row, 16 rows of a
+// warp in flight) into shared memory, then written out as the tile's 2048
+// float4 in order.  Grid-stride over the tiles.
+__global__ void __launch_bounds__(256) stage_targets(const float *__restrict__ y, int64_t n, int64_t i0, uint64_t a,
+                                                     uint64_t c, int64_t tiles, float4 *__restrict__ yt) {
+    __shared__ float rows[kTRows][2 * kLayersOut + 5];  // odd stride: the column reads below are conflict-free
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        // lane k < 16 finds the source of row warp + 8 k
+        const int64_t my_src =
+            (int64_t)((a * (uint64_t)(i0 + tile * kTRows + warp + 8 * (lane & 15)) + c) % (uint64_t)n);
+        float2 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int64_t src = __shfl_sync(0xFFFFFFFFu, my_src, k);
+            v[k] = lane < kLayersOut ? *reinterpret_cast<const float2 *>(y + src * (2 * kLayersOut) + 2 * lane)
+                                     : make_float2(0.0f, 0.0f);  // lanes 30, 31: columns 60..63 zero
+        }
+        __syncthreads();  // the previous tile's rows are written out
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            rows[warp + 8 * k][2 * lane] = v[k].x;
+            rows[warp + 8 * k][2 * lane + 1] = v[k].y;
+        }
+        __syncthreads();
+        float4 *out = yt + tile * kStagedPerTile;
+        for (int i = threadIdx.x; i < kStagedPerTile; i += 256) {
+            const int ln = i & 31, k = (i >> 5) & 3, q = (i >> 7) & 3, h = i >> 9;
+            const float *row = rows[32 * q + ln] + (k < 2 ? 0 : kLayersOut) + 8 * h + 4 * (k & 1);
+            out[i] = make_float4(row[0], row[1], row[2], row[3]);
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kTThreads, 1)
     train_mlp_kernel(const __grid_constant__ TrainMapSet mp, const TrainPassArgs g) {
@@ -354,11 +390,10 @@ __global__ void __launch_bounds__(kTThreads, 1)
         };
         for (int t = 0; t < my_tiles && ok; ++t) {
             const int tile = (int)blockIdx.x + t * (int)gridDim.x;
-            const int row = tile * kTRows + r;
             // GELU'(z) is kept in thread order, so that each warp's stores and loads of it are
             // whole 512-byte runs: per layer and tile 64 KB, [epilogue warp][K-block][half][lane]
             // x 16 bytes (the same thread reads back what it wrote)
-            const size_t gp_at = (size_t)tile * (kTRows * 256 / 8) + (size_t)(warp - 4) * 256 + lane;
+            const uint32_t gp_at = (uint32_t)tile * (kTRows * 256 / 8) + (uint32_t)(warp - 4) * 256u + (uint32_t)lane;
             // ---- forward: z = acc + b; GELU(z) to the operand, GELU'(z) kept for the backward ----
             for (int l = 0; l < 3 && ok; ++l) {
                 if (!wait_acc()) { ok = false; break; }
@@ -399,21 +434,12 @@ __global__ void __launch_bounds__(kTThreads, 1)
             //      writes d out (bf16) into the A buffer as the operand of d out W4 ----
             {
                 const int j0 = 8 * h, nj = h < 3 ? 8 : kLayersOut - 24;
-                // the targets load while the output layer's MMAs run
-                const int64_t src = (int64_t)((g.perm_a * (uint64_t)(g.i0 + row) + g.perm_c) % (uint64_t)g.n);
-                const float *yrow = g.y + src * (2 * kLayersOut);
-                float yv[8], yr[8];
-#pragma unroll
-                for (int i = 0; i < 8; i += 2) {
-                    if (i < nj) {
-                        const float2 a = *reinterpret_cast<const float2 *>(yrow + j0 + i);
-                        const float2 b = *reinterpret_cast<const float2 *>(yrow + kLayersOut + j0 + i);
-                        yv[i] = a.x; yv[i + 1] = a.y;
-                        yr[i] = b.x; yr[i + 1] = b.y;
-                    } else {
-                        yv[i] = yv[i + 1] = yr[i] = yr[i + 1] = 0.0f;
-                    }
-                }
+                // the targets load while the output layer's MMAs run: staged in thread
+                // order, each warp's four loads are whole 512-byte runs
+                const float4 *yt = g.yt + (size_t)tile * kStagedPerTile + (size_t)((h * 4 + q) * 4) * 32 + lane;
+                const float4 ya = yt[0], yb = yt[32], yc = yt[64], yd = yt[96];
+                const float yv[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+                const float yr[8] = {yc.x, yc.y, yc.z, yc.w, yd.x, yd.y, yd.z, yd.w};
                 if (!wait_acc()) { ok = false; break; }
                 const uint32_t acc = tmem + lane_off + (uint32_t)(np & 1) * 256u;
                 float om[8], os[8], orh[8];
@@ -539,6 +565,17 @@ __global__ void __launch_bounds__(kTThreads, 1)
 }
 
 }  // namespace
+
+cudaError_t launch_stage_targets(const float *y, int64_t n, int64_t i0, uint64_t a, uint64_t c, int64_t tiles,
+                                 float4 *yt, cudaStream_t st) {
+    if (tiles < 1 || n < 1) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)sms * 8);
+    stage_targets<<<(unsigned)grid, 256, 0, st>>>(y, n, i0, a, c, tiles, yt);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_train_pass(const TrainMapSet &maps, const TrainPassArgs &a, cudaStream_t st) {
     if (a.B < kTRows || a.B % kTRows) return cudaErrorInvalidValue;
