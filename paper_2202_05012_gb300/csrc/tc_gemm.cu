@@ -56,8 +56,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         if (i == g.nprob) items = pl.item0[i];
     if (item >= items) return;
     // this CTA's problem (constant indices, so the parameters stay in place)
-    int p = 0, first = 0, splits = 1, kbps = 1, N = 64, ld = 0;
-    float *out_base = nullptr;
+    int p = 0, first = 0, splits = 1, kbps = 1, N = 64;
 #pragma unroll
     for (int i = 0; i < kWgradMax; ++i)
         if (i < g.nprob && item >= pl.item0[i]) {
@@ -66,8 +65,6 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             splits = pl.splits[i];
             kbps = pl.kbps[i];
             N = g.p[i].N;
-            ld = g.p[i].ld;
-            out_base = g.p[i].out;
         }
     const int local = item - first;
     const int mt = local / splits, sp = local % splits;
