@@ -195,3 +195,71 @@ def test_gradients_with_several_tiles_per_cta():
         assert abs(loss2 - loss) <= 1e-5 * abs(loss)
     finally:
         S.supa_surrogate_destroy(s)
+
+
+def _epoch_permutation(seed, n):
+    """The rows i -> (a i + c) mod n of an epoch, as supa_surrogate_train_epoch
+    picks a and c from the seed (host arithmetic restated)."""
+    from math import gcd
+    m = 2**64 - 1
+    a = ((seed * 0x9E3779B97F4A7C15) & m) + 0x632BE59BD9B4E019
+    a = (a & m) % n
+    if a == 0:
+        a = 1
+    while gcd(a, n) != 1:
+        a = 1 if (a + 1) % n == 0 else a + 1
+    c = (seed ^ 0xD1B54A32D192ED03) % n
+    return (a * np.arange(n, dtype=object) + c) % n
+
+
+def test_epoch_with_staged_targets_equals_its_steps():
+    """An epoch (targets staged once in the training pass's order) against
+    the same minibatches, gathered on the host, as single Adam steps: the
+    same parameters and the same loss, up to the order of float additions."""
+    import torch
+    B, steps, seed = 256, 3, 11
+    n = B * steps + 77  # a ragged remainder the epoch leaves out
+    vec, _ = _f32_params(5)
+    X, Y = _batch(n, 8)
+    perm = np.array(_epoch_permutation(seed, n), dtype=np.int64)
+    a = S.supa_surrogate_create(B, vec)
+    b = S.supa_surrogate_create(B, vec)
+    try:
+        xd = torch.from_numpy(X.astype(np.float32)).cuda()
+        yd = torch.from_numpy(Y.astype(np.float32)).cuda()
+        acc_a = torch.zeros(1, dtype=torch.float64, device="cuda")
+        acc_b = torch.zeros(1, dtype=torch.float64, device="cuda")
+        S.supa_surrogate_train_epoch(a, xd, yd, n, seed, 1e-3, acc_a)
+        for k in range(steps):
+            rows = perm[k * B:(k + 1) * B]
+            xs = torch.from_numpy(X[rows].astype(np.float32)).cuda()
+            ys = torch.from_numpy(Y[rows].astype(np.float32)).cuda()
+            S.supa_surrogate_train_step(b, xs, ys, 1e-3, acc_b)
+        S.supa_surrogate_check(a)
+        S.supa_surrogate_check(b)
+        np.testing.assert_allclose(acc_a.item(), acc_b.item(), rtol=1e-5)
+        pa, pb = S.supa_surrogate_get_params(a), S.supa_surrogate_get_params(b)
+        np.testing.assert_allclose(pa, pb, rtol=0, atol=1e-5 * np.abs(pb).max())
+    finally:
+        S.supa_surrogate_destroy(a)
+        S.supa_surrogate_destroy(b)
+
+
+def test_misaligned_targets_are_refused():
+    import torch
+    B = 128
+    vec, _ = _f32_params(5)
+    X, Y = _batch(B + 1, 8)
+    s = S.supa_surrogate_create(B, vec)
+    try:
+        xd = torch.from_numpy(X.astype(np.float32)).cuda()
+        buf = torch.from_numpy(np.concatenate([[0.0], Y.ravel()]).astype(np.float32)).cuda()
+        y_odd = buf[1:]  # 4 bytes past an aligned allocation: not 8-byte aligned
+        for call in (lambda: S.supa_surrogate_gradients(s, xd, y_odd),
+                     lambda: S.supa_surrogate_train_step(s, xd, y_odd, 1e-3),
+                     lambda: S.supa_surrogate_train_epoch(s, xd, y_odd, B, 1, 1e-3)):
+            with pytest.raises(S.SupaError) as e:
+                call()
+            assert e.value.code == S.SUPA_ERR_INVALID_ARG
+    finally:
+        S.supa_surrogate_destroy(s)
