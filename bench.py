@@ -65,6 +65,8 @@ def parse():
                     help="hybrid workload: sub-showers from diverted particles, or generic starts (smaller)")
     ap.add_argument("--c5-showers", type=int, default=10_000_000,
                     help="showers of the 50-layer hybrid comparison in the default run (0: skip it)")
+    ap.add_argument("--c5-e-s-low", type=float, default=1.5,
+                    help="second, lower E_s of the 50-layer hybrid comparison (0: only --e-s)")
     ap.add_argument("--no-mixed4", action="store_true", help="skip the uneven-batch measurement in the default run")
     ap.add_argument("--pipeline", type=int, default=1,
                     help="sub-batches per step; >1 overlaps simulation of one with downsampling of the previous")
@@ -1090,7 +1092,9 @@ def hybrid_c5(args, S) -> dict:
     chunk with the point cloud), run plainly and with the network below E_s
     in both modes on the same seeds; the network is trained first on 10M
     sub-showers started from the particles showers of the same workload
-    (another seed) divert, 20 epochs."""
+    (another seed) divert, 20 epochs.  The same again at the lower cutoff
+    --c5-e-s-low (fewer particles diverted: less speed-up, smaller errors)
+    under "low_e_s"."""
     import torch
 
     from paper_2202_05012_gb300 import inputs
@@ -1117,15 +1121,30 @@ def hybrid_c5(args, S) -> dict:
         ref = plain.pop("profiles")
         out["plain"] = plain
         sub_h = 100_000
-        for mode, name in ((S.SUPA_SURROGATE_MEAN, "mean"), (S.SUPA_SURROGATE_SAMPLE, "sample")):
-            c5_pass(S, gh, p5, d5, 20_000, 4, 20_000, V, grid, oor, max(400, 40 * mean_e), net, args.e_s, mode)
-            r = c5_pass(S, gh, p5, d5, n, 4, sub_h, V, grid, oor, max(400, 40 * mean_e), net, args.e_s, mode)
-            r["profile_error"] = profile_errors(ref, r.pop("profiles"))
-            r["vs_plain"] = {"showers_per_s": r["showers_per_s"] / plain["showers_per_s"],
-                             "simulate_showers_per_s": r["simulate_showers_per_s"] / plain["simulate_showers_per_s"]}
-            out[name] = r
+
+        def both_modes(net, e_s, dst):
+            for mode, name in ((S.SUPA_SURROGATE_MEAN, "mean"), (S.SUPA_SURROGATE_SAMPLE, "sample")):
+                c5_pass(S, gh, p5, d5, 20_000, 4, 20_000, V, grid, oor, max(400, 40 * mean_e), net, e_s, mode)
+                r = c5_pass(S, gh, p5, d5, n, 4, sub_h, V, grid, oor, max(400, 40 * mean_e), net, e_s, mode)
+                r["profile_error"] = profile_errors(ref, r.pop("profiles"))
+                r["vs_plain"] = {"showers_per_s": r["showers_per_s"] / plain["showers_per_s"],
+                                 "simulate_showers_per_s": r["simulate_showers_per_s"] / plain["simulate_showers_per_s"]}
+                dst[name] = r
+
+        both_modes(net, args.e_s, out)
+        if args.c5_e_s_low > 0:
+            S.supa_surrogate_destroy(net)
+            net = None
+            net, tlog2 = matched_training(args, T, lambda m: inputs.workload_plain50(m, seed=14), args.c5_e_s_low,
+                                          mean_e)
+            low = {"e_s": args.c5_e_s_low,
+                   "training": {k: v for k, v in tlog2.items() if k != "loss_per_epoch"},
+                   "training_loss_last_epoch": tlog2["loss_per_epoch"][-1]}
+            both_modes(net, args.c5_e_s_low, low)
+            out["low_e_s"] = low
     finally:
-        S.supa_surrogate_destroy(net)
+        if net is not None:
+            S.supa_surrogate_destroy(net)
         S.supa_destroy_geometry(gh)
         del grid, oor, d5
         torch.cuda.empty_cache()
