@@ -412,7 +412,11 @@ int supa_surrogate_average(supa_surrogate *s, int32_t mode, void *stream);
  * floor(n / batch) Adam steps on minibatches gathered in the order of the
  * permutation i -> (a i + c) mod n that `seed` picks.  Asynchronous; adds
  * each minibatch loss to *loss_acc_dev when it is not NULL.  x_dev 4-byte and
- * y_dev 8-byte aligned, else SUPA_ERR_INVALID_ARG. */
+ * y_dev 8-byte aligned, else SUPA_ERR_INVALID_ARG.  Before its first step the
+ * epoch's targets are copied once into the order the training pass reads
+ * them: a device buffer of 256 bytes per row of the full minibatches, kept
+ * with the surrogate (grown, after a synchronisation of `stream`, when a
+ * larger epoch needs it; SUPA_ERR_OOM if it cannot be had). */
 int supa_surrogate_train_epoch(supa_surrogate *s, const float *x_dev, const float *y_dev, int64_t n, uint64_t seed,
                                float lr, double *loss_acc_dev, void *stream);
 /* Inference: x_dev float32 [n][6] (8-byte aligned) -> out_dev float32
