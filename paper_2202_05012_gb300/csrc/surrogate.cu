@@ -67,26 +67,50 @@ struct WeightCopies {
 // inv_c1 = 1 / c1, inv_sqrt_c2 = 1 / sqrt(c2): the step is
 // lr (m / c1) / (sqrt(v / c2) + eps) = lr m inv_c1 / (sqrt(v) inv_sqrt_c2 + eps).
 // With avg set, the updated parameters are also added to the running
-// average avg with weight w (1 / (steps averaged + 1)).
+// average avg with weight w (1 / (steps averaged + 1)).  Four parameters a
+// thread (n, the offsets and sizes of the weight copies multiples of 4, all
+// blocks 16-byte aligned): 16-byte loads and stores.
+__device__ __forceinline__ float adam_one(float &p, float &m, float &v, float g, float lr, float b1, float b2,
+                                          float eps, float inv_c1, float inv_sqrt_c2) {
+    m = b1 * m + (1.0f - b1) * g;
+    v = b2 * v + (1.0f - b2) * g * g;
+    p = p - __fdividef(lr * m * inv_c1, fmaf(sqrtf(v), inv_sqrt_c2, eps));
+    return p;
+}
+
 __global__ void adam_update(float *p, float *m, float *v, float *g, int n, float lr, float b1, float b2,
                             float eps, float inv_c1, float inv_sqrt_c2, const WeightCopies wc, float *avg, float w) {
     pdl_wait();  // the weight gradients are complete
     pdl_trigger();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float pi = p[i] - __fdividef(lr * mi * inv_c1, fmaf(sqrtf(vi), inv_sqrt_c2, eps));
-    p[i] = pi;
-    g[i] = 0.0f;  // ready for the next minibatch's gradients
-    if (avg) avg[i] = fmaf(w, pi - avg[i], avg[i]);
+    const float4 gi = *reinterpret_cast<const float4 *>(g + i);
+    float4 pi = *reinterpret_cast<const float4 *>(p + i), mi = *reinterpret_cast<const float4 *>(m + i),
+           vi = *reinterpret_cast<const float4 *>(v + i);
+    adam_one(pi.x, mi.x, vi.x, gi.x, lr, b1, b2, eps, inv_c1, inv_sqrt_c2);
+    adam_one(pi.y, mi.y, vi.y, gi.y, lr, b1, b2, eps, inv_c1, inv_sqrt_c2);
+    adam_one(pi.z, mi.z, vi.z, gi.z, lr, b1, b2, eps, inv_c1, inv_sqrt_c2);
+    adam_one(pi.w, mi.w, vi.w, gi.w, lr, b1, b2, eps, inv_c1, inv_sqrt_c2);
+    *reinterpret_cast<float4 *>(m + i) = mi;
+    *reinterpret_cast<float4 *>(v + i) = vi;
+    *reinterpret_cast<float4 *>(p + i) = pi;
+    *reinterpret_cast<float4 *>(g + i) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // ready for the next minibatch
+    if (avg) {
+        float4 a = *reinterpret_cast<const float4 *>(avg + i);
+        a = make_float4(fmaf(w, pi.x - a.x, a.x), fmaf(w, pi.y - a.y, a.y), fmaf(w, pi.z - a.z, a.z),
+                        fmaf(w, pi.w - a.w, a.w));
+        *reinterpret_cast<float4 *>(avg + i) = a;
+    }
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        const int j = i - wc.off[w];
-        if (j >= 0 && j < wc.size[w]) wc.Wb[w][j] = __float2bfloat16_rn(pi);
+    for (int c = 0; c < 4; ++c) {
+        const int j = i - wc.off[c];
+        if (j >= 0 && j < wc.size[c]) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(pi.x, pi.y), hi = __floats2bfloat162_rn(pi.z, pi.w);
+            uint2 u;
+            u.x = *reinterpret_cast<uint32_t *>(&lo);
+            u.y = *reinterpret_cast<uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(wc.Wb[c] + j) = u;
+        }
     }
 }
 
@@ -408,7 +432,10 @@ int train_minibatch(supa_surrogate *s, const float *x, const float *y, int64_t n
     const WeightCopies wc{{(int)Off::W1, (int)Off::W2, (int)Off::W3, (int)Off::W4},
                           {kHid * kInPad, kHid * kHid, kHid * kHid, kOutPad * kHid},
                           {s->W1b, s->W2b, s->W3b, s->W4b}};
-    if (launch_pdl(adam_update, dim3((unsigned)((Off::total + 255) / 256)), dim3(256), 0, st, s->master, s->m, s->v,
+    static_assert(Off::total % 4 == 0 && Off::W1 % 4 == 0 && Off::W2 % 4 == 0 && Off::W3 % 4 == 0 &&
+                      Off::W4 % 4 == 0 && (kHid * kInPad) % 4 == 0 && (kOutPad * kHid) % 4 == 0,
+                  "the Adam update takes four parameters a thread");
+    if (launch_pdl(adam_update, dim3((unsigned)((Off::total / 4 + 255) / 256)), dim3(256), 0, st, s->master, s->m, s->v,
                    s->grad, (int)Off::total, lr, s->beta1, s->beta2, s->eps, 1.0f / c1, 1.0f / std::sqrt(c2), wc,
                    s->avg_on ? s->avg : (float *)nullptr, s->avg_on ? 1.0f / (float)(s->avg_n + 1) : 0.0f) !=
         cudaSuccess)
