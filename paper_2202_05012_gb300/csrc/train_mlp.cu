@@ -6,15 +6,18 @@
 // Per layer and tile the tensor core takes the operand from shared memory,
 // the 16 epilogue warps turn its TMEM accumulator into the next operand.
 //
-// Gathers its minibatch rows itself (one warp packs the rows of x into the
-// input tile), and writes what the weight-gradient GEMM and the optimiser
-// need: every operand tile it builds -- the packed inputs, the activations
-// H1..H3, the output gradient d out and the hidden gradients G3..G1 -- leaves
-// shared memory row-major through TMA stores issued by one thread (the
-// weight-gradient GEMM reads them as MN-major operands, so no transposed copy
-// is written); GELU'(z) of the hidden layers (bf16 [B][256], two 16-byte
-// stores per thread and K-block, read back by the same thread in the
-// backward); the bias gradients (column sums) and the minibatch loss.  The
+// Gathers its minibatch rows of x itself (one warp packs them into the input
+// tile); the targets come staged by stage_targets (once an epoch) in the
+// order the loss phase reads them, each warp's loads whole 512-byte runs.
+// Writes what the weight-gradient GEMM and the optimiser need: every operand
+// tile it builds -- the packed inputs, the activations H1..H3, the output
+// gradient d out and the hidden gradients G3..G1 -- leaves shared memory
+// row-major through TMA stores issued by one thread (the weight-gradient GEMM
+// reads them as MN-major operands, so no transposed copy is written);
+// GELU'(z) of the hidden layers (bf16, B x 256, in thread order: each warp's
+// two 16-byte stores per K-block are whole 512-byte runs, read back by the
+// same thread in the backward); the bias gradients (column sums) and the
+// minibatch loss.  The
 // per-layer launches it replaces each gave every CTA one 128-row tile and
 // spent most of their 15-20 us on the latency of one tile's loads, MMAs and
 // stores.
